@@ -1,0 +1,507 @@
+/*
+ * FP64 CPU oracle for fast orthogonality deficiency compensated frequency
+ * selective extrapolation (FOFSE; Seiler & Kaup, arXiv 2207.01205).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the test suite, the package's smoke check and the
+ * benchmark's CPU-baseline leg use it.  It shares no code, header, table or
+ * constant with the CUDA implementation.
+ *
+ * The oracle follows the algorithm in the paper's order, in the spatial
+ * domain, re-projecting the weighted residual onto every 2-D DFT basis
+ * function in every iteration (as the original OFSE does), which is slow and
+ * obviously tied to the equations:
+ *
+ *   Sec. 2, Eq. 1-2   model g = sum c_k phi_k, built one basis pair per iteration
+ *   Sec. 2, Eq. 3     residual r = f - g on the support area A, 0 on B
+ *   Sec. 2, Eq. 4     weighting w = rho[m,n] on A, 0 on B
+ *   Sec. 4, Eq. 15    isotropic rho[m,n] = rho_hat ^ distance to the B centre
+ *   Sec. 2, Eq. 5     projection coefficient p_k = <r w, phi_k> / <w phi_k, phi_k>
+ *   Sec. 2, Eq. 7-9   selection u = argmax_k |T{r w}[k]|
+ *   Sec. 2, Eq. 14    constant compensation c_u = gamma * p_u
+ *
+ * Readings of points the paper leaves open:
+ *  - basis phi_k[m,n] = exp(+j 2 pi (k1 m + k2 n) / T) over a T x T grid with
+ *    the area L at its origin; the projection uses the conjugate basis, so
+ *    p_k = P[k] / W0 with P = unnormalised forward DFT of r*w and W0 = sum w
+ *    (|phi_k| = 1, so the Eq. 5 denominator is W0 for every k);
+ *  - a real model needs conjugate pairs: one iteration adds c_u phi_u and
+ *    conj(c_u) phi_{-u}, i.e. g += (1 + s(u)) Re(c_u phi_u), s(u) = 0 for the
+ *    four self-conjugate indices (2u = 0 mod T), whose coefficient is real;
+ *  - the argmax runs over the canonical set H = {k : k1 T + k2 <= (-k)1 T + (-k)2}
+ *    (one index per conjugate pair); exact ties go to the smallest k1 T + k2;
+ *  - the weighting centre is the centre of B; samples outside the frame,
+ *    in other lost blocks, or outside the chosen support shape get w = 0.
+ *
+ * Frozen-path companions (the selection sequence fixed, so the output is
+ * linear in f): a replay, a reverse-mode adjoint of the spatial recursion,
+ * and a forward-mode tangent in rho and gamma.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_NO_SUPPORT 1
+#define ORC_NONFINITE 2
+
+typedef struct {
+    int block;     /* lost block side b                         */
+    int border;    /* support border width                      */
+    int fft_size;  /* T                                         */
+    int iters;     /* I                                         */
+    int support;   /* 0 = full frame around B, 1 = causal L     */
+    double rho;    /* rho_hat of Eq. 15                         */
+    double gamma;  /* constant compensation factor of Eq. 14    */
+} oracle_plan;
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+/* s(u) = 0 for self-conjugate u (2u = 0 mod T in both coordinates), else 1. */
+static int pair_weight_s(int u1, int u2, int T) {
+    return ((2 * u1) % T == 0 && (2 * u2) % T == 0) ? 0 : 1;
+}
+
+/* k is in the canonical set H when its row-major index does not exceed its mirror's. */
+static int in_canonical_set(int k1, int k2, int T) {
+    int mk1 = (T - k1) % T, mk2 = (T - k2) % T;
+    return k1 * T + k2 <= mk1 * T + mk2;
+}
+
+static void twiddles(int T, double* c, double* s) {
+    for (int p = 0; p < T; ++p) {
+        c[p] = cos(TWO_PI * (double)p / (double)T);
+        s[p] = sin(TWO_PI * (double)p / (double)T);
+    }
+}
+
+/* -------------------------------------------------------------------------- */
+/* Geometry and weighting (Eq. 4, Eq. 15)                                      */
+/* -------------------------------------------------------------------------- */
+
+/* Distance of every sample of L to the centre of B (the centre of L when B is
+ * central).  L is Ls x Ls with B at rows/cols [border, border+block). */
+void oracle_distance(int block, int border, double* dist) {
+    int Ls = block + 2 * border;
+    double c = border + (block - 1) / 2.0;
+    for (int m = 0; m < Ls; ++m)
+        for (int n = 0; n < Ls; ++n)
+            dist[m * Ls + n] = sqrt((m - c) * (m - c) + (n - c) * (n - c));
+}
+
+/* Membership of (m, n) in the support shape (excluding B itself). */
+static int in_support_shape(int block, int border, int support, int m, int n) {
+    int inB = m >= border && m < border + block && n >= border && n < border + block;
+    if (inB) return 0;
+    if (support == 0) return 1;
+    /* causal L: everything above B's rows up to B's right edge, and left of B in B's rows */
+    if (m < border) return n < border + block;
+    if (m < border + block) return n < border;
+    return 0;
+}
+
+/* w[m,n] = rho_hat^dist on A, 0 elsewhere.  availL: 1 for usable samples of L. */
+void oracle_weights(int block, int border, int support, double rho, const unsigned char* availL,
+                    double* w) {
+    int Ls = block + 2 * border;
+    double* dist = (double*)malloc(sizeof(double) * Ls * Ls);
+    oracle_distance(block, border, dist);
+    for (int m = 0; m < Ls; ++m)
+        for (int n = 0; n < Ls; ++n) {
+            int i = m * Ls + n;
+            int inA = availL[i] && in_support_shape(block, border, support, m, n);
+            w[i] = inA ? pow(rho, dist[i]) : 0.0;
+        }
+    free(dist);
+}
+
+/* Cut the area L of a block out of the frame; samples outside the frame are
+ * unavailable (and read as 0). */
+void oracle_cut_area(const float* frame, const unsigned char* avail, int height, int width,
+                     int pitch, int y, int x, int block, int border, double* fL,
+                     unsigned char* aL) {
+    int Ls = block + 2 * border;
+    for (int m = 0; m < Ls; ++m)
+        for (int n = 0; n < Ls; ++n) {
+            int fy = y - border + m, fx = x - border + n;
+            int in = fy >= 0 && fy < height && fx >= 0 && fx < width;
+            fL[m * Ls + n] = in ? (double)frame[(size_t)fy * pitch + fx] : 0.0;
+            aL[m * Ls + n] = in ? avail[(size_t)fy * pitch + fx] : 0;
+        }
+}
+
+/* -------------------------------------------------------------------------- */
+/* Transform operator T of Eq. 8: all T^2 weighted projections                 */
+/* -------------------------------------------------------------------------- */
+
+/* P[k1,k2] = sum_{m,n in L} rw[m,n] exp(-j 2 pi (k1 m + k2 n) / T), computed
+ * separably (first along n, then along m) with twiddles from integer phases. */
+void oracle_project(int Ls, int T, const double* rw, double* P_re, double* P_im) {
+    double* c = (double*)malloc(sizeof(double) * T);
+    double* s = (double*)malloc(sizeof(double) * T);
+    double* Y_re = (double*)malloc(sizeof(double) * Ls * T);
+    double* Y_im = (double*)malloc(sizeof(double) * Ls * T);
+    twiddles(T, c, s);
+    for (int m = 0; m < Ls; ++m)
+        for (int k2 = 0; k2 < T; ++k2) {
+            double re = 0.0, im = 0.0;
+            for (int n = 0; n < Ls; ++n) {
+                int p = (k2 * n) % T;
+                re += rw[m * Ls + n] * c[p];
+                im -= rw[m * Ls + n] * s[p];
+            }
+            Y_re[m * T + k2] = re;
+            Y_im[m * T + k2] = im;
+        }
+    for (int k1 = 0; k1 < T; ++k1)
+        for (int k2 = 0; k2 < T; ++k2) {
+            double re = 0.0, im = 0.0;
+            for (int m = 0; m < Ls; ++m) {
+                int p = (k1 * m) % T;
+                double yr = Y_re[m * T + k2], yi = Y_im[m * T + k2];
+                /* (yr + j yi)(c - j s) */
+                re += yr * c[p] + yi * s[p];
+                im += yi * c[p] - yr * s[p];
+            }
+            P_re[k1 * T + k2] = re;
+            P_im[k1 * T + k2] = im;
+        }
+    free(c); free(s); free(Y_re); free(Y_im);
+}
+
+/* Selection of Eq. 9 over the canonical set H; returns the relative gap
+ * (best - runner-up) / best of |P|^2 over H through *gap. */
+void oracle_select(int T, const double* P_re, const double* P_im, int* u1, int* u2, double* gap) {
+    double best = -1.0, second = -1.0;
+    int bi = 0;
+    for (int k1 = 0; k1 < T; ++k1)
+        for (int k2 = 0; k2 < T; ++k2) {
+            if (!in_canonical_set(k1, k2, T)) continue;
+            int i = k1 * T + k2;
+            double v = P_re[i] * P_re[i] + P_im[i] * P_im[i];
+            if (v > best) {
+                second = best;
+                best = v;
+                bi = i;
+            } else if (v > second) {
+                second = v;
+            }
+        }
+    *u1 = bi / T;
+    *u2 = bi % T;
+    if (gap) *gap = best > 0.0 ? (best - (second < 0.0 ? 0.0 : second)) / best : 0.0;
+}
+
+/* g += (1 + s(u)) Re(c phi_u) over L (Eq. 2 with the conjugate partner). */
+static void add_basis_pair(int Ls, int T, const double* c, const double* s, int u1, int u2,
+                           double c_re, double c_im, double* g) {
+    double mult = 1.0 + pair_weight_s(u1, u2, T);
+    for (int m = 0; m < Ls; ++m)
+        for (int n = 0; n < Ls; ++n) {
+            int p = (u1 * m + u2 * n) % T;
+            g[m * Ls + n] += mult * (c_re * c[p] - c_im * s[p]);
+        }
+}
+
+/* -------------------------------------------------------------------------- */
+/* Extrapolation of one area (Sec. 2, Eq. 1-9, Eq. 14)                         */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * fL, wL: Ls x Ls samples and weights of L (w = 0 outside A).  Returns the
+ * status; on ORC_OK fills g (final model over L), the selection path, the
+ * coefficients c_u (dc) and the per-iteration relative gap.  Any of the path
+ * outputs may be NULL.
+ */
+int oracle_extrapolate_area(int Ls, int T, const double* fL, const double* wL, double gamma,
+                            int iters, double* g, int* path_u1, int* path_u2, double* dc_re,
+                            double* dc_im, double* gap, double* w0_out) {
+    int N = Ls * Ls;
+    double W0 = 0.0;
+    for (int i = 0; i < N; ++i) W0 += wL[i];
+    if (w0_out) *w0_out = W0;
+    for (int i = 0; i < N; ++i) g[i] = 0.0;            /* g^(0) = 0 */
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    for (int i = 0; i < N; ++i)
+        if (wL[i] != 0.0 && !isfinite(fL[i])) return ORC_NONFINITE;
+
+    double* c = (double*)malloc(sizeof(double) * T);
+    double* s = (double*)malloc(sizeof(double) * T);
+    double* rw = (double*)malloc(sizeof(double) * N);
+    double* P_re = (double*)malloc(sizeof(double) * T * T);
+    double* P_im = (double*)malloc(sizeof(double) * T * T);
+    twiddles(T, c, s);
+    for (int it = 0; it < iters; ++it) {
+        /* Eq. 3 and Eq. 7: weighted residual, zero outside A */
+        for (int i = 0; i < N; ++i) rw[i] = wL[i] != 0.0 ? wL[i] * (fL[i] - g[i]) : 0.0;
+        /* Eq. 8: decomposition onto every basis function */
+        oracle_project(Ls, T, rw, P_re, P_im);
+        /* Eq. 9 */
+        int u1, u2;
+        double gp;
+        oracle_select(T, P_re, P_im, &u1, &u2, &gp);
+        /* Eq. 5 (p_u = P[u] / W0) and Eq. 14 (c_u = gamma p_u) */
+        int ui = u1 * T + u2;
+        double cr = gamma * P_re[ui] / W0;
+        double ci = pair_weight_s(u1, u2, T) ? gamma * P_im[ui] / W0 : 0.0;
+        /* Eq. 2 */
+        add_basis_pair(Ls, T, c, s, u1, u2, cr, ci, g);
+        if (path_u1) path_u1[it] = u1;
+        if (path_u2) path_u2[it] = u2;
+        if (dc_re) dc_re[it] = cr;
+        if (dc_im) dc_im[it] = ci;
+        if (gap) gap[it] = gp;
+    }
+    free(c); free(s); free(rw); free(P_re); free(P_im);
+    return ORC_OK;
+}
+
+/* -------------------------------------------------------------------------- */
+/* Frozen-path companions                                                      */
+/* -------------------------------------------------------------------------- */
+
+/* The coefficient of iteration i along a fixed path: c = gamma * P[u] / W0 with
+ * P[u] the weighted projection of the current residual onto phi_u. */
+static void project_one(int Ls, int T, const double* c, const double* s, const double* rw, int u1,
+                        int u2, double* p_re, double* p_im) {
+    double re = 0.0, im = 0.0;
+    for (int m = 0; m < Ls; ++m)
+        for (int n = 0; n < Ls; ++n) {
+            int p = (u1 * m + u2 * n) % T;
+            re += rw[m * Ls + n] * c[p];
+            im -= rw[m * Ls + n] * s[p];
+        }
+    *p_re = re;
+    *p_im = im;
+}
+
+/* Forward pass along a given path (no selection).  g_hist, if non-NULL,
+ * receives g^(0..iters-1) (the model before each iteration), iters * Ls^2. */
+int oracle_replay_area(int Ls, int T, const double* fL, const double* wL, double gamma, int iters,
+                       const int* u1, const int* u2, double* g, double* dc_re, double* dc_im,
+                       double* g_hist) {
+    int N = Ls * Ls;
+    double W0 = 0.0;
+    for (int i = 0; i < N; ++i) W0 += wL[i];
+    for (int i = 0; i < N; ++i) g[i] = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    double* c = (double*)malloc(sizeof(double) * T);
+    double* s = (double*)malloc(sizeof(double) * T);
+    double* rw = (double*)malloc(sizeof(double) * N);
+    twiddles(T, c, s);
+    for (int it = 0; it < iters; ++it) {
+        if (g_hist) memcpy(g_hist + (size_t)it * N, g, sizeof(double) * N);
+        for (int i = 0; i < N; ++i) rw[i] = wL[i] != 0.0 ? wL[i] * (fL[i] - g[i]) : 0.0;
+        double pr, pi;
+        project_one(Ls, T, c, s, rw, u1[it], u2[it], &pr, &pi);
+        double cr = gamma * pr / W0;
+        double ci = pair_weight_s(u1[it], u2[it], T) ? gamma * pi / W0 : 0.0;
+        add_basis_pair(Ls, T, c, s, u1[it], u2[it], cr, ci, g);
+        if (dc_re) dc_re[it] = cr;
+        if (dc_im) dc_im[it] = ci;
+    }
+    free(c); free(s); free(rw);
+    return ORC_OK;
+}
+
+/*
+ * Reverse-mode adjoint of the spatial recursion along a fixed path.
+ *   gbar_out: adjoint of the final model g^(I) over L (Ls x Ls), e.g. dloss/dB on B, 0 elsewhere.
+ * Outputs: fbar (Ls x Ls, nonzero only on A), wbar (Ls x Ls, on A), gammabar.
+ * rho enters only through w; the caller chains wbar to rho (rhobar below).
+ */
+int oracle_adjoint_area(int Ls, int T, const double* fL, const double* wL, double gamma,
+                        int iters, const int* u1, const int* u2, const double* gbar_out,
+                        double* fbar, double* wbar, double* gammabar) {
+    int N = Ls * Ls;
+    double W0 = 0.0;
+    for (int i = 0; i < N; ++i) W0 += wL[i];
+    for (int i = 0; i < N; ++i) fbar[i] = wbar[i] = 0.0;
+    *gammabar = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    double* c = (double*)malloc(sizeof(double) * T);
+    double* s = (double*)malloc(sizeof(double) * T);
+    double* g = (double*)malloc(sizeof(double) * N);
+    double* gh = (double*)malloc(sizeof(double) * (size_t)iters * N);
+    double* dcr = (double*)malloc(sizeof(double) * iters);
+    double* dci = (double*)malloc(sizeof(double) * iters);
+    double* gbar = (double*)malloc(sizeof(double) * N);
+    double* q = (double*)malloc(sizeof(double) * N);
+    twiddles(T, c, s);
+    oracle_replay_area(Ls, T, fL, wL, gamma, iters, u1, u2, g, dcr, dci, gh);
+    memcpy(gbar, gbar_out, sizeof(double) * N);
+    double W0bar = 0.0;
+    for (int it = iters - 1; it >= 0; --it) {
+        int a1 = u1[it], a2 = u2[it];
+        int sp = pair_weight_s(a1, a2, T);
+        double mult = 1.0 + sp;
+        const double* gprev = gh + (size_t)it * N;
+        /* g_it = g_prev + mult (c_re cos - c_im sin): adjoint of the coefficient */
+        double cbar_re = 0.0, cbar_im = 0.0;
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) {
+                int p = (a1 * m + a2 * n) % T;
+                cbar_re += mult * gbar[m * Ls + n] * c[p];
+                cbar_im -= mult * gbar[m * Ls + n] * s[p];
+            }
+        if (!sp) cbar_im = 0.0;               /* the self-conjugate coefficient is real */
+        /* c = gamma p / W0 */
+        double p_re = dcr[it] * W0 / gamma, p_im = dci[it] * W0 / gamma;
+        *gammabar += (cbar_re * p_re + cbar_im * p_im) / W0;
+        W0bar -= (cbar_re * dcr[it] + cbar_im * dci[it]) / W0;
+        double pbar_re = gamma / W0 * cbar_re, pbar_im = gamma / W0 * cbar_im;
+        /* p_re = sum rw cos, p_im = -sum rw sin, rw = w (f - g_prev) on A */
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) {
+                int p = (a1 * m + a2 * n) % T;
+                q[m * Ls + n] = pbar_re * c[p] - pbar_im * s[p];
+            }
+        for (int i = 0; i < N; ++i) {
+            if (wL[i] == 0.0) continue;
+            fbar[i] += wL[i] * q[i];
+            gbar[i] -= wL[i] * q[i];
+            wbar[i] += (fL[i] - gprev[i]) * q[i];
+        }
+    }
+    for (int i = 0; i < N; ++i)
+        if (wL[i] != 0.0) wbar[i] += W0bar;    /* W0 = sum of w over A */
+    free(c); free(s); free(g); free(gh); free(dcr); free(dci); free(gbar); free(q);
+    return ORC_OK;
+}
+
+/* rho_bar = sum_A wbar * d/d rho (rho^dist) = sum_A wbar * dist * rho^(dist - 1). */
+double oracle_rho_chain(int N, const double* wL, const double* dist, double rho, const double* wbar) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i)
+        if (wL[i] != 0.0) acc += wbar[i] * dist[i] * pow(rho, dist[i] - 1.0);
+    return acc;
+}
+
+/*
+ * Forward-mode tangent along a fixed path: derivative of the final model over
+ * L with respect to a perturbation (w_dot, gamma_dot); w_dot = dist rho^(dist-1)
+ * on A for d/d rho.
+ */
+int oracle_tangent_area(int Ls, int T, const double* fL, const double* wL, const double* wdot,
+                        double gamma, double gamma_dot, int iters, const int* u1, const int* u2,
+                        double* gdot) {
+    int N = Ls * Ls;
+    double W0 = 0.0, W0dot = 0.0;
+    for (int i = 0; i < N; ++i) {
+        W0 += wL[i];
+        if (wL[i] != 0.0) W0dot += wdot[i];
+    }
+    for (int i = 0; i < N; ++i) gdot[i] = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    double* c = (double*)malloc(sizeof(double) * T);
+    double* s = (double*)malloc(sizeof(double) * T);
+    double* g = (double*)calloc(N, sizeof(double));
+    double* rw = (double*)malloc(sizeof(double) * N);
+    double* rwdot = (double*)malloc(sizeof(double) * N);
+    twiddles(T, c, s);
+    for (int it = 0; it < iters; ++it) {
+        for (int i = 0; i < N; ++i) {
+            if (wL[i] == 0.0) {
+                rw[i] = rwdot[i] = 0.0;
+            } else {
+                rw[i] = wL[i] * (fL[i] - g[i]);
+                rwdot[i] = wdot[i] * (fL[i] - g[i]) - wL[i] * gdot[i];
+            }
+        }
+        double pr, pi, pdr, pdi;
+        project_one(Ls, T, c, s, rw, u1[it], u2[it], &pr, &pi);
+        project_one(Ls, T, c, s, rwdot, u1[it], u2[it], &pdr, &pdi);
+        int sp = pair_weight_s(u1[it], u2[it], T);
+        double cr = gamma * pr / W0, ci = sp ? gamma * pi / W0 : 0.0;
+        double cdr = gamma_dot * pr / W0 + gamma * pdr / W0 - gamma * pr * W0dot / (W0 * W0);
+        double cdi = sp ? gamma_dot * pi / W0 + gamma * pdi / W0 - gamma * pi * W0dot / (W0 * W0) : 0.0;
+        add_basis_pair(Ls, T, c, s, u1[it], u2[it], cr, ci, g);
+        add_basis_pair(Ls, T, c, s, u1[it], u2[it], cdr, cdi, gdot);
+    }
+    free(c); free(s); free(g); free(rw); free(rwdot);
+    return ORC_OK;
+}
+
+/* -------------------------------------------------------------------------- */
+/* Whole batches of lost blocks (independent; threads over blocks)            */
+/* -------------------------------------------------------------------------- */
+
+typedef struct {
+    const float* frame;
+    const unsigned char* avail;
+    int height, width, pitch;
+    const int* blocks;          /* n x 3: y, x, plan */
+    const oracle_plan* plans;
+    int n_blocks;
+    int out_stride;             /* floats per block in out_blocks */
+    int trace_stride;           /* entries per block in the path arrays */
+    double* out_blocks;         /* n x out_stride, B row-major b x b */
+    int* status;                /* n */
+    double* w0;                 /* n */
+    int* path_u1;               /* n x trace_stride (nullable) */
+    int* path_u2;
+    double* dc_re;
+    double* dc_im;
+    double* gap;
+    int next;                   /* work counter */
+    pthread_mutex_t lock;
+} batch_job;
+
+static void run_one(batch_job* J, int bi) {
+    const int* bd = J->blocks + 3 * bi;
+    const oracle_plan* P = J->plans + bd[2];
+    int Ls = P->block + 2 * P->border, N = Ls * Ls;
+    double* fL = (double*)malloc(sizeof(double) * N);
+    double* wL = (double*)malloc(sizeof(double) * N);
+    double* g = (double*)malloc(sizeof(double) * N);
+    unsigned char* aL = (unsigned char*)malloc(N);
+    oracle_cut_area(J->frame, J->avail, J->height, J->width, J->pitch, bd[0], bd[1], P->block,
+                    P->border, fL, aL);
+    oracle_weights(P->block, P->border, P->support, P->rho, aL, wL);
+    size_t to = (size_t)bi * J->trace_stride;
+    int st = oracle_extrapolate_area(
+        Ls, P->fft_size, fL, wL, P->gamma, P->iters, g, J->path_u1 ? J->path_u1 + to : NULL,
+        J->path_u2 ? J->path_u2 + to : NULL, J->dc_re ? J->dc_re + to : NULL,
+        J->dc_im ? J->dc_im + to : NULL, J->gap ? J->gap + to : NULL, J->w0 ? J->w0 + bi : NULL);
+    J->status[bi] = st;
+    double* ob = J->out_blocks + (size_t)bi * J->out_stride;
+    for (int m = 0; m < P->block; ++m)
+        for (int n = 0; n < P->block; ++n)
+            ob[m * P->block + n] = g[(m + P->border) * Ls + (n + P->border)];
+    free(fL); free(wL); free(g); free(aL);
+}
+
+static void* batch_worker(void* arg) {
+    batch_job* J = (batch_job*)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int bi = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (bi >= J->n_blocks) break;
+        run_one(J, bi);
+    }
+    return NULL;
+}
+
+/* Extrapolate every listed block of a frame; returns the number of threads used. */
+int oracle_batch(const float* frame, const unsigned char* avail, int height, int width, int pitch,
+                 const int* blocks, int n_blocks, const oracle_plan* plans, int out_stride,
+                 int trace_stride, double* out_blocks, int* status, double* w0, int* path_u1,
+                 int* path_u2, double* dc_re, double* dc_im, double* gap, int n_threads) {
+    batch_job J;
+    J.frame = frame; J.avail = avail; J.height = height; J.width = width; J.pitch = pitch;
+    J.blocks = blocks; J.plans = plans; J.n_blocks = n_blocks; J.out_stride = out_stride;
+    J.trace_stride = trace_stride; J.out_blocks = out_blocks; J.status = status; J.w0 = w0;
+    J.path_u1 = path_u1; J.path_u2 = path_u2; J.dc_re = dc_re; J.dc_im = dc_im; J.gap = gap;
+    J.next = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_blocks) n_threads = n_blocks > 0 ? n_blocks : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, batch_worker, &J);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.lock);
+    return n_threads;
+}
