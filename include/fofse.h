@@ -1,0 +1,183 @@
+/*
+ * fofse.h -- C ABI of the GB300 (sm_103a) implementation of fast
+ * orthogonality deficiency compensated frequency selective extrapolation
+ * (FOFSE; J. Seiler and A. Kaup, arXiv 2207.01205).
+ *
+ * What the library computes (per lost block; paper Sec. 2 and Sec. 4):
+ *   L     the area of the lost b x b block B plus a border of `border`
+ *         samples on each side (Fig. 1); A = the usable samples of L outside B.
+ *   w     w[m,n] = rho^dist[m,n] on A, 0 elsewhere (Eq. 4 with the isotropic
+ *         model of Eq. 15), dist = Euclidean distance to the centre of B.
+ *   R_w   = DFT_TxT(w f), W = DFT_TxT(w), L placed at the origin of a T x T
+ *         grid (T = fft_size), unnormalised forward DFT (the transform
+ *         operator of Eq. 8 for the 2-D DFT basis; "complete formulation in
+ *         the transform domain", end of Sec. 2).
+ *   loop  iters times: u = argmax |R_w[k]| over one index of every conjugate
+ *         pair (Eq. 9); c = gamma * R_w[u] / W[0] (Eq. 5 and Eq. 14);
+ *         R_w[k] -= c W[k-u] + s(u) conj(c) W[k+u]  (the spectrum of the
+ *         added basis pair, Eq. 2-3 and Eq. 7), s(u) = 0 for the four
+ *         self-conjugate indices (2u = 0 mod T), else 1.
+ *   out   B_hat[m,n] = sum_i (1 + s(u_i)) Re(c_i exp(+j 2 pi (u_i . (m,n)) / T))
+ *         over B (Eq. 1).
+ * Readings of points the paper leaves open: the argmax runs over the
+ * canonical set H = {k : k1 T + k2 <= (-k)1 T + (-k)2} and exact ties go to
+ * the smallest k1 T + k2; the coefficient of a self-conjugate index is real;
+ * samples outside the frame, in other lost blocks or outside the chosen
+ * support shape are not in A.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are DEVICE memory owned by the caller, on the device
+ *    that was current when the plans were created.  The library never
+ *    allocates or frees memory on the launch path (plans allocate their small
+ *    constant tables once, in fofse_plan_create).
+ *  - Frames are row-major float32 with `pitch` elements per row; availability
+ *    masks are uint8 (1 = usable sample, 0 = lost) with the same pitch.
+ *  - Argument errors are reported synchronously through the return value and
+ *    nothing is launched.  Per-block conditions go to d_block_status.  Device
+ *    faults the kernels detect themselves (a bounded wait that ran out) set a
+ *    device error word read by fofse_check.  No kernel traps.
+ *  - All launches go to `stream` (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream) and are asynchronous.
+ */
+#ifndef FOFSE_H_
+#define FOFSE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fofse_plan_s* fofse_plan;
+
+typedef enum {
+  FOFSE_OK = 0,
+  FOFSE_E_ARG = 1,          /* invalid argument (null pointer, size, range)        */
+  FOFSE_E_UNSUPPORTED = 2,  /* valid but not implemented (e.g. fft_size 256)       */
+  FOFSE_E_NOMEM = 3,        /* plan table allocation failed                        */
+  FOFSE_E_CUDA = 4,         /* a CUDA runtime call failed                          */
+  FOFSE_E_TIMEOUT = 5,      /* a device-side bounded wait ran out (fofse_check)    */
+  FOFSE_E_STATE = 6         /* call out of order                                   */
+} fofse_status;
+
+/* support shapes: which part of L may be in A */
+enum { FOFSE_SUPPORT_FULL = 0,      /* all of L outside B (concealment)                 */
+       FOFSE_SUPPORT_CAUSAL_L = 1 }; /* rows above B up to B's right edge, plus the
+                                        samples left of B in B's rows (prediction)      */
+/* arithmetic of the kernels */
+enum { FOFSE_FP32 = 0,           /* compensated float-float (pairs of FP32): the product */
+       FOFSE_FP64_VALIDATE = 1,  /* IEEE double; slow on GB300, for validation           */
+       FOFSE_FP32_PLAIN = 2 };   /* plain FP32; diverges from the exact selection path at
+                                    near-ties, kept for comparison                       */
+/* per-block status written to d_block_status */
+enum { FOFSE_BLK_OK = 0, FOFSE_BLK_NO_SUPPORT = 1, FOFSE_BLK_NONFINITE = 2 };
+
+/* One lost block: top-left corner of B in the frame and the plan index. */
+typedef struct {
+  int32_t y, x;
+  int32_t plan;
+} fofse_block;
+
+/* One iteration of the selection path: canonical index u (0 <= u1, u2 < T)
+ * and the coefficient c = gamma R_w[u] / W[0], rounded to FP32. */
+typedef struct {
+  int16_t u1, u2;
+  float dc_re, dc_im;
+} fofse_trace_entry;
+
+/*
+ * fofse_plan_create -- parameters of one block class (paper Sec. 4:
+ * 16 x 16 blocks, border 16, 64 x 64 FFT, rho 0.8, gamma, iterations).
+ *   block     lost block side b, 1 <= b
+ *   border    support border width, 0 <= border
+ *   fft_size  T in {32, 64}, T >= block + 2 * border
+ *   rho       rho_hat of Eq. 15, 0 < rho <= 1
+ *   gamma     constant compensation factor of Eq. 14, 0 < gamma <= 1
+ *   iters     number of iterations I, 1 <= I <= 4096
+ * Builds the plan's constant tables (rho^dist in FP64, split into float pairs;
+ * DFT twiddles from integer phases) in device memory of the current device.
+ * Returns FOFSE_E_ARG for invalid values, FOFSE_E_UNSUPPORTED for a valid but
+ * unimplemented fft_size, FOFSE_E_NOMEM / FOFSE_E_CUDA if the tables cannot
+ * be allocated.  *out is set only on FOFSE_OK.  Plans are immutable during a
+ * launch and may be shared by concurrent launches.
+ */
+fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, float gamma,
+                               int iters, fofse_plan* out);
+/* Support shape (FOFSE_SUPPORT_*); default FULL.  FOFSE_E_ARG for other values. */
+fofse_status fofse_plan_set_support(fofse_plan plan, int shape);
+/* Arithmetic (FOFSE_FP32 default, FOFSE_FP64_VALIDATE, FOFSE_FP32_PLAIN). */
+fofse_status fofse_plan_set_precision(fofse_plan plan, int precision);
+/* Frees the plan's tables (synchronises the device).  NULL is ignored. */
+void fofse_plan_destroy(fofse_plan plan);
+
+/*
+ * fofse_workspace_bytes -- device scratch needed by fofse_extrapolate_batch and
+ * fofse_backward for this batch (work-queue counters).  Returns 0 for invalid
+ * arguments.
+ */
+size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks);
+
+/*
+ * fofse_extrapolate_batch -- extrapolate every block of d_blocks (forward).
+ *   plans, n_plans     host array of plans; d_blocks[i].plan indexes it
+ *   d_blocks           device array of n_blocks fofse_block; B must lie inside
+ *                      the frame (the rest of L may extend beyond it)
+ *   d_frame, d_avail   device frame (float32) and availability (uint8),
+ *                      height x width, `pitch` elements per row; the values of
+ *                      unavailable samples are never read into the arithmetic
+ *   d_rho_gamma        must be NULL (device-side overrides are not implemented;
+ *                      FOFSE_E_UNSUPPORTED otherwise)
+ *   d_out_frame        nullable; B_hat is written into it at each block (other
+ *                      samples untouched); may alias d_frame only if no block's
+ *                      L overlaps another block's B
+ *   d_out_blocks       nullable; n_blocks x out_stride floats, out_stride =
+ *                      (max block side over the plans)^2; B_hat row-major b x b
+ *   d_trace, d_w0      nullable; n_blocks x max_iters entries / n_blocks floats
+ *                      (W[0] = sum of w); required for fofse_backward
+ *   d_block_status     nullable; n_blocks int32 (FOFSE_BLK_*).  Blocks that are
+ *                      not OK get B_hat = 0 and an all-zero trace
+ *   d_workspace        fofse_workspace_bytes() bytes (may be NULL if that is 0)
+ *   stream             cudaStream_t
+ * All plans of one call must share the precision.  Returns FOFSE_OK once the
+ * work is queued.
+ */
+fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
+                                     const fofse_block* d_blocks, int n_blocks,
+                                     const float* d_frame, const uint8_t* d_avail, int height,
+                                     int width, int pitch, const float* d_rho_gamma,
+                                     float* d_out_frame, float* d_out_blocks,
+                                     fofse_trace_entry* d_trace, float* d_w0,
+                                     int32_t* d_block_status, void* d_workspace, void* stream);
+
+/*
+ * fofse_backward -- adjoint of fofse_extrapolate_batch with the selection path
+ * frozen (the map from the support samples to B_hat is then linear).
+ *   d_trace, d_w0      from the forward call with the same inputs
+ *   d_grad_blocks      dloss/dB_hat, n_blocks x out_stride (as d_out_blocks)
+ *   d_grad_frame       nullable; dloss/df ACCUMULATED (+=) at every sample of A
+ *   d_grad_rho_gamma   nullable; n_plans x 2 floats, ACCUMULATED (+=)
+ * Not implemented for FOFSE_FP64_VALIDATE plans (FOFSE_E_UNSUPPORTED).
+ */
+fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_block* d_blocks,
+                            int n_blocks, const float* d_frame, const uint8_t* d_avail,
+                            int height, int width, int pitch, const float* d_rho_gamma,
+                            const fofse_trace_entry* d_trace, const float* d_w0,
+                            const float* d_grad_blocks, float* d_grad_frame,
+                            float* d_grad_rho_gamma, void* d_workspace, void* stream);
+
+/* Synchronises `stream`, then reads and clears the device error word of the
+ * current device: FOFSE_OK, FOFSE_E_TIMEOUT, or FOFSE_E_CUDA if the stream
+ * reported an error. */
+fofse_status fofse_check(void* stream);
+
+/* Static, human-readable name of a status code. */
+const char* fofse_status_string(fofse_status status);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int fofse_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FOFSE_H_ */

@@ -1,0 +1,88 @@
+"""Python-level API over the C ABI: plans as objects and batch calls that
+allocate their outputs with torch on the frame's device."""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+TRACE_DTYPE = np.dtype([("u1", "<i2"), ("u2", "<i2"), ("re", "<f4"), ("im", "<f4")])
+
+
+class Plan:
+    """One block class: b x b lost blocks, support border, T x T FFT, rho_hat,
+    gamma and the number of iterations (paper Sec. 4 notation)."""
+
+    def __init__(self, block, border, fft_size, rho, gamma, iters, support=0, precision="fp32"):
+        self.block, self.border, self.fft_size = int(block), int(border), int(fft_size)
+        self.rho, self.gamma, self.iters = float(rho), float(gamma), int(iters)
+        self.support = int(support)
+        self.precision = precision
+        self.handle = B.fofse_plan_create(block, border, fft_size, rho, gamma, iters)
+        try:
+            B.fofse_plan_set_support(self.handle, self.support)
+            B.fofse_plan_set_precision(self.handle, B.PRECISIONS[precision])
+        except Exception:
+            B.fofse_plan_destroy(self.handle)
+            raise
+
+    @classmethod
+    def from_spec(cls, spec, precision="fp32"):
+        return cls(spec.block, spec.border, spec.fft_size, spec.rho, spec.gamma, spec.iters,
+                   getattr(spec, "support", 0), precision)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.fofse_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclasses.dataclass
+class Result:
+    blocks: torch.Tensor       # (n, bmax, bmax) float32
+    trace: torch.Tensor        # (n, imax, 3) int32 storage of fofse_trace_entry
+    w0: torch.Tensor           # (n,) float32
+    status: torch.Tensor       # (n,) int32
+    out_frame: torch.Tensor | None = None
+
+    def trace_numpy(self):
+        return self.trace.cpu().numpy().view(TRACE_DTYPE).reshape(self.trace.shape[:2])
+
+    def path(self):
+        t = self.trace_numpy()
+        return np.stack([t["u1"], t["u2"]], axis=-1).astype(np.int32)
+
+    def dc(self):
+        t = self.trace_numpy()
+        return t["re"].astype(np.float64) + 1j * t["im"].astype(np.float64)
+
+
+def alloc_outputs(plans, n, device, with_trace=True):
+    bmax = max(p.block for p in plans)
+    imax = max(p.iters for p in plans)
+    blocks = torch.empty((n, bmax, bmax), dtype=torch.float32, device=device)
+    trace = torch.empty((n, imax, 3), dtype=torch.int32, device=device) if with_trace else None
+    w0 = torch.empty((n,), dtype=torch.float32, device=device)
+    status = torch.empty((n,), dtype=torch.int32, device=device)
+    return blocks, trace, w0, status
+
+
+def extrapolate(plans, blocks, frame, avail, *, out_frame=None, with_trace=True, stream=None) -> Result:
+    """Run the forward pass of every block.  ``blocks``: (n, 3) int32 tensor on
+    the device (y, x, plan index); ``frame`` float32 and ``avail`` uint8 (H, W)
+    tensors on the same device."""
+    plans = list(plans)
+    n = int(blocks.shape[0])
+    ob, tr, w0, st = alloc_outputs(plans, n, frame.device, with_trace)
+    B.fofse_extrapolate_batch([p.handle for p in plans], blocks, frame, avail, out_frame=out_frame,
+                              out_blocks=ob, trace=tr, w0=w0, status=st, stream=stream)
+    return Result(ob, tr, w0, st, out_frame)

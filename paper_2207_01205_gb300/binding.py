@@ -1,0 +1,183 @@
+"""Thin ctypes binding of the C ABI in ``include/fofse.h`` (same names).
+
+Argument marshalling only: every step of the extrapolation runs in the CUDA
+kernels of ``libfofse.so``.  Device buffers are torch tensors (PyTorch is used
+for device memory and streams).  There is no CPU fallback: if the library
+cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+from . import build as _build
+
+OK, E_ARG, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_STATE = range(7)
+SUPPORT_FULL, SUPPORT_CAUSAL_L = 0, 1
+FP32, FP64_VALIDATE, FP32_PLAIN = 0, 1, 2
+BLK_OK, BLK_NO_SUPPORT, BLK_NONFINITE, BLK_TIMEOUT = 0, 1, 2, 3
+PRECISIONS = {"fp32": FP32, "fp64": FP64_VALIDATE, "fp32_plain": FP32_PLAIN}
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "fofse.h")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FofseError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.fofse_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("u1", ctypes.c_int16), ("u2", ctypes.c_int16), ("dc_re", ctypes.c_float),
+                ("dc_im", ctypes.c_float)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/fofse.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fofse_\w+)\s*\(", txt)))
+
+
+def _declare(L):
+    L.fofse_status_string.argtypes = [_i]
+    L.fofse_status_string.restype = ctypes.c_char_p
+    L.fofse_version.restype = _i
+    L.fofse_plan_create.argtypes = [_i, _i, _i, ctypes.c_float, ctypes.c_float, _i,
+                                    ctypes.POINTER(_vp)]
+    L.fofse_plan_create.restype = _i
+    L.fofse_plan_set_support.argtypes = [_vp, _i]
+    L.fofse_plan_set_support.restype = _i
+    L.fofse_plan_set_precision.argtypes = [_vp, _i]
+    L.fofse_plan_set_precision.restype = _i
+    L.fofse_plan_destroy.argtypes = [_vp]
+    L.fofse_plan_destroy.restype = None
+    L.fofse_workspace_bytes.argtypes = [ctypes.POINTER(_vp), _i, _i]
+    L.fofse_workspace_bytes.restype = ctypes.c_size_t
+    L.fofse_extrapolate_batch.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i,
+                                          _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.fofse_extrapolate_batch.restype = _i
+    L.fofse_backward.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i, _vp, _vp,
+                                 _vp, _vp, _vp, _vp, _vp, _vp]
+    L.fofse_backward.restype = _i
+    L.fofse_check.argtypes = [_vp]
+    L.fofse_check.restype = _i
+
+
+def load(build: bool = True):
+    """Load ``libfofse.so`` (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libfofse.so not built ({path})")
+            L = ctypes.CDLL(path)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(st, where):
+    if st != OK:
+        raise FofseError(st, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+# ----------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# ----------------------------------------------------------------------------
+
+def fofse_status_string(status: int) -> str:
+    return load().fofse_status_string(status).decode()
+
+
+def fofse_version() -> int:
+    return load().fofse_version()
+
+
+def fofse_plan_create(block, border, fft_size, rho, gamma, iters) -> int:
+    h = ctypes.c_void_p()
+    _check(load().fofse_plan_create(int(block), int(border), int(fft_size), float(rho),
+                                    float(gamma), int(iters), ctypes.byref(h)), "fofse_plan_create")
+    return h.value
+
+
+def fofse_plan_set_support(plan, shape):
+    _check(load().fofse_plan_set_support(ctypes.c_void_p(plan), int(shape)), "fofse_plan_set_support")
+
+
+def fofse_plan_set_precision(plan, precision):
+    _check(load().fofse_plan_set_precision(ctypes.c_void_p(plan), int(precision)),
+           "fofse_plan_set_precision")
+
+
+def fofse_plan_destroy(plan):
+    if plan:
+        load().fofse_plan_destroy(ctypes.c_void_p(plan))
+
+
+def _plan_array(plans):
+    arr = (ctypes.c_void_p * len(plans))()
+    for i, p in enumerate(plans):
+        arr[i] = p
+    return arr
+
+
+def fofse_workspace_bytes(plans, n_blocks) -> int:
+    return load().fofse_workspace_bytes(_plan_array(plans), len(plans), int(n_blocks))
+
+
+def fofse_extrapolate_batch(plans, blocks, frame, avail, *, out_frame=None, out_blocks=None,
+                            trace=None, w0=None, status=None, workspace=None, rho_gamma=None,
+                            stream=None):
+    """blocks: (n, 3) int32 device tensor; frame float32 and avail uint8 device
+    tensors of shape (H, W) (row pitch = stride(0))."""
+    H, W = frame.shape
+    pitch = frame.stride(0)
+    assert frame.stride(1) == 1 and avail.stride(1) == 1 and avail.stride(0) == pitch
+    _check(load().fofse_extrapolate_batch(
+        _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
+        _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(out_frame), _ptr(out_blocks), _ptr(trace),
+        _ptr(w0), _ptr(status), _ptr(workspace), _stream(stream)), "fofse_extrapolate_batch")
+
+
+def fofse_backward(plans, blocks, frame, avail, trace, w0, grad_blocks, *, grad_frame=None,
+                   grad_rho_gamma=None, workspace=None, rho_gamma=None, stream=None):
+    H, W = frame.shape
+    pitch = frame.stride(0)
+    _check(load().fofse_backward(
+        _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
+        _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(trace), _ptr(w0), _ptr(grad_blocks),
+        _ptr(grad_frame), _ptr(grad_rho_gamma), _ptr(workspace), _stream(stream)), "fofse_backward")
+
+
+def fofse_check(stream=None):
+    _check(load().fofse_check(_stream(stream)), "fofse_check")

@@ -1,0 +1,359 @@
+// Host side of the C ABI declared in include/fofse.h: plan construction
+// (constant tables computed in FP64 on the host), argument validation,
+// TMA tensor-map encoding, kernel dispatch and the device error word.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fofse_internal.h"
+
+using namespace fofse;
+
+struct fofse_plan_s {
+  PlanDev dev;   // scalars + device table pointers
+  void* mem;     // one device allocation holding every table
+  int device;
+};
+
+namespace {
+
+__device__ unsigned g_err_word;  // device error word (FOFSE kErr* bits)
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kMaxIters = 4096;
+
+unsigned* err_word_ptr() {
+  static std::mutex mu;
+  static unsigned* cache[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cache[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_err_word) != cudaSuccess) return nullptr;
+    cache[dev] = static_cast<unsigned*>(p);
+  }
+  return cache[dev];
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool encode_2d(CUtensorMap* map, CUtensorMapDataType ty, int esize, const void* base, int width,
+               int height, int pitch, int box_w, int box_h) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)height};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * (cuuint64_t)esize};
+  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, ty, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+bool supported_T(int T) { return T == 32 || T == 64; }
+
+}  // namespace
+
+extern "C" {
+
+const char* fofse_status_string(fofse_status s) {
+  switch (s) {
+    case FOFSE_OK: return "ok";
+    case FOFSE_E_ARG: return "invalid argument";
+    case FOFSE_E_UNSUPPORTED: return "unsupported configuration";
+    case FOFSE_E_NOMEM: return "out of device memory";
+    case FOFSE_E_CUDA: return "CUDA error";
+    case FOFSE_E_TIMEOUT: return "device wait timed out";
+    case FOFSE_E_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+int fofse_version(void) { return 100; }
+
+fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, float gamma,
+                               int iters, fofse_plan* out) {
+  if (!out) return FOFSE_E_ARG;
+  if (block < 1 || border < 0 || iters < 1 || iters > kMaxIters) return FOFSE_E_ARG;
+  if (!(rho > 0.f && rho <= 1.f) || !(gamma > 0.f && gamma <= 1.f)) return FOFSE_E_ARG;
+  if (fft_size < 2 || (fft_size & (fft_size - 1)) != 0) return FOFSE_E_ARG;
+  const int Ls = block + 2 * border;
+  if (fft_size < Ls) return FOFSE_E_ARG;
+  if (!supported_T(fft_size)) return FOFSE_E_UNSUPPORTED;
+  const int T = fft_size;
+  const int N = Ls * Ls;
+
+  // host tables in FP64, split or rounded for each back-end
+  std::vector<float2> w_ff(N);
+  std::vector<double> w_f64(N);
+  std::vector<float> w_f32(N);
+  const double c = border + (block - 1) / 2.0;
+  for (int m = 0; m < Ls; ++m)
+    for (int n = 0; n < Ls; ++n) {
+      const double d = std::sqrt((m - c) * (m - c) + (n - c) * (n - c));
+      const double w = std::pow((double)rho, d);  // Eq. 15
+      const float hi = (float)w;
+      w_ff[m * Ls + n] = make_float2(hi, (float)(w - (double)hi));
+      w_f64[m * Ls + n] = w;
+      w_f32[m * Ls + n] = hi;
+    }
+  std::vector<float4> tw_ff(T / 2);
+  std::vector<double2> tw_f64(T / 2);
+  std::vector<float2> tw_f32(T / 2);
+  for (int e = 0; e < T / 2; ++e) {  // exp(-j 2 pi e / T), integer phase
+    const double cr = std::cos(kTwoPi * e / T), ci = -std::sin(kTwoPi * e / T);
+    const float hr = (float)cr, hi = (float)ci;
+    tw_ff[e] = make_float4(hr, hi, (float)(cr - hr), (float)(ci - hi));
+    tw_f64[e] = make_double2(cr, ci);
+    tw_f32[e] = make_float2(hr, hi);
+  }
+  std::vector<float2> syn_f32(T);
+  std::vector<double2> syn_f64(T);
+  for (int p = 0; p < T; ++p) {
+    const double cr = std::cos(kTwoPi * p / T), ci = std::sin(kTwoPi * p / T);
+    syn_f32[p] = make_float2((float)cr, (float)ci);
+    syn_f64[p] = make_double2(cr, ci);
+  }
+
+  // one allocation, 256-byte aligned sections
+  size_t off = 0;
+  auto sec = [&](size_t bytes) {
+    size_t o = off;
+    off = (off + bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_wff = sec(sizeof(float2) * N), o_w64 = sec(sizeof(double) * N),
+               o_w32 = sec(sizeof(float) * N), o_tff = sec(sizeof(float4) * (T / 2)),
+               o_t64 = sec(sizeof(double2) * (T / 2)), o_t32 = sec(sizeof(float2) * (T / 2)),
+               o_s32 = sec(sizeof(float2) * T), o_s64 = sec(sizeof(double2) * T);
+  const size_t total = off;
+  std::vector<unsigned char> host(total, 0);
+  std::memcpy(&host[o_wff], w_ff.data(), sizeof(float2) * N);
+  std::memcpy(&host[o_w64], w_f64.data(), sizeof(double) * N);
+  std::memcpy(&host[o_w32], w_f32.data(), sizeof(float) * N);
+  std::memcpy(&host[o_tff], tw_ff.data(), sizeof(float4) * (T / 2));
+  std::memcpy(&host[o_t64], tw_f64.data(), sizeof(double2) * (T / 2));
+  std::memcpy(&host[o_t32], tw_f32.data(), sizeof(float2) * (T / 2));
+  std::memcpy(&host[o_s32], syn_f32.data(), sizeof(float2) * T);
+  std::memcpy(&host[o_s64], syn_f64.data(), sizeof(double2) * T);
+
+  void* mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, total);
+  if (e == cudaErrorMemoryAllocation) return FOFSE_E_NOMEM;
+  if (e != cudaSuccess) return FOFSE_E_CUDA;
+  if (cudaMemcpy(mem, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(mem);
+    return FOFSE_E_CUDA;
+  }
+  fofse_plan p = new (std::nothrow) fofse_plan_s;
+  if (!p) {
+    cudaFree(mem);
+    return FOFSE_E_NOMEM;
+  }
+  unsigned char* base = static_cast<unsigned char*>(mem);
+  PlanDev& d = p->dev;
+  d.block = block;
+  d.border = border;
+  d.Ls = Ls;
+  d.T = T;
+  d.iters = iters;
+  d.support = FOFSE_SUPPORT_FULL;
+  d.precision = FOFSE_FP32;
+  d.rho = rho;
+  d.gamma = (double)gamma;
+  d.gamma_h = gamma;
+  d.gamma_l = 0.f;
+  d.tab.w_ff = reinterpret_cast<const float2*>(base + o_wff);
+  d.tab.w_f64 = reinterpret_cast<const double*>(base + o_w64);
+  d.tab.w_f32 = reinterpret_cast<const float*>(base + o_w32);
+  d.tab.tw_ff = reinterpret_cast<const float4*>(base + o_tff);
+  d.tab.tw_f64 = reinterpret_cast<const double2*>(base + o_t64);
+  d.tab.tw_f32 = reinterpret_cast<const float2*>(base + o_t32);
+  d.tab.syn_f32 = reinterpret_cast<const float2*>(base + o_s32);
+  d.tab.syn_f64 = reinterpret_cast<const double2*>(base + o_s64);
+  p->mem = mem;
+  cudaGetDevice(&p->device);
+  *out = p;
+  return FOFSE_OK;
+}
+
+fofse_status fofse_plan_set_support(fofse_plan plan, int shape) {
+  if (!plan || (shape != FOFSE_SUPPORT_FULL && shape != FOFSE_SUPPORT_CAUSAL_L)) return FOFSE_E_ARG;
+  plan->dev.support = shape;
+  return FOFSE_OK;
+}
+
+fofse_status fofse_plan_set_precision(fofse_plan plan, int precision) {
+  if (!plan || (precision != FOFSE_FP32 && precision != FOFSE_FP64_VALIDATE &&
+                precision != FOFSE_FP32_PLAIN))
+    return FOFSE_E_ARG;
+  plan->dev.precision = precision;
+  return FOFSE_OK;
+}
+
+void fofse_plan_destroy(fofse_plan plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  cudaFree(plan->mem);
+  delete plan;
+}
+
+size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks) {
+  if (!plans || n_plans < 1 || n_blocks < 0) return 0;
+  return 0;
+}
+
+fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
+                                     const fofse_block* d_blocks, int n_blocks,
+                                     const float* d_frame, const uint8_t* d_avail, int height,
+                                     int width, int pitch, const float* d_rho_gamma,
+                                     float* d_out_frame, float* d_out_blocks,
+                                     fofse_trace_entry* d_trace, float* d_w0,
+                                     int32_t* d_block_status, void* d_workspace, void* stream) {
+  (void)d_workspace;
+  if (!plans || n_plans < 1 || n_blocks < 0) return FOFSE_E_ARG;
+  if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail)) return FOFSE_E_ARG;
+  if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
+  if (d_rho_gamma) return FOFSE_E_UNSUPPORTED;
+  int bmax = 0, imax = 0;
+  for (int i = 0; i < n_plans; ++i) {
+    if (!plans[i]) return FOFSE_E_ARG;
+    if (plans[i]->dev.precision != plans[0]->dev.precision) return FOFSE_E_ARG;
+    bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
+    imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
+  }
+  if (n_blocks == 0) return FOFSE_OK;
+  unsigned* err = err_word_ptr();
+  if (!err) return FOFSE_E_CUDA;
+
+  const uintptr_t fa = reinterpret_cast<uintptr_t>(d_frame), aa = reinterpret_cast<uintptr_t>(d_avail);
+  const bool tma_ok = encode_fn() && (fa % 16 == 0) && (aa % 16 == 0) && (pitch % 16 == 0);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int pi = 0; pi < n_plans; ++pi) {
+    const PlanDev& P = plans[pi]->dev;
+    FwdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.plan = P;
+    a.plan_index = pi;
+    a.blocks = d_blocks;
+    a.n_blocks = n_blocks;
+    a.frame = d_frame;
+    a.avail = d_avail;
+    a.height = height;
+    a.width = width;
+    a.pitch = pitch;
+    a.out_frame = d_out_frame;
+    a.out_blocks = d_out_blocks;
+    a.out_stride = bmax * bmax;
+    a.trace = d_trace;
+    a.trace_stride = imax;
+    a.w0 = d_w0;
+    a.status = d_block_status;
+    a.err = err;
+    a.box_f = round_up(P.Ls + 3, 4);
+    a.box_a = round_up(P.Ls + 15, 16);
+    CUtensorMap tf, ta;
+    std::memset(&tf, 0, sizeof(tf));
+    std::memset(&ta, 0, sizeof(ta));
+    a.use_tma = 0;
+    if (tma_ok && a.box_f <= 256 && a.box_a <= 256 && P.Ls <= 256 &&
+        encode_2d(&tf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d_frame, width, height, pitch, a.box_f,
+                  P.Ls) &&
+        encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d_avail, width, height, pitch, a.box_a,
+                  P.Ls))
+      a.use_tma = 1;
+    cudaError_t e = launch_forward(a, &tf, &ta, s);
+    if (e != cudaSuccess) return FOFSE_E_CUDA;
+  }
+  return FOFSE_OK;
+}
+
+fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_block* d_blocks,
+                            int n_blocks, const float* d_frame, const uint8_t* d_avail,
+                            int height, int width, int pitch, const float* d_rho_gamma,
+                            const fofse_trace_entry* d_trace, const float* d_w0,
+                            const float* d_grad_blocks, float* d_grad_frame,
+                            float* d_grad_rho_gamma, void* d_workspace, void* stream) {
+  (void)d_workspace;
+  if (!plans || n_plans < 1 || n_blocks < 0) return FOFSE_E_ARG;
+  if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail || !d_trace || !d_w0 || !d_grad_blocks))
+    return FOFSE_E_ARG;
+  if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
+  if (d_rho_gamma) return FOFSE_E_UNSUPPORTED;
+  int bmax = 0, imax = 0;
+  for (int i = 0; i < n_plans; ++i) {
+    if (!plans[i]) return FOFSE_E_ARG;
+    if (plans[i]->dev.precision == FOFSE_FP64_VALIDATE) return FOFSE_E_UNSUPPORTED;
+    bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
+    imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
+  }
+  if (n_blocks == 0 || (!d_grad_frame && !d_grad_rho_gamma)) return FOFSE_OK;
+  unsigned* err = err_word_ptr();
+  if (!err) return FOFSE_E_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int pi = 0; pi < n_plans; ++pi) {
+    BwdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.plan = plans[pi]->dev;
+    a.plan_index = pi;
+    a.blocks = d_blocks;
+    a.n_blocks = n_blocks;
+    a.frame = d_frame;
+    a.avail = d_avail;
+    a.height = height;
+    a.width = width;
+    a.pitch = pitch;
+    a.trace = d_trace;
+    a.trace_stride = imax;
+    a.w0 = d_w0;
+    a.grad_blocks = d_grad_blocks;
+    a.grad_stride = bmax * bmax;
+    a.grad_frame = d_grad_frame;
+    a.grad_rho_gamma = d_grad_rho_gamma ? d_grad_rho_gamma + 2 * pi : nullptr;
+    a.err = err;
+    cudaError_t e = launch_backward(a, s);
+    if (e == cudaErrorNotSupported) return FOFSE_E_UNSUPPORTED;
+    if (e != cudaSuccess) return FOFSE_E_CUDA;
+  }
+  return FOFSE_OK;
+}
+
+fofse_status fofse_check(void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FOFSE_E_CUDA;
+  unsigned* err = err_word_ptr();
+  if (!err) return FOFSE_E_CUDA;
+  unsigned v = 0;
+  if (cudaMemcpy(&v, err, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return FOFSE_E_CUDA;
+  if (v) {
+    unsigned z = 0;
+    if (cudaMemcpy(err, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return FOFSE_E_CUDA;
+  }
+  if (v & kErrTimeout) return FOFSE_E_TIMEOUT;
+  return FOFSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Internal declarations shared by the host API and the kernel translation units.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fofse.h"
+
+namespace fofse {
+
+// Per-block status beyond the public FOFSE_BLK_* values: the block's input
+// staging did not complete within its bounded wait.
+constexpr int kBlkTimeout = 3;
+// Bits of the device error word.
+constexpr unsigned kErrTimeout = 1u;
+
+// Device copies of a plan's constant tables (allocated in fofse_plan_create).
+struct PlanTables {
+  const float2* w_ff;     // Ls*Ls: rho^dist as (hi, lo) float pair
+  const double* w_f64;    // Ls*Ls
+  const float* w_f32;     // Ls*Ls
+  const float4* tw_ff;    // T/2: exp(-j 2 pi e / T) as (re.h, im.h, re.l, im.l)
+  const double2* tw_f64;  // T/2
+  const float2* tw_f32;   // T/2
+  const float2* syn_f32;  // T: (cos, sin)(2 pi p / T)
+  const double2* syn_f64; // T
+};
+
+struct PlanDev {
+  int block, border, Ls, T, iters, support, precision;
+  float gamma_h, gamma_l;  // gamma as float pair
+  double gamma;
+  float rho;
+  PlanTables tab;
+};
+
+struct FwdArgs {
+  PlanDev plan;
+  int plan_index;
+  const fofse_block* blocks;
+  int n_blocks;
+  const float* frame;
+  const uint8_t* avail;
+  int height, width, pitch;
+  float* out_frame;
+  float* out_blocks;
+  int out_stride;
+  fofse_trace_entry* trace;
+  int trace_stride;
+  float* w0;
+  int32_t* status;
+  int use_tma;
+  int box_f, box_a;  // TMA box widths (elements) of the frame and mask tiles
+  unsigned* err;
+};
+
+struct BwdArgs {
+  PlanDev plan;
+  int plan_index;
+  const fofse_block* blocks;
+  int n_blocks;
+  const float* frame;
+  const uint8_t* avail;
+  int height, width, pitch;
+  const fofse_trace_entry* trace;
+  int trace_stride;
+  const float* w0;
+  const float* grad_blocks;
+  int grad_stride;
+  float* grad_frame;
+  float* grad_rho_gamma;  // points at this plan's pair
+  unsigned* err;
+};
+
+// Launchers (one per translation unit).  Return cudaSuccess or the launch error.
+cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tm_frame,
+                           const CUtensorMap* tm_avail, cudaStream_t stream);
+size_t forward_smem_bytes(int precision, int T, int iters);
+cudaError_t launch_backward(const BwdArgs& a, cudaStream_t stream);
+
+}  // namespace fofse

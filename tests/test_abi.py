@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point declared in include/fofse.h; host-side argument validation."""
+import ctypes
+
+import pytest
+
+from paper_2207_01205_gb300 import binding as B
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return B.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = B.header_functions()
+    assert {"fofse_plan_create", "fofse_extrapolate_batch", "fofse_backward"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_version(lib):
+    for s in range(7):
+        assert B.fofse_status_string(s) != "unknown status"
+    assert B.fofse_status_string(99) == "unknown status"
+    assert B.fofse_version() >= 100
+
+
+@pytest.mark.parametrize("args", [
+    (0, 16, 64, 0.8, 0.5, 200),        # block < 1
+    (16, -1, 64, 0.8, 0.5, 200),       # border < 0
+    (16, 16, 48, 0.8, 0.5, 200),       # T not a power of two
+    (16, 25, 64, 0.8, 0.5, 200),       # T < block + 2 border
+    (16, 16, 64, 0.0, 0.5, 200),       # rho out of (0, 1]
+    (16, 16, 64, 1.5, 0.5, 200),
+    (16, 16, 64, 0.8, 0.0, 200),       # gamma out of (0, 1]
+    (16, 16, 64, 0.8, 1.01, 200),
+    (16, 16, 64, 0.8, 0.5, 0),         # iters < 1
+    (16, 16, 64, float("nan"), 0.5, 10),
+])
+def test_plan_create_rejects_invalid_arguments(lib, args):
+    h = ctypes.c_void_p()
+    assert lib.fofse_plan_create(*args, ctypes.byref(h)) == B.E_ARG
+    assert h.value is None
+
+
+def test_plan_create_unsupported_fft_size(lib):
+    h = ctypes.c_void_p()
+    assert lib.fofse_plan_create(16, 16, 512, 0.8, 0.5, 10, ctypes.byref(h)) == B.E_UNSUPPORTED
+    assert lib.fofse_plan_create(16, 16, 64, 0.8, 0.5, 10, None) == B.E_ARG
+
+
+def test_batch_calls_reject_null_arguments(lib):
+    null = ctypes.c_void_p()
+    assert lib.fofse_extrapolate_batch(None, 1, null, 1, null, null, 8, 8, 8, null, null, null,
+                                       null, null, null, null, null) == B.E_ARG
+    assert lib.fofse_backward(None, 1, null, 1, null, null, 8, 8, 8, null, null, null, null, null,
+                              null, null, null) == B.E_ARG
+    assert lib.fofse_plan_set_support(None, 0) == B.E_ARG
+    assert lib.fofse_plan_set_precision(None, 0) == B.E_ARG
+    assert lib.fofse_workspace_bytes(None, 1, 10) == 0
+    lib.fofse_plan_destroy(None)
