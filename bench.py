@@ -1,0 +1,344 @@
+"""Benchmark of the FOFSE GB300 library on the 1920x1080 concealment workload.
+
+Workload: a seeded 1920x1080 8-bit synthetic frame (stand-in for the paper's
+natural test images), 10 % of its 16x16 tiles lost (804 blocks), support
+border 16, 64x64 FFT, rho 0.8, gamma 0.5, 200 iterations; one step = one
+forward pass over all 804 blocks (one kernel launch).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is device-timed (CUDA events on the
+launching stream, inputs resident in HBM, L2 flushed between steps);
+``e2e`` is the same metric through the public C-ABI call with host buffers
+(pinned host -> device copy of the frame, mask and block list, launch,
+device -> host copy of the extrapolated blocks, all inside the timed region).
+``--impl reference`` times the FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "16x16 blocks/s (64x64 FFT, 200 it) fwd and fwd+bwd; % smem roofline; CPU ratio"
+WORKLOAD = "conceal-1920x1080: 804 lost 16x16 blocks, border 16, 64x64 FFT, rho 0.8, gamma 0.5, 200 it"
+L2_FLUSH_BYTES = 512 << 20
+
+# float-float FP32 instructions the transform-domain update needs per
+# conjugate-pair bin and iteration (four pair sums 4 x 8, two two-term products
+# 2 x 16, two compensated subtractions 2 x 11, |R|^2 estimate 2, compare 1);
+# shared-memory bytes: two shifted W gathers of 16 bytes (R in registers).
+FF_OPS_PER_BIN_ITER = 89
+SMEM_BYTES_PER_BIN_ITER = 32
+FP32_LANES_PER_SM = 128
+SMEM_BYTES_PER_CLK_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-block-per-launch form")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a scalar over ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fofse_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def cpu_baseline(wl, sample_blocks: int, threads: int | None = None):
+    """The FP64 oracle as it stands, on the host cores, over a bounded sample of
+    the workload's blocks; returns blocks/s."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    blocks = wl.blocks[:sample_blocks]
+    oracle.build()
+    t0 = time.perf_counter()
+    res = oracle.run_batch(wl.frame, wl.avail, blocks, wl.plans, threads=threads, with_path=False)
+    dt = time.perf_counter() - t0
+    return {"value": len(blocks) / dt, "unit": "blocks/s", "cores": int(res.threads), "kind": "oracle",
+            "sample": f"{len(blocks)} of the {wl.n_blocks} blocks, FP64 spatial re-projection, "
+                      f"{res.threads} threads, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle timed on the host cores."""
+    if rank != 0:
+        return
+    from paper_2207_01205_gb300 import synth
+    import oracle
+    wl = synth.frame_concealment()
+    threads = os.cpu_count() or 1
+    sample = max(threads, 16)
+    oracle.build()
+    for _ in range(max(args.warmup, 0)):
+        oracle.run_batch(wl.frame, wl.avail, wl.blocks[:threads], wl.plans, threads=threads,
+                         with_path=False)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run_batch(wl.frame, wl.avail, wl.blocks[:sample], wl.plans, threads=threads,
+                         with_path=False)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = sample * args.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_blocks_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": "blocks/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} of {wl.n_blocks} blocks per step"},
+            "e2e": {"value": value, "unit": "blocks/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    from paper_2207_01205_gb300 import api, binding, synth
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    init_dist(world, "nccl")
+    binding.load()
+
+    wl = synth.frame_concealment()
+    n = wl.n_blocks
+    plans = [api.Plan.from_spec(p, "fp32") for p in wl.plans]
+    handles = [p.handle for p in plans]
+    frame = torch.from_numpy(wl.frame).to(dev)
+    avail = torch.from_numpy(wl.avail).to(dev)
+    blocks = torch.from_numpy(wl.blocks).to(dev)
+    ob, tr, w0, st = api.alloc_outputs(plans, n, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def fwd():
+        binding.fofse_extrapolate_batch(handles, blocks, frame, avail, out_blocks=ob, trace=tr, w0=w0,
+                                        status=st, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        fwd()
+    torch.cuda.synchronize(dev)
+    binding.fofse_check(stream)
+    assert int((st != 0).sum()) == 0
+
+    # ---- device-timed steps (inputs resident; L2 flushed between steps) ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            fwd()
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    local_ms = sum(step_ms)
+    tot_ms = reduce_max(local_ms, world, dev)
+    ms_per_step = tot_ms / args.steps
+    value = world * n * args.steps / (tot_ms * 1e-3)
+    clocks = clk.summary()
+
+    # ---- end to end through the C ABI with host buffers ----
+    h_frame = torch.from_numpy(wl.frame).pin_memory()
+    h_avail = torch.from_numpy(wl.avail).pin_memory()
+    h_blocks = torch.from_numpy(wl.blocks).pin_memory()
+    h_out = torch.empty(ob.shape, dtype=torch.float32).pin_memory()
+    d_frame = torch.empty_like(frame)
+    d_avail = torch.empty_like(avail)
+    d_blocks = torch.empty_like(blocks)
+
+    def e2e_step():
+        d_frame.copy_(h_frame, non_blocking=True)
+        d_avail.copy_(h_avail, non_blocking=True)
+        d_blocks.copy_(h_blocks, non_blocking=True)
+        binding.fofse_extrapolate_batch(handles, d_blocks, d_frame, d_avail, out_blocks=ob, trace=tr,
+                                        w0=w0, status=st, stream=stream)
+        h_out.copy_(ob, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = reduce_max(e0.elapsed_time(e1), world, dev)
+    h2d = h_frame.numel() * 4 + h_avail.numel() + h_blocks.numel() * 4
+    d2h = h_out.numel() * 4
+    e2e = {"value": world * n * args.steps / (e2e_ms * 1e-3), "unit": "blocks/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- one-block-per-launch form on the same GPU ----
+    plain = None
+    if not args.no_plain:
+        singles = [blocks[i:i + 1] for i in range(n)]
+        ob1 = [ob[i:i + 1] for i in range(n)]
+
+        def one_by_one():
+            for i in range(n):
+                binding.fofse_extrapolate_batch(handles, singles[i], frame, avail, out_blocks=ob1[i],
+                                                stream=stream)
+        one_by_one()
+        torch.cuda.synchronize(dev)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        one_by_one()
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        pms = p0.elapsed_time(p1)
+        plain = {"ms_per_step": pms, "blocks_per_s": n / (pms * 1e-3), "launches_per_step": n}
+
+    # ---- roofline of the dominant kernel ----
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    mhz = clocks.get("sm_mhz") or 1500.0
+    bins = 64 * 64 // 2 + 2
+    iters = wl.plans[0].iters
+    ops = n * iters * bins * FF_OPS_PER_BIN_ITER
+    alu_peak = sms * FP32_LANES_PER_SM * mhz * 1e6
+    achieved = ops / (ms_per_step * 1e-3)
+    smem_bytes = n * iters * bins * SMEM_BYTES_PER_BIN_ITER
+    smem_peak = sms * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
+                "unit": "Tops/s (FP32 lane instructions)", "frac": achieved / alu_peak,
+                "traffic": None, "kernel": "fofse_forward_kernel<ArFF,64,256>",
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (sampled)",
+                "smem": {"achieved_TBps": smem_bytes / (ms_per_step * 1e-3) / 1e12,
+                         "peak_TBps": smem_peak / 1e12,
+                         "frac": smem_bytes / (ms_per_step * 1e-3) / smem_peak}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl, sample_blocks=min(n, 8 * (os.cpu_count() or 1)))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world,
+                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "blocks_per_gpu": n, "arith": "float-float (f32 pairs)",
+                           "l2": "flushed between steps (512 MiB write)",
+                           "parallelism": f"replicas x{world}"},
+                "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline,
+                "cpu_baseline": cpu, "plain_one_block_per_launch": plain,
+                "device": props.name, "sms": sms}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -123,6 +123,82 @@ __device__ __forceinline__ Cand<ArF32> shfl(const Cand<ArF32>& c, int off) {
   return o;
 }
 
+// Warp-wide argmax; every lane returns the winner.  Exact compare for the
+// FP64 / plain FP32 back-ends.  For float-float, the FP32 estimates are
+// reduced first; only if another lane's estimate lies within the near margin
+// of the maximum are the float-float magnitudes compared (rare).
+template <class A> __device__ __forceinline__ Cand<A> warp_argmax(Cand<A> c, int) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const Cand<A> other = shfl(c, o);
+    if (better(other, c)) c = other;
+  }
+  return c;
+}
+__device__ __forceinline__ Cand<ArFF> warp_argmax(Cand<ArFF> c, int lane) {
+  float M = c.m;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
+  const unsigned near = __ballot_sync(0xffffffffu, c.m >= M - fabsf(M) * kNearRel);
+  if (__popc(near) != 1) {  // a near-tie: decide with the float-float magnitudes
+    if (!((near >> lane) & 1u)) c = empty_cand<ArFF>();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const Cand<ArFF> other = shfl(c, o);
+      if (better(other, c)) c = other;
+    }
+    return c;
+  }
+  const int src = __ffs(near) - 1;
+  Cand<ArFF> w;
+  w.m = M;
+  w.code = __shfl_sync(0xffffffffu, c.code, src);
+  w.re.h = __shfl_sync(0xffffffffu, c.re.h, src);
+  w.re.l = __shfl_sync(0xffffffffu, c.re.l, src);
+  w.im.h = __shfl_sync(0xffffffffu, c.im.h, src);
+  w.im.l = __shfl_sync(0xffffffffu, c.im.l, src);
+  return w;
+}
+template <int NW, class A> __device__ __forceinline__ Cand<A> block_argmax_generic(const Cand<A>* sl) {
+  Cand<A> win = sl[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) {
+    const Cand<A> c = sl[w];
+    if (better(c, win)) win = c;
+  }
+  return win;
+}
+template <int NW> __device__ __forceinline__ Cand<ArF64> block_argmax(const Cand<ArF64>* sl) {
+  return block_argmax_generic<NW>(sl);
+}
+template <int NW> __device__ __forceinline__ Cand<ArF32> block_argmax(const Cand<ArF32>* sl) {
+  return block_argmax_generic<NW>(sl);
+}
+template <int NW> __device__ __forceinline__ Cand<ArFF> block_argmax(const Cand<ArFF>* sl) {
+  float M = sl[0].m;
+  int wi = 0;
+#pragma unroll
+  for (int w = 1; w < NW; ++w) {
+    const float m = sl[w].m;
+    if (m > M) {
+      M = m;
+      wi = w;
+    }
+  }
+  const float thr = M - fabsf(M) * kNearRel;
+  int cnt = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) cnt += sl[w].m >= thr ? 1 : 0;
+  if (cnt == 1) return sl[wi];
+  Cand<ArFF> win = empty_cand<ArFF>();  // near-tie across warps
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const Cand<ArFF> c = sl[w];
+    if (c.m >= thr && better(c, win)) win = c;
+  }
+  return win;
+}
+
 // ---------------------------------------------------------------------------
 // coefficient (Eq. 5 with |phi| = 1, Eq. 14) and the rank-1 shifted update
 // ---------------------------------------------------------------------------
@@ -316,21 +392,25 @@ template <class A, int T> struct Geo {
   static constexpr int NBINS = T * T / 2 + 2;  // one index per conjugate pair
 };
 
-// bin j of the canonical set in half-spectrum storage -> packed x_k = k1*2T + k2
-template <int T> __device__ __forceinline__ int bin_xk(int j) {
-  constexpr int NI = T / 2 - 1;  // interior columns 1..T/2-1
-  int k1, k2;
-  if (j < T * NI) {
-    k1 = j / NI;
-    k2 = 1 + j - k1 * NI;
-  } else if (j < T * NI + T / 2 + 1) {
-    k1 = j - T * NI;
-    k2 = 0;
-  } else {
-    k1 = j - (T * NI + T / 2 + 1);
+// Slot s of the T x T/2 slot grid (row = s / (T/2), column = s % (T/2)) ->
+// packed x_k = k1*2T + k2 of a bin of the canonical set.  Columns 1..T/2-1
+// are the interior bins of every row; column 0 holds bins (r, 0) for
+// r <= T/2 and, in rows T/2+1..T-1, the bins (r - T/2 - 1, T/2) of the last
+// half-spectrum column.  Two bins remain, (T/2 - 1, T/2) and (T/2, T/2): the
+// "extra" slots.  Consecutive lanes hold consecutive columns of one row, so
+// the shifted gathers W[k -+ u] of a warp hit 32 consecutive columns (mod T)
+// of one shared-memory row: no bank conflicts.
+template <int T> __device__ __forceinline__ int slot_xk(int s) {
+  const int row = s >> (ilog2(T) - 1), col = s & (T / 2 - 1);
+  int k1 = row, k2 = col;
+  if (col == 0 && row > T / 2) {
+    k1 = row - (T / 2 + 1);
     k2 = T / 2;
   }
   return k1 * 2 * T + k2;
+}
+template <int T> __device__ __forceinline__ int extra_xk(int e) {
+  return (T / 2 - 1 + e) * 2 * T + T / 2;
 }
 template <int T> __device__ __forceinline__ int code_of(int xk) {
   int k1 = xk >> (ilog2(T) + 1), k2 = xk & (2 * T - 1);
@@ -339,8 +419,8 @@ template <int T> __device__ __forceinline__ int code_of(int xk) {
   return canon * 2 + (mir ? 1 : 0);
 }
 
-template <class A, int T, int NT>
-__global__ void __launch_bounds__(NT) fofse_forward_kernel(const __grid_constant__ FwdArgs args,
+template <class A, int T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_constant__ FwdArgs args,
                                                            const __grid_constant__ CUtensorMap tmF,
                                                            const __grid_constant__ CUtensorMap tmA) {
   using C = typename A::C;
@@ -348,10 +428,12 @@ __global__ void __launch_bounds__(NT) fofse_forward_kernel(const __grid_constant
   using IO = PlanIO<A>;
   using G = Geo<A, T>;
   constexpr int T2 = G::T2, LOGT = G::LOGT, NBINS = G::NBINS;
-  constexpr int NBF = NBINS / NT, REM = NBINS % NT;
-  constexpr int NB = NBF + (REM ? 1 : 0);
+  constexpr int NSLOT = T * T / 2;
+  constexpr int NBF = NSLOT / NT;  // full steps; the 2 extra bins go to threads 0 and 1
+  constexpr int NB = NBF + 1;
   constexpr int NW = NT / 32;
-  static_assert(REM < NT, "bins");
+  static_assert(NSLOT % NT == 0 && NT >= 64, "slot grid");
+  static_assert(NBINS == NSLOT + 2, "bins");
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -499,11 +581,10 @@ __global__ void __launch_bounds__(NT) fofse_forward_kernel(const __grid_constant
   int kc[NB];  // x_k | code << 16
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
-    const int j = tid + i * NT;
     kc[i] = 0;
     R[i] = A::zero();
-    if (i < NBF || j < NBINS) {
-      const int x = bin_xk<T>(j);
+    if (i < NBF || tid < 2) {
+      const int x = i < NBF ? slot_xk<T>(tid + i * NT) : extra_xk<T>(tid);
       kc[i] = x | (code_of<T>(x) << 16);
       const int k1 = x >> (LOGT + 1), k2 = x & (T2 - 1);
       const int mx = ((T - k1) & (T - 1)) * T2 + ((T - k2) & (T - 1));
@@ -542,7 +623,7 @@ __global__ void __launch_bounds__(NT) fofse_forward_kernel(const __grid_constant
     Cand<A> best = empty_cand<A>();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-      if (i < NBF || tid + i * NT < NBINS) {
+      if (i < NBF || tid < 2) {
         const Cand<A> c = make_cand(R[i], kc[i] >> 16);
         if (better(c, best)) best = c;
       }
@@ -550,20 +631,11 @@ __global__ void __launch_bounds__(NT) fofse_forward_kernel(const __grid_constant
 #pragma unroll 1
     for (int it = 0; it < iters; ++it) {
       // ---- 4a. block argmax (Eq. 9) ----
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        Cand<A> other = shfl(best, o);
-        if (better(other, best)) best = other;
-      }
+      best = warp_argmax(best, lane);
       Cand<A>* sl = slots + (it & 1) * NW;
       if (lane == 0) sl[warp] = best;
       __syncthreads();
-      Cand<A> win = sl[0];
-#pragma unroll
-      for (int w = 1; w < NW; ++w) {
-        Cand<A> c = sl[w];
-        if (better(c, win)) win = c;
-      }
+      const Cand<A> win = block_argmax<NW>(sl);
       // ---- 4b. coefficient (Eq. 5, Eq. 14) ----
       const int canon = win.code >> 1;
       const bool mir = win.code & 1;
@@ -588,7 +660,7 @@ __global__ void __launch_bounds__(NT) fofse_forward_kernel(const __grid_constant
       if (!sc) {
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-          if (i < NBF || tid + i * NT < NBINS) {
+          if (i < NBF || tid < 2) {
             const int x = kc[i] & 0xffff;
             const C Wm = A::load(Z, (x + T - y) & G::M, T);
             const C Wp = A::load(Z, (x + y) & G::M, T);
@@ -600,7 +672,7 @@ __global__ void __launch_bounds__(NT) fofse_forward_kernel(const __grid_constant
       } else {
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-          if (i < NBF || tid + i * NT < NBINS) {
+          if (i < NBF || tid < 2) {
             const C Wm = A::load(Z, ((kc[i] & 0xffff) + T - y) & G::M, T);
             Upd<A>::single(R[i], c, Wm);
             const Cand<A> cd = make_cand(R[i], kc[i] >> 16);
@@ -665,11 +737,11 @@ template <class A, int T, int NT> size_t smem_bytes(int iters) {
   return off;
 }
 
-template <class A, int T, int NT>
+template <class A, int T, int NT, int MINB = 1>
 cudaError_t launch_one(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
                        cudaStream_t s) {
   const size_t sm = smem_bytes<A, T, NT>(a.plan.iters);
-  auto kern = fofse_forward_kernel<A, T, NT>;
+  auto kern = fofse_forward_kernel<A, T, NT, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   kern<<<a.n_blocks, NT, sm, s>>>(a, *tf, *ta);
@@ -698,7 +770,7 @@ cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tf, const CUtens
   if (T == 64) {
     if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 64, 256>(a, tf, ta, s);
     if (pr == FOFSE_FP32_PLAIN) return launch_one<ArF32, 64, 256>(a, tf, ta, s);
-    return launch_one<ArFF, 64, 256>(a, tf, ta, s);
+    return launch_one<ArFF, 64, 256, 3>(a, tf, ta, s);
   }
   if (T == 32) {
     if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 32, 128>(a, tf, ta, s);
