@@ -86,6 +86,10 @@ def _declare(L):
                                ctypes.POINTER(OraclePlan), _c_int, _c_int, _dp, _ip, _dp, _ip, _ip,
                                _dp, _dp, _dp, _c_int]
     L.oracle_batch.restype = _c_int
+    L.oracle_batch_adjoint.argtypes = [_fp, _u8p, _c_int, _c_int, _c_int, _ip, _c_int,
+                                       ctypes.POINTER(OraclePlan), _c_int, _ip, _ip, _c_int, _dp,
+                                       _c_int, _dp, _dp, _c_int]
+    L.oracle_batch_adjoint.restype = _c_int
 
 
 def _p(a, t):
@@ -285,3 +289,29 @@ def block_gradients(frame, avail, y, x, plan, path, e_B):
     fbar, wbar, gam = adjoint_area(fL, wL, plan.fft_size, plan.gamma, path, gbar)
     rho_bar = rho_chain(wL, distance(b, br), plan.rho, wbar)
     return fbar, rho_bar, gam
+
+
+def batch_adjoint(frame, avail, blocks, plans, path, e_blocks, threads: int | None = None):
+    """Frozen-path gradients of sum_i <e_i, B_hat_i> over a batch: returns
+    (grad_frame (H, W), grad_rho_gamma (n_plans, 2)).  ``path``: (n, imax, 2)
+    int selection paths; ``e_blocks``: (n, bmax, bmax) dloss/dB."""
+    frame = np.ascontiguousarray(frame, dtype=np.float32)
+    avail = np.ascontiguousarray(avail, dtype=np.uint8)
+    blocks = _i32(blocks).reshape(-1, 3)
+    H, W = frame.shape
+    n = blocks.shape[0]
+    imax = path.shape[1]
+    u1 = _i32(path[:, :, 0])
+    u2 = _i32(path[:, :, 1])
+    bmax = e_blocks.shape[1]
+    e = np.zeros((n, bmax * bmax))
+    for i in range(n):
+        b = plans[blocks[i, 2]].block
+        e[i, :b * b] = np.asarray(e_blocks[i, :b, :b], dtype=np.float64).ravel()
+    gf = np.zeros((H, W))
+    grg = np.zeros((len(plans), 2))
+    lib().oracle_batch_adjoint(_p(frame, _fp), _p(avail, _u8p), H, W, W, _p(blocks, _ip), n,
+                               plans_to_c(plans), len(plans), _p(u1, _ip), _p(u2, _ip), imax,
+                               _p(e, _dp), bmax * bmax, _p(gf, _dp), _p(grg, _dp),
+                               threads or os.cpu_count() or 1)
+    return gf, grg

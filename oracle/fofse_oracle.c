@@ -505,3 +505,120 @@ int oracle_batch(const float* frame, const unsigned char* avail, int height, int
     pthread_mutex_destroy(&J.lock);
     return n_threads;
 }
+
+/* -------------------------------------------------------------------------- */
+/* Adjoint of a whole batch along given paths                                  */
+/* -------------------------------------------------------------------------- */
+
+typedef struct {
+    const float* frame;
+    const unsigned char* avail;
+    int height, width, pitch;
+    const int* blocks;
+    const oracle_plan* plans;
+    int n_blocks;
+    const int* path_u1;         /* n x trace_stride */
+    const int* path_u2;
+    int trace_stride;
+    const double* e_blocks;     /* n x e_stride: dloss/dB, b x b row-major */
+    int e_stride;
+    int n_plans;
+    double** grad_frame_t;      /* per thread: height x width accumulators */
+    double** grad_rg_t;         /* per thread: n_plans x 2 */
+    int next;
+    pthread_mutex_t lock;
+} adj_job;
+
+typedef struct { adj_job* J; int t; } adj_arg;
+
+static void adj_one(adj_job* J, int bi, double* gf, double* grg) {
+    const int* bd = J->blocks + 3 * bi;
+    const oracle_plan* P = J->plans + bd[2];
+    int b = P->block, br = P->border, Ls = b + 2 * br, N = Ls * Ls;
+    double* fL = (double*)malloc(sizeof(double) * N);
+    double* wL = (double*)malloc(sizeof(double) * N);
+    double* dist = (double*)malloc(sizeof(double) * N);
+    double* gbar = (double*)calloc(N, sizeof(double));
+    double* fbar = (double*)malloc(sizeof(double) * N);
+    double* wbar = (double*)malloc(sizeof(double) * N);
+    unsigned char* aL = (unsigned char*)malloc(N);
+    oracle_cut_area(J->frame, J->avail, J->height, J->width, J->pitch, bd[0], bd[1], b, br, fL, aL);
+    oracle_weights(b, br, P->support, P->rho, aL, wL);
+    oracle_distance(b, br, dist);
+    const double* e = J->e_blocks + (size_t)bi * J->e_stride;
+    for (int m = 0; m < b; ++m)
+        for (int n = 0; n < b; ++n) gbar[(m + br) * Ls + (n + br)] = e[m * b + n];
+    double gam = 0.0;
+    size_t to = (size_t)bi * J->trace_stride;
+    int st = oracle_adjoint_area(Ls, P->fft_size, fL, wL, P->gamma, P->iters, J->path_u1 + to,
+                                 J->path_u2 + to, gbar, fbar, wbar, &gam);
+    if (st == ORC_OK) {
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) {
+                int i = m * Ls + n;
+                if (wL[i] == 0.0) continue;
+                int fy = bd[0] - br + m, fx = bd[1] - br + n;
+                gf[(size_t)fy * J->width + fx] += fbar[i];
+            }
+        grg[2 * bd[2]] += oracle_rho_chain(N, wL, dist, P->rho, wbar);
+        grg[2 * bd[2] + 1] += gam;
+    }
+    free(fL); free(wL); free(dist); free(gbar); free(fbar); free(wbar); free(aL);
+}
+
+static void* adj_worker(void* arg) {
+    adj_arg* a = (adj_arg*)arg;
+    adj_job* J = a->J;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int bi = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (bi >= J->n_blocks) break;
+        adj_one(J, bi, J->grad_frame_t[a->t], J->grad_rg_t[a->t]);
+    }
+    return NULL;
+}
+
+/* Gradients of sum_blocks <e_block, B_hat_block> with every path frozen: adds
+ * dloss/dframe into grad_frame (height x width, row-major, unit pitch) and
+ * dloss/drho, dloss/dgamma into grad_rg (n_plans x 2).  Per-thread
+ * accumulators are summed in thread order, so the result is deterministic for
+ * a given thread count. */
+int oracle_batch_adjoint(const float* frame, const unsigned char* avail, int height, int width,
+                         int pitch, const int* blocks, int n_blocks, const oracle_plan* plans,
+                         int n_plans, const int* path_u1, const int* path_u2, int trace_stride,
+                         const double* e_blocks, int e_stride, double* grad_frame,
+                         double* grad_rg, int n_threads) {
+    adj_job J;
+    J.frame = frame; J.avail = avail; J.height = height; J.width = width; J.pitch = pitch;
+    J.blocks = blocks; J.plans = plans; J.n_blocks = n_blocks; J.path_u1 = path_u1;
+    J.path_u2 = path_u2; J.trace_stride = trace_stride; J.e_blocks = e_blocks;
+    J.e_stride = e_stride; J.n_plans = n_plans; J.next = 0;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_blocks) n_threads = n_blocks > 0 ? n_blocks : 1;
+    size_t HW = (size_t)height * width;
+    J.grad_frame_t = (double**)malloc(sizeof(double*) * n_threads);
+    J.grad_rg_t = (double**)malloc(sizeof(double*) * n_threads);
+    for (int t = 0; t < n_threads; ++t) {
+        J.grad_frame_t[t] = (double*)calloc(HW, sizeof(double));
+        J.grad_rg_t[t] = (double*)calloc(2 * n_plans, sizeof(double));
+    }
+    pthread_mutex_init(&J.lock, NULL);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * n_threads);
+    adj_arg* args = (adj_arg*)malloc(sizeof(adj_arg) * n_threads);
+    for (int t = 0; t < n_threads; ++t) {
+        args[t].J = &J;
+        args[t].t = t;
+        pthread_create(&th[t], NULL, adj_worker, &args[t]);
+    }
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    for (int t = 0; t < n_threads; ++t) {
+        for (size_t i = 0; i < HW; ++i) grad_frame[i] += J.grad_frame_t[t][i];
+        for (int i = 0; i < 2 * n_plans; ++i) grad_rg[i] += J.grad_rg_t[t][i];
+        free(J.grad_frame_t[t]);
+        free(J.grad_rg_t[t]);
+    }
+    free(J.grad_frame_t); free(J.grad_rg_t); free(th); free(args);
+    pthread_mutex_destroy(&J.lock);
+    return n_threads;
+}

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "fofse_arith.cuh"
+#include "fofse_fft.cuh"
 #include "fofse_internal.h"
 
 namespace fofse {
@@ -544,37 +545,7 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
   __syncthreads();
 
   // ---- 3. FFT: rows that hold data, then all columns (radix-2 DIT) ----------
-#pragma unroll 1
-  for (int lh = 0; lh < LOGT; ++lh) {
-    const int h = 1 << lh;
-    for (int it = tid; it < Ls * (T / 2); it += NT) {
-      const int rr = it >> (LOGT - 1), q = it & (T / 2 - 1);
-      const int row = __brev(rr) >> (32 - LOGT);
-      const int i = ((q >> lh) << (lh + 1)) | (q & (h - 1));
-      const int ex = (q & (h - 1)) << (LOGT - 1 - lh);
-      const int ia = row * T2 + i, ib = ia + h;
-      C a = A::load(Z, ia, T), bb = A::load(Z, ib, T);
-      C wb = A::mul_norm(tw[ex], bb);
-      A::store(Z, ia, T, A::add(a, wb));
-      A::store(Z, ib, T, A::sub(a, wb));
-    }
-    __syncthreads();
-  }
-#pragma unroll 1
-  for (int lh = 0; lh < LOGT; ++lh) {
-    const int h = 1 << lh;
-    for (int it = tid; it < T * (T / 2); it += NT) {
-      const int c = it & (T - 1), q = it >> LOGT;
-      const int i = ((q >> lh) << (lh + 1)) | (q & (h - 1));
-      const int ex = (q & (h - 1)) << (LOGT - 1 - lh);
-      const int ia = i * T2 + c, ib = ia + h * T2;
-      C a = A::load(Z, ia, T), bb = A::load(Z, ib, T);
-      C wb = A::mul_norm(tw[ex], bb);
-      A::store(Z, ia, T, A::add(a, wb));
-      A::store(Z, ib, T, A::sub(a, wb));
-    }
-    __syncthreads();
-  }
+  fft2d_dit<A, T, NT, false>(Z, tw, Ls, T);
 
   // ---- split: R_w[k] = (Z[k] + conj Z[-k]) / 2 into registers ---------------
   C R[NB];
