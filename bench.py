@@ -247,6 +247,43 @@ def main():
     value = world * n * args.steps / (tot_ms * 1e-3)
     clocks = clk.summary()
 
+    # ---- forward + backward (squared error over B against the ground truth) ----
+    truth = torch.from_numpy(np.stack([wl.truth[y:y + 16, x:x + 16] for (y, x, _) in wl.blocks])).to(dev)
+    gframe = torch.zeros_like(frame)
+    grg = torch.zeros((1, 2), dtype=torch.float32, device=dev)
+    gblk = torch.empty_like(ob)
+
+    def fwd_bwd():
+        fwd()
+        torch.mul(torch.sub(ob, truth, out=gblk), 2.0, out=gblk)   # dl/dB for l = sum (B - f)^2
+        binding.fofse_backward(handles, blocks, frame, avail, tr, w0, gblk, grad_frame=gframe,
+                               grad_rho_gamma=grg, stream=stream)
+
+    for _ in range(3):
+        fwd_bwd()
+    torch.cuda.synchronize(dev)
+    binding.fofse_check(stream)
+    fb_ms = []
+    bw_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    bw_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        fwd()
+        bw_s[k].record(stream)
+        torch.mul(torch.sub(ob, truth, out=gblk), 2.0, out=gblk)
+        binding.fofse_backward(handles, blocks, frame, avail, tr, w0, gblk, grad_frame=gframe,
+                               grad_rho_gamma=grg, stream=stream)
+        bw_e[k].record(stream)
+    torch.cuda.synchronize(dev)
+    fb_tot = reduce_max(sum(s.elapsed_time(e) for s, e in zip(starts, bw_e)), world, dev)
+    bw_only = sum(s.elapsed_time(e) for s, e in zip(bw_s, bw_e)) / args.steps
+    fwd_bwd_line = {"ms_per_step": fb_tot / args.steps,
+                    "blocks_per_s": world * n * args.steps / (fb_tot * 1e-3),
+                    "backward_ms": bw_only, "loss": "sum over B of (B_hat - f_true)^2",
+                    "grads": "support samples, rho, gamma (path frozen)"}
+
     # ---- end to end through the C ABI with host buffers ----
     h_frame = torch.from_numpy(wl.frame).pin_memory()
     h_avail = torch.from_numpy(wl.avail).pin_memory()
@@ -331,6 +368,7 @@ def main():
                 "config": {"workload": WORKLOAD, "blocks_per_gpu": n, "arith": "float-float (f32 pairs)",
                            "l2": "flushed between steps (512 MiB write)",
                            "parallelism": f"replicas x{world}"},
+                "fwd_bwd": fwd_bwd_line,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu, "plain_one_block_per_launch": plain,
                 "device": props.name, "sms": sms}
