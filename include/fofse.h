@@ -91,7 +91,7 @@ typedef struct {
  * 16 x 16 blocks, border 16, 64 x 64 FFT, rho 0.8, gamma, iterations).
  *   block     lost block side b, 1 <= b
  *   border    support border width, 0 <= border
- *   fft_size  T in {32, 64}, T >= block + 2 * border
+ *   fft_size  T in {32, 64, 128}, T >= block + 2 * border
  *   rho       rho_hat of Eq. 15, 0 < rho <= 1
  *   gamma     constant compensation factor of Eq. 14, 0 < gamma <= 1
  *   iters     number of iterations I, 1 <= I <= 4096
@@ -112,9 +112,11 @@ fofse_status fofse_plan_set_precision(fofse_plan plan, int precision);
 void fofse_plan_destroy(fofse_plan plan);
 
 /*
- * fofse_workspace_bytes -- device scratch needed by fofse_extrapolate_batch and
- * fofse_backward for this batch (work-queue counters).  Returns 0 for invalid
- * arguments.
+ * fofse_workspace_bytes -- device scratch for fofse_extrapolate_batch with
+ * these plans on the current device: 256 bytes of work-queue counters (one per
+ * plan, zeroed by every call) plus, when a plan has fft_size 128, one 256 KB
+ * FFT buffer per SM.  Returns 0 for invalid arguments (more than 64 plans, a
+ * NULL plan).
  */
 size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks);
 
@@ -137,10 +139,16 @@ size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks)
  *                      (W[0] = sum of w); required for fofse_backward
  *   d_block_status     nullable; n_blocks int32 (FOFSE_BLK_*).  Blocks that are
  *                      not OK get B_hat = 0 and an all-zero trace
- *   d_workspace        fofse_workspace_bytes() bytes (may be NULL if that is 0)
+ *   d_workspace        fofse_workspace_bytes() bytes, caller-owned, 256-byte
+ *                      aligned; may be NULL when no plan has fft_size 128 (blocks
+ *                      are then dealt to the CTAs round-robin instead of through
+ *                      the work queue).  A workspace must not be shared by calls
+ *                      that may run concurrently.
  *   stream             cudaStream_t
- * All plans of one call must share the precision.  Returns FOFSE_OK once the
- * work is queued.
+ * Plans are processed largest first (iters * T^2), each by a persistent kernel
+ * whose CTAs take that plan's blocks from a work queue.  All plans of one call
+ * must share the precision; at most 64 plans.  Returns FOFSE_OK once the work
+ * is queued, FOFSE_E_ARG if a fft_size-128 plan is given no workspace.
  */
 fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
                                      const fofse_block* d_blocks, int n_blocks,
@@ -157,7 +165,8 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
  *   d_grad_blocks      dloss/dB_hat, n_blocks x out_stride (as d_out_blocks)
  *   d_grad_frame       nullable; dloss/df ACCUMULATED (+=) at every sample of A
  *   d_grad_rho_gamma   nullable; n_plans x 2 floats, ACCUMULATED (+=)
- * Not implemented for FOFSE_FP64_VALIDATE plans (FOFSE_E_UNSUPPORTED).
+ * Not implemented for FOFSE_FP64_VALIDATE plans or fft_size 128
+ * (FOFSE_E_UNSUPPORTED).
  */
 fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_block* d_blocks,
                             int n_blocks, const float* d_frame, const uint8_t* d_avail,

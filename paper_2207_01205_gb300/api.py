@@ -76,13 +76,24 @@ def alloc_outputs(plans, n, device, with_trace=True):
     return blocks, trace, w0, status
 
 
-def extrapolate(plans, blocks, frame, avail, *, out_frame=None, with_trace=True, stream=None) -> Result:
+def workspace(plans, n_blocks, device):
+    """Device scratch for a batch call with these plans (work-queue counters
+    and, for fft_size 128, per-SM FFT buffers)."""
+    nbytes = B.fofse_workspace_bytes([p.handle for p in plans], n_blocks)
+    return torch.empty((max(nbytes, 1),), dtype=torch.uint8, device=device)
+
+
+def extrapolate(plans, blocks, frame, avail, *, out_frame=None, with_trace=True, stream=None,
+                ws=None) -> Result:
     """Run the forward pass of every block.  ``blocks``: (n, 3) int32 tensor on
     the device (y, x, plan index); ``frame`` float32 and ``avail`` uint8 (H, W)
     tensors on the same device."""
     plans = list(plans)
     n = int(blocks.shape[0])
     ob, tr, w0, st = alloc_outputs(plans, n, frame.device, with_trace)
+    if ws is None:
+        ws = workspace(plans, n, frame.device)
     B.fofse_extrapolate_batch([p.handle for p in plans], blocks, frame, avail, out_frame=out_frame,
-                              out_blocks=ob, trace=tr, w0=w0, status=st, stream=stream)
+                              out_blocks=ob, trace=tr, w0=w0, status=st, workspace=ws,
+                              stream=stream)
     return Result(ob, tr, w0, st, out_frame)

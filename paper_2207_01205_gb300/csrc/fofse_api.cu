@@ -73,7 +73,26 @@ bool encode_2d(CUtensorMap* map, CUtensorMapDataType ty, int esize, const void* 
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-bool supported_T(int T) { return T == 32 || T == 64; }
+bool supported_T(int T) { return T == 32 || T == 64 || T == 128; }
+
+constexpr int kMaxPlans = 64;
+constexpr size_t kCounterBytes = 256;  // one int work-queue counter per plan
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+size_t scratch_bytes(const fofse_plan* plans, int n_plans, int sms) {
+  size_t per = 0;
+  for (int i = 0; i < n_plans; ++i) {
+    const size_t b = forward_scratch_bytes_per_cta(plans[i]->dev.T);
+    per = b > per ? b : per;
+  }
+  return per * (size_t)sms;
+}
 
 }  // namespace
 
@@ -222,8 +241,10 @@ void fofse_plan_destroy(fofse_plan plan) {
 }
 
 size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks) {
-  if (!plans || n_plans < 1 || n_blocks < 0) return 0;
-  return 0;
+  if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return 0;
+  for (int i = 0; i < n_plans; ++i)
+    if (!plans[i]) return 0;
+  return kCounterBytes + scratch_bytes(plans, n_plans, sm_count());
 }
 
 fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
@@ -233,8 +254,7 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
                                      float* d_out_frame, float* d_out_blocks,
                                      fofse_trace_entry* d_trace, float* d_w0,
                                      int32_t* d_block_status, void* d_workspace, void* stream) {
-  (void)d_workspace;
-  if (!plans || n_plans < 1 || n_blocks < 0) return FOFSE_E_ARG;
+  if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return FOFSE_E_ARG;
   if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail)) return FOFSE_E_ARG;
   if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
   if (d_rho_gamma) return FOFSE_E_UNSUPPORTED;
@@ -248,11 +268,34 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
   if (n_blocks == 0) return FOFSE_OK;
   unsigned* err = err_word_ptr();
   if (!err) return FOFSE_E_CUDA;
+  const int sms = sm_count();
+  const size_t scratch = scratch_bytes(plans, n_plans, sms);
+  if (scratch > 0 && !d_workspace) return FOFSE_E_ARG;  // T = 128 needs its FFT scratch
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* queue = nullptr;
+  unsigned char* scratch_base = nullptr;
+  if (d_workspace) {
+    queue = static_cast<int*>(d_workspace);
+    scratch_base = static_cast<unsigned char*>(d_workspace) + kCounterBytes;
+    if (cudaMemsetAsync(queue, 0, kCounterBytes, s) != cudaSuccess) return FOFSE_E_CUDA;
+  }
 
   const uintptr_t fa = reinterpret_cast<uintptr_t>(d_frame), aa = reinterpret_cast<uintptr_t>(d_avail);
   const bool tma_ok = encode_fn() && (fa % 16 == 0) && (aa % 16 == 0) && (pitch % 16 == 0);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (int pi = 0; pi < n_plans; ++pi) {
+  // largest blocks first (longest-processing-time order across plans)
+  int order[kMaxPlans];
+  for (int i = 0; i < n_plans; ++i) order[i] = i;
+  for (int i = 1; i < n_plans; ++i)
+    for (int j = i; j > 0; --j) {
+      const PlanDev& a = plans[order[j]]->dev;
+      const PlanDev& b = plans[order[j - 1]]->dev;
+      if ((double)a.iters * a.T * a.T <= (double)b.iters * b.T * b.T) break;
+      const int t = order[j];
+      order[j] = order[j - 1];
+      order[j - 1] = t;
+    }
+  for (int oi = 0; oi < n_plans; ++oi) {
+    const int pi = order[oi];
     const PlanDev& P = plans[pi]->dev;
     FwdArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -273,6 +316,9 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
     a.w0 = d_w0;
     a.status = d_block_status;
     a.err = err;
+    a.queue = queue ? queue + pi : nullptr;
+    a.scratch = scratch_base;
+    a.scratch_ctas = sms;
     a.box_f = round_up(P.Ls + 3, 4);
     a.box_a = round_up(P.Ls + 15, 16);
     CUtensorMap tf, ta;
@@ -298,7 +344,7 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
                             const float* d_grad_blocks, float* d_grad_frame,
                             float* d_grad_rho_gamma, void* d_workspace, void* stream) {
   (void)d_workspace;
-  if (!plans || n_plans < 1 || n_blocks < 0) return FOFSE_E_ARG;
+  if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return FOFSE_E_ARG;
   if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail || !d_trace || !d_w0 || !d_grad_blocks))
     return FOFSE_E_ARG;
   if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;

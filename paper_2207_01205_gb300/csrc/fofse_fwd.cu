@@ -26,6 +26,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "fofse_arith.cuh"
 #include "fofse_fft.cuh"
 #include "fofse_internal.h"
@@ -358,6 +360,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
@@ -420,44 +425,93 @@ template <int T> __device__ __forceinline__ int code_of(int xk) {
   return canon * 2 + (mir ? 1 : 0);
 }
 
-template <class A, int T, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_constant__ FwdArgs args,
-                                                           const __grid_constant__ CUtensorMap tmF,
-                                                           const __grid_constant__ CUtensorMap tmA) {
+// Where W lives during the iterations.  Full: the whole T x T grid in shared
+// memory in the two-plane layout above (T <= 64; the FFT runs in place).
+// Half: only the Hermitian half k2 in [0, T/2] (rows of 2 (T/2 + 1)
+// elements: part 0 at r*HS + c, part 1 at r*HS + HO + c); a gather at
+// a2 > T/2 reads the mirror and conjugates.  Used at T = 128, where the full
+// float-float grid (256 KB) does not fit; the FFT then runs in a per-CTA slot
+// of global scratch (L2-resident).
+template <class A, int T, bool HALF> struct WTab;
+template <class A, int T> struct WTab<A, T, false> {
+  using C = typename A::C;
+  using E = typename A::E;
+  static constexpr int M = (T - 1) * 2 * T + (T - 1);
+  static constexpr size_t elems = (size_t)T * 2 * T;
+  __device__ __forceinline__ static C minus(const E* W, int x, int y) {
+    return A::load(W, (x + T - y) & M, T);
+  }
+  __device__ __forceinline__ static C plus(const E* W, int x, int y) {
+    return A::load(W, (x + y) & M, T);
+  }
+  __device__ __forceinline__ static C at0(const E* W) { return A::load(W, 0, T); }
+};
+template <class A, int T> struct WTab<A, T, true> {
+  using C = typename A::C;
+  using E = typename A::E;
+  static constexpr int LOGT = ilog2(T);
+  static constexpr int M = (T - 1) * 2 * T + (T - 1);
+  static constexpr int HO = T / 2 + 1, HS = 2 * HO;
+  static constexpr size_t elems = (size_t)T * HS;
+  __device__ __forceinline__ static C get(const E* W, int a) {  // a = a1*2T + a2, a2 < T
+    const int a1 = a >> (LOGT + 1), a2 = a & (T - 1);
+    const bool mir = a2 > T / 2;
+    const int r = mir ? ((T - a1) & (T - 1)) : a1;
+    const int c = mir ? (T - a2) : a2;
+    const C v = A::load(W + r * HS, c, HO);
+    return mir ? A::conj(v) : v;
+  }
+  __device__ __forceinline__ static C minus(const E* W, int x, int y) { return get(W, (x + T - y) & M); }
+  __device__ __forceinline__ static C plus(const E* W, int x, int y) { return get(W, (x + y) & M); }
+  __device__ __forceinline__ static C at0(const E* W) { return A::load(W, 0, HO); }
+};
+
+template <class A, int T, int NT, bool HALF> struct FwdLayout {
   using C = typename A::C;
   using E = typename A::E;
   using IO = PlanIO<A>;
-  using G = Geo<A, T>;
-  constexpr int T2 = G::T2, LOGT = G::LOGT, NBINS = G::NBINS;
+  static constexpr int NW = NT / 32;
+  // offsets (bytes) from the 1024-aligned base of dynamic shared memory
+  static constexpr size_t w_bytes = sizeof(E) * WTab<A, T, HALF>::elems;
+  static constexpr size_t tw_off = w_bytes;
+  static constexpr size_t syn_off = tw_off + sizeof(C) * (T / 2);
+  static constexpr size_t slot_off = syn_off + sizeof(typename IO::Syn) * T;
+  static constexpr size_t ex_off = (slot_off + sizeof(Cand<A>) * 2 * NW + 15) & ~size_t(15);
+  static constexpr size_t tr_off = (ex_off + 2 * sizeof(C) + 15) & ~size_t(15);
+  static size_t bytes(int iters) { return 1024 + tr_off + sizeof(TraceSm<A>) * (size_t)iters; }
+  static constexpr size_t scratch_elems = HALF ? (size_t)T * 2 * T : 0;  // per CTA, global
+};
+
+template <class A, int T, int NT, bool HALF>
+__device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtensorMap* tmF,
+                                              const CUtensorMap* tmA, int blk, unsigned char* smem,
+                                              uint64_t* mbar, unsigned& tma_phase,
+                                              typename A::E* Zg) {
+  using C = typename A::C;
+  using E = typename A::E;
+  using IO = PlanIO<A>;
+  using L = FwdLayout<A, T, NT, HALF>;
+  using WT = WTab<A, T, HALF>;
+  constexpr int T2 = 2 * T, LOGT = ilog2(T), NBINS = T * T / 2 + 2;
   constexpr int NSLOT = T * T / 2;
-  constexpr int NBF = NSLOT / NT;  // full steps; the 2 extra bins go to threads 0 and 1
-  constexpr int NB = NBF + 1;
+  constexpr int NB = NSLOT / NT;  // register-resident bins per thread
   constexpr int NW = NT / 32;
   static_assert(NSLOT % NT == 0 && NT >= 64, "slot grid");
   static_assert(NBINS == NSLOT + 2, "bins");
 
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  E* Z = reinterpret_cast<E*>(smem);
-  size_t off = sizeof(E) * T * T2;
-  C* tw = reinterpret_cast<C*>(smem + off);
-  off += sizeof(C) * (T / 2);
+  E* Wsm = reinterpret_cast<E*>(smem);              // W table (and staging, and FFT if full)
+  E* Z = HALF ? Zg : Wsm;                           // FFT buffer
+  C* tw = reinterpret_cast<C*>(smem + L::tw_off);
   using Syn = typename IO::Syn;
-  Syn* syn = reinterpret_cast<Syn*>(smem + off);
-  off += sizeof(Syn) * T;
-  Cand<A>* slots = reinterpret_cast<Cand<A>*>(smem + off);
-  off += sizeof(Cand<A>) * 2 * NW;
-  off = (off + 15) & ~size_t(15);
-  TraceSm<A>* tr = reinterpret_cast<TraceSm<A>*>(smem + off);
-  __shared__ uint64_t mbar;
+  Syn* syn = reinterpret_cast<Syn*>(smem + L::syn_off);
+  Cand<A>* slots = reinterpret_cast<Cand<A>*>(smem + L::slot_off);
+  TraceSm<A>* tr = reinterpret_cast<TraceSm<A>*>(smem + L::tr_off);
+  C* ex = reinterpret_cast<C*>(smem + L::ex_off);  // the two bins beyond the slot grid
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int blk = blockIdx.x;
   const PlanDev& P = args.plan;
   const fofse_block bd = args.blocks[blk];
-  if (bd.plan != args.plan_index) return;
   const int b = P.block, br = P.border, Ls = P.Ls, iters = P.iters;
   const int ly0 = bd.y - br, lx0 = bd.x - br;  // L's top-left in the frame
 
@@ -469,30 +523,30 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
   const int ax0 = lx0 & ~15, ao = lx0 - ax0;
   if (args.use_tma) {
     if (tid == 0) {
-      mbar_init(&mbar, 1);
-      fence_proxy_async();
-    }
-    __syncthreads();
-    if (tid == 0) {
-      mbar_expect_tx(&mbar, (unsigned)(bytesF + args.box_a * Ls));
-      tma_load_2d(stF, &tmF, fx0, ly0, &mbar);
-      tma_load_2d(stA, &tmA, ax0, ly0, &mbar);
+      fence_proxy_async();  // earlier generic writes to this area before the async copies
+      mbar_expect_tx(mbar, (unsigned)(bytesF + args.box_a * Ls));
+      tma_load_2d(stF, tmF, fx0, ly0, mbar);
+      tma_load_2d(stA, tmA, ax0, ly0, mbar);
     }
     bool done = false;
-    for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(&mbar, 0);
+    for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mbar, tma_phase);
     if (!done) {
       atomicOr(args.err, kErrTimeout);
-      if (args.status && tid == 0) args.status[blk] = kBlkTimeout;
-      // wait (bounded again) for the copy in flight before the CTA retires
-      for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(&mbar, 0);
+      // wait (bounded again) for the copy in flight before giving up on the block
+      for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mbar, tma_phase);
+    }
+    tma_phase ^= 1u;
+    if (!__syncthreads_and(done)) {
+      if (tid == 0 && args.status) args.status[blk] = kBlkTimeout;
       return;
     }
   }
 
   // ---- 2. weighting and the packed input z = w f + j w (bit-reversed) -------
   constexpr int PER = (T * T + NT - 1) / NT;
+  using Mask = typename std::conditional<(PER > 32), unsigned long long, unsigned>::type;
   float fv[PER];
-  unsigned use = 0;
+  Mask use = 0;
   bool bad = false;
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
@@ -518,21 +572,21 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
           f = in ? args.frame[(size_t)fy * args.pitch + fx] : 0.f;
         }
         if (av && !inB && inS) {
-          use |= 1u << s;
+          use |= Mask(1) << s;
           fv[s] = f;
           bad |= !isfinite(f);
         }
       }
     }
   }
-  int any_bad = __syncthreads_or(bad);  // the staging area is overwritten below
+  int any_bad = __syncthreads_or(bad);  // the staging area may be overwritten below
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
     const int e = tid + s * NT;
     if (e < T * T) {
       const int r = e >> LOGT, c = e & (T - 1);
       C z = A::zero();
-      if (use & (1u << s)) {
+      if (use & (Mask(1) << s)) {
         const int m = __brev(r) >> (32 - LOGT), n = __brev(c) >> (32 - LOGT);
         C wdummy;
         z = IO::weighted(P.tab, m * Ls + n, fv[s], wdummy);
@@ -551,53 +605,72 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
   C R[NB];
   int kc[NB];  // x_k | code << 16
 #pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    kc[i] = 0;
-    R[i] = A::zero();
-    if (i < NBF || tid < 2) {
-      const int x = i < NBF ? slot_xk<T>(tid + i * NT) : extra_xk<T>(tid);
+  for (int i = 0; i <= NB; ++i) {
+    if (i == NB && tid >= 2) break;
+    const int x = i < NB ? slot_xk<T>(tid + i * NT) : extra_xk<T>(tid);
+    const int k1 = x >> (LOGT + 1), k2 = x & (T2 - 1);
+    const int mx = ((T - k1) & (T - 1)) * T2 + ((T - k2) & (T - 1));
+    const C a = A::load(Z, x, T), m = A::load(Z, mx, T);
+    const C r = A::half(A::add(a, A::conj(m)));
+    if (!A::finite(r)) bad = true;
+    if (i < NB) {
       kc[i] = x | (code_of<T>(x) << 16);
-      const int k1 = x >> (LOGT + 1), k2 = x & (T2 - 1);
-      const int mx = ((T - k1) & (T - 1)) * T2 + ((T - k2) & (T - 1));
-      C a = A::load(Z, x, T), m = A::load(Z, mx, T);
-      R[i] = A::half(A::add(a, A::conj(m)));
-      if (!A::finite(R[i])) bad = true;
+      R[i] = r;
+    } else {
+      ex[tid] = r;
     }
   }
   any_bad |= __syncthreads_or(bad);
-  // ---- W[k] = (Z[k] - conj Z[-k]) / (2j) in place, W[-k] = conj W[k] ---------
-  for (int e = tid; e < T * T; e += NT) {
-    const int k1 = e >> LOGT, k2 = e & (T - 1);
-    const int m1 = (T - k1) & (T - 1), m2 = (T - k2) & (T - 1);
-    const int me = m1 * T + m2;
-    if (e <= me) {
+  // ---- W[k] = (Z[k] - conj Z[-k]) / (2j) ----------------------------------------
+  if (!HALF) {  // in place over the full grid, W[-k] = conj W[k]
+    for (int e = tid; e < T * T; e += NT) {
+      const int k1 = e >> LOGT, k2 = e & (T - 1);
+      const int m1 = (T - k1) & (T - 1), m2 = (T - k2) & (T - 1);
+      const int me = m1 * T + m2;
+      if (e <= me) {
+        C a = A::load(Z, k1 * T2 + k2, T), m = A::load(Z, m1 * T2 + m2, T);
+        C d = A::sub(a, A::conj(m));  // W = -j d / 2
+        C wv;
+        wv.re = d.im;
+        wv.im = d.re;
+        wv = A::conj(A::half(wv));
+        A::store(Z, k1 * T2 + k2, T, wv);
+        if (me != e) A::store(Z, m1 * T2 + m2, T, A::conj(wv));
+      }
+    }
+  } else {  // Hermitian half from the global FFT buffer into shared memory
+    constexpr int HO = WTab<A, T, true>::HO, HS = WTab<A, T, true>::HS;
+    for (int e = tid; e < T * HO; e += NT) {
+      const int k1 = e / HO, k2 = e - k1 * HO;
+      const int m1 = (T - k1) & (T - 1), m2 = (T - k2) & (T - 1);
       C a = A::load(Z, k1 * T2 + k2, T), m = A::load(Z, m1 * T2 + m2, T);
-      C d = A::sub(a, A::conj(m));  // W = -j d / 2
+      C d = A::sub(a, A::conj(m));
       C wv;
       wv.re = d.im;
       wv.im = d.re;
       wv = A::conj(A::half(wv));
-      A::store(Z, k1 * T2 + k2, T, wv);
-      if (me != e) A::store(Z, m1 * T2 + m2, T, A::conj(wv));
+      A::store(Wsm + k1 * HS, k2, HO, wv);
     }
   }
   __syncthreads();
 
-  const C W0c = A::load(Z, 0, T);
+  const C W0c = WT::at0(Wsm);
   int st = FOFSE_BLK_OK;
   if (IO::w0_zero(W0c)) st = FOFSE_BLK_NO_SUPPORT;
   else if (any_bad || !IO::w0_finite(W0c)) st = FOFSE_BLK_NONFINITE;
 
   if (st == FOFSE_BLK_OK) {
     const auto inv = IO::inv_w0(IO::gamma(P), W0c.re);
-    // initial candidates
     Cand<A> best = empty_cand<A>();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-      if (i < NBF || tid < 2) {
-        const Cand<A> c = make_cand(R[i], kc[i] >> 16);
-        if (better(c, best)) best = c;
-      }
+      const Cand<A> c = make_cand(R[i], kc[i] >> 16);
+      if (better(c, best)) best = c;
+    }
+    if (tid < 2) {
+      const int x = extra_xk<T>(tid);
+      const Cand<A> c = make_cand(ex[tid], code_of<T>(x));
+      if (better(c, best)) best = c;
     }
 #pragma unroll 1
     for (int it = 0; it < iters; ++it) {
@@ -631,25 +704,31 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
       if (!sc) {
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-          if (i < NBF || tid < 2) {
-            const int x = kc[i] & 0xffff;
-            const C Wm = A::load(Z, (x + T - y) & G::M, T);
-            const C Wp = A::load(Z, (x + y) & G::M, T);
-            Upd<A>::pair(R[i], c, Wm, Wp);
-            const Cand<A> cd = make_cand(R[i], kc[i] >> 16);
-            if (better(cd, best)) best = cd;
-          }
+          const int x = kc[i] & 0xffff;
+          const C Wm = WT::minus(Wsm, x, y);
+          const C Wp = WT::plus(Wsm, x, y);
+          Upd<A>::pair(R[i], c, Wm, Wp);
+          const Cand<A> cd = make_cand(R[i], kc[i] >> 16);
+          if (better(cd, best)) best = cd;
         }
       } else {
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-          if (i < NBF || tid < 2) {
-            const C Wm = A::load(Z, ((kc[i] & 0xffff) + T - y) & G::M, T);
-            Upd<A>::single(R[i], c, Wm);
-            const Cand<A> cd = make_cand(R[i], kc[i] >> 16);
-            if (better(cd, best)) best = cd;
-          }
+          const C Wm = WT::minus(Wsm, kc[i] & 0xffff, y);
+          Upd<A>::single(R[i], c, Wm);
+          const Cand<A> cd = make_cand(R[i], kc[i] >> 16);
+          if (better(cd, best)) best = cd;
         }
+      }
+      if (tid < 2) {  // the two bins kept in shared memory (only this thread touches its own)
+        const int x = extra_xk<T>(tid);
+        C r = ex[tid];
+        const C Wm = WT::minus(Wsm, x, y);
+        if (!sc) Upd<A>::pair(r, c, Wm, WT::plus(Wsm, x, y));
+        else Upd<A>::single(r, c, Wm);
+        ex[tid] = r;
+        const Cand<A> cd = make_cand(r, code_of<T>(x));
+        if (better(cd, best)) best = cd;
       }
     }
   }
@@ -696,57 +775,113 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
     if (args.w0) args.w0[blk] = st == FOFSE_BLK_OK ? IO::w0_out(W0c) : 0.f;
     if (args.status) args.status[blk] = st;
   }
+  __syncthreads();  // shared memory is reused by the next block
 }
 
-template <class A, int T, int NT> size_t smem_bytes(int iters) {
-  size_t off = 1024 + sizeof(typename A::E) * T * 2 * T;  // + alignment slack
-  off += sizeof(typename A::C) * (T / 2);
-  off += sizeof(typename PlanIO<A>::Syn) * T;
-  off += sizeof(Cand<A>) * 2 * (NT / 32);
-  off = (off + 15) & ~size_t(15);
-  off += sizeof(TraceSm<A>) * (size_t)iters;
-  return off;
+// Persistent kernel: each CTA takes blocks from the work queue of its plan (an
+// atomic counter over the block list; entries of other plans are skipped)
+// until the list is exhausted.  Without a queue, block i goes to CTA i mod grid.
+template <class A, int T, int NT, int MINB, bool HALF>
+__global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_constant__ FwdArgs args,
+                                                           const __grid_constant__ CUtensorMap tmF,
+                                                           const __grid_constant__ CUtensorMap tmA) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t mbar;
+  __shared__ int s_item;
+  unsigned tma_phase = 0;
+  if (args.use_tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(&mbar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  typename A::E* Zg = nullptr;
+  if (HALF)
+    Zg = reinterpret_cast<typename A::E*>(args.scratch) +
+         (size_t)blockIdx.x * FwdLayout<A, T, NT, HALF>::scratch_elems;
+  int next = blockIdx.x;
+  for (;;) {
+    int item;
+    if (args.queue) {
+      if (threadIdx.x == 0) s_item = atomicAdd(args.queue, 1);
+      __syncthreads();
+      item = s_item;
+      __syncthreads();
+    } else {
+      item = next;
+      next += gridDim.x;
+    }
+    if (item >= args.n_blocks) break;
+    if (args.blocks[item].plan != args.plan_index) continue;
+    forward_block<A, T, NT, HALF>(args, &tmF, &tmA, item, smem, &mbar, tma_phase, Zg);
+  }
 }
 
-template <class A, int T, int NT, int MINB = 1>
+template <class A, int T, int NT, int MINB, bool HALF>
 cudaError_t launch_one(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
                        cudaStream_t s) {
-  const size_t sm = smem_bytes<A, T, NT>(a.plan.iters);
-  auto kern = fofse_forward_kernel<A, T, NT, MINB>;
+  const size_t sm = FwdLayout<A, T, NT, HALF>::bytes(a.plan.iters);
+  auto kern = fofse_forward_kernel<A, T, NT, MINB, HALF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  kern<<<a.n_blocks, NT, sm, s>>>(a, *tf, *ta);
+  int dev = 0, sms = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, sm)) != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  int grid = sms * per;
+  if (HALF) grid = sms < a.scratch_ctas ? sms : a.scratch_ctas;  // one scratch slot per CTA
+  if (grid > a.n_blocks) grid = a.n_blocks;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, NT, sm, s>>>(a, *tf, *ta);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t forward_smem_bytes(int precision, int T, int iters) {
+  if (T == 128) {
+    if (precision == FOFSE_FP64_VALIDATE) return FwdLayout<ArF64, 128, 512, true>::bytes(iters);
+    if (precision == FOFSE_FP32_PLAIN) return FwdLayout<ArF32, 128, 512, true>::bytes(iters);
+    return FwdLayout<ArFF, 128, 512, true>::bytes(iters);
+  }
   if (T == 64) {
-    if (precision == FOFSE_FP64_VALIDATE) return smem_bytes<ArF64, 64, 256>(iters);
-    if (precision == FOFSE_FP32_PLAIN) return smem_bytes<ArF32, 64, 256>(iters);
-    return smem_bytes<ArFF, 64, 256>(iters);
+    if (precision == FOFSE_FP64_VALIDATE) return FwdLayout<ArF64, 64, 256, false>::bytes(iters);
+    if (precision == FOFSE_FP32_PLAIN) return FwdLayout<ArF32, 64, 256, false>::bytes(iters);
+    return FwdLayout<ArFF, 64, 256, false>::bytes(iters);
   }
   if (T == 32) {
-    if (precision == FOFSE_FP64_VALIDATE) return smem_bytes<ArF64, 32, 128>(iters);
-    if (precision == FOFSE_FP32_PLAIN) return smem_bytes<ArF32, 32, 128>(iters);
-    return smem_bytes<ArFF, 32, 128>(iters);
+    if (precision == FOFSE_FP64_VALIDATE) return FwdLayout<ArF64, 32, 128, false>::bytes(iters);
+    if (precision == FOFSE_FP32_PLAIN) return FwdLayout<ArF32, 32, 128, false>::bytes(iters);
+    return FwdLayout<ArFF, 32, 128, false>::bytes(iters);
   }
   return 0;
+}
+
+size_t forward_scratch_bytes_per_cta(int T) {
+  return T == 128 ? sizeof(float2) * 128 * 256 : 0;  // E is 8 bytes for every back-end
 }
 
 cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
                            cudaStream_t s) {
   const int T = a.plan.T, pr = a.plan.precision;
+  if (T == 128) {
+    if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 128, 512, 1, true>(a, tf, ta, s);
+    if (pr == FOFSE_FP32_PLAIN) return launch_one<ArF32, 128, 512, 1, true>(a, tf, ta, s);
+    return launch_one<ArFF, 128, 512, 1, true>(a, tf, ta, s);
+  }
   if (T == 64) {
-    if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 64, 256>(a, tf, ta, s);
-    if (pr == FOFSE_FP32_PLAIN) return launch_one<ArF32, 64, 256>(a, tf, ta, s);
-    return launch_one<ArFF, 64, 256, 3>(a, tf, ta, s);
+    if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 64, 256, 1, false>(a, tf, ta, s);
+    if (pr == FOFSE_FP32_PLAIN) return launch_one<ArF32, 64, 256, 3, false>(a, tf, ta, s);
+    return launch_one<ArFF, 64, 256, 3, false>(a, tf, ta, s);
   }
   if (T == 32) {
-    if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 32, 128>(a, tf, ta, s);
-    if (pr == FOFSE_FP32_PLAIN) return launch_one<ArF32, 32, 128>(a, tf, ta, s);
-    return launch_one<ArFF, 32, 128>(a, tf, ta, s);
+    if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 32, 128, 1, false>(a, tf, ta, s);
+    if (pr == FOFSE_FP32_PLAIN) return launch_one<ArF32, 32, 128, 1, false>(a, tf, ta, s);
+    return launch_one<ArFF, 32, 128, 6, false>(a, tf, ta, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -52,6 +52,9 @@ struct FwdArgs {
   int use_tma;
   int box_f, box_a;  // TMA box widths (elements) of the frame and mask tiles
   unsigned* err;
+  int* queue;        // work-queue counter of this plan (zeroed before the launch); may be null
+  void* scratch;     // per-CTA global scratch (FFT buffers at T = 128)
+  int scratch_ctas;  // number of scratch slots
 };
 
 struct BwdArgs {
@@ -76,6 +79,7 @@ struct BwdArgs {
 cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tm_frame,
                            const CUtensorMap* tm_avail, cudaStream_t stream);
 size_t forward_smem_bytes(int precision, int T, int iters);
+size_t forward_scratch_bytes_per_cta(int T);
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t stream);
 
 }  // namespace fofse

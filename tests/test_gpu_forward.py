@@ -163,3 +163,47 @@ def test_plain_fp32_mode_runs_and_is_close(c1):
     assert c["status_equal"]
     assert c["frac"] > 0.3, c["frac"]
     assert c["max_err"] <= 0.05, c["max_err"]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_fft128_class_small_frame(precision):
+    """32x32 blocks, border 16, 128x128 FFT (Hermitian-half W in shared memory,
+    FFT in global scratch), 400 iterations; corners included."""
+    spec = synth.PlanSpec(32, 16, 128, 0.8, 0.5, 400)
+    wl = synth.small_frame(31, height=160, width=192, plan=spec, n_lost=5, fill=np.nan)
+    ora = _oracle(wl)
+    res, _ = run_gpu(wl, precision)
+    c = compare(wl, res, ora)
+    assert c["status_equal"]
+    assert c["same"] == c["n"], c
+    assert c["max_err"] <= (1e-3 if precision == "fp32" else FP32_OUT)
+
+
+def test_uneven_batch_4k_sampled():
+    """The 3840x2160 uneven batch (4x4 / 8x8 / 16x16 / 32x32 blocks, T 32/32/64/128,
+    50/100/200/400 iterations, ~20 % of the area lost) in one call; the oracle
+    checks a sample of blocks of every class one by one."""
+    wl = synth.uneven_batch()
+    res, _ = run_gpu(wl, "fp32")
+    st = res.status.cpu().numpy()
+    assert (st == 0).mean() > 0.98          # bursts can leave small blocks without support
+    assert set(np.unique(st)) <= {0, 1}
+    rng = np.random.default_rng(7)
+    pick = []
+    for c in range(len(wl.plans)):
+        idx = np.flatnonzero(wl.blocks[:, 2] == c)
+        assert len(idx) > 100
+        pick += list(rng.choice(idx, size=6 if c == 3 else 12, replace=False))
+    pick = np.array(sorted(pick))
+    sub = synth.Workload(wl.name, wl.frame, wl.truth, wl.avail, wl.blocks[pick], wl.plans)
+    ora = _oracle(sub)
+    assert np.array_equal(st[pick], ora.status)
+    g_path = res.path()[pick]
+    g_blocks = res.blocks.cpu().numpy()[pick].astype(np.float64)
+    same = 0
+    for j, i in enumerate(pick):
+        p = wl.plans[wl.blocks[i, 2]]
+        if np.array_equal(g_path[j, :p.iters], ora.path[j, :p.iters]):
+            same += 1
+            assert np.abs(g_blocks[j, :p.block, :p.block] - ora.blocks[j, :p.block, :p.block]).max() <= 1e-3
+    assert same == len(pick)
