@@ -133,10 +133,14 @@ size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks)
  *   d_out_frame        nullable; B_hat is written into it at each block (other
  *                      samples untouched); may alias d_frame only if no block's
  *                      L overlaps another block's B
- *   d_out_blocks       nullable; n_blocks x out_stride floats, out_stride =
- *                      (max block side over the plans)^2; B_hat row-major b x b
- *   d_trace, d_w0      nullable; n_blocks x max_iters entries / n_blocks floats
- *                      (W[0] = sum of w); required for fofse_backward
+ *   d_out_blocks       nullable; n_blocks x bmax x bmax floats, bmax = the
+ *                      largest block side over the plans; B_hat fills the
+ *                      top-left b x b corner of its bmax x bmax row-major tile,
+ *                      the rest is written as zero
+ *   d_trace, d_w0      nullable; n_blocks x max_iters entries (max over the plans;
+ *                      entries past a block's own iteration count are zero) /
+ *                      n_blocks floats (W[0] = sum of w); required for
+ *                      fofse_backward
  *   d_block_status     nullable; n_blocks int32 (FOFSE_BLK_*).  Blocks that are
  *                      not OK get B_hat = 0 and an all-zero trace
  *   d_workspace        fofse_workspace_bytes() bytes, caller-owned, 256-byte
@@ -162,7 +166,7 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
  * fofse_backward -- adjoint of fofse_extrapolate_batch with the selection path
  * frozen (the map from the support samples to B_hat is then linear).
  *   d_trace, d_w0      from the forward call with the same inputs
- *   d_grad_blocks      dloss/dB_hat, n_blocks x out_stride (as d_out_blocks)
+ *   d_grad_blocks      dloss/dB_hat, n_blocks x bmax x bmax (as d_out_blocks)
  *   d_grad_frame       nullable; dloss/df ACCUMULATED (+=) at every sample of A
  *   d_grad_rho_gamma   nullable; n_plans x 2 floats, ACCUMULATED (+=)
  * Not implemented for FOFSE_FP64_VALIDATE plans or fft_size 128

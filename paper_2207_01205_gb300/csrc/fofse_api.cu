@@ -311,6 +311,7 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
     a.out_frame = d_out_frame;
     a.out_blocks = d_out_blocks;
     a.out_stride = bmax * bmax;
+    a.out_ld = bmax;
     a.trace = d_trace;
     a.trace_stride = imax;
     a.w0 = d_w0;
@@ -377,6 +378,7 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
     a.w0 = d_w0;
     a.grad_blocks = d_grad_blocks;
     a.grad_stride = bmax * bmax;
+    a.grad_ld = bmax;
     a.grad_frame = d_grad_frame;
     a.grad_rho_gamma = d_grad_rho_gamma ? d_grad_rho_gamma + 2 * pi : nullptr;
     a.err = err;

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
       const int fy = ly0 + m, fx = lx0 + n;
       const bool in = fy >= 0 && fy < args.height && fx >= 0 && fx < args.width;
       if (in && !inB && inS && args.avail[(size_t)fy * args.pitch + fx]) wv = P.tab.w_f32[m * Ls + n];
-      if (inB) ev = args.grad_blocks[(size_t)blk * args.grad_stride + (m - br) * b + (n - br)];
+      if (inB) ev = args.grad_blocks[(size_t)blk * args.grad_stride + (m - br) * args.grad_ld + (n - br)];
     }
     Z[r * T2 + c] = wv;
     Z[r * T2 + T + c] = ev;

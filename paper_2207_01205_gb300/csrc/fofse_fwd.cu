@@ -735,28 +735,34 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
   __syncthreads();
 
   // ---- 5. synthesis of B (Eq. 1) and outputs ---------------------------------
+  // The packed output row of a block is out_ld x out_ld (the largest block side
+  // of the call); B_hat fills its top-left b x b corner, the rest is zero.
   using SA = typename IO::SynAcc;
   const int nIt = (st == FOFSE_BLK_OK) ? iters : 0;
-  for (int p = tid; p < b * b; p += NT) {
-    const int bm = p / b, bn = p - bm * b;
-    const int m = br + bm, n = br + bn;
-    SA acc = 0;
-    for (int i = 0; i < nIt; ++i) {
-      const TraceSm<A> t = tr[i];
-      const int ph = ((t.u >> 16) * m + (t.u & 0xffff) * n) & (T - 1);
-      const Syn cs = syn[ph];
-      acc += t.re * cs.x - t.im * cs.y;
+  const int ld = args.out_ld;
+  for (int p = tid; p < ld * ld; p += NT) {
+    const int bm = p / ld, bn = p - bm * ld;
+    float v = 0.f;
+    if (bm < b && bn < b) {
+      const int m = br + bm, n = br + bn;
+      SA acc = 0;
+      for (int i = 0; i < nIt; ++i) {
+        const TraceSm<A> t = tr[i];
+        const int ph = ((t.u >> 16) * m + (t.u & 0xffff) * n) & (T - 1);
+        const Syn cs = syn[ph];
+        acc += t.re * cs.x - t.im * cs.y;
+      }
+      v = (float)acc;
+      if (args.out_frame) {
+        const int fy = bd.y + bm, fx = bd.x + bn;
+        if (fy >= 0 && fy < args.height && fx >= 0 && fx < args.width)
+          args.out_frame[(size_t)fy * args.pitch + fx] = v;
+      }
     }
-    const float v = (float)acc;
     if (args.out_blocks) args.out_blocks[(size_t)blk * args.out_stride + p] = v;
-    if (args.out_frame) {
-      const int fy = bd.y + bm, fx = bd.x + bn;
-      if (fy >= 0 && fy < args.height && fx >= 0 && fx < args.width)
-        args.out_frame[(size_t)fy * args.pitch + fx] = v;
-    }
   }
-  if (args.trace) {
-    for (int i = tid; i < iters; i += NT) {
+  if (args.trace) {  // the whole row: entries past this plan's iterations are zero
+    for (int i = tid; i < args.trace_stride; i += NT) {
       fofse_trace_entry e;
       if (i < nIt) {
         const TraceSm<A> t = tr[i];

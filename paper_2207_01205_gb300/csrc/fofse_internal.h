@@ -44,7 +44,8 @@ struct FwdArgs {
   int height, width, pitch;
   float* out_frame;
   float* out_blocks;
-  int out_stride;
+  int out_stride;     // floats per block row = out_ld * out_ld
+  int out_ld;         // largest block side of the call
   fofse_trace_entry* trace;
   int trace_stride;
   float* w0;
@@ -70,6 +71,7 @@ struct BwdArgs {
   const float* w0;
   const float* grad_blocks;
   int grad_stride;
+  int grad_ld;
   float* grad_frame;
   float* grad_rho_gamma;  // points at this plan's pair
   unsigned* err;
