@@ -163,6 +163,36 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
                                      int32_t* d_block_status, void* d_workspace, void* stream);
 
 /*
+ * fofse_extrapolate_batch_noalloc -- fofse_extrapolate_batch for callers that
+ * cannot allocate device memory at all: code running where cudaMalloc is not
+ * allowed (for example inside a host callback or under a custom allocator that
+ * forbids it), or a host framework that owns every device buffer and passes
+ * only its inputs and outputs.  This entry point has no counterpart in the
+ * paper; it exists only for those callers.
+ *
+ * Arguments as in fofse_extrapolate_batch, without d_rho_gamma and
+ * d_workspace.  Instead of a workspace it uses one fixed array inside the
+ * library: 64 int work-queue counters (256 bytes) that every GPU loading the
+ * library holds until the process exits.  It never calls cudaMalloc or
+ * cudaFree.  Limits: at most 64 plans (FOFSE_E_ARG beyond), fft_size 32 or 64
+ * only (a 128 x 128 FFT needs 256 KB of scratch per SM: FOFSE_E_UNSUPPORTED).
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array and clears the counters it uses at its start
+ *    (an asynchronous memset on `stream`).  Calls whose work can overlap on the
+ *    GPU (different streams, or different host threads) race on it: serialise
+ *    them.
+ */
+fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plans,
+                                             const fofse_block* d_blocks, int n_blocks,
+                                             const float* d_frame, const uint8_t* d_avail,
+                                             int height, int width, int pitch,
+                                             float* d_out_frame, float* d_out_blocks,
+                                             fofse_trace_entry* d_trace, float* d_w0,
+                                             int32_t* d_block_status, void* stream);
+
+/*
  * fofse_backward -- adjoint of fofse_extrapolate_batch with the selection path
  * frozen (the map from the support samples to B_hat is then linear).
  *   d_trace, d_w0      from the forward call with the same inputs

@@ -68,6 +68,9 @@ def _declare(L):
     L.fofse_extrapolate_batch.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i,
                                           _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.fofse_extrapolate_batch.restype = _i
+    L.fofse_extrapolate_batch_noalloc.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i,
+                                                  _i, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.fofse_extrapolate_batch_noalloc.restype = _i
     L.fofse_backward.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i, _vp, _vp,
                                  _vp, _vp, _vp, _vp, _vp, _vp]
     L.fofse_backward.restype = _i
@@ -167,6 +170,21 @@ def fofse_extrapolate_batch(plans, blocks, frame, avail, *, out_frame=None, out_
         _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
         _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(out_frame), _ptr(out_blocks), _ptr(trace),
         _ptr(w0), _ptr(status), _ptr(workspace), _stream(stream)), "fofse_extrapolate_batch")
+
+
+def fofse_extrapolate_batch_noalloc(plans, blocks, frame, avail, *, out_frame=None, out_blocks=None,
+                                    trace=None, w0=None, status=None, stream=None):
+    """The forward batch call for callers that cannot allocate device memory:
+    no workspace argument; the library's fixed 256-byte counter array is used
+    instead (fft_size 32/64 only; calls that overlap on the GPU must be
+    serialised)."""
+    H, W = frame.shape
+    pitch = frame.stride(0)
+    assert frame.stride(1) == 1 and avail.stride(1) == 1 and avail.stride(0) == pitch
+    _check(load().fofse_extrapolate_batch_noalloc(
+        _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
+        _ptr(avail), H, W, pitch, _ptr(out_frame), _ptr(out_blocks), _ptr(trace), _ptr(w0),
+        _ptr(status), _stream(stream)), "fofse_extrapolate_batch_noalloc")
 
 
 def fofse_backward(plans, blocks, frame, avail, trace, w0, grad_blocks, *, grad_frame=None,

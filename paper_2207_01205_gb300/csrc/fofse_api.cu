@@ -43,6 +43,30 @@ unsigned* err_word_ptr() {
   return cache[dev];
 }
 
+// Scratch of fofse_extrapolate_batch_noalloc: the per-plan work-queue
+// counters, in a fixed array that every device loading this library keeps
+// until the process exits (kNoAllocCounters ints = 256 bytes).  Host code must
+// not pass `g_noalloc_queue` itself to a kernel (on the host it only names a
+// stand-in); it passes the device address looked up below.
+constexpr int kNoAllocCounters = 64;
+static __device__ __align__(256) int g_noalloc_queue[kNoAllocCounters];
+
+// Device address of g_noalloc_queue on the current device, looked up once per
+// device (the first call on a device does this; later calls reuse it).
+int* noalloc_queue_ptr() {
+  static std::mutex mu;
+  static int* cache[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cache[dev]) {
+    int* ptr = nullptr;
+    if (cudaGetSymbolAddress((void**)&ptr, g_noalloc_queue) != cudaSuccess) return nullptr;
+    cache[dev] = ptr;
+  }
+  return cache[dev];
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -334,6 +358,81 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
       a.use_tma = 1;
     cudaError_t e = launch_forward(a, &tf, &ta, s);
     if (e != cudaSuccess) return FOFSE_E_CUDA;
+  }
+  return FOFSE_OK;
+}
+
+// fofse_extrapolate_batch without a workspace: see include/fofse.h.  It
+// launches the same forward kernels as fofse_extrapolate_batch; only the
+// work-queue counters come from the library's fixed device array instead of
+// the caller's workspace.  Nothing here allocates or frees device memory.
+fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plans,
+                                             const fofse_block* d_blocks, int n_blocks,
+                                             const float* d_frame, const uint8_t* d_avail,
+                                             int height, int width, int pitch,
+                                             float* d_out_frame, float* d_out_blocks,
+                                             fofse_trace_entry* d_trace, float* d_w0,
+                                             int32_t* d_block_status, void* stream) {
+  if (!plans || n_plans < 1 || n_blocks < 0) return FOFSE_E_ARG;
+  if (n_plans > kNoAllocCounters) return FOFSE_E_ARG;  // one counter per plan in the fixed array
+  if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail)) return FOFSE_E_ARG;
+  if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
+  int bmax = 0, imax = 0;
+  for (int i = 0; i < n_plans; ++i) {
+    if (!plans[i]) return FOFSE_E_ARG;
+    if (plans[i]->dev.precision != plans[0]->dev.precision) return FOFSE_E_ARG;
+    // a 128 x 128 FFT needs 256 KB of scratch per SM, beyond the fixed array
+    if (forward_scratch_bytes_per_cta(plans[i]->dev.T) > 0) return FOFSE_E_UNSUPPORTED;
+    bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
+    imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
+  }
+  if (n_blocks == 0) return FOFSE_OK;
+  unsigned* err = err_word_ptr();
+  int* queue = noalloc_queue_ptr();
+  if (!err || !queue) return FOFSE_E_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the counters keep the previous call's values: clear them on this stream
+  if (cudaMemsetAsync(queue, 0, sizeof(int) * kNoAllocCounters, s) != cudaSuccess) return FOFSE_E_CUDA;
+  const uintptr_t fa = reinterpret_cast<uintptr_t>(d_frame), aa = reinterpret_cast<uintptr_t>(d_avail);
+  const bool tma_ok = encode_fn() && (fa % 16 == 0) && (aa % 16 == 0) && (pitch % 16 == 0);
+  for (int pi = 0; pi < n_plans; ++pi) {
+    const PlanDev& P = plans[pi]->dev;
+    FwdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.plan = P;
+    a.plan_index = pi;
+    a.blocks = d_blocks;
+    a.n_blocks = n_blocks;
+    a.frame = d_frame;
+    a.avail = d_avail;
+    a.height = height;
+    a.width = width;
+    a.pitch = pitch;
+    a.out_frame = d_out_frame;
+    a.out_blocks = d_out_blocks;
+    a.out_stride = bmax * bmax;
+    a.out_ld = bmax;
+    a.trace = d_trace;
+    a.trace_stride = imax;
+    a.w0 = d_w0;
+    a.status = d_block_status;
+    a.err = err;
+    a.queue = queue + pi;
+    a.scratch = nullptr;
+    a.scratch_ctas = 0;
+    a.box_f = round_up(P.Ls + 3, 4);
+    a.box_a = round_up(P.Ls + 15, 16);
+    CUtensorMap tf, ta;
+    std::memset(&tf, 0, sizeof(tf));
+    std::memset(&ta, 0, sizeof(ta));
+    a.use_tma = 0;
+    if (tma_ok && a.box_f <= 256 && a.box_a <= 256 && P.Ls <= 256 &&
+        encode_2d(&tf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d_frame, width, height, pitch, a.box_f,
+                  P.Ls) &&
+        encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d_avail, width, height, pitch, a.box_a,
+                  P.Ls))
+      a.use_tma = 1;
+    if (launch_forward(a, &tf, &ta, s) != cudaSuccess) return FOFSE_E_CUDA;
   }
   return FOFSE_OK;
 }
