@@ -199,8 +199,7 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
  *   d_grad_blocks      dloss/dB_hat, n_blocks x bmax x bmax (as d_out_blocks)
  *   d_grad_frame       nullable; dloss/df ACCUMULATED (+=) at every sample of A
  *   d_grad_rho_gamma   nullable; n_plans x 2 floats, ACCUMULATED (+=)
- * Not implemented for FOFSE_FP64_VALIDATE plans or fft_size 128
- * (FOFSE_E_UNSUPPORTED).
+ * Not implemented for FOFSE_FP64_VALIDATE plans (FOFSE_E_UNSUPPORTED).
  */
 fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_block* d_blocks,
                             int n_blocks, const float* d_frame, const uint8_t* d_avail,

@@ -9,16 +9,20 @@
 // with R0 = DFT(w f), W = DFT(w).  Its reverse sweep, per CTA (one block):
 //   1. one packed FFT of w + j e (e = dl/dB_hat on B) gives W (kept in shared
 //      memory) and E = DFT(e); cbar_i = (1 + s_i) E[u_i];
-//   2. for i = I..1 (one barrier each): abar_i = gamma/W0 cbar_i;
-//      gammabar += Re(conj(cbar_i) c_i)/gamma; W0bar -= Re(conj(cbar_i) c_i)/W0;
-//      R0bar[u_i] += abar_i; and in parallel over j < i:
-//      cbar_j -= abar_i conj(W[u_i-u_j]) + s_j conj(abar_i) W[u_i+u_j],
-//      Wbar[u_i-u_j] -= abar_i conj(c_j), Wbar[u_i+u_j] -= s_j abar_i c_j
-//      (shared-memory atomics);
-//   3. xbar_R = Re IDFT(R0bar), xbar_W = Re IDFT(Wbar) on L from one packed
-//      inverse FFT of the Hermitian parts;
-//   4. fbar = w xbar_R on A (atomically added into the frame gradient),
-//      wbar = f xbar_R + xbar_W, rhobar = sum_A wbar w dist / rho (Eq. 15).
+//   2. for i = I..1: abar_i = gamma/W0 cbar_i and, for j < i,
+//      cbar_j -= abar_i conj(W[u_i-u_j]) + s_j conj(abar_i) W[u_i+u_j]
+//      (a triangular solve, in tiles of 32 iterations);
+//      gammabar = sum_i Re(conj(cbar_i) c_i)/gamma, W0bar = -sum_i Re(conj(cbar_i) c_i)/W0;
+//   3. back to the samples without a W-adjoint grid: summing the pair terms
+//      over j < i gives the model before iteration i (g_{i-1} = sum_{j<i}
+//      (1 + s_j) Re(c_j phi_{u_j})), so on every sample of A
+//        xbar[m,n] = sum_i Re(abar_i phi_{u_i}[m,n])            (dl/dx, x = w f)
+//        wbar[m,n] = sum_i (f - g_{i-1})[m,n] Re(abar_i phi_{u_i}[m,n]) + W0bar,
+//      accumulated in one pass over the trace while the residual f - g is
+//      rebuilt sample by sample (no atomics, deterministic; wbar comes from
+//      the residual, not from the difference of two large terms);
+//   4. fbar = w xbar on A (atomically added into the frame gradient, blocks
+//      overlap), rhobar = sum_A wbar w dist / rho (Eq. 15).
 // FP32 arithmetic throughout (the gradients' tolerance is relative 1e-3).
 #include <cuda_runtime.h>
 
@@ -44,14 +48,14 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const PlanDev& P = args.plan;
   const int iters = P.iters;
-  float* Z = reinterpret_cast<float*>(smem);  // FFT buffer, then W, then the packed adjoint
-  float* GR = Z + T * T2;                     // R0bar grid (two planes)
-  float* GW = GR + T * T2;                    // Wbar grid
-  Cx* tw = reinterpret_cast<Cx*>(GW + T * T2);
+  float* Z = reinterpret_cast<float*>(smem);  // FFT buffer, then W
+  float2* syn = reinterpret_cast<float2*>(Z + T * T2);  // (cos, sin)(2 pi p / T)
+  Cx* tw = reinterpret_cast<Cx*>(syn + T);
   int* tu = reinterpret_cast<int*>(tw + T / 2);         // u1 << 16 | u2
   float2* tc = reinterpret_cast<float2*>(tu + ((iters + 1) & ~1));  // c_i
   float2* tg = tc + iters;                              // cbar_i
-  double* red = reinterpret_cast<double*>(tg + iters);  // 4 NW
+  float2* ta = tg + iters;                              // abar_i
+  double* red = reinterpret_cast<double*>(ta + iters);  // 4 NW
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int blk = blockIdx.x;
@@ -69,10 +73,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
     tu[i] = ((int)(uint16_t)e.u1 << 16) | (int)(uint16_t)e.u2;
     tc[i] = make_float2(e.dc_re, e.dc_im);
   }
-  for (int e = tid; e < T * T2; e += NT) {
-    GR[e] = 0.f;
-    GW[e] = 0.f;
-  }
+  for (int e = tid; e < T; e += NT) syn[e] = P.tab.syn_f32[e];
   for (int e = tid; e < T / 2; e += NT) tw[e] = {P.tab.tw_f32[e].x, P.tab.tw_f32[e].y};
   for (int e = tid; e < T * T; e += NT) {
     const int r = e >> LOGT, c = e & (T - 1);
@@ -119,44 +120,71 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
   __syncthreads();
 
   // ---- reverse sweep of the triangular recurrence -----------------------------
+  // (a) cbar / abar: a lower-triangular solve, sequential in i (descending).
+  //     It runs in tiles of 32 iterations: warp 0 resolves a tile's diagonal
+  //     part warp-synchronously (lane = iteration within the tile), then every
+  //     thread applies the tile's abar to the earlier iterations.  Two barriers
+  //     per tile instead of one per iteration.
   const float g_w0 = gamma / w0;
-  float gam_acc = 0.f, w0bar = 0.f;
-#pragma unroll 1
-  for (int i = iters - 1; i >= 0; --i) {
-    const int ui = tu[i];
-    const int ui1 = ui >> 16, ui2 = ui & 0xffff;
-    const bool si = !self_conj<T>(ui1, ui2);
-    const float2 cb = tg[i], ci = tc[i];
-    const float dbr = cb.x, dbi = si ? cb.y : 0.f;
-    const float abr = g_w0 * dbr, abi = g_w0 * dbi;
-    if (tid == 0) {
-      const float dot = dbr * ci.x + dbi * ci.y;
-      gam_acc += dot / gamma;
-      w0bar -= dot / w0;
-      GR[ui1 * T2 + ui2] += abr;
-      GR[ui1 * T2 + T + ui2] += abi;
+  for (int hi = iters; hi > 0; hi -= 32) {
+    const int lo = hi > 32 ? hi - 32 : 0;
+    if (warp == 0) {
+      const int j = lo + lane;
+      const bool act = j < hi;
+      const int uj = act ? tu[j] : 0;
+      const int uj1 = uj >> 16, uj2 = uj & 0xffff;
+      const bool sj = !self_conj<T>(uj1, uj2);
+      float2 g = act ? tg[j] : make_float2(0.f, 0.f);
+      float2 ab = make_float2(0.f, 0.f);
+      for (int i = hi - 1; i >= lo; --i) {
+        const int li = i - lo;
+        const int ui = __shfl_sync(0xffffffffu, uj, li);
+        const float gr_i = __shfl_sync(0xffffffffu, g.x, li);
+        const float gi_i = __shfl_sync(0xffffffffu, g.y, li);
+        const int ui1 = ui >> 16, ui2 = ui & 0xffff;
+        const bool si = !self_conj<T>(ui1, ui2);
+        const float abr = g_w0 * gr_i, abi = si ? g_w0 * gi_i : 0.f;
+        if (lane == li) ab = make_float2(abr, abi);
+        if (act && lane < li) {
+          const int dm = ((ui1 - uj1) & (T - 1)) * T2 + ((ui2 - uj2) & (T - 1));
+          const Cx Wm = A::load(Z, dm, T);
+          float gr = abr * Wm.re + abi * Wm.im;
+          float gi = abi * Wm.re - abr * Wm.im;
+          if (sj) {
+            const int dp = ((ui1 + uj1) & (T - 1)) * T2 + ((ui2 + uj2) & (T - 1));
+            const Cx Wp = A::load(Z, dp, T);
+            gr += abr * Wp.re + abi * Wp.im;
+            gi += abr * Wp.im - abi * Wp.re;
+          }
+          g.x -= gr;
+          g.y -= gi;
+        }
+      }
+      if (act) {
+        tg[j] = g;
+        ta[j] = ab;
+      }
     }
-    for (int j = tid; j < i; j += NT) {
+    __syncthreads();
+    for (int j = tid; j < lo; j += NT) {
       const int uj = tu[j];
       const int uj1 = uj >> 16, uj2 = uj & 0xffff;
       const bool sj = !self_conj<T>(uj1, uj2);
-      const int dm = ((ui1 - uj1) & (T - 1)) * T2 + ((ui2 - uj2) & (T - 1));
-      const int dp = ((ui1 + uj1) & (T - 1)) * T2 + ((ui2 + uj2) & (T - 1));
-      const Cx Wm = A::load(Z, dm, T);
-      const float2 cj = tc[j];
-      // cbar_j -= abar conj(Wm) + s_j conj(abar) Wp
-      float gr = abr * Wm.re + abi * Wm.im;
-      float gi = abi * Wm.re - abr * Wm.im;
-      // Wbar[u_i - u_j] -= abar conj(c_j)
-      atomicAdd(&GW[dm], -(abr * cj.x + abi * cj.y));
-      atomicAdd(&GW[dm + T], -(abi * cj.x - abr * cj.y));
-      if (sj) {
-        const Cx Wp = A::load(Z, dp, T);
-        gr += abr * Wp.re + abi * Wp.im;
-        gi += abr * Wp.im - abi * Wp.re;
-        // Wbar[u_i + u_j] -= abar c_j
-        atomicAdd(&GW[dp], -(abr * cj.x - abi * cj.y));
-        atomicAdd(&GW[dp + T], -(abr * cj.y + abi * cj.x));
+      float gr = 0.f, gi = 0.f;
+      for (int i = lo; i < hi; ++i) {
+        const int ui = tu[i];
+        const int ui1 = ui >> 16, ui2 = ui & 0xffff;
+        const float2 ab = ta[i];
+        const int dm = ((ui1 - uj1) & (T - 1)) * T2 + ((ui2 - uj2) & (T - 1));
+        const Cx Wm = A::load(Z, dm, T);
+        gr += ab.x * Wm.re + ab.y * Wm.im;
+        gi += ab.y * Wm.re - ab.x * Wm.im;
+        if (sj) {
+          const int dp = ((ui1 + uj1) & (T - 1)) * T2 + ((ui2 + uj2) & (T - 1));
+          const Cx Wp = A::load(Z, dp, T);
+          gr += ab.x * Wp.re + ab.y * Wp.im;
+          gi += ab.x * Wp.im - ab.y * Wp.re;
+        }
       }
       float2 g = tg[j];
       g.x -= gr;
@@ -165,25 +193,24 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    GW[0] += w0bar;  // W0 = W[0]
-    if (args.grad_rho_gamma) atomicAdd(&args.grad_rho_gamma[1], gam_acc);
+  // (b) gammabar and W0bar from the final cbar; (1 + s_i) c_i for the model rebuild
+  float dot_acc = 0.f;
+  for (int i = tid; i < iters; i += NT) {
+    const int ui = tu[i];
+    const bool si = !self_conj<T>(ui >> 16, ui & 0xffff);
+    const float2 cb = tg[i], ci = tc[i];
+    dot_acc += cb.x * ci.x + (si ? cb.y * ci.y : 0.f);
+    tg[i] = si ? make_float2(2.f * ci.x, 2.f * ci.y) : ci;  // cbar no longer needed
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dot_acc += __shfl_xor_sync(0xffffffffu, dot_acc, o);
+  if (lane == 0) red[warp] = dot_acc;
   __syncthreads();
-
-  // ---- packed inverse DFT of the Hermitian parts of R0bar and Wbar ------------
-  for (int e = tid; e < T * T; e += NT) {
-    const int k1 = e >> LOGT, k2 = e & (T - 1);
-    const int m1 = (T - k1) & (T - 1), m2 = (T - k2) & (T - 1);
-    const Cx ra = A::load(GR, k1 * T2 + k2, T), rm = A::load(GR, m1 * T2 + m2, T);
-    const Cx wa = A::load(GW, k1 * T2 + k2, T), wm = A::load(GW, m1 * T2 + m2, T);
-    const Cx ah = A::half(A::add(ra, A::conj(rm)));
-    const Cx bh = A::half(A::add(wa, A::conj(wm)));
-    const int r = __brev(k1) >> (32 - LOGT), c = __brev(k2) >> (32 - LOGT);
-    A::store(Z, r * T2 + c, T, Cx{ah.re - bh.im, ah.im + bh.re});
-  }
-  __syncthreads();
-  fft2d_dit<A, T, NT, true>(Z, tw, T, Ls);
+  double dot = 0.0;
+  for (int w = 0; w < NW; ++w) dot += red[w];
+  const float w0bar = (float)(-dot / w0);  // W0 = W[0] = sum of w
+  if (tid == 0 && args.grad_rho_gamma) atomicAdd(&args.grad_rho_gamma[1], (float)(dot / gamma));
+  __syncthreads();  // red is reused below
 
   // ---- chain to the samples, rho and gamma ------------------------------------
   // B_hat is homogeneous of degree 0 in w (scaling w scales R0, W and W[0]
@@ -203,10 +230,22 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
     if (!in || inB || !inS) continue;
     const size_t fi = (size_t)fy * args.pitch + fx;
     if (!args.avail[fi]) continue;
-    const Cx xb = A::load(Z, m * T2 + n, T);  // xbar_R + j xbar_W
+    // rebuild the residual f - g_{i-1} and accumulate xbar, wbar along the trace
+    const float f = args.frame[fi];
+    float r = f, xbar = 0.f, wb = 0.f;
+    for (int i = 0; i < iters; ++i) {
+      const int ui = tu[i];
+      const int ph = ((ui >> 16) * m + (ui & 0xffff) * n) & (T - 1);
+      const float2 cs = syn[ph];
+      const float2 ab = ta[i], cm = tg[i];
+      const float q = ab.x * cs.x - ab.y * cs.y;  // Re(abar_i phi_{u_i})
+      xbar += q;
+      wb = fmaf(r, q, wb);
+      r -= cm.x * cs.x - cm.y * cs.y;             // (1 + s_i) Re(c_i phi_{u_i})
+    }
     const float w = P.tab.w_f32[m * Ls + n];
-    if (args.grad_frame) atomicAdd(&args.grad_frame[fi], w * xb.re);
-    const float wbar = args.frame[fi] * xb.re + xb.im;
+    if (args.grad_frame) atomicAdd(&args.grad_frame[fi], w * xbar);
+    const float wbar = wb + w0bar;
     const float dm = m - c0, dn = n - c0;
     const double d = (double)sqrtf(dm * dm + dn * dn);
     const double ww = (double)wbar * (double)w;
@@ -245,8 +284,8 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
 }
 
 template <int T, int NT> size_t bwd_smem(int iters) {
-  size_t off = 128 + 3 * sizeof(float) * T * 2 * T + sizeof(Cx) * (T / 2);
-  off += sizeof(int) * ((iters + 1) & ~1) + 2 * sizeof(float2) * iters + 4 * sizeof(double) * (NT / 32);
+  size_t off = 128 + sizeof(float) * T * 2 * T + sizeof(float2) * T + sizeof(Cx) * (T / 2);
+  off += sizeof(int) * ((iters + 1) & ~1) + 3 * sizeof(float2) * iters + 4 * sizeof(double) * (NT / 32);
   return off;
 }
 
@@ -263,6 +302,7 @@ template <int T, int NT> cudaError_t launch_bwd(const BwdArgs& a, cudaStream_t s
 
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s) {
   if (a.plan.precision == FOFSE_FP64_VALIDATE) return cudaErrorNotSupported;
+  if (a.plan.T == 128) return launch_bwd<128, 512>(a, s);
   if (a.plan.T == 64) return launch_bwd<64, 256>(a, s);
   if (a.plan.T == 32) return launch_bwd<32, 128>(a, s);
   return cudaErrorNotSupported;

@@ -622,7 +622,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
   }
   any_bad |= __syncthreads_or(bad);
   // ---- W[k] = (Z[k] - conj Z[-k]) / (2j) ----------------------------------------
-  if (!HALF) {  // in place over the full grid, W[-k] = conj W[k]
+  if constexpr (!HALF) {  // in place over the full grid, W[-k] = conj W[k]
     for (int e = tid; e < T * T; e += NT) {
       const int k1 = e >> LOGT, k2 = e & (T - 1);
       const int m1 = (T - k1) & (T - 1), m2 = (T - k2) & (T - 1);
