@@ -66,10 +66,16 @@ enum { FOFSE_SUPPORT_FULL = 0,      /* all of L outside B (concealment)         
        FOFSE_SUPPORT_CAUSAL_L = 1 }; /* rows above B up to B's right edge, plus the
                                         samples left of B in B's rows (prediction)      */
 /* arithmetic of the kernels */
-enum { FOFSE_FP32 = 0,           /* compensated float-float (pairs of FP32): the product */
+enum { FOFSE_FP32 = 0,           /* the product: exact selection path and coefficients
+                                    with FP32 instructions (currently FOFSE_FP32_FULLFF) */
        FOFSE_FP64_VALIDATE = 1,  /* IEEE double; slow on GB300, for validation           */
-       FOFSE_FP32_PLAIN = 2 };   /* plain FP32; diverges from the exact selection path at
+       FOFSE_FP32_PLAIN = 2,     /* plain FP32; diverges from the exact selection path at
                                     near-ties, kept for comparison                       */
+       FOFSE_FP32_FULLFF = 3,    /* every bin updated in float-float (pairs of FP32)      */
+       FOFSE_FP32_FILTERED = 4 };/* FP32 working spectrum with a rigorous error bound;
+                                    the argmax near ties and every coefficient evaluated
+                                    exactly in float-float.  Needs the workspace's
+                                    scratch; without it runs as FOFSE_FP32_FULLFF      */
 /* per-block status written to d_block_status */
 enum { FOFSE_BLK_OK = 0, FOFSE_BLK_NO_SUPPORT = 1, FOFSE_BLK_NONFINITE = 2 };
 
@@ -106,7 +112,8 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
                                int iters, fofse_plan* out);
 /* Support shape (FOFSE_SUPPORT_*); default FULL.  FOFSE_E_ARG for other values. */
 fofse_status fofse_plan_set_support(fofse_plan plan, int shape);
-/* Arithmetic (FOFSE_FP32 default, FOFSE_FP64_VALIDATE, FOFSE_FP32_PLAIN). */
+/* Arithmetic (FOFSE_FP32 default, FOFSE_FP64_VALIDATE, FOFSE_FP32_PLAIN,
+ * FOFSE_FP32_FULLFF, FOFSE_FP32_FILTERED). */
 fofse_status fofse_plan_set_precision(fofse_plan plan, int precision);
 /* Frees the plan's tables (synchronises the device).  NULL is ignored. */
 void fofse_plan_destroy(fofse_plan plan);
@@ -114,9 +121,11 @@ void fofse_plan_destroy(fofse_plan plan);
 /*
  * fofse_workspace_bytes -- device scratch for fofse_extrapolate_batch with
  * these plans on the current device: 256 bytes of work-queue counters (one per
- * plan, zeroed by every call) plus, when a plan has fft_size 128, one 256 KB
- * FFT buffer per SM.  Returns 0 for invalid arguments (more than 64 plans, a
- * NULL plan).
+ * plan, zeroed by every call) plus one slot per resident CTA of the largest
+ * plan kernel: the exact initial spectrum of the block in flight (FOFSE_FP32,
+ * 16 bytes per conjugate pair) and, at fft_size 128, a 256 KB FFT buffer
+ * (about 15 MB for 16x16 blocks with a 64x64 FFT on 152 SMs).  Returns 0 for
+ * invalid arguments (more than 64 plans, a NULL plan).
  */
 size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks);
 
@@ -146,8 +155,9 @@ size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks)
  *   d_workspace        fofse_workspace_bytes() bytes, caller-owned, 256-byte
  *                      aligned; may be NULL when no plan has fft_size 128 (blocks
  *                      are then dealt to the CTAs round-robin instead of through
- *                      the work queue).  A workspace must not be shared by calls
- *                      that may run concurrently.
+ *                      the work queue, and FOFSE_FP32 plans run as
+ *                      FOFSE_FP32_FULLFF).  A workspace must not be shared by
+ *                      calls that may run concurrently.
  *   stream             cudaStream_t
  * Plans are processed largest first (iters * T^2), each by a persistent kernel
  * whose CTAs take that plan's blocks from a work queue.  All plans of one call

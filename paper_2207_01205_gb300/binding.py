@@ -16,9 +16,10 @@ from . import build as _build
 
 OK, E_ARG, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_STATE = range(7)
 SUPPORT_FULL, SUPPORT_CAUSAL_L = 0, 1
-FP32, FP64_VALIDATE, FP32_PLAIN = 0, 1, 2
+FP32, FP64_VALIDATE, FP32_PLAIN, FP32_FULLFF, FP32_FILTERED = 0, 1, 2, 3, 4
 BLK_OK, BLK_NO_SUPPORT, BLK_NONFINITE, BLK_TIMEOUT = 0, 1, 2, 3
-PRECISIONS = {"fp32": FP32, "fp64": FP64_VALIDATE, "fp32_plain": FP32_PLAIN}
+PRECISIONS = {"fp32": FP32, "fp64": FP64_VALIDATE, "fp32_plain": FP32_PLAIN,
+              "fp32_fullff": FP32_FULLFF, "fp32_filtered": FP32_FILTERED}
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                       "fofse.h")

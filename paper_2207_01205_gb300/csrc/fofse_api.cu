@@ -109,13 +109,14 @@ int sm_count() {
   return sms;
 }
 
-size_t scratch_bytes(const fofse_plan* plans, int n_plans, int sms) {
-  size_t per = 0;
+// Plans run one after another on the stream and share one scratch region.
+size_t scratch_bytes(const fofse_plan* plans, int n_plans) {
+  size_t m = 0;
   for (int i = 0; i < n_plans; ++i) {
-    const size_t b = forward_scratch_bytes_per_cta(plans[i]->dev.T);
-    per = b > per ? b : per;
+    const size_t b = forward_scratch_bytes(plans[i]->dev);
+    m = b > m ? b : m;
   }
-  return per * (size_t)sms;
+  return (m + 255) & ~size_t(255);
 }
 
 }  // namespace
@@ -251,7 +252,8 @@ fofse_status fofse_plan_set_support(fofse_plan plan, int shape) {
 
 fofse_status fofse_plan_set_precision(fofse_plan plan, int precision) {
   if (!plan || (precision != FOFSE_FP32 && precision != FOFSE_FP64_VALIDATE &&
-                precision != FOFSE_FP32_PLAIN))
+                precision != FOFSE_FP32_PLAIN && precision != FOFSE_FP32_FULLFF &&
+                precision != FOFSE_FP32_FILTERED))
     return FOFSE_E_ARG;
   plan->dev.precision = precision;
   return FOFSE_OK;
@@ -268,7 +270,7 @@ size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks)
   if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return 0;
   for (int i = 0; i < n_plans; ++i)
     if (!plans[i]) return 0;
-  return kCounterBytes + scratch_bytes(plans, n_plans, sm_count());
+  return kCounterBytes + scratch_bytes(plans, n_plans);
 }
 
 fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
@@ -292,9 +294,9 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
   if (n_blocks == 0) return FOFSE_OK;
   unsigned* err = err_word_ptr();
   if (!err) return FOFSE_E_CUDA;
-  const int sms = sm_count();
-  const size_t scratch = scratch_bytes(plans, n_plans, sms);
-  if (scratch > 0 && !d_workspace) return FOFSE_E_ARG;  // T = 128 needs its FFT scratch
+  const size_t scratch = scratch_bytes(plans, n_plans);
+  for (int i = 0; i < n_plans; ++i)  // T = 128 needs its FFT scratch
+    if (forward_needs_scratch(plans[i]->dev) && !d_workspace) return FOFSE_E_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* queue = nullptr;
   unsigned char* scratch_base = nullptr;
@@ -343,7 +345,7 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
     a.err = err;
     a.queue = queue ? queue + pi : nullptr;
     a.scratch = scratch_base;
-    a.scratch_ctas = sms;
+    a.scratch_bytes = scratch_base ? scratch : 0;
     a.box_f = round_up(P.Ls + 3, 4);
     a.box_a = round_up(P.Ls + 15, 16);
     CUtensorMap tf, ta;
@@ -382,7 +384,7 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
     if (!plans[i]) return FOFSE_E_ARG;
     if (plans[i]->dev.precision != plans[0]->dev.precision) return FOFSE_E_ARG;
     // a 128 x 128 FFT needs 256 KB of scratch per SM, beyond the fixed array
-    if (forward_scratch_bytes_per_cta(plans[i]->dev.T) > 0) return FOFSE_E_UNSUPPORTED;
+    if (forward_needs_scratch(plans[i]->dev)) return FOFSE_E_UNSUPPORTED;
     bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
     imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
   }
@@ -418,8 +420,8 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
     a.status = d_block_status;
     a.err = err;
     a.queue = queue + pi;
-    a.scratch = nullptr;
-    a.scratch_ctas = 0;
+    a.scratch = nullptr;  // FOFSE_FP32 then runs every bin in float-float (no scratch)
+    a.scratch_bytes = 0;
     a.box_f = round_up(P.Ls + 3, 4);
     a.box_a = round_up(P.Ls + 15, 16);
     CUtensorMap tf, ta;

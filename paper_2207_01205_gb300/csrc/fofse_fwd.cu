@@ -445,6 +445,9 @@ template <class A, int T> struct WTab<A, T, false> {
     return A::load(W, (x + y) & M, T);
   }
   __device__ __forceinline__ static C at0(const E* W) { return A::load(W, 0, T); }
+  // part 0 only (the hi plane of a float-float table)
+  __device__ __forceinline__ static E minus0(const E* W, int x, int y) { return W[(x + T - y) & M]; }
+  __device__ __forceinline__ static E plus0(const E* W, int x, int y) { return W[(x + y) & M]; }
 };
 template <class A, int T> struct WTab<A, T, true> {
   using C = typename A::C;
@@ -464,33 +467,203 @@ template <class A, int T> struct WTab<A, T, true> {
   __device__ __forceinline__ static C minus(const E* W, int x, int y) { return get(W, (x + T - y) & M); }
   __device__ __forceinline__ static C plus(const E* W, int x, int y) { return get(W, (x + y) & M); }
   __device__ __forceinline__ static C at0(const E* W) { return A::load(W, 0, HO); }
+  __device__ __forceinline__ static float2 get0(const E* W, int a) {  // float-float hi plane only
+    const int a1 = a >> (LOGT + 1), a2 = a & (T - 1);
+    const bool mir = a2 > T / 2;
+    const int r = mir ? ((T - a1) & (T - 1)) : a1;
+    const int c = mir ? (T - a2) : a2;
+    const float2 v = W[r * HS + c];
+    return mir ? make_float2(v.x, -v.y) : v;
+  }
+  __device__ __forceinline__ static float2 minus0(const E* W, int x, int y) { return get0(W, (x + T - y) & M); }
+  __device__ __forceinline__ static float2 plus0(const E* W, int x, int y) { return get0(W, (x + y) & M); }
 };
 
-template <class A, int T, int NT, bool HALF> struct FwdLayout {
+// Per-thread top-2 of the FP32 magnitude estimates (filtered variant).
+struct Top2 {
+  float m1;   // largest |R32|^2
+  int c1;     // its code (2 * canonical index + mirror flag)
+  int s1;     // its slot (where its exact initial value R0 is kept)
+  float m2;   // largest |R32|^2 among the other bins
+};
+
+template <class A, int T, int NT, bool HALF, bool FILT> struct FwdLayout {
   using C = typename A::C;
   using E = typename A::E;
   using IO = PlanIO<A>;
   static constexpr int NW = NT / 32;
+  static constexpr int NSLOT = T * T / 2;
   // offsets (bytes) from the 1024-aligned base of dynamic shared memory
   static constexpr size_t w_bytes = sizeof(E) * WTab<A, T, HALF>::elems;
   static constexpr size_t tw_off = w_bytes;
   static constexpr size_t syn_off = tw_off + sizeof(C) * (T / 2);
   static constexpr size_t slot_off = syn_off + sizeof(typename IO::Syn) * T;
   static constexpr size_t ex_off = (slot_off + sizeof(Cand<A>) * 2 * NW + 15) & ~size_t(15);
-  static constexpr size_t tr_off = (ex_off + 2 * sizeof(C) + 15) & ~size_t(15);
-  static size_t bytes(int iters) { return 1024 + tr_off + sizeof(TraceSm<A>) * (size_t)iters; }
-  static constexpr size_t scratch_elems = HALF ? (size_t)T * 2 * T : 0;  // per CTA, global
+  // filtered variant: top-2 slots, warp partial sums, candidate list, warp winners
+  static constexpr size_t t2_off = (ex_off + 2 * sizeof(C) + 15) & ~size_t(15);
+  static constexpr size_t red_off = t2_off + (FILT ? sizeof(Top2) * 2 * NW : 0);
+  static constexpr size_t list_off = red_off + (FILT ? sizeof(float4) * NW + 16 * NW : 0);
+  static constexpr size_t ww_off = list_off + (FILT ? sizeof(int2) * NT : 0);
+  static constexpr size_t tr_off = (ww_off + (FILT ? 32 * NW : 0) + 15) & ~size_t(15);
+  // exact trace of the filtered variant: canonical packed index y and c as float-float
+  __host__ __device__ static size_t trx_off(int iters) {
+    return (tr_off + sizeof(TraceSm<A>) * (size_t)iters + 15) & ~size_t(15);
+  }
+  __host__ __device__ static size_t bytes(int iters) {
+    return 1024 + (FILT ? trx_off(iters) + sizeof(int) * (((size_t)iters + 3) & ~size_t(3)) +
+                              sizeof(float4) * (size_t)iters
+                        : tr_off + sizeof(TraceSm<A>) * (size_t)iters);
+  }
+  // per-CTA global scratch: the FFT buffer (half-W variant) and the exact R0 (filtered)
+  static constexpr size_t fft_scratch_bytes = HALF ? sizeof(E) * (size_t)T * 2 * T : 0;
+  static constexpr size_t rx_scratch_bytes = FILT ? sizeof(float4) * (size_t)(NSLOT + 2) : 0;
+  static constexpr size_t scratch_bytes = fft_scratch_bytes + rx_scratch_bytes;
 };
 
+// Build W[k] = (Z[k] - conj Z[-k]) / (2j) from the packed FFT: in place over the
+// full grid (W[-k] = conj W[k]), or its Hermitian half into shared memory.
 template <class A, int T, int NT, bool HALF>
+__device__ __forceinline__ void build_wtab(typename A::E* Z, typename A::E* Wsm) {
+  using C = typename A::C;
+  constexpr int T2 = 2 * T, LOGT = ilog2(T);
+  const int tid = threadIdx.x;
+  if constexpr (!HALF) {
+    for (int e = tid; e < T * T; e += NT) {
+      const int k1 = e >> LOGT, k2 = e & (T - 1);
+      const int m1 = (T - k1) & (T - 1), m2 = (T - k2) & (T - 1);
+      const int me = m1 * T + m2;
+      if (e <= me) {
+        C a = A::load(Z, k1 * T2 + k2, T), m = A::load(Z, m1 * T2 + m2, T);
+        C d = A::sub(a, A::conj(m));  // W = -j d / 2
+        C wv;
+        wv.re = d.im;
+        wv.im = d.re;
+        wv = A::conj(A::half(wv));
+        A::store(Z, k1 * T2 + k2, T, wv);
+        if (me != e) A::store(Z, m1 * T2 + m2, T, A::conj(wv));
+      }
+    }
+  } else {
+    constexpr int HO = WTab<A, T, true>::HO, HS = WTab<A, T, true>::HS;
+    for (int e = tid; e < T * HO; e += NT) {
+      const int k1 = e / HO, k2 = e - k1 * HO;
+      const int m1 = (T - k1) & (T - 1), m2 = (T - k2) & (T - 1);
+      C a = A::load(Z, k1 * T2 + k2, T), m = A::load(Z, m1 * T2 + m2, T);
+      C d = A::sub(a, A::conj(m));
+      C wv;
+      wv.re = d.im;
+      wv.im = d.re;
+      wv = A::conj(A::half(wv));
+      A::store(Wsm + k1 * HS, k2, HO, wv);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// filtered-exact helpers (float-float exact values, FP32 working spectrum)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void top2_insert(Top2& t, float m, int code, int slot) {
+  if (m > t.m1) {
+    t.m2 = t.m1;
+    t.m1 = m;
+    t.c1 = code;
+    t.s1 = slot;
+  } else {
+    t.m2 = fmaxf(t.m2, m);
+  }
+}
+__device__ __forceinline__ void top2_merge(Top2& a, const Top2& b) {
+  if (b.m1 > a.m1 || (b.m1 == a.m1 && b.c1 < a.c1)) {
+    a.m2 = fmaxf(a.m1, b.m2);
+    a.m1 = b.m1;
+    a.c1 = b.c1;
+    a.s1 = b.s1;
+  } else {
+    a.m2 = fmaxf(a.m2, b.m1);
+  }
+}
+__device__ __forceinline__ Top2 top2_shfl(const Top2& t, int o) {
+  Top2 r;
+  r.m1 = __shfl_xor_sync(0xffffffffu, t.m1, o);
+  r.c1 = __shfl_xor_sync(0xffffffffu, t.c1, o);
+  r.s1 = __shfl_xor_sync(0xffffffffu, t.s1, o);
+  r.m2 = __shfl_xor_sync(0xffffffffu, t.m2, o);
+  return r;
+}
+__device__ __forceinline__ float m32(float2 r) { return __fmaf_rn(r.x, r.x, __fmul_rn(r.y, r.y)); }
+
+// FP32 update of one working bin: R -= c W[k-u] + s conj(c) W[k+u] (hi parts of W)
+template <class WT>
+__device__ __forceinline__ void upd32(float2& R, float p, float q, const float2* Wsm, int x, int y,
+                                      bool pair) {
+  const float2 Wm = WT::minus0(Wsm, x, y);
+  float br = 0.f, bi = 0.f;
+  if (pair) {
+    const float2 Wp = WT::plus0(Wsm, x, y);
+    br = Wp.x;
+    bi = Wp.y;
+  }
+  R.x -= __fmaf_rn(p, Wm.x + br, -(q * (Wm.y - bi)));
+  R.y -= __fmaf_rn(p, Wm.y + bi, q * (Wm.x - br));
+}
+
+struct ffc { ff re, im; };
+__device__ __forceinline__ ffc ffc_add(ffc a, ffc b) { return {ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+__device__ __forceinline__ ffc ffc_shfl(ffc v, int o) {
+  return {{__shfl_xor_sync(0xffffffffu, v.re.h, o), __shfl_xor_sync(0xffffffffu, v.re.l, o)},
+          {__shfl_xor_sync(0xffffffffu, v.im.h, o), __shfl_xor_sync(0xffffffffu, v.im.l, o)}};
+}
+__device__ __forceinline__ ffc ffc_warp_sum(ffc v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = ffc_add(v, ffc_shfl(v, o));
+  return v;
+}
+// sum over j in {j0, j0 + stride, ...} < j1 of  c_j W[k - u_j] + s_j conj(c_j) W[k + u_j]
+// (exact float-float; canonical u_j packed as y_j = u1 * 2T + u2, c_j as (re.h, re.l, im.h, im.l))
+template <class WT, int T>
+__device__ __forceinline__ ffc recur_partial(const ArFF::E* Wsm, const int* ty, const float4* tc,
+                                             int x, int j0, int j1, int stride) {
+  ffc acc = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int j = j0; j < j1; j += stride) {
+    const int y = ty[j];
+    const float4 c4 = tc[j];
+    const ArFF::C c = {{c4.x, c4.y}, {c4.z, c4.w}};
+    const int u1 = y >> (ilog2(T) + 1), u2 = y & (2 * T - 1);
+    const bool sc = ((u1 & (T / 2 - 1)) == 0) && ((u2 & (T / 2 - 1)) == 0);
+    const ArFF::C Wm = WT::minus(Wsm, x, y);
+    ArFF::C t;
+    if (!sc) {
+      const ArFF::C Wp = WT::plus(Wsm, x, y);
+      ff s1 = ff_add_raw(Wm.re, Wp.re), s2 = ff_sub_raw(Wm.im, Wp.im);
+      ff s3 = ff_sub_raw(Wm.re, Wp.re), s4 = ff_add_raw(Wm.im, Wp.im);
+      t.re = ff_dot2(c.re, s1, ff_neg(c.im), s2);
+      t.im = ff_dot2(c.re, s4, c.im, s3);
+    } else {
+      t.re = ff_dot2(c.re, Wm.re, ff{0.f, 0.f}, ff{0.f, 0.f});
+      t.im = ff_dot2(c.re, Wm.im, ff{0.f, 0.f}, ff{0.f, 0.f});
+    }
+    acc.re = ff_add(acc.re, t.re);
+    acc.im = ff_add(acc.im, t.im);
+  }
+  return acc;
+}
+// exact order on (value, code): larger |R|^2 first, then the smaller code
+__device__ __forceinline__ bool exact_better(const ffc& a, int ca, const ffc& b, int cb) {
+  const ff ma = ff_norm2(a.re, a.im), mb = ff_norm2(b.re, b.im);
+  if (ma.h != mb.h) return ma.h > mb.h;
+  if (ma.l != mb.l) return ma.l > mb.l;
+  return ca < cb;
+}
+
+template <class A, int T, int NT, bool HALF, bool FILT>
 __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtensorMap* tmF,
                                               const CUtensorMap* tmA, int blk, unsigned char* smem,
                                               uint64_t* mbar, unsigned& tma_phase,
-                                              typename A::E* Zg) {
+                                              unsigned char* cta_scratch) {
   using C = typename A::C;
   using E = typename A::E;
   using IO = PlanIO<A>;
-  using L = FwdLayout<A, T, NT, HALF>;
+  using L = FwdLayout<A, T, NT, HALF, FILT>;
   using WT = WTab<A, T, HALF>;
   constexpr int T2 = 2 * T, LOGT = ilog2(T), NBINS = T * T / 2 + 2;
   constexpr int NSLOT = T * T / 2;
@@ -500,7 +673,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
   static_assert(NBINS == NSLOT + 2, "bins");
 
   E* Wsm = reinterpret_cast<E*>(smem);              // W table (and staging, and FFT if full)
-  E* Z = HALF ? Zg : Wsm;                           // FFT buffer
+  E* Z = HALF ? reinterpret_cast<E*>(cta_scratch) : Wsm;  // FFT buffer
   C* tw = reinterpret_cast<C*>(smem + L::tw_off);
   using Syn = typename IO::Syn;
   Syn* syn = reinterpret_cast<Syn*>(smem + L::syn_off);
@@ -601,6 +774,10 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
   // ---- 3. FFT: rows that hold data, then all columns (radix-2 DIT) ----------
   fft2d_dit<A, T, NT, false>(Z, tw, Ls, T);
 
+  C W0c;
+  int st;
+  if constexpr (!FILT) {
+    // ===== every bin in float-float (or FP64 / plain FP32) =====
   // ---- split: R_w[k] = (Z[k] + conj Z[-k]) / 2 into registers ---------------
   C R[NB];
   int kc[NB];  // x_k | code << 16
@@ -621,44 +798,12 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
     }
   }
   any_bad |= __syncthreads_or(bad);
-  // ---- W[k] = (Z[k] - conj Z[-k]) / (2j) ----------------------------------------
-  if constexpr (!HALF) {  // in place over the full grid, W[-k] = conj W[k]
-    for (int e = tid; e < T * T; e += NT) {
-      const int k1 = e >> LOGT, k2 = e & (T - 1);
-      const int m1 = (T - k1) & (T - 1), m2 = (T - k2) & (T - 1);
-      const int me = m1 * T + m2;
-      if (e <= me) {
-        C a = A::load(Z, k1 * T2 + k2, T), m = A::load(Z, m1 * T2 + m2, T);
-        C d = A::sub(a, A::conj(m));  // W = -j d / 2
-        C wv;
-        wv.re = d.im;
-        wv.im = d.re;
-        wv = A::conj(A::half(wv));
-        A::store(Z, k1 * T2 + k2, T, wv);
-        if (me != e) A::store(Z, m1 * T2 + m2, T, A::conj(wv));
-      }
-    }
-  } else {  // Hermitian half from the global FFT buffer into shared memory
-    constexpr int HO = WTab<A, T, true>::HO, HS = WTab<A, T, true>::HS;
-    for (int e = tid; e < T * HO; e += NT) {
-      const int k1 = e / HO, k2 = e - k1 * HO;
-      const int m1 = (T - k1) & (T - 1), m2 = (T - k2) & (T - 1);
-      C a = A::load(Z, k1 * T2 + k2, T), m = A::load(Z, m1 * T2 + m2, T);
-      C d = A::sub(a, A::conj(m));
-      C wv;
-      wv.re = d.im;
-      wv.im = d.re;
-      wv = A::conj(A::half(wv));
-      A::store(Wsm + k1 * HS, k2, HO, wv);
-    }
-  }
-  __syncthreads();
-
-  const C W0c = WT::at0(Wsm);
-  int st = FOFSE_BLK_OK;
-  if (IO::w0_zero(W0c)) st = FOFSE_BLK_NO_SUPPORT;
-  else if (any_bad || !IO::w0_finite(W0c)) st = FOFSE_BLK_NONFINITE;
-
+    build_wtab<A, T, NT, HALF>(Z, Wsm);
+    __syncthreads();
+    W0c = WT::at0(Wsm);
+    st = FOFSE_BLK_OK;
+    if (IO::w0_zero(W0c)) st = FOFSE_BLK_NO_SUPPORT;
+    else if (any_bad || !IO::w0_finite(W0c)) st = FOFSE_BLK_NONFINITE;
   if (st == FOFSE_BLK_OK) {
     const auto inv = IO::inv_w0(IO::gamma(P), W0c.re);
     Cand<A> best = empty_cand<A>();
@@ -732,6 +877,225 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
       }
     }
   }
+    } else {
+    // ===== FP32 working spectrum, exact (float-float) decisions =====
+    // R32 approximates the exact spectrum R~ of the transform-domain recursion
+    // with a running bound B >= |R32[k] - R~[k]| for every k:
+    //   rounding R0 to FP32 and each FP32 subtraction: <= 1.01 u sqrt(max |R32|^2);
+    //   each FP32 update product: <= 16 u (|Re c| + |Im c|) W[0]  (|W[k]| <= W[0]).
+    // The FP32 top-2 decide the argmax when they are more than 2B apart;
+    // otherwise every bin within the band is evaluated exactly.  The winner's
+    // value, hence its coefficient, is always exact:
+    //   R~[k] = R0[k] - sum_{j<i} ( c_j W[k - u_j] + s_j conj(c_j) W[k + u_j] ).
+    static_assert(std::is_same<A, ArFF>::value, "the filtered variant runs on float-float values");
+    constexpr float kU = 5.9604644775390625e-08f;  // 2^-24
+    constexpr float kUp = 1.f + 4.f * kU, kDn = 1.f - 4.f * kU;
+    Top2* t2s = reinterpret_cast<Top2*>(smem + L::t2_off);
+    float4* red4 = reinterpret_cast<float4*>(smem + L::red_off);
+    int* wtot = reinterpret_cast<int*>(smem + L::red_off + sizeof(float4) * NW);
+    int2* list = reinterpret_cast<int2*>(smem + L::list_off);
+    float4* wwv = reinterpret_cast<float4*>(smem + L::ww_off);
+    int2* wwc = reinterpret_cast<int2*>(smem + L::ww_off + sizeof(float4) * NW);
+    int* trY = reinterpret_cast<int*>(smem + L::trx_off(iters));
+    float4* trC = reinterpret_cast<float4*>(smem + L::trx_off(iters) + sizeof(int) * (((size_t)iters + 3) & ~size_t(3)));
+    float4* Rx = reinterpret_cast<float4*>(cta_scratch + L::fft_scratch_bytes);
+    float2* ex32 = reinterpret_cast<float2*>(ex);
+
+    // ---- split: exact R0 to scratch, FP32 copy to registers ----
+    float2 R32[NB];
+    int kc[NB];
+    Top2 loc = {-1.f, 0x7fffffff, -1, -1.f};
+#pragma unroll
+    for (int i = 0; i <= NB; ++i) {
+      if (i == NB && tid >= 2) break;
+      const int slot = i < NB ? tid + i * NT : NSLOT + tid;
+      const int x = i < NB ? slot_xk<T>(slot) : extra_xk<T>(tid);
+      const int k1 = x >> (LOGT + 1), k2 = x & (T2 - 1);
+      const int mx = ((T - k1) & (T - 1)) * T2 + ((T - k2) & (T - 1));
+      const C a = A::load(Z, x, T), m = A::load(Z, mx, T);
+      const C r = A::half(A::add(a, A::conj(m)));
+      if (!A::finite(r)) bad = true;
+      Rx[slot] = make_float4(r.re.h, r.re.l, r.im.h, r.im.l);
+      const float2 r32 = make_float2(r.re.h, r.im.h);
+      const int code = code_of<T>(x);
+      if (i < NB) {
+        kc[i] = x | (code << 16);
+        R32[i] = r32;
+      } else {
+        ex32[tid] = r32;
+      }
+      top2_insert(loc, m32(r32), code, slot);
+    }
+    any_bad |= __syncthreads_or(bad);
+    build_wtab<A, T, NT, HALF>(Z, Wsm);
+    __syncthreads();
+    W0c = WT::at0(Wsm);
+    st = FOFSE_BLK_OK;
+    if (IO::w0_zero(W0c)) st = FOFSE_BLK_NO_SUPPORT;
+    else if (any_bad || !IO::w0_finite(W0c)) st = FOFSE_BLK_NONFINITE;
+
+    if (st == FOFSE_BLK_OK) {
+      const ff inv = IO::inv_w0(IO::gamma(P), W0c.re);
+      const float W0f = W0c.re.h * (1.f + 1e-6f);
+      float bnd = 0.f, prevabs = 0.f;
+#pragma unroll 1
+      for (int it = 0; it < iters; ++it) {
+        // ---- FP32 top-2 over the block ----
+        Top2 t = loc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) top2_merge(t, top2_shfl(t, o));
+        Top2* ts = t2s + (it & 1) * NW;
+        if (lane == 0) ts[warp] = t;
+        __syncthreads();
+        Top2 g = ts[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) top2_merge(g, ts[w]);
+        const float sM1 = sqrtf(fmaxf(g.m1, 0.f)), sM2 = sqrtf(fmaxf(g.m2, 0.f));
+        bnd += 1.01f * kU * sM1 + 16.f * kU * W0f * prevabs;
+        const bool certain = (sM1 * kDn - bnd * kUp) > (sM2 * kUp + bnd * kUp) ||
+                             (bnd == 0.f && g.m1 == 0.f);  // all exactly zero: index 0 wins
+        int wcode, wslot;
+        ffc Rt;
+        if (certain) {
+          // ---- exact value of the certain winner (all threads share the sum) ----
+          wcode = g.c1;
+          wslot = g.s1;
+          const int canon = wcode >> 1;
+          const int w1 = canon >> LOGT, w2 = canon & (T - 1);
+          const int x = (wcode & 1) ? (((T - w1) & (T - 1)) * T2 + ((T - w2) & (T - 1))) : (w1 * T2 + w2);
+          const float4 r0 = Rx[wslot];
+          ffc part = recur_partial<WT, T>(Wsm, trY, trC, x, tid, it, NT);
+          part = ffc_warp_sum(part);
+          if (lane == 0) red4[warp] = make_float4(part.re.h, part.re.l, part.im.h, part.im.l);
+          __syncthreads();
+          ffc S = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const float4 v = red4[w];
+            S = ffc_add(S, ffc{{v.x, v.y}, {v.z, v.w}});
+          }
+          Rt = {ff_sub(ff{r0.x, r0.y}, S.re), ff_sub(ff{r0.z, r0.w}, S.im)};
+        } else {
+          // ---- near-tie: exact values of every bin within the band ----
+          const float Lb = (sM1 * kDn - 2.f * bnd * kUp) / kUp;
+          const float thr = Lb > 0.f ? Lb * Lb * kDn : -1.f;
+          int cnt = 0;
+#pragma unroll
+          for (int i = 0; i < NB; ++i) cnt += m32(R32[i]) >= thr ? 1 : 0;
+          if (tid < 2) cnt += m32(ex32[tid]) >= thr ? 1 : 0;
+          int incl = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+          }
+          if (lane == 31) wtot[warp] = incl;
+          __syncthreads();
+          int before = 0, total = 0;
+          for (int w = 0; w < NW; ++w) {
+            const int v = wtot[w];
+            before += w < warp ? v : 0;
+            total += v;
+          }
+          const int rank0 = before + incl - cnt;
+          ffc wb = {{0.f, 0.f}, {0.f, 0.f}};
+          int wbc = 0x7fffffff, wbs = -1;
+          for (int pass = 0; pass < total; pass += NT) {
+            int r = rank0;
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+              if (m32(R32[i]) >= thr) {
+                if (r >= pass && r < pass + NT) list[r - pass] = make_int2(kc[i], tid + i * NT);
+                ++r;
+              }
+            }
+            if (tid < 2 && m32(ex32[tid]) >= thr) {
+              if (r >= pass && r < pass + NT) {
+                const int x = extra_xk<T>(tid);
+                list[r - pass] = make_int2(x | (code_of<T>(x) << 16), NSLOT + tid);
+              }
+            }
+            __syncthreads();
+            const int n = min(NT, total - pass);
+            for (int c = warp; c < n; c += NW) {
+              const int2 e = list[c];
+              const float4 r0 = Rx[e.y];
+              ffc part = recur_partial<WT, T>(Wsm, trY, trC, e.x & 0xffff, lane, it, 32);
+              part = ffc_warp_sum(part);
+              const ffc v = {ff_sub(ff{r0.x, r0.y}, part.re), ff_sub(ff{r0.z, r0.w}, part.im)};
+              const int code = e.x >> 16;
+              if (wbc == 0x7fffffff || exact_better(v, code, wb, wbc)) {
+                wb = v;
+                wbc = code;
+                wbs = e.y;
+              }
+            }
+            __syncthreads();
+          }
+          if (lane == 0) {
+            wwv[warp] = make_float4(wb.re.h, wb.re.l, wb.im.h, wb.im.l);
+            wwc[warp] = make_int2(wbc, wbs);
+          }
+          __syncthreads();
+          wcode = 0x7fffffff;
+          wslot = -1;
+          Rt = {{0.f, 0.f}, {0.f, 0.f}};
+          for (int w = 0; w < NW; ++w) {
+            const int2 cs = wwc[w];
+            if (cs.x == 0x7fffffff) continue;
+            const float4 v4 = wwv[w];
+            const ffc v = {{v4.x, v4.y}, {v4.z, v4.w}};
+            if (wcode == 0x7fffffff || exact_better(v, cs.x, Rt, wcode)) {
+              Rt = v;
+              wcode = cs.x;
+              wslot = cs.y;
+            }
+          }
+        }
+        // ---- coefficient (Eq. 5, Eq. 14), exact ----
+        const int canon = wcode >> 1;
+        const bool mir = wcode & 1;
+        const int u1 = canon >> LOGT, u2 = canon & (T - 1);
+        const int s1 = mir ? ((T - u1) & (T - 1)) : u1;
+        const int s2 = mir ? ((T - u2) & (T - 1)) : u2;
+        const bool sc = ((s1 & (T / 2 - 1)) == 0) && ((s2 & (T / 2 - 1)) == 0);
+        C c;
+        c.re = ff_mul(Rt.re, inv);
+        c.im = sc ? ff{0.f, 0.f} : ff_mul(Rt.im, inv);
+        if (tid == 0) {
+          TraceSm<A> tt;
+          tt.u = (u1 << 16) | u2;
+          const float mult = sc ? 1.f : 2.f;
+          tt.re = mult * c.re.h;
+          tt.im = (mir ? -mult : mult) * c.im.h;
+          tt.dre = c.re.h;
+          tt.dim = mir ? -c.im.h : c.im.h;
+          tr[it] = tt;
+          trY[it] = u1 * T2 + u2;
+          trC[it] = mir ? make_float4(c.re.h, c.re.l, -c.im.h, -c.im.l)
+                        : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
+        }
+        // ---- FP32 update of the working spectrum + next local top-2 ----
+        const float p = c.re.h, q = c.im.h;
+        prevabs = fabsf(p) + fabsf(q);
+        const int y = s1 * T2 + s2;
+        loc = {-1.f, 0x7fffffff, -1, -1.f};
+        const float2* W2 = reinterpret_cast<const float2*>(Wsm);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          upd32<WT>(R32[i], p, q, W2, kc[i] & 0xffff, y, !sc);
+          top2_insert(loc, m32(R32[i]), kc[i] >> 16, tid + i * NT);
+        }
+        if (tid < 2) {
+          const int x = extra_xk<T>(tid);
+          float2 r = ex32[tid];
+          upd32<WT>(r, p, q, W2, x, y, !sc);
+          ex32[tid] = r;
+          top2_insert(loc, m32(r), code_of<T>(x), NSLOT + tid);
+        }
+      }
+    }
+  }
   __syncthreads();
 
   // ---- 5. synthesis of B (Eq. 1) and outputs ---------------------------------
@@ -787,7 +1151,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
 // Persistent kernel: each CTA takes blocks from the work queue of its plan (an
 // atomic counter over the block list; entries of other plans are skipped)
 // until the list is exhausted.  Without a queue, block i goes to CTA i mod grid.
-template <class A, int T, int NT, int MINB, bool HALF>
+template <class A, int T, int NT, int MINB, bool HALF, bool FILT>
 __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_constant__ FwdArgs args,
                                                            const __grid_constant__ CUtensorMap tmF,
                                                            const __grid_constant__ CUtensorMap tmA) {
@@ -804,10 +1168,10 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
     }
     __syncthreads();
   }
-  typename A::E* Zg = nullptr;
-  if (HALF)
-    Zg = reinterpret_cast<typename A::E*>(args.scratch) +
-         (size_t)blockIdx.x * FwdLayout<A, T, NT, HALF>::scratch_elems;
+  unsigned char* cta_scratch = nullptr;
+  if (HALF || FILT)
+    cta_scratch = static_cast<unsigned char*>(args.scratch) +
+                  (size_t)blockIdx.x * FwdLayout<A, T, NT, HALF, FILT>::scratch_bytes;
   int next = blockIdx.x;
   for (;;) {
     int item;
@@ -822,73 +1186,112 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
     }
     if (item >= args.n_blocks) break;
     if (args.blocks[item].plan != args.plan_index) continue;
-    forward_block<A, T, NT, HALF>(args, &tmF, &tmA, item, smem, &mbar, tma_phase, Zg);
+    forward_block<A, T, NT, HALF, FILT>(args, &tmF, &tmA, item, smem, &mbar, tma_phase, cta_scratch);
   }
 }
 
-template <class A, int T, int NT, int MINB, bool HALF>
-cudaError_t launch_one(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
-                       cudaStream_t s) {
-  const size_t sm = FwdLayout<A, T, NT, HALF>::bytes(a.plan.iters);
-  auto kern = fofse_forward_kernel<A, T, NT, MINB, HALF>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, sm)) != cudaSuccess) return e;
-  if (per < 1) return cudaErrorInvalidConfiguration;
-  int grid = sms * per;
-  if (HALF) grid = sms < a.scratch_ctas ? sms : a.scratch_ctas;  // one scratch slot per CTA
-  if (grid > a.n_blocks) grid = a.n_blocks;
-  if (grid < 1) return cudaSuccess;
-  kern<<<grid, NT, sm, s>>>(a, *tf, *ta);
-  return cudaGetLastError();
+template <class A, int T, int NT, int MINB, bool HALF, bool FILT> struct Variant {
+  static constexpr size_t per_cta = FwdLayout<A, T, NT, HALF, FILT>::scratch_bytes;
+  static cudaError_t prepare(int iters, size_t* smem, int* max_ctas) {
+    *smem = FwdLayout<A, T, NT, HALF, FILT>::bytes(iters);
+    auto kern = fofse_forward_kernel<A, T, NT, MINB, HALF, FILT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, *smem)) != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    *max_ctas = sms * per;
+    return cudaSuccess;
+  }
+  static cudaError_t scratch(int iters, size_t* bytes) {
+    size_t sm;
+    int ctas;
+    cudaError_t e = prepare(iters, &sm, &ctas);
+    *bytes = e == cudaSuccess ? per_cta * (size_t)ctas : 0;
+    return e;
+  }
+  static cudaError_t launch(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
+                            cudaStream_t s) {
+    size_t sm;
+    int grid;
+    cudaError_t e = prepare(a.plan.iters, &sm, &grid);
+    if (e != cudaSuccess) return e;
+    if (per_cta > 0) {  // one scratch slot per persistent CTA
+      const size_t fit = a.scratch ? a.scratch_bytes / per_cta : 0;
+      if (fit < 1) return cudaErrorInvalidValue;
+      if ((size_t)grid > fit) grid = (int)fit;
+    }
+    if (grid > a.n_blocks) grid = a.n_blocks;
+    if (grid < 1) return cudaSuccess;
+    fofse_forward_kernel<A, T, NT, MINB, HALF, FILT><<<grid, NT, sm, s>>>(a, *tf, *ta);
+    return cudaGetLastError();
+  }
+};
+
+// Kernel choice per (precision, T).  FOFSE_FP32 runs the filtered-exact variant
+// when scratch is available and the all-bins float-float variant otherwise.
+template <int T> struct Pick;
+template <> struct Pick<32> {
+  using FF = Variant<ArFF, 32, 128, 6, false, false>;
+  using FILT = Variant<ArFF, 32, 128, 6, false, true>;
+  using F64 = Variant<ArF64, 32, 128, 1, false, false>;
+  using F32 = Variant<ArF32, 32, 128, 6, false, false>;
+};
+template <> struct Pick<64> {
+  using FF = Variant<ArFF, 64, 256, 3, false, false>;
+  using FILT = Variant<ArFF, 64, 256, 3, false, true>;
+  using F64 = Variant<ArF64, 64, 256, 1, false, false>;
+  using F32 = Variant<ArF32, 64, 256, 3, false, false>;
+};
+template <> struct Pick<128> {
+  using FF = Variant<ArFF, 128, 512, 1, true, false>;
+  using FILT = Variant<ArFF, 128, 512, 1, true, true>;
+  using F64 = Variant<ArF64, 128, 512, 1, true, false>;
+  using F32 = Variant<ArF32, 128, 512, 1, true, false>;
+};
+
+template <int T>
+cudaError_t launch_T(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta, cudaStream_t s) {
+  using Pk = Pick<T>;
+  switch (a.plan.precision) {
+    case FOFSE_FP64_VALIDATE: return Pk::F64::launch(a, tf, ta, s);
+    case FOFSE_FP32_PLAIN: return Pk::F32::launch(a, tf, ta, s);
+    case FOFSE_FP32_FILTERED:
+      if (a.scratch && a.scratch_bytes >= Pk::FILT::per_cta) return Pk::FILT::launch(a, tf, ta, s);
+      return Pk::FF::launch(a, tf, ta, s);
+    default: return Pk::FF::launch(a, tf, ta, s);  // FOFSE_FP32, FOFSE_FP32_FULLFF
+  }
+}
+template <int T> cudaError_t scratch_T(const PlanDev& p, size_t* bytes) {
+  using Pk = Pick<T>;
+  switch (p.precision) {
+    case FOFSE_FP64_VALIDATE: return Pk::F64::scratch(p.iters, bytes);
+    case FOFSE_FP32_PLAIN: return Pk::F32::scratch(p.iters, bytes);
+    case FOFSE_FP32_FILTERED: return Pk::FILT::scratch(p.iters, bytes);
+    default: return Pk::FF::scratch(p.iters, bytes);
+  }
 }
 
 }  // namespace
 
-size_t forward_smem_bytes(int precision, int T, int iters) {
-  if (T == 128) {
-    if (precision == FOFSE_FP64_VALIDATE) return FwdLayout<ArF64, 128, 512, true>::bytes(iters);
-    if (precision == FOFSE_FP32_PLAIN) return FwdLayout<ArF32, 128, 512, true>::bytes(iters);
-    return FwdLayout<ArFF, 128, 512, true>::bytes(iters);
-  }
-  if (T == 64) {
-    if (precision == FOFSE_FP64_VALIDATE) return FwdLayout<ArF64, 64, 256, false>::bytes(iters);
-    if (precision == FOFSE_FP32_PLAIN) return FwdLayout<ArF32, 64, 256, false>::bytes(iters);
-    return FwdLayout<ArFF, 64, 256, false>::bytes(iters);
-  }
-  if (T == 32) {
-    if (precision == FOFSE_FP64_VALIDATE) return FwdLayout<ArF64, 32, 128, false>::bytes(iters);
-    if (precision == FOFSE_FP32_PLAIN) return FwdLayout<ArF32, 32, 128, false>::bytes(iters);
-    return FwdLayout<ArFF, 32, 128, false>::bytes(iters);
-  }
-  return 0;
+size_t forward_scratch_bytes(const PlanDev& p) {
+  size_t b = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (p.T == 32) e = scratch_T<32>(p, &b);
+  if (p.T == 64) e = scratch_T<64>(p, &b);
+  if (p.T == 128) e = scratch_T<128>(p, &b);
+  return e == cudaSuccess ? b : 0;
 }
 
-size_t forward_scratch_bytes_per_cta(int T) {
-  return T == 128 ? sizeof(float2) * 128 * 256 : 0;  // E is 8 bytes for every back-end
-}
+bool forward_needs_scratch(const PlanDev& p) { return p.T == 128; }
 
 cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
                            cudaStream_t s) {
-  const int T = a.plan.T, pr = a.plan.precision;
-  if (T == 128) {
-    if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 128, 512, 1, true>(a, tf, ta, s);
-    if (pr == FOFSE_FP32_PLAIN) return launch_one<ArF32, 128, 512, 1, true>(a, tf, ta, s);
-    return launch_one<ArFF, 128, 512, 1, true>(a, tf, ta, s);
-  }
-  if (T == 64) {
-    if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 64, 256, 1, false>(a, tf, ta, s);
-    if (pr == FOFSE_FP32_PLAIN) return launch_one<ArF32, 64, 256, 3, false>(a, tf, ta, s);
-    return launch_one<ArFF, 64, 256, 3, false>(a, tf, ta, s);
-  }
-  if (T == 32) {
-    if (pr == FOFSE_FP64_VALIDATE) return launch_one<ArF64, 32, 128, 1, false>(a, tf, ta, s);
-    if (pr == FOFSE_FP32_PLAIN) return launch_one<ArF32, 32, 128, 1, false>(a, tf, ta, s);
-    return launch_one<ArFF, 32, 128, 6, false>(a, tf, ta, s);
-  }
+  if (a.plan.T == 128) return launch_T<128>(a, tf, ta, s);
+  if (a.plan.T == 64) return launch_T<64>(a, tf, ta, s);
+  if (a.plan.T == 32) return launch_T<32>(a, tf, ta, s);
   return cudaErrorInvalidValue;
 }
 

@@ -53,9 +53,9 @@ struct FwdArgs {
   int use_tma;
   int box_f, box_a;  // TMA box widths (elements) of the frame and mask tiles
   unsigned* err;
-  int* queue;        // work-queue counter of this plan (zeroed before the launch); may be null
-  void* scratch;     // per-CTA global scratch (FFT buffers at T = 128)
-  int scratch_ctas;  // number of scratch slots
+  int* queue;            // work-queue counter of this plan (zeroed before the launch); may be null
+  void* scratch;         // global scratch, one slot per persistent CTA (may be null)
+  size_t scratch_bytes;  // bytes available at scratch
 };
 
 struct BwdArgs {
@@ -80,8 +80,10 @@ struct BwdArgs {
 // Launchers (one per translation unit).  Return cudaSuccess or the launch error.
 cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tm_frame,
                            const CUtensorMap* tm_avail, cudaStream_t stream);
-size_t forward_smem_bytes(int precision, int T, int iters);
-size_t forward_scratch_bytes_per_cta(int T);
+// Global scratch the forward kernel of this plan uses when given enough
+// (0 if none); a plan with forward_needs_scratch() fails without it.
+size_t forward_scratch_bytes(const PlanDev& p);
+bool forward_needs_scratch(const PlanDev& p);
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t stream);
 
 }  // namespace fofse

@@ -52,7 +52,7 @@ def test_single_block_fp32_matches_oracle():
                                   synth.PlanSpec(8, 8, 32, 0.8, 0.5, 100),
                                   synth.PlanSpec(4, 4, 32, 0.7, 0.3, 50),
                                   synth.PlanSpec(8, 8, 32, 0.8, 0.5, 64, support=1)])
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_filtered"])
 def test_small_frames_with_edge_blocks(spec, precision):
     """Several tiles, blocks in the frame corners (partial support, L beyond the
     frame), lost neighbours, and the lost samples poisoned with NaN."""
@@ -62,7 +62,7 @@ def test_small_frames_with_edge_blocks(spec, precision):
     c = compare(wl, res, ora)
     assert c["status_equal"]
     assert c["same"] == c["n"], c
-    assert c["max_err"] <= (1e-3 if precision == "fp32" else FP32_OUT)
+    assert c["max_err"] <= (FP32_OUT if precision == "fp64" else 1e-3)
 
 
 def test_out_frame_scatter_and_untouched_samples():
@@ -144,6 +144,16 @@ def test_full_frame_1080p_fp32_acceptance(c1):
     assert abs(d_psnr) <= 0.01, d_psnr
 
 
+def test_full_frame_1080p_filtered_exact_paths(c1):
+    """The FP32-working-spectrum variant with exact near-tie resolution."""
+    wl, ora = c1
+    res, _ = run_gpu(wl, "fp32_filtered")
+    c = compare(wl, res, ora)
+    assert c["status_equal"]
+    assert c["same"] == c["n"], c
+    assert c["max_err"] <= 1e-3, c
+
+
 def test_full_frame_1080p_fp64_validation_identical_paths(c1):
     wl, ora = c1
     res, _ = run_gpu(wl, "fp64")
@@ -165,7 +175,7 @@ def test_plain_fp32_mode_runs_and_is_close(c1):
     assert c["max_err"] <= 0.05, c["max_err"]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_filtered"])
 def test_fft128_class_small_frame(precision):
     """32x32 blocks, border 16, 128x128 FFT (Hermitian-half W in shared memory,
     FFT in global scratch), 400 iterations; corners included."""
@@ -176,7 +186,7 @@ def test_fft128_class_small_frame(precision):
     c = compare(wl, res, ora)
     assert c["status_equal"]
     assert c["same"] == c["n"], c
-    assert c["max_err"] <= (1e-3 if precision == "fp32" else FP32_OUT)
+    assert c["max_err"] <= (FP32_OUT if precision == "fp64" else 1e-3)
 
 
 def test_uneven_batch_4k_sampled():
