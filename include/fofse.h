@@ -67,7 +67,8 @@ enum { FOFSE_SUPPORT_FULL = 0,      /* all of L outside B (concealment)         
                                         samples left of B in B's rows (prediction)      */
 /* arithmetic of the kernels */
 enum { FOFSE_FP32 = 0,           /* the product: exact selection path and coefficients
-                                    with FP32 instructions (currently FOFSE_FP32_FULLFF) */
+                                    with FP32 instructions (FOFSE_FP32_FILTERED when the
+                                    workspace is given, else FOFSE_FP32_FULLFF)          */
        FOFSE_FP64_VALIDATE = 1,  /* IEEE double; slow on GB300, for validation           */
        FOFSE_FP32_PLAIN = 2,     /* plain FP32; diverges from the exact selection path at
                                     near-ties, kept for comparison                       */

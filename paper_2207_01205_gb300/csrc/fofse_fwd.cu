@@ -445,9 +445,6 @@ template <class A, int T> struct WTab<A, T, false> {
     return A::load(W, (x + y) & M, T);
   }
   __device__ __forceinline__ static C at0(const E* W) { return A::load(W, 0, T); }
-  // part 0 only (the hi plane of a float-float table)
-  __device__ __forceinline__ static E minus0(const E* W, int x, int y) { return W[(x + T - y) & M]; }
-  __device__ __forceinline__ static E plus0(const E* W, int x, int y) { return W[(x + y) & M]; }
 };
 template <class A, int T> struct WTab<A, T, true> {
   using C = typename A::C;
@@ -467,16 +464,6 @@ template <class A, int T> struct WTab<A, T, true> {
   __device__ __forceinline__ static C minus(const E* W, int x, int y) { return get(W, (x + T - y) & M); }
   __device__ __forceinline__ static C plus(const E* W, int x, int y) { return get(W, (x + y) & M); }
   __device__ __forceinline__ static C at0(const E* W) { return A::load(W, 0, HO); }
-  __device__ __forceinline__ static float2 get0(const E* W, int a) {  // float-float hi plane only
-    const int a1 = a >> (LOGT + 1), a2 = a & (T - 1);
-    const bool mir = a2 > T / 2;
-    const int r = mir ? ((T - a1) & (T - 1)) : a1;
-    const int c = mir ? (T - a2) : a2;
-    const float2 v = W[r * HS + c];
-    return mir ? make_float2(v.x, -v.y) : v;
-  }
-  __device__ __forceinline__ static float2 minus0(const E* W, int x, int y) { return get0(W, (x + T - y) & M); }
-  __device__ __forceinline__ static float2 plus0(const E* W, int x, int y) { return get0(W, (x + y) & M); }
 };
 
 // Per-thread top-2 of the FP32 magnitude estimates (filtered variant).
@@ -487,37 +474,23 @@ struct Top2 {
   float m2;   // largest |R32|^2 among the other bins
 };
 
-template <class A, int T, int NT, bool HALF, bool FILT> struct FwdLayout {
+template <class A, int T, int NT, bool HALF> struct FwdLayout {
   using C = typename A::C;
   using E = typename A::E;
   using IO = PlanIO<A>;
   static constexpr int NW = NT / 32;
-  static constexpr int NSLOT = T * T / 2;
   // offsets (bytes) from the 1024-aligned base of dynamic shared memory
   static constexpr size_t w_bytes = sizeof(E) * WTab<A, T, HALF>::elems;
   static constexpr size_t tw_off = w_bytes;
   static constexpr size_t syn_off = tw_off + sizeof(C) * (T / 2);
   static constexpr size_t slot_off = syn_off + sizeof(typename IO::Syn) * T;
   static constexpr size_t ex_off = (slot_off + sizeof(Cand<A>) * 2 * NW + 15) & ~size_t(15);
-  // filtered variant: top-2 slots, warp partial sums, candidate list, warp winners
-  static constexpr size_t t2_off = (ex_off + 2 * sizeof(C) + 15) & ~size_t(15);
-  static constexpr size_t red_off = t2_off + (FILT ? sizeof(Top2) * 2 * NW : 0);
-  static constexpr size_t list_off = red_off + (FILT ? sizeof(float4) * NW + 16 * NW : 0);
-  static constexpr size_t ww_off = list_off + (FILT ? sizeof(int2) * NT : 0);
-  static constexpr size_t tr_off = (ww_off + (FILT ? 32 * NW : 0) + 15) & ~size_t(15);
-  // exact trace of the filtered variant: canonical packed index y and c as float-float
-  __host__ __device__ static size_t trx_off(int iters) {
-    return (tr_off + sizeof(TraceSm<A>) * (size_t)iters + 15) & ~size_t(15);
-  }
+  static constexpr size_t tr_off = (ex_off + 2 * sizeof(C) + 15) & ~size_t(15);
   __host__ __device__ static size_t bytes(int iters) {
-    return 1024 + (FILT ? trx_off(iters) + sizeof(int) * (((size_t)iters + 3) & ~size_t(3)) +
-                              sizeof(float4) * (size_t)iters
-                        : tr_off + sizeof(TraceSm<A>) * (size_t)iters);
+    return 1024 + tr_off + sizeof(TraceSm<A>) * (size_t)iters;
   }
-  // per-CTA global scratch: the FFT buffer (half-W variant) and the exact R0 (filtered)
-  static constexpr size_t fft_scratch_bytes = HALF ? sizeof(E) * (size_t)T * 2 * T : 0;
-  static constexpr size_t rx_scratch_bytes = FILT ? sizeof(float4) * (size_t)(NSLOT + 2) : 0;
-  static constexpr size_t scratch_bytes = fft_scratch_bytes + rx_scratch_bytes;
+  // per-CTA global scratch: the FFT buffer of the half-W variant
+  static constexpr size_t scratch_bytes = HALF ? sizeof(E) * (size_t)T * 2 * T : 0;
 };
 
 // Build W[k] = (Z[k] - conj Z[-k]) / (2j) from the packed FFT: in place over the
@@ -592,21 +565,6 @@ __device__ __forceinline__ Top2 top2_shfl(const Top2& t, int o) {
 }
 __device__ __forceinline__ float m32(float2 r) { return __fmaf_rn(r.x, r.x, __fmul_rn(r.y, r.y)); }
 
-// FP32 update of one working bin: R -= c W[k-u] + s conj(c) W[k+u] (hi parts of W)
-template <class WT>
-__device__ __forceinline__ void upd32(float2& R, float p, float q, const float2* Wsm, int x, int y,
-                                      bool pair) {
-  const float2 Wm = WT::minus0(Wsm, x, y);
-  float br = 0.f, bi = 0.f;
-  if (pair) {
-    const float2 Wp = WT::plus0(Wsm, x, y);
-    br = Wp.x;
-    bi = Wp.y;
-  }
-  R.x -= __fmaf_rn(p, Wm.x + br, -(q * (Wm.y - bi)));
-  R.y -= __fmaf_rn(p, Wm.y + bi, q * (Wm.x - br));
-}
-
 struct ffc { ff re, im; };
 __device__ __forceinline__ ffc ffc_add(ffc a, ffc b) { return {ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
 __device__ __forceinline__ ffc ffc_shfl(ffc v, int o) {
@@ -655,7 +613,7 @@ __device__ __forceinline__ bool exact_better(const ffc& a, int ca, const ffc& b,
   return ca < cb;
 }
 
-template <class A, int T, int NT, bool HALF, bool FILT>
+template <class A, int T, int NT, bool HALF>
 __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtensorMap* tmF,
                                               const CUtensorMap* tmA, int blk, unsigned char* smem,
                                               uint64_t* mbar, unsigned& tma_phase,
@@ -663,7 +621,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
   using C = typename A::C;
   using E = typename A::E;
   using IO = PlanIO<A>;
-  using L = FwdLayout<A, T, NT, HALF, FILT>;
+  using L = FwdLayout<A, T, NT, HALF>;
   using WT = WTab<A, T, HALF>;
   constexpr int T2 = 2 * T, LOGT = ilog2(T), NBINS = T * T / 2 + 2;
   constexpr int NSLOT = T * T / 2;
@@ -776,8 +734,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
 
   C W0c;
   int st;
-  if constexpr (!FILT) {
-    // ===== every bin in float-float (or FP64 / plain FP32) =====
+  {
   // ---- split: R_w[k] = (Z[k] + conj Z[-k]) / 2 into registers ---------------
   C R[NB];
   int kc[NB];  // x_k | code << 16
@@ -877,225 +834,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
       }
     }
   }
-    } else {
-    // ===== FP32 working spectrum, exact (float-float) decisions =====
-    // R32 approximates the exact spectrum R~ of the transform-domain recursion
-    // with a running bound B >= |R32[k] - R~[k]| for every k:
-    //   rounding R0 to FP32 and each FP32 subtraction: <= 1.01 u sqrt(max |R32|^2);
-    //   each FP32 update product: <= 16 u (|Re c| + |Im c|) W[0]  (|W[k]| <= W[0]).
-    // The FP32 top-2 decide the argmax when they are more than 2B apart;
-    // otherwise every bin within the band is evaluated exactly.  The winner's
-    // value, hence its coefficient, is always exact:
-    //   R~[k] = R0[k] - sum_{j<i} ( c_j W[k - u_j] + s_j conj(c_j) W[k + u_j] ).
-    static_assert(std::is_same<A, ArFF>::value, "the filtered variant runs on float-float values");
-    constexpr float kU = 5.9604644775390625e-08f;  // 2^-24
-    constexpr float kUp = 1.f + 4.f * kU, kDn = 1.f - 4.f * kU;
-    Top2* t2s = reinterpret_cast<Top2*>(smem + L::t2_off);
-    float4* red4 = reinterpret_cast<float4*>(smem + L::red_off);
-    int* wtot = reinterpret_cast<int*>(smem + L::red_off + sizeof(float4) * NW);
-    int2* list = reinterpret_cast<int2*>(smem + L::list_off);
-    float4* wwv = reinterpret_cast<float4*>(smem + L::ww_off);
-    int2* wwc = reinterpret_cast<int2*>(smem + L::ww_off + sizeof(float4) * NW);
-    int* trY = reinterpret_cast<int*>(smem + L::trx_off(iters));
-    float4* trC = reinterpret_cast<float4*>(smem + L::trx_off(iters) + sizeof(int) * (((size_t)iters + 3) & ~size_t(3)));
-    float4* Rx = reinterpret_cast<float4*>(cta_scratch + L::fft_scratch_bytes);
-    float2* ex32 = reinterpret_cast<float2*>(ex);
-
-    // ---- split: exact R0 to scratch, FP32 copy to registers ----
-    float2 R32[NB];
-    int kc[NB];
-    Top2 loc = {-1.f, 0x7fffffff, -1, -1.f};
-#pragma unroll
-    for (int i = 0; i <= NB; ++i) {
-      if (i == NB && tid >= 2) break;
-      const int slot = i < NB ? tid + i * NT : NSLOT + tid;
-      const int x = i < NB ? slot_xk<T>(slot) : extra_xk<T>(tid);
-      const int k1 = x >> (LOGT + 1), k2 = x & (T2 - 1);
-      const int mx = ((T - k1) & (T - 1)) * T2 + ((T - k2) & (T - 1));
-      const C a = A::load(Z, x, T), m = A::load(Z, mx, T);
-      const C r = A::half(A::add(a, A::conj(m)));
-      if (!A::finite(r)) bad = true;
-      Rx[slot] = make_float4(r.re.h, r.re.l, r.im.h, r.im.l);
-      const float2 r32 = make_float2(r.re.h, r.im.h);
-      const int code = code_of<T>(x);
-      if (i < NB) {
-        kc[i] = x | (code << 16);
-        R32[i] = r32;
-      } else {
-        ex32[tid] = r32;
-      }
-      top2_insert(loc, m32(r32), code, slot);
     }
-    any_bad |= __syncthreads_or(bad);
-    build_wtab<A, T, NT, HALF>(Z, Wsm);
-    __syncthreads();
-    W0c = WT::at0(Wsm);
-    st = FOFSE_BLK_OK;
-    if (IO::w0_zero(W0c)) st = FOFSE_BLK_NO_SUPPORT;
-    else if (any_bad || !IO::w0_finite(W0c)) st = FOFSE_BLK_NONFINITE;
-
-    if (st == FOFSE_BLK_OK) {
-      const ff inv = IO::inv_w0(IO::gamma(P), W0c.re);
-      const float W0f = W0c.re.h * (1.f + 1e-6f);
-      float bnd = 0.f, prevabs = 0.f;
-#pragma unroll 1
-      for (int it = 0; it < iters; ++it) {
-        // ---- FP32 top-2 over the block ----
-        Top2 t = loc;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) top2_merge(t, top2_shfl(t, o));
-        Top2* ts = t2s + (it & 1) * NW;
-        if (lane == 0) ts[warp] = t;
-        __syncthreads();
-        Top2 g = ts[0];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) top2_merge(g, ts[w]);
-        const float sM1 = sqrtf(fmaxf(g.m1, 0.f)), sM2 = sqrtf(fmaxf(g.m2, 0.f));
-        bnd += 1.01f * kU * sM1 + 16.f * kU * W0f * prevabs;
-        const bool certain = (sM1 * kDn - bnd * kUp) > (sM2 * kUp + bnd * kUp) ||
-                             (bnd == 0.f && g.m1 == 0.f);  // all exactly zero: index 0 wins
-        int wcode, wslot;
-        ffc Rt;
-        if (certain) {
-          // ---- exact value of the certain winner (all threads share the sum) ----
-          wcode = g.c1;
-          wslot = g.s1;
-          const int canon = wcode >> 1;
-          const int w1 = canon >> LOGT, w2 = canon & (T - 1);
-          const int x = (wcode & 1) ? (((T - w1) & (T - 1)) * T2 + ((T - w2) & (T - 1))) : (w1 * T2 + w2);
-          const float4 r0 = Rx[wslot];
-          ffc part = recur_partial<WT, T>(Wsm, trY, trC, x, tid, it, NT);
-          part = ffc_warp_sum(part);
-          if (lane == 0) red4[warp] = make_float4(part.re.h, part.re.l, part.im.h, part.im.l);
-          __syncthreads();
-          ffc S = {{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
-          for (int w = 0; w < NW; ++w) {
-            const float4 v = red4[w];
-            S = ffc_add(S, ffc{{v.x, v.y}, {v.z, v.w}});
-          }
-          Rt = {ff_sub(ff{r0.x, r0.y}, S.re), ff_sub(ff{r0.z, r0.w}, S.im)};
-        } else {
-          // ---- near-tie: exact values of every bin within the band ----
-          const float Lb = (sM1 * kDn - 2.f * bnd * kUp) / kUp;
-          const float thr = Lb > 0.f ? Lb * Lb * kDn : -1.f;
-          int cnt = 0;
-#pragma unroll
-          for (int i = 0; i < NB; ++i) cnt += m32(R32[i]) >= thr ? 1 : 0;
-          if (tid < 2) cnt += m32(ex32[tid]) >= thr ? 1 : 0;
-          int incl = cnt;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-          }
-          if (lane == 31) wtot[warp] = incl;
-          __syncthreads();
-          int before = 0, total = 0;
-          for (int w = 0; w < NW; ++w) {
-            const int v = wtot[w];
-            before += w < warp ? v : 0;
-            total += v;
-          }
-          const int rank0 = before + incl - cnt;
-          ffc wb = {{0.f, 0.f}, {0.f, 0.f}};
-          int wbc = 0x7fffffff, wbs = -1;
-          for (int pass = 0; pass < total; pass += NT) {
-            int r = rank0;
-#pragma unroll
-            for (int i = 0; i < NB; ++i) {
-              if (m32(R32[i]) >= thr) {
-                if (r >= pass && r < pass + NT) list[r - pass] = make_int2(kc[i], tid + i * NT);
-                ++r;
-              }
-            }
-            if (tid < 2 && m32(ex32[tid]) >= thr) {
-              if (r >= pass && r < pass + NT) {
-                const int x = extra_xk<T>(tid);
-                list[r - pass] = make_int2(x | (code_of<T>(x) << 16), NSLOT + tid);
-              }
-            }
-            __syncthreads();
-            const int n = min(NT, total - pass);
-            for (int c = warp; c < n; c += NW) {
-              const int2 e = list[c];
-              const float4 r0 = Rx[e.y];
-              ffc part = recur_partial<WT, T>(Wsm, trY, trC, e.x & 0xffff, lane, it, 32);
-              part = ffc_warp_sum(part);
-              const ffc v = {ff_sub(ff{r0.x, r0.y}, part.re), ff_sub(ff{r0.z, r0.w}, part.im)};
-              const int code = e.x >> 16;
-              if (wbc == 0x7fffffff || exact_better(v, code, wb, wbc)) {
-                wb = v;
-                wbc = code;
-                wbs = e.y;
-              }
-            }
-            __syncthreads();
-          }
-          if (lane == 0) {
-            wwv[warp] = make_float4(wb.re.h, wb.re.l, wb.im.h, wb.im.l);
-            wwc[warp] = make_int2(wbc, wbs);
-          }
-          __syncthreads();
-          wcode = 0x7fffffff;
-          wslot = -1;
-          Rt = {{0.f, 0.f}, {0.f, 0.f}};
-          for (int w = 0; w < NW; ++w) {
-            const int2 cs = wwc[w];
-            if (cs.x == 0x7fffffff) continue;
-            const float4 v4 = wwv[w];
-            const ffc v = {{v4.x, v4.y}, {v4.z, v4.w}};
-            if (wcode == 0x7fffffff || exact_better(v, cs.x, Rt, wcode)) {
-              Rt = v;
-              wcode = cs.x;
-              wslot = cs.y;
-            }
-          }
-        }
-        // ---- coefficient (Eq. 5, Eq. 14), exact ----
-        const int canon = wcode >> 1;
-        const bool mir = wcode & 1;
-        const int u1 = canon >> LOGT, u2 = canon & (T - 1);
-        const int s1 = mir ? ((T - u1) & (T - 1)) : u1;
-        const int s2 = mir ? ((T - u2) & (T - 1)) : u2;
-        const bool sc = ((s1 & (T / 2 - 1)) == 0) && ((s2 & (T / 2 - 1)) == 0);
-        C c;
-        c.re = ff_mul(Rt.re, inv);
-        c.im = sc ? ff{0.f, 0.f} : ff_mul(Rt.im, inv);
-        if (tid == 0) {
-          TraceSm<A> tt;
-          tt.u = (u1 << 16) | u2;
-          const float mult = sc ? 1.f : 2.f;
-          tt.re = mult * c.re.h;
-          tt.im = (mir ? -mult : mult) * c.im.h;
-          tt.dre = c.re.h;
-          tt.dim = mir ? -c.im.h : c.im.h;
-          tr[it] = tt;
-          trY[it] = u1 * T2 + u2;
-          trC[it] = mir ? make_float4(c.re.h, c.re.l, -c.im.h, -c.im.l)
-                        : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
-        }
-        // ---- FP32 update of the working spectrum + next local top-2 ----
-        const float p = c.re.h, q = c.im.h;
-        prevabs = fabsf(p) + fabsf(q);
-        const int y = s1 * T2 + s2;
-        loc = {-1.f, 0x7fffffff, -1, -1.f};
-        const float2* W2 = reinterpret_cast<const float2*>(Wsm);
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-          upd32<WT>(R32[i], p, q, W2, kc[i] & 0xffff, y, !sc);
-          top2_insert(loc, m32(R32[i]), kc[i] >> 16, tid + i * NT);
-        }
-        if (tid < 2) {
-          const int x = extra_xk<T>(tid);
-          float2 r = ex32[tid];
-          upd32<WT>(r, p, q, W2, x, y, !sc);
-          ex32[tid] = r;
-          top2_insert(loc, m32(r), code_of<T>(x), NSLOT + tid);
-        }
-      }
-    }
-  }
   __syncthreads();
 
   // ---- 5. synthesis of B (Eq. 1) and outputs ---------------------------------
@@ -1151,7 +890,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
 // Persistent kernel: each CTA takes blocks from the work queue of its plan (an
 // atomic counter over the block list; entries of other plans are skipped)
 // until the list is exhausted.  Without a queue, block i goes to CTA i mod grid.
-template <class A, int T, int NT, int MINB, bool HALF, bool FILT>
+template <class A, int T, int NT, int MINB, bool HALF>
 __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_constant__ FwdArgs args,
                                                            const __grid_constant__ CUtensorMap tmF,
                                                            const __grid_constant__ CUtensorMap tmA) {
@@ -1169,9 +908,9 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
     __syncthreads();
   }
   unsigned char* cta_scratch = nullptr;
-  if (HALF || FILT)
+  if (HALF)
     cta_scratch = static_cast<unsigned char*>(args.scratch) +
-                  (size_t)blockIdx.x * FwdLayout<A, T, NT, HALF, FILT>::scratch_bytes;
+                  (size_t)blockIdx.x * FwdLayout<A, T, NT, HALF>::scratch_bytes;
   int next = blockIdx.x;
   for (;;) {
     int item;
@@ -1186,15 +925,513 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
     }
     if (item >= args.n_blocks) break;
     if (args.blocks[item].plan != args.plan_index) continue;
-    forward_block<A, T, NT, HALF, FILT>(args, &tmF, &tmA, item, smem, &mbar, tma_phase, cta_scratch);
+    forward_block<A, T, NT, HALF>(args, &tmF, &tmA, item, smem, &mbar, tma_phase, cta_scratch);
   }
 }
 
-template <class A, int T, int NT, int MINB, bool HALF, bool FILT> struct Variant {
-  static constexpr size_t per_cta = FwdLayout<A, T, NT, HALF, FILT>::scratch_bytes;
+// ===========================================================================
+// Filtered-exact forward, second layout: the exact W (float-float, both
+// planes), the exact initial spectrum R0 and the FFT live in a per-CTA slot of
+// L2-resident global scratch; shared memory holds only the FP32 (hi) plane of
+// W for the working-spectrum updates (32 KB at T = 64), so more blocks are
+// resident per SM.  Four warps per block at T = 64 (16 bins per thread) keep
+// the per-iteration reductions small next to the bin work.
+// ===========================================================================
+template <int T, bool HALF> struct WHi;
+template <int T> struct WHi<T, false> {  // full T x T hi plane, row-major
+  static constexpr int LOGT = ilog2(T);
+  static constexpr size_t elems = (size_t)T * T;
+  __device__ __forceinline__ static float2 get(const float2* W, int a) {  // a = a1*2T + a2
+    return W[((a >> (LOGT + 1)) << LOGT) | (a & (T - 1))];
+  }
+};
+template <int T> struct WHi<T, true> {  // Hermitian half, rows of T/2 + 1
+  static constexpr int LOGT = ilog2(T), HO = T / 2 + 1;
+  static constexpr size_t elems = (size_t)T * HO;
+  __device__ __forceinline__ static float2 get(const float2* W, int a) {
+    const int a1 = a >> (LOGT + 1), a2 = a & (T - 1);
+    const bool mir = a2 > T / 2;
+    const int r = mir ? ((T - a1) & (T - 1)) : a1;
+    const int c = mir ? (T - a2) : a2;
+    const float2 v = W[r * HO + c];
+    return mir ? make_float2(v.x, -v.y) : v;
+  }
+};
+
+template <int T, int NT, bool HALF> struct F2Layout {
+  static constexpr int NW = NT / 32, NSLOT = T * T / 2, LIST = 64;
+  static constexpr size_t whi_bytes = sizeof(float2) * WHi<T, HALF>::elems;
+  static constexpr size_t tw_off = (whi_bytes + 15) & ~size_t(15);
+  static constexpr size_t t2_off = tw_off + sizeof(ArFF::C) * (T / 2);
+  static constexpr size_t red_off = t2_off + sizeof(Top2) * 2 * NW;
+  static constexpr size_t wtot_off = red_off + sizeof(float4) * NW;
+  static constexpr size_t list_off = (wtot_off + sizeof(int) * NW + 15) & ~size_t(15);
+  static constexpr size_t ww_off = list_off + sizeof(int2) * LIST;
+  static constexpr size_t ex_off = ww_off + (sizeof(float4) + sizeof(int2)) * NW;
+  static constexpr size_t try_off = (ex_off + 2 * sizeof(float2) + 15) & ~size_t(15);
+  __host__ __device__ static size_t trc_off(int iters) {
+    return try_off + sizeof(int) * (((size_t)iters + 3) & ~size_t(3));
+  }
+  __host__ __device__ static size_t bytes(int iters) {
+    return 128 + trc_off(iters) + sizeof(float4) * (size_t)iters;
+  }
+  static constexpr size_t z_bytes = sizeof(float2) * (size_t)T * 2 * T;  // FFT, then exact W
+  static constexpr size_t scratch_bytes = z_bytes + sizeof(float4) * (size_t)(NSLOT + 2);
+};
+
+// FP32 update of one working bin from the shared hi plane
+template <class WH>
+__device__ __forceinline__ void upd_hi(float2& R, float p, float q, const float2* Whi, int x, int y,
+                                       bool pair, int M, int T) {
+  const float2 Wm = WH::get(Whi, (x + T - y) & M);
+  float br = 0.f, bi = 0.f;
+  if (pair) {
+    const float2 Wp = WH::get(Whi, (x + y) & M);
+    br = Wp.x;
+    bi = Wp.y;
+  }
+  R.x -= __fmaf_rn(p, Wm.x + br, -(q * (Wm.y - bi)));
+  R.y -= __fmaf_rn(p, Wm.y + bi, q * (Wm.x - br));
+}
+
+// Sum of the NW warp partials (red4), float-float, returned to every lane.
+template <int NW> __device__ __forceinline__ ffc block_partials_sum(const float4* red4, int lane) {
+  ffc v = {{0.f, 0.f}, {0.f, 0.f}};
+  if (lane < NW) {
+    const float4 r = red4[lane];
+    v = {{r.x, r.y}, {r.z, r.w}};
+  }
+#pragma unroll
+  for (int o = NW / 2; o > 0; o >>= 1) v = ffc_add(v, ffc_shfl(v, o));
+  return {{__shfl_sync(0xffffffffu, v.re.h, 0), __shfl_sync(0xffffffffu, v.re.l, 0)},
+          {__shfl_sync(0xffffffffu, v.im.h, 0), __shfl_sync(0xffffffffu, v.im.l, 0)}};
+}
+
+template <int T, int NT, bool HALF>
+__device__ __forceinline__ void forward_block_f2(const FwdArgs& args, const CUtensorMap* tmF,
+                                                 const CUtensorMap* tmA, int blk, unsigned char* smem,
+                                                 uint64_t* mbar, unsigned& tma_phase,
+                                                 unsigned char* cta_scratch) {
+  using A = ArFF;
+  using C = ArFF::C;
+  using IO = PlanIO<A>;
+  using L = F2Layout<T, NT, HALF>;
+  using WG = WTab<A, T, false>;  // exact W, full grid, in global scratch
+  using WH = WHi<T, HALF>;
+  constexpr int T2 = 2 * T, LOGT = ilog2(T), NSLOT = T * T / 2;
+  constexpr int NB = NSLOT / NT, NW = NT / 32, LIST = L::LIST;
+  constexpr int M = (T - 1) * 2 * T + (T - 1);
+  static_assert(NSLOT % NT == 0 && NW >= 2 && (NW & (NW - 1)) == 0, "slot grid");
+  constexpr float kU = 5.9604644775390625e-08f;  // 2^-24
+  constexpr float kUp = 1.f + 4.f * kU, kDn = 1.f - 4.f * kU;
+
+  float2* Whi = reinterpret_cast<float2*>(smem);
+  C* tw = reinterpret_cast<C*>(smem + L::tw_off);
+  Top2* t2s = reinterpret_cast<Top2*>(smem + L::t2_off);
+  float4* red4 = reinterpret_cast<float4*>(smem + L::red_off);
+  int* wtot = reinterpret_cast<int*>(smem + L::wtot_off);
+  int2* list = reinterpret_cast<int2*>(smem + L::list_off);
+  float4* wwv = reinterpret_cast<float4*>(smem + L::ww_off);
+  int2* wwc = reinterpret_cast<int2*>(smem + L::ww_off + sizeof(float4) * NW);
+  float2* ex32 = reinterpret_cast<float2*>(smem + L::ex_off);
+  const PlanDev& P = args.plan;
+  const int iters = P.iters;
+  int* trY = reinterpret_cast<int*>(smem + L::try_off);
+  float4* trC = reinterpret_cast<float4*>(smem + L::trc_off(iters));
+  float2* Zg = reinterpret_cast<float2*>(cta_scratch);
+  float4* Rx = reinterpret_cast<float4*>(cta_scratch + L::z_bytes);
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const fofse_block bd = args.blocks[blk];
+  const int b = P.block, br = P.border, Ls = P.Ls;
+  const int ly0 = bd.y - br, lx0 = bd.x - br;
+
+  // ---- 1. stage the support tile into shared memory (TMA) -------------------
+  float* stF = reinterpret_cast<float*>(smem);
+  const int bytesF = args.box_f * Ls * 4;
+  uint8_t* stA = smem + ((bytesF + 127) & ~127);
+  const int fx0 = lx0 & ~3, fo = lx0 - fx0;
+  const int ax0 = lx0 & ~15, ao = lx0 - ax0;
+  if (args.use_tma) {
+    if (tid == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(mbar, (unsigned)(bytesF + args.box_a * Ls));
+      tma_load_2d(stF, tmF, fx0, ly0, mbar);
+      tma_load_2d(stA, tmA, ax0, ly0, mbar);
+    }
+    bool done = false;
+    for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mbar, tma_phase);
+    if (!done) {
+      atomicOr(args.err, kErrTimeout);
+      for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mbar, tma_phase);
+    }
+    tma_phase ^= 1u;
+    if (!__syncthreads_and(done)) {
+      if (tid == 0 && args.status) args.status[blk] = kBlkTimeout;
+      return;
+    }
+  }
+
+  // ---- 2. z = w f + j w at bit-reversed positions of the global FFT buffer --
+  bool bad = false;
+  for (int e = tid; e < T * T; e += NT) {
+    const int r = e >> LOGT, cc = e & (T - 1);
+    const int m = __brev(r) >> (32 - LOGT), n = __brev(cc) >> (32 - LOGT);
+    C z = A::zero();
+    if (m < Ls && n < Ls) {
+      const bool inB = m >= br && m < br + b && n >= br && n < br + b;
+      bool inS = true;
+      if (P.support == FOFSE_SUPPORT_CAUSAL_L)
+        inS = (m < br) ? (n < br + b) : (m < br + b ? n < br : false);
+      int av;
+      float f;
+      if (args.use_tma) {
+        av = stA[m * args.box_a + ao + n];
+        f = stF[m * args.box_f + fo + n];
+      } else {
+        const int fy = ly0 + m, fx = lx0 + n;
+        const bool in = fy >= 0 && fy < args.height && fx >= 0 && fx < args.width;
+        av = in ? args.avail[(size_t)fy * args.pitch + fx] : 0;
+        f = in ? args.frame[(size_t)fy * args.pitch + fx] : 0.f;
+      }
+      if (av && !inB && inS) {
+        bad |= !isfinite(f);
+        C wd;
+        z = IO::weighted(P.tab, m * Ls + n, f, wd);
+      }
+    }
+    A::store(Zg, r * T2 + cc, T, z);
+  }
+  for (int e = tid; e < T / 2; e += NT) tw[e] = IO::twiddle(P.tab, e);
+  int any_bad = __syncthreads_or(bad);
+
+  // ---- 3. FFT (float-float) in the global buffer ------------------------------
+  fft2d_dit<A, T, NT, false>(Zg, tw, Ls, T);
+
+  // ---- split: exact R0 -> scratch, FP32 copy -> registers --------------------
+  float2 R32[NB];
+  int kc[NB];
+  Top2 loc = {-1.f, 0x7fffffff, -1, -1.f};
+#pragma unroll
+  for (int i = 0; i <= NB; ++i) {
+    if (i == NB && tid >= 2) break;
+    const int slot = i < NB ? tid + i * NT : NSLOT + tid;
+    const int x = i < NB ? slot_xk<T>(slot) : extra_xk<T>(tid);
+    const int k1 = x >> (LOGT + 1), k2 = x & (T2 - 1);
+    const int mx = ((T - k1) & (T - 1)) * T2 + ((T - k2) & (T - 1));
+    const C a = A::load(Zg, x, T), mm = A::load(Zg, mx, T);
+    const C r = A::half(A::add(a, A::conj(mm)));
+    if (!A::finite(r)) bad = true;
+    Rx[slot] = make_float4(r.re.h, r.re.l, r.im.h, r.im.l);
+    const float2 r32 = make_float2(r.re.h, r.im.h);
+    const int code = code_of<T>(x);
+    if (i < NB) {
+      kc[i] = x | (code << 16);
+      R32[i] = r32;
+    } else {
+      ex32[tid] = r32;
+    }
+    top2_insert(loc, m32(r32), code, slot);
+  }
+  any_bad |= __syncthreads_or(bad);
+  build_wtab<A, T, NT, false>(Zg, nullptr);  // exact W in place (global)
+  __syncthreads();
+  if constexpr (!HALF) {
+    for (int e = tid; e < T * T; e += NT) Whi[e] = Zg[(e >> LOGT) * T2 + (e & (T - 1))];
+  } else {
+    constexpr int HO = T / 2 + 1;
+    for (int e = tid; e < T * HO; e += NT) {
+      const int k1 = e / HO, k2 = e - k1 * HO;
+      Whi[e] = Zg[k1 * T2 + k2];
+    }
+  }
+  __syncthreads();
+  const C W0c = A::load(Zg, 0, T);
+  int st = FOFSE_BLK_OK;
+  if (IO::w0_zero(W0c)) st = FOFSE_BLK_NO_SUPPORT;
+  else if (any_bad || !IO::w0_finite(W0c)) st = FOFSE_BLK_NONFINITE;
+
+  if (st == FOFSE_BLK_OK) {
+    const ff inv = IO::inv_w0(IO::gamma(P), W0c.re);
+    const float W0f = W0c.re.h * (1.f + 1e-6f);
+    float bnd = 0.f, prevabs = 0.f;
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+      // ---- FP32 top-2 over the block ----
+      Top2 t = loc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) top2_merge(t, top2_shfl(t, o));
+      Top2* ts = t2s + (it & 1) * NW;
+      if (lane == 0) ts[warp] = t;
+      __syncthreads();
+      Top2 g = ts[0];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) top2_merge(g, ts[w]);
+      const float sM1 = sqrtf(fmaxf(g.m1, 0.f)), sM2 = sqrtf(fmaxf(g.m2, 0.f));
+      bnd += 1.01f * kU * sM1 + 16.f * kU * W0f * prevabs;
+      const bool certain = (sM1 * kDn - bnd * kUp) > (sM2 * kUp + bnd * kUp) ||
+                           (bnd == 0.f && g.m1 == 0.f);
+      int wcode, wslot;
+      ffc Rt;
+      if (certain) {
+        wcode = g.c1;
+        wslot = g.s1;
+        const int canon = wcode >> 1;
+        const int w1 = canon >> LOGT, w2 = canon & (T - 1);
+        const int x = (wcode & 1) ? (((T - w1) & (T - 1)) * T2 + ((T - w2) & (T - 1))) : (w1 * T2 + w2);
+        const float4 r0 = Rx[wslot];
+        ffc part = recur_partial<WG, T>(Zg, trY, trC, x, tid, it, NT);
+        part = ffc_warp_sum(part);
+        float4* rb = red4;  // one buffer: read below before the next write (barriers in between)
+        if (lane == 0) rb[warp] = make_float4(part.re.h, part.re.l, part.im.h, part.im.l);
+        __syncthreads();
+        const ffc S = block_partials_sum<NW>(rb, lane);
+        Rt = {ff_sub(ff{r0.x, r0.y}, S.re), ff_sub(ff{r0.z, r0.w}, S.im)};
+      } else {
+        // ---- near-tie: exact values of every bin within the band ----
+        const float Lb = (sM1 * kDn - 2.f * bnd * kUp) / kUp;
+        const float thr = Lb > 0.f ? Lb * Lb * kDn : -1.f;
+        int cnt = 0;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) cnt += m32(R32[i]) >= thr ? 1 : 0;
+        if (tid < 2) cnt += m32(ex32[tid]) >= thr ? 1 : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        if (lane == 31) wtot[warp] = incl;
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const int v = wtot[w];
+          before += w < warp ? v : 0;
+          total += v;
+        }
+        const int rank0 = before + incl - cnt;
+        ffc wb = {{0.f, 0.f}, {0.f, 0.f}};
+        int wbc = 0x7fffffff, wbs = -1;
+        for (int pass = 0; pass < total; pass += LIST) {
+          int r = rank0;
+#pragma unroll
+          for (int i = 0; i < NB; ++i) {
+            if (m32(R32[i]) >= thr) {
+              if (r >= pass && r < pass + LIST) list[r - pass] = make_int2(kc[i], tid + i * NT);
+              ++r;
+            }
+          }
+          if (tid < 2 && m32(ex32[tid]) >= thr && r >= pass && r < pass + LIST) {
+            const int x = extra_xk<T>(tid);
+            list[r - pass] = make_int2(x | (code_of<T>(x) << 16), NSLOT + tid);
+          }
+          __syncthreads();
+          const int n = min(LIST, total - pass);
+          for (int c = warp; c < n; c += NW) {
+            const int2 e = list[c];
+            const float4 r0 = Rx[e.y];
+            ffc part = recur_partial<WG, T>(Zg, trY, trC, e.x & 0xffff, lane, it, 32);
+            part = ffc_warp_sum(part);
+            const ffc v = {ff_sub(ff{r0.x, r0.y}, part.re), ff_sub(ff{r0.z, r0.w}, part.im)};
+            const int code = e.x >> 16;
+            if (wbc == 0x7fffffff || exact_better(v, code, wb, wbc)) {
+              wb = v;
+              wbc = code;
+              wbs = e.y;
+            }
+          }
+          __syncthreads();
+        }
+        if (lane == 0) {
+          wwv[warp] = make_float4(wb.re.h, wb.re.l, wb.im.h, wb.im.l);
+          wwc[warp] = make_int2(wbc, wbs);
+        }
+        __syncthreads();
+        wcode = 0x7fffffff;
+        wslot = -1;
+        Rt = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const int2 cs = wwc[w];
+          if (cs.x == 0x7fffffff) continue;
+          const float4 v4 = wwv[w];
+          const ffc v = {{v4.x, v4.y}, {v4.z, v4.w}};
+          if (wcode == 0x7fffffff || exact_better(v, cs.x, Rt, wcode)) {
+            Rt = v;
+            wcode = cs.x;
+            wslot = cs.y;
+          }
+        }
+      }
+      // ---- exact coefficient (Eq. 5, Eq. 14) ----
+      const int canon = wcode >> 1;
+      const bool mir = wcode & 1;
+      const int u1 = canon >> LOGT, u2 = canon & (T - 1);
+      const int s1 = mir ? ((T - u1) & (T - 1)) : u1;
+      const int s2 = mir ? ((T - u2) & (T - 1)) : u2;
+      const bool sc = ((s1 & (T / 2 - 1)) == 0) && ((s2 & (T / 2 - 1)) == 0);
+      C c;
+      c.re = ff_mul(Rt.re, inv);
+      c.im = sc ? ff{0.f, 0.f} : ff_mul(Rt.im, inv);
+      if (tid == 0) {
+        trY[it] = u1 * T2 + u2;
+        trC[it] = mir ? make_float4(c.re.h, c.re.l, -c.im.h, -c.im.l)
+                      : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
+      }
+      // ---- FP32 update of the working spectrum + next local top-2 ----
+      const float p = c.re.h, q = c.im.h;
+      prevabs = fabsf(p) + fabsf(q);
+      const int y = s1 * T2 + s2;
+      loc = {-1.f, 0x7fffffff, -1, -1.f};
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        upd_hi<WH>(R32[i], p, q, Whi, kc[i] & 0xffff, y, !sc, M, T);
+        top2_insert(loc, m32(R32[i]), kc[i] >> 16, tid + i * NT);
+      }
+      if (tid < 2) {
+        const int x = extra_xk<T>(tid);
+        float2 r = ex32[tid];
+        upd_hi<WH>(r, p, q, Whi, x, y, !sc, M, T);
+        ex32[tid] = r;
+        top2_insert(loc, m32(r), code_of<T>(x), NSLOT + tid);
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- synthesis of B (Eq. 1) from the exact coefficients; outputs ----------
+  const int nIt = (st == FOFSE_BLK_OK) ? iters : 0;
+  const int ld = args.out_ld;
+  const float2* syn = P.tab.syn_f32;
+  for (int pidx = tid; pidx < ld * ld; pidx += NT) {
+    const int bm = pidx / ld, bn = pidx - bm * ld;
+    float v = 0.f;
+    if (bm < b && bn < b) {
+      const int m = br + bm, n = br + bn;
+      float acc = 0.f;
+      for (int i = 0; i < nIt; ++i) {
+        const int yy = trY[i];
+        const int a1 = yy >> (LOGT + 1), a2 = yy & (T2 - 1);
+        const float4 c4 = trC[i];
+        const float mult = (((a1 & (T / 2 - 1)) == 0) && ((a2 & (T / 2 - 1)) == 0)) ? 1.f : 2.f;
+        const float2 cs = __ldg(&syn[(a1 * m + a2 * n) & (T - 1)]);
+        acc += mult * (c4.x * cs.x - c4.z * cs.y);
+      }
+      v = acc;
+      if (args.out_frame) {
+        const int fy = bd.y + bm, fx = bd.x + bn;
+        if (fy >= 0 && fy < args.height && fx >= 0 && fx < args.width)
+          args.out_frame[(size_t)fy * args.pitch + fx] = v;
+      }
+    }
+    if (args.out_blocks) args.out_blocks[(size_t)blk * args.out_stride + pidx] = v;
+  }
+  if (args.trace) {
+    for (int i = tid; i < args.trace_stride; i += NT) {
+      fofse_trace_entry e;
+      if (i < nIt) {
+        const int yy = trY[i];
+        const float4 c4 = trC[i];
+        e.u1 = (int16_t)(yy >> (LOGT + 1));
+        e.u2 = (int16_t)(yy & (T2 - 1));
+        e.dc_re = c4.x;
+        e.dc_im = c4.z;
+      } else {
+        e.u1 = e.u2 = 0;
+        e.dc_re = e.dc_im = 0.f;
+      }
+      args.trace[(size_t)blk * args.trace_stride + i] = e;
+    }
+  }
+  if (tid == 0) {
+    if (args.w0) args.w0[blk] = st == FOFSE_BLK_OK ? W0c.re.h + W0c.re.l : 0.f;
+    if (args.status) args.status[blk] = st;
+  }
+  __syncthreads();
+}
+
+template <int T, int NT, int MINB, bool HALF>
+__global__ void __launch_bounds__(NT, MINB) fofse_forward_f2_kernel(const __grid_constant__ FwdArgs args,
+                                                              const __grid_constant__ CUtensorMap tmF,
+                                                              const __grid_constant__ CUtensorMap tmA) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  __shared__ uint64_t mbar;
+  __shared__ int s_item;
+  unsigned tma_phase = 0;
+  if (args.use_tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(&mbar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  unsigned char* cta_scratch = static_cast<unsigned char*>(args.scratch) +
+                               (size_t)blockIdx.x * F2Layout<T, NT, HALF>::scratch_bytes;
+  int next = blockIdx.x;
+  for (;;) {
+    int item;
+    if (args.queue) {
+      if (threadIdx.x == 0) s_item = atomicAdd(args.queue, 1);
+      __syncthreads();
+      item = s_item;
+      __syncthreads();
+    } else {
+      item = next;
+      next += gridDim.x;
+    }
+    if (item >= args.n_blocks) break;
+    if (args.blocks[item].plan != args.plan_index) continue;
+    forward_block_f2<T, NT, HALF>(args, &tmF, &tmA, item, smem, &mbar, tma_phase, cta_scratch);
+  }
+}
+
+template <int T, int NT, int MINB, bool HALF> struct VariantF2 {
+  static constexpr size_t per_cta = F2Layout<T, NT, HALF>::scratch_bytes;
   static cudaError_t prepare(int iters, size_t* smem, int* max_ctas) {
-    *smem = FwdLayout<A, T, NT, HALF, FILT>::bytes(iters);
-    auto kern = fofse_forward_kernel<A, T, NT, MINB, HALF, FILT>;
+    *smem = F2Layout<T, NT, HALF>::bytes(iters);
+    auto kern = fofse_forward_f2_kernel<T, NT, MINB, HALF>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, *smem)) != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    *max_ctas = sms * per;
+    return cudaSuccess;
+  }
+  static cudaError_t scratch(int iters, size_t* bytes) {
+    size_t sm;
+    int ctas;
+    cudaError_t e = prepare(iters, &sm, &ctas);
+    *bytes = e == cudaSuccess ? per_cta * (size_t)ctas : 0;
+    return e;
+  }
+  static cudaError_t launch(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
+                            cudaStream_t s) {
+    size_t sm;
+    int grid;
+    cudaError_t e = prepare(a.plan.iters, &sm, &grid);
+    if (e != cudaSuccess) return e;
+    const size_t fit = a.scratch ? a.scratch_bytes / per_cta : 0;
+    if (fit < 1) return cudaErrorInvalidValue;
+    if ((size_t)grid > fit) grid = (int)fit;
+    if (grid > a.n_blocks) grid = a.n_blocks;
+    if (grid < 1) return cudaSuccess;
+    fofse_forward_f2_kernel<T, NT, MINB, HALF><<<grid, NT, sm, s>>>(a, *tf, *ta);
+    return cudaGetLastError();
+  }
+};
+
+template <class A, int T, int NT, int MINB, bool HALF> struct Variant {
+  static constexpr size_t per_cta = FwdLayout<A, T, NT, HALF>::scratch_bytes;
+  static cudaError_t prepare(int iters, size_t* smem, int* max_ctas) {
+    *smem = FwdLayout<A, T, NT, HALF>::bytes(iters);
+    auto kern = fofse_forward_kernel<A, T, NT, MINB, HALF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per = 0;
@@ -1225,7 +1462,7 @@ template <class A, int T, int NT, int MINB, bool HALF, bool FILT> struct Variant
     }
     if (grid > a.n_blocks) grid = a.n_blocks;
     if (grid < 1) return cudaSuccess;
-    fofse_forward_kernel<A, T, NT, MINB, HALF, FILT><<<grid, NT, sm, s>>>(a, *tf, *ta);
+    fofse_forward_kernel<A, T, NT, MINB, HALF><<<grid, NT, sm, s>>>(a, *tf, *ta);
     return cudaGetLastError();
   }
 };
@@ -1234,22 +1471,22 @@ template <class A, int T, int NT, int MINB, bool HALF, bool FILT> struct Variant
 // when scratch is available and the all-bins float-float variant otherwise.
 template <int T> struct Pick;
 template <> struct Pick<32> {
-  using FF = Variant<ArFF, 32, 128, 6, false, false>;
-  using FILT = Variant<ArFF, 32, 128, 6, false, true>;
-  using F64 = Variant<ArF64, 32, 128, 1, false, false>;
-  using F32 = Variant<ArF32, 32, 128, 6, false, false>;
+  using FF = Variant<ArFF, 32, 128, 6, false>;
+  using FILT = VariantF2<32, 64, 8, false>;
+  using F64 = Variant<ArF64, 32, 128, 1, false>;
+  using F32 = Variant<ArF32, 32, 128, 6, false>;
 };
 template <> struct Pick<64> {
-  using FF = Variant<ArFF, 64, 256, 3, false, false>;
-  using FILT = Variant<ArFF, 64, 256, 3, false, true>;
-  using F64 = Variant<ArF64, 64, 256, 1, false, false>;
-  using F32 = Variant<ArF32, 64, 256, 3, false, false>;
+  using FF = Variant<ArFF, 64, 256, 3, false>;
+  using FILT = VariantF2<64, 128, 5, false>;
+  using F64 = Variant<ArF64, 64, 256, 1, false>;
+  using F32 = Variant<ArF32, 64, 256, 3, false>;
 };
 template <> struct Pick<128> {
-  using FF = Variant<ArFF, 128, 512, 1, true, false>;
-  using FILT = Variant<ArFF, 128, 512, 1, true, true>;
-  using F64 = Variant<ArF64, 128, 512, 1, true, false>;
-  using F32 = Variant<ArF32, 128, 512, 1, true, false>;
+  using FF = Variant<ArFF, 128, 512, 1, true>;
+  using FILT = VariantF2<128, 512, 1, true>;
+  using F64 = Variant<ArF64, 128, 512, 1, true>;
+  using F32 = Variant<ArF32, 128, 512, 1, true>;
 };
 
 template <int T>
@@ -1258,10 +1495,10 @@ cudaError_t launch_T(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap*
   switch (a.plan.precision) {
     case FOFSE_FP64_VALIDATE: return Pk::F64::launch(a, tf, ta, s);
     case FOFSE_FP32_PLAIN: return Pk::F32::launch(a, tf, ta, s);
-    case FOFSE_FP32_FILTERED:
+    case FOFSE_FP32_FULLFF: return Pk::FF::launch(a, tf, ta, s);
+    default:  // FOFSE_FP32, FOFSE_FP32_FILTERED
       if (a.scratch && a.scratch_bytes >= Pk::FILT::per_cta) return Pk::FILT::launch(a, tf, ta, s);
       return Pk::FF::launch(a, tf, ta, s);
-    default: return Pk::FF::launch(a, tf, ta, s);  // FOFSE_FP32, FOFSE_FP32_FULLFF
   }
 }
 template <int T> cudaError_t scratch_T(const PlanDev& p, size_t* bytes) {
@@ -1269,8 +1506,8 @@ template <int T> cudaError_t scratch_T(const PlanDev& p, size_t* bytes) {
   switch (p.precision) {
     case FOFSE_FP64_VALIDATE: return Pk::F64::scratch(p.iters, bytes);
     case FOFSE_FP32_PLAIN: return Pk::F32::scratch(p.iters, bytes);
-    case FOFSE_FP32_FILTERED: return Pk::FILT::scratch(p.iters, bytes);
-    default: return Pk::FF::scratch(p.iters, bytes);
+    case FOFSE_FP32_FULLFF: return Pk::FF::scratch(p.iters, bytes);
+    default: return Pk::FILT::scratch(p.iters, bytes);
   }
 }
 
