@@ -26,6 +26,10 @@
 // FP32 arithmetic throughout (the gradients' tolerance is relative 1e-3).
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "fofse_arith.cuh"
 #include "fofse_fft.cuh"
 #include "fofse_internal.h"
@@ -292,8 +296,19 @@ template <int T, int NT> size_t bwd_smem(int iters) {
 template <int T, int NT> cudaError_t launch_bwd(const BwdArgs& a, cudaStream_t s) {
   const size_t sm = bwd_smem<T, NT>(a.plan.iters);
   auto kern = fofse_backward_kernel<T, NT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+  {  // raise the kernel's shared-memory limit once per device and size
+    static std::mutex mu;
+    static std::set<std::pair<int, size_t>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count({dev, sm})) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      done.insert({dev, sm});
+    }
+  }
   kern<<<a.n_blocks, NT, sm, s>>>(a);
   return cudaGetLastError();
 }

@@ -26,7 +26,10 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "fofse_arith.cuh"
 #include "fofse_fft.cuh"
@@ -929,6 +932,32 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
   }
 }
 
+// Kernel attribute setting and occupancy query, done once per (kernel, device,
+// shared-memory size) and cached: launches then issue no query, which keeps
+// the batch call cheap and safe to record in a CUDA graph.
+template <class K> cudaError_t prepare_kernel(K kern, int nt, size_t smem, int* max_ctas) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find({dev, smem});
+  if (it != cache.end()) {
+    *max_ctas = it->second;
+    return cudaSuccess;
+  }
+  int sms = 0, per = 0;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, nt, smem)) != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  cache[{dev, smem}] = sms * per;
+  *max_ctas = sms * per;
+  return cudaSuccess;
+}
+
 // ===========================================================================
 // Filtered-exact forward, second layout: the exact W (float-float, both
 // planes), the exact initial spectrum R0 and the FFT live in a per-CTA slot of
@@ -1393,16 +1422,7 @@ template <int T, int NT, int MINB, bool HALF> struct VariantF2 {
   static constexpr size_t per_cta = F2Layout<T, NT, HALF>::scratch_bytes;
   static cudaError_t prepare(int iters, size_t* smem, int* max_ctas) {
     *smem = F2Layout<T, NT, HALF>::bytes(iters);
-    auto kern = fofse_forward_f2_kernel<T, NT, MINB, HALF>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, *smem)) != cudaSuccess) return e;
-    if (per < 1) return cudaErrorInvalidConfiguration;
-    *max_ctas = sms * per;
-    return cudaSuccess;
+    return prepare_kernel(fofse_forward_f2_kernel<T, NT, MINB, HALF>, NT, *smem, max_ctas);
   }
   static cudaError_t scratch(int iters, size_t* bytes) {
     size_t sm;
@@ -1431,16 +1451,7 @@ template <class A, int T, int NT, int MINB, bool HALF> struct Variant {
   static constexpr size_t per_cta = FwdLayout<A, T, NT, HALF>::scratch_bytes;
   static cudaError_t prepare(int iters, size_t* smem, int* max_ctas) {
     *smem = FwdLayout<A, T, NT, HALF>::bytes(iters);
-    auto kern = fofse_forward_kernel<A, T, NT, MINB, HALF>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, *smem)) != cudaSuccess) return e;
-    if (per < 1) return cudaErrorInvalidConfiguration;
-    *max_ctas = sms * per;
-    return cudaSuccess;
+    return prepare_kernel(fofse_forward_kernel<A, T, NT, MINB, HALF>, NT, *smem, max_ctas);
   }
   static cudaError_t scratch(int iters, size_t* bytes) {
     size_t sm;
