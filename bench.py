@@ -32,12 +32,17 @@ METRIC = "16x16 blocks/s (64x64 FFT, 200 it) fwd and fwd+bwd; % smem roofline; C
 WORKLOAD = "conceal-1920x1080: 804 lost 16x16 blocks, border 16, 64x64 FFT, rho 0.8, gamma 0.5, 200 it"
 L2_FLUSH_BYTES = 512 << 20
 
-# float-float FP32 instructions the transform-domain update needs per
-# conjugate-pair bin and iteration (four pair sums 4 x 8, two two-term products
-# 2 x 16, two compensated subtractions 2 x 11, |R|^2 estimate 2, compare 1);
-# shared-memory bytes: two shifted W gathers of 16 bytes (R in registers).
-FF_OPS_PER_BIN_ITER = 89
-SMEM_BYTES_PER_BIN_ITER = 32
+# Algorithmic work of the product kernel (FP32 working spectrum, exact
+# decisions).  Per conjugate-pair bin and iteration: the FP32 update
+# R -= c W[k-u] + conj(c) W[k+u] written as 4 pair sums and 4 multiply-adds
+# (8), the subtraction from R (2), |R|^2 (2) and the top-2 compare (2): 14 FP32
+# operations and two 8-byte shared-memory gathers of W's FP32 plane.  Per
+# iteration i additionally the exact float-float recurrence for the winner:
+# i terms of about 66 FP32 operations (two float-float complex products and a
+# float-float accumulation).
+OPS_PER_BIN_ITER = 14
+SMEM_BYTES_PER_BIN_ITER = 16
+OPS_PER_RECURRENCE_TERM = 66
 FP32_LANES_PER_SM = 128
 SMEM_BYTES_PER_CLK_PER_SM = 128
 
@@ -156,6 +161,36 @@ def cpu_baseline(wl, sample_blocks: int, threads: int | None = None):
                       f"{res.threads} threads, {dt:.1f} s"}
 
 
+def parity_summary(wl, ob, tr, st):
+    """The product's outputs of this run against the FP64 oracle on every block:
+    identical selection paths, near-tie flips, max |B_gpu - B_oracle| on
+    matching paths, aggregate PSNR over B (clipped to [0, 255])."""
+    import numpy as np
+    import oracle
+    from paper_2207_01205_gb300.api import TRACE_DTYPE
+    t0 = time.perf_counter()
+    ora = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans)
+    g_blocks = ob.cpu().numpy().astype(np.float64)
+    t = tr.cpu().numpy().view(TRACE_DTYPE).reshape(tr.shape[:2])
+    g_path = np.stack([t["u1"], t["u2"]], axis=-1).astype(np.int32)
+    g_st = st.cpu().numpy()
+    same, flips, max_err = 0, 0, 0.0
+    for i in range(wl.n_blocks):
+        eq = (g_path[i] == ora.path[i]).all(axis=1)
+        if eq.all() and g_st[i] == ora.status[i]:
+            same += 1
+            max_err = max(max_err, float(np.abs(g_blocks[i] - ora.blocks[i]).max()))
+        elif ora.gap[i, int(np.argmin(eq))] < 1e-4:
+            flips += 1
+    truth = np.stack([wl.truth[y:y + 16, x:x + 16] for (y, x, _) in wl.blocks]).astype(np.float64)
+
+    def psnr(b):
+        return float(10 * np.log10(255.0 ** 2 / np.mean((np.clip(b, 0, 255) - truth) ** 2)))
+    return {"blocks": wl.n_blocks, "identical_paths": same, "near_tie_flips": flips,
+            "max_abs_err": max_err, "psnr_gpu_db": psnr(g_blocks), "psnr_oracle_db": psnr(ora.blocks),
+            "oracle_s": time.perf_counter() - t0}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the FP64 oracle timed on the host cores."""
     if rank != 0:
@@ -214,12 +249,13 @@ def main():
     avail = torch.from_numpy(wl.avail).to(dev)
     blocks = torch.from_numpy(wl.blocks).to(dev)
     ob, tr, w0, st = api.alloc_outputs(plans, n, dev)
+    ws = api.workspace(plans, n, dev)  # work queue + exact-spectrum scratch, allocated once
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def fwd():
         binding.fofse_extrapolate_batch(handles, blocks, frame, avail, out_blocks=ob, trace=tr, w0=w0,
-                                        status=st, stream=stream)
+                                        status=st, workspace=ws, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         fwd()
@@ -298,7 +334,7 @@ def main():
         d_avail.copy_(h_avail, non_blocking=True)
         d_blocks.copy_(h_blocks, non_blocking=True)
         binding.fofse_extrapolate_batch(handles, d_blocks, d_frame, d_avail, out_blocks=ob, trace=tr,
-                                        w0=w0, status=st, stream=stream)
+                                        w0=w0, status=st, workspace=ws, stream=stream)
         h_out.copy_(ob, non_blocking=True)
 
     for _ in range(2):
@@ -326,7 +362,7 @@ def main():
         def one_by_one():
             for i in range(n):
                 binding.fofse_extrapolate_batch(handles, singles[i], frame, avail, out_blocks=ob1[i],
-                                                stream=stream)
+                                                workspace=ws, stream=stream)
         one_by_one()
         torch.cuda.synchronize(dev)
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -343,22 +379,52 @@ def main():
     mhz = clocks.get("sm_mhz") or 1500.0
     bins = 64 * 64 // 2 + 2
     iters = wl.plans[0].iters
-    ops = n * iters * bins * FF_OPS_PER_BIN_ITER
+    ops = n * (iters * bins * OPS_PER_BIN_ITER + OPS_PER_RECURRENCE_TERM * iters * (iters - 1) // 2)
     alu_peak = sms * FP32_LANES_PER_SM * mhz * 1e6
     achieved = ops / (ms_per_step * 1e-3)
     smem_bytes = n * iters * bins * SMEM_BYTES_PER_BIN_ITER
     smem_peak = sms * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
-                "unit": "Tops/s (FP32 lane instructions)", "frac": achieved / alu_peak,
-                "traffic": None, "kernel": "fofse_forward_kernel<ArFF,64,256>",
+                "unit": "Tops/s (FP32 lane operations)", "frac": achieved / alu_peak,
+                "traffic": None, "kernel": "fofse_forward_f2_kernel<64,128,5,false>",
+                "work_per_launch": f"{ops:.4g} FP32 ops ({OPS_PER_BIN_ITER}/bin-iteration + "
+                                   f"{OPS_PER_RECURRENCE_TERM}/recurrence term)",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (sampled)",
                 "smem": {"achieved_TBps": smem_bytes / (ms_per_step * 1e-3) / 1e12,
                          "peak_TBps": smem_peak / 1e12,
                          "frac": smem_bytes / (ms_per_step * 1e-3) / smem_peak}}
 
+    # ---- the other arithmetic variants, same launch form (context) ----
+    variants = {}
+    for prec in ("fp32_fullff", "fp32_plain"):
+        vplans = [api.Plan.from_spec(p, prec) for p in wl.plans]
+        vws = api.workspace(vplans, n, dev)
+        vh = [p.handle for p in vplans]
+
+        def vrun():
+            binding.fofse_extrapolate_batch(vh, blocks, frame, avail, out_blocks=ob, trace=tr, w0=w0,
+                                            status=st, workspace=vws, stream=stream)
+        for _ in range(2):
+            vrun()
+        torch.cuda.synchronize(dev)
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        vt = 0.0
+        for _ in range(5):
+            flush.zero_()
+            v0.record(stream)
+            vrun()
+            v1.record(stream)
+            torch.cuda.synchronize(dev)
+            vt += v0.elapsed_time(v1)
+        variants[prec] = {"ms_per_step": vt / 5, "blocks_per_s": n / (vt / 5 * 1e-3)}
+    fwd()  # leave the product's outputs in place for the parity check
+    torch.cuda.synchronize(dev)
+
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, sample_blocks=min(n, 8 * (os.cpu_count() or 1)))
+        parity = parity_summary(wl, ob, tr, st)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world,
@@ -371,6 +437,7 @@ def main():
                 "fwd_bwd": fwd_bwd_line,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu, "plain_one_block_per_launch": plain,
+                "parity": parity, "variants": variants,
                 "device": props.name, "sms": sms}
         print(json.dumps(line), flush=True)
     if world > 1:
