@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the one-block-per-launch form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     return ap.parse_args()
 
 
@@ -250,6 +251,10 @@ def main():
     blocks = torch.from_numpy(wl.blocks).to(dev)
     ob, tr, w0, st = api.alloc_outputs(plans, n, dev)
     ws = api.workspace(plans, n, dev)  # work queue + exact-spectrum scratch, allocated once
+    tuned = None
+    if not args.no_tune:  # launch shape per plan, timed on this batch once per machine (cached)
+        from paper_2207_01205_gb300 import autotune
+        tuned = autotune.autotune(plans, blocks, frame, avail)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -433,6 +438,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "blocks_per_gpu": n, "arith": "float-float (f32 pairs)",
                            "l2": "flushed between steps (512 MiB write)",
+                "launch_shape": tuned["choices"] if tuned else "default",
                            "parallelism": f"replicas x{world}"},
                 "fwd_bwd": fwd_bwd_line,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline,

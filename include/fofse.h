@@ -116,6 +116,14 @@ fofse_status fofse_plan_set_support(fofse_plan plan, int shape);
 /* Arithmetic (FOFSE_FP32 default, FOFSE_FP64_VALIDATE, FOFSE_FP32_PLAIN,
  * FOFSE_FP32_FULLFF, FOFSE_FP32_FILTERED). */
 fofse_status fofse_plan_set_precision(fofse_plan plan, int precision);
+/* Number of launch shapes (threads per block / resident blocks per SM) of the
+ * plan's kernel for its current precision; 0 for a NULL plan. */
+int fofse_plan_variant_count(fofse_plan plan);
+/* Selects launch shape `variant` (0 <= variant < fofse_plan_variant_count;
+ * default 0), e.g. from an autotuner.  Every shape computes the same result up
+ * to the rounding of float-float sums.  FOFSE_E_ARG otherwise.  Changing the
+ * precision resets an out-of-range variant to 0. */
+fofse_status fofse_plan_set_variant(fofse_plan plan, int variant);
 /* Frees the plan's tables (synchronises the device).  NULL is ignored. */
 void fofse_plan_destroy(fofse_plan plan);
 

@@ -1,0 +1,100 @@
+"""Autotuner of the kernels' launch shapes (threads per block and resident
+blocks per SM of the product kernel, selected per plan with
+fofse_plan_set_variant).
+
+It times every shape of every plan on the caller's own batch with CUDA events
+and keeps the fastest; choices are cached in a JSON file keyed by the GPU
+name, the plan's parameters and the batch size (rounded to a power of two),
+so a workload is timed once per machine.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import torch
+
+from . import api
+from . import binding as B
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+_lock = threading.Lock()
+
+
+def _key(plan, n_blocks, device):
+    name = torch.cuda.get_device_name(device)
+    bucket = 1 << max(0, int(n_blocks) - 1).bit_length()
+    return (f"{name}|T{plan.fft_size}|b{plan.block}|br{plan.border}|I{plan.iters}|"
+            f"{plan.precision}|s{plan.support}|n{bucket}")
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def autotune(plans, blocks, frame, avail, *, reps: int = 3, use_cache: bool = True,
+             cache_path: str = CACHE, stream=None) -> dict:
+    """Select the fastest launch shape of every plan for this batch.  Returns
+    {"choices": [variant per plan], "timings_ms": [...], "cached": [bool]}."""
+    plans = list(plans)
+    n = int(blocks.shape[0])
+    dev = frame.device
+    stream = stream or torch.cuda.current_stream(dev)
+    with _lock:
+        cache = _load(cache_path) if use_cache else {}
+    choices, timings, cached = [], [], []
+    ob, tr, w0, st = api.alloc_outputs(plans, n, dev)
+    ws = api.workspace(plans, n, dev)
+    handles = [p.handle for p in plans]
+
+    def run():
+        B.fofse_extrapolate_batch(handles, blocks, frame, avail, out_blocks=ob, trace=tr, w0=w0,
+                                  status=st, workspace=ws, stream=stream)
+
+    for p in plans:
+        count = B.fofse_plan_variant_count(p.handle)
+        key = _key(p, n, dev)
+        if use_cache and key in cache and 0 <= cache[key]["variant"] < count:
+            B.fofse_plan_set_variant(p.handle, cache[key]["variant"])
+            choices.append(cache[key]["variant"])
+            timings.append(cache[key]["ms"])
+            cached.append(True)
+            continue
+        ms = []
+        for v in range(count):
+            B.fofse_plan_set_variant(p.handle, v)
+            run()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                run()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1) / reps)
+        best = min(range(count), key=lambda v: ms[v])
+        B.fofse_plan_set_variant(p.handle, best)
+        choices.append(best)
+        timings.append(ms)
+        cached.append(False)
+        cache[key] = {"variant": best, "ms": ms}
+    B.fofse_check(stream)
+    if use_cache:
+        with _lock:
+            merged = _load(cache_path)
+            merged.update(cache)
+            _save(cache_path, merged)
+    return {"choices": choices, "timings_ms": timings, "cached": cached}

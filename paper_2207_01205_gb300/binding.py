@@ -62,6 +62,10 @@ def _declare(L):
     L.fofse_plan_set_support.restype = _i
     L.fofse_plan_set_precision.argtypes = [_vp, _i]
     L.fofse_plan_set_precision.restype = _i
+    L.fofse_plan_variant_count.argtypes = [_vp]
+    L.fofse_plan_variant_count.restype = _i
+    L.fofse_plan_set_variant.argtypes = [_vp, _i]
+    L.fofse_plan_set_variant.restype = _i
     L.fofse_plan_destroy.argtypes = [_vp]
     L.fofse_plan_destroy.restype = None
     L.fofse_workspace_bytes.argtypes = [ctypes.POINTER(_vp), _i, _i]
@@ -141,6 +145,14 @@ def fofse_plan_set_support(plan, shape):
 def fofse_plan_set_precision(plan, precision):
     _check(load().fofse_plan_set_precision(ctypes.c_void_p(plan), int(precision)),
            "fofse_plan_set_precision")
+
+
+def fofse_plan_variant_count(plan) -> int:
+    return load().fofse_plan_variant_count(ctypes.c_void_p(plan))
+
+
+def fofse_plan_set_variant(plan, variant):
+    _check(load().fofse_plan_set_variant(ctypes.c_void_p(plan), int(variant)), "fofse_plan_set_variant")
 
 
 def fofse_plan_destroy(plan):

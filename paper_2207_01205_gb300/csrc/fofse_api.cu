@@ -226,6 +226,7 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   d.iters = iters;
   d.support = FOFSE_SUPPORT_FULL;
   d.precision = FOFSE_FP32;
+  d.variant = 0;
   d.rho = rho;
   d.gamma = (double)gamma;
   d.gamma_h = gamma;
@@ -256,6 +257,17 @@ fofse_status fofse_plan_set_precision(fofse_plan plan, int precision) {
                 precision != FOFSE_FP32_FILTERED))
     return FOFSE_E_ARG;
   plan->dev.precision = precision;
+  if (plan->dev.variant >= forward_variant_count(plan->dev)) plan->dev.variant = 0;
+  return FOFSE_OK;
+}
+
+int fofse_plan_variant_count(fofse_plan plan) {
+  return plan ? forward_variant_count(plan->dev) : 0;
+}
+
+fofse_status fofse_plan_set_variant(fofse_plan plan, int variant) {
+  if (!plan || variant < 0 || variant >= forward_variant_count(plan->dev)) return FOFSE_E_ARG;
+  plan->dev.variant = variant;
   return FOFSE_OK;
 }
 

@@ -1481,24 +1481,48 @@ template <class A, int T, int NT, int MINB, bool HALF> struct Variant {
 // Kernel choice per (precision, T).  FOFSE_FP32 runs the filtered-exact variant
 // when scratch is available and the all-bins float-float variant otherwise.
 template <int T> struct Pick;
+// Launch shapes of the product (filtered) kernel: threads per block and the
+// minimum resident blocks per SM the register allocation is held to.  The
+// autotuner picks one per plan (fofse_plan_set_variant); variant 0 is the default.
 template <> struct Pick<32> {
   using FF = Variant<ArFF, 32, 128, 6, false>;
-  using FILT = VariantF2<32, 64, 8, false>;
   using F64 = Variant<ArF64, 32, 128, 1, false>;
   using F32 = Variant<ArF32, 32, 128, 6, false>;
+  using V0 = VariantF2<32, 64, 8, false>;
+  using V1 = VariantF2<32, 128, 6, false>;
+  using V2 = VariantF2<32, 64, 12, false>;
+  static constexpr int NV = 3;
 };
 template <> struct Pick<64> {
   using FF = Variant<ArFF, 64, 256, 3, false>;
-  using FILT = VariantF2<64, 128, 5, false>;
   using F64 = Variant<ArF64, 64, 256, 1, false>;
   using F32 = Variant<ArF32, 64, 256, 3, false>;
+  using V0 = VariantF2<64, 128, 5, false>;
+  using V1 = VariantF2<64, 256, 3, false>;
+  using V2 = VariantF2<64, 64, 6, false>;
+  static constexpr int NV = 3;
 };
 template <> struct Pick<128> {
   using FF = Variant<ArFF, 128, 512, 1, true>;
-  using FILT = VariantF2<128, 512, 1, true>;
   using F64 = Variant<ArF64, 128, 512, 1, true>;
   using F32 = Variant<ArF32, 128, 512, 1, true>;
+  using V0 = VariantF2<128, 512, 1, true>;
+  using V1 = VariantF2<128, 512, 1, true>;
+  using V2 = VariantF2<128, 512, 1, true>;
+  static constexpr int NV = 1;
 };
+
+template <int T>
+cudaError_t launch_filtered(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
+                            cudaStream_t s) {
+  using Pk = Pick<T>;
+  switch (a.plan.variant) {
+    case 1: if (a.scratch_bytes >= Pk::V1::per_cta) return Pk::V1::launch(a, tf, ta, s); break;
+    case 2: if (a.scratch_bytes >= Pk::V2::per_cta) return Pk::V2::launch(a, tf, ta, s); break;
+    default: if (a.scratch_bytes >= Pk::V0::per_cta) return Pk::V0::launch(a, tf, ta, s); break;
+  }
+  return Pk::FF::launch(a, tf, ta, s);
+}
 
 template <int T>
 cudaError_t launch_T(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta, cudaStream_t s) {
@@ -1508,18 +1532,29 @@ cudaError_t launch_T(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap*
     case FOFSE_FP32_PLAIN: return Pk::F32::launch(a, tf, ta, s);
     case FOFSE_FP32_FULLFF: return Pk::FF::launch(a, tf, ta, s);
     default:  // FOFSE_FP32, FOFSE_FP32_FILTERED
-      if (a.scratch && a.scratch_bytes >= Pk::FILT::per_cta) return Pk::FILT::launch(a, tf, ta, s);
-      return Pk::FF::launch(a, tf, ta, s);
+      if (!a.scratch) return Pk::FF::launch(a, tf, ta, s);
+      return launch_filtered<T>(a, tf, ta, s);
   }
 }
+// Scratch for whichever variant the plan may select (the largest of them).
 template <int T> cudaError_t scratch_T(const PlanDev& p, size_t* bytes) {
   using Pk = Pick<T>;
   switch (p.precision) {
     case FOFSE_FP64_VALIDATE: return Pk::F64::scratch(p.iters, bytes);
     case FOFSE_FP32_PLAIN: return Pk::F32::scratch(p.iters, bytes);
     case FOFSE_FP32_FULLFF: return Pk::FF::scratch(p.iters, bytes);
-    default: return Pk::FILT::scratch(p.iters, bytes);
+    default: {
+      size_t b0 = 0, b1 = 0, b2 = 0;
+      cudaError_t e = Pk::V0::scratch(p.iters, &b0);
+      if (e == cudaSuccess && Pk::NV > 1) e = Pk::V1::scratch(p.iters, &b1);
+      if (e == cudaSuccess && Pk::NV > 2) e = Pk::V2::scratch(p.iters, &b2);
+      *bytes = b0 > b1 ? (b0 > b2 ? b0 : b2) : (b1 > b2 ? b1 : b2);
+      return e;
+    }
   }
+}
+template <int T> int variants_T(const PlanDev& p) {
+  return (p.precision == FOFSE_FP32 || p.precision == FOFSE_FP32_FILTERED) ? Pick<T>::NV : 1;
 }
 
 }  // namespace
@@ -1534,6 +1569,13 @@ size_t forward_scratch_bytes(const PlanDev& p) {
 }
 
 bool forward_needs_scratch(const PlanDev& p) { return p.T == 128; }
+
+int forward_variant_count(const PlanDev& p) {
+  if (p.T == 32) return variants_T<32>(p);
+  if (p.T == 64) return variants_T<64>(p);
+  if (p.T == 128) return variants_T<128>(p);
+  return 1;
+}
 
 cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
                            cudaStream_t s) {

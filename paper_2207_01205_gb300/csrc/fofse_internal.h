@@ -28,6 +28,7 @@ struct PlanTables {
 
 struct PlanDev {
   int block, border, Ls, T, iters, support, precision;
+  int variant;  // launch shape of the product kernel (0 = default)
   float gamma_h, gamma_l;  // gamma as float pair
   double gamma;
   float rho;
@@ -84,6 +85,7 @@ cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tm_frame,
 // (0 if none); a plan with forward_needs_scratch() fails without it.
 size_t forward_scratch_bytes(const PlanDev& p);
 bool forward_needs_scratch(const PlanDev& p);
+int forward_variant_count(const PlanDev& p);
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t stream);
 
 }  // namespace fofse

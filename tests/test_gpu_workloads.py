@@ -112,3 +112,29 @@ def test_prediction_workload_rho_gamma_gradients(pred):
         o_rg += rg[0]
     assert g_rg[0] == pytest.approx(o_rg[0], rel=1e-3)
     assert g_rg[1] == pytest.approx(o_rg[1], rel=1e-3)
+
+
+def test_autotuner_picks_a_shape_and_all_shapes_agree(tmp_path):
+    """Every launch shape gives the same selection paths (and samples within
+    the parity tolerance); the tuned choice is cached and reused."""
+    from paper_2207_01205_gb300 import autotune
+    wl = synth.small_frame(61, plan=synth.PlanSpec(16, 16, 64, 0.8, 0.5, 80), n_lost=9)
+    plans = [api.Plan.from_spec(p) for p in wl.plans]
+    frame, avail, blocks = to_device(wl)
+    count = binding.fofse_plan_variant_count(plans[0].handle)
+    assert count >= 2
+    outs = []
+    for v in range(count):
+        binding.fofse_plan_set_variant(plans[0].handle, v)
+        outs.append(api.extrapolate(plans, blocks, frame, avail))
+    torch.cuda.synchronize()
+    for r in outs[1:]:
+        assert np.array_equal(r.path(), outs[0].path())
+        assert float((r.blocks - outs[0].blocks).abs().max()) <= 1e-3
+    path = str(tmp_path / "tune.json")
+    first = autotune.autotune(plans, blocks, frame, avail, cache_path=path)
+    assert first["cached"] == [False] and 0 <= first["choices"][0] < count
+    again = autotune.autotune(plans, blocks, frame, avail, cache_path=path)
+    assert again["cached"] == [True] and again["choices"] == first["choices"]
+    with pytest.raises(binding.FofseError):
+        binding.fofse_plan_set_variant(plans[0].handle, count)
