@@ -526,7 +526,7 @@ def main():
                 "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "blocks_per_gpu": n, "arith": "float-float (f32 pairs)",
+                "config": {"workload": WORKLOAD, "blocks_per_gpu": n, "arith": "FP32 spectrum with an error bound; exact float-float decisions and coefficients",
                            "l2": "flushed between steps (512 MiB write)",
                 "launch_shape": tuned["choices"] if tuned else "default",
                            "parallelism": f"replicas x{world}"},
