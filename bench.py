@@ -345,6 +345,7 @@ def main():
     if not args.no_tune:  # launch shape per plan, timed on this batch once per machine (cached)
         from paper_2207_01205_gb300 import autotune
         tuned = autotune.autotune(plans, blocks, frame, avail)
+    variant = tuned["choices"][0] if tuned else 0
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -481,7 +482,7 @@ def main():
     smem_peak = sms * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                 "unit": "Tops/s (FP32 lane operations)", "frac": achieved / alu_peak,
-                "traffic": None, "kernel": "fofse_forward_f2_kernel<64,128,5,false>",
+                "traffic": None, "kernel": f"fofse_forward_f3_kernel<64,...> (launch shape variant {variant})",
                 "work_per_launch": f"{ops:.4g} FP32 ops ({OPS_PER_BIN_ITER}/bin-iteration + "
                                    f"{OPS_PER_RECURRENCE_TERM}/recurrence term)",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (sampled)",
@@ -491,7 +492,7 @@ def main():
 
     # ---- the other arithmetic variants, same launch form (context) ----
     variants = {}
-    for prec in ("fp32_fullff", "fp32_plain"):
+    for prec in ("fp32_filtered", "fp32_fullff", "fp32_plain"):
         vplans = [api.Plan.from_spec(p, prec) for p in wl.plans]
         vws = api.workspace(vplans, n, dev)
         vh = [p.handle for p in vplans]

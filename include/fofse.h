@@ -232,6 +232,13 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
  * reported an error. */
 fofse_status fofse_check(void* stream);
 
+/* The cudaError_t value behind the most recent FOFSE_E_CUDA returned to the
+ * calling thread (0 if there was none), and its static name (e.g.
+ * "cudaErrorInvalidValue").  No counterpart in the paper: host-side error
+ * reporting of this library. */
+int fofse_last_cuda_error(void);
+const char* fofse_last_cuda_error_string(void);
+
 /* Static, human-readable name of a status code. */
 const char* fofse_status_string(fofse_status status);
 

@@ -32,6 +32,8 @@ class FofseError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
         msg = _lib.fofse_status_string(status).decode() if _lib is not None else str(status)
+        if _lib is not None and status == E_CUDA:
+            msg += f" [{_lib.fofse_last_cuda_error_string().decode()}]"
         super().__init__(f"{where}: {msg} (status {status})")
 
 
@@ -81,6 +83,8 @@ def _declare(L):
     L.fofse_backward.restype = _i
     L.fofse_check.argtypes = [_vp]
     L.fofse_check.restype = _i
+    L.fofse_last_cuda_error.restype = _i
+    L.fofse_last_cuda_error_string.restype = ctypes.c_char_p
 
 
 def load(build: bool = True):
@@ -208,6 +212,14 @@ def fofse_backward(plans, blocks, frame, avail, trace, w0, grad_blocks, *, grad_
         _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
         _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(trace), _ptr(w0), _ptr(grad_blocks),
         _ptr(grad_frame), _ptr(grad_rho_gamma), _ptr(workspace), _stream(stream)), "fofse_backward")
+
+
+def fofse_last_cuda_error() -> int:
+    return load().fofse_last_cuda_error()
+
+
+def fofse_last_cuda_error_string() -> str:
+    return load().fofse_last_cuda_error_string().decode()
 
 
 def fofse_check(stream=None):

@@ -99,6 +99,13 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 bool supported_T(int T) { return T == 32 || T == 64 || T == 128; }
 
+// CUDA runtime error behind the most recent FOFSE_E_CUDA of this thread
+thread_local int g_last_cuda = 0;
+fofse_status cuda_fail(cudaError_t e) {
+  g_last_cuda = static_cast<int>(e);
+  return FOFSE_E_CUDA;
+}
+
 constexpr int kMaxPlans = 64;
 constexpr size_t kCounterBytes = 256;  // one int work-queue counter per plan
 
@@ -207,10 +214,10 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   void* mem = nullptr;
   cudaError_t e = cudaMalloc(&mem, total);
   if (e == cudaErrorMemoryAllocation) return FOFSE_E_NOMEM;
-  if (e != cudaSuccess) return FOFSE_E_CUDA;
-  if (cudaMemcpy(mem, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (e != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemcpy(mem, host.data(), total, cudaMemcpyHostToDevice)) != cudaSuccess) {
     cudaFree(mem);
-    return FOFSE_E_CUDA;
+    return cuda_fail(e);
   }
   fofse_plan p = new (std::nothrow) fofse_plan_s;
   if (!p) {
@@ -305,7 +312,7 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
   }
   if (n_blocks == 0) return FOFSE_OK;
   unsigned* err = err_word_ptr();
-  if (!err) return FOFSE_E_CUDA;
+  if (!err) return cuda_fail(cudaGetLastError());
   const size_t scratch = scratch_bytes(plans, n_plans);
   for (int i = 0; i < n_plans; ++i)  // T = 128 needs its FFT scratch
     if (forward_needs_scratch(plans[i]->dev) && !d_workspace) return FOFSE_E_ARG;
@@ -315,7 +322,8 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
   if (d_workspace) {
     queue = static_cast<int*>(d_workspace);
     scratch_base = static_cast<unsigned char*>(d_workspace) + kCounterBytes;
-    if (cudaMemsetAsync(queue, 0, kCounterBytes, s) != cudaSuccess) return FOFSE_E_CUDA;
+    const cudaError_t e = cudaMemsetAsync(queue, 0, kCounterBytes, s);
+    if (e != cudaSuccess) return cuda_fail(e);
   }
 
   const uintptr_t fa = reinterpret_cast<uintptr_t>(d_frame), aa = reinterpret_cast<uintptr_t>(d_avail);
@@ -371,7 +379,7 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
                   P.Ls))
       a.use_tma = 1;
     cudaError_t e = launch_forward(a, &tf, &ta, s);
-    if (e != cudaSuccess) return FOFSE_E_CUDA;
+    if (e != cudaSuccess) return cuda_fail(e);
   }
   return FOFSE_OK;
 }
@@ -403,10 +411,11 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
   if (n_blocks == 0) return FOFSE_OK;
   unsigned* err = err_word_ptr();
   int* queue = noalloc_queue_ptr();
-  if (!err || !queue) return FOFSE_E_CUDA;
+  if (!err || !queue) return cuda_fail(cudaGetLastError());
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the counters keep the previous call's values: clear them on this stream
-  if (cudaMemsetAsync(queue, 0, sizeof(int) * kNoAllocCounters, s) != cudaSuccess) return FOFSE_E_CUDA;
+  cudaError_t e0 = cudaMemsetAsync(queue, 0, sizeof(int) * kNoAllocCounters, s);
+  if (e0 != cudaSuccess) return cuda_fail(e0);
   const uintptr_t fa = reinterpret_cast<uintptr_t>(d_frame), aa = reinterpret_cast<uintptr_t>(d_avail);
   const bool tma_ok = encode_fn() && (fa % 16 == 0) && (aa % 16 == 0) && (pitch % 16 == 0);
   for (int pi = 0; pi < n_plans; ++pi) {
@@ -446,7 +455,8 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
         encode_2d(&ta, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d_avail, width, height, pitch, a.box_a,
                   P.Ls))
       a.use_tma = 1;
-    if (launch_forward(a, &tf, &ta, s) != cudaSuccess) return FOFSE_E_CUDA;
+    const cudaError_t e = launch_forward(a, &tf, &ta, s);
+    if (e != cudaSuccess) return cuda_fail(e);
   }
   return FOFSE_OK;
 }
@@ -472,7 +482,7 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
   }
   if (n_blocks == 0 || (!d_grad_frame && !d_grad_rho_gamma)) return FOFSE_OK;
   unsigned* err = err_word_ptr();
-  if (!err) return FOFSE_E_CUDA;
+  if (!err) return cuda_fail(cudaGetLastError());
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int pi = 0; pi < n_plans; ++pi) {
     BwdArgs a;
@@ -497,21 +507,26 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
     a.err = err;
     cudaError_t e = launch_backward(a, s);
     if (e == cudaErrorNotSupported) return FOFSE_E_UNSUPPORTED;
-    if (e != cudaSuccess) return FOFSE_E_CUDA;
+    if (e != cudaSuccess) return cuda_fail(e);
   }
   return FOFSE_OK;
 }
 
+int fofse_last_cuda_error(void) { return g_last_cuda; }
+
+const char* fofse_last_cuda_error_string(void) { return cudaGetErrorName(static_cast<cudaError_t>(g_last_cuda)); }
+
 fofse_status fofse_check(void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return FOFSE_E_CUDA;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e);
   unsigned* err = err_word_ptr();
-  if (!err) return FOFSE_E_CUDA;
+  if (!err) return cuda_fail(cudaGetLastError());
   unsigned v = 0;
-  if (cudaMemcpy(&v, err, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return FOFSE_E_CUDA;
+  if ((e = cudaMemcpy(&v, err, sizeof(v), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
   if (v) {
     unsigned z = 0;
-    if (cudaMemcpy(err, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return FOFSE_E_CUDA;
+    if ((e = cudaMemcpy(err, &z, sizeof(z), cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_fail(e);
   }
   if (v & kErrTimeout) return FOFSE_E_TIMEOUT;
   return FOFSE_OK;

@@ -26,6 +26,7 @@
 // FP32 arithmetic throughout (the gradients' tolerance is relative 1e-3).
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -296,17 +297,19 @@ template <int T, int NT> size_t bwd_smem(int iters) {
 template <int T, int NT> cudaError_t launch_bwd(const BwdArgs& a, cudaStream_t s) {
   const size_t sm = bwd_smem<T, NT>(a.plan.iters);
   auto kern = fofse_backward_kernel<T, NT>;
-  {  // raise the kernel's shared-memory limit once per device and size
+  {  // the kernel's shared-memory limit (one per device) only grows: a smaller
+     // request never lowers it below a size launched before
     static std::mutex mu;
-    static std::set<std::pair<int, size_t>> done;
+    static std::map<int, size_t> limit;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(mu);
-    if (!done.count({dev, sm})) {
+    auto lim = limit.find(dev);
+    if (lim == limit.end() || lim->second < sm) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
-      done.insert({dev, sm});
+      limit[dev] = sm;
     }
   }
   kern<<<a.n_blocks, NT, sm, s>>>(a);

@@ -87,5 +87,11 @@ size_t forward_scratch_bytes(const PlanDev& p);
 bool forward_needs_scratch(const PlanDev& p);
 int forward_variant_count(const PlanDev& p);
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t stream);
+// The register-blocked filtered-exact forward (fofse_fwd3.cu): launch (needs
+// scratch), the scratch it uses, and its number of launch shapes.
+cudaError_t launch_forward_f3(const FwdArgs& a, const CUtensorMap* tm_frame,
+                              const CUtensorMap* tm_avail, cudaStream_t stream);
+size_t forward_f3_scratch_bytes(const PlanDev& p);
+int forward_f3_variant_count(const PlanDev& p);
 
 }  // namespace fofse

@@ -122,6 +122,25 @@ def test_repeated_calls_are_bitwise_identical():
     assert np.array_equal(r1.trace.cpu().numpy(), r2.trace.cpu().numpy())
 
 
+def test_longer_then_shorter_then_longer_iteration_counts():
+    """A kernel's shared-memory size grows with the iteration count; a call with
+    fewer iterations must not break a later call with more (same FFT size),
+    forward and backward."""
+    from paper_2207_01205_gb300 import api, binding
+    import torch
+    for iters in (230, 17, 230):
+        wl = synth.small_frame(13, plan=synth.PlanSpec(16, 16, 64, 0.8, 0.5, iters), n_lost=3)
+        res, plans = run_gpu(wl, "fp32")
+        frame = torch.from_numpy(wl.frame).cuda()
+        avail = torch.from_numpy(wl.avail).cuda()
+        blocks = torch.from_numpy(wl.blocks).cuda()
+        gf = torch.zeros_like(frame)
+        binding.fofse_backward([p.handle for p in plans], blocks, frame, avail, res.trace, res.w0,
+                               torch.ones_like(res.blocks), grad_frame=gf)
+        binding.fofse_check()
+        assert (res.status.cpu().numpy() == 0).all()
+
+
 @pytest.fixture(scope="module")
 def c1():
     wl = synth.frame_concealment()
