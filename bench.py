@@ -246,7 +246,7 @@ def run_other_workload(args, rank, world, local):
     def bwd():
         torch.mul(torch.sub(ob, truth, out=gblk), 2.0, out=gblk)
         binding.fofse_backward(handles, blocks, frame, avail, tr, w0, gblk, grad_frame=gframe,
-                               grad_rho_gamma=grg, stream=stream)
+                               grad_rho_gamma=grg, workspace=ws, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         fwd()
@@ -389,7 +389,7 @@ def main():
         fwd()
         torch.mul(torch.sub(ob, truth, out=gblk), 2.0, out=gblk)   # dl/dB for l = sum (B - f)^2
         binding.fofse_backward(handles, blocks, frame, avail, tr, w0, gblk, grad_frame=gframe,
-                               grad_rho_gamma=grg, stream=stream)
+                               grad_rho_gamma=grg, workspace=ws, stream=stream)
 
     for _ in range(3):
         fwd_bwd()
@@ -406,7 +406,7 @@ def main():
         bw_s[k].record(stream)
         torch.mul(torch.sub(ob, truth, out=gblk), 2.0, out=gblk)
         binding.fofse_backward(handles, blocks, frame, avail, tr, w0, gblk, grad_frame=gframe,
-                               grad_rho_gamma=grg, stream=stream)
+                               grad_rho_gamma=grg, workspace=ws, stream=stream)
         bw_e[k].record(stream)
     torch.cuda.synchronize(dev)
     fb_tot = reduce_max(sum(s.elapsed_time(e) for s, e in zip(starts, bw_e)), world, dev)

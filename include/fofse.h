@@ -128,13 +128,16 @@ fofse_status fofse_plan_set_variant(fofse_plan plan, int variant);
 void fofse_plan_destroy(fofse_plan plan);
 
 /*
- * fofse_workspace_bytes -- device scratch for fofse_extrapolate_batch with
- * these plans on the current device: 256 bytes of work-queue counters (one per
- * plan, zeroed by every call) plus one slot per resident CTA of the largest
- * plan kernel: the exact initial spectrum of the block in flight (FOFSE_FP32,
- * 16 bytes per conjugate pair) and, at fft_size 128, a 256 KB FFT buffer
- * (about 15 MB for 16x16 blocks with a 64x64 FFT on 152 SMs).  Returns 0 for
- * invalid arguments (more than 64 plans, a NULL plan).
+ * fofse_workspace_bytes -- device scratch for fofse_extrapolate_batch and
+ * fofse_backward with these plans and n_blocks blocks on the current device;
+ * the larger of the two needs (the calls never use it at the same time).
+ * Forward: 256 bytes of work-queue counters (one per plan, zeroed by every
+ * call) plus one slot per resident CTA of the largest plan kernel: the block's
+ * FFT buffer, then its exact W, and its exact initial spectrum (FOFSE_FP32:
+ * 96 KB per CTA at fft_size 64, about 90 MB on 152 SMs; 384 KB at fft_size
+ * 128).  Backward: per block, the adjoint coefficients (8 bytes per iteration)
+ * and 44 bytes of sums and counters.  Returns 0 for invalid arguments (more
+ * than 64 plans, a NULL plan).
  */
 size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks);
 
@@ -218,6 +221,13 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
  *   d_grad_blocks      dloss/dB_hat, n_blocks x bmax x bmax (as d_out_blocks)
  *   d_grad_frame       nullable; dloss/df ACCUMULATED (+=) at every sample of A
  *   d_grad_rho_gamma   nullable; n_plans x 2 floats, ACCUMULATED (+=)
+ *   d_workspace        nullable; fofse_workspace_bytes() bytes for the same
+ *                      plans and n_blocks.  With it the adjoint runs as two
+ *                      kernels (a per-block triangular solve, then a sample
+ *                      pass spread over several CTAs per block); without it,
+ *                      as one kernel per block (slower on large batches).
+ *                      Must not be shared with a call that may run at the
+ *                      same time.
  * Not implemented for FOFSE_FP64_VALIDATE plans (FOFSE_E_UNSUPPORTED).
  */
 fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_block* d_blocks,

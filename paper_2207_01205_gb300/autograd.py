@@ -30,9 +30,10 @@ class FOFSEFunction(torch.autograd.Function):
         need_f, need_r, need_g = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
         gf = torch.zeros_like(frame) if need_f else None
         grg = torch.zeros((len(ctx.plans), 2), dtype=torch.float32, device=frame.device)
+        ws = api.workspace(ctx.plans, int(blocks.shape[0]), frame.device)
         B.fofse_backward([p.handle for p in ctx.plans], blocks, frame, avail, trace, w0,
                          grad_blocks.contiguous(), grad_frame=gf,
-                         grad_rho_gamma=grg if (need_r or need_g) else None)
+                         grad_rho_gamma=grg if (need_r or need_g) else None, workspace=ws)
         gr = grg[:, 0].reshape(ctx.rho_shape) if need_r else None
         gg = grg[:, 1].reshape(ctx.gamma_shape) if need_g else None
         return gf, gr, gg, None, None, None, None

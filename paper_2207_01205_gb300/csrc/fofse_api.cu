@@ -116,6 +116,23 @@ int sm_count() {
   return sms;
 }
 
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Backward workspace: abar (n x imax float2), W0bar (n floats), then the
+// FP64 d/drho accumulators (n x 4) and the finished-CTA counters (n), the
+// last two contiguous so that one memset clears them.
+struct BwdLayout {
+  size_t abar, w0bar, acc, cnt, total, clear;
+  BwdLayout(int n, int imax) {
+    abar = 0;
+    w0bar = align256((size_t)n * imax * sizeof(float2));
+    acc = w0bar + align256((size_t)n * sizeof(float));
+    cnt = acc + align256((size_t)n * 4 * sizeof(double));
+    total = cnt + align256((size_t)n * sizeof(unsigned));
+    clear = total - acc;
+  }
+};
+
 // Plans run one after another on the stream and share one scratch region.
 size_t scratch_bytes(const fofse_plan* plans, int n_plans) {
   size_t m = 0;
@@ -287,9 +304,14 @@ void fofse_plan_destroy(fofse_plan plan) {
 
 size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks) {
   if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return 0;
-  for (int i = 0; i < n_plans; ++i)
+  int imax = 0;
+  for (int i = 0; i < n_plans; ++i) {
     if (!plans[i]) return 0;
-  return kCounterBytes + scratch_bytes(plans, n_plans);
+    imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
+  }
+  const size_t fwd = kCounterBytes + scratch_bytes(plans, n_plans);
+  const size_t bwd = BwdLayout(n_blocks, imax).total;
+  return fwd > bwd ? fwd : bwd;
 }
 
 fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
@@ -467,7 +489,6 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
                             const fofse_trace_entry* d_trace, const float* d_w0,
                             const float* d_grad_blocks, float* d_grad_frame,
                             float* d_grad_rho_gamma, void* d_workspace, void* stream) {
-  (void)d_workspace;
   if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return FOFSE_E_ARG;
   if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail || !d_trace || !d_w0 || !d_grad_blocks))
     return FOFSE_E_ARG;
@@ -484,6 +505,12 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
   unsigned* err = err_word_ptr();
   if (!err) return cuda_fail(cudaGetLastError());
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const BwdLayout L(n_blocks, imax);
+  unsigned char* ws = static_cast<unsigned char*>(d_workspace);
+  if (ws) {
+    const cudaError_t e = cudaMemsetAsync(ws + L.acc, 0, L.clear, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   for (int pi = 0; pi < n_plans; ++pi) {
     BwdArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -505,6 +532,12 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
     a.grad_frame = d_grad_frame;
     a.grad_rho_gamma = d_grad_rho_gamma ? d_grad_rho_gamma + 2 * pi : nullptr;
     a.err = err;
+    if (ws) {
+      a.abar = reinterpret_cast<float2*>(ws + L.abar);
+      a.w0bar = reinterpret_cast<float*>(ws + L.w0bar);
+      a.acc = reinterpret_cast<double*>(ws + L.acc);
+      a.cnt = reinterpret_cast<unsigned*>(ws + L.cnt);
+    }
     cudaError_t e = launch_backward(a, s);
     if (e == cudaErrorNotSupported) return FOFSE_E_UNSUPPORTED;
     if (e != cudaSuccess) return cuda_fail(e);

@@ -45,7 +45,7 @@ template <int T> __device__ __forceinline__ bool self_conj(int u1, int u2) {
   return ((u1 & (T / 2 - 1)) == 0) && ((u2 & (T / 2 - 1)) == 0);
 }
 
-template <int T, int NT>
+template <int T, int NT, bool SPLIT>
 __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constant__ BwdArgs args) {
   constexpr int LOGT = ilog2c(T), T2 = 2 * T, NW = NT / 32;
   extern __shared__ unsigned char smem_raw[];
@@ -215,6 +215,11 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
   for (int w = 0; w < NW; ++w) dot += red[w];
   const float w0bar = (float)(-dot / w0);  // W0 = W[0] = sum of w
   if (tid == 0 && args.grad_rho_gamma) atomicAdd(&args.grad_rho_gamma[1], (float)(dot / gamma));
+  if constexpr (SPLIT) {  // the sample kernel takes it from here
+    for (int i = tid; i < iters; i += NT) args.abar[(size_t)blk * args.trace_stride + i] = ta[i];
+    if (tid == 0) args.w0bar[blk] = w0bar;
+    return;
+  }
   __syncthreads();  // red is reused below
 
   // ---- chain to the samples, rho and gamma ------------------------------------
@@ -288,31 +293,231 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
   }
 }
 
+// Number of support positions of a block (A's shape inside L, B excluded) and
+// the position of rank k in L coordinates.  Full support: the rows above B,
+// the rows of B without B, the rows below B.  Causal L shape: the rows above B
+// up to its right edge, then the samples left of B in B's rows.
+__device__ __forceinline__ int support_positions(int support, int Ls, int b, int br) {
+  return support == FOFSE_SUPPORT_CAUSAL_L ? br * (br + b) + b * br : Ls * Ls - b * b;
+}
+__device__ __forceinline__ void support_rank_to_mn(int k, int support, int Ls, int b, int br, int& m,
+                                                   int& n) {
+  if (support == FOFSE_SUPPORT_CAUSAL_L) {
+    const int top = br * (br + b);
+    if (k < top) {
+      m = k / (br + b);
+      n = k - m * (br + b);
+    } else {
+      const int k2 = k - top;
+      m = br + k2 / br;
+      n = k2 - (m - br) * br;
+    }
+    return;
+  }
+  const int top = br * Ls, mid = b * (Ls - b);
+  if (k < top) {
+    m = k / Ls;
+    n = k - m * Ls;
+  } else if (k < top + mid) {
+    const int k2 = k - top, w = Ls - b;
+    const int r = k2 / w, c = k2 - r * w;
+    m = br + r;
+    n = c < br ? c : c + b;
+  } else {
+    const int k2 = k - top - mid;
+    const int r = k2 / Ls;
+    m = br + b + r;
+    n = k2 - r * Ls;
+  }
+}
+
+// Sample pass of the split backward: CTA (block, chunk) rebuilds the residual
+// f - g_{i-1} along the trace and accumulates xbar and wbar (see the header
+// comment) for S support samples per thread at a time.  Per sample and
+// iteration: the phase (u1 m + u2 n) mod T from one 32-bit multiply of packed
+// operands (mn = m 2^(32-L) + n 2^(16-L), U = u1 + u2 2^16, L = log2 T: the
+// product's top L bits are the phase, the cross term n u1 2^(16-L) stays
+// below them), one table load and six FP32 operations.  The chunk CTAs of a
+// block add their FP64 d/drho sums into the block's accumulators; the last to
+// finish turns them into the block's d/drho.
+template <int T, int NT, int S>
+__global__ void __launch_bounds__(NT) fofse_backward_samples_kernel(const __grid_constant__ BwdArgs args,
+                                                                    int chunks) {
+  constexpr int LOGT = ilog2c(T), NW = NT / 32;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 15) & ~uintptr_t(15));
+  const PlanDev& P = args.plan;
+  const int iters = P.iters;
+  float2* syn = reinterpret_cast<float2*>(smem);  // (cos, sin)(2 pi p / T)
+  float2* tab = syn + T;                           // abar_i
+  float2* tcm = tab + iters;                       // (1 + s_i) c_i
+  unsigned* tU = reinterpret_cast<unsigned*>(tcm + iters);  // u1 + u2 2^16
+  double* red = reinterpret_cast<double*>(smem + ((sizeof(float2) * (T + 2 * iters) +
+                                                    sizeof(unsigned) * iters + 15) & ~size_t(15)));
+  __shared__ bool s_last;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int blk = blockIdx.x / chunks, chunk = blockIdx.x - blk * chunks;
+  const fofse_block bd = args.blocks[blk];
+  if (bd.plan != args.plan_index) return;
+  const float w0 = args.w0[blk];
+  if (!(w0 > 0.f)) return;  // no support: zero gradient (the solve kernel skipped it too)
+  const int b = P.block, br = P.border, Ls = P.Ls;
+  const int ly0 = bd.y - br, lx0 = bd.x - br;
+
+  for (int e = tid; e < T; e += NT) syn[e] = P.tab.syn_f32[e];
+  for (int i = tid; i < iters; i += NT) {
+    const fofse_trace_entry e = args.trace[(size_t)blk * args.trace_stride + i];
+    const int u1 = (uint16_t)e.u1, u2 = (uint16_t)e.u2;
+    const float mult = self_conj<T>(u1, u2) ? 1.f : 2.f;
+    tcm[i] = make_float2(mult * e.dc_re, mult * e.dc_im);
+    tU[i] = (unsigned)u1 | ((unsigned)u2 << 16);
+    tab[i] = args.abar[(size_t)blk * args.trace_stride + i];
+  }
+  __syncthreads();
+
+  const int npos = support_positions(P.support, Ls, b, br);
+  const float c0 = br + (b - 1) * 0.5f;
+  const float w0bar = args.w0bar[blk];
+  double s_wwd = 0.0, s_ww = 0.0, s_wd = 0.0, s_w = 0.0;
+  for (int base = chunk * NT * S; base < npos; base += chunks * NT * S) {
+    float r[S], xb[S], wb[S];
+    unsigned mn[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const int k = base + tid + j * NT;
+      r[j] = 0.f;
+      xb[j] = 0.f;
+      wb[j] = 0.f;
+      mn[j] = 0u;
+      if (k < npos) {
+        int m, n;
+        support_rank_to_mn(k, P.support, Ls, b, br, m, n);
+        const int fy = ly0 + m, fx = lx0 + n;
+        if (fy >= 0 && fy < args.height && fx >= 0 && fx < args.width) {
+          const size_t fi = (size_t)fy * args.pitch + fx;
+          if (args.avail[fi]) r[j] = args.frame[fi];
+        }
+        mn[j] = ((unsigned)m << (32 - LOGT)) | ((unsigned)n << (16 - LOGT));
+      }
+    }
+    for (int i = 0; i < iters; ++i) {
+      const unsigned U = tU[i];
+      const float2 ab = tab[i], cm = tcm[i];
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const float2 cs = syn[(mn[j] * U) >> (32 - LOGT)];
+        const float q = __fmaf_rn(ab.x, cs.x, -ab.y * cs.y);  // Re(abar_i phi_{u_i})
+        xb[j] += q;
+        wb[j] = __fmaf_rn(r[j], q, wb[j]);
+        r[j] = __fmaf_rn(-cm.x, cs.x, __fmaf_rn(cm.y, cs.y, r[j]));  // - (1 + s) Re(c phi)
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const int k = base + tid + j * NT;
+      if (k >= npos) continue;
+      int m, n;
+      support_rank_to_mn(k, P.support, Ls, b, br, m, n);
+      const int fy = ly0 + m, fx = lx0 + n;
+      if (fy < 0 || fy >= args.height || fx < 0 || fx >= args.width) continue;
+      const size_t fi = (size_t)fy * args.pitch + fx;
+      if (!args.avail[fi]) continue;
+      const float w = P.tab.w_f32[m * Ls + n];
+      if (args.grad_frame) atomicAdd(&args.grad_frame[fi], w * xb[j]);
+      const float wbar = wb[j] + w0bar;
+      const float dm = m - c0, dn = n - c0;
+      const double d = (double)sqrtf(dm * dm + dn * dn);
+      const double ww = (double)wbar * (double)w;
+      s_wwd += ww * d;
+      s_ww += ww;
+      s_wd += (double)w * d;
+      s_w += (double)w;
+    }
+  }
+  if (!args.grad_rho_gamma) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s_wwd += __shfl_xor_sync(0xffffffffu, s_wwd, o);
+    s_ww += __shfl_xor_sync(0xffffffffu, s_ww, o);
+    s_wd += __shfl_xor_sync(0xffffffffu, s_wd, o);
+    s_w += __shfl_xor_sync(0xffffffffu, s_w, o);
+  }
+  if (lane == 0) {
+    red[4 * warp + 0] = s_wwd;
+    red[4 * warp + 1] = s_ww;
+    red[4 * warp + 2] = s_wd;
+    red[4 * warp + 3] = s_w;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < NW; ++w)
+      for (int q = 0; q < 4; ++q) v[q] += red[4 * w + q];
+    double* acc = args.acc + 4 * (size_t)blk;
+    for (int q = 0; q < 4; ++q) atomicAdd(&acc[q], v[q]);
+    __threadfence();
+    s_last = atomicAdd(&args.cnt[blk], 1u) == (unsigned)(chunks - 1);
+  }
+  __syncthreads();
+  if (s_last && tid == 0) {  // every chunk's sums are in: d/drho of this block
+    __threadfence();
+    const volatile double* acc = args.acc + 4 * (size_t)blk;
+    const double a = acc[0], bb = acc[1], c = acc[2], d = acc[3];
+    const double dbar = d > 0 ? c / d : 0.0;
+    atomicAdd(&args.grad_rho_gamma[0], (float)((a - dbar * bb) / (double)P.rho));
+  }
+}
+
 template <int T, int NT> size_t bwd_smem(int iters) {
   size_t off = 128 + sizeof(float) * T * 2 * T + sizeof(float2) * T + sizeof(Cx) * (T / 2);
   off += sizeof(int) * ((iters + 1) & ~1) + 3 * sizeof(float2) * iters + 4 * sizeof(double) * (NT / 32);
   return off;
 }
 
-template <int T, int NT> cudaError_t launch_bwd(const BwdArgs& a, cudaStream_t s) {
-  const size_t sm = bwd_smem<T, NT>(a.plan.iters);
-  auto kern = fofse_backward_kernel<T, NT>;
-  {  // the kernel's shared-memory limit (one per device) only grows: a smaller
-     // request never lowers it below a size launched before
-    static std::mutex mu;
-    static std::map<int, size_t> limit;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+// The shared-memory limit of a kernel is one attribute per device; it only
+// grows, so a smaller request never lowers it below a size launched before.
+template <class K> cudaError_t raise_smem_limit(K kern, size_t sm) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const void* kp = reinterpret_cast<const void*>(kern);
+  std::lock_guard<std::mutex> lk(mu);
+  auto lim = limit.find({kp, dev});
+  if (lim == limit.end() || lim->second < sm) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lk(mu);
-    auto lim = limit.find(dev);
-    if (lim == limit.end() || lim->second < sm) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      if (e != cudaSuccess) return e;
-      limit[dev] = sm;
-    }
+    limit[{kp, dev}] = sm;
   }
-  kern<<<a.n_blocks, NT, sm, s>>>(a);
+  return cudaSuccess;
+}
+
+template <int T, int NT, int NTS, int S> cudaError_t launch_bwd(const BwdArgs& a, cudaStream_t s) {
+  const size_t sm = bwd_smem<T, NT>(a.plan.iters);
+  cudaError_t e;
+  if (!a.abar) {  // one kernel per block
+    auto kern = fofse_backward_kernel<T, NT, false>;
+    if ((e = raise_smem_limit(kern, sm)) != cudaSuccess) return e;
+    kern<<<a.n_blocks, NT, sm, s>>>(a);
+    return cudaGetLastError();
+  }
+  auto solve = fofse_backward_kernel<T, NT, true>;
+  if ((e = raise_smem_limit(solve, sm)) != cudaSuccess) return e;
+  solve<<<a.n_blocks, NT, sm, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int iters = a.plan.iters;
+  const size_t sms = ((sizeof(float2) * (T + 2 * iters) + sizeof(unsigned) * iters + 15) & ~size_t(15)) +
+                     sizeof(double) * 4 * (NTS / 32) + 16;
+  const int Ls = a.plan.Ls, b = a.plan.block, br = a.plan.border;
+  const int npos = a.plan.support == FOFSE_SUPPORT_CAUSAL_L ? br * (br + b) + b * br : Ls * Ls - b * b;
+  const int chunks = (npos + NTS * S - 1) / (NTS * S);
+  if ((size_t)a.n_blocks * chunks > 0x7fffffffu) return cudaErrorInvalidValue;
+  auto samples = fofse_backward_samples_kernel<T, NTS, S>;
+  if ((e = raise_smem_limit(samples, sms)) != cudaSuccess) return e;
+  samples<<<(unsigned)(a.n_blocks * chunks), NTS, sms, s>>>(a, chunks);
   return cudaGetLastError();
 }
 
@@ -320,9 +525,9 @@ template <int T, int NT> cudaError_t launch_bwd(const BwdArgs& a, cudaStream_t s
 
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s) {
   if (a.plan.precision == FOFSE_FP64_VALIDATE) return cudaErrorNotSupported;
-  if (a.plan.T == 128) return launch_bwd<128, 512>(a, s);
-  if (a.plan.T == 64) return launch_bwd<64, 256>(a, s);
-  if (a.plan.T == 32) return launch_bwd<32, 128>(a, s);
+  if (a.plan.T == 128) return launch_bwd<128, 512, 128, 8>(a, s);
+  if (a.plan.T == 64) return launch_bwd<64, 256, 128, 8>(a, s);
+  if (a.plan.T == 32) return launch_bwd<32, 128, 64, 4>(a, s);
   return cudaErrorNotSupported;
 }
 

@@ -153,6 +153,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   constexpr int STEP8 = G::RS * T * 8, MSK8 = T * T * 8 - 8;
   constexpr float kU = 5.9604644775390625e-08f;  // 2^-24
   constexpr float kDn = 1.f - 16.f * kU, kUp = 1.f + 256.f * kU, kUpB = 1.f + 16.f * kU;
+  constexpr float kTiny = 7.888609052210118e-31f;     // 2^-100: below it, sqrt is bounded by
+  constexpr float kTinySqrt = 8.881784197001252e-16f; // 2^-50
 
   uint4* t2s = reinterpret_cast<uint4*>(dsm + G::t2_off);
   longlong2* red = reinterpret_cast<longlong2*>(dsm + G::red_off);
@@ -300,9 +302,15 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           g.y = max(g.y, o.x);
         }
       }
-      const float sM1 = sqrtf(__uint_as_float(g.x & ~63u));
-      const float sM2 = sqrtf(__uint_as_float(g.y & ~63u));
-      bnd += 2.1f * kU * sM1 + 12.f * kU * W0f * prevabs;
+      // square roots from the hardware reciprocal square root (relative
+      // error a few ulp, inside the 16u / 256u margins): sM1 is a lower and
+      // sM1u an upper bound of the largest |R32|, sM2 an upper bound of the rest
+      const float m1 = __uint_as_float(g.x & ~63u), m2 = __uint_as_float(g.y & ~63u);
+      const bool n1 = m1 >= kTiny, n2 = m2 >= kTiny;
+      const float r1 = m1 * rsqrtf(n1 ? m1 : 1.f), r2 = m2 * rsqrtf(n2 ? m2 : 1.f);
+      const float sM1 = n1 ? r1 : 0.f, sM1u = n1 ? r1 * kUp : kTinySqrt;
+      const float sM2 = n2 ? r2 : kTinySqrt;
+      bnd += 2.1f * kU * sM1u + 12.f * kU * W0f * prevabs;
       const bool certain = (sM1 * kDn - bnd * kUpB) > (sM2 * kUp + bnd * kUpB);
       // fixed-point unit of the recurrence: every partial sum is below
       // 2 W0 sum_j (|Re c_j| + |Im c_j|) <= 4 W0f csum

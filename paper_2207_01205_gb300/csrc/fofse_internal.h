@@ -76,6 +76,12 @@ struct BwdArgs {
   float* grad_frame;
   float* grad_rho_gamma;  // points at this plan's pair
   unsigned* err;
+  // split form (set when the caller gives a workspace): the solve kernel
+  // writes abar and W0bar per block, the sample kernel reads them
+  float2* abar;      // n_blocks x trace_stride
+  float* w0bar;      // n_blocks
+  double* acc;       // n_blocks x 4 FP64 sums for d/drho (zeroed before the call)
+  unsigned* cnt;     // n_blocks finished-CTA counters (zeroed before the call)
 };
 
 // Launchers (one per translation unit).  Return cudaSuccess or the launch error.

@@ -20,13 +20,16 @@ def _lib(gpu_lib):
     return gpu_lib
 
 
-def _gpu_grads(wl, res, plans, e):
+def _gpu_grads(wl, res, plans, e, split=True):
+    """split: with a workspace (solve kernel + sample-pass kernel); else the
+    one-kernel-per-block form."""
     frame, avail, blocks = to_device(wl)
     gf = torch.zeros_like(frame)
     grg = torch.zeros((len(plans), 2), dtype=torch.float32, device="cuda")
     ge = torch.from_numpy(np.ascontiguousarray(e, dtype=np.float32)).cuda()
+    ws = api.workspace(plans, len(wl.blocks), frame.device) if split else None
     binding.fofse_backward([p.handle for p in plans], blocks, frame, avail, res.trace, res.w0, ge,
-                           grad_frame=gf, grad_rho_gamma=grg)
+                           grad_frame=gf, grad_rho_gamma=grg, workspace=ws)
     torch.cuda.synchronize()
     binding.fofse_check()
     return gf.cpu().numpy().astype(np.float64), grg.cpu().numpy().astype(np.float64)
@@ -42,13 +45,14 @@ def _check(wl, e_fn, tol=1e-3, tol_rho=1e-3):
     ora = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans)
     assert np.array_equal(path, ora.path)
     e = e_fn(res.blocks.cpu().numpy().astype(np.float64))
-    gf, grg = _gpu_grads(wl, res, plans, e)
     ogf, ogrg = oracle.batch_adjoint(wl.frame, wl.avail, wl.blocks, wl.plans, ora.path, e)
-    assert _rel_l2(gf, ogf) <= tol, _rel_l2(gf, ogf)
-    assert np.all(gf[wl.avail == 0] == 0)
-    for p in range(len(wl.plans)):
-        assert grg[p, 0] == pytest.approx(ogrg[p, 0], rel=tol_rho), (grg, ogrg)
-        assert grg[p, 1] == pytest.approx(ogrg[p, 1], rel=tol), (grg, ogrg)
+    for split in (True, False):
+        gf, grg = _gpu_grads(wl, res, plans, e, split)
+        assert _rel_l2(gf, ogf) <= tol, (split, _rel_l2(gf, ogf))
+        assert np.all(gf[wl.avail == 0] == 0)
+        for p in range(len(wl.plans)):
+            assert grg[p, 0] == pytest.approx(ogrg[p, 0], rel=tol_rho), (split, grg, ogrg)
+            assert grg[p, 1] == pytest.approx(ogrg[p, 1], rel=tol), (split, grg, ogrg)
     return res, plans, gf, grg, ogf, ogrg
 
 

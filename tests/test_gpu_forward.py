@@ -134,10 +134,11 @@ def test_longer_then_shorter_then_longer_iteration_counts():
         frame = torch.from_numpy(wl.frame).cuda()
         avail = torch.from_numpy(wl.avail).cuda()
         blocks = torch.from_numpy(wl.blocks).cuda()
-        gf = torch.zeros_like(frame)
-        binding.fofse_backward([p.handle for p in plans], blocks, frame, avail, res.trace, res.w0,
-                               torch.ones_like(res.blocks), grad_frame=gf)
-        binding.fofse_check()
+        for ws in (None, api.workspace(plans, len(wl.blocks), frame.device)):
+            gf = torch.zeros_like(frame)
+            binding.fofse_backward([p.handle for p in plans], blocks, frame, avail, res.trace,
+                                   res.w0, torch.ones_like(res.blocks), grad_frame=gf, workspace=ws)
+            binding.fofse_check()
         assert (res.status.cpu().numpy() == 0).all()
 
 
