@@ -53,14 +53,16 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const PlanDev& P = args.plan;
   const int iters = P.iters;
+  // split form: no synthesis table and no copy of c_i (the sample kernel
+  // has them), so that six blocks fit on an SM
   float* Z = reinterpret_cast<float*>(smem);  // FFT buffer, then W
   float2* syn = reinterpret_cast<float2*>(Z + T * T2);  // (cos, sin)(2 pi p / T)
-  Cx* tw = reinterpret_cast<Cx*>(syn + T);
-  int* tu = reinterpret_cast<int*>(tw + T / 2);         // u1 << 16 | u2
+  int* tu = reinterpret_cast<int*>(syn + (SPLIT ? 0 : T));  // u1 << 16 | u2
   float2* tc = reinterpret_cast<float2*>(tu + ((iters + 1) & ~1));  // c_i
-  float2* tg = tc + iters;                              // cbar_i
+  float2* tg = tc + (SPLIT ? 0 : iters);                // cbar_i
   float2* ta = tg + iters;                              // abar_i
-  double* red = reinterpret_cast<double*>(ta + iters);  // 4 NW
+  double* red = reinterpret_cast<double*>(ta + iters);  // 4 NW (NW when split)
+  const Cx* tw = reinterpret_cast<const Cx*>(P.tab.tw_f32);  // read through L1
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int blk = blockIdx.x;
@@ -76,10 +78,10 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
   for (int i = tid; i < iters; i += NT) {
     const fofse_trace_entry e = args.trace[(size_t)blk * args.trace_stride + i];
     tu[i] = ((int)(uint16_t)e.u1 << 16) | (int)(uint16_t)e.u2;
-    tc[i] = make_float2(e.dc_re, e.dc_im);
+    if (!SPLIT) tc[i] = make_float2(e.dc_re, e.dc_im);
   }
-  for (int e = tid; e < T; e += NT) syn[e] = P.tab.syn_f32[e];
-  for (int e = tid; e < T / 2; e += NT) tw[e] = {P.tab.tw_f32[e].x, P.tab.tw_f32[e].y};
+  if (!SPLIT)
+    for (int e = tid; e < T; e += NT) syn[e] = P.tab.syn_f32[e];
   for (int e = tid; e < T * T; e += NT) {
     const int r = e >> LOGT, c = e & (T - 1);
     const int m = __brev(r) >> (32 - LOGT), n = __brev(c) >> (32 - LOGT);
@@ -203,9 +205,16 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
   for (int i = tid; i < iters; i += NT) {
     const int ui = tu[i];
     const bool si = !self_conj<T>(ui >> 16, ui & 0xffff);
-    const float2 cb = tg[i], ci = tc[i];
+    float2 ci;
+    if (SPLIT) {
+      const fofse_trace_entry e = args.trace[(size_t)blk * args.trace_stride + i];
+      ci = make_float2(e.dc_re, e.dc_im);
+    } else {
+      ci = tc[i];
+    }
+    const float2 cb = tg[i];
     dot_acc += cb.x * ci.x + (si ? cb.y * ci.y : 0.f);
-    tg[i] = si ? make_float2(2.f * ci.x, 2.f * ci.y) : ci;  // cbar no longer needed
+    if (!SPLIT) tg[i] = si ? make_float2(2.f * ci.x, 2.f * ci.y) : ci;  // cbar no longer needed
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dot_acc += __shfl_xor_sync(0xffffffffu, dot_acc, o);
@@ -349,11 +358,17 @@ __global__ void __launch_bounds__(NT) fofse_backward_samples_kernel(const __grid
       (reinterpret_cast<uintptr_t>(smem_raw) + 15) & ~uintptr_t(15));
   const PlanDev& P = args.plan;
   const int iters = P.iters;
-  float2* syn = reinterpret_cast<float2*>(smem);  // (cos, sin)(2 pi p / T)
-  float2* tab = syn + T;                           // abar_i
+  // phase packing: mn = m 2^(32-L) + n 2^SN, U = u1 + u2 2^TU with SN + TU =
+  // 32 - L puts (m u1 + n u2) mod T in the product's top L bits; the cross
+  // term n u1 2^SN < 2^(29-L) stays below them, so the product shifted right
+  // by 29 - L is the byte offset (phase x 8) of the table entry
+  constexpr int SN = 29 - 3 * LOGT, TU = 3 + 2 * LOGT;
+  static_assert(SN >= 0 && TU >= LOGT, "phase packing");
+  __shared__ __align__(16) float2 syn[T];  // (cos, sin)(2 pi p / T)
+  float2* tab = reinterpret_cast<float2*>(smem);   // abar_i
   float2* tcm = tab + iters;                       // (1 + s_i) c_i
-  unsigned* tU = reinterpret_cast<unsigned*>(tcm + iters);  // u1 + u2 2^16
-  double* red = reinterpret_cast<double*>(smem + ((sizeof(float2) * (T + 2 * iters) +
+  unsigned* tU = reinterpret_cast<unsigned*>(tcm + iters);  // u1 + u2 2^TU
+  double* red = reinterpret_cast<double*>(smem + ((sizeof(float2) * 2 * iters +
                                                     sizeof(unsigned) * iters + 15) & ~size_t(15)));
   __shared__ bool s_last;
 
@@ -372,7 +387,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_samples_kernel(const __grid
     const int u1 = (uint16_t)e.u1, u2 = (uint16_t)e.u2;
     const float mult = self_conj<T>(u1, u2) ? 1.f : 2.f;
     tcm[i] = make_float2(mult * e.dc_re, mult * e.dc_im);
-    tU[i] = (unsigned)u1 | ((unsigned)u2 << 16);
+    tU[i] = (unsigned)u1 | ((unsigned)u2 << TU);
     tab[i] = args.abar[(size_t)blk * args.trace_stride + i];
   }
   __syncthreads();
@@ -380,7 +395,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_samples_kernel(const __grid
   const int npos = support_positions(P.support, Ls, b, br);
   const float c0 = br + (b - 1) * 0.5f;
   const float w0bar = args.w0bar[blk];
-  double s_wwd = 0.0, s_ww = 0.0, s_wd = 0.0, s_w = 0.0;
+  float p_wwd = 0.f, p_ww = 0.f, p_wd = 0.f, p_w = 0.f;  // this thread's samples
   for (int base = chunk * NT * S; base < npos; base += chunks * NT * S) {
     float r[S], xb[S], wb[S];
     unsigned mn[S];
@@ -399,7 +414,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_samples_kernel(const __grid
           const size_t fi = (size_t)fy * args.pitch + fx;
           if (args.avail[fi]) r[j] = args.frame[fi];
         }
-        mn[j] = ((unsigned)m << (32 - LOGT)) | ((unsigned)n << (16 - LOGT));
+        mn[j] = ((unsigned)m << (32 - LOGT)) | ((unsigned)n << SN);
       }
     }
     for (int i = 0; i < iters; ++i) {
@@ -407,7 +422,8 @@ __global__ void __launch_bounds__(NT) fofse_backward_samples_kernel(const __grid
       const float2 ab = tab[i], cm = tcm[i];
 #pragma unroll
       for (int j = 0; j < S; ++j) {
-        const float2 cs = syn[(mn[j] * U) >> (32 - LOGT)];
+        const float2 cs = *reinterpret_cast<const float2*>(
+            reinterpret_cast<const char*>(syn) + ((mn[j] * U) >> (29 - LOGT)));
         const float q = __fmaf_rn(ab.x, cs.x, -ab.y * cs.y);  // Re(abar_i phi_{u_i})
         xb[j] += q;
         wb[j] = __fmaf_rn(r[j], q, wb[j]);
@@ -428,15 +444,17 @@ __global__ void __launch_bounds__(NT) fofse_backward_samples_kernel(const __grid
       if (args.grad_frame) atomicAdd(&args.grad_frame[fi], w * xb[j]);
       const float wbar = wb[j] + w0bar;
       const float dm = m - c0, dn = n - c0;
-      const double d = (double)sqrtf(dm * dm + dn * dn);
-      const double ww = (double)wbar * (double)w;
-      s_wwd += ww * d;
-      s_ww += ww;
-      s_wd += (double)w * d;
-      s_w += (double)w;
+      const float d = sqrtf(dm * dm + dn * dn);
+      const float ww = wbar * w;
+      p_wwd = __fmaf_rn(ww, d, p_wwd);
+      p_ww += ww;
+      p_wd = __fmaf_rn(w, d, p_wd);
+      p_w += w;
     }
   }
   if (!args.grad_rho_gamma) return;
+  // a few samples per thread in FP32, the sums over threads and CTAs in FP64
+  double s_wwd = p_wwd, s_ww = p_ww, s_wd = p_wd, s_w = p_w;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     s_wwd += __shfl_xor_sync(0xffffffffu, s_wwd, o);
@@ -470,10 +488,10 @@ __global__ void __launch_bounds__(NT) fofse_backward_samples_kernel(const __grid
   }
 }
 
-template <int T, int NT> size_t bwd_smem(int iters) {
-  size_t off = 128 + sizeof(float) * T * 2 * T + sizeof(float2) * T + sizeof(Cx) * (T / 2);
-  off += sizeof(int) * ((iters + 1) & ~1) + 3 * sizeof(float2) * iters + 4 * sizeof(double) * (NT / 32);
-  return off;
+template <int T, int NT> size_t bwd_smem(int iters, bool split) {
+  size_t off = 128 + sizeof(float) * T * 2 * T + (split ? 0 : sizeof(float2) * T);
+  off += sizeof(int) * ((iters + 1) & ~1) + (split ? 2 : 3) * sizeof(float2) * iters;
+  return off + (split ? 1 : 4) * sizeof(double) * (NT / 32);
 }
 
 // The shared-memory limit of a kernel is one attribute per device; it only
@@ -496,7 +514,7 @@ template <class K> cudaError_t raise_smem_limit(K kern, size_t sm) {
 }
 
 template <int T, int NT, int NTS, int S> cudaError_t launch_bwd(const BwdArgs& a, cudaStream_t s) {
-  const size_t sm = bwd_smem<T, NT>(a.plan.iters);
+  const size_t sm = bwd_smem<T, NT>(a.plan.iters, a.abar != nullptr);
   cudaError_t e;
   if (!a.abar) {  // one kernel per block
     auto kern = fofse_backward_kernel<T, NT, false>;
@@ -509,7 +527,7 @@ template <int T, int NT, int NTS, int S> cudaError_t launch_bwd(const BwdArgs& a
   solve<<<a.n_blocks, NT, sm, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int iters = a.plan.iters;
-  const size_t sms = ((sizeof(float2) * (T + 2 * iters) + sizeof(unsigned) * iters + 15) & ~size_t(15)) +
+  const size_t sms = ((sizeof(float2) * 2 * iters + sizeof(unsigned) * iters + 15) & ~size_t(15)) +
                      sizeof(double) * 4 * (NTS / 32) + 16;
   const int Ls = a.plan.Ls, b = a.plan.block, br = a.plan.border;
   const int npos = a.plan.support == FOFSE_SUPPORT_CAUSAL_L ? br * (br + b) + b * br : Ls * Ls - b * b;
@@ -525,8 +543,8 @@ template <int T, int NT, int NTS, int S> cudaError_t launch_bwd(const BwdArgs& a
 
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s) {
   if (a.plan.precision == FOFSE_FP64_VALIDATE) return cudaErrorNotSupported;
-  if (a.plan.T == 128) return launch_bwd<128, 512, 128, 8>(a, s);
-  if (a.plan.T == 64) return launch_bwd<64, 256, 128, 8>(a, s);
+  if (a.plan.T == 128) return launch_bwd<128, 512, 128, 4>(a, s);
+  if (a.plan.T == 64) return launch_bwd<64, 256, 128, 4>(a, s);
   if (a.plan.T == 32) return launch_bwd<32, 128, 64, 4>(a, s);
   return cudaErrorNotSupported;
 }
