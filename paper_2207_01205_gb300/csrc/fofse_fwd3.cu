@@ -280,172 +280,268 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
     const float W0f = W0c.re.h * (1.f + 1e-6f);
     const char* wb8 = reinterpret_cast<const char*>(Whi);
     float bnd = 0.f, prevabs = 0.f, csum = 0.f;
+    bool dc_run = true;   // every winner so far was the DC bin
+    float kA = 2.1f * kU, kB = 12.f * kU;  // bound increments (raised once after a refresh)
+    // The iteration loop runs in two stretches: the first ends at the first
+    // winner that is not the DC bin, where the working spectrum is refreshed
+    // from exact values (below, outside the hot loop), then the loop resumes.
+    // Only at fft_size 128 (400 iterations, where near-ties are frequent
+    // enough to repay it; at 32 and 64 the extra code costs more than it saves).
+    constexpr bool kRefresh = T >= 128;
+    int it = 0, wk1 = 0, wk2 = 0;
+    bool sc = false;
+    float p = 0.f, q = 0.f;
 #pragma unroll 1
-    for (int it = 0; it < iters; ++it) {
-      // ---- top-2 over the block (packed keys) ----
-      const unsigned wm1 = __reduce_max_sync(kFull, m1k);
-      const unsigned hold = __ballot_sync(kFull, m1k == wm1);
-      const int ldr = __ffs(hold) - 1;
-      const unsigned wm2 = __reduce_max_sync(kFull, lane == ldr ? m2k : m1k);
-      uint4* ts = t2s + (it & 1) * NW;
-      if (lane == 0) ts[warp] = make_uint4(wm1, wm2, (unsigned)(warp * 32 + ldr), 0u);
-      __syncthreads();
-      uint4 g = ts[0];
+    for (;;) {
+      bool refresh = false;
+#pragma unroll 1
+      for (; it < iters; ++it) {
+        // ---- top-2 over the block (packed keys) ----
+        const unsigned wm1 = __reduce_max_sync(kFull, m1k);
+        const unsigned hold = __ballot_sync(kFull, m1k == wm1);
+        const int ldr = __ffs(hold) - 1;
+        const unsigned wm2 = __reduce_max_sync(kFull, lane == ldr ? m2k : m1k);
+        uint4* ts = t2s + (it & 1) * NW;
+        if (lane == 0) ts[warp] = make_uint4(wm1, wm2, (unsigned)(warp * 32 + ldr), 0u);
+        __syncthreads();
+        uint4 g = ts[0];
 #pragma unroll
-      for (int w = 1; w < NW; ++w) {
-        const uint4 o = ts[w];
-        if (o.x > g.x) {
-          g.y = max(g.x, o.y);
-          g.x = o.x;
-          g.z = o.z;
-        } else {
-          g.y = max(g.y, o.x);
+        for (int w = 1; w < NW; ++w) {
+          const uint4 o = ts[w];
+          if (o.x > g.x) {
+            g.y = max(g.x, o.y);
+            g.x = o.x;
+            g.z = o.z;
+          } else {
+            g.y = max(g.y, o.x);
+          }
         }
-      }
-      // square roots from the hardware reciprocal square root (relative
-      // error a few ulp, inside the 16u / 256u margins): sM1 is a lower and
-      // sM1u an upper bound of the largest |R32|, sM2 an upper bound of the rest
-      const float m1 = __uint_as_float(g.x & ~63u), m2 = __uint_as_float(g.y & ~63u);
-      const bool n1 = m1 >= kTiny, n2 = m2 >= kTiny;
-      const float r1 = m1 * rsqrtf(n1 ? m1 : 1.f), r2 = m2 * rsqrtf(n2 ? m2 : 1.f);
-      const float sM1 = n1 ? r1 : 0.f, sM1u = n1 ? r1 * kUp : kTinySqrt;
-      const float sM2 = n2 ? r2 : kTinySqrt;
-      bnd += 2.1f * kU * sM1u + 12.f * kU * W0f * prevabs;
-      const bool certain = (sM1 * kDn - bnd * kUpB) > (sM2 * kUp + bnd * kUpB);
-      // fixed-point unit of the recurrence: every partial sum is below
-      // 2 W0 sum_j (|Re c_j| + |Im c_j|) <= 4 W0f csum
-      const int sh = fx_shift(4.f * W0f * csum);
-      const float scale = pow2f(sh), iscale = pow2f(-sh);
+        // square roots from the hardware reciprocal square root (relative
+        // error a few ulp, inside the 16u / 256u margins): sM1 is a lower and
+        // sM1u an upper bound of the largest |R32|, sM2 an upper bound of the rest
+        const float m1 = __uint_as_float(g.x & ~63u), m2 = __uint_as_float(g.y & ~63u);
+        const bool n1 = m1 >= kTiny, n2 = m2 >= kTiny;
+        const float r1 = m1 * rsqrtf(n1 ? m1 : 1.f), r2 = m2 * rsqrtf(n2 ? m2 : 1.f);
+        const float sM1 = n1 ? r1 : 0.f, sM1u = n1 ? r1 * kUp : kTinySqrt;
+        const float sM2 = n2 ? r2 : kTinySqrt;
+        bnd += kA * sM1u + kB * W0f * prevabs;
+        kA = 2.1f * kU;
+        kB = 12.f * kU;
+        const bool certain = (sM1 * kDn - bnd * kUpB) > (sM2 * kUp + bnd * kUpB);
+        // fixed-point unit of the recurrence: every partial sum is below
+        // 2 W0 sum_j (|Re c_j| + |Im c_j|) <= 4 W0f csum
+        const int sh = fx_shift(4.f * W0f * csum);
+        const float scale = pow2f(sh), iscale = pow2f(-sh);
 
-      int wk1, wk2;  // held bin of the winner
-      ffc Rt;
-      if (certain) {
-        const int wt = (int)g.z, li = (int)(g.x & 63u);
-        int wslot;
-        if (li < NB) {
-          const int2 kk = f3_bin<T, NT>(wt, li);
-          wk1 = kk.x;
-          wk2 = kk.y;
-          wslot = wt + li * NT;
+        ffc Rt;
+        if (certain) {
+          const int wt = (int)g.z, li = (int)(g.x & 63u);
+          int wslot;
+          if (li < NB) {
+            const int2 kk = f3_bin<T, NT>(wt, li);
+            wk1 = kk.x;
+            wk2 = kk.y;
+            wslot = wt + li * NT;
+          } else {
+            const int2 kk = f3_extra<T>(wt);
+            wk1 = kk.x;
+            wk2 = kk.y;
+            wslot = NSLOT + wt;
+          }
+          const float4 r0 = Rx[wslot];
+          long long sre = 0, sim = 0;
+          if (warp * 32 < it) {  // warp-uniform: this warp holds terms
+            recur_fixed<T>(Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
+            warp_sum64(sre, sim);
+          }
+          if (lane == 0) red[warp] = make_longlong2(sre, sim);
+          __syncthreads();
+          long long Sr = 0, Si = 0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const longlong2 v = red[w];
+            Sr += v.x;
+            Si += v.y;
+          }
+          Rt = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(Sr, iscale)), ff_sub(ff{r0.z, r0.w}, fx_to_ff(Si, iscale))};
         } else {
-          const int2 kk = f3_extra<T>(wt);
-          wk1 = kk.x;
-          wk2 = kk.y;
-          wslot = NSLOT + wt;
-        }
-        const float4 r0 = Rx[wslot];
-        long long sre = 0, sim = 0;
-        if (warp * 32 < it) {  // warp-uniform: this warp holds terms
-          recur_fixed<T>(Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
-          warp_sum64(sre, sim);
-        }
-        if (lane == 0) red[warp] = make_longlong2(sre, sim);
-        __syncthreads();
-        long long Sr = 0, Si = 0;
+          // ---- near-tie: exact values of every bin within the band ----
+          const float Lb = (sM1 * kDn - 2.f * bnd * kUpB) * kDn;
+          const float thr = Lb > 0.f ? Lb * Lb * kDn : -1.f;
+          int cnt = 0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const longlong2 v = red[w];
-          Sr += v.x;
-          Si += v.y;
-        }
-        Rt = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(Sr, iscale)), ff_sub(ff{r0.z, r0.w}, fx_to_ff(Si, iscale))};
-      } else {
-        // ---- near-tie: exact values of every bin within the band ----
-        const float Lb = (sM1 * kDn - 2.f * bnd * kUpB) * kDn;
-        const float thr = Lb > 0.f ? Lb * Lb * kDn : -1.f;
-        int cnt = 0;
+          for (int i = 0; i < NB; ++i) cnt += m32(R32[i]) >= thr ? 1 : 0;
+          if (tid < 2) cnt += m32(rex) >= thr ? 1 : 0;
+          int incl = cnt;
 #pragma unroll
-        for (int i = 0; i < NB; ++i) cnt += m32(R32[i]) >= thr ? 1 : 0;
-        if (tid < 2) cnt += m32(rex) >= thr ? 1 : 0;
-        int incl = cnt;
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+          }
+          if (lane == 31) wtot[warp] = incl;
+          __syncthreads();
+          int before = 0, total = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += v;
-        }
-        if (lane == 31) wtot[warp] = incl;
-        __syncthreads();
-        int before = 0, total = 0;
+          for (int w = 0; w < NW; ++w) {
+            const int v = wtot[w];
+            before += w < warp ? v : 0;
+            total += v;
+          }
+          const int rank0 = before + incl - cnt;
+          ffc wb = {{0.f, 0.f}, {0.f, 0.f}};
+          int wbc = 0x7fffffff, wbx = 0;
+          for (int pass = 0; pass < total; pass += LIST) {
+            int r = rank0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const int v = wtot[w];
-          before += w < warp ? v : 0;
-          total += v;
+            for (int i = 0; i < NB; ++i) {
+              if (m32(R32[i]) >= thr) {
+                if (r >= pass && r < pass + LIST) {
+                  const int2 kk = f3_bin<T, NT>(tid, i);
+                  list[r - pass] = make_int4(kk.x * T2 + kk.y, f3_code<T>(kk.x, kk.y), tid + i * NT, 0);
+                }
+                ++r;
+              }
+            }
+            if (tid < 2 && m32(rex) >= thr && r >= pass && r < pass + LIST) {
+              const int2 kk = f3_extra<T>(tid);
+              list[r - pass] = make_int4(kk.x * T2 + kk.y, f3_code<T>(kk.x, kk.y), NSLOT + tid, 0);
+            }
+            __syncthreads();
+            const int n = min(LIST, total - pass);
+            for (int c = warp; c < n; c += NW) {
+              const int4 e = list[c];
+              const float4 r0 = Rx[e.z];
+              long long sre = 0, sim = 0;
+              recur_fixed<T>(Zg, trY, trC, e.x, lane, it, 32, scale, sre, sim);
+              warp_sum64(sre, sim);
+              const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
+                             ff_sub(ff{r0.z, r0.w}, fx_to_ff(sim, iscale))};
+              if (wbc == 0x7fffffff || exact_better(v, e.y, wb, wbc)) {
+                wb = v;
+                wbc = e.y;
+                wbx = e.x;
+              }
+            }
+            __syncthreads();
+          }
+          if (lane == 0) {
+            wwv[warp] = make_float4(wb.re.h, wb.re.l, wb.im.h, wb.im.l);
+            wwc[warp] = make_int2(wbc, wbx);
+          }
+          __syncthreads();
+          int wcode = 0x7fffffff, wx = 0;
+          Rt = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const int2 cs = wwc[w];
+            if (cs.x == 0x7fffffff) continue;
+            const float4 v4 = wwv[w];
+            const ffc v = {{v4.x, v4.y}, {v4.z, v4.w}};
+            if (wcode == 0x7fffffff || exact_better(v, cs.x, Rt, wcode)) {
+              Rt = v;
+              wcode = cs.x;
+              wx = cs.y;
+            }
+          }
+          wk1 = wx >> (LOGT + 1);
+          wk2 = wx & (T2 - 1);
         }
-        const int rank0 = before + incl - cnt;
-        ffc wb = {{0.f, 0.f}, {0.f, 0.f}};
-        int wbc = 0x7fffffff, wbx = 0;
-        for (int pass = 0; pass < total; pass += LIST) {
-          int r = rank0;
+        // ---- exact coefficient (Eq. 5, Eq. 14) of the held winner ----
+        const bool mir = wk1 > T / 2;
+        const int u1 = mir ? ((T - wk1) & (T - 1)) : wk1;
+        const int u2 = mir ? ((T - wk2) & (T - 1)) : wk2;
+        sc = ((wk1 & (T / 2 - 1)) == 0) && ((wk2 & (T / 2 - 1)) == 0);
+        C c;
+        c.re = ff_mul(Rt.re, inv);
+        c.im = sc ? ff{0.f, 0.f} : ff_mul(Rt.im, inv);
+        if (tid == 0) {
+          trY[it] = (short)(u1 * T2 + u2);
+          trC[it] = mir ? make_float4(c.re.h, c.re.l, -c.im.h, -c.im.l)
+                        : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
+        }
+        p = c.re.h;
+        q = c.im.h;
+        if (kRefresh && dc_run && !(wk1 == 0 && wk2 == 0)) {
+          dc_run = false;
+          if (it > 0) {
+            refresh = true;
+            break;
+          }
+        }
+        // ---- FP32 update of the working spectrum + next top-2 keys ----
+        prevabs = fabsf(p) + fabsf(q);
+        csum += prevabs;
+        const int rm = ((rt - wk1) & (T - 1)) << LOGT, rp = ((rt + wk1) & (T - 1)) << LOGT;
+        const int bml = (rm | ((ct - wk2) & (T - 1))) << 3, bmh = (rm | ((chi - wk2) & (T - 1))) << 3;
+        const int bpl = (rp | ((ct + wk2) & (T - 1))) << 3, bph = (rp | ((chi + wk2) & (T - 1))) << 3;
+        const int bmi = rt > 0 ? bmh : bml, bpi = rt > 0 ? bph : bpl;
+        m1k = 0u;
+        m2k = 0u;
+        if (!sc) {
 #pragma unroll
           for (int i = 0; i < NB; ++i) {
-            if (m32(R32[i]) >= thr) {
-              if (r >= pass && r < pass + LIST) {
-                const int2 kk = f3_bin<T, NT>(tid, i);
-                list[r - pass] = make_int4(kk.x * T2 + kk.y, f3_code<T>(kk.x, kk.y), tid + i * NT, 0);
-              }
-              ++r;
-            }
+            const int bm = i < IB ? bml : (i == IB ? bmi : bmh);
+            const int bp = i < IB ? bpl : (i == IB ? bpi : bph);
+            const float2 Wm = *reinterpret_cast<const float2*>(wb8 + ((bm + i * STEP8) & MSK8));
+            const float2 Wp = *reinterpret_cast<const float2*>(wb8 + ((bp + i * STEP8) & MSK8));
+            const float a = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
+            R32[i].x = __fmaf_rn(-p, a, __fmaf_rn(q, bb, R32[i].x));
+            R32[i].y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, R32[i].y));
+            key_insert(m1k, m2k, m32(R32[i]), i);
           }
-          if (tid < 2 && m32(rex) >= thr && r >= pass && r < pass + LIST) {
-            const int2 kk = f3_extra<T>(tid);
-            list[r - pass] = make_int4(kk.x * T2 + kk.y, f3_code<T>(kk.x, kk.y), NSLOT + tid, 0);
-          }
-          __syncthreads();
-          const int n = min(LIST, total - pass);
-          for (int c = warp; c < n; c += NW) {
-            const int4 e = list[c];
-            const float4 r0 = Rx[e.z];
-            long long sre = 0, sim = 0;
-            recur_fixed<T>(Zg, trY, trC, e.x, lane, it, 32, scale, sre, sim);
-            warp_sum64(sre, sim);
-            const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
-                           ff_sub(ff{r0.z, r0.w}, fx_to_ff(sim, iscale))};
-            if (wbc == 0x7fffffff || exact_better(v, e.y, wb, wbc)) {
-              wb = v;
-              wbc = e.y;
-              wbx = e.x;
-            }
-          }
-          __syncthreads();
-        }
-        if (lane == 0) {
-          wwv[warp] = make_float4(wb.re.h, wb.re.l, wb.im.h, wb.im.l);
-          wwc[warp] = make_int2(wbc, wbx);
-        }
-        __syncthreads();
-        int wcode = 0x7fffffff, wx = 0;
-        Rt = {{0.f, 0.f}, {0.f, 0.f}};
+        } else {
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const int2 cs = wwc[w];
-          if (cs.x == 0x7fffffff) continue;
-          const float4 v4 = wwv[w];
-          const ffc v = {{v4.x, v4.y}, {v4.z, v4.w}};
-          if (wcode == 0x7fffffff || exact_better(v, cs.x, Rt, wcode)) {
-            Rt = v;
-            wcode = cs.x;
-            wx = cs.y;
+          for (int i = 0; i < NB; ++i) {
+            const int bm = i < IB ? bml : (i == IB ? bmi : bmh);
+            const float2 Wm = *reinterpret_cast<const float2*>(wb8 + ((bm + i * STEP8) & MSK8));
+            R32[i].x = __fmaf_rn(-p, Wm.x, R32[i].x);
+            R32[i].y = __fmaf_rn(-p, Wm.y, R32[i].y);
+            key_insert(m1k, m2k, m32(R32[i]), i);
           }
         }
-        wk1 = wx >> (LOGT + 1);
-        wk2 = wx & (T2 - 1);
+        if (tid < 2) {
+          const int2 kk = f3_extra<T>(tid);
+          const float2 Wm = Whi[(((kk.x - wk1) & (T - 1)) << LOGT) | ((kk.y - wk2) & (T - 1))];
+          float2 Wp = make_float2(0.f, 0.f);
+          if (!sc) Wp = Whi[(((kk.x + wk1) & (T - 1)) << LOGT) | ((kk.y + wk2) & (T - 1))];
+          const float a = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
+          rex.x = __fmaf_rn(-p, a, __fmaf_rn(q, bb, rex.x));
+          rex.y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, rex.y));
+          key_insert(m1k, m2k, m32(rex), NB);
+        }
       }
-      // ---- exact coefficient (Eq. 5, Eq. 14) of the held winner ----
-      const bool mir = wk1 > T / 2;
-      const int u1 = mir ? ((T - wk1) & (T - 1)) : wk1;
-      const int u2 = mir ? ((T - wk2) & (T - 1)) : wk2;
-      const bool sc = ((wk1 & (T / 2 - 1)) == 0) && ((wk2 & (T / 2 - 1)) == 0);
-      C c;
-      c.re = ff_mul(Rt.re, inv);
-      c.im = sc ? ff{0.f, 0.f} : ff_mul(Rt.im, inv);
-      if (tid == 0) {
-        trY[it] = (short)(u1 * T2 + u2);
-        trC[it] = mir ? make_float4(c.re.h, c.re.l, -c.im.h, -c.im.l)
-                      : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
+      if (!refresh) break;
+      // ---- refresh after the initial run of DC picks ----
+      // The first picks are usually the DC bin (u = 0, real c_j), with large
+      // coefficients whose FP32 rounding dominates the bound.  At the first
+      // other winner the working spectrum is rebuilt from the exact values,
+      // R~[k] = R0[k] - C W[k] with C = sum_{j<it} c_j, and the bound restarts:
+      // the rounding of R~ (u |R~| <= u (max|R32| + 2 |c| W[0]) after this
+      // iteration's update) is added with the next increment.
+      {
+        ff Cs = {0.f, 0.f};
+        for (int j = 0; j < it; ++j) {
+          const float4 c4 = trC[j];
+          Cs = ff_add(Cs, ff{c4.x, c4.y});
+        }
+#pragma unroll
+        for (int i = 0; i <= NB; ++i) {
+          if (i == NB && tid >= 2) break;
+          const int2 kk = i < NB ? f3_bin<T, NT>(tid, i) : f3_extra<T>(tid);
+          const int x = kk.x * T2 + kk.y;
+          const float4 r0 = Rx[i < NB ? tid + i * NT : NSLOT + tid];
+          const float2 wh = Zg[x], wl = Zg[x + T];
+          const float2 r = make_float2(ff_sub(ff{r0.x, r0.y}, ff_mul(Cs, ff{wh.x, wl.x})).h,
+                                       ff_sub(ff{r0.z, r0.w}, ff_mul(Cs, ff{wh.y, wl.y})).h);
+          if (i < NB) R32[i] = r;
+          else rex = r;
+        }
+        bnd = 0.f;
+        kA = (2.1f + 1.1f) * kU;
+        kB = (12.f + 2.1f) * kU;
       }
+      // this iteration's update, then back to the loop
       // ---- FP32 update of the working spectrum + next top-2 keys ----
-      const float p = c.re.h, q = c.im.h;
       prevabs = fabsf(p) + fabsf(q);
       csum += prevabs;
       const int rm = ((rt - wk1) & (T - 1)) << LOGT, rp = ((rt + wk1) & (T - 1)) << LOGT;
@@ -486,6 +582,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
         rex.y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, rex.y));
         key_insert(m1k, m2k, m32(rex), NB);
       }
+      ++it;
     }
   }
   __syncthreads();
