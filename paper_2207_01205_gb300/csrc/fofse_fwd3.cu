@@ -108,6 +108,14 @@ __device__ __forceinline__ void warp_sum64(long long& a, long long& b) {
     b += __shfl_xor_sync(kFull, b, o);
   }
 }
+// The same sum by redux.sync on three 21-bit limbs (|v| < 2^62: the limb sums
+// of 32 lanes fit in 32 bits); shorter latency than five shuffle rounds.
+__device__ __forceinline__ long long redux_sum64(long long v) {
+  const int l0 = (int)(v & 0x1FFFFF), l1 = (int)((v >> 21) & 0x1FFFFF), l2 = (int)(v >> 42);
+  const long long s0 = __reduce_add_sync(kFull, l0), s1 = __reduce_add_sync(kFull, l1);
+  const long long s2 = __reduce_add_sync(kFull, l2);
+  return s2 * 4398046511104LL + s1 * 2097152LL + s0;  // 2^42, 2^21
+}
 
 // sum over j in {j0, j0 + stride, ...} < j1 of c_j W[k - u_j] + s_j conj(c_j) W[k + u_j]
 // (float-float terms, exact W from the global table) in fixed point with unit 1/scale
@@ -349,19 +357,35 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
             wslot = NSLOT + wt;
           }
           const float4 r0 = Rx[wslot];
+          // one term per thread and iteration at most; up to four warps the
+          // partial sums go through shuffles and a short block sum, beyond
+          // that through redux.sync (warp and block level)
           long long sre = 0, sim = 0;
-          if (warp * 32 < it) {  // warp-uniform: this warp holds terms
-            recur_fixed<T>(Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
-            warp_sum64(sre, sim);
-          }
-          if (lane == 0) red[warp] = make_longlong2(sre, sim);
-          __syncthreads();
           long long Sr = 0, Si = 0;
+          if constexpr (NW <= 4) {
+            if (warp * 32 < it) {  // warp-uniform: this warp holds terms
+              recur_fixed<T>(Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
+              warp_sum64(sre, sim);
+            }
+            if (lane == 0) red[warp] = make_longlong2(sre, sim);
+            __syncthreads();
 #pragma unroll
-          for (int w = 0; w < NW; ++w) {
-            const longlong2 v = red[w];
-            Sr += v.x;
-            Si += v.y;
+            for (int w = 0; w < NW; ++w) {
+              const longlong2 v = red[w];
+              Sr += v.x;
+              Si += v.y;
+            }
+          } else {
+            if (warp * 32 < it) {
+              recur_fixed<T>(Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
+              sre = redux_sum64(sre);
+              sim = redux_sum64(sim);
+            }
+            if (lane == 0) red[warp] = make_longlong2(sre, sim);
+            __syncthreads();
+            const longlong2 v = lane < NW ? red[lane] : make_longlong2(0, 0);
+            Sr = redux_sum64(v.x);
+            Si = redux_sum64(v.y);
           }
           Rt = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(Sr, iscale)), ff_sub(ff{r0.z, r0.w}, fx_to_ff(Si, iscale))};
         } else {
@@ -413,7 +437,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               const float4 r0 = Rx[e.z];
               long long sre = 0, sim = 0;
               recur_fixed<T>(Zg, trY, trC, e.x, lane, it, 32, scale, sre, sim);
-              warp_sum64(sre, sim);
+              sre = redux_sum64(sre);
+              sim = redux_sum64(sim);
               const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
                              ff_sub(ff{r0.z, r0.w}, fx_to_ff(sim, iscale))};
               if (wbc == 0x7fffffff || exact_better(v, e.y, wb, wbc)) {
