@@ -19,7 +19,7 @@
 //     (T/2, T/2) are held by threads 0 and 1 outside the grid.
 //   * W's FP32 plane in shared memory with row stride T (static shared memory
 //     for T <= 64, so that its address folds into the load instruction).
-//   * top-2 tracking with packed keys: the bits of |R32|^2 with the low six
+//   * top-2 tracking with packed keys: the bits of |R32|^2 with the low seven
 //     replaced by the bin's local index, three unsigned min/max per bin, the
 //     warp's top-2 by redux.sync.
 //   * the recurrence sum accumulated in 64-bit fixed point: each float-float
@@ -48,7 +48,7 @@ template <int T, int NT> struct F3 {
   static constexpr int IB = NB / 2;      // the bin whose row is T/2 + r_t
   static constexpr int LIST = 32;        // near-tie candidates per pass
   static constexpr bool STATIC_W = T <= 64;
-  static_assert(NSLOT % NT == 0 && NB >= 2 && NB <= 32 && NW >= 1 && (NW & (NW - 1)) == 0,
+  static_assert(NSLOT % NT == 0 && NB >= 2 && NB <= 64 && NW >= 1 && (NW & (NW - 1)) == 0,
                 "slot grid");
   // dynamic shared memory, bytes from a 128-aligned base
   static constexpr size_t w_bytes = STATIC_W ? 0 : sizeof(float2) * (size_t)T * T;
@@ -84,8 +84,12 @@ template <int T> __device__ __forceinline__ int f3_code(int k1, int k2) {
   return canon * 2 + (mir ? 1 : 0);
 }
 
+// low bits of a key that hold the bin's local index (up to 64 bins per thread
+// plus one extra); truncating them lowers |R32|^2 by less than 2^-16 relative
+constexpr unsigned kKeyMask = 127u;
+
 __device__ __forceinline__ void key_insert(unsigned& k1, unsigned& k2, float m, int i) {
-  const unsigned key = (__float_as_uint(m) & ~63u) | (unsigned)i;  // m >= 0: bits are monotone
+  const unsigned key = (__float_as_uint(m) & ~kKeyMask) | (unsigned)i;  // m >= 0: monotone bits
   k2 = max(k2, min(k1, key));
   k1 = max(k1, key);
 }
@@ -327,7 +331,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
         // square roots from the hardware reciprocal square root (relative
         // error a few ulp, inside the 16u / 256u margins): sM1 is a lower and
         // sM1u an upper bound of the largest |R32|, sM2 an upper bound of the rest
-        const float m1 = __uint_as_float(g.x & ~63u), m2 = __uint_as_float(g.y & ~63u);
+        const float m1 = __uint_as_float(g.x & ~kKeyMask), m2 = __uint_as_float(g.y & ~kKeyMask);
         const bool n1 = m1 >= kTiny, n2 = m2 >= kTiny;
         const float r1 = m1 * rsqrtf(n1 ? m1 : 1.f), r2 = m2 * rsqrtf(n2 ? m2 : 1.f);
         const float sM1 = n1 ? r1 : 0.f, sM1u = n1 ? r1 * kUp : kTinySqrt;
@@ -343,7 +347,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
 
         ffc Rt;
         if (certain) {
-          const int wt = (int)g.z, li = (int)(g.x & 63u);
+          const int wt = (int)g.z, li = (int)(g.x & kKeyMask);
           int wslot;
           if (li < NB) {
             const int2 kk = f3_bin<T, NT>(wt, li);
@@ -739,25 +743,29 @@ template <int T, int NT, int MINB> struct VariantF3 {
 
 // Launch shapes (threads per block, minimum resident blocks per SM that the
 // register allocation is held to); variant 0 is the default, the autotuner
-// may pick another per plan.
+// may pick another per plan.  Fewer warps per block means less of the
+// per-iteration work (top-2 merge, certainty test, coefficient) repeated per
+// warp; the limit is the register file (2 registers per held bin): measured
+// on the GB300, one warp per block is fastest at fft_size 32, two at 64 and
+// eight at 128.
 template <int T> struct PickF3;
 template <> struct PickF3<32> {
-  using V0 = VariantF3<32, 64, 12>;
-  using V1 = VariantF3<32, 128, 6>;
-  using V2 = VariantF3<32, 64, 16>;
+  using V0 = VariantF3<32, 32, 16>;
+  using V1 = VariantF3<32, 64, 12>;
+  using V2 = VariantF3<32, 128, 6>;
   static constexpr int NV = 3;
 };
 template <> struct PickF3<64> {
-  using V0 = VariantF3<64, 128, 6>;
-  using V1 = VariantF3<64, 128, 5>;
-  using V2 = VariantF3<64, 128, 4>;
+  using V0 = VariantF3<64, 64, 6>;
+  using V1 = VariantF3<64, 128, 6>;
+  using V2 = VariantF3<64, 32, 6>;
   static constexpr int NV = 3;
 };
 template <> struct PickF3<128> {
-  using V0 = VariantF3<128, 512, 1>;
-  using V1 = VariantF3<128, 1024, 1>;
-  using V2 = VariantF3<128, 512, 1>;
-  static constexpr int NV = 2;
+  using V0 = VariantF3<128, 256, 1>;
+  using V1 = VariantF3<128, 512, 1>;
+  using V2 = VariantF3<128, 1024, 1>;
+  static constexpr int NV = 3;
 };
 
 template <int T>
