@@ -100,10 +100,28 @@ __device__ __forceinline__ int fx_shift(float bound) {
   return min(188 - eb, 126);
 }
 __device__ __forceinline__ float pow2f(int s) { return __int_as_float((s + 127) << 23); }
+// Conversions between FP32 and the 64-bit fixed-point sums use 32-bit
+// conversion instructions only (the 64-bit ones go through the FP64 pipe,
+// two lanes per clock on this GPU).
+// Nearest integer to v, |v| < 2^62.  For |v| >= 2^30, v is a multiple of 2^7,
+// so v = h 2^31 + r with h = floor(v / 2^31) and r = v - h 2^31 in [0, 2^31)
+// both exact in FP32.
+__device__ __forceinline__ long long fx_round(float v) {
+  const bool big = fabsf(v) >= 1073741824.f;                   // 2^30
+  const float h = floorf(v * 4.656612873077393e-10f);          // v / 2^31
+  const float r = __fmaf_rn(-h, 2147483648.f, v);
+  const long long vb = ((long long)__float2int_rn(h) << 31) + (long long)__float2uint_rn(r);
+  const long long vs = (long long)__float2int_rn(v);
+  return big ? vb : vs;
+}
+// Float-float value of v / scale (|v| < 2^62): v split into a signed 20-bit
+// limb and two 21-bit limbs, each exact in FP32, summed in float-float.
 __device__ __forceinline__ ff fx_to_ff(long long v, float inv_scale) {
-  const float h = __ll2float_rn(v);
-  const float l = __ll2float_rn(v - __float2ll_rn(h));
-  return {h * inv_scale, l * inv_scale};
+  const int a = (int)(v >> 42);
+  const int b = (int)((v >> 21) & 0x1FFFFF), c = (int)(v & 0x1FFFFF);
+  const ff t = ff_add(ff_two_sum(__int2float_rn(a) * 4398046511104.f, __int2float_rn(b) * 2097152.f),
+                      ff{__int2float_rn(c), 0.f});
+  return {t.h * inv_scale, t.l * inv_scale};
 }
 __device__ __forceinline__ void warp_sum64(long long& a, long long& b) {
 #pragma unroll
@@ -146,8 +164,8 @@ __device__ __forceinline__ void recur_fixed(const float2* Zg, const short* ty, c
       tre = ff_mul(c.re, Wm.re);
       tim = ff_mul(c.re, Wm.im);
     }
-    sre += __float2ll_rn(tre.h * scale) + __float2ll_rn(tre.l * scale);
-    sim += __float2ll_rn(tim.h * scale) + __float2ll_rn(tim.l * scale);
+    sre += fx_round(tre.h * scale) + fx_round(tre.l * scale);
+    sim += fx_round(tim.h * scale) + fx_round(tim.l * scale);
   }
 }
 
