@@ -67,16 +67,19 @@ enum { FOFSE_SUPPORT_FULL = 0,      /* all of L outside B (concealment)         
                                         samples left of B in B's rows (prediction)      */
 /* arithmetic of the kernels */
 enum { FOFSE_FP32 = 0,           /* the product: exact selection path and coefficients
-                                    with FP32 instructions (FOFSE_FP32_FILTERED when the
-                                    workspace is given, else FOFSE_FP32_FULLFF)          */
+                                    with FP32 instructions.  With the workspace: FP32
+                                    working spectrum with a rigorous error bound, near
+                                    ties and every coefficient evaluated exactly (the
+                                    register-blocked kernel); without it, as
+                                    FOFSE_FP32_FULLFF                                   */
        FOFSE_FP64_VALIDATE = 1,  /* IEEE double; slow on GB300, for validation           */
        FOFSE_FP32_PLAIN = 2,     /* plain FP32; diverges from the exact selection path at
                                     near-ties, kept for comparison                       */
        FOFSE_FP32_FULLFF = 3,    /* every bin updated in float-float (pairs of FP32)      */
-       FOFSE_FP32_FILTERED = 4 };/* FP32 working spectrum with a rigorous error bound;
-                                    the argmax near ties and every coefficient evaluated
-                                    exactly in float-float.  Needs the workspace's
-                                    scratch; without it runs as FOFSE_FP32_FULLFF      */
+       FOFSE_FP32_FILTERED = 4 };/* the same decisions as FOFSE_FP32 by the earlier
+                                    filtered kernel layout (kept for comparison).
+                                    Needs the workspace's scratch; without it runs as
+                                    FOFSE_FP32_FULLFF                                   */
 /* per-block status written to d_block_status */
 enum { FOFSE_BLK_OK = 0, FOFSE_BLK_NO_SUPPORT = 1, FOFSE_BLK_NONFINITE = 2 };
 
