@@ -87,6 +87,12 @@ def reduce_max(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def job_value(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling, every rank runs its own batch)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -267,7 +273,7 @@ def run_other_workload(args, rank, world, local):
     fwd_ms = reduce_max(sum(e[0].elapsed_time(e[1]) for e in ev), world, dev) / args.steps
     fb_ms = reduce_max(sum(e[0].elapsed_time(e[2]) for e in ev), world, dev) / args.steps
     if rank == 0:
-        line = {"metric": f"blocks/s ({args.workload})", "value": world * n / (fwd_ms * 1e-3),
+        line = {"metric": f"blocks/s ({args.workload})", "value": job_value(n, world, fwd_ms),
                 "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": fwd_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -376,7 +382,7 @@ def main():
     local_ms = sum(step_ms)
     tot_ms = reduce_max(local_ms, world, dev)
     ms_per_step = tot_ms / args.steps
-    value = world * n * args.steps / (tot_ms * 1e-3)
+    value = job_value(n * args.steps, world, tot_ms)
     clocks = clk.summary()
 
     # ---- forward + backward (squared error over B against the ground truth) ----
@@ -446,7 +452,7 @@ def main():
     e2e_ms = reduce_max(e0.elapsed_time(e1), world, dev)
     h2d = h_frame.numel() * 4 + h_avail.numel() + h_blocks.numel() * 4
     d2h = h_out.numel() * 4
-    e2e = {"value": world * n * args.steps / (e2e_ms * 1e-3), "unit": "blocks/s",
+    e2e = {"value": job_value(n * args.steps, world, e2e_ms), "unit": "blocks/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- one-block-per-launch form on the same GPU ----
