@@ -237,3 +237,45 @@ def test_uneven_batch_4k_sampled():
             same += 1
             assert np.abs(g_blocks[j, :p.block, :p.block] - ora.blocks[j, :p.block, :p.block]).max() <= 1e-3
     assert same == len(pick)
+
+
+def test_empty_batch_is_a_no_op():
+    import torch
+    from paper_2207_01205_gb300 import api, binding
+    wl = synth.small_frame(3, plan=synth.PlanSpec(8, 8, 32, 0.8, 0.5, 20), n_lost=2)
+    plans = [api.Plan.from_spec(p, "fp32") for p in wl.plans]
+    frame = torch.from_numpy(wl.frame).cuda()
+    avail = torch.from_numpy(wl.avail).cuda()
+    blocks = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
+    out = torch.full((1, 8, 8), 7.0, device="cuda")
+    binding.fofse_extrapolate_batch([p.handle for p in plans], blocks, frame, avail,
+                                    out_blocks=out, workspace=api.workspace(plans, 0, frame.device))
+    binding.fofse_check()
+    assert float(out.min()) == 7.0 and float(out.max()) == 7.0
+
+
+@pytest.mark.parametrize("spec", [synth.PlanSpec(16, 8, 32, 0.8, 0.5, 120),    # L = 32 x 32 = T
+                                  synth.PlanSpec(32, 16, 64, 0.8, 0.5, 250),   # L = 64 x 64 = T
+                                  synth.PlanSpec(64, 32, 128, 0.8, 0.5, 300)]) # L = 128 x 128 = T
+def test_largest_area_per_fft_size(spec):
+    """The support area fills the whole FFT grid (no zero padding), corner
+    blocks included."""
+    wl = synth.small_frame(31, height=4 * spec.block, width=5 * spec.block, plan=spec, n_lost=3)
+    ora = _oracle(wl)
+    for prec in ("fp32", "fp32_fullff"):
+        res, _ = run_gpu(wl, prec)
+        c = compare(wl, res, ora)
+        assert c["status_equal"] and c["same"] == c["n"], (prec, c)
+        assert c["max_err"] <= 1e-3, (prec, c)
+
+
+def test_long_run_of_iterations():
+    """1500 iterations (the error bound grows with every iteration, so late
+    near-ties go to the exact path more often); paths stay identical."""
+    spec = synth.PlanSpec(16, 16, 64, 0.8, 0.5, 1500)
+    wl = synth.small_frame(41, plan=spec, n_lost=3)
+    ora = _oracle(wl)
+    res, _ = run_gpu(wl, "fp32")
+    c = compare(wl, res, ora)
+    assert c["status_equal"] and c["same"] == c["n"], c
+    assert c["max_err"] <= 1e-3, c
