@@ -180,6 +180,10 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   using G = F3<T, NT>;
   constexpr int T2 = G::T2, LOGT = G::LOGT, NSLOT = G::NSLOT, NB = G::NB, NW = G::NW;
   constexpr int IB = G::IB, LIST = G::LIST;
+  // with 32 or more bins per thread the top-2 keys run in two independent
+  // chains (even and odd bins), merged after the update loop: a shorter
+  // dependency chain (measured faster there, slower with 16 bins)
+  constexpr bool kTwoChains = NB >= 32;
   constexpr int STEP8 = G::RS * T * 8, MSK8 = T * T * 8 - 8;
   constexpr float kU = 5.9604644775390625e-08f;  // 2^-24
   constexpr float kDn = 1.f - 16.f * kU, kUp = 1.f + 256.f * kU, kUpB = 1.f + 16.f * kU;
@@ -522,8 +526,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
         const int bml = (rm | ((ct - wk2) & (T - 1))) << 3, bmh = (rm | ((chi - wk2) & (T - 1))) << 3;
         const int bpl = (rp | ((ct + wk2) & (T - 1))) << 3, bph = (rp | ((chi + wk2) & (T - 1))) << 3;
         const int bmi = rt > 0 ? bmh : bml, bpi = rt > 0 ? bph : bpl;
-        m1k = 0u;
-        m2k = 0u;
+        unsigned k1a = 0u, k2a = 0u, k1b = 0u, k2b = 0u;  // two key chains (even / odd bins)
         if (!sc) {
 #pragma unroll
           for (int i = 0; i < NB; ++i) {
@@ -534,7 +537,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
             const float a = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
             R32[i].x = __fmaf_rn(-p, a, __fmaf_rn(q, bb, R32[i].x));
             R32[i].y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, R32[i].y));
-            key_insert(m1k, m2k, m32(R32[i]), i);
+            if (kTwoChains && (i & 1)) key_insert(k1b, k2b, m32(R32[i]), i);
+            else key_insert(k1a, k2a, m32(R32[i]), i);
           }
         } else {
 #pragma unroll
@@ -543,7 +547,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
             const float2 Wm = *reinterpret_cast<const float2*>(wb8 + ((bm + i * STEP8) & MSK8));
             R32[i].x = __fmaf_rn(-p, Wm.x, R32[i].x);
             R32[i].y = __fmaf_rn(-p, Wm.y, R32[i].y);
-            key_insert(m1k, m2k, m32(R32[i]), i);
+            if (kTwoChains && (i & 1)) key_insert(k1b, k2b, m32(R32[i]), i);
+            else key_insert(k1a, k2a, m32(R32[i]), i);
           }
         }
         if (tid < 2) {
@@ -554,8 +559,10 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           const float a = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
           rex.x = __fmaf_rn(-p, a, __fmaf_rn(q, bb, rex.x));
           rex.y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, rex.y));
-          key_insert(m1k, m2k, m32(rex), NB);
+          key_insert(k1a, k2a, m32(rex), NB);
         }
+        m1k = max(k1a, k1b);
+        m2k = max(max(k2a, k2b), min(k1a, k1b));
       }
       if (!refresh) break;
       // ---- refresh after the initial run of DC picks ----
@@ -595,8 +602,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
       const int bml = (rm | ((ct - wk2) & (T - 1))) << 3, bmh = (rm | ((chi - wk2) & (T - 1))) << 3;
       const int bpl = (rp | ((ct + wk2) & (T - 1))) << 3, bph = (rp | ((chi + wk2) & (T - 1))) << 3;
       const int bmi = rt > 0 ? bmh : bml, bpi = rt > 0 ? bph : bpl;
-      m1k = 0u;
-      m2k = 0u;
+      unsigned k1a = 0u, k2a = 0u, k1b = 0u, k2b = 0u;  // two key chains (even / odd bins)
       if (!sc) {
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
@@ -607,7 +613,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           const float a = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
           R32[i].x = __fmaf_rn(-p, a, __fmaf_rn(q, bb, R32[i].x));
           R32[i].y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, R32[i].y));
-          key_insert(m1k, m2k, m32(R32[i]), i);
+          if (kTwoChains && (i & 1)) key_insert(k1b, k2b, m32(R32[i]), i);
+            else key_insert(k1a, k2a, m32(R32[i]), i);
         }
       } else {
 #pragma unroll
@@ -616,7 +623,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           const float2 Wm = *reinterpret_cast<const float2*>(wb8 + ((bm + i * STEP8) & MSK8));
           R32[i].x = __fmaf_rn(-p, Wm.x, R32[i].x);
           R32[i].y = __fmaf_rn(-p, Wm.y, R32[i].y);
-          key_insert(m1k, m2k, m32(R32[i]), i);
+          if (kTwoChains && (i & 1)) key_insert(k1b, k2b, m32(R32[i]), i);
+            else key_insert(k1a, k2a, m32(R32[i]), i);
         }
       }
       if (tid < 2) {
@@ -627,8 +635,10 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
         const float a = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
         rex.x = __fmaf_rn(-p, a, __fmaf_rn(q, bb, rex.x));
         rex.y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, rex.y));
-        key_insert(m1k, m2k, m32(rex), NB);
+        key_insert(k1a, k2a, m32(rex), NB);
       }
+      m1k = max(k1a, k1b);
+      m2k = max(max(k2a, k2b), min(k1a, k1b));
       ++it;
     }
   }
