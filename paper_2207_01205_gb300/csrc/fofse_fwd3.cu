@@ -169,6 +169,82 @@ __device__ __forceinline__ void recur_fixed(const float2* Zg, const short* ty, c
   }
 }
 
+// 2-D FFT of the packed block, which sits in the per-CTA global scratch
+// (two-plane float-float layout, input at bit-reversed positions, storage
+// rows brev(m), m < Ls, nonzero), through shared memory: the row pass in
+// chunks of T/2 storage rows, the column pass in chunks of T/2 columns, each
+// chunk loaded into `buf` (8 T^2 bytes: the region of W's FP32 plane, free
+// during the setup), transformed there by radix-2 DIT stages and written
+// back.  Two reads and three writes of the scratch instead of one read and
+// one write per stage.  Twiddles exp(-j 2 pi e / T) come from the plan table.
+template <int T, int NT>
+__device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const PlanTables& tab, int Ls) {
+  using A = ArFF;
+  using C = ArFF::C;
+  using IO = PlanIO<A>;
+  constexpr int LOGT = ilog2(T), T2 = 2 * T, CH = T / 2;
+  const int tid = threadIdx.x;
+  // ---- rows: chunk rows are storage rows brev(rr), rr in [r0, r0 + CH) ----
+#pragma unroll 1
+  for (int r0 = 0; r0 < Ls; r0 += CH) {
+    const int nr = min(CH, Ls - r0);
+    for (int e = tid; e < nr * T; e += NT) {
+      const int lr = e >> LOGT, c = e & (T - 1);
+      const int row = __brev(r0 + lr) >> (32 - LOGT);
+      A::store(buf, lr * T2 + c, T, A::load(Z, row * T2 + c, T));
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int lh = 0; lh < LOGT; ++lh) {
+      const int h = 1 << lh;
+      for (int it = tid; it < nr * (T / 2); it += NT) {
+        const int lr = it >> (LOGT - 1), q = it & (T / 2 - 1);
+        const int i = ((q >> lh) << (lh + 1)) | (q & (h - 1));
+        const int ia = lr * T2 + i, ib = ia + h;
+        const C a = A::load(buf, ia, T), bb = A::load(buf, ib, T);
+        const C wb = A::mul_norm(IO::twiddle(tab, (q & (h - 1)) << (LOGT - 1 - lh)), bb);
+        A::store(buf, ia, T, A::add(a, wb));
+        A::store(buf, ib, T, A::sub(a, wb));
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < nr * T; e += NT) {
+      const int lr = e >> LOGT, c = e & (T - 1);
+      const int row = __brev(r0 + lr) >> (32 - LOGT);
+      A::store(Z, row * T2 + c, T, A::load(buf, lr * T2 + c, T));
+    }
+    __syncthreads();
+  }
+  // ---- columns: chunk of CH columns, all T rows, rows of 2 CH elements ----
+#pragma unroll 1
+  for (int c0 = 0; c0 < T; c0 += CH) {
+    for (int e = tid; e < T * CH; e += NT) {
+      const int r = e / CH, lc = e - r * CH;
+      A::store(buf, r * 2 * CH + lc, CH, A::load(Z, r * T2 + c0 + lc, T));
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int lh = 0; lh < LOGT; ++lh) {
+      const int h = 1 << lh;
+      for (int it = tid; it < CH * (T / 2); it += NT) {
+        const int lc = it % CH, q = it / CH;
+        const int i = ((q >> lh) << (lh + 1)) | (q & (h - 1));
+        const int ia = i * 2 * CH + lc, ib = ia + h * 2 * CH;
+        const C a = A::load(buf, ia, CH), bb = A::load(buf, ib, CH);
+        const C wb = A::mul_norm(IO::twiddle(tab, (q & (h - 1)) << (LOGT - 1 - lh)), bb);
+        A::store(buf, ia, CH, A::add(a, wb));
+        A::store(buf, ib, CH, A::sub(a, wb));
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < T * CH; e += NT) {
+      const int r = e / CH, lc = e - r * CH;
+      A::store(Z, r * T2 + c0 + lc, T, A::load(buf, r * 2 * CH + lc, CH));
+    }
+    __syncthreads();
+  }
+}
+
 template <int T, int NT>
 __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUtensorMap* tmF,
                                                  const CUtensorMap* tmA, int blk, float2* Whi,
@@ -202,9 +278,6 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   short* trY = reinterpret_cast<short*>(dsm + G::try_off(iters));
   float2* Zg = reinterpret_cast<float2*>(cta_scratch);
   float4* Rx = reinterpret_cast<float4*>(cta_scratch + G::z_bytes);
-  // FFT twiddles at the end of the W region (free until W is copied in)
-  C* tw = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(Whi) + sizeof(float2) * T * T -
-                               sizeof(C) * (T / 2));
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -270,14 +343,11 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
     }
     A::store(Zg, r * T2 + cc, T, z);
   }
-  // the twiddles go to the end of the W region, after every read of the
-  // staging tiles at its start
-  __syncthreads();
-  for (int e = tid; e < T / 2; e += NT) tw[e] = IO::twiddle(P.tab, e);
+  // the staging tiles are read: the W region becomes the FFT's chunk buffer
   int any_bad = __syncthreads_or(bad);
 
-  // ---- 3. FFT (float-float) in the global buffer ------------------------------
-  fft2d_dit<A, T, NT, false>(Zg, tw, Ls, T);
+  // ---- 3. FFT (float-float), through shared memory in chunks -------------------
+  fft2d_chunked<T, NT>(Zg, Whi, P.tab, Ls);
 
   // ---- split: exact R0 -> scratch, FP32 copy -> registers, first top-2 -------
   float2 R32[NB];
