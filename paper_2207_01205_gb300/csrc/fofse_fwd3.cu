@@ -140,12 +140,15 @@ __device__ __forceinline__ long long redux_sum64(long long v) {
 }
 
 // sum over j in {j0, j0 + stride, ...} < j1 of c_j W[k - u_j] + s_j conj(c_j) W[k + u_j]
-// (float-float terms, exact W from the global table) in fixed point with unit 1/scale
+// (float-float terms, exact W from the global table), added to sre / sim in
+// fixed point with unit 1/scale
 template <int T>
 __device__ __forceinline__ void recur_fixed(const float2* Zg, const short* ty, const float4* tc,
                                             int x, int j0, int j1, int stride, float scale,
                                             long long& sre, long long& sim) {
   using WG = WTab<ArFF, T, false>;
+  // a thread's few terms are summed in float-float and converted once
+  ff are = {0.f, 0.f}, aim = {0.f, 0.f};
   for (int j = j0; j < j1; j += stride) {
     const int y = ty[j];
     const float4 c4 = tc[j];
@@ -164,8 +167,12 @@ __device__ __forceinline__ void recur_fixed(const float2* Zg, const short* ty, c
       tre = ff_mul(c.re, Wm.re);
       tim = ff_mul(c.re, Wm.im);
     }
-    sre += fx_round(tre.h * scale) + fx_round(tre.l * scale);
-    sim += fx_round(tim.h * scale) + fx_round(tim.l * scale);
+    are = ff_add(are, tre);
+    aim = ff_add(aim, tim);
+  }
+  if (j0 < j1) {
+    sre += fx_round(are.h * scale) + fx_round(are.l * scale);
+    sim += fx_round(aim.h * scale) + fx_round(aim.l * scale);
   }
 }
 
