@@ -272,6 +272,34 @@ def run_other_workload(args, rank, world, local):
         torch.cuda.synchronize(dev)
     fwd_ms = reduce_max(sum(e[0].elapsed_time(e[1]) for e in ev), world, dev) / args.steps
     fb_ms = reduce_max(sum(e[0].elapsed_time(e[2]) for e in ev), world, dev) / args.steps
+
+    # the same forward call recorded once in a CUDA graph and replayed
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        fwd_side = lambda: binding.fofse_extrapolate_batch(
+            handles, blocks, frame, avail, out_blocks=ob, trace=tr, w0=w0, status=st, workspace=ws,
+            stream=side)
+        fwd_side()
+        torch.cuda.synchronize(dev)
+        with torch.cuda.graph(graph, stream=side):
+            fwd_side()
+    torch.cuda.synchronize(dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        g0.record(stream)
+        graph.replay()
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        g_ms += g0.elapsed_time(g1)
+    g_ms /= args.steps
+
+    stream64 = None
+    if args.workload == "predict-720p" and rank == 0:
+        stream64 = stream_prediction_frames(plans, handles, blocks, ws, dev, bmax)
     if rank == 0:
         line = {"metric": f"blocks/s ({args.workload})", "value": job_value(n, world, fwd_ms),
                 "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
@@ -281,8 +309,75 @@ def run_other_workload(args, rank, world, local):
                            "status_ok": int((st == 0).sum()),
                            "l2": "flushed between steps (512 MiB write)"},
                 "fwd_bwd": {"ms_per_step": fb_ms, "blocks_per_s": world * n / (fb_ms * 1e-3)},
+                "graph_replay": {"ms_per_step": g_ms, "blocks_per_s": world * n / (g_ms * 1e-3)},
+                "stream64": stream64,
                 "gpu_launches": args.steps * 2 * len(plans), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
+
+
+def stream_prediction_frames(plans, handles, blocks, ws, dev, bmax, n_frames=64):
+    """The streamed prediction workload: n_frames frames (cumulative random
+    0-4 px translations) go from pinned host memory through the forward call
+    and the rho / gamma gradient of the total prediction error (squared error
+    of every predicted block against the frame itself), the predicted blocks
+    come back to pinned host memory.  Copies run on their own stream, double
+    buffered against the computation; the timed region spans all frames."""
+    import numpy as np
+    import torch
+    from paper_2207_01205_gb300 import api, binding, synth
+    frames, _, specs = synth.prediction_sequence(n_frames=n_frames)
+    H, W = frames[0].shape
+    host = torch.from_numpy(np.stack(frames)).pin_memory()
+    n = int(blocks.shape[0])
+    out_host = torch.empty((n_frames, n, bmax, bmax), dtype=torch.float32).pin_memory()
+    avail = torch.ones((H, W), dtype=torch.uint8, device=dev)
+    fbuf = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in range(2)]
+    obuf = [api.alloc_outputs(plans, n, dev) for _ in range(2)]
+    truth = [torch.empty((n, bmax, bmax), dtype=torch.float32, device=dev) for _ in range(2)]
+    gblk = torch.empty((n, bmax, bmax), dtype=torch.float32, device=dev)
+    grg = torch.zeros((len(plans), 2), dtype=torch.float32, device=dev)
+    by = blocks[:, 0].long()
+    bx = blocks[:, 1].long()
+    iy = by[:, None, None] + torch.arange(bmax, device=dev)[None, :, None]
+    ix = bx[:, None, None] + torch.arange(bmax, device=dev)[None, None, :]
+    comp = torch.cuda.current_stream(dev)
+    copy = torch.cuda.Stream(dev)
+    done = [torch.cuda.Event() for _ in range(2)]
+    loaded = [torch.cuda.Event() for _ in range(2)]
+
+    def run(record):
+        for k in range(n_frames):
+            s = k & 1
+            with torch.cuda.stream(copy):
+                copy.wait_event(done[s])
+                fbuf[s].copy_(host[k], non_blocking=True)
+                loaded[s].record(copy)
+            comp.wait_event(loaded[s])
+            ob, tr, w0, st = obuf[s]
+            binding.fofse_extrapolate_batch(handles, blocks, fbuf[s], avail, out_blocks=ob, trace=tr,
+                                            w0=w0, status=st, workspace=ws, stream=comp)
+            truth[s].copy_(fbuf[s][iy, ix])
+            torch.mul(torch.sub(ob, truth[s], out=gblk), 2.0, out=gblk)
+            binding.fofse_backward(handles, blocks, fbuf[s], avail, tr, w0, gblk,
+                                   grad_rho_gamma=grg, workspace=ws, stream=comp)
+            out_host[k].copy_(ob, non_blocking=True)
+            done[s].record(comp)
+
+    run(False)
+    torch.cuda.synchronize(dev)
+    grg.zero_()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(comp)
+    run(True)
+    t1.record(comp)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1)
+    return {"frames": n_frames, "ms": ms, "frames_per_s": n_frames / (ms * 1e-3),
+            "blocks_per_s": n_frames * n / (ms * 1e-3),
+            "h2d_bytes_per_frame": H * W * 4, "d2h_bytes_per_frame": n * bmax * bmax * 4,
+            "grad_rho_gamma": [float(v) for v in grg[0].cpu()],
+            "includes": "H2D frame, forward, prediction-error gradient w.r.t. rho and gamma, D2H blocks"}
 
 
 def run_reference(args, rank, world):
