@@ -143,10 +143,17 @@ __device__ __forceinline__ long long redux_sum64(long long v) {
 // (float-float terms, exact W from the global table), added to sre / sim in
 // fixed point with unit 1/scale
 template <int T>
-__device__ __forceinline__ void recur_fixed(const float2* Zg, const short* ty, const float4* tc,
-                                            int x, int j0, int j1, int stride, float scale,
-                                            long long& sre, long long& sim) {
-  using WG = WTab<ArFF, T, false>;
+__device__ __forceinline__ void recur_fixed(const float2* Whi, const float2* Zg, const short* ty,
+                                            const float4* tc, int x, int j0, int j1, int stride,
+                                            float scale, long long& sre, long long& sim) {
+  constexpr int LOGT = ilog2(T), M = (T - 1) * 2 * T + (T - 1);
+  // exact W: hi part from the FP32 plane in shared memory (row stride T), lo
+  // part from the global table (two planes of row stride 2T)
+  auto wex = [&](int a) -> ArFF::C {  // a = packed a1 * 2T + a2
+    const float2 h = Whi[((a >> (LOGT + 1)) << LOGT) | (a & (T - 1))];
+    const float2 l = Zg[a + T];
+    return {{h.x, l.x}, {h.y, l.y}};
+  };
   // a thread's few terms are summed in float-float and converted once
   ff are = {0.f, 0.f}, aim = {0.f, 0.f};
   for (int j = j0; j < j1; j += stride) {
@@ -155,10 +162,10 @@ __device__ __forceinline__ void recur_fixed(const float2* Zg, const short* ty, c
     const ArFF::C c = {{c4.x, c4.y}, {c4.z, c4.w}};
     const int u1 = y >> (ilog2(T) + 1), u2 = y & (2 * T - 1);
     const bool sc = ((u1 & (T / 2 - 1)) == 0) && ((u2 & (T / 2 - 1)) == 0);
-    const ArFF::C Wm = WG::minus(Zg, x, y);
+    const ArFF::C Wm = wex((x + T - y) & M);
     ff tre, tim;
     if (!sc) {
-      const ArFF::C Wp = WG::plus(Zg, x, y);
+      const ArFF::C Wp = wex((x + y) & M);
       const ff s1 = ff_add_raw(Wm.re, Wp.re), s2 = ff_sub_raw(Wm.im, Wp.im);
       const ff s3 = ff_sub_raw(Wm.re, Wp.re), s4 = ff_add_raw(Wm.im, Wp.im);
       tre = ff_dot2(c.re, s1, ff_neg(c.im), s2);
@@ -467,7 +474,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           long long Sr = 0, Si = 0;
           if constexpr (NW <= 4) {
             if (warp * 32 < it) {  // warp-uniform: this warp holds terms
-              recur_fixed<T>(Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
+              recur_fixed<T>(Whi, Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
               warp_sum64(sre, sim);
             }
             if (lane == 0) red[warp] = make_longlong2(sre, sim);
@@ -480,7 +487,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
             }
           } else {
             if (warp * 32 < it) {
-              recur_fixed<T>(Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
+              recur_fixed<T>(Whi, Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
             }
@@ -539,7 +546,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               const int4 e = list[c];
               const float4 r0 = Rx[e.z];
               long long sre = 0, sim = 0;
-              recur_fixed<T>(Zg, trY, trC, e.x, lane, it, 32, scale, sre, sim);
+              recur_fixed<T>(Whi, Zg, trY, trC, e.x, lane, it, 32, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
               const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
