@@ -156,6 +156,22 @@ def measured_peaks():
         return None
 
 
+def cpu_transform_domain(wl, threads: int | None = None):
+    """The same method in its transform-domain form (FP64, C, all host cores)
+    on every block of the workload: the like-for-like CPU program for the
+    GPU/CPU ratio (the spatial oracle re-projects every iteration)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    oracle.build()
+    t0 = time.perf_counter()
+    res = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans, threads=threads, with_path=False,
+                           transform_domain=True)
+    dt = time.perf_counter() - t0
+    return {"value": wl.n_blocks / dt, "unit": "blocks/s", "cores": int(res.threads),
+            "kind": "transform-domain FOFSE, FP64 C",
+            "sample": f"all {wl.n_blocks} blocks, {int(res.threads)} threads, {dt:.1f} s"}
+
+
 def cpu_baseline(wl, sample_blocks: int, threads: int | None = None):
     """The FP64 oracle as it stands, on the host cores, over a bounded sample of
     the workload's blocks; returns blocks/s."""
@@ -618,9 +634,11 @@ def main():
     torch.cuda.synchronize(dev)
 
     cpu = None
+    cpu_fd = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, sample_blocks=min(n, 8 * (os.cpu_count() or 1)))
+        cpu_fd = cpu_transform_domain(wl)
         parity = parity_summary(wl, ob, tr, st)
 
     if rank == 0:
@@ -634,7 +652,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "fwd_bwd": fwd_bwd_line,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline,
-                "cpu_baseline": cpu, "plain_one_block_per_launch": plain,
+                "cpu_baseline": cpu, "cpu_transform_domain": cpu_fd, "plain_one_block_per_launch": plain,
                 "parity": parity, "variants": variants,
                 "device": props.name, "sms": sms}
         print(json.dumps(line), flush=True)

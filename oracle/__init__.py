@@ -71,6 +71,8 @@ def _declare(L):
     L.oracle_extrapolate_area.argtypes = [_c_int, _c_int, _dp, _dp, _c_double, _c_int, _dp, _ip, _ip,
                                           _dp, _dp, _dp, _dp]
     L.oracle_extrapolate_area.restype = _c_int
+    L.oracle_extrapolate_area_fd.argtypes = L.oracle_extrapolate_area.argtypes
+    L.oracle_extrapolate_area_fd.restype = _c_int
     L.oracle_replay_area.argtypes = [_c_int, _c_int, _dp, _dp, _c_double, _c_int, _ip, _ip, _dp, _dp,
                                      _dp, _dp]
     L.oracle_replay_area.restype = _c_int
@@ -86,6 +88,8 @@ def _declare(L):
                                ctypes.POINTER(OraclePlan), _c_int, _c_int, _dp, _ip, _dp, _ip, _ip,
                                _dp, _dp, _dp, _c_int]
     L.oracle_batch.restype = _c_int
+    L.oracle_batch_mode.argtypes = L.oracle_batch.argtypes + [_c_int]
+    L.oracle_batch_mode.restype = _c_int
     L.oracle_batch_adjoint.argtypes = [_fp, _u8p, _c_int, _c_int, _c_int, _ip, _c_int,
                                        ctypes.POINTER(OraclePlan), _c_int, _ip, _ip, _c_int, _dp,
                                        _c_int, _dp, _dp, _c_int]
@@ -161,8 +165,9 @@ class AreaResult:
         self.status, self.g, self.u, self.dc, self.gap, self.w0 = status, g, u, dc, gap, w0
 
 
-def extrapolate_area(fL, wL, T: int, gamma: float, iters: int) -> AreaResult:
-    """Spatial re-projection FOFSE over one area L (Sec. 2)."""
+def extrapolate_area(fL, wL, T: int, gamma: float, iters: int, transform_domain: bool = False) -> AreaResult:
+    """Spatial re-projection FOFSE over one area L (Sec. 2); with
+    ``transform_domain`` the paper's transform-domain form instead."""
     fL, wL = _f64(fL), _f64(wL)
     Ls = fL.shape[0]
     g = np.empty((Ls, Ls))
@@ -172,7 +177,8 @@ def extrapolate_area(fL, wL, T: int, gamma: float, iters: int) -> AreaResult:
     di = np.zeros(iters)
     gap = np.zeros(iters)
     w0 = ctypes.c_double()
-    st = lib().oracle_extrapolate_area(Ls, T, _p(fL, _dp), _p(wL, _dp), float(gamma), iters,
+    fn = lib().oracle_extrapolate_area_fd if transform_domain else lib().oracle_extrapolate_area
+    st = fn(Ls, T, _p(fL, _dp), _p(wL, _dp), float(gamma), iters,
                                        _p(g, _dp), _p(u1, _ip), _p(u2, _ip), _p(dr, _dp),
                                        _p(di, _dp), _p(gap, _dp), ctypes.byref(w0))
     return AreaResult(st, g, np.stack([u1, u2], axis=1), dr + 1j * di, gap, w0.value)
@@ -245,8 +251,11 @@ def plans_to_c(plans):
     return arr
 
 
-def run_batch(frame, avail, blocks, plans, threads: int | None = None, with_path: bool = True) -> BatchResult:
-    """Extrapolate every block of ``blocks`` ((n, 3) int: y, x, plan index)."""
+def run_batch(frame, avail, blocks, plans, threads: int | None = None, with_path: bool = True,
+              transform_domain: bool = False) -> BatchResult:
+    """Extrapolate every block of ``blocks`` ((n, 3) int: y, x, plan index);
+    ``transform_domain`` runs the transform-domain form (the CPU program timed
+    beside the GPU) instead of the spatial re-projection."""
     frame = np.ascontiguousarray(frame, dtype=np.float32)
     avail = np.ascontiguousarray(avail, dtype=np.uint8)
     blocks = _i32(blocks).reshape(-1, 3)
@@ -264,10 +273,10 @@ def run_batch(frame, avail, blocks, plans, threads: int | None = None, with_path
     gap = np.zeros((n, imax)) if with_path else None
     cplans = plans_to_c(plans)
     threads = threads or os.cpu_count() or 1
-    used = lib().oracle_batch(_p(frame, _fp), _p(avail, _u8p), H, W, W, _p(blocks, _ip), n, cplans,
-                              bmax * bmax, imax, _p(out, _dp), _p(status, _ip), _p(w0, _dp),
-                              _p(u1, _ip), _p(u2, _ip), _p(dr, _dp), _p(di, _dp), _p(gap, _dp),
-                              threads)
+    used = lib().oracle_batch_mode(_p(frame, _fp), _p(avail, _u8p), H, W, W, _p(blocks, _ip), n,
+                                   cplans, bmax * bmax, imax, _p(out, _dp), _p(status, _ip),
+                                   _p(w0, _dp), _p(u1, _ip), _p(u2, _ip), _p(dr, _dp), _p(di, _dp),
+                                   _p(gap, _dp), threads, 1 if transform_domain else 0)
     res_blocks = np.zeros((n, bmax, bmax))
     for i in range(n):
         b = plans[blocks[i, 2]].block

@@ -258,6 +258,76 @@ int oracle_extrapolate_area(int Ls, int T, const double* fL, const double* wL, d
 }
 
 /* -------------------------------------------------------------------------- */
+/* The transform-domain form (Sec. 2, closing remark)                          */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * The same extrapolation in the paper's complete transform-domain
+ * formulation: R_w = DFT(w f) and W = DFT(w) are formed once; each iteration
+ * takes the argmax of Eq. 9 over the canonical set, c = gamma R_w[u] / W0
+ * (Eq. 5, Eq. 14), and subtracts the spectrum of the added pair from every
+ * bin: R_w[k] -= c W[k - u] + s(u) conj(c) W[k + u] (Eq. 2, Eq. 3, Eq. 7 in
+ * the DFT domain).  O(I T^2) per block instead of O(I T^2 Ls).  It is the
+ * CPU program the GPU path is timed against for a like-for-like ratio, and a
+ * second, independently written check of the spatial re-projection above
+ * (same interface and outputs as oracle_extrapolate_area).
+ */
+int oracle_extrapolate_area_fd(int Ls, int T, const double* fL, const double* wL, double gamma,
+                               int iters, double* g, int* path_u1, int* path_u2, double* dc_re,
+                               double* dc_im, double* gap, double* w0_out) {
+    int N = Ls * Ls, TT = T * T;
+    double W0 = 0.0;
+    for (int i = 0; i < N; ++i) W0 += wL[i];
+    if (w0_out) *w0_out = W0;
+    for (int i = 0; i < N; ++i) g[i] = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    for (int i = 0; i < N; ++i)
+        if (wL[i] != 0.0 && !isfinite(fL[i])) return ORC_NONFINITE;
+
+    double* c = (double*)malloc(sizeof(double) * T);
+    double* s = (double*)malloc(sizeof(double) * T);
+    double* rw = (double*)malloc(sizeof(double) * N);
+    double* R_re = (double*)malloc(sizeof(double) * TT);
+    double* R_im = (double*)malloc(sizeof(double) * TT);
+    double* W_re = (double*)malloc(sizeof(double) * TT);
+    double* W_im = (double*)malloc(sizeof(double) * TT);
+    twiddles(T, c, s);
+    for (int i = 0; i < N; ++i) rw[i] = wL[i] != 0.0 ? wL[i] * fL[i] : 0.0;
+    oracle_project(Ls, T, rw, R_re, R_im);            /* R_w = DFT(w f) */
+    oracle_project(Ls, T, wL, W_re, W_im);            /* W = DFT(w)     */
+    for (int it = 0; it < iters; ++it) {
+        int u1, u2;
+        double gp;
+        oracle_select(T, R_re, R_im, &u1, &u2, &gp);
+        int ui = u1 * T + u2, pair = pair_weight_s(u1, u2, T);
+        double cr = gamma * R_re[ui] / W0;
+        double ci = pair ? gamma * R_im[ui] / W0 : 0.0;
+        for (int k1 = 0; k1 < T; ++k1)
+            for (int k2 = 0; k2 < T; ++k2) {
+                int a = ((k1 - u1 + T) % T) * T + (k2 - u2 + T) % T;  /* k - u */
+                int b = ((k1 + u1) % T) * T + (k2 + u2) % T;          /* k + u */
+                /* c W[k - u] + s conj(c) W[k + u] */
+                double tr = cr * W_re[a] - ci * W_im[a];
+                double ti = cr * W_im[a] + ci * W_re[a];
+                if (pair) {
+                    tr += cr * W_re[b] + ci * W_im[b];
+                    ti += cr * W_im[b] - ci * W_re[b];
+                }
+                R_re[k1 * T + k2] -= tr;
+                R_im[k1 * T + k2] -= ti;
+            }
+        add_basis_pair(Ls, T, c, s, u1, u2, cr, ci, g);   /* Eq. 2, for the output */
+        if (path_u1) path_u1[it] = u1;
+        if (path_u2) path_u2[it] = u2;
+        if (dc_re) dc_re[it] = cr;
+        if (dc_im) dc_im[it] = ci;
+        if (gap) gap[it] = gp;
+    }
+    free(c); free(s); free(rw); free(R_re); free(R_im); free(W_re); free(W_im);
+    return ORC_OK;
+}
+
+/* -------------------------------------------------------------------------- */
 /* Frozen-path companions                                                      */
 /* -------------------------------------------------------------------------- */
 
@@ -444,6 +514,7 @@ typedef struct {
     double* dc_re;
     double* dc_im;
     double* gap;
+    int transform_domain;       /* 0: spatial re-projection, 1: transform-domain form */
     int next;                   /* work counter */
     pthread_mutex_t lock;
 } batch_job;
@@ -460,7 +531,7 @@ static void run_one(batch_job* J, int bi) {
                     P->border, fL, aL);
     oracle_weights(P->block, P->border, P->support, P->rho, aL, wL);
     size_t to = (size_t)bi * J->trace_stride;
-    int st = oracle_extrapolate_area(
+    int st = (J->transform_domain ? oracle_extrapolate_area_fd : oracle_extrapolate_area)(
         Ls, P->fft_size, fL, wL, P->gamma, P->iters, g, J->path_u1 ? J->path_u1 + to : NULL,
         J->path_u2 ? J->path_u2 + to : NULL, J->dc_re ? J->dc_re + to : NULL,
         J->dc_im ? J->dc_im + to : NULL, J->gap ? J->gap + to : NULL, J->w0 ? J->w0 + bi : NULL);
@@ -484,12 +555,16 @@ static void* batch_worker(void* arg) {
     return NULL;
 }
 
-/* Extrapolate every listed block of a frame; returns the number of threads used. */
-int oracle_batch(const float* frame, const unsigned char* avail, int height, int width, int pitch,
-                 const int* blocks, int n_blocks, const oracle_plan* plans, int out_stride,
-                 int trace_stride, double* out_blocks, int* status, double* w0, int* path_u1,
-                 int* path_u2, double* dc_re, double* dc_im, double* gap, int n_threads) {
+/* Extrapolate every listed block of a frame; returns the number of threads used.
+ * transform_domain selects oracle_extrapolate_area_fd instead of the spatial
+ * re-projection. */
+int oracle_batch_mode(const float* frame, const unsigned char* avail, int height, int width,
+                      int pitch, const int* blocks, int n_blocks, const oracle_plan* plans,
+                      int out_stride, int trace_stride, double* out_blocks, int* status, double* w0,
+                      int* path_u1, int* path_u2, double* dc_re, double* dc_im, double* gap,
+                      int n_threads, int transform_domain) {
     batch_job J;
+    J.transform_domain = transform_domain;
     J.frame = frame; J.avail = avail; J.height = height; J.width = width; J.pitch = pitch;
     J.blocks = blocks; J.plans = plans; J.n_blocks = n_blocks; J.out_stride = out_stride;
     J.trace_stride = trace_stride; J.out_blocks = out_blocks; J.status = status; J.w0 = w0;
@@ -504,6 +579,15 @@ int oracle_batch(const float* frame, const unsigned char* avail, int height, int
     free(th);
     pthread_mutex_destroy(&J.lock);
     return n_threads;
+}
+
+int oracle_batch(const float* frame, const unsigned char* avail, int height, int width, int pitch,
+                 const int* blocks, int n_blocks, const oracle_plan* plans, int out_stride,
+                 int trace_stride, double* out_blocks, int* status, double* w0, int* path_u1,
+                 int* path_u2, double* dc_re, double* dc_im, double* gap, int n_threads) {
+    return oracle_batch_mode(frame, avail, height, width, pitch, blocks, n_blocks, plans,
+                             out_stride, trace_stride, out_blocks, status, w0, path_u1, path_u2,
+                             dc_re, dc_im, gap, n_threads, 0);
 }
 
 /* -------------------------------------------------------------------------- */

@@ -242,6 +242,32 @@ def test_transform_domain_recursion_equals_spatial_reprojection(seed):
     assert np.max(np.abs(dcs - res.dc)) < 1e-12 * np.max(np.abs(res.dc))
 
 
+@pytest.mark.parametrize("seed", [0, 1])
+def test_c_transform_domain_form_matches_numpy_restatement_and_spatial_oracle(seed):
+    """The C transform-domain form (the CPU program timed beside the GPU) agrees
+    with the numpy restatement above and with the spatial re-projection:
+    identical paths, coefficients to 1e-12, samples to 1e-9."""
+    wl = synth.single_block(seed=seed + 9)
+    fL, aL = oracle.cut_area(wl.frame, wl.avail, 16, 16, 16, 16)
+    w = oracle.weights(16, 16, 0.8, aL)
+    sp = oracle.extrapolate_area(fL, w, 64, 0.5, 60)
+    fd = oracle.extrapolate_area(fL, w, 64, 0.5, 60, transform_domain=True)
+    path, dcs = _spectral_fofse(fL, w, 64, 0.5, 60)
+    assert fd.status == 0 and np.array_equal(fd.u, sp.u) and np.array_equal(fd.u, path)
+    scale = np.max(np.abs(sp.dc))
+    assert np.max(np.abs(fd.dc - sp.dc)) < 1e-12 * scale
+    assert np.max(np.abs(fd.dc - dcs)) < 1e-12 * scale
+    assert np.max(np.abs(fd.g - sp.g)) < 1e-9
+
+
+def test_c_transform_domain_batch_matches_oracle_batch():
+    wl = synth.small_frame(17, plan=synth.PlanSpec(8, 8, 32, 0.7, 0.4, 40), n_lost=5)
+    a = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans, threads=2)
+    b = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans, threads=2, transform_domain=True)
+    assert np.array_equal(a.status, b.status) and np.array_equal(a.path, b.path)
+    assert np.max(np.abs(a.blocks - b.blocks)) < 1e-9
+
+
 def test_cyclic_translation_of_L_inside_the_grid():
     """|DFT| is invariant under a cyclic shift, and the model update uses the
     same basis, so moving L inside the T x T grid leaves the path and the
