@@ -31,7 +31,7 @@ STATUS_OK, STATUS_NO_SUPPORT, STATUS_NONFINITE = 0, 1, 2
 class OraclePlan(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("border", ctypes.c_int), ("fft_size", ctypes.c_int),
                 ("iters", ctypes.c_int), ("support", ctypes.c_int), ("rho", ctypes.c_double),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("compensation", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -88,7 +88,10 @@ def _declare(L):
                                ctypes.POINTER(OraclePlan), _c_int, _c_int, _dp, _ip, _dp, _ip, _ip,
                                _dp, _dp, _dp, _c_int]
     L.oracle_batch.restype = _c_int
-    L.oracle_batch_mode.argtypes = L.oracle_batch.argtypes + [_c_int]
+    L.oracle_batch_mode.argtypes = L.oracle_batch.argtypes + [_c_int, _dp, _dp]
+    L.oracle_extrapolate_area_ofse.argtypes = [_c_int, _c_int, _dp, _dp, _c_int, _dp, _ip, _ip, _dp,
+                                               _dp, _dp, _dp, _dp, _dp]
+    L.oracle_extrapolate_area_ofse.restype = _c_int
     L.oracle_batch_mode.restype = _c_int
     L.oracle_batch_adjoint.argtypes = [_fp, _u8p, _c_int, _c_int, _c_int, _ip, _c_int,
                                        ctypes.POINTER(OraclePlan), _c_int, _ip, _ip, _c_int, _dp,
@@ -184,6 +187,23 @@ def extrapolate_area(fL, wL, T: int, gamma: float, iters: int, transform_domain:
     return AreaResult(st, g, np.stack([u1, u2], axis=1), dr + 1j * di, gap, w0.value)
 
 
+def extrapolate_area_ofse(fL, wL, T: int, iters: int):
+    """Spatial re-projection with OFSE's compensation (Eq. 10-13); returns the
+    AreaResult and the compensation factors gamma_u per iteration (complex)."""
+    fL, wL = _f64(fL), _f64(wL)
+    Ls = fL.shape[0]
+    g = np.empty((Ls, Ls))
+    u1 = np.zeros(iters, dtype=np.int32)
+    u2 = np.zeros(iters, dtype=np.int32)
+    dr, di, gr, gi, gap = (np.zeros(iters) for _ in range(5))
+    w0 = ctypes.c_double()
+    st = lib().oracle_extrapolate_area_ofse(Ls, T, _p(fL, _dp), _p(wL, _dp), iters, _p(g, _dp),
+                                            _p(u1, _ip), _p(u2, _ip), _p(dr, _dp), _p(di, _dp),
+                                            _p(gr, _dp), _p(gi, _dp), _p(gap, _dp),
+                                            ctypes.byref(w0))
+    return AreaResult(st, g, np.stack([u1, u2], axis=1), dr + 1j * di, gap, w0.value), gr + 1j * gi
+
+
 def replay_area(fL, wL, T: int, gamma: float, path) -> tuple:
     """Forward along a fixed path; returns (g over L, coefficients)."""
     fL, wL = _f64(fL), _f64(wL)
@@ -247,7 +267,7 @@ def plans_to_c(plans):
     arr = (OraclePlan * len(plans))()
     for i, p in enumerate(plans):
         arr[i] = OraclePlan(p.block, p.border, p.fft_size, p.iters, getattr(p, "support", 0),
-                            float(p.rho), float(p.gamma))
+                            float(p.rho), float(p.gamma), int(getattr(p, "compensation", 0)))
     return arr
 
 
@@ -271,19 +291,24 @@ def run_batch(frame, avail, blocks, plans, threads: int | None = None, with_path
     dr = np.zeros((n, imax)) if with_path else None
     di = np.zeros((n, imax)) if with_path else None
     gap = np.zeros((n, imax)) if with_path else None
+    gre = np.zeros((n, imax)) if with_path else None
+    gim = np.zeros((n, imax)) if with_path else None
     cplans = plans_to_c(plans)
     threads = threads or os.cpu_count() or 1
     used = lib().oracle_batch_mode(_p(frame, _fp), _p(avail, _u8p), H, W, W, _p(blocks, _ip), n,
                                    cplans, bmax * bmax, imax, _p(out, _dp), _p(status, _ip),
                                    _p(w0, _dp), _p(u1, _ip), _p(u2, _ip), _p(dr, _dp), _p(di, _dp),
-                                   _p(gap, _dp), threads, 1 if transform_domain else 0)
+                                   _p(gap, _dp), threads, 1 if transform_domain else 0,
+                                   _p(gre, _dp), _p(gim, _dp))
     res_blocks = np.zeros((n, bmax, bmax))
     for i in range(n):
         b = plans[blocks[i, 2]].block
         res_blocks[i, :b, :b] = out[i, :b * b].reshape(b, b)
     path = np.stack([u1, u2], axis=2) if with_path else None
     dc = (dr + 1j * di) if with_path else None
-    return BatchResult(res_blocks, status, w0, path, dc, gap, used)
+    res = BatchResult(res_blocks, status, w0, path, dc, gap, used)
+    res.ofse_gamma = (gre + 1j * gim) if with_path else None  # per iteration, OFSE plans only
+    return res
 
 
 def block_gradients(frame, avail, y, x, plan, path, e_B):

@@ -54,6 +54,7 @@ typedef struct {
     int support;   /* 0 = full frame around B, 1 = causal L     */
     double rho;    /* rho_hat of Eq. 15                         */
     double gamma;  /* constant compensation factor of Eq. 14    */
+    int compensation; /* 0 = constant gamma (Eq. 14), 1 = OFSE's compensation (Eq. 10-12) */
 } oracle_plan;
 
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -254,6 +255,88 @@ int oracle_extrapolate_area(int Ls, int T, const double* fL, const double* wL, d
         if (gap) gap[it] = gp;
     }
     free(c); free(s); free(rw); free(P_re); free(P_im);
+    return ORC_OK;
+}
+
+/* -------------------------------------------------------------------------- */
+/* OFSE's orthogonality deficiency compensation (Sec. 3, Eq. 10-12)            */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * The spatial re-projection with the compensation FOFSE replaces: every
+ * iteration all projections P[l] of the weighted residual are formed (Eq. 8)
+ * and the coefficient of the selected u is
+ *     c_u = p_u / sum_l (p_l / p_u) Khat[u, l]                          (Eq. 10)
+ * with Khat = diag(K)^-1 K (Eq. 11) and K the matrix of weighted scalar
+ * products of the basis functions (Eq. 12).  For the DFT basis K[u, l] =
+ * sum w phi_l conj(phi_u) = W[u - l] with W = DFT(w), diag(K) = W0, so
+ *     sum_l p_l Khat[u, l] = Q[u] / W0^2,  Q[u] = sum_l P[l] W[u - l],
+ *     c_u = P[u]^2 / Q[u],   gamma_u = c_u / p_u = P[u] W0 / Q[u]      (Eq. 13)
+ * (p_l = P[l] / W0).  Q[u] is summed directly over all T^2 bins l.  The
+ * conjugate partner gets conj(c_u), as with the constant compensation; for
+ * the four self-conjugate u both P[u] and Q[u] are real.  gamma_u (complex for
+ * the complex basis) is returned per iteration for the distribution of Fig. 2.
+ */
+int oracle_extrapolate_area_ofse(int Ls, int T, const double* fL, const double* wL, int iters,
+                                 double* g, int* path_u1, int* path_u2, double* dc_re,
+                                 double* dc_im, double* gamma_re, double* gamma_im, double* gap,
+                                 double* w0_out) {
+    int N = Ls * Ls, TT = T * T;
+    double W0 = 0.0;
+    for (int i = 0; i < N; ++i) W0 += wL[i];
+    if (w0_out) *w0_out = W0;
+    for (int i = 0; i < N; ++i) g[i] = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    for (int i = 0; i < N; ++i)
+        if (wL[i] != 0.0 && !isfinite(fL[i])) return ORC_NONFINITE;
+
+    double* c = (double*)malloc(sizeof(double) * T);
+    double* s = (double*)malloc(sizeof(double) * T);
+    double* rw = (double*)malloc(sizeof(double) * N);
+    double* P_re = (double*)malloc(sizeof(double) * TT);
+    double* P_im = (double*)malloc(sizeof(double) * TT);
+    double* W_re = (double*)malloc(sizeof(double) * TT);
+    double* W_im = (double*)malloc(sizeof(double) * TT);
+    twiddles(T, c, s);
+    oracle_project(Ls, T, wL, W_re, W_im);             /* K[u, l] = W[u - l] */
+    for (int it = 0; it < iters; ++it) {
+        for (int i = 0; i < N; ++i) rw[i] = wL[i] != 0.0 ? wL[i] * (fL[i] - g[i]) : 0.0;
+        oracle_project(Ls, T, rw, P_re, P_im);
+        int u1, u2;
+        double gp;
+        oracle_select(T, P_re, P_im, &u1, &u2, &gp);
+        /* Q[u] = sum_l P[l] W[u - l] */
+        double q_re = 0.0, q_im = 0.0;
+        for (int l1 = 0; l1 < T; ++l1)
+            for (int l2 = 0; l2 < T; ++l2) {
+                int a = ((u1 - l1 + T) % T) * T + (u2 - l2 + T) % T;
+                double pr = P_re[l1 * T + l2], pi = P_im[l1 * T + l2];
+                q_re += pr * W_re[a] - pi * W_im[a];
+                q_im += pr * W_im[a] + pi * W_re[a];
+            }
+        int ui = u1 * T + u2, pair = pair_weight_s(u1, u2, T);
+        double pr = P_re[ui], pi = pair ? P_im[ui] : 0.0;
+        if (!pair) q_im = 0.0;
+        /* c = P^2 / Q,  gamma = P W0 / Q */
+        double den = q_re * q_re + q_im * q_im;
+        double sq_re = pr * pr - pi * pi, sq_im = 2.0 * pr * pi;
+        double cr = 0.0, ci = 0.0, gr = 0.0, gi = 0.0;
+        if (den > 0.0) {
+            cr = (sq_re * q_re + sq_im * q_im) / den;
+            ci = (sq_im * q_re - sq_re * q_im) / den;
+            gr = W0 * (pr * q_re + pi * q_im) / den;
+            gi = W0 * (pi * q_re - pr * q_im) / den;
+        }
+        add_basis_pair(Ls, T, c, s, u1, u2, cr, ci, g);
+        if (path_u1) path_u1[it] = u1;
+        if (path_u2) path_u2[it] = u2;
+        if (dc_re) dc_re[it] = cr;
+        if (dc_im) dc_im[it] = ci;
+        if (gamma_re) gamma_re[it] = gr;
+        if (gamma_im) gamma_im[it] = gi;
+        if (gap) gap[it] = gp;
+    }
+    free(c); free(s); free(rw); free(P_re); free(P_im); free(W_re); free(W_im);
     return ORC_OK;
 }
 
@@ -514,6 +597,8 @@ typedef struct {
     double* dc_re;
     double* dc_im;
     double* gap;
+    double* gamma_re;           /* OFSE compensation factors (nullable) */
+    double* gamma_im;
     int transform_domain;       /* 0: spatial re-projection, 1: transform-domain form */
     int next;                   /* work counter */
     pthread_mutex_t lock;
@@ -531,10 +616,19 @@ static void run_one(batch_job* J, int bi) {
                     P->border, fL, aL);
     oracle_weights(P->block, P->border, P->support, P->rho, aL, wL);
     size_t to = (size_t)bi * J->trace_stride;
-    int st = (J->transform_domain ? oracle_extrapolate_area_fd : oracle_extrapolate_area)(
-        Ls, P->fft_size, fL, wL, P->gamma, P->iters, g, J->path_u1 ? J->path_u1 + to : NULL,
-        J->path_u2 ? J->path_u2 + to : NULL, J->dc_re ? J->dc_re + to : NULL,
-        J->dc_im ? J->dc_im + to : NULL, J->gap ? J->gap + to : NULL, J->w0 ? J->w0 + bi : NULL);
+    int st;
+    if (P->compensation == 1)
+        st = oracle_extrapolate_area_ofse(
+            Ls, P->fft_size, fL, wL, P->iters, g, J->path_u1 ? J->path_u1 + to : NULL,
+            J->path_u2 ? J->path_u2 + to : NULL, J->dc_re ? J->dc_re + to : NULL,
+            J->dc_im ? J->dc_im + to : NULL, J->gamma_re ? J->gamma_re + to : NULL,
+            J->gamma_im ? J->gamma_im + to : NULL, J->gap ? J->gap + to : NULL,
+            J->w0 ? J->w0 + bi : NULL);
+    else
+        st = (J->transform_domain ? oracle_extrapolate_area_fd : oracle_extrapolate_area)(
+            Ls, P->fft_size, fL, wL, P->gamma, P->iters, g, J->path_u1 ? J->path_u1 + to : NULL,
+            J->path_u2 ? J->path_u2 + to : NULL, J->dc_re ? J->dc_re + to : NULL,
+            J->dc_im ? J->dc_im + to : NULL, J->gap ? J->gap + to : NULL, J->w0 ? J->w0 + bi : NULL);
     J->status[bi] = st;
     double* ob = J->out_blocks + (size_t)bi * J->out_stride;
     for (int m = 0; m < P->block; ++m)
@@ -562,9 +656,11 @@ int oracle_batch_mode(const float* frame, const unsigned char* avail, int height
                       int pitch, const int* blocks, int n_blocks, const oracle_plan* plans,
                       int out_stride, int trace_stride, double* out_blocks, int* status, double* w0,
                       int* path_u1, int* path_u2, double* dc_re, double* dc_im, double* gap,
-                      int n_threads, int transform_domain) {
+                      int n_threads, int transform_domain, double* gamma_re, double* gamma_im) {
     batch_job J;
     J.transform_domain = transform_domain;
+    J.gamma_re = gamma_re;
+    J.gamma_im = gamma_im;
     J.frame = frame; J.avail = avail; J.height = height; J.width = width; J.pitch = pitch;
     J.blocks = blocks; J.plans = plans; J.n_blocks = n_blocks; J.out_stride = out_stride;
     J.trace_stride = trace_stride; J.out_blocks = out_blocks; J.status = status; J.w0 = w0;
@@ -587,7 +683,7 @@ int oracle_batch(const float* frame, const unsigned char* avail, int height, int
                  int* path_u2, double* dc_re, double* dc_im, double* gap, int n_threads) {
     return oracle_batch_mode(frame, avail, height, width, pitch, blocks, n_blocks, plans,
                              out_stride, trace_stride, out_blocks, status, w0, path_u1, path_u2,
-                             dc_re, dc_im, gap, n_threads, 0);
+                             dc_re, dc_im, gap, n_threads, 0, NULL, NULL);
 }
 
 /* -------------------------------------------------------------------------- */

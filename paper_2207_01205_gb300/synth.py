@@ -125,6 +125,7 @@ class PlanSpec:
     gamma: float
     iters: int
     support: int = 0  # 0 = full frame around B, 1 = causal L shape (top/left)
+    compensation: int = 0  # 0 = constant gamma (FOFSE, Eq. 14), 1 = OFSE's (Eq. 10-12)
 
 
 @dataclasses.dataclass

@@ -1,0 +1,179 @@
+"""Pins of the oracle's OFSE compensation (Sec. 3, Eq. 10-13).
+
+The oracle sums Q[u] = sum_l P[l] W[u - l] directly over the bins; these
+tests reach the same numbers by other routes: the paper's matrix form with a
+brute-force Gram matrix K of the basis functions (Eq. 10-12), the
+convolution theorem with numpy's FFT, a closed form for a constant signal,
+the orthogonal case, and the centre of the factor distribution the paper
+reports for its concealment setting (Fig. 2).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_01205_gb300 import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def _canonical_mask(T):
+    k1, k2 = np.meshgrid(np.arange(T), np.arange(T), indexing="ij")
+    return (k1 * T + k2) <= (((T - k1) % T) * T + (T - k2) % T)
+
+
+def _ofse_matrix_form(fL, wL, T, iters):
+    """Eq. 10-12 as printed: K[u, l] = sum w phi_l conj(phi_u) (weighted scalar
+    products, brute force over L), Khat = diag(diag K)^-1 K, p_l = projection
+    coefficients of Eq. 5, c_u = p_u / sum_l (p_l / p_u) Khat[u, l]; the pair
+    (u, -u) of a real model gets c_u and conj(c_u)."""
+    Ls = fL.shape[0]
+    m, n = np.meshgrid(np.arange(Ls), np.arange(Ls), indexing="ij")
+    k1, k2 = np.meshgrid(np.arange(T), np.arange(T), indexing="ij")
+    phi = np.exp(2j * np.pi * (k1.reshape(-1, 1, 1) * m + k2.reshape(-1, 1, 1) * n) / T)  # (T^2, Ls, Ls)
+    K = np.einsum("xy,lxy,uxy->ul", wL, phi, np.conj(phi))
+    Khat = K / np.diag(K)[:, None]
+    H = _canonical_mask(T).reshape(-1)
+    g = np.zeros((Ls, Ls))
+    path, cs, gammas = [], [], []
+    for _ in range(iters):
+        r = fL - g
+        p = np.einsum("xy,lxy->l", wL * r, np.conj(phi)) / np.real(np.diag(K))
+        mag = np.where(H, np.abs(p) ** 2, -1.0)
+        ui = int(np.argmax(mag))
+        u1, u2 = divmod(ui, T)
+        sc = (2 * u1) % T == 0 and (2 * u2) % T == 0
+        denom = np.sum(p / p[ui] * Khat[ui, :])
+        c = p[ui] / denom
+        gam = 1.0 / denom
+        if sc:
+            c, gam = c.real, gam.real
+            g = g + np.real(c * phi[ui])
+        else:
+            g = g + 2.0 * np.real(c * phi[ui])
+        path.append((u1, u2))
+        cs.append(c)
+        gammas.append(gam)
+    return np.array(path), np.array(cs), np.array(gammas), g
+
+
+@pytest.mark.parametrize("seed,T,Ls,lost", [(0, 8, 6, 0.0), (1, 8, 7, 0.25), (2, 8, 8, 0.3), (3, 16, 9, 0.2)])
+def test_ofse_equals_matrix_form_with_bruteforce_gram_matrix(seed, T, Ls, lost):
+    """Eq. 10-12 with K built sample by sample (an O(T^4 Ls^2) Gram matrix)
+    against the oracle's convolution of spectra: same path, coefficients,
+    factors and model to rounding."""
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0, 255, size=(Ls, Ls))
+    w = rng.uniform(0.05, 1.0, size=(Ls, Ls))
+    w[rng.uniform(size=(Ls, Ls)) < lost] = 0.0
+    iters = 12
+    res, gam = oracle.extrapolate_area_ofse(f, w, T, iters)
+    path, cs, gms, g = _ofse_matrix_form(f, w, T, iters)
+    assert res.status == 0
+    assert np.array_equal(res.u, path)
+    assert np.max(np.abs(res.dc - cs)) <= 1e-9 * np.max(np.abs(cs))
+    assert np.max(np.abs(gam - gms)) <= 1e-9
+    assert np.max(np.abs(res.g - g)) <= 1e-8 * np.max(np.abs(g))
+
+
+def test_ofse_first_factor_by_convolution_theorem():
+    """sum_l P[l] W[u - l] is a cyclic convolution of spectra, i.e.
+    T^2 DFT(w^2 r)[u]; so gamma_u = W0 P[u] / (T^2 DFT(w^2 f)[u]) in the first
+    iteration, with numpy's FFT."""
+    wl = synth.single_block(seed=2)
+    fL, aL = oracle.cut_area(wl.frame, wl.avail, 16, 16, 16, 16)
+    w = oracle.weights(16, 16, 0.8, aL)
+    T = 64
+    res, gam = oracle.extrapolate_area_ofse(fL, w, T, 2)
+    Z = np.zeros((T, T))
+    Z[:48, :48] = w * fL
+    Z2 = np.zeros((T, T))
+    Z2[:48, :48] = w * w * fL
+    P, Q = np.fft.fft2(Z), T * T * np.fft.fft2(Z2)
+    u = tuple(res.u[0])
+    g_ref = w.sum() * P[u] / Q[u]
+    c_ref = P[u] ** 2 / Q[u]
+    if (2 * u[0]) % T == 0 and (2 * u[1]) % T == 0:
+        g_ref, c_ref = g_ref.real, c_ref.real
+    assert abs(gam[0] - g_ref) <= 1e-12 * abs(g_ref)
+    assert abs(res.dc[0] - c_ref) <= 1e-12 * abs(c_ref)
+
+
+def test_ofse_constant_signal_closed_form():
+    """f = c on A: every residual is constant, its spectrum (c - g) W peaks at
+    DC, and Q[0] = T^2 (c - g) sum w^2, so each step keeps the fraction
+    kappa = (sum w)^2 / (T^2 sum w^2) (<= 1 by Cauchy-Schwarz) and
+    g = c (1 - (1 - kappa)^nu)."""
+    rng = np.random.default_rng(5)
+    b, br, T = 8, 8, 32
+    Ls = b + 2 * br
+    a = (rng.uniform(size=(Ls, Ls)) > 0.2).astype(np.uint8)
+    w = oracle.weights(b, br, 0.8, a)
+    kappa = w.sum() ** 2 / (T * T * np.sum(w * w))
+    c = 91.0
+    for nu in (1, 4, 9):
+        res, gam = oracle.extrapolate_area_ofse(np.full((Ls, Ls), c), w, T, nu)
+        assert np.all(res.u == 0)
+        assert np.allclose(gam, kappa, rtol=1e-12, atol=0)
+        assert np.allclose(res.g, c * (1 - (1 - kappa) ** nu), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_ofse_orthogonal_case_is_fofse_with_gamma_one(seed):
+    """w = 1 on the whole T x T grid: K = T^2 I (Eq. 12), Khat = I, so every
+    factor is 1 and OFSE is the constant compensation with gamma = 1."""
+    rng = np.random.default_rng(seed)
+    T = 16
+    f = rng.uniform(0, 255, size=(T, T))
+    w = np.ones((T, T))
+    res, gam = oracle.extrapolate_area_ofse(f, w, T, 20)
+    ref = oracle.extrapolate_area(f, w, T, 1.0, 20)
+    assert np.max(np.abs(gam - 1.0)) < 1e-12
+    assert np.array_equal(res.u, ref.u)
+    assert np.max(np.abs(res.dc - ref.dc)) < 1e-9 * np.max(np.abs(ref.dc))
+    assert np.max(np.abs(res.g - ref.g)) < 1e-9 * np.max(np.abs(ref.g))
+
+
+def test_ofse_zero_signal_and_no_support():
+    """Zero residual: every projection is zero, the first canonical bin is
+    picked and the coefficient is zero (Q = 0).  No support: status 1."""
+    w = oracle.weights(8, 8, 0.8, np.ones((24, 24), dtype=np.uint8))
+    res, gam = oracle.extrapolate_area_ofse(np.zeros((24, 24)), w, 32, 3)
+    assert res.status == 0 and np.all(res.u == 0) and np.all(res.dc == 0) and np.all(res.g == 0)
+    res, _ = oracle.extrapolate_area_ofse(np.ones((24, 24)), np.zeros((24, 24)), 32, 3)
+    assert res.status == 1
+
+
+def test_ofse_factor_distribution_centre_matches_fig2():
+    """Fig. 2 (16 x 16 blocks, border 16, 64 x 64 FFT, 200 iterations): the
+    compensation factors cluster about 0.2.  On synthetic blocks of the same
+    geometry the median real part and the interquartile range lie there too
+    (a lost T^2 or W0 would move them by orders of magnitude)."""
+    gs = []
+    for s in range(4):
+        wl = synth.single_block(seed=s)
+        fL, aL = oracle.cut_area(wl.frame, wl.avail, 16, 16, 16, 16)
+        w = oracle.weights(16, 16, 0.8, aL)
+        _, gam = oracle.extrapolate_area_ofse(fL, w, 64, 200)
+        gs.append(gam)
+    g = np.concatenate(gs)
+    q25, q50, q75 = np.percentile(g.real, [25, 50, 75])
+    assert 0.12 <= q50 <= 0.28
+    assert 0.08 <= q25 and q75 <= 0.35
+    assert np.median(np.abs(g.imag)) < 0.05
+
+
+def test_ofse_batch_matches_single_area_calls():
+    """The batch driver with compensation = 1 runs the same function per block."""
+    plan = synth.PlanSpec(16, 16, 64, 0.8, 0.5, 25, 0, 1)
+    wl = synth.small_frame(3, plan=plan)
+    plans = [plan]
+    out = oracle.run_batch(wl.frame, wl.avail, wl.blocks, plans, with_path=True)
+    for i, (y, x, pi) in enumerate(wl.blocks[:4]):
+        P = plans[pi]
+        fL, aL = oracle.cut_area(wl.frame, wl.avail, y, x, P.block, P.border)
+        w = oracle.weights(P.block, P.border, P.rho, aL, P.support)
+        res, gam = oracle.extrapolate_area_ofse(fL, w, P.fft_size, P.iters)
+        assert np.array_equal(out.path[i, :P.iters], res.u)
+        assert np.allclose(out.ofse_gamma[i, :P.iters], gam, rtol=0, atol=0)
+        b, br = P.block, P.border
+        assert np.array_equal(out.blocks[i][:b, :b], res.g[br:br + b, br:br + b])
