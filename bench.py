@@ -630,6 +630,43 @@ def main():
             torch.cuda.synchronize(dev)
             vt += v0.elapsed_time(v1)
         variants[prec] = {"ms_per_step": vt / 5, "blocks_per_s": n / (vt / 5 * 1e-3)}
+    # ---- OFSE's compensation (Eq. 10-13) on the same batch, with the factor
+    # of every iteration returned: its distribution is the analogue of Fig. 2 ----
+    import dataclasses
+    oplans = [api.Plan.from_spec(dataclasses.replace(p, compensation=1), "fp32") for p in wl.plans]
+    ows = api.workspace(oplans, n, dev)
+    oh = [p.handle for p in oplans]
+    ogam = torch.empty((n, max(p.iters for p in wl.plans), 2), dtype=torch.float32, device=dev)
+
+    def orun():
+        binding.fofse_extrapolate_batch_gamma(oh, blocks, frame, avail, out_blocks=ob, trace=tr,
+                                              w0=w0, status=st, gamma=ogam, workspace=ows,
+                                              stream=stream)
+    for _ in range(2):
+        orun()
+    torch.cuda.synchronize(dev)
+    o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ot = 0.0
+    for _ in range(5):
+        flush.zero_()
+        o0.record(stream)
+        orun()
+        o1.record(stream)
+        torch.cuda.synchronize(dev)
+        ot += o0.elapsed_time(o1)
+    gre = ogam[..., 0].cpu().numpy().reshape(-1)
+    gim = ogam[..., 1].cpu().numpy().reshape(-1)
+    edges = np.linspace(0.0, 1.0, 21)
+    hist = np.histogram(gre, bins=edges)[0]
+    ofse = {"ms_per_step": ot / 5, "blocks_per_s": n / (ot / 5 * 1e-3),
+            "gamma_distribution": {
+                "what": "Re gamma_u per iteration over all blocks (Fig. 2 analogue)",
+                "median": float(np.median(gre)), "q25": float(np.percentile(gre, 25)),
+                "q75": float(np.percentile(gre, 75)), "median_abs_im": float(np.median(np.abs(gim))),
+                "frac_in_0.1_0.3": float(np.mean((gre >= 0.1) & (gre < 0.3))),
+                "below_0": int(np.sum(gre < 0)), "above_1": int(np.sum(gre >= 1)),
+                "hist_edges": [round(float(e), 2) for e in edges], "hist": [int(h) for h in hist]}}
+    del oplans, ows
     fwd()  # leave the product's outputs in place for the parity check
     torch.cuda.synchronize(dev)
 
@@ -653,7 +690,7 @@ def main():
                 "fwd_bwd": fwd_bwd_line,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu, "cpu_transform_domain": cpu_fd, "plain_one_block_per_launch": plain,
-                "parity": parity, "variants": variants,
+                "parity": parity, "variants": variants, "ofse": ofse,
                 "device": props.name, "sms": sms}
         print(json.dumps(line), flush=True)
     if world > 1:

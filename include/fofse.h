@@ -80,6 +80,13 @@ enum { FOFSE_FP32 = 0,           /* the product: exact selection path and coeffi
                                     filtered kernel layout (kept for comparison).
                                     Needs the workspace's scratch; without it runs as
                                     FOFSE_FP32_FULLFF                                   */
+/* compensation of the projection coefficient */
+enum { FOFSE_COMP_CONSTANT = 0,  /* c = gamma p_u with the plan's constant gamma (Eq. 14):
+                                    FOFSE, the default                                  */
+       FOFSE_COMP_OFSE = 1 };    /* OFSE's compensation (Eq. 10-12): c = p_u / sum_l
+                                    (p_l / p_u) Khat[u, l]; with the DFT basis
+                                    Khat[u, l] = W[u - l] / W[0], so c = P[u]^2 / Q[u]
+                                    with Q[u] = sum_l P[l] W[u - l], gamma unused      */
 /* per-block status written to d_block_status */
 enum { FOFSE_BLK_OK = 0, FOFSE_BLK_NO_SUPPORT = 1, FOFSE_BLK_NONFINITE = 2 };
 
@@ -90,7 +97,8 @@ typedef struct {
 } fofse_block;
 
 /* One iteration of the selection path: canonical index u (0 <= u1, u2 < T)
- * and the coefficient c = gamma R_w[u] / W[0], rounded to FP32. */
+ * and the coefficient c = gamma R_w[u] / W[0] (OFSE plans: P[u]^2 / Q[u]),
+ * rounded to FP32. */
 typedef struct {
   int16_t u1, u2;
   float dc_re, dc_im;
@@ -119,6 +127,12 @@ fofse_status fofse_plan_set_support(fofse_plan plan, int shape);
 /* Arithmetic (FOFSE_FP32 default, FOFSE_FP64_VALIDATE, FOFSE_FP32_PLAIN,
  * FOFSE_FP32_FULLFF, FOFSE_FP32_FILTERED). */
 fofse_status fofse_plan_set_precision(fofse_plan plan, int precision);
+/* Compensation (FOFSE_COMP_*); default FOFSE_COMP_CONSTANT.  FOFSE_COMP_OFSE
+ * runs only with FOFSE_FP32 and a workspace (fofse_extrapolate_batch returns
+ * FOFSE_E_UNSUPPORTED otherwise) and has no backward (fofse_backward returns
+ * FOFSE_E_UNSUPPORTED: c is not linear in the samples).  It needs twice the
+ * forward scratch of the constant compensation.  FOFSE_E_ARG for other values. */
+fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation);
 /* Number of launch shapes (threads per block / resident blocks per SM) of the
  * plan's kernel for its current precision; 0 for a NULL plan. */
 int fofse_plan_variant_count(fofse_plan plan);
@@ -188,6 +202,28 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
                                      int32_t* d_block_status, void* d_workspace, void* stream);
 
 /*
+ * fofse_extrapolate_batch_gamma -- fofse_extrapolate_batch that also writes
+ * the compensation factor of every iteration, gamma_u = c_u / p_u (Eq. 13):
+ *   d_gamma   nullable; n_blocks x max_iters x 2 floats (re, im), the trace's
+ *             layout: the plan's constant gamma (im 0) for FOFSE_COMP_CONSTANT
+ *             plans, W[0] P[u] / Q[u] for FOFSE_COMP_OFSE plans (complex with
+ *             the complex DFT basis; the canonical member u of the pair).
+ *             Entries past a block's iteration count, and all entries of a
+ *             block that is not OK, are zero.
+ * A non-NULL d_gamma needs FOFSE_FP32 plans and a workspace
+ * (FOFSE_E_UNSUPPORTED otherwise).  Other arguments and returns as
+ * fofse_extrapolate_batch (which is this call with d_gamma = NULL).
+ */
+fofse_status fofse_extrapolate_batch_gamma(const fofse_plan* plans, int n_plans,
+                                           const fofse_block* d_blocks, int n_blocks,
+                                           const float* d_frame, const uint8_t* d_avail,
+                                           int height, int width, int pitch,
+                                           const float* d_rho_gamma, float* d_out_frame,
+                                           float* d_out_blocks, fofse_trace_entry* d_trace,
+                                           float* d_w0, int32_t* d_block_status,
+                                           float* d_gamma, void* d_workspace, void* stream);
+
+/*
  * fofse_extrapolate_batch_noalloc -- fofse_extrapolate_batch for callers that
  * cannot allocate device memory at all: code running where cudaMalloc is not
  * allowed (for example inside a host callback or under a custom allocator that
@@ -231,7 +267,8 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
  *                      as one kernel per block (slower on large batches).
  *                      Must not be shared with a call that may run at the
  *                      same time.
- * Not implemented for FOFSE_FP64_VALIDATE plans (FOFSE_E_UNSUPPORTED).
+ * Not implemented for FOFSE_FP64_VALIDATE plans nor for FOFSE_COMP_OFSE plans
+ * (FOFSE_E_UNSUPPORTED).
  */
 fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_block* d_blocks,
                             int n_blocks, const float* d_frame, const uint8_t* d_avail,

@@ -14,17 +14,21 @@ TRACE_DTYPE = np.dtype([("u1", "<i2"), ("u2", "<i2"), ("re", "<f4"), ("im", "<f4
 
 class Plan:
     """One block class: b x b lost blocks, support border, T x T FFT, rho_hat,
-    gamma and the number of iterations (paper Sec. 4 notation)."""
+    gamma and the number of iterations (paper Sec. 4 notation); compensation
+    0 = the constant gamma of Eq. 14 (FOFSE), 1 = OFSE's (Eq. 10-13)."""
 
-    def __init__(self, block, border, fft_size, rho, gamma, iters, support=0, precision="fp32"):
+    def __init__(self, block, border, fft_size, rho, gamma, iters, support=0, precision="fp32",
+                 compensation=0):
         self.block, self.border, self.fft_size = int(block), int(border), int(fft_size)
         self.rho, self.gamma, self.iters = float(rho), float(gamma), int(iters)
         self.support = int(support)
         self.precision = precision
+        self.compensation = int(compensation)
         self.handle = B.fofse_plan_create(block, border, fft_size, rho, gamma, iters)
         try:
             B.fofse_plan_set_support(self.handle, self.support)
             B.fofse_plan_set_precision(self.handle, B.PRECISIONS[precision])
+            B.fofse_plan_set_compensation(self.handle, self.compensation)
         except Exception:
             B.fofse_plan_destroy(self.handle)
             raise
@@ -32,7 +36,7 @@ class Plan:
     @classmethod
     def from_spec(cls, spec, precision="fp32"):
         return cls(spec.block, spec.border, spec.fft_size, spec.rho, spec.gamma, spec.iters,
-                   getattr(spec, "support", 0), precision)
+                   getattr(spec, "support", 0), precision, getattr(spec, "compensation", 0))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -53,6 +57,7 @@ class Result:
     w0: torch.Tensor           # (n,) float32
     status: torch.Tensor       # (n,) int32
     out_frame: torch.Tensor | None = None
+    gamma: torch.Tensor | None = None  # (n, imax, 2) float32: compensation factor per iteration
 
     def trace_numpy(self):
         return self.trace.cpu().numpy().view(TRACE_DTYPE).reshape(self.trace.shape[:2])
@@ -84,16 +89,25 @@ def workspace(plans, n_blocks, device):
 
 
 def extrapolate(plans, blocks, frame, avail, *, out_frame=None, with_trace=True, stream=None,
-                ws=None) -> Result:
+                ws=None, with_gamma=False) -> Result:
     """Run the forward pass of every block.  ``blocks``: (n, 3) int32 tensor on
     the device (y, x, plan index); ``frame`` float32 and ``avail`` uint8 (H, W)
-    tensors on the same device."""
+    tensors on the same device.  ``with_gamma`` also returns the compensation
+    factor of every iteration (FOFSE_FP32 plans)."""
     plans = list(plans)
     n = int(blocks.shape[0])
     ob, tr, w0, st = alloc_outputs(plans, n, frame.device, with_trace)
     if ws is None:
         ws = workspace(plans, n, frame.device)
-    B.fofse_extrapolate_batch([p.handle for p in plans], blocks, frame, avail, out_frame=out_frame,
+    handles = [p.handle for p in plans]
+    if with_gamma:
+        imax = max(p.iters for p in plans)
+        gm = torch.empty((n, imax, 2), dtype=torch.float32, device=frame.device)
+        B.fofse_extrapolate_batch_gamma(handles, blocks, frame, avail, out_frame=out_frame,
+                                        out_blocks=ob, trace=tr, w0=w0, status=st, gamma=gm,
+                                        workspace=ws, stream=stream)
+        return Result(ob, tr, w0, st, out_frame, gm)
+    B.fofse_extrapolate_batch(handles, blocks, frame, avail, out_frame=out_frame,
                               out_blocks=ob, trace=tr, w0=w0, status=st, workspace=ws,
                               stream=stream)
     return Result(ob, tr, w0, st, out_frame)

@@ -18,6 +18,7 @@ OK, E_ARG, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_STATE = range(7)
 SUPPORT_FULL, SUPPORT_CAUSAL_L = 0, 1
 FP32, FP64_VALIDATE, FP32_PLAIN, FP32_FULLFF, FP32_FILTERED = 0, 1, 2, 3, 4
 BLK_OK, BLK_NO_SUPPORT, BLK_NONFINITE, BLK_TIMEOUT = 0, 1, 2, 3
+COMP_CONSTANT, COMP_OFSE = 0, 1
 PRECISIONS = {"fp32": FP32, "fp64": FP64_VALIDATE, "fp32_plain": FP32_PLAIN,
               "fp32_fullff": FP32_FULLFF, "fp32_filtered": FP32_FILTERED}
 
@@ -64,6 +65,8 @@ def _declare(L):
     L.fofse_plan_set_support.restype = _i
     L.fofse_plan_set_precision.argtypes = [_vp, _i]
     L.fofse_plan_set_precision.restype = _i
+    L.fofse_plan_set_compensation.argtypes = [_vp, _i]
+    L.fofse_plan_set_compensation.restype = _i
     L.fofse_plan_variant_count.argtypes = [_vp]
     L.fofse_plan_variant_count.restype = _i
     L.fofse_plan_set_variant.argtypes = [_vp, _i]
@@ -75,6 +78,9 @@ def _declare(L):
     L.fofse_extrapolate_batch.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i,
                                           _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.fofse_extrapolate_batch.restype = _i
+    L.fofse_extrapolate_batch_gamma.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i,
+                                                _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.fofse_extrapolate_batch_gamma.restype = _i
     L.fofse_extrapolate_batch_noalloc.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i,
                                                   _i, _vp, _vp, _vp, _vp, _vp, _vp]
     L.fofse_extrapolate_batch_noalloc.restype = _i
@@ -151,6 +157,11 @@ def fofse_plan_set_precision(plan, precision):
            "fofse_plan_set_precision")
 
 
+def fofse_plan_set_compensation(plan, compensation):
+    _check(load().fofse_plan_set_compensation(ctypes.c_void_p(plan), int(compensation)),
+           "fofse_plan_set_compensation")
+
+
 def fofse_plan_variant_count(plan) -> int:
     return load().fofse_plan_variant_count(ctypes.c_void_p(plan))
 
@@ -187,6 +198,21 @@ def fofse_extrapolate_batch(plans, blocks, frame, avail, *, out_frame=None, out_
         _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
         _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(out_frame), _ptr(out_blocks), _ptr(trace),
         _ptr(w0), _ptr(status), _ptr(workspace), _stream(stream)), "fofse_extrapolate_batch")
+
+
+def fofse_extrapolate_batch_gamma(plans, blocks, frame, avail, *, out_frame=None, out_blocks=None,
+                                  trace=None, w0=None, status=None, gamma=None, workspace=None,
+                                  rho_gamma=None, stream=None):
+    """fofse_extrapolate_batch that also writes the compensation factor of
+    every iteration into ``gamma`` ((n, max_iters, 2) float32 device tensor)."""
+    H, W = frame.shape
+    pitch = frame.stride(0)
+    assert frame.stride(1) == 1 and avail.stride(1) == 1 and avail.stride(0) == pitch
+    _check(load().fofse_extrapolate_batch_gamma(
+        _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
+        _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(out_frame), _ptr(out_blocks), _ptr(trace),
+        _ptr(w0), _ptr(status), _ptr(gamma), _ptr(workspace), _stream(stream)),
+        "fofse_extrapolate_batch_gamma")
 
 
 def fofse_extrapolate_batch_noalloc(plans, blocks, frame, avail, *, out_frame=None, out_blocks=None,

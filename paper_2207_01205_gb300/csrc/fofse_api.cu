@@ -200,10 +200,13 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   }
   std::vector<float2> syn_f32(T);
   std::vector<double2> syn_f64(T);
+  std::vector<float4> syn_ff(T);
   for (int p = 0; p < T; ++p) {
     const double cr = std::cos(kTwoPi * p / T), ci = std::sin(kTwoPi * p / T);
-    syn_f32[p] = make_float2((float)cr, (float)ci);
+    const float hr = (float)cr, hi = (float)ci;
+    syn_f32[p] = make_float2(hr, hi);
     syn_f64[p] = make_double2(cr, ci);
+    syn_ff[p] = make_float4(hr, hi, (float)(cr - hr), (float)(ci - hi));
   }
 
   // one allocation, 256-byte aligned sections
@@ -216,7 +219,8 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   const size_t o_wff = sec(sizeof(float2) * N), o_w64 = sec(sizeof(double) * N),
                o_w32 = sec(sizeof(float) * N), o_tff = sec(sizeof(float4) * (T / 2)),
                o_t64 = sec(sizeof(double2) * (T / 2)), o_t32 = sec(sizeof(float2) * (T / 2)),
-               o_s32 = sec(sizeof(float2) * T), o_s64 = sec(sizeof(double2) * T);
+               o_s32 = sec(sizeof(float2) * T), o_s64 = sec(sizeof(double2) * T),
+               o_sff = sec(sizeof(float4) * T);
   const size_t total = off;
   std::vector<unsigned char> host(total, 0);
   std::memcpy(&host[o_wff], w_ff.data(), sizeof(float2) * N);
@@ -227,6 +231,7 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   std::memcpy(&host[o_t32], tw_f32.data(), sizeof(float2) * (T / 2));
   std::memcpy(&host[o_s32], syn_f32.data(), sizeof(float2) * T);
   std::memcpy(&host[o_s64], syn_f64.data(), sizeof(double2) * T);
+  std::memcpy(&host[o_sff], syn_ff.data(), sizeof(float4) * T);
 
   void* mem = nullptr;
   cudaError_t e = cudaMalloc(&mem, total);
@@ -251,6 +256,7 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   d.support = FOFSE_SUPPORT_FULL;
   d.precision = FOFSE_FP32;
   d.variant = 0;
+  d.compensation = FOFSE_COMP_CONSTANT;
   d.rho = rho;
   d.gamma = (double)gamma;
   d.gamma_h = gamma;
@@ -263,6 +269,7 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   d.tab.tw_f32 = reinterpret_cast<const float2*>(base + o_t32);
   d.tab.syn_f32 = reinterpret_cast<const float2*>(base + o_s32);
   d.tab.syn_f64 = reinterpret_cast<const double2*>(base + o_s64);
+  d.tab.syn_ff = reinterpret_cast<const float4*>(base + o_sff);
   p->mem = mem;
   cudaGetDevice(&p->device);
   *out = p;
@@ -272,6 +279,14 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
 fofse_status fofse_plan_set_support(fofse_plan plan, int shape) {
   if (!plan || (shape != FOFSE_SUPPORT_FULL && shape != FOFSE_SUPPORT_CAUSAL_L)) return FOFSE_E_ARG;
   plan->dev.support = shape;
+  return FOFSE_OK;
+}
+
+fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation) {
+  if (!plan || (compensation != FOFSE_COMP_CONSTANT && compensation != FOFSE_COMP_OFSE))
+    return FOFSE_E_ARG;
+  plan->dev.compensation = compensation;
+  if (plan->dev.variant >= forward_variant_count(plan->dev)) plan->dev.variant = 0;
   return FOFSE_OK;
 }
 
@@ -321,6 +336,20 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
                                      float* d_out_frame, float* d_out_blocks,
                                      fofse_trace_entry* d_trace, float* d_w0,
                                      int32_t* d_block_status, void* d_workspace, void* stream) {
+  return fofse_extrapolate_batch_gamma(plans, n_plans, d_blocks, n_blocks, d_frame, d_avail,
+                                       height, width, pitch, d_rho_gamma, d_out_frame,
+                                       d_out_blocks, d_trace, d_w0, d_block_status, nullptr,
+                                       d_workspace, stream);
+}
+
+fofse_status fofse_extrapolate_batch_gamma(const fofse_plan* plans, int n_plans,
+                                           const fofse_block* d_blocks, int n_blocks,
+                                           const float* d_frame, const uint8_t* d_avail,
+                                           int height, int width, int pitch,
+                                           const float* d_rho_gamma, float* d_out_frame,
+                                           float* d_out_blocks, fofse_trace_entry* d_trace,
+                                           float* d_w0, int32_t* d_block_status,
+                                           float* d_gamma, void* d_workspace, void* stream) {
   if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return FOFSE_E_ARG;
   if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail)) return FOFSE_E_ARG;
   if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
@@ -331,6 +360,13 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
     if (plans[i]->dev.precision != plans[0]->dev.precision) return FOFSE_E_ARG;
     bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
     imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
+  }
+  // OFSE and the per-iteration factors exist only in the register-blocked
+  // FOFSE_FP32 kernel, which needs the workspace
+  for (int i = 0; i < n_plans; ++i) {
+    const bool needs_f3 = d_gamma || plans[i]->dev.compensation == FOFSE_COMP_OFSE;
+    if (needs_f3 && (plans[i]->dev.precision != FOFSE_FP32 || !d_workspace))
+      return FOFSE_E_UNSUPPORTED;
   }
   if (n_blocks == 0) return FOFSE_OK;
   unsigned* err = err_word_ptr();
@@ -388,6 +424,7 @@ fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
     a.queue = queue ? queue + pi : nullptr;
     a.scratch = scratch_base;
     a.scratch_bytes = scratch_base ? scratch : 0;
+    a.gamma_out = reinterpret_cast<float2*>(d_gamma);
     a.box_f = round_up(P.Ls + 3, 4);
     a.box_a = round_up(P.Ls + 15, 16);
     CUtensorMap tf, ta;
@@ -425,8 +462,10 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
   for (int i = 0; i < n_plans; ++i) {
     if (!plans[i]) return FOFSE_E_ARG;
     if (plans[i]->dev.precision != plans[0]->dev.precision) return FOFSE_E_ARG;
-    // a 128 x 128 FFT needs 256 KB of scratch per SM, beyond the fixed array
+    // a 128 x 128 FFT needs 256 KB of scratch per SM, beyond the fixed array;
+    // OFSE needs the scratch of the register-blocked kernel
     if (forward_needs_scratch(plans[i]->dev)) return FOFSE_E_UNSUPPORTED;
+    if (plans[i]->dev.compensation == FOFSE_COMP_OFSE) return FOFSE_E_UNSUPPORTED;
     bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
     imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
   }
@@ -498,6 +537,7 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
   for (int i = 0; i < n_plans; ++i) {
     if (!plans[i]) return FOFSE_E_ARG;
     if (plans[i]->dev.precision == FOFSE_FP64_VALIDATE) return FOFSE_E_UNSUPPORTED;
+    if (plans[i]->dev.compensation == FOFSE_COMP_OFSE) return FOFSE_E_UNSUPPORTED;
     bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
     imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
   }

@@ -24,11 +24,13 @@ struct PlanTables {
   const float2* tw_f32;   // T/2
   const float2* syn_f32;  // T: (cos, sin)(2 pi p / T)
   const double2* syn_f64; // T
+  const float4* syn_ff;   // T: (cos.h, sin.h, cos.l, sin.l)(2 pi p / T)
 };
 
 struct PlanDev {
   int block, border, Ls, T, iters, support, precision;
   int variant;  // launch shape of the product kernel (0 = default)
+  int compensation;  // FOFSE_COMP_CONSTANT (Eq. 14) or FOFSE_COMP_OFSE (Eq. 10-13)
   float gamma_h, gamma_l;  // gamma as float pair
   double gamma;
   float rho;
@@ -57,6 +59,7 @@ struct FwdArgs {
   int* queue;            // work-queue counter of this plan (zeroed before the launch); may be null
   void* scratch;         // global scratch, one slot per persistent CTA (may be null)
   size_t scratch_bytes;  // bytes available at scratch
+  float2* gamma_out;     // nullable: compensation factor per iteration (trace layout)
 };
 
 struct BwdArgs {
@@ -99,5 +102,9 @@ cudaError_t launch_forward_f3(const FwdArgs& a, const CUtensorMap* tm_frame,
                               const CUtensorMap* tm_avail, cudaStream_t stream);
 size_t forward_f3_scratch_bytes(const PlanDev& p);
 int forward_f3_variant_count(const PlanDev& p);
+// The same kernel with OFSE's compensation (fofse_ofse.cu); one launch shape.
+cudaError_t launch_forward_ofse(const FwdArgs& a, const CUtensorMap* tm_frame,
+                                const CUtensorMap* tm_avail, cudaStream_t stream);
+size_t forward_ofse_scratch_bytes(const PlanDev& p);
 
 }  // namespace fofse

@@ -127,6 +127,13 @@ class PlanSpec:
     support: int = 0  # 0 = full frame around B, 1 = causal L shape (top/left)
     compensation: int = 0  # 0 = constant gamma (FOFSE, Eq. 14), 1 = OFSE's (Eq. 10-12)
 
+    def __post_init__(self):
+        # rho and gamma cross the C ABI as single-precision numbers: hold the
+        # single-precision values so that every consumer of the spec sees the
+        # same parameters
+        self.rho = float(np.float32(self.rho))
+        self.gamma = float(np.float32(self.gamma))
+
 
 @dataclasses.dataclass
 class Workload:

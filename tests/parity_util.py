@@ -15,13 +15,13 @@ def to_device(wl, device="cuda"):
     return frame, avail, blocks
 
 
-def run_gpu(wl, precision="fp32", out_frame=False):
+def run_gpu(wl, precision="fp32", out_frame=False, with_gamma=False):
     import torch
     from paper_2207_01205_gb300 import api
     plans = [api.Plan.from_spec(p, precision) for p in wl.plans]
     frame, avail, blocks = to_device(wl)
     of = frame.clone() if out_frame else None
-    res = api.extrapolate(plans, blocks, frame, avail, out_frame=of)
+    res = api.extrapolate(plans, blocks, frame, avail, out_frame=of, with_gamma=with_gamma)
     torch.cuda.synchronize()
     from paper_2207_01205_gb300 import binding
     binding.fofse_check()

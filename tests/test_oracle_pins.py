@@ -358,8 +358,9 @@ def test_batch_matches_single_area_calls_and_ignores_lost_content():
     assert np.array_equal(res.blocks, res2.blocks)
     for i, (y, x, _) in enumerate(wl.blocks):
         fL, aL = oracle.cut_area(wl.frame, wl.avail, y, x, 8, 8)
-        w = oracle.weights(8, 8, 0.8, aL)
-        one = oracle.extrapolate_area(fL, w, 32, 0.5, 20)
+        P = wl.plans[0]  # rho and gamma as the plan holds them (single precision)
+        w = oracle.weights(8, 8, P.rho, aL)
+        one = oracle.extrapolate_area(fL, w, 32, P.gamma, 20)
         assert res.status[i] == one.status
         assert np.array_equal(res.blocks[i], one.g[8:16, 8:16])
         assert np.array_equal(res.path[i], one.u)
