@@ -667,6 +667,38 @@ def main():
                 "below_0": int(np.sum(gre < 0)), "above_1": int(np.sum(gre >= 1)),
                 "hist_edges": [round(float(e), 2) for e in edges], "hist": [int(h) for h in hist]}}
     del oplans, ows
+
+    # ---- quality over iterations for several compensation factors (Fig. 4 and
+    # Fig. 5 analogues): PSNR over the lost samples after every iteration
+    # count, from the error-curve kernel; gamma = 1 is the uncompensated FSE ----
+    truth = torch.from_numpy(np.ascontiguousarray(wl.truth, dtype=np.float32)).to(dev)
+    imax = max(p.iters for p in wl.plans)
+    sse = torch.empty((n, imax), dtype=torch.float32, device=dev)
+    npx = sum(wl.plans[pi].block ** 2 for pi in wl.blocks[:, 2])
+    marks = [nu for nu in (1, 2, 5, 10, 20, 50, 100, 150, 200) if nu <= imax]
+    sweep = {}
+    curve_ms = None
+    for label, comp, g in [(f"gamma={g}", 0, g) for g in (0.1, 0.2, 0.3, 0.5, 0.7, 0.9, 1.0)] + [("ofse", 1, 0.5)]:
+        specs = [dataclasses.replace(p, gamma=g, compensation=comp) for p in wl.plans]
+        qplans = [api.Plan.from_spec(p, "fp32") for p in specs]
+        qws = api.workspace(qplans, n, dev)
+        qh = [p.handle for p in qplans]
+        binding.fofse_extrapolate_batch(qh, blocks, frame, avail, out_blocks=ob, trace=tr, w0=w0,
+                                        status=st, workspace=qws, stream=stream)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        binding.fofse_error_curve(qh, blocks, tr, truth, sse, stream=stream)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        curve_ms = c0.elapsed_time(c1)
+        psnr_nu = 10 * np.log10(255.0 ** 2 * npx / sse.double().sum(dim=0).cpu().numpy())
+        k = int(np.argmax(psnr_nu))
+        sweep[label] = {"psnr_db_at": {str(nu): round(float(psnr_nu[nu - 1]), 3) for nu in marks},
+                        "peak_db": round(float(psnr_nu[k]), 3), "peak_iteration": k + 1}
+        del qplans, qws
+    quality = {"what": "PSNR over the 804 lost blocks after nu iterations (synthetic frame), "
+                       "per compensation; gamma=1.0 is FSE without compensation",
+               "error_curve_kernel_ms": curve_ms, "curves": sweep}
     fwd()  # leave the product's outputs in place for the parity check
     torch.cuda.synchronize(dev)
 
@@ -690,7 +722,7 @@ def main():
                 "fwd_bwd": fwd_bwd_line,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu, "cpu_transform_domain": cpu_fd, "plain_one_block_per_launch": plain,
-                "parity": parity, "variants": variants, "ofse": ofse,
+                "parity": parity, "variants": variants, "ofse": ofse, "quality_sweep": quality,
                 "device": props.name, "sms": sms}
         print(json.dumps(line), flush=True)
     if world > 1:

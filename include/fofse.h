@@ -277,6 +277,26 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
                             const float* d_grad_blocks, float* d_grad_frame,
                             float* d_grad_rho_gamma, void* d_workspace, void* stream);
 
+/*
+ * fofse_error_curve -- the squared error of the extrapolation after every
+ * iteration count (the PSNR-over-iterations curves of Fig. 4 and Fig. 5):
+ *   d_trace       from fofse_extrapolate_batch with the same plans and blocks
+ *   d_truth       device float32 reference frame, height x width, `pitch`
+ *                 elements per row (the same geometry as the frame)
+ *   d_sse         n_blocks x max_iters floats: entry nu - 1 is the sum over B
+ *                 of (clip(B_hat_nu, 0, 255) - truth)^2, with B_hat_nu the
+ *                 model of Eq. 1 built from the first nu trace entries; zero
+ *                 past a block's iteration count.  PSNR over a set of blocks
+ *                 is 10 log10(255^2 N / sum of their entries) for N samples.
+ * The model is rebuilt from the trace's FP32 coefficients in FP32.  Blocks
+ * with side above 32 are not supported (FOFSE_E_UNSUPPORTED); argument errors
+ * as fofse_extrapolate_batch.  Asynchronous on `stream`.
+ */
+fofse_status fofse_error_curve(const fofse_plan* plans, int n_plans, const fofse_block* d_blocks,
+                               int n_blocks, const fofse_trace_entry* d_trace,
+                               const float* d_truth, int height, int width, int pitch,
+                               float* d_sse, void* stream);
+
 /* Synchronises `stream`, then reads and clears the device error word of the
  * current device: FOFSE_OK, FOFSE_E_TIMEOUT, or FOFSE_E_CUDA if the stream
  * reported an error. */

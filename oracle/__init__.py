@@ -92,6 +92,8 @@ def _declare(L):
     L.oracle_extrapolate_area_ofse.argtypes = [_c_int, _c_int, _dp, _dp, _c_int, _dp, _ip, _ip, _dp,
                                                _dp, _dp, _dp, _dp, _dp]
     L.oracle_extrapolate_area_ofse.restype = _c_int
+    L.oracle_error_curve.argtypes = [_c_int, _c_int, _c_int, _c_int, _ip, _ip, _dp, _dp, _c_int, _dp, _dp]
+    L.oracle_error_curve.restype = None
     L.oracle_batch_mode.restype = _c_int
     L.oracle_batch_adjoint.argtypes = [_fp, _u8p, _c_int, _c_int, _c_int, _ip, _c_int,
                                        ctypes.POINTER(OraclePlan), _c_int, _ip, _ip, _c_int, _dp,
@@ -202,6 +204,21 @@ def extrapolate_area_ofse(fL, wL, T: int, iters: int):
                                             _p(gr, _dp), _p(gi, _dp), _p(gap, _dp),
                                             ctypes.byref(w0))
     return AreaResult(st, g, np.stack([u1, u2], axis=1), dr + 1j * di, gap, w0.value), gr + 1j * gi
+
+
+def error_curve(Ls: int, T: int, block: int, border: int, path, dc, truth_B) -> np.ndarray:
+    """Squared error over B (model clipped to [0, 255]) after each iteration of
+    the given path and coefficients (Fig. 4 / Fig. 5 quantity)."""
+    path = np.ascontiguousarray(np.asarray(path).reshape(-1, 2), dtype=np.int32)
+    u1, u2 = np.ascontiguousarray(path[:, 0]), np.ascontiguousarray(path[:, 1])
+    dc = np.asarray(dc)
+    dr, di = _f64(dc.real), _f64(dc.imag)
+    tb = _f64(truth_B)
+    n = path.shape[0]
+    out = np.zeros(n)
+    lib().oracle_error_curve(Ls, T, block, border, _p(u1, _ip), _p(u2, _ip), _p(dr, _dp),
+                             _p(di, _dp), n, _p(tb, _dp), _p(out, _dp))
+    return out
 
 
 def replay_area(fL, wL, T: int, gamma: float, path) -> tuple:

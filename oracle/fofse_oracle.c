@@ -259,6 +259,38 @@ int oracle_extrapolate_area(int Ls, int T, const double* fL, const double* wL, d
 }
 
 /* -------------------------------------------------------------------------- */
+/* Error over the iterations (the PSNR-over-iterations curves, Fig. 4, Fig. 5) */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * The model of Eq. 1 rebuilt iteration by iteration from a selection path and
+ * its coefficients; after the nu-th iteration sse[nu - 1] = sum over B of
+ * (clip(g, 0, 255) - truth)^2, truthB the block x block reference samples of
+ * B (row-major), B at (border, border) inside L.
+ */
+void oracle_error_curve(int Ls, int T, int block, int border, const int* path_u1,
+                        const int* path_u2, const double* dc_re, const double* dc_im, int iters,
+                        const double* truthB, double* sse) {
+    double* c = (double*)malloc(sizeof(double) * T);
+    double* s = (double*)malloc(sizeof(double) * T);
+    double* g = (double*)calloc((size_t)Ls * Ls, sizeof(double));
+    twiddles(T, c, s);
+    for (int it = 0; it < iters; ++it) {
+        add_basis_pair(Ls, T, c, s, path_u1[it], path_u2[it], dc_re[it], dc_im[it], g);
+        double e = 0.0;
+        for (int bm = 0; bm < block; ++bm)
+            for (int bn = 0; bn < block; ++bn) {
+                double v = g[(border + bm) * Ls + border + bn];
+                v = v < 0.0 ? 0.0 : (v > 255.0 ? 255.0 : v);
+                double d = v - truthB[bm * block + bn];
+                e += d * d;
+            }
+        sse[it] = e;
+    }
+    free(c); free(s); free(g);
+}
+
+/* -------------------------------------------------------------------------- */
 /* OFSE's orthogonality deficiency compensation (Sec. 3, Eq. 10-12)            */
 /* -------------------------------------------------------------------------- */
 

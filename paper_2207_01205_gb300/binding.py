@@ -87,6 +87,8 @@ def _declare(L):
     L.fofse_backward.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i, _vp, _vp,
                                  _vp, _vp, _vp, _vp, _vp, _vp]
     L.fofse_backward.restype = _i
+    L.fofse_error_curve.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i, _vp, _vp]
+    L.fofse_error_curve.restype = _i
     L.fofse_check.argtypes = [_vp]
     L.fofse_check.restype = _i
     L.fofse_last_cuda_error.restype = _i
@@ -238,6 +240,17 @@ def fofse_backward(plans, blocks, frame, avail, trace, w0, grad_blocks, *, grad_
         _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
         _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(trace), _ptr(w0), _ptr(grad_blocks),
         _ptr(grad_frame), _ptr(grad_rho_gamma), _ptr(workspace), _stream(stream)), "fofse_backward")
+
+
+def fofse_error_curve(plans, blocks, trace, truth, sse, *, stream=None):
+    """Squared error over B after every iteration count into ``sse``
+    ((n, max_iters) float32 device tensor); ``truth`` (H, W) float32."""
+    H, W = truth.shape
+    pitch = truth.stride(0)
+    assert truth.stride(1) == 1
+    _check(load().fofse_error_curve(
+        _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(trace),
+        _ptr(truth), H, W, pitch, _ptr(sse), _stream(stream)), "fofse_error_curve")
 
 
 def fofse_last_cuda_error() -> int:

@@ -522,6 +522,41 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
   return FOFSE_OK;
 }
 
+fofse_status fofse_error_curve(const fofse_plan* plans, int n_plans, const fofse_block* d_blocks,
+                               int n_blocks, const fofse_trace_entry* d_trace,
+                               const float* d_truth, int height, int width, int pitch,
+                               float* d_sse, void* stream) {
+  if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return FOFSE_E_ARG;
+  if (n_blocks > 0 && (!d_blocks || !d_trace || !d_truth || !d_sse)) return FOFSE_E_ARG;
+  if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
+  int imax = 0;
+  for (int i = 0; i < n_plans; ++i) {
+    if (!plans[i]) return FOFSE_E_ARG;
+    if (plans[i]->dev.block > 32) return FOFSE_E_UNSUPPORTED;
+    imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
+  }
+  if (n_blocks == 0) return FOFSE_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int pi = 0; pi < n_plans; ++pi) {
+    CurveArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.plan = plans[pi]->dev;
+    a.plan_index = pi;
+    a.blocks = d_blocks;
+    a.n_blocks = n_blocks;
+    a.trace = d_trace;
+    a.trace_stride = imax;
+    a.truth = d_truth;
+    a.height = height;
+    a.width = width;
+    a.pitch = pitch;
+    a.sse = d_sse;
+    const cudaError_t e = launch_error_curve(a, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return FOFSE_OK;
+}
+
 fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_block* d_blocks,
                             int n_blocks, const float* d_frame, const uint8_t* d_avail,
                             int height, int width, int pitch, const float* d_rho_gamma,

@@ -87,6 +87,18 @@ struct BwdArgs {
   unsigned* cnt;     // n_blocks finished-CTA counters (zeroed before the call)
 };
 
+struct CurveArgs {
+  PlanDev plan;
+  int plan_index;
+  const fofse_block* blocks;
+  int n_blocks;
+  const fofse_trace_entry* trace;
+  int trace_stride;
+  const float* truth;
+  int height, width, pitch;
+  float* sse;  // n_blocks x trace_stride
+};
+
 // Launchers (one per translation unit).  Return cudaSuccess or the launch error.
 cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tm_frame,
                            const CUtensorMap* tm_avail, cudaStream_t stream);
@@ -96,6 +108,8 @@ size_t forward_scratch_bytes(const PlanDev& p);
 bool forward_needs_scratch(const PlanDev& p);
 int forward_variant_count(const PlanDev& p);
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t stream);
+// Squared error over B after each iteration count (fofse_curve.cu).
+cudaError_t launch_error_curve(const CurveArgs& a, cudaStream_t stream);
 // The register-blocked filtered-exact forward (fofse_fwd3.cu): launch (needs
 // scratch), the scratch it uses, and its number of launch shapes.
 cudaError_t launch_forward_f3(const FwdArgs& a, const CUtensorMap* tm_frame,

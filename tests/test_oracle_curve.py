@@ -1,0 +1,56 @@
+"""Pins of the oracle's error-over-iterations curve (the quantity behind the
+PSNR-over-iterations curves of Fig. 4 and Fig. 5): closed forms, explicit
+basis functions, clipping, and consistency with the final model."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_01205_gb300 import synth
+
+
+def test_last_entry_is_the_error_of_the_final_model():
+    wl = synth.single_block(seed=4)
+    fL, aL = oracle.cut_area(wl.frame, wl.avail, 16, 16, 16, 16)
+    w = oracle.weights(16, 16, 0.8, aL)
+    res = oracle.extrapolate_area(fL, w, 64, 0.5, 60)
+    truth = wl.truth[16:32, 16:32].astype(np.float64)
+    sse = oracle.error_curve(48, 64, 16, 16, res.u, res.dc, truth)
+    gB = np.clip(res.g[16:32, 16:32], 0, 255)
+    assert sse.shape == (60,)
+    assert sse[-1] == pytest.approx(np.sum((gB - truth) ** 2), rel=1e-12)
+    short = oracle.extrapolate_area(fL, w, 64, 0.5, 17)
+    gB = np.clip(short.g[16:32, 16:32], 0, 255)
+    assert sse[16] == pytest.approx(np.sum((gB - truth) ** 2), rel=1e-12)
+
+
+@pytest.mark.parametrize("gamma", [0.2, 0.5, 1.0])
+def test_constant_signal_closed_form(gamma):
+    """f = c on A and truth = c on B: g = c (1 - (1 - gamma)^nu) on B, so the
+    squared error after nu iterations is b^2 (c (1 - gamma)^nu)^2."""
+    b, br, T = 8, 8, 32
+    Ls = b + 2 * br
+    w = oracle.weights(b, br, 0.8, np.ones((Ls, Ls), dtype=np.uint8))
+    c = 120.0
+    res = oracle.extrapolate_area(np.full((Ls, Ls), c), w, T, gamma, 12)
+    sse = oracle.error_curve(Ls, T, b, br, res.u, res.dc, np.full((b, b), c))
+    nu = np.arange(1, 13)
+    np.testing.assert_allclose(sse, b * b * (c * (1 - gamma) ** nu) ** 2, rtol=1e-9, atol=1e-9)
+
+
+def test_first_entry_by_explicit_basis_functions_and_clipping():
+    """One pair (u, -u) with coefficient c adds 2 Re(c phi_u) on L (c phi_u for
+    a self-conjugate u); values are clipped to [0, 255] before the error."""
+    b, br, T = 6, 5, 16
+    Ls = b + 2 * br
+    m, n = np.meshgrid(np.arange(Ls), np.arange(Ls), indexing="ij")
+    rng = np.random.default_rng(3)
+    truth = rng.uniform(0, 255, size=(b, b))
+    path = np.array([[3, 5], [0, 0], [8, 8]])
+    dc = np.array([40.0 - 70.0j, 300.0, -500.0])
+    sse = oracle.error_curve(Ls, T, b, br, path, dc, truth)
+    g = 2 * np.real(dc[0] * np.exp(2j * np.pi * (3 * m + 5 * n) / T))
+    assert sse[0] == pytest.approx(np.sum((np.clip(g[br:br + b, br:br + b], 0, 255) - truth) ** 2), rel=1e-12)
+    g = g + 300.0
+    assert sse[1] == pytest.approx(np.sum((np.clip(g[br:br + b, br:br + b], 0, 255) - truth) ** 2), rel=1e-12)
+    g = g - 500.0 * np.real(np.exp(2j * np.pi * (8 * m + 8 * n) / T))   # (-1)^(m+n)
+    assert sse[2] == pytest.approx(np.sum((np.clip(g[br:br + b, br:br + b], 0, 255) - truth) ** 2), rel=1e-12)
