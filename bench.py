@@ -41,6 +41,11 @@ L2_FLUSH_BYTES = 512 << 20
 # i terms of about 66 FP32 operations (two float-float complex products and a
 # float-float accumulation).
 OPS_PER_BIN_ITER = 14
+# DRAM bytes of one launch of the product kernel on the 1080p batch, launch
+# shape 0, from an ncu capture (dram__bytes_read.sum 9.04 MB +
+# dram__bytes_write.sum 62.09 MB: the write-back of the per-CTA scratch, not
+# algorithmic bytes; the kernel is ALU-bound)
+F3_TRAFFIC_BYTES_1080P = 71.13e6
 SMEM_BYTES_PER_BIN_ITER = 16
 OPS_PER_RECURRENCE_TERM = 66
 FP32_LANES_PER_SM = 128
@@ -599,7 +604,9 @@ def main():
     smem_peak = sms * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                 "unit": "Tops/s (FP32 lane operations)", "frac": achieved / alu_peak,
-                "traffic": None, "kernel": f"fofse_forward_f3_kernel<64,...> (launch shape variant {variant})",
+                "traffic": F3_TRAFFIC_BYTES_1080P if variant == 0 else None,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "kernel": f"fofse_forward_f3_kernel<64,...> (launch shape variant {variant})",
                 "work_per_launch": f"{ops:.4g} FP32 ops ({OPS_PER_BIN_ITER}/bin-iteration + "
                                    f"{OPS_PER_RECURRENCE_TERM}/recurrence term)",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (sampled)",
