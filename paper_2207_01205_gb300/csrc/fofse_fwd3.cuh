@@ -60,7 +60,8 @@ template <int T, int NT> struct F3 {
   static constexpr size_t wtot_off = red_off + 32 * NW;                    // int [NW]
   static constexpr size_t list_off = (wtot_off + 4 * NW + 15) & ~size_t(15);  // int4 [LIST]
   static constexpr size_t ww_off = list_off + 16 * LIST;                   // float4 [NW], int2 [NW]
-  static constexpr size_t trc_off = (ww_off + 24 * NW + 15) & ~size_t(15);  // float4 [iters]
+  static constexpr size_t nd_off = ww_off + 24 * NW;                       // int: terms in the list
+  static constexpr size_t trc_off = (nd_off + 4 + 15) & ~size_t(15);       // float4 [iters]
   __host__ __device__ static size_t try_off(int iters) { return trc_off + 16 * (size_t)iters; }
   __host__ __device__ static size_t bytes(int iters) {  // + alignment slack
     return 128 + try_off(iters) + 2 * (((size_t)iters + 7) & ~size_t(7));
@@ -303,8 +304,15 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   int2* wwc = reinterpret_cast<int2*>(dsm + G::ww_off + 16 * NW);
   const PlanDev& P = args.plan;
   const int iters = P.iters;
+  // The recurrence's terms: one entry per distinct selected index, in order
+  // of first selection, with the sum of that index's coefficients (float-float,
+  // canonical orientation).  A pair picked again adds to its entry, so the
+  // exact recurrence sums over the distinct indices (about 40 % of the
+  // iterations on natural content) instead of over every earlier iteration.
   float4* trC = reinterpret_cast<float4*>(dsm + G::trc_off);
   short* trY = reinterpret_cast<short*>(dsm + G::try_off(iters));
+  int* nd_s = reinterpret_cast<int*>(dsm + G::nd_off);
+  int nd = 0;  // entries in the list (warp 0 maintains it; the others read it each iteration)
   float2* Zg = reinterpret_cast<float2*>(cta_scratch);
   float4* Rx = reinterpret_cast<float4*>(cta_scratch + G::z_bytes);
   // OFSE: the packed FFT of w^2 f + j w^2, then the exact V = DFT(w^2) (the
@@ -451,9 +459,10 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
         const int ldr = __ffs(hold) - 1;
         const unsigned wm2 = __reduce_max_sync(kFull, lane == ldr ? m2k : m1k);
         uint4* ts = t2s + (it & 1) * NW;
-        if (lane == 0) ts[warp] = make_uint4(wm1, wm2, (unsigned)(warp * 32 + ldr), 0u);
+        if (lane == 0) ts[warp] = make_uint4(wm1, wm2, (unsigned)(warp * 32 + ldr), (unsigned)nd);
         __syncthreads();
         uint4 g = ts[0];
+        nd = (int)g.w;  // warp 0's count, after its update of the previous iteration
 #pragma unroll
         for (int w = 1; w < NW; ++w) {
           const uint4 o = ts[w];
@@ -504,8 +513,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           long long sre = 0, sim = 0;
           long long Sr = 0, Si = 0;
           if constexpr (NW <= 4) {
-            if (warp * 32 < it) {  // warp-uniform: this warp holds terms
-              recur_fixed<T>(Whi, Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
+            if (warp * 32 < nd) {  // warp-uniform: this warp holds terms
+              recur_fixed<T>(Whi, Zg, trY, trC, wk1 * T2 + wk2, tid, nd, NT, scale, sre, sim);
               warp_sum64(sre, sim);
             }
             if (lane == 0) red[warp] = make_longlong2(sre, sim);
@@ -517,8 +526,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               Si += v.y;
             }
           } else {
-            if (warp * 32 < it) {
-              recur_fixed<T>(Whi, Zg, trY, trC, wk1 * T2 + wk2, tid, it, NT, scale, sre, sim);
+            if (warp * 32 < nd) {
+              recur_fixed<T>(Whi, Zg, trY, trC, wk1 * T2 + wk2, tid, nd, NT, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
             }
@@ -577,7 +586,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               const int4 e = list[c];
               const float4 r0 = Rx[e.z];
               long long sre = 0, sim = 0;
-              recur_fixed<T>(Whi, Zg, trY, trC, e.x, lane, it, 32, scale, sre, sim);
+              recur_fixed<T>(Whi, Zg, trY, trC, e.x, lane, nd, 32, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
               const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
@@ -633,8 +642,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           longlong2* red2 = red + NW;
           long long sre = 0, sim = 0, Sr = 0, Si = 0;
           if constexpr (NW <= 4) {
-            if (warp * 32 < it) {
-              recur_fixed<T, true>(Whi, Vg, trY, trC, xw, tid, it, NT, scale, sre, sim);
+            if (warp * 32 < nd) {
+              recur_fixed<T, true>(Whi, Vg, trY, trC, xw, tid, nd, NT, scale, sre, sim);
               warp_sum64(sre, sim);
             }
             if (lane == 0) red2[warp] = make_longlong2(sre, sim);
@@ -646,8 +655,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               Si += v.y;
             }
           } else {
-            if (warp * 32 < it) {
-              recur_fixed<T, true>(Whi, Vg, trY, trC, xw, tid, it, NT, scale, sre, sim);
+            if (warp * 32 < nd) {
+              recur_fixed<T, true>(Whi, Vg, trY, trC, xw, tid, nd, NT, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
             }
@@ -678,10 +687,41 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
             args.gamma_out[(size_t)blk * args.trace_stride + it] = mir ? make_float2(gm.x, -gm.y) : gm;
           }
         }
-        if (tid == 0) {
-          trY[it] = (short)(u1 * T2 + u2);
-          trC[it] = mir ? make_float4(c.re.h, c.re.l, -c.im.h, -c.im.l)
-                        : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
+        // ---- record: the trace entry, and the term of the recurrence ----
+        // (every read of the list in this iteration lies before a barrier
+        // that precedes this update)
+        if (warp == 0) {
+          const float4 cc = mir ? make_float4(c.re.h, c.re.l, -c.im.h, -c.im.l)
+                                : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
+          const short y = (short)(u1 * T2 + u2);
+          int pos = -1;
+          for (int j0 = 0; j0 < nd; j0 += 32) {
+            const int j = j0 + lane;
+            const unsigned hit = __ballot_sync(kFull, j < nd && trY[j] == y);
+            if (hit) {
+              pos = j0 + __ffs(hit) - 1;
+              break;
+            }
+          }
+          if (lane == 0) {
+            if (pos >= 0) {
+              const float4 o = trC[pos];
+              const ff sr = ff_add(ff{o.x, o.y}, ff{cc.x, cc.y}), si = ff_add(ff{o.z, o.w}, ff{cc.z, cc.w});
+              trC[pos] = make_float4(sr.h, sr.l, si.h, si.l);
+            } else {
+              trY[nd] = y;
+              trC[nd] = cc;
+            }
+            if (args.trace) {
+              fofse_trace_entry e;
+              e.u1 = (int16_t)u1;
+              e.u2 = (int16_t)u2;
+              e.dc_re = cc.x;
+              e.dc_im = cc.z;
+              args.trace[(size_t)blk * args.trace_stride + it] = e;
+            }
+          }
+          if (pos < 0) ++nd;
         }
         p = c.re.h;
         q = c.im.h;
@@ -746,11 +786,10 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
       // the rounding of R~ (u |R~| <= u (max|R32| + 2 |c| W[0]) after this
       // iteration's update) is added with the next increment.
       {
-        ff Cs = {0.f, 0.f};
-        for (int j = 0; j < it; ++j) {
-          const float4 c4 = trC[j];
-          Cs = ff_add(Cs, ff{c4.x, c4.y});
-        }
+        // every earlier pick was the DC bin: its single list entry holds the
+        // sum C (the entry is not written in this iteration)
+        const float4 c0 = trC[0];
+        const ff Cs = {c0.x, c0.y};
 #pragma unroll
         for (int i = 0; i <= NB; ++i) {
           if (i == NB && tid >= 2) break;
@@ -815,10 +854,12 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
       ++it;
     }
   }
+  if (tid == 0) *nd_s = nd;  // thread 0 is in warp 0, which holds the count
   __syncthreads();
 
   // ---- synthesis of B (Eq. 1) from the exact coefficients; outputs ----------
   const int nIt = (st == FOFSE_BLK_OK) ? iters : 0;
+  const int nTerms = (st == FOFSE_BLK_OK) ? *nd_s : 0;
   const int ld = args.out_ld;
   const float2* syn = P.tab.syn_f32;
   for (int pidx = tid; pidx < ld * ld; pidx += NT) {
@@ -828,7 +869,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
       const int m = br + bm, n = br + bn;
       if constexpr (!OFSE) {
         float acc = 0.f;
-        for (int i = 0; i < nIt; ++i) {
+        for (int i = 0; i < nTerms; ++i) {
           const int yy = trY[i];
           const int a1 = yy >> (LOGT + 1), a2 = yy & (T2 - 1);
           const float4 c4 = trC[i];
@@ -842,7 +883,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
         // to tens), so the FP32 sum would lose more than the output
         // tolerance: float-float terms and sum
         ff acc = {0.f, 0.f};
-        for (int i = 0; i < nIt; ++i) {
+        for (int i = 0; i < nTerms; ++i) {
           const int yy = trY[i];
           const int a1 = yy >> (LOGT + 1), a2 = yy & (T2 - 1);
           const float4 c4 = trC[i];
@@ -861,20 +902,11 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
     }
     if (args.out_blocks) args.out_blocks[(size_t)blk * args.out_stride + pidx] = v;
   }
-  if (args.trace) {
-    for (int i = tid; i < args.trace_stride; i += NT) {
+  if (args.trace) {  // entries of the iterations were written as they ran
+    for (int i = nIt + tid; i < args.trace_stride; i += NT) {
       fofse_trace_entry e;
-      if (i < nIt) {
-        const int yy = trY[i];
-        const float4 c4 = trC[i];
-        e.u1 = (int16_t)(yy >> (LOGT + 1));
-        e.u2 = (int16_t)(yy & (T2 - 1));
-        e.dc_re = c4.x;
-        e.dc_im = c4.z;
-      } else {
-        e.u1 = e.u2 = 0;
-        e.dc_re = e.dc_im = 0.f;
-      }
+      e.u1 = e.u2 = 0;
+      e.dc_re = e.dc_im = 0.f;
       args.trace[(size_t)blk * args.trace_stride + i] = e;
     }
   }
