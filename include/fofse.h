@@ -113,8 +113,11 @@ typedef struct {
  *   rho       rho_hat of Eq. 15, 0 < rho <= 1
  *   gamma     constant compensation factor of Eq. 14, 0 < gamma <= 1
  *   iters     number of iterations I, 1 <= I <= 4096
- * Builds the plan's constant tables (rho^dist in FP64, split into float pairs;
- * DFT twiddles from integer phases) in device memory of the current device.
+ * Builds the plan's constant tables in device memory of the current device:
+ * distances to the centre of B and DFT twiddles (from integer phases) on the
+ * host in FP64, the weights rho^dist by a kernel (FP64, also split into float
+ * pairs and rounded to float), after which it synchronises the legacy default
+ * stream (so not while a CUDA graph is being captured).
  * Returns FOFSE_E_ARG for invalid values, FOFSE_E_UNSUPPORTED for a valid but
  * unimplemented fft_size, FOFSE_E_NOMEM / FOFSE_E_CUDA if the tables cannot
  * be allocated.  *out is set only on FOFSE_OK.  Plans are immutable during a
@@ -141,13 +144,16 @@ int fofse_plan_variant_count(fofse_plan plan);
  * to the rounding of float-float sums.  FOFSE_E_ARG otherwise.  Changing the
  * precision resets an out-of-range variant to 0. */
 fofse_status fofse_plan_set_variant(fofse_plan plan, int variant);
-/* Frees the plan's tables (synchronises the device).  NULL is ignored. */
+/* Frees the plan's tables (synchronises the device, so not while a CUDA graph
+ * is being captured on it).  NULL is ignored. */
 void fofse_plan_destroy(fofse_plan plan);
 
 /*
  * fofse_workspace_bytes -- device scratch for fofse_extrapolate_batch and
  * fofse_backward with these plans and n_blocks blocks on the current device;
- * the larger of the two needs (the calls never use it at the same time).
+ * the weight tables of a call with device-side (rho, gamma) (20 bytes per
+ * sample of L per plan), then the larger of the two calls' own needs (the
+ * calls never use it at the same time).
  * Forward: 256 bytes of work-queue counters (one per plan, zeroed by every
  * call) plus one slot per resident CTA of the largest plan kernel: the block's
  * FFT buffer, then its exact W, and its exact initial spectrum (FOFSE_FP32:
@@ -166,8 +172,16 @@ size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks)
  *   d_frame, d_avail   device frame (float32) and availability (uint8),
  *                      height x width, `pitch` elements per row; the values of
  *                      unavailable samples are never read into the arithmetic
- *   d_rho_gamma        must be NULL (device-side overrides are not implemented;
- *                      FOFSE_E_UNSUPPORTED otherwise)
+ *   d_rho_gamma        nullable; n_plans x 2 floats in device memory, (rho, gamma)
+ *                      of each plan for this call in place of the plan's own
+ *                      values (tuning loops and CUDA graphs that change them
+ *                      without a host round trip).  The weights rho^dist are
+ *                      rebuilt on the device at the start of the call (into
+ *                      the workspace, which is then required: FOFSE_E_ARG
+ *                      without it).  A value out of range (rho or gamma not
+ *                      in (0, 1], NaN) gives that plan's blocks status
+ *                      FOFSE_BLK_NONFINITE and makes fofse_check return
+ *                      FOFSE_E_ARG.
  *   d_out_frame        nullable; B_hat is written into it at each block (other
  *                      samples untouched); may alias d_frame only if no block's
  *                      L overlaps another block's B
@@ -256,6 +270,8 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
 /*
  * fofse_backward -- adjoint of fofse_extrapolate_batch with the selection path
  * frozen (the map from the support samples to B_hat is then linear).
+ *   d_rho_gamma        nullable; as in fofse_extrapolate_batch (the same values
+ *                      as the forward call), needs the workspace
  *   d_trace, d_w0      from the forward call with the same inputs
  *   d_grad_blocks      dloss/dB_hat, n_blocks x bmax x bmax (as d_out_blocks)
  *   d_grad_frame       nullable; dloss/df ACCUMULATED (+=) at every sample of A
@@ -298,8 +314,9 @@ fofse_status fofse_error_curve(const fofse_plan* plans, int n_plans, const fofse
                                float* d_sse, void* stream);
 
 /* Synchronises `stream`, then reads and clears the device error word of the
- * current device: FOFSE_OK, FOFSE_E_TIMEOUT, or FOFSE_E_CUDA if the stream
- * reported an error. */
+ * current device: FOFSE_OK, FOFSE_E_TIMEOUT (a bounded wait ran out),
+ * FOFSE_E_ARG (a device-side rho / gamma was out of range), or FOFSE_E_CUDA if
+ * the stream reported an error. */
 fofse_status fofse_check(void* stream);
 
 /* The cudaError_t value behind the most recent FOFSE_E_CUDA returned to the

@@ -11,6 +11,28 @@ from . import binding as B
 
 TRACE_DTYPE = np.dtype([("u1", "<i2"), ("u2", "<i2"), ("re", "<f4"), ("im", "<f4")])
 
+# Plans released while a CUDA graph is being captured (for example by the
+# garbage collector, inside the capture) are destroyed later: destroying a
+# plan synchronises the device and frees memory, which would invalidate the
+# capture.
+_deferred = []
+
+
+def _capturing() -> bool:
+    try:
+        return bool(torch.cuda.is_available() and torch.cuda.is_current_stream_capturing())
+    except Exception:
+        return False
+
+
+def _release(handle):
+    if _capturing():
+        _deferred.append(handle)
+        return
+    while _deferred:
+        B.fofse_plan_destroy(_deferred.pop())
+    B.fofse_plan_destroy(handle)
+
 
 class Plan:
     """One block class: b x b lost blocks, support border, T x T FFT, rho_hat,
@@ -24,6 +46,8 @@ class Plan:
         self.support = int(support)
         self.precision = precision
         self.compensation = int(compensation)
+        while _deferred and not _capturing():
+            B.fofse_plan_destroy(_deferred.pop())
         self.handle = B.fofse_plan_create(block, border, fft_size, rho, gamma, iters)
         try:
             B.fofse_plan_set_support(self.handle, self.support)
@@ -39,9 +63,10 @@ class Plan:
                    getattr(spec, "support", 0), precision, getattr(spec, "compensation", 0))
 
     def close(self):
-        if getattr(self, "handle", None):
-            B.fofse_plan_destroy(self.handle)
+        h = getattr(self, "handle", None)
+        if h:
             self.handle = None
+            _release(h)
 
     def __del__(self):
         try:
@@ -89,11 +114,13 @@ def workspace(plans, n_blocks, device):
 
 
 def extrapolate(plans, blocks, frame, avail, *, out_frame=None, with_trace=True, stream=None,
-                ws=None, with_gamma=False) -> Result:
+                ws=None, with_gamma=False, rho_gamma=None) -> Result:
     """Run the forward pass of every block.  ``blocks``: (n, 3) int32 tensor on
     the device (y, x, plan index); ``frame`` float32 and ``avail`` uint8 (H, W)
     tensors on the same device.  ``with_gamma`` also returns the compensation
-    factor of every iteration (FOFSE_FP32 plans)."""
+    factor of every iteration (FOFSE_FP32 plans).  ``rho_gamma``: optional
+    (n_plans, 2) float32 device tensor of (rho, gamma) per plan for this call
+    (read on the device; no host round trip)."""
     plans = list(plans)
     n = int(blocks.shape[0])
     ob, tr, w0, st = alloc_outputs(plans, n, frame.device, with_trace)
@@ -105,9 +132,9 @@ def extrapolate(plans, blocks, frame, avail, *, out_frame=None, with_trace=True,
         gm = torch.empty((n, imax, 2), dtype=torch.float32, device=frame.device)
         B.fofse_extrapolate_batch_gamma(handles, blocks, frame, avail, out_frame=out_frame,
                                         out_blocks=ob, trace=tr, w0=w0, status=st, gamma=gm,
-                                        workspace=ws, stream=stream)
+                                        workspace=ws, rho_gamma=rho_gamma, stream=stream)
         return Result(ob, tr, w0, st, out_frame, gm)
     B.fofse_extrapolate_batch(handles, blocks, frame, avail, out_frame=out_frame,
                               out_blocks=ob, trace=tr, w0=w0, status=st, workspace=ws,
-                              stream=stream)
+                              rho_gamma=rho_gamma, stream=stream)
     return Result(ob, tr, w0, st, out_frame)

@@ -16,6 +16,33 @@
 
 using namespace fofse;
 
+namespace fofse {
+
+__global__ void fofse_plan_weights_kernel(const double* dist, int n, const float* rho_gamma,
+                                          float2* w_ff, double* w_f64, float* w_f32,
+                                          unsigned* err) {
+  const float rho = rho_gamma[0], gamma = rho_gamma[1];
+  const bool ok = rho > 0.f && rho <= 1.f && gamma > 0.f && gamma <= 1.f;  // false for NaN
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && !ok) atomicOr(err, kErrParam);
+  if (i >= n) return;
+  const double w = ok ? pow((double)rho, dist[i]) : __longlong_as_double(0x7ff8000000000000LL);  // Eq. 15
+  const float hi = (float)w;
+  w_ff[i] = make_float2(hi, (float)(w - (double)hi));
+  w_f64[i] = w;
+  w_f32[i] = hi;
+}
+
+cudaError_t launch_plan_weights(const PlanDev& p, const float* rho_gamma, float2* w_ff,
+                                double* w_f64, float* w_f32, unsigned* err, cudaStream_t s) {
+  const int n = p.Ls * p.Ls;
+  fofse_plan_weights_kernel<<<(n + 255) / 256, 256, 0, s>>>(p.tab.dist, n, rho_gamma, w_ff, w_f64,
+                                                            w_f32, err);
+  return cudaGetLastError();
+}
+
+}  // namespace fofse
+
 struct fofse_plan_s {
   PlanDev dev;   // scalars + device table pointers
   void* mem;     // one device allocation holding every table
@@ -133,6 +160,40 @@ struct BwdLayout {
   }
 };
 
+// Device-side (rho, gamma): per plan, the three weight tables rebuilt for the
+// call sit at the start of the workspace, before the forward or backward part.
+size_t override_bytes(const fofse_plan* plans, int n_plans) {
+  size_t b = 0;
+  for (int i = 0; i < n_plans; ++i) {
+    const size_t N = (size_t)plans[i]->dev.Ls * plans[i]->dev.Ls;
+    b += align256(N * sizeof(float2)) + align256(N * sizeof(double)) + align256(N * sizeof(float));
+  }
+  return b;
+}
+
+// Points plan `pi`'s weight tables at its part of the override region and
+// queues their rebuild from d_rho_gamma[2 pi], [2 pi + 1] on `s`.
+cudaError_t apply_override(const fofse_plan* plans, int pi, const float* d_rho_gamma,
+                           unsigned char* region, unsigned* err, PlanDev& P, cudaStream_t s) {
+  size_t off = 0;
+  for (int i = 0; i < pi; ++i) {
+    const size_t N = (size_t)plans[i]->dev.Ls * plans[i]->dev.Ls;
+    off += align256(N * sizeof(float2)) + align256(N * sizeof(double)) + align256(N * sizeof(float));
+  }
+  const size_t N = (size_t)P.Ls * P.Ls;
+  float2* wff = reinterpret_cast<float2*>(region + off);
+  double* w64 = reinterpret_cast<double*>(region + off + align256(N * sizeof(float2)));
+  float* w32 = reinterpret_cast<float*>(region + off + align256(N * sizeof(float2)) +
+                                        align256(N * sizeof(double)));
+  const float* rg = d_rho_gamma + 2 * pi;
+  const cudaError_t e = launch_plan_weights(P, rg, wff, w64, w32, err, s);
+  P.tab.w_ff = wff;
+  P.tab.w_f64 = w64;
+  P.tab.w_f32 = w32;
+  P.rho_gamma_dev = rg;
+  return e;
+}
+
 // Plans run one after another on the stream and share one scratch region.
 size_t scratch_bytes(const fofse_plan* plans, int n_plans) {
   size_t m = 0;
@@ -174,20 +235,14 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   const int T = fft_size;
   const int N = Ls * Ls;
 
-  // host tables in FP64, split or rounded for each back-end
-  std::vector<float2> w_ff(N);
-  std::vector<double> w_f64(N);
-  std::vector<float> w_f32(N);
+  // distances to the centre of B in FP64 (Eq. 15); the weights rho^dist are
+  // built from them on the device (the same kernel rebuilds them for a call
+  // that passes rho and gamma in device memory)
+  std::vector<double> dist(N);
   const double c = border + (block - 1) / 2.0;
   for (int m = 0; m < Ls; ++m)
-    for (int n = 0; n < Ls; ++n) {
-      const double d = std::sqrt((m - c) * (m - c) + (n - c) * (n - c));
-      const double w = std::pow((double)rho, d);  // Eq. 15
-      const float hi = (float)w;
-      w_ff[m * Ls + n] = make_float2(hi, (float)(w - (double)hi));
-      w_f64[m * Ls + n] = w;
-      w_f32[m * Ls + n] = hi;
-    }
+    for (int n = 0; n < Ls; ++n)
+      dist[m * Ls + n] = std::sqrt((m - c) * (m - c) + (n - c) * (n - c));
   std::vector<float4> tw_ff(T / 2);
   std::vector<double2> tw_f64(T / 2);
   std::vector<float2> tw_f32(T / 2);
@@ -220,12 +275,13 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
                o_w32 = sec(sizeof(float) * N), o_tff = sec(sizeof(float4) * (T / 2)),
                o_t64 = sec(sizeof(double2) * (T / 2)), o_t32 = sec(sizeof(float2) * (T / 2)),
                o_s32 = sec(sizeof(float2) * T), o_s64 = sec(sizeof(double2) * T),
-               o_sff = sec(sizeof(float4) * T);
+               o_sff = sec(sizeof(float4) * T), o_dist = sec(sizeof(double) * N),
+               o_rg = sec(sizeof(float2));
   const size_t total = off;
   std::vector<unsigned char> host(total, 0);
-  std::memcpy(&host[o_wff], w_ff.data(), sizeof(float2) * N);
-  std::memcpy(&host[o_w64], w_f64.data(), sizeof(double) * N);
-  std::memcpy(&host[o_w32], w_f32.data(), sizeof(float) * N);
+  std::memcpy(&host[o_dist], dist.data(), sizeof(double) * N);
+  const float2 rg = make_float2(rho, gamma);
+  std::memcpy(&host[o_rg], &rg, sizeof(float2));
   std::memcpy(&host[o_tff], tw_ff.data(), sizeof(float4) * (T / 2));
   std::memcpy(&host[o_t64], tw_f64.data(), sizeof(double2) * (T / 2));
   std::memcpy(&host[o_t32], tw_f32.data(), sizeof(float2) * (T / 2));
@@ -270,6 +326,23 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   d.tab.syn_f32 = reinterpret_cast<const float2*>(base + o_s32);
   d.tab.syn_f64 = reinterpret_cast<const double2*>(base + o_s64);
   d.tab.syn_ff = reinterpret_cast<const float4*>(base + o_sff);
+  d.tab.dist = reinterpret_cast<const double*>(base + o_dist);
+  d.rho_gamma_dev = nullptr;
+  {
+    unsigned* err = err_word_ptr();
+    cudaError_t e2 = err ? cudaSuccess : cudaGetLastError();
+    if (e2 == cudaSuccess)
+      e2 = launch_plan_weights(d, reinterpret_cast<const float*>(base + o_rg),
+                               reinterpret_cast<float2*>(base + o_wff),
+                               reinterpret_cast<double*>(base + o_w64),
+                               reinterpret_cast<float*>(base + o_w32), err, 0);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(0);
+    if (e2 != cudaSuccess) {
+      cudaFree(mem);
+      delete p;
+      return cuda_fail(e2);
+    }
+  }
   p->mem = mem;
   cudaGetDevice(&p->device);
   *out = p;
@@ -326,7 +399,7 @@ size_t fofse_workspace_bytes(const fofse_plan* plans, int n_plans, int n_blocks)
   }
   const size_t fwd = kCounterBytes + scratch_bytes(plans, n_plans);
   const size_t bwd = BwdLayout(n_blocks, imax).total;
-  return fwd > bwd ? fwd : bwd;
+  return override_bytes(plans, n_plans) + (fwd > bwd ? fwd : bwd);
 }
 
 fofse_status fofse_extrapolate_batch(const fofse_plan* plans, int n_plans,
@@ -353,7 +426,7 @@ fofse_status fofse_extrapolate_batch_gamma(const fofse_plan* plans, int n_plans,
   if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return FOFSE_E_ARG;
   if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail)) return FOFSE_E_ARG;
   if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
-  if (d_rho_gamma) return FOFSE_E_UNSUPPORTED;
+  if (d_rho_gamma && !d_workspace) return FOFSE_E_ARG;  // the rebuilt weights live there
   int bmax = 0, imax = 0;
   for (int i = 0; i < n_plans; ++i) {
     if (!plans[i]) return FOFSE_E_ARG;
@@ -377,9 +450,11 @@ fofse_status fofse_extrapolate_batch_gamma(const fofse_plan* plans, int n_plans,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* queue = nullptr;
   unsigned char* scratch_base = nullptr;
+  unsigned char* region = static_cast<unsigned char*>(d_workspace);
   if (d_workspace) {
-    queue = static_cast<int*>(d_workspace);
-    scratch_base = static_cast<unsigned char*>(d_workspace) + kCounterBytes;
+    unsigned char* fw = region + override_bytes(plans, n_plans);
+    queue = reinterpret_cast<int*>(fw);
+    scratch_base = fw + kCounterBytes;
     const cudaError_t e = cudaMemsetAsync(queue, 0, kCounterBytes, s);
     if (e != cudaSuccess) return cuda_fail(e);
   }
@@ -425,6 +500,10 @@ fofse_status fofse_extrapolate_batch_gamma(const fofse_plan* plans, int n_plans,
     a.scratch = scratch_base;
     a.scratch_bytes = scratch_base ? scratch : 0;
     a.gamma_out = reinterpret_cast<float2*>(d_gamma);
+    if (d_rho_gamma) {
+      const cudaError_t eo = apply_override(plans, pi, d_rho_gamma, region, err, a.plan, s);
+      if (eo != cudaSuccess) return cuda_fail(eo);
+    }
     a.box_f = round_up(P.Ls + 3, 4);
     a.box_a = round_up(P.Ls + 15, 16);
     CUtensorMap tf, ta;
@@ -567,7 +646,7 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
   if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail || !d_trace || !d_w0 || !d_grad_blocks))
     return FOFSE_E_ARG;
   if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
-  if (d_rho_gamma) return FOFSE_E_UNSUPPORTED;
+  if (d_rho_gamma && !d_workspace) return FOFSE_E_ARG;
   int bmax = 0, imax = 0;
   for (int i = 0; i < n_plans; ++i) {
     if (!plans[i]) return FOFSE_E_ARG;
@@ -581,7 +660,8 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
   if (!err) return cuda_fail(cudaGetLastError());
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const BwdLayout L(n_blocks, imax);
-  unsigned char* ws = static_cast<unsigned char*>(d_workspace);
+  unsigned char* region = static_cast<unsigned char*>(d_workspace);
+  unsigned char* ws = region ? region + override_bytes(plans, n_plans) : nullptr;
   if (ws) {
     const cudaError_t e = cudaMemsetAsync(ws + L.acc, 0, L.clear, s);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -607,6 +687,10 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
     a.grad_frame = d_grad_frame;
     a.grad_rho_gamma = d_grad_rho_gamma ? d_grad_rho_gamma + 2 * pi : nullptr;
     a.err = err;
+    if (d_rho_gamma) {
+      const cudaError_t eo = apply_override(plans, pi, d_rho_gamma, region, err, a.plan, s);
+      if (eo != cudaSuccess) return cuda_fail(eo);
+    }
     if (ws) {
       a.abar = reinterpret_cast<float2*>(ws + L.abar);
       a.w0bar = reinterpret_cast<float*>(ws + L.w0bar);
@@ -637,6 +721,7 @@ fofse_status fofse_check(void* stream) {
     if ((e = cudaMemcpy(err, &z, sizeof(z), cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_fail(e);
   }
   if (v & kErrTimeout) return FOFSE_E_TIMEOUT;
+  if (v & kErrParam) return FOFSE_E_ARG;
   return FOFSE_OK;
 }
 

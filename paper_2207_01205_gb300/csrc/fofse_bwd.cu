@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
   if (!(w0 > 0.f)) return;  // block without support (or not finite): zero gradient
   const int b = P.block, br = P.border, Ls = P.Ls;
   const int ly0 = bd.y - br, lx0 = bd.x - br;
-  const float gamma = (float)P.gamma;
+  const float gamma = P.rho_gamma_dev ? P.rho_gamma_dev[1] : (float)P.gamma;
 
   // ---- trace, cleared gradient grids, packed input z = w + j e ---------------
   for (int i = tid; i < iters; i += NT) {
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constan
         d += red[4 * w + 3];
       }
       const double dbar = d > 0 ? c / d : 0.0;
-      atomicAdd(&args.grad_rho_gamma[0], (float)((a - dbar * bb) / (double)P.rho));
+      atomicAdd(&args.grad_rho_gamma[0], (float)((a - dbar * bb) / (double)(P.rho_gamma_dev ? P.rho_gamma_dev[0] : P.rho)));
     }
   }
 }
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_samples_kernel(const __grid
     const volatile double* acc = args.acc + 4 * (size_t)blk;
     const double a = acc[0], bb = acc[1], c = acc[2], d = acc[3];
     const double dbar = d > 0 ? c / d : 0.0;
-    atomicAdd(&args.grad_rho_gamma[0], (float)((a - dbar * bb) / (double)P.rho));
+    atomicAdd(&args.grad_rho_gamma[0], (float)((a - dbar * bb) / (double)(P.rho_gamma_dev ? P.rho_gamma_dev[0] : P.rho)));
   }
 }
 

@@ -914,7 +914,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
     for (int i = tid; i < args.trace_stride; i += NT) {
       float2* gp = args.gamma_out + (size_t)blk * args.trace_stride + i;
       if (i >= nIt) *gp = make_float2(0.f, 0.f);
-      else if (!OFSE) *gp = make_float2(P.gamma_h, 0.f);  // OFSE: written per iteration
+      else if (!OFSE) *gp = make_float2(IO::gamma(P).h, 0.f);  // OFSE: written per iteration
     }
   }
   if (tid == 0) {

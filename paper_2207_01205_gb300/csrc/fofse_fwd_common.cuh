@@ -44,7 +44,9 @@ template <> struct PlanIO<ArFF> {
     wout = {{w.x, w.y}, {0.f, 0.f}};
     return {x, {w.x, w.y}};  // z = x + j w
   }
-  __device__ static ff gamma(const PlanDev& p) { return {p.gamma_h, p.gamma_l}; }
+  __device__ static ff gamma(const PlanDev& p) {
+    return p.rho_gamma_dev ? ff{p.rho_gamma_dev[1], 0.f} : ff{p.gamma_h, p.gamma_l};
+  }
   __device__ static ff inv_w0(ff g, ff w0) { return ff_div(g, w0); }
   __device__ static bool w0_zero(const ArFF::C& w) { return w.re.h == 0.f; }
   __device__ static bool w0_finite(const ArFF::C& w) { return isfinite(w.re.h); }
@@ -66,7 +68,9 @@ template <> struct PlanIO<ArF64> {
     wout = {w, 0.0};
     return {w * (double)f, w};
   }
-  __device__ static double gamma(const PlanDev& p) { return p.gamma; }
+  __device__ static double gamma(const PlanDev& p) {
+    return p.rho_gamma_dev ? (double)p.rho_gamma_dev[1] : p.gamma;
+  }
   __device__ static double inv_w0(double g, double w0) { return g / w0; }
   __device__ static bool w0_zero(const ArF64::C& w) { return w.re == 0.0; }
   __device__ static bool w0_finite(const ArF64::C& w) { return isfinite(w.re); }
@@ -88,7 +92,9 @@ template <> struct PlanIO<ArF32> {
     wout = {w, 0.f};
     return {w * f, w};
   }
-  __device__ static float gamma(const PlanDev& p) { return (float)p.gamma; }
+  __device__ static float gamma(const PlanDev& p) {
+    return p.rho_gamma_dev ? p.rho_gamma_dev[1] : (float)p.gamma;
+  }
   __device__ static float inv_w0(float g, float w0) { return g / w0; }
   __device__ static bool w0_zero(const ArF32::C& w) { return w.re == 0.f; }
   __device__ static bool w0_finite(const ArF32::C& w) { return isfinite(w.re); }

@@ -13,6 +13,7 @@ namespace fofse {
 constexpr int kBlkTimeout = 3;
 // Bits of the device error word.
 constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned kErrParam = 2u;  // a device-side rho / gamma out of range
 
 // Device copies of a plan's constant tables (allocated in fofse_plan_create).
 struct PlanTables {
@@ -25,6 +26,7 @@ struct PlanTables {
   const float2* syn_f32;  // T: (cos, sin)(2 pi p / T)
   const double2* syn_f64; // T
   const float4* syn_ff;   // T: (cos.h, sin.h, cos.l, sin.l)(2 pi p / T)
+  const double* dist;     // Ls*Ls: distance to the centre of B (Eq. 15)
 };
 
 struct PlanDev {
@@ -35,7 +37,17 @@ struct PlanDev {
   double gamma;
   float rho;
   PlanTables tab;
+  // nullable: this plan's (rho, gamma) in device memory, read by the kernels
+  // instead of rho / gamma above (the weight tables in `tab` then come from
+  // the same rho, rebuilt on the device for the call)
+  const float* rho_gamma_dev;
 };
+
+// w = rho^dist of one plan into the three weight tables (FP64, float pair,
+// float), rho and gamma read from device memory; out-of-range values give NaN
+// weights and set kErrParam.
+cudaError_t launch_plan_weights(const PlanDev& p, const float* rho_gamma, float2* w_ff,
+                                double* w_f64, float* w_f32, unsigned* err, cudaStream_t s);
 
 struct FwdArgs {
   PlanDev plan;
