@@ -37,9 +37,11 @@ L2_FLUSH_BYTES = 512 << 20
 # R -= c W[k-u] + conj(c) W[k+u] written as 4 pair sums and 4 multiply-adds
 # (8), the subtraction from R (2), |R|^2 (2) and the top-2 compare (2): 14 FP32
 # operations and two 8-byte shared-memory gathers of W's FP32 plane.  Per
-# iteration i additionally the exact float-float recurrence for the winner:
-# i terms of about 66 FP32 operations (two float-float complex products and a
-# float-float accumulation).
+# iteration additionally the exact float-float recurrence for the winner: one
+# term per distinct index selected before (coefficients of a re-selected pair
+# are merged), about 66 FP32 operations each (two float-float complex
+# products and a float-float accumulation); the bench counts the terms from
+# the run's trace.
 OPS_PER_BIN_ITER = 14
 # DRAM bytes of one launch of the product kernel on the 1080p batch, launch
 # shape 0, from an ncu capture (dram__bytes_read.sum 9.04 MB +
@@ -597,7 +599,33 @@ def main():
     mhz = clocks.get("sm_mhz") or 1500.0
     bins = 64 * 64 // 2 + 2
     iters = wl.plans[0].iters
-    ops = n * (iters * bins * OPS_PER_BIN_ITER + OPS_PER_RECURRENCE_TERM * iters * (iters - 1) // 2)
+    # the exact recurrence runs over the distinct indices selected so far
+    # (a re-selected pair's coefficients are merged): count its terms from
+    # this run's trace
+    fwd()
+    torch.cuda.synchronize(dev)
+    tnp = tr.cpu().numpy().view(api.TRACE_DTYPE).reshape(n, -1)
+    codes = tnp["u1"].astype(np.int64) * 256 + tnp["u2"].astype(np.int64)
+    rec_terms = 0
+    for b_i in range(n):
+        seen = set()
+        for it_i in range(iters):
+            rec_terms += len(seen)
+            seen.add(int(codes[b_i, it_i]))
+    ops = n * iters * bins * OPS_PER_BIN_ITER + OPS_PER_RECURRENCE_TERM * rec_terms
+    # measured rates of this GPU: shared-memory loads and FP32 FMAs (probe
+    # kernels, timed alone; the clock is the one sampled in the timed region)
+    sink = torch.empty(2 * sms * 1024, dtype=torch.float32, device=dev)
+    probe = {}
+    for name, fn, rounds in (("smem_bytes_per_clk_per_sm", binding.fofse_probe_smem, 2000),
+                             ("fma_lanes_per_clk_per_sm", binding.fofse_probe_fma, 20000)):
+        fn(2 * sms, rounds, sink, stream=stream)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        work = fn(2 * sms, rounds, sink, stream=stream)
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        probe[name] = work / (q0.elapsed_time(q1) * 1e-3 * mhz * 1e6 * sms)
     alu_peak = sms * FP32_LANES_PER_SM * mhz * 1e6
     achieved = ops / (ms_per_step * 1e-3)
     smem_bytes = n * iters * bins * SMEM_BYTES_PER_BIN_ITER
@@ -608,11 +636,14 @@ def main():
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "kernel": f"fofse_forward_f3_kernel<64,...> (launch shape variant {variant})",
                 "work_per_launch": f"{ops:.4g} FP32 ops ({OPS_PER_BIN_ITER}/bin-iteration + "
-                                   f"{OPS_PER_RECURRENCE_TERM}/recurrence term)",
+                                   f"{OPS_PER_RECURRENCE_TERM} x {rec_terms} recurrence terms)",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (sampled)",
+                "probe": {k: round(v, 2) for k, v in probe.items()},
                 "smem": {"achieved_TBps": smem_bytes / (ms_per_step * 1e-3) / 1e12,
                          "peak_TBps": smem_peak / 1e12,
-                         "frac": smem_bytes / (ms_per_step * 1e-3) / smem_peak}}
+                         "frac": smem_bytes / (ms_per_step * 1e-3) / smem_peak,
+                         "peak_basis": f"{sms} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x {mhz:.0f} MHz "
+                                       f"(probe: {probe['smem_bytes_per_clk_per_sm']:.1f} B/clk)"}}
 
     # ---- the other arithmetic variants, same launch form (context) ----
     variants = {}

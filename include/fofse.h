@@ -326,6 +326,19 @@ fofse_status fofse_check(void* stream);
 int fofse_last_cuda_error(void);
 const char* fofse_last_cuda_error_string(void);
 
+/*
+ * Measurement probes (no counterpart in the paper): kernels that only load
+ * shared memory (16 B per thread and load, no bank conflicts) or only issue
+ * FP32 fused multiply-adds, giving this GPU's rates for the rooflines of the
+ * kernels above.  Each launches `ctas` blocks of 1024 threads doing `rounds`
+ * rounds on `stream` and returns the work queued: *bytes loaded from shared
+ * memory, or *fmas lane FMAs.  d_sink: device buffer of ctas x 1024 floats
+ * (it keeps the work from being optimised away; in practice never written).
+ * The caller times the launch.  FOFSE_E_ARG for non-positive sizes or NULL.
+ */
+fofse_status fofse_probe_smem(int ctas, int rounds, float* d_sink, double* bytes, void* stream);
+fofse_status fofse_probe_fma(int ctas, int rounds, float* d_sink, double* fmas, void* stream);
+
 /* Static, human-readable name of a status code. */
 const char* fofse_status_string(fofse_status status);
 

@@ -89,6 +89,10 @@ def _declare(L):
     L.fofse_backward.restype = _i
     L.fofse_error_curve.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i, _vp, _vp]
     L.fofse_error_curve.restype = _i
+    L.fofse_probe_smem.argtypes = [_i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+    L.fofse_probe_smem.restype = _i
+    L.fofse_probe_fma.argtypes = [_i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+    L.fofse_probe_fma.restype = _i
     L.fofse_check.argtypes = [_vp]
     L.fofse_check.restype = _i
     L.fofse_last_cuda_error.restype = _i
@@ -251,6 +255,22 @@ def fofse_error_curve(plans, blocks, trace, truth, sse, *, stream=None):
     _check(load().fofse_error_curve(
         _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(trace),
         _ptr(truth), H, W, pitch, _ptr(sse), _stream(stream)), "fofse_error_curve")
+
+
+def fofse_probe_smem(ctas, rounds, sink, *, stream=None) -> float:
+    """Queues the shared-memory load probe; returns the bytes it loads."""
+    out = ctypes.c_double()
+    _check(load().fofse_probe_smem(int(ctas), int(rounds), _ptr(sink), ctypes.byref(out),
+                                   _stream(stream)), "fofse_probe_smem")
+    return out.value
+
+
+def fofse_probe_fma(ctas, rounds, sink, *, stream=None) -> float:
+    """Queues the FP32 FMA probe; returns the lane FMAs it issues."""
+    out = ctypes.c_double()
+    _check(load().fofse_probe_fma(int(ctas), int(rounds), _ptr(sink), ctypes.byref(out),
+                                  _stream(stream)), "fofse_probe_fma")
+    return out.value
 
 
 def fofse_last_cuda_error() -> int:

@@ -138,3 +138,17 @@ def test_autotuner_picks_a_shape_and_all_shapes_agree(tmp_path):
     assert again["cached"] == [True] and again["choices"] == first["choices"]
     with pytest.raises(binding.FofseError):
         binding.fofse_plan_set_variant(plans[0].handle, count)
+
+
+def test_measurement_probes_run_and_report_their_work():
+    """The shared-memory and FMA probe kernels used for the rooflines."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sink = torch.empty(sms * 1024, dtype=torch.float32, device="cuda")
+    b = binding.fofse_probe_smem(sms, 10, sink)
+    f = binding.fofse_probe_fma(sms, 10, sink)
+    torch.cuda.synchronize()
+    binding.fofse_check()
+    assert b == sms * 1024 * 10 * 8 * 16
+    assert f == sms * 1024 * 10 * 8
+    with pytest.raises(binding.FofseError):
+        binding.fofse_probe_smem(0, 10, sink)
