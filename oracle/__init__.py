@@ -31,7 +31,7 @@ STATUS_OK, STATUS_NO_SUPPORT, STATUS_NONFINITE = 0, 1, 2
 class OraclePlan(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("border", ctypes.c_int), ("fft_size", ctypes.c_int),
                 ("iters", ctypes.c_int), ("support", ctypes.c_int), ("rho", ctypes.c_double),
-                ("gamma", ctypes.c_double), ("compensation", ctypes.c_int)]
+                ("gamma", ctypes.c_double), ("compensation", ctypes.c_int), ("basis", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -92,6 +92,9 @@ def _declare(L):
     L.oracle_extrapolate_area_ofse.argtypes = [_c_int, _c_int, _dp, _dp, _c_int, _dp, _ip, _ip, _dp,
                                                _dp, _dp, _dp, _dp, _dp]
     L.oracle_extrapolate_area_ofse.restype = _c_int
+    L.oracle_extrapolate_area_dct.argtypes = [_c_int, _c_int, _dp, _dp, ctypes.c_double, _c_int, _dp,
+                                              _ip, _ip, _dp, _dp, _dp]
+    L.oracle_extrapolate_area_dct.restype = _c_int
     L.oracle_error_curve.argtypes = [_c_int, _c_int, _c_int, _c_int, _ip, _ip, _dp, _dp, _c_int, _dp, _dp]
     L.oracle_error_curve.restype = None
     L.oracle_batch_mode.restype = _c_int
@@ -206,6 +209,21 @@ def extrapolate_area_ofse(fL, wL, T: int, iters: int):
     return AreaResult(st, g, np.stack([u1, u2], axis=1), dr + 1j * di, gap, w0.value), gr + 1j * gi
 
 
+def extrapolate_area_dct(fL, wL, T: int, gamma: float, iters: int) -> AreaResult:
+    """FOFSE with the 2-D DCT-II basis (spatial re-projection, FP64); dc real."""
+    fL, wL = _f64(fL), _f64(wL)
+    Ls = fL.shape[0]
+    g = np.empty((Ls, Ls))
+    u1 = np.zeros(iters, dtype=np.int32)
+    u2 = np.zeros(iters, dtype=np.int32)
+    dc, gap = np.zeros(iters), np.zeros(iters)
+    w0 = ctypes.c_double()
+    st = lib().oracle_extrapolate_area_dct(Ls, T, _p(fL, _dp), _p(wL, _dp), float(gamma), iters,
+                                           _p(g, _dp), _p(u1, _ip), _p(u2, _ip), _p(dc, _dp),
+                                           _p(gap, _dp), ctypes.byref(w0))
+    return AreaResult(st, g, np.stack([u1, u2], axis=1), dc.astype(complex), gap, w0.value)
+
+
 def error_curve(Ls: int, T: int, block: int, border: int, path, dc, truth_B) -> np.ndarray:
     """Squared error over B (model clipped to [0, 255]) after each iteration of
     the given path and coefficients (Fig. 4 / Fig. 5 quantity)."""
@@ -284,7 +302,8 @@ def plans_to_c(plans):
     arr = (OraclePlan * len(plans))()
     for i, p in enumerate(plans):
         arr[i] = OraclePlan(p.block, p.border, p.fft_size, p.iters, getattr(p, "support", 0),
-                            float(p.rho), float(p.gamma), int(getattr(p, "compensation", 0)))
+                            float(p.rho), float(p.gamma), int(getattr(p, "compensation", 0)),
+                            int(getattr(p, "basis", 0)))
     return arr
 
 

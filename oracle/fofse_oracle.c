@@ -55,6 +55,7 @@ typedef struct {
     double rho;    /* rho_hat of Eq. 15                         */
     double gamma;  /* constant compensation factor of Eq. 14    */
     int compensation; /* 0 = constant gamma (Eq. 14), 1 = OFSE's compensation (Eq. 10-12) */
+    int basis;        /* 0 = 2-D DFT, 1 = 2-D DCT-II (Sec. 2, transform-domain remark) */
 } oracle_plan;
 
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -255,6 +256,92 @@ int oracle_extrapolate_area(int Ls, int T, const double* fL, const double* wL, d
         if (gap) gap[it] = gp;
     }
     free(c); free(s); free(rw); free(P_re); free(P_im);
+    return ORC_OK;
+}
+
+/* -------------------------------------------------------------------------- */
+/* The 2-D DCT basis (Sec. 2: the DCT admits the transform-domain form too)     */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * FOFSE with the real basis of the 2-D DCT-II on the T x T grid, L at the
+ * origin: phi_k[m,n] = cos(pi k1 (2m+1) / (2T)) cos(pi k2 (2n+1) / (2T)).
+ * Every iteration (spatial re-projection, FP64):
+ *   P[k] = sum w r phi_k                                (Eq. 8, unnormalised)
+ *   u    = argmax_k (a_k1 a_k2 P[k])^2                   (Eq. 9; a_0 = sqrt(1/T),
+ *          a_k = sqrt(2/T): the orthonormal DCT, so that the magnitude is the
+ *          energy of the basis function's portion; ties: smallest k1 T + k2)
+ *   c    = gamma P[u] / sum w phi_u^2                    (Eq. 5, Eq. 14)
+ *   g   += c phi_u                                       (Eq. 2; real basis, no pairs)
+ * path/dc/gap as for the DFT (dc real); the energies drop the common 1/T^2
+ * (factors 1, 2 or 4).
+ */
+int oracle_extrapolate_area_dct(int Ls, int T, const double* fL, const double* wL, double gamma,
+                                int iters, double* g, int* path_u1, int* path_u2, double* dc,
+                                double* gap, double* w0_out) {
+    int N = Ls * Ls;
+    double W0 = 0.0;
+    for (int i = 0; i < N; ++i) W0 += wL[i];
+    if (w0_out) *w0_out = W0;
+    for (int i = 0; i < N; ++i) g[i] = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    for (int i = 0; i < N; ++i)
+        if (wL[i] != 0.0 && !isfinite(fL[i])) return ORC_NONFINITE;
+
+    /* cs[a * Ls + m] = cos(pi a (2m+1) / (2T)) from the integer phase a(2m+1) mod 4T */
+    double* cs = (double*)malloc(sizeof(double) * T * Ls);
+    for (int a = 0; a < T; ++a)
+        for (int m = 0; m < Ls; ++m) {
+            int p = (a * (2 * m + 1)) % (4 * T);
+            cs[a * Ls + m] = cos(TWO_PI * (double)p / (double)(4 * T));
+        }
+    double* rw = (double*)malloc(sizeof(double) * N);
+    double* Y = (double*)malloc(sizeof(double) * Ls * T);
+    double* P = (double*)malloc(sizeof(double) * T * T);
+    for (int it = 0; it < iters; ++it) {
+        for (int i = 0; i < N; ++i) rw[i] = wL[i] != 0.0 ? wL[i] * (fL[i] - g[i]) : 0.0;
+        for (int m = 0; m < Ls; ++m)
+            for (int k2 = 0; k2 < T; ++k2) {
+                double acc = 0.0;
+                for (int n = 0; n < Ls; ++n) acc += rw[m * Ls + n] * cs[k2 * Ls + n];
+                Y[m * T + k2] = acc;
+            }
+        for (int k1 = 0; k1 < T; ++k1)
+            for (int k2 = 0; k2 < T; ++k2) {
+                double acc = 0.0;
+                for (int m = 0; m < Ls; ++m) acc += cs[k1 * Ls + m] * Y[m * T + k2];
+                P[k1 * T + k2] = acc;
+            }
+        double best = -1.0, second = -1.0;
+        int bi = 0;
+        for (int k1 = 0; k1 < T; ++k1)
+            for (int k2 = 0; k2 < T; ++k2) {
+                int i = k1 * T + k2;
+                double e = P[i] * P[i] * (k1 ? 2.0 : 1.0) * (k2 ? 2.0 : 1.0);
+                if (e > best) {
+                    second = best;
+                    best = e;
+                    bi = i;
+                } else if (e > second) {
+                    second = e;
+                }
+            }
+        int u1 = bi / T, u2 = bi % T;
+        double nrm = 0.0;
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) {
+                double ph = cs[u1 * Ls + m] * cs[u2 * Ls + n];
+                nrm += wL[m * Ls + n] * ph * ph;
+            }
+        double c = nrm > 0.0 ? gamma * P[bi] / nrm : 0.0;
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) g[m * Ls + n] += c * cs[u1 * Ls + m] * cs[u2 * Ls + n];
+        if (path_u1) path_u1[it] = u1;
+        if (path_u2) path_u2[it] = u2;
+        if (dc) dc[it] = c;
+        if (gap) gap[it] = best > 0.0 ? (best - (second < 0.0 ? 0.0 : second)) / best : 0.0;
+    }
+    free(cs); free(rw); free(Y); free(P);
     return ORC_OK;
 }
 
@@ -649,7 +736,15 @@ static void run_one(batch_job* J, int bi) {
     oracle_weights(P->block, P->border, P->support, P->rho, aL, wL);
     size_t to = (size_t)bi * J->trace_stride;
     int st;
-    if (P->compensation == 1)
+    if (P->basis == 1) {
+        st = oracle_extrapolate_area_dct(Ls, P->fft_size, fL, wL, P->gamma, P->iters, g,
+                                         J->path_u1 ? J->path_u1 + to : NULL,
+                                         J->path_u2 ? J->path_u2 + to : NULL,
+                                         J->dc_re ? J->dc_re + to : NULL,
+                                         J->gap ? J->gap + to : NULL, J->w0 ? J->w0 + bi : NULL);
+        if (J->dc_im)
+            for (int i = 0; i < P->iters; ++i) J->dc_im[to + i] = 0.0;
+    } else if (P->compensation == 1)
         st = oracle_extrapolate_area_ofse(
             Ls, P->fft_size, fL, wL, P->iters, g, J->path_u1 ? J->path_u1 + to : NULL,
             J->path_u2 ? J->path_u2 + to : NULL, J->dc_re ? J->dc_re + to : NULL,

@@ -126,6 +126,7 @@ class PlanSpec:
     iters: int
     support: int = 0  # 0 = full frame around B, 1 = causal L shape (top/left)
     compensation: int = 0  # 0 = constant gamma (FOFSE, Eq. 14), 1 = OFSE's (Eq. 10-12)
+    basis: int = 0  # 0 = 2-D DFT, 1 = 2-D DCT-II
 
     def __post_init__(self):
         # rho and gamma cross the C ABI as single-precision numbers: hold the
