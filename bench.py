@@ -706,6 +706,37 @@ def main():
                 "hist_edges": [round(float(e), 2) for e in edges], "hist": [int(h) for h in hist]}}
     del oplans, ows
 
+    # ---- the 2-D DCT-II basis on the same batch (all bins float-float) ----
+    dplans = [api.Plan.from_spec(dataclasses.replace(p, basis=1), "fp32") for p in wl.plans]
+    dws = api.workspace(dplans, n, dev)
+    dh = [p.handle for p in dplans]
+
+    def drun():
+        binding.fofse_extrapolate_batch(dh, blocks, frame, avail, out_blocks=ob, trace=tr, w0=w0,
+                                        status=st, workspace=dws, stream=stream)
+    drun()
+    torch.cuda.synchronize(dev)
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dt = 0.0
+    for _ in range(3):
+        flush.zero_()
+        d0.record(stream)
+        drun()
+        d1.record(stream)
+        torch.cuda.synchronize(dev)
+        dt += d0.elapsed_time(d1)
+    truth_b = np.stack([wl.truth[y:y + 16, x:x + 16] for (y, x, _) in wl.blocks]).astype(np.float64)
+
+    def psnr_b(bl_):
+        e = np.clip(bl_.cpu().numpy().astype(np.float64)[:, :16, :16], 0, 255) - truth_b
+        return float(10 * np.log10(255.0 ** 2 / np.mean(e * e)))
+    dct = {"ms_per_step": dt / 3, "blocks_per_s": n / (dt / 3 * 1e-3), "psnr_db": psnr_b(ob),
+           "kernel": "fofse_forward_dct_kernel<64,256> (every bin in float-float)"}
+    fwd()
+    torch.cuda.synchronize(dev)
+    dct["psnr_db_dft"] = psnr_b(ob)
+    del dplans, dws
+
     # ---- quality over iterations for several compensation factors (Fig. 4 and
     # Fig. 5 analogues): PSNR over the lost samples after every iteration
     # count, from the error-curve kernel; gamma = 1 is the uncompensated FSE ----
@@ -760,7 +791,8 @@ def main():
                 "fwd_bwd": fwd_bwd_line,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu, "cpu_transform_domain": cpu_fd, "plain_one_block_per_launch": plain,
-                "parity": parity, "variants": variants, "ofse": ofse, "quality_sweep": quality,
+                "parity": parity, "variants": variants, "ofse": ofse, "dct": dct,
+                "quality_sweep": quality,
                 "device": props.name, "sms": sms}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -87,6 +87,12 @@ enum { FOFSE_COMP_CONSTANT = 0,  /* c = gamma p_u with the plan's constant gamma
                                     (p_l / p_u) Khat[u, l]; with the DFT basis
                                     Khat[u, l] = W[u - l] / W[0], so c = P[u]^2 / Q[u]
                                     with Q[u] = sum_l P[l] W[u - l], gamma unused      */
+/* basis functions */
+enum { FOFSE_BASIS_DFT = 0,      /* 2-D DFT on the T x T grid (the paper's experiments)   */
+       FOFSE_BASIS_DCT = 1 };    /* 2-D DCT-II on the T x T grid, L at its origin: real
+                                    phi_k = cos(pi k1 (2m+1)/(2T)) cos(pi k2 (2n+1)/(2T));
+                                    selection by the orthonormal DCT magnitude, c =
+                                    gamma sum w r phi_u / sum w phi_u^2 (Eq. 5, 14)    */
 /* per-block status written to d_block_status */
 enum { FOFSE_BLK_OK = 0, FOFSE_BLK_NO_SUPPORT = 1, FOFSE_BLK_NONFINITE = 2 };
 
@@ -136,6 +142,14 @@ fofse_status fofse_plan_set_precision(fofse_plan plan, int precision);
  * FOFSE_E_UNSUPPORTED: c is not linear in the samples).  It needs twice the
  * forward scratch of the constant compensation.  FOFSE_E_ARG for other values. */
 fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation);
+/* Basis (FOFSE_BASIS_*); default FOFSE_BASIS_DFT.  FOFSE_BASIS_DCT runs one
+ * kernel with every bin in float-float (exact decisions), for fft_size 32 and
+ * 64, precision FOFSE_FP32 or FOFSE_FP32_FULLFF and the constant compensation
+ * (the batch calls return FOFSE_E_UNSUPPORTED otherwise); it needs no
+ * workspace (work-queue counters are used when one is given).  The trace holds
+ * u = (k1, k2) in [0, T)^2 and the real coefficient (dc_im = 0).  No backward
+ * (FOFSE_E_UNSUPPORTED).  FOFSE_E_ARG for other values. */
+fofse_status fofse_plan_set_basis(fofse_plan plan, int basis);
 /* Number of launch shapes (threads per block / resident blocks per SM) of the
  * plan's kernel for its current precision; 0 for a NULL plan. */
 int fofse_plan_variant_count(fofse_plan plan);

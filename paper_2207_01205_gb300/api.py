@@ -37,15 +37,17 @@ def _release(handle):
 class Plan:
     """One block class: b x b lost blocks, support border, T x T FFT, rho_hat,
     gamma and the number of iterations (paper Sec. 4 notation); compensation
-    0 = the constant gamma of Eq. 14 (FOFSE), 1 = OFSE's (Eq. 10-13)."""
+    0 = the constant gamma of Eq. 14 (FOFSE), 1 = OFSE's (Eq. 10-13); basis
+    0 = 2-D DFT, 1 = 2-D DCT-II."""
 
     def __init__(self, block, border, fft_size, rho, gamma, iters, support=0, precision="fp32",
-                 compensation=0):
+                 compensation=0, basis=0):
         self.block, self.border, self.fft_size = int(block), int(border), int(fft_size)
         self.rho, self.gamma, self.iters = float(rho), float(gamma), int(iters)
         self.support = int(support)
         self.precision = precision
         self.compensation = int(compensation)
+        self.basis = int(basis)
         while _deferred and not _capturing():
             B.fofse_plan_destroy(_deferred.pop())
         self.handle = B.fofse_plan_create(block, border, fft_size, rho, gamma, iters)
@@ -53,6 +55,7 @@ class Plan:
             B.fofse_plan_set_support(self.handle, self.support)
             B.fofse_plan_set_precision(self.handle, B.PRECISIONS[precision])
             B.fofse_plan_set_compensation(self.handle, self.compensation)
+            B.fofse_plan_set_basis(self.handle, self.basis)
         except Exception:
             B.fofse_plan_destroy(self.handle)
             raise
@@ -60,7 +63,8 @@ class Plan:
     @classmethod
     def from_spec(cls, spec, precision="fp32"):
         return cls(spec.block, spec.border, spec.fft_size, spec.rho, spec.gamma, spec.iters,
-                   getattr(spec, "support", 0), precision, getattr(spec, "compensation", 0))
+                   getattr(spec, "support", 0), precision, getattr(spec, "compensation", 0),
+                   getattr(spec, "basis", 0))
 
     def close(self):
         h = getattr(self, "handle", None)

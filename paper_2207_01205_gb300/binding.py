@@ -19,6 +19,7 @@ SUPPORT_FULL, SUPPORT_CAUSAL_L = 0, 1
 FP32, FP64_VALIDATE, FP32_PLAIN, FP32_FULLFF, FP32_FILTERED = 0, 1, 2, 3, 4
 BLK_OK, BLK_NO_SUPPORT, BLK_NONFINITE, BLK_TIMEOUT = 0, 1, 2, 3
 COMP_CONSTANT, COMP_OFSE = 0, 1
+BASIS_DFT, BASIS_DCT = 0, 1
 PRECISIONS = {"fp32": FP32, "fp64": FP64_VALIDATE, "fp32_plain": FP32_PLAIN,
               "fp32_fullff": FP32_FULLFF, "fp32_filtered": FP32_FILTERED}
 
@@ -67,6 +68,8 @@ def _declare(L):
     L.fofse_plan_set_precision.restype = _i
     L.fofse_plan_set_compensation.argtypes = [_vp, _i]
     L.fofse_plan_set_compensation.restype = _i
+    L.fofse_plan_set_basis.argtypes = [_vp, _i]
+    L.fofse_plan_set_basis.restype = _i
     L.fofse_plan_variant_count.argtypes = [_vp]
     L.fofse_plan_variant_count.restype = _i
     L.fofse_plan_set_variant.argtypes = [_vp, _i]
@@ -166,6 +169,10 @@ def fofse_plan_set_precision(plan, precision):
 def fofse_plan_set_compensation(plan, compensation):
     _check(load().fofse_plan_set_compensation(ctypes.c_void_p(plan), int(compensation)),
            "fofse_plan_set_compensation")
+
+
+def fofse_plan_set_basis(plan, basis):
+    _check(load().fofse_plan_set_basis(ctypes.c_void_p(plan), int(basis)), "fofse_plan_set_basis")
 
 
 def fofse_plan_variant_count(plan) -> int:

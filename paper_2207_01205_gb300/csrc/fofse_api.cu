@@ -126,6 +126,14 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 bool supported_T(int T) { return T == 32 || T == 64 || T == 128; }
 
+// The DCT basis runs in one kernel: fft_size 32 or 64, FOFSE_FP32 or
+// FOFSE_FP32_FULLFF, constant compensation.
+bool dct_supported(const PlanDev& p) {
+  if (p.basis != FOFSE_BASIS_DCT) return true;
+  return (p.T == 32 || p.T == 64) && (p.precision == FOFSE_FP32 || p.precision == FOFSE_FP32_FULLFF) &&
+         p.compensation == FOFSE_COMP_CONSTANT;
+}
+
 // CUDA runtime error behind the most recent FOFSE_E_CUDA of this thread
 thread_local int g_last_cuda = 0;
 fofse_status cuda_fail(cudaError_t e) {
@@ -256,6 +264,12 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   std::vector<float2> syn_f32(T);
   std::vector<double2> syn_f64(T);
   std::vector<float4> syn_ff(T);
+  std::vector<float2> dct_cos(4 * T);
+  for (int p = 0; p < 4 * T; ++p) {  // cos(2 pi p / (4T)), integer phase
+    const double v = std::cos(kTwoPi * p / (4.0 * T));
+    const float h = (float)v;
+    dct_cos[p] = make_float2(h, (float)(v - (double)h));
+  }
   for (int p = 0; p < T; ++p) {
     const double cr = std::cos(kTwoPi * p / T), ci = std::sin(kTwoPi * p / T);
     const float hr = (float)cr, hi = (float)ci;
@@ -276,10 +290,12 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
                o_t64 = sec(sizeof(double2) * (T / 2)), o_t32 = sec(sizeof(float2) * (T / 2)),
                o_s32 = sec(sizeof(float2) * T), o_s64 = sec(sizeof(double2) * T),
                o_sff = sec(sizeof(float4) * T), o_dist = sec(sizeof(double) * N),
+               o_dcos = sec(sizeof(float2) * 4 * T),
                o_rg = sec(sizeof(float2));
   const size_t total = off;
   std::vector<unsigned char> host(total, 0);
   std::memcpy(&host[o_dist], dist.data(), sizeof(double) * N);
+  std::memcpy(&host[o_dcos], dct_cos.data(), sizeof(float2) * 4 * T);
   const float2 rg = make_float2(rho, gamma);
   std::memcpy(&host[o_rg], &rg, sizeof(float2));
   std::memcpy(&host[o_tff], tw_ff.data(), sizeof(float4) * (T / 2));
@@ -313,6 +329,7 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   d.precision = FOFSE_FP32;
   d.variant = 0;
   d.compensation = FOFSE_COMP_CONSTANT;
+  d.basis = FOFSE_BASIS_DFT;
   d.rho = rho;
   d.gamma = (double)gamma;
   d.gamma_h = gamma;
@@ -327,6 +344,7 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   d.tab.syn_f64 = reinterpret_cast<const double2*>(base + o_s64);
   d.tab.syn_ff = reinterpret_cast<const float4*>(base + o_sff);
   d.tab.dist = reinterpret_cast<const double*>(base + o_dist);
+  d.tab.dct_cos_ff = reinterpret_cast<const float2*>(base + o_dcos);
   d.rho_gamma_dev = nullptr;
   {
     unsigned* err = err_word_ptr();
@@ -359,6 +377,13 @@ fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation) {
   if (!plan || (compensation != FOFSE_COMP_CONSTANT && compensation != FOFSE_COMP_OFSE))
     return FOFSE_E_ARG;
   plan->dev.compensation = compensation;
+  if (plan->dev.variant >= forward_variant_count(plan->dev)) plan->dev.variant = 0;
+  return FOFSE_OK;
+}
+
+fofse_status fofse_plan_set_basis(fofse_plan plan, int basis) {
+  if (!plan || (basis != FOFSE_BASIS_DFT && basis != FOFSE_BASIS_DCT)) return FOFSE_E_ARG;
+  plan->dev.basis = basis;
   if (plan->dev.variant >= forward_variant_count(plan->dev)) plan->dev.variant = 0;
   return FOFSE_OK;
 }
@@ -437,9 +462,10 @@ fofse_status fofse_extrapolate_batch_gamma(const fofse_plan* plans, int n_plans,
   // OFSE and the per-iteration factors exist only in the register-blocked
   // FOFSE_FP32 kernel, which needs the workspace
   for (int i = 0; i < n_plans; ++i) {
-    const bool needs_f3 = d_gamma || plans[i]->dev.compensation == FOFSE_COMP_OFSE;
-    if (needs_f3 && (plans[i]->dev.precision != FOFSE_FP32 || !d_workspace))
-      return FOFSE_E_UNSUPPORTED;
+    const PlanDev& q = plans[i]->dev;
+    const bool needs_f3 = d_gamma || q.compensation == FOFSE_COMP_OFSE;
+    if (needs_f3 && (q.precision != FOFSE_FP32 || !d_workspace)) return FOFSE_E_UNSUPPORTED;
+    if (!dct_supported(q)) return FOFSE_E_UNSUPPORTED;
   }
   if (n_blocks == 0) return FOFSE_OK;
   unsigned* err = err_word_ptr();
@@ -545,6 +571,7 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
     // OFSE needs the scratch of the register-blocked kernel
     if (forward_needs_scratch(plans[i]->dev)) return FOFSE_E_UNSUPPORTED;
     if (plans[i]->dev.compensation == FOFSE_COMP_OFSE) return FOFSE_E_UNSUPPORTED;
+    if (!dct_supported(plans[i]->dev)) return FOFSE_E_UNSUPPORTED;
     bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
     imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
   }
@@ -652,6 +679,7 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
     if (!plans[i]) return FOFSE_E_ARG;
     if (plans[i]->dev.precision == FOFSE_FP64_VALIDATE) return FOFSE_E_UNSUPPORTED;
     if (plans[i]->dev.compensation == FOFSE_COMP_OFSE) return FOFSE_E_UNSUPPORTED;
+    if (plans[i]->dev.basis == FOFSE_BASIS_DCT) return FOFSE_E_UNSUPPORTED;
     bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
     imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
   }

@@ -1,0 +1,355 @@
+// FOFSE with the real basis of the 2-D DCT-II (Sec. 2: like the DFT, the
+// DCT admits the complete transform-domain formulation).  On the T x T grid
+// with the area L at its origin,
+//   phi_k[m,n] = cos(pi k1 (2m+1) / (2T)) cos(pi k2 (2n+1) / (2T)),
+// and with C[a1,a2] = sum w cos(pi a1 (2m+1)/(2T)) cos(pi a2 (2n+1)/(2T)) for
+// 0 <= a < 2T - 1, the product-to-sum identities give
+//   sum w phi_k phi_u = 1/4 sum_{+-,+-} C[|k1 +- u1|, |k2 +- u2|],
+// so one iteration of the method is, on the working spectrum
+// R[k] = sum w r phi_k (all T^2 bins, real):
+//   u = argmax_k e_k R[k]^2,  e_k = (k1 > 0 ? 2 : 1)(k2 > 0 ? 2 : 1)
+//       (the orthonormal DCT's magnitude, Eq. 9; ties: smallest k1 T + k2)
+//   c = gamma R[u] / N_u,  N_u = 1/4 (C[0,0] + C[2u1,0] + C[0,2u2] + C[2u1,2u2])
+//       (Eq. 5 with the weighted norm sum w phi_u^2, Eq. 14)
+//   R[k] -= c/4 sum_{+-,+-} C[|k1 +- u1|, |k2 +- u2|]     for every k.
+// Every bin is kept in float-float (pairs of FP32, about 48 bits) in
+// registers and compared exactly, C in float-float in shared memory, so the
+// decisions are those of the exact algorithm up to float-float rounding.
+// Setup per block: R0 = DCT of w f and the table C of w, both by separable
+// float-float sums over the rows of L in chunks (cosines from integer phases,
+// table of the plan).  The model of B is rebuilt from the trace.
+#include "fofse_fwd_common.cuh"
+
+namespace fofse {
+namespace {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+template <int T, int NT> struct Dct {
+  static constexpr int TT = 2 * T - 1;      // rows / columns of C
+  static constexpr int S = 2 * T;           // row stride of C's planes (floats)
+  static constexpr int NB = T * T / NT;     // bins per thread
+  static constexpr int RS = NT / T;         // rows between a thread's bins
+  static constexpr int NW = NT / 32;
+  static constexpr int CH = 16;             // rows of L per setup chunk
+  static_assert(T * T % NT == 0 && NT % T == 0 && NB >= 1, "bin grid");
+  static constexpr size_t ct_bytes = sizeof(float) * (size_t)TT * S;   // one plane
+  static constexpr size_t cos_off = 2 * ct_bytes;                      // float2 [4T]
+  static constexpr size_t red_off = cos_off + sizeof(float2) * 4 * T;  // float4 [2][NW], float2 [2][NW]
+  static constexpr size_t chunk_off = (red_off + 48 * NW + 15) & ~size_t(15);
+  // setup chunk: masked w and x = w f (CH x T each), then the row sums of C
+  // (CH x TT) and of R0 (CH x T), all float-float
+  static constexpr size_t chunk_bytes = sizeof(float2) * (size_t)CH * (T + T + TT + T);
+  __host__ __device__ static size_t trace_bytes(int iters) { return 10 * (size_t)iters + 16; }
+  __host__ __device__ static size_t bytes(int iters) {
+    const size_t tb = trace_bytes(iters);
+    return 128 + chunk_off + (chunk_bytes > tb ? chunk_bytes : tb);
+  }
+};
+
+// float-float accumulation of a product of two float-float numbers, without
+// renormalising the sum at every step (a few dozen terms)
+__device__ __forceinline__ void ff_mac(ff& acc, ff a, ff b) {
+  const ff p = ff_two_prod(a.h, b.h);
+  const float e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l));
+  const ff s = ff_two_sum(acc.h, p.h);
+  acc = {s.h, s.l + (acc.l + e)};
+}
+__device__ __forceinline__ ff ff_norm(ff a) { return ff_fast_two_sum(a.h, a.l); }
+
+// (a, b) better than (c, d): larger value, or equal value and smaller index
+__device__ __forceinline__ bool better(ff a, int ia, ff b, int ib) {
+  return a.h > b.h || (a.h == b.h && (a.l > b.l || (a.l == b.l && ia < ib)));
+}
+
+template <int T, int NT>
+__device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, unsigned char* dsm) {
+  using G = Dct<T, NT>;
+  using IO = PlanIO<ArFF>;
+  constexpr int TT = G::TT, S = G::S, NB = G::NB, RS = G::RS, NW = G::NW, CH = G::CH;
+  float* cth = reinterpret_cast<float*>(dsm);
+  float* ctl = reinterpret_cast<float*>(dsm + G::ct_bytes);
+  float2* cosT = reinterpret_cast<float2*>(dsm + G::cos_off);
+  float4* redv = reinterpret_cast<float4*>(dsm + G::red_off);             // [2][NW]: e.h, e.l, idx, -
+  float2* redr = reinterpret_cast<float2*>(dsm + G::red_off + 32 * NW);  // [2][NW]: R[idx]
+  unsigned char* chunk = dsm + G::chunk_off;
+  float2* wsm = reinterpret_cast<float2*>(chunk);                  // [CH][T]
+  float2* xsm = wsm + CH * T;                                      // [CH][T]
+  float2* zc = xsm + CH * T;                                       // [CH][TT]
+  float2* yc = zc + CH * TT;                                       // [CH][T]
+  const PlanDev& P = args.plan;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int iters = P.iters, b = P.block, br = P.border, Ls = P.Ls;
+  const fofse_block bd = args.blocks[blk];
+  const int ly0 = bd.y - br, lx0 = bd.x - br;
+  auto cosv = [&](int a, int m) -> ff {  // cos(pi a (2m+1) / (2T))
+    const float2 v = cosT[(a * (2 * m + 1)) & (4 * T - 1)];
+    return {v.x, v.y};
+  };
+
+  // ---- setup: C and R0 by chunks of CH rows of L ----------------------------
+  for (int e = tid; e < 4 * T; e += NT) cosT[e] = P.tab.dct_cos_ff[e];
+  for (int e = tid; e < TT * S; e += NT) {
+    cth[e] = 0.f;
+    ctl[e] = 0.f;
+  }
+  const int k2 = tid & (T - 1), r0 = tid / T;  // bins (r0 + j RS, k2)
+  ff R[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) R[j] = {0.f, 0.f};
+  bool bad = false;
+  __syncthreads();
+  for (int m0 = 0; m0 < Ls; m0 += CH) {
+    const int nr = min(CH, Ls - m0);
+    // masked weights and weighted samples of rows m0 .. m0 + nr (zero beyond Ls)
+    for (int e = tid; e < CH * T; e += NT) {
+      const int r = e / T, n = e - r * T, m = m0 + r;
+      float2 wv = make_float2(0.f, 0.f), xv = make_float2(0.f, 0.f);
+      if (r < nr && n < Ls) {
+        const bool inB = m >= br && m < br + b && n >= br && n < br + b;
+        bool inS = true;
+        if (P.support == FOFSE_SUPPORT_CAUSAL_L)
+          inS = (m < br) ? (n < br + b) : (m < br + b ? n < br : false);
+        const int fy = ly0 + m, fx = lx0 + n;
+        const bool in = fy >= 0 && fy < args.height && fx >= 0 && fx < args.width;
+        if (in && !inB && inS && args.avail[(size_t)fy * args.pitch + fx]) {
+          const float f = args.frame[(size_t)fy * args.pitch + fx];
+          bad |= !isfinite(f);
+          ArFF::C wd;
+          const ArFF::C z = IO::weighted(P.tab, m * Ls + n, f, wd);
+          wv = make_float2(wd.re.h, wd.re.l);
+          xv = make_float2(z.re.h, z.re.l);
+        }
+      }
+      wsm[e] = wv;
+      xsm[e] = xv;
+    }
+    __syncthreads();
+    // row sums over n: zc[r][a2] = sum_n w cos(a2, n), yc[r][k] = sum_n x cos(k, n)
+    for (int e = tid; e < CH * (TT + T); e += NT) {
+      const bool isz = e < CH * TT;
+      const int ee = isz ? e : e - CH * TT;
+      const int r = isz ? ee / TT : ee / T, a = isz ? ee - r * TT : ee - r * T;
+      const float2* src = (isz ? wsm : xsm) + r * T;
+      ff acc = {0.f, 0.f};
+      for (int n = 0; n < Ls; ++n) {
+        const float2 v = src[n];
+        ff_mac(acc, ff{v.x, v.y}, cosv(a, n));
+      }
+      acc = ff_norm(acc);
+      if (isz) zc[r * TT + a] = make_float2(acc.h, acc.l);
+      else yc[r * T + a] = make_float2(acc.h, acc.l);
+    }
+    __syncthreads();
+    // C[a1][a2] += sum_r cos(a1, m0 + r) zc[r][a2]
+    for (int e = tid; e < TT * TT; e += NT) {
+      const int a1 = e / TT, a2 = e - a1 * TT;
+      ff acc = {cth[a1 * S + a2], ctl[a1 * S + a2]};
+      for (int r = 0; r < nr; ++r) {
+        const float2 v = zc[r * TT + a2];
+        ff_mac(acc, cosv(a1, m0 + r), ff{v.x, v.y});
+      }
+      acc = ff_norm(acc);
+      cth[a1 * S + a2] = acc.h;
+      ctl[a1 * S + a2] = acc.l;
+    }
+    // R0 of the held bins: R[k1][k2] += sum_r cos(k1, m0 + r) yc[r][k2]
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int k1 = r0 + j * RS;
+      ff acc = R[j];
+      for (int r = 0; r < nr; ++r) {
+        const float2 v = yc[r * T + k2];
+        ff_mac(acc, cosv(k1, m0 + r), ff{v.x, v.y});
+      }
+      R[j] = ff_norm(acc);
+    }
+    __syncthreads();
+  }
+  const int any_bad = __syncthreads_or(bad);
+  // the chunk region now holds the trace: packed index and coefficient
+  short* trU = reinterpret_cast<short*>(chunk);
+  float2* trC = reinterpret_cast<float2*>(chunk + ((2 * (size_t)iters + 15) & ~size_t(15)));
+  const ff W0 = {cth[0], ctl[0]};  // C[0,0] = sum w
+  int st = FOFSE_BLK_OK;
+  if (W0.h == 0.f) st = FOFSE_BLK_NO_SUPPORT;
+  else if (any_bad || !isfinite(W0.h)) st = FOFSE_BLK_NONFINITE;
+
+  if (st == FOFSE_BLK_OK) {
+    const ff gam = IO::gamma(P);
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+      // ---- argmax of e_k R[k]^2 (exact comparison in float-float) ----
+      ff best = {-1.f, 0.f}, bestR = {0.f, 0.f};
+      int bidx = 0x7fffffff;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int k1 = r0 + j * RS;
+        const float sc = (k1 > 0 ? 2.f : 1.f) * (k2 > 0 ? 2.f : 1.f);
+        const ff q = ff_two_prod(R[j].h, R[j].h);
+        const ff e2 = ff_fast_two_sum(q.h, __fmaf_rn(2.f * R[j].h, R[j].l, q.l));
+        const ff ev = {e2.h * sc, e2.l * sc};
+        const int idx = k1 * T + k2;
+        if (better(ev, idx, best, bidx)) {
+          best = ev;
+          bidx = idx;
+          bestR = R[j];
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const ff ob = {__shfl_xor_sync(kFullMask, best.h, o), __shfl_xor_sync(kFullMask, best.l, o)};
+        const int oi = __shfl_xor_sync(kFullMask, bidx, o);
+        const ff orr = {__shfl_xor_sync(kFullMask, bestR.h, o), __shfl_xor_sync(kFullMask, bestR.l, o)};
+        if (better(ob, oi, best, bidx)) {
+          best = ob;
+          bidx = oi;
+          bestR = orr;
+        }
+      }
+      float4* rv = redv + (it & 1) * NW;
+      float2* rr = redr + (it & 1) * NW;
+      if (lane == 0) {
+        rv[warp] = make_float4(best.h, best.l, __int_as_float(bidx), 0.f);
+        rr[warp] = make_float2(bestR.h, bestR.l);
+      }
+      __syncthreads();
+      float4 g = rv[0];
+      float2 gr = rr[0];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) {
+        const float4 o = rv[w];
+        if (better(ff{o.x, o.y}, __float_as_int(o.z), ff{g.x, g.y}, __float_as_int(g.z))) {
+          g = o;
+          gr = rr[w];
+        }
+      }
+      int ui = __float_as_int(g.z);
+      if (ui < 0 || ui >= T * T) ui = 0;  // no comparable value (cannot happen for finite data)
+      const int u1 = ui / T, u2 = ui - u1 * T;
+      // ---- coefficient (Eq. 5, Eq. 14) ----
+      ff nrm = ff_add(ff_add(ff{cth[0], ctl[0]}, ff{cth[2 * u1 * S], ctl[2 * u1 * S]}),
+                      ff_add(ff{cth[2 * u2], ctl[2 * u2]}, ff{cth[2 * u1 * S + 2 * u2], ctl[2 * u1 * S + 2 * u2]}));
+      nrm = ff_scale(nrm, 0.25f);
+      const ff cff = nrm.h > 0.f ? ff_div(ff_mul(gam, ff{gr.x, gr.y}), nrm) : ff{0.f, 0.f};
+      if (tid == 0) {
+        trU[it] = (short)ui;
+        trC[it] = make_float2(cff.h, cff.l);
+      }
+      // ---- R[k] -= c/4 sum C[|k1 +- u1|, |k2 +- u2|] ----
+      const ff c4 = ff_scale(cff, 0.25f);
+      const int cp = k2 + u2, cm = abs(k2 - u2);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int k1 = r0 + j * RS;
+        const int rp = (k1 + u1) * S, rm = abs(k1 - u1) * S;
+        const ff t = ff_add(ff_add(ff{cth[rp + cp], ctl[rp + cp]}, ff{cth[rp + cm], ctl[rp + cm]}),
+                            ff_add(ff{cth[rm + cp], ctl[rm + cp]}, ff{cth[rm + cm], ctl[rm + cm]}));
+        R[j] = ff_sub(R[j], ff_mul(c4, t));
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- synthesis of B (Eq. 1) from the trace; outputs ----------------------
+  const int nIt = st == FOFSE_BLK_OK ? iters : 0;
+  const int ld = args.out_ld;
+  for (int pidx = tid; pidx < ld * ld; pidx += NT) {
+    const int bm = pidx / ld, bn = pidx - bm * ld;
+    float v = 0.f;
+    if (bm < b && bn < b) {
+      const int m = br + bm, n = br + bn;
+      ff acc = {0.f, 0.f};
+      for (int i = 0; i < nIt; ++i) {
+        const int yy = trU[i];
+        const int a1 = yy / T, a2 = yy - a1 * T;
+        const float2 c = trC[i];
+        ff_mac(acc, ff{c.x, c.y}, ff_mul(cosv(a1, m), cosv(a2, n)));
+      }
+      acc = ff_norm(acc);
+      v = acc.h + acc.l;
+      if (args.out_frame) {
+        const int fy = bd.y + bm, fx = bd.x + bn;
+        if (fy >= 0 && fy < args.height && fx >= 0 && fx < args.width)
+          args.out_frame[(size_t)fy * args.pitch + fx] = v;
+      }
+    }
+    if (args.out_blocks) args.out_blocks[(size_t)blk * args.out_stride + pidx] = v;
+  }
+  if (args.trace) {
+    for (int i = tid; i < args.trace_stride; i += NT) {
+      fofse_trace_entry e;
+      if (i < nIt) {
+        const int yy = trU[i];
+        e.u1 = (int16_t)(yy / T);
+        e.u2 = (int16_t)(yy - (yy / T) * T);
+        e.dc_re = trC[i].x;
+      } else {
+        e.u1 = e.u2 = 0;
+        e.dc_re = 0.f;
+      }
+      e.dc_im = 0.f;
+      args.trace[(size_t)blk * args.trace_stride + i] = e;
+    }
+  }
+  if (args.gamma_out) {
+    for (int i = tid; i < args.trace_stride; i += NT)
+      args.gamma_out[(size_t)blk * args.trace_stride + i] =
+          make_float2(i < nIt ? IO::gamma(P).h : 0.f, 0.f);
+  }
+  if (tid == 0) {
+    if (args.w0) args.w0[blk] = st == FOFSE_BLK_OK ? W0.h + W0.l : 0.f;
+    if (args.status) args.status[blk] = st;
+  }
+  __syncthreads();
+}
+
+template <int T, int NT>
+__global__ void __launch_bounds__(NT) fofse_forward_dct_kernel(const __grid_constant__ FwdArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* dsm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  __shared__ int s_item;
+  int next = blockIdx.x;
+  for (;;) {
+    int item;
+    if (args.queue) {
+      if (threadIdx.x == 0) s_item = atomicAdd(args.queue, 1);
+      __syncthreads();
+      item = s_item;
+      __syncthreads();
+    } else {
+      item = next;
+      next += gridDim.x;
+    }
+    if (item >= args.n_blocks) break;
+    if (args.blocks[item].plan != args.plan_index) continue;
+    forward_block_dct<T, NT>(args, item, dsm);
+  }
+}
+
+template <int T, int NT> struct VariantDct {
+  static cudaError_t launch(const FwdArgs& a, cudaStream_t s) {
+    const size_t sm = Dct<T, NT>::bytes(a.plan.iters);
+    int grid = 0;
+    const cudaError_t e = prepare_kernel(fofse_forward_dct_kernel<T, NT>, NT, sm, &grid);
+    if (e != cudaSuccess) return e;
+    if (grid > a.n_blocks) grid = a.n_blocks;
+    if (grid < 1) return cudaSuccess;
+    fofse_forward_dct_kernel<T, NT><<<grid, NT, sm, s>>>(a);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace
+
+cudaError_t launch_forward_dct(const FwdArgs& a, cudaStream_t s) {
+  const bool alt = a.plan.variant == 1;
+  if (a.plan.T == 32) return alt ? VariantDct<32, 256>::launch(a, s) : VariantDct<32, 128>::launch(a, s);
+  if (a.plan.T == 64) return alt ? VariantDct<64, 512>::launch(a, s) : VariantDct<64, 256>::launch(a, s);
+  return cudaErrorNotSupported;
+}
+
+int forward_dct_variant_count(const PlanDev& p) { return (p.T == 32 || p.T == 64) ? 2 : 1; }
+
+}  // namespace fofse

@@ -1240,6 +1240,7 @@ template <int T> int variants_T(const PlanDev& p) {
 }  // namespace
 
 size_t forward_scratch_bytes(const PlanDev& p) {
+  if (p.basis == FOFSE_BASIS_DCT) return 0;  // everything in shared memory
   size_t b = 0;
   cudaError_t e = cudaErrorInvalidValue;
   if (p.T == 32) e = scratch_T<32>(p, &b);
@@ -1248,9 +1249,10 @@ size_t forward_scratch_bytes(const PlanDev& p) {
   return e == cudaSuccess ? b : 0;
 }
 
-bool forward_needs_scratch(const PlanDev& p) { return p.T == 128; }
+bool forward_needs_scratch(const PlanDev& p) { return p.T == 128 && p.basis != FOFSE_BASIS_DCT; }
 
 int forward_variant_count(const PlanDev& p) {
+  if (p.basis == FOFSE_BASIS_DCT) return forward_dct_variant_count(p);
   if (p.T == 32) return variants_T<32>(p);
   if (p.T == 64) return variants_T<64>(p);
   if (p.T == 128) return variants_T<128>(p);
@@ -1259,6 +1261,7 @@ int forward_variant_count(const PlanDev& p) {
 
 cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
                            cudaStream_t s) {
+  if (a.plan.basis == FOFSE_BASIS_DCT) return launch_forward_dct(a, s);
   if (a.plan.T == 128) return launch_T<128>(a, tf, ta, s);
   if (a.plan.T == 64) return launch_T<64>(a, tf, ta, s);
   if (a.plan.T == 32) return launch_T<32>(a, tf, ta, s);

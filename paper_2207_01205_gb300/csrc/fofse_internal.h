@@ -27,12 +27,14 @@ struct PlanTables {
   const double2* syn_f64; // T
   const float4* syn_ff;   // T: (cos.h, sin.h, cos.l, sin.l)(2 pi p / T)
   const double* dist;     // Ls*Ls: distance to the centre of B (Eq. 15)
+  const float2* dct_cos_ff;  // 4T: cos(2 pi p / (4T)) as (hi, lo), the DCT basis' phases
 };
 
 struct PlanDev {
   int block, border, Ls, T, iters, support, precision;
   int variant;  // launch shape of the product kernel (0 = default)
   int compensation;  // FOFSE_COMP_CONSTANT (Eq. 14) or FOFSE_COMP_OFSE (Eq. 10-13)
+  int basis;         // FOFSE_BASIS_DFT or FOFSE_BASIS_DCT
   float gamma_h, gamma_l;  // gamma as float pair
   double gamma;
   float rho;
@@ -128,6 +130,9 @@ cudaError_t launch_forward_f3(const FwdArgs& a, const CUtensorMap* tm_frame,
                               const CUtensorMap* tm_avail, cudaStream_t stream);
 size_t forward_f3_scratch_bytes(const PlanDev& p);
 int forward_f3_variant_count(const PlanDev& p);
+// FOFSE with the 2-D DCT-II basis (fofse_dct.cu): all bins in float-float.
+cudaError_t launch_forward_dct(const FwdArgs& a, cudaStream_t stream);
+int forward_dct_variant_count(const PlanDev& p);
 // The same kernel with OFSE's compensation (fofse_ofse.cu); one launch shape.
 cudaError_t launch_forward_ofse(const FwdArgs& a, const CUtensorMap* tm_frame,
                                 const CUtensorMap* tm_avail, cudaStream_t stream);

@@ -1,0 +1,99 @@
+"""Parity of the CUDA path with the 2-D DCT-II basis against the oracle's
+(same bar as the DFT basis: identical selection paths, max |B_gpu - B_oracle|
+<= 1e-3 on the 0-255 scale, PSNR within 0.01 dB)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_01205_gb300 import synth
+
+from parity_util import compare, psnr, run_gpu, to_device, truth_blocks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(gpu_lib):
+    return gpu_lib
+
+
+def _dct(wl):
+    wl.plans = [dataclasses.replace(p, basis=1) for p in wl.plans]
+    return wl
+
+
+@pytest.mark.parametrize("spec", [synth.PlanSpec(16, 16, 64, 0.8, 0.5, 120),
+                                  synth.PlanSpec(8, 8, 32, 0.8, 0.5, 100),
+                                  synth.PlanSpec(4, 4, 32, 0.7, 0.3, 50),
+                                  synth.PlanSpec(8, 8, 32, 0.8, 0.5, 64, support=1),
+                                  synth.PlanSpec(16, 8, 32, 0.8, 0.5, 60)])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fullff"])
+def test_dct_small_frames_with_edge_blocks(spec, precision):
+    """Corner blocks (partial support), lost neighbours, NaN-poisoned lost
+    samples, the causal support, and L = T (16 + 2 x 8 = 32)."""
+    wl = _dct(synth.small_frame(29, plan=spec, n_lost=7, fill=np.nan))
+    ora = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans)
+    res, _ = run_gpu(wl, precision)
+    c = compare(wl, res, ora)
+    assert c["status_equal"]
+    assert c["same"] == c["n"], c
+    assert c["max_err"] <= 1e-3, c
+    assert c["max_dc_rel"] < 1e-5, c
+
+
+def test_dct_launch_shapes_agree_bitwise():
+    import torch
+    from paper_2207_01205_gb300 import api, binding
+    spec = dataclasses.replace(synth.PlanSpec(16, 16, 64, 0.8, 0.5, 80), basis=1)
+    wl = synth.small_frame(30, plan=spec, n_lost=5)
+    fr, av, bl = to_device(wl)
+    outs = []
+    for v in range(2):
+        p = api.Plan.from_spec(spec)
+        binding.fofse_plan_set_variant(p.handle, v)
+        outs.append(api.extrapolate([p], bl, fr, av))
+    torch.cuda.synchronize()
+    binding.fofse_check()
+    assert torch.equal(outs[0].blocks, outs[1].blocks)
+    assert torch.equal(outs[0].trace, outs[1].trace)
+
+
+def test_dct_full_frame_1080p():
+    """The 1920x1080 concealment batch (804 blocks, 64x64 grid, 200 iterations)
+    with the DCT basis."""
+    wl = _dct(synth.frame_concealment())
+    ora = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans)
+    res, _ = run_gpu(wl, "fp32")
+    c = compare(wl, res, ora)
+    assert c["status_equal"]
+    assert c["frac"] >= 0.999, c
+    assert c["max_err"] <= 1e-3, c
+    tb, mask = truth_blocks(wl)
+    g = res.blocks.cpu().numpy().astype(np.float64)
+    assert abs(psnr(g, tb, mask) - psnr(ora.blocks, tb, mask)) <= 0.01
+
+
+def test_dct_unsupported_combinations():
+    import torch
+    from paper_2207_01205_gb300 import api, binding
+    wl = synth.small_frame(31, plan=synth.PlanSpec(8, 8, 32, 0.8, 0.5, 20), n_lost=3)
+    fr, av, bl = to_device(wl)
+    cases = [api.Plan(8, 8, 32, 0.8, 0.5, 20, 0, "fp64", 0, 1),
+             api.Plan(8, 8, 32, 0.8, 0.5, 20, 0, "fp32", 1, 1),
+             api.Plan(32, 16, 128, 0.8, 0.5, 20, 0, "fp32", 0, 1)]
+    for p in cases:
+        with pytest.raises(binding.FofseError) as e:
+            api.extrapolate([p], bl, fr, av)
+        assert e.value.status == binding.E_UNSUPPORTED
+    p = api.Plan(8, 8, 32, 0.8, 0.5, 20, 0, "fp32", 0, 1)
+    res = api.extrapolate([p], bl, fr, av)
+    with pytest.raises(binding.FofseError) as e:
+        binding.fofse_backward([p.handle], bl, fr, av, res.trace, res.w0, torch.ones_like(res.blocks),
+                               grad_frame=torch.zeros_like(fr))
+    assert e.value.status == binding.E_UNSUPPORTED
+    with pytest.raises(binding.FofseError):
+        binding.fofse_plan_set_basis(p.handle, 2)
+    torch.cuda.synchronize()
+    binding.fofse_check()
