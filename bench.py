@@ -163,35 +163,69 @@ def measured_peaks():
         return None
 
 
-def cpu_transform_domain(wl, threads: int | None = None):
+def _sample(wl, k):
+    """Seeded random subset of k of the workload's blocks (all when k is None
+    or not smaller), so that a mixed batch keeps its class mix."""
+    import numpy as np
+    n = len(wl.blocks)
+    if k is None or k >= n:
+        return wl.blocks
+    idx = np.sort(np.random.default_rng(2207).choice(n, size=k, replace=False))
+    return np.ascontiguousarray(wl.blocks[idx])
+
+
+def cpu_transform_domain(wl, threads: int | None = None, sample: int | None = None):
     """The same method in its transform-domain form (FP64, C, all host cores)
-    on every block of the workload: the like-for-like CPU program for the
-    GPU/CPU ratio (the spatial oracle re-projects every iteration)."""
+    on every block of the workload (or a seeded random sample of `sample`
+    blocks): the like-for-like CPU program for the GPU/CPU ratio (the spatial
+    oracle re-projects every iteration)."""
     import oracle
     threads = threads or os.cpu_count() or 1
+    blocks = _sample(wl, sample)
     oracle.build()
     t0 = time.perf_counter()
-    res = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans, threads=threads, with_path=False,
+    res = oracle.run_batch(wl.frame, wl.avail, blocks, wl.plans, threads=threads, with_path=False,
                            transform_domain=True)
     dt = time.perf_counter() - t0
-    return {"value": wl.n_blocks / dt, "unit": "blocks/s", "cores": int(res.threads),
+    what = f"all {len(blocks)} blocks" if len(blocks) == len(wl.blocks) else \
+        f"a random {len(blocks)} of the {len(wl.blocks)} blocks"
+    return {"value": len(blocks) / dt, "unit": "blocks/s", "cores": int(res.threads),
             "kind": "transform-domain FOFSE, FP64 C",
-            "sample": f"all {wl.n_blocks} blocks, {int(res.threads)} threads, {dt:.1f} s"}
+            "sample": f"{what}, {int(res.threads)} threads, {dt:.1f} s"}
 
 
 def cpu_baseline(wl, sample_blocks: int, threads: int | None = None):
     """The FP64 oracle as it stands, on the host cores, over a bounded sample of
-    the workload's blocks; returns blocks/s."""
+    the workload's blocks (a seeded random subset); returns blocks/s."""
     import oracle
     threads = threads or os.cpu_count() or 1
-    blocks = wl.blocks[:sample_blocks]
+    blocks = _sample(wl, sample_blocks)
     oracle.build()
     t0 = time.perf_counter()
     res = oracle.run_batch(wl.frame, wl.avail, blocks, wl.plans, threads=threads, with_path=False)
     dt = time.perf_counter() - t0
     return {"value": len(blocks) / dt, "unit": "blocks/s", "cores": int(res.threads), "kind": "oracle",
-            "sample": f"{len(blocks)} of the {wl.n_blocks} blocks, FP64 spatial re-projection, "
+            "sample": f"{len(blocks)} of the {len(wl.blocks)} blocks, FP64 spatial re-projection, "
                       f"{res.threads} threads, {dt:.1f} s"}
+
+
+def alu_work(trace_np, blocks_np, specs):
+    """FP32 operations of the product kernel's algorithm for one call: per
+    block, bins x iterations x OPS_PER_BIN_ITER plus OPS_PER_RECURRENCE_TERM
+    per exact-recurrence term (one per distinct index selected before, counted
+    from the trace).  Returns (operations, recurrence terms)."""
+    codes = trace_np["u1"].astype("int64") * 256 + trace_np["u2"].astype("int64")
+    ops, terms_all = 0, 0
+    for i in range(len(blocks_np)):
+        p = specs[int(blocks_np[i][2])]
+        bins = p.fft_size * p.fft_size // 2 + 2
+        seen, terms = set(), 0
+        for it in range(p.iters):
+            terms += len(seen)
+            seen.add(int(codes[i, it]))
+        ops += p.iters * bins * OPS_PER_BIN_ITER + OPS_PER_RECURRENCE_TERM * terms
+        terms_all += terms
+    return ops, terms_all
 
 
 def parity_summary(wl, ob, tr, st):
@@ -323,6 +357,33 @@ def run_other_workload(args, rank, world, local):
     stream64 = None
     if args.workload == "predict-720p" and rank == 0:
         stream64 = stream_prediction_frames(plans, handles, blocks, ws, dev, bmax)
+
+    # ALU roofline of the call (every plan's product kernel), work from the trace
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz") or 1500.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fwd()
+    torch.cuda.synchronize(dev)
+    ops, terms = alu_work(tr.cpu().numpy().view(api.TRACE_DTYPE).reshape(n, -1), blocks_np, specs)
+    alu_peak = sms * FP32_LANES_PER_SM * mhz * 1e6
+    achieved = ops / (fwd_ms * 1e-3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
+                "unit": "Tops/s (FP32 lane operations)", "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "fofse_forward_f3_kernel, every plan of the call",
+                "work_per_launch": f"{ops:.4g} FP32 ops ({OPS_PER_BIN_ITER}/bin-iteration + "
+                                   f"{OPS_PER_RECURRENCE_TERM} x {terms} recurrence terms)",
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (sampled)"}
+    cpu = cpu_fd = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import types
+        wl_c = types.SimpleNamespace(frame=frame_np, avail=avail_np, blocks=blocks_np, plans=specs)
+        cores = os.cpu_count() or 1
+        if args.workload == "uneven-4k":
+            cpu = cpu_baseline(wl_c, sample_blocks=2 * cores)
+            cpu_fd = cpu_transform_domain(wl_c, sample=32 * cores)
+        else:
+            cpu = cpu_baseline(wl_c, sample_blocks=32 * cores)
+            cpu_fd = cpu_transform_domain(wl_c)
     if rank == 0:
         line = {"metric": f"blocks/s ({args.workload})", "value": job_value(n, world, fwd_ms),
                 "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
@@ -333,8 +394,9 @@ def run_other_workload(args, rank, world, local):
                            "l2": "flushed between steps (512 MiB write)"},
                 "fwd_bwd": {"ms_per_step": fb_ms, "blocks_per_s": world * n / (fb_ms * 1e-3)},
                 "graph_replay": {"ms_per_step": g_ms, "blocks_per_s": world * n / (g_ms * 1e-3)},
-                "stream64": stream64,
-                "gpu_launches": args.steps * 2 * len(plans), "clocks": clk.summary()}
+                "stream64": stream64, "roofline": roofline, "cpu_baseline": cpu,
+                "cpu_transform_domain": cpu_fd,
+                "gpu_launches": args.steps * 2 * len(plans), "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
@@ -605,14 +667,7 @@ def main():
     fwd()
     torch.cuda.synchronize(dev)
     tnp = tr.cpu().numpy().view(api.TRACE_DTYPE).reshape(n, -1)
-    codes = tnp["u1"].astype(np.int64) * 256 + tnp["u2"].astype(np.int64)
-    rec_terms = 0
-    for b_i in range(n):
-        seen = set()
-        for it_i in range(iters):
-            rec_terms += len(seen)
-            seen.add(int(codes[b_i, it_i]))
-    ops = n * iters * bins * OPS_PER_BIN_ITER + OPS_PER_RECURRENCE_TERM * rec_terms
+    ops, rec_terms = alu_work(tnp, wl.blocks, wl.plans)
     # measured rates of this GPU: shared-memory loads and FP32 FMAs (probe
     # kernels, timed alone; the clock is the one sampled in the timed region)
     sink = torch.empty(2 * sms * 1024, dtype=torch.float32, device=dev)
