@@ -33,8 +33,8 @@ template <int T, int NT> struct Dct {
   static constexpr int NW = NT / 32;
   static constexpr int CH = 16;             // rows of L per setup chunk
   static_assert(T * T % NT == 0 && NT % T == 0 && NB >= 1, "bin grid");
-  static constexpr size_t ct_bytes = sizeof(float) * (size_t)TT * S;   // one plane
-  static constexpr size_t cos_off = 2 * ct_bytes;                      // float2 [4T]
+  static constexpr size_t ct_bytes = sizeof(float2) * (size_t)TT * S;  // (hi, lo) pairs
+  static constexpr size_t cos_off = ct_bytes;                          // float2 [4T]
   static constexpr size_t red_off = cos_off + sizeof(float2) * 4 * T;  // float4 [2][NW], float2 [2][NW]
   static constexpr size_t chunk_off = (red_off + 48 * NW + 15) & ~size_t(15);
   // setup chunk: masked w and x = w f (CH x T each), then the row sums of C
@@ -67,8 +67,7 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   using G = Dct<T, NT>;
   using IO = PlanIO<ArFF>;
   constexpr int TT = G::TT, S = G::S, NB = G::NB, RS = G::RS, NW = G::NW, CH = G::CH;
-  float* cth = reinterpret_cast<float*>(dsm);
-  float* ctl = reinterpret_cast<float*>(dsm + G::ct_bytes);
+  float2* ct = reinterpret_cast<float2*>(dsm);
   float2* cosT = reinterpret_cast<float2*>(dsm + G::cos_off);
   float4* redv = reinterpret_cast<float4*>(dsm + G::red_off);             // [2][NW]: e.h, e.l, idx, -
   float2* redr = reinterpret_cast<float2*>(dsm + G::red_off + 32 * NW);  // [2][NW]: R[idx]
@@ -89,10 +88,7 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
 
   // ---- setup: C and R0 by chunks of CH rows of L ----------------------------
   for (int e = tid; e < 4 * T; e += NT) cosT[e] = P.tab.dct_cos_ff[e];
-  for (int e = tid; e < TT * S; e += NT) {
-    cth[e] = 0.f;
-    ctl[e] = 0.f;
-  }
+  for (int e = tid; e < TT * S; e += NT) ct[e] = make_float2(0.f, 0.f);
   const int k2 = tid & (T - 1), r0 = tid / T;  // bins (r0 + j RS, k2)
   ff R[NB];
 #pragma unroll
@@ -144,14 +140,14 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
     // C[a1][a2] += sum_r cos(a1, m0 + r) zc[r][a2]
     for (int e = tid; e < TT * TT; e += NT) {
       const int a1 = e / TT, a2 = e - a1 * TT;
-      ff acc = {cth[a1 * S + a2], ctl[a1 * S + a2]};
+      const float2 c0 = ct[a1 * S + a2];
+      ff acc = {c0.x, c0.y};
       for (int r = 0; r < nr; ++r) {
         const float2 v = zc[r * TT + a2];
         ff_mac(acc, cosv(a1, m0 + r), ff{v.x, v.y});
       }
       acc = ff_norm(acc);
-      cth[a1 * S + a2] = acc.h;
-      ctl[a1 * S + a2] = acc.l;
+      ct[a1 * S + a2] = make_float2(acc.h, acc.l);
     }
     // R0 of the held bins: R[k1][k2] += sum_r cos(k1, m0 + r) yc[r][k2]
 #pragma unroll
@@ -170,32 +166,35 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   // the chunk region now holds the trace: packed index and coefficient
   short* trU = reinterpret_cast<short*>(chunk);
   float2* trC = reinterpret_cast<float2*>(chunk + ((2 * (size_t)iters + 15) & ~size_t(15)));
-  const ff W0 = {cth[0], ctl[0]};  // C[0,0] = sum w
+  const ff W0 = {ct[0].x, ct[0].y};  // C[0,0] = sum w
   int st = FOFSE_BLK_OK;
   if (W0.h == 0.f) st = FOFSE_BLK_NO_SUPPORT;
   else if (any_bad || !isfinite(W0.h)) st = FOFSE_BLK_NONFINITE;
 
   if (st == FOFSE_BLK_OK) {
     const ff gam = IO::gamma(P);
+    // this thread's best bin by e_k R[k]^2 (exact comparison in float-float);
+    // kept up to date by the update loop below
+    ff best = {-1.f, 0.f}, bestR = {0.f, 0.f};
+    int bidx = 0x7fffffff;
+    auto consider = [&](int j) {
+      const int k1 = r0 + j * RS;
+      const float sc = (k1 > 0 ? 2.f : 1.f) * (k2 > 0 ? 2.f : 1.f);
+      const ff q = ff_two_prod(R[j].h, R[j].h);
+      const ff e2 = ff_fast_two_sum(q.h, __fmaf_rn(2.f * R[j].h, R[j].l, q.l));
+      const ff ev = {e2.h * sc, e2.l * sc};
+      const int idx = k1 * T + k2;
+      if (better(ev, idx, best, bidx)) {
+        best = ev;
+        bidx = idx;
+        bestR = R[j];
+      }
+    };
+#pragma unroll
+    for (int j = 0; j < NB; ++j) consider(j);
 #pragma unroll 1
     for (int it = 0; it < iters; ++it) {
-      // ---- argmax of e_k R[k]^2 (exact comparison in float-float) ----
-      ff best = {-1.f, 0.f}, bestR = {0.f, 0.f};
-      int bidx = 0x7fffffff;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int k1 = r0 + j * RS;
-        const float sc = (k1 > 0 ? 2.f : 1.f) * (k2 > 0 ? 2.f : 1.f);
-        const ff q = ff_two_prod(R[j].h, R[j].h);
-        const ff e2 = ff_fast_two_sum(q.h, __fmaf_rn(2.f * R[j].h, R[j].l, q.l));
-        const ff ev = {e2.h * sc, e2.l * sc};
-        const int idx = k1 * T + k2;
-        if (better(ev, idx, best, bidx)) {
-          best = ev;
-          bidx = idx;
-          bestR = R[j];
-        }
-      }
+      // ---- block argmax ----
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const ff ob = {__shfl_xor_sync(kFullMask, best.h, o), __shfl_xor_sync(kFullMask, best.l, o)};
@@ -228,24 +227,34 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
       if (ui < 0 || ui >= T * T) ui = 0;  // no comparable value (cannot happen for finite data)
       const int u1 = ui / T, u2 = ui - u1 * T;
       // ---- coefficient (Eq. 5, Eq. 14) ----
-      ff nrm = ff_add(ff_add(ff{cth[0], ctl[0]}, ff{cth[2 * u1 * S], ctl[2 * u1 * S]}),
-                      ff_add(ff{cth[2 * u2], ctl[2 * u2]}, ff{cth[2 * u1 * S + 2 * u2], ctl[2 * u1 * S + 2 * u2]}));
+      const float2 n0 = ct[0], n1 = ct[2 * u1 * S], n2 = ct[2 * u2], n3 = ct[2 * u1 * S + 2 * u2];
+      ff nrm = ff_add(ff_add(ff{n0.x, n0.y}, ff{n1.x, n1.y}), ff_add(ff{n2.x, n2.y}, ff{n3.x, n3.y}));
       nrm = ff_scale(nrm, 0.25f);
       const ff cff = nrm.h > 0.f ? ff_div(ff_mul(gam, ff{gr.x, gr.y}), nrm) : ff{0.f, 0.f};
       if (tid == 0) {
         trU[it] = (short)ui;
         trC[it] = make_float2(cff.h, cff.l);
       }
-      // ---- R[k] -= c/4 sum C[|k1 +- u1|, |k2 +- u2|] ----
+      // ---- R[k] -= c/4 sum C[|k1 +- u1|, |k2 +- u2|], and the next best ----
       const ff c4 = ff_scale(cff, 0.25f);
       const int cp = k2 + u2, cm = abs(k2 - u2);
+      best = {-1.f, 0.f};
+      bestR = {0.f, 0.f};
+      bidx = 0x7fffffff;
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
         const int k1 = r0 + j * RS;
         const int rp = (k1 + u1) * S, rm = abs(k1 - u1) * S;
-        const ff t = ff_add(ff_add(ff{cth[rp + cp], ctl[rp + cp]}, ff{cth[rp + cm], ctl[rp + cm]}),
-                            ff_add(ff{cth[rm + cp], ctl[rm + cp]}, ff{cth[rm + cm], ctl[rm + cm]}));
-        R[j] = ff_sub(R[j], ff_mul(c4, t));
+        const float2 a = ct[rp + cp], bq = ct[rp + cm], cq = ct[rm + cp], d = ct[rm + cm];
+        // four-term float-float sum: exact sums of the high parts, low parts added
+        const ff s1 = ff_two_sum(a.x, bq.x), s2 = ff_two_sum(cq.x, d.x), s = ff_two_sum(s1.h, s2.h);
+        const float lo = ((a.y + bq.y) + (cq.y + d.y)) + (s1.l + s2.l) + s.l;
+        // R - c4 t with one product and one compensated subtraction
+        const ff pr = ff_two_prod(c4.h, s.h);
+        const float pe = __fmaf_rn(c4.h, lo, __fmaf_rn(c4.l, s.h, pr.l));
+        const ff dd = ff_two_sum(R[j].h, -pr.h);
+        R[j] = ff_fast_two_sum(dd.h, dd.l + (R[j].l - pe));
+        consider(j);
       }
     }
   }
