@@ -97,3 +97,39 @@ def test_dct_unsupported_combinations():
         binding.fofse_plan_set_basis(p.handle, 2)
     torch.cuda.synchronize()
     binding.fofse_check()
+
+
+def test_dct_long_run_and_device_values():
+    """3000 iterations at fft_size 32 (the trace outgrows the setup's chunk
+    region), and device-side (rho, gamma) equal to a plan built with them."""
+    import torch
+    from paper_2207_01205_gb300 import api, binding
+    spec = synth.PlanSpec(8, 8, 32, 0.8, 0.5, 3000, 0, 0, 1)
+    wl = synth.small_frame(33, plan=spec, n_lost=3)
+    ora = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans)
+    res, _ = run_gpu(wl, "fp32")
+    c = compare(wl, res, ora)
+    assert c["same"] == c["n"], c
+    assert c["max_err"] <= 1e-3, c
+    fr, av, bl = to_device(wl)
+    spec2 = dataclasses.replace(spec, iters=200)
+    own = api.extrapolate([api.Plan.from_spec(spec2)], bl, fr, av)
+    other = api.Plan(8, 8, 32, 0.6, 0.3, 200, 0, "fp32", 0, 1)
+    rg = torch.tensor([[spec2.rho, spec2.gamma]], dtype=torch.float32, device="cuda")
+    dev = api.extrapolate([other], bl, fr, av, rho_gamma=rg)
+    torch.cuda.synchronize()
+    binding.fofse_check()
+    assert torch.equal(own.blocks, dev.blocks)
+    assert torch.equal(own.trace, dev.trace)
+
+
+def test_dct_empty_batch_is_a_no_op():
+    import torch
+    from paper_2207_01205_gb300 import api, binding
+    p = api.Plan(8, 8, 32, 0.8, 0.5, 20, 0, "fp32", 0, 1)
+    fr = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
+    av = torch.ones((64, 64), dtype=torch.uint8, device="cuda")
+    bl = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
+    binding.fofse_extrapolate_batch([p.handle], bl, fr, av)
+    torch.cuda.synchronize()
+    binding.fofse_check()
