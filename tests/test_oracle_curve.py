@@ -60,7 +60,8 @@ def test_quality_over_iterations_follows_the_papers_fig5_description():
     """Sec. 5 on Fig. 4 / Fig. 5: with a smaller gamma the PSNR peaks later but
     higher; only for large gamma (here 1, the uncompensated FSE) does it drop
     after the peak; compensation gains up to about 2 dB over the uncompensated
-    extrapolation.  Checked on 16 blocks of the synthetic 1080p batch."""
+    extrapolation (tests/golden/sec5_quality_claims.txt; here between half and
+    twice that).  Checked on 16 blocks of the synthetic 1080p batch."""
     wl = synth.frame_concealment()
     P = wl.plans[0]
     sel = np.arange(0, wl.n_blocks, 50)[:16]
@@ -75,8 +76,14 @@ def test_quality_over_iterations_follows_the_papers_fig5_description():
             tot += oracle.error_curve(P.block + 2 * P.border, P.fft_size, P.block, P.border, r.u, r.dc,
                                       wl.truth[y:y + P.block, x:x + P.block].astype(np.float64))
         curves[g] = 10 * np.log10(255.0 ** 2 * len(sel) * P.block ** 2 / tot)
+    import os
+    gain = None
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "sec5_quality_claims.txt")):
+        if line.startswith("gain_db_up_to"):
+            gain = float(line.split()[1])
     lo, hi = curves[0.3], curves[1.0]
     assert np.argmax(hi) < np.argmax(lo)
-    assert lo.max() > hi.max() + 1.0
+    # compensation gains on the order the paper reports (up to about 2 dB)
+    assert 0.5 * gain < lo.max() - hi.max() < 2.0 * gain
     assert hi[-1] < hi.max() - 0.1
     assert lo[-1] >= lo.max() - 0.05
