@@ -315,7 +315,8 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
  *                 elements per row (the same geometry as the frame)
  *   d_sse         n_blocks x max_iters floats: entry nu - 1 is the sum over B
  *                 of (clip(B_hat_nu, 0, 255) - truth)^2, with B_hat_nu the
- *                 model of Eq. 1 built from the first nu trace entries; zero
+ *                 model of Eq. 1 built from the first nu trace entries (in the
+ *                 plan's basis); zero
  *                 past a block's iteration count.  PSNR over a set of blocks
  *                 is 10 log10(255^2 N / sum of their entries) for N samples.
  * The model is rebuilt from the trace's FP32 coefficients in FP32.  Blocks

@@ -95,7 +95,8 @@ def _declare(L):
     L.oracle_extrapolate_area_dct.argtypes = [_c_int, _c_int, _dp, _dp, ctypes.c_double, _c_int, _dp,
                                               _ip, _ip, _dp, _dp, _dp]
     L.oracle_extrapolate_area_dct.restype = _c_int
-    L.oracle_error_curve.argtypes = [_c_int, _c_int, _c_int, _c_int, _ip, _ip, _dp, _dp, _c_int, _dp, _dp]
+    L.oracle_error_curve.argtypes = [_c_int, _c_int, _c_int, _c_int, _ip, _ip, _dp, _dp, _c_int, _dp, _dp,
+                                     _c_int]
     L.oracle_error_curve.restype = None
     L.oracle_batch_mode.restype = _c_int
     L.oracle_batch_adjoint.argtypes = [_fp, _u8p, _c_int, _c_int, _c_int, _ip, _c_int,
@@ -224,9 +225,10 @@ def extrapolate_area_dct(fL, wL, T: int, gamma: float, iters: int) -> AreaResult
     return AreaResult(st, g, np.stack([u1, u2], axis=1), dc.astype(complex), gap, w0.value)
 
 
-def error_curve(Ls: int, T: int, block: int, border: int, path, dc, truth_B) -> np.ndarray:
+def error_curve(Ls: int, T: int, block: int, border: int, path, dc, truth_B, basis: int = 0) -> np.ndarray:
     """Squared error over B (model clipped to [0, 255]) after each iteration of
-    the given path and coefficients (Fig. 4 / Fig. 5 quantity)."""
+    the given path and coefficients (Fig. 4 / Fig. 5 quantity); basis 0 = DFT
+    pairs, 1 = DCT-II."""
     path = np.ascontiguousarray(np.asarray(path).reshape(-1, 2), dtype=np.int32)
     u1, u2 = np.ascontiguousarray(path[:, 0]), np.ascontiguousarray(path[:, 1])
     dc = np.asarray(dc)
@@ -235,7 +237,7 @@ def error_curve(Ls: int, T: int, block: int, border: int, path, dc, truth_B) -> 
     n = path.shape[0]
     out = np.zeros(n)
     lib().oracle_error_curve(Ls, T, block, border, _p(u1, _ip), _p(u2, _ip), _p(dr, _dp),
-                             _p(di, _dp), n, _p(tb, _dp), _p(out, _dp))
+                             _p(di, _dp), n, _p(tb, _dp), _p(out, _dp), int(basis))
     return out
 
 

@@ -357,13 +357,23 @@ int oracle_extrapolate_area_dct(int Ls, int T, const double* fL, const double* w
  */
 void oracle_error_curve(int Ls, int T, int block, int border, const int* path_u1,
                         const int* path_u2, const double* dc_re, const double* dc_im, int iters,
-                        const double* truthB, double* sse) {
+                        const double* truthB, double* sse, int basis) {
     double* c = (double*)malloc(sizeof(double) * T);
     double* s = (double*)malloc(sizeof(double) * T);
     double* g = (double*)calloc((size_t)Ls * Ls, sizeof(double));
     twiddles(T, c, s);
     for (int it = 0; it < iters; ++it) {
-        add_basis_pair(Ls, T, c, s, path_u1[it], path_u2[it], dc_re[it], dc_im[it], g);
+        if (basis == 1) {  /* DCT-II: g += c cos(pi u1 (2m+1)/(2T)) cos(pi u2 (2n+1)/(2T)) */
+            for (int m = 0; m < Ls; ++m)
+                for (int n = 0; n < Ls; ++n) {
+                    int p1 = (path_u1[it] * (2 * m + 1)) % (4 * T);
+                    int p2 = (path_u2[it] * (2 * n + 1)) % (4 * T);
+                    g[m * Ls + n] += dc_re[it] * cos(TWO_PI * (double)p1 / (4.0 * T)) *
+                                     cos(TWO_PI * (double)p2 / (4.0 * T));
+                }
+        } else {
+            add_basis_pair(Ls, T, c, s, path_u1[it], path_u2[it], dc_re[it], dc_im[it], g);
+        }
         double e = 0.0;
         for (int bm = 0; bm < block; ++bm)
             for (int bn = 0; bn < block; ++bn) {

@@ -1,6 +1,7 @@
 // Error of the extrapolation over the iterations: for every block and every
 // iteration count nu, the squared error over B of the model of Eq. 1 built
-// from the first nu entries of the selection trace (the quantity behind the
+// from the first nu entries of the selection trace (DFT pairs, or the DCT-II
+// basis for plans that use it) (the quantity behind the
 // quality-over-iterations curves of Fig. 4 and Fig. 5).  The model's values
 // at B are accumulated iteration by iteration, one pixel per thread (up to
 // four for 32 x 32 blocks), from the trace's FP32 coefficients; each
@@ -23,6 +24,8 @@ __global__ void __launch_bounds__(kCurveThreads) fofse_error_curve_kernel(const 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = P.block, br = P.border, T = P.T, iters = P.iters;
   const float2* syn = P.tab.syn_f32;
+  const float2* dcs = P.tab.dct_cos_ff;  // DCT basis: cos(2 pi p / (4T)), p = u (2m+1) mod 4T
+  const bool dct = P.basis == FOFSE_BASIS_DCT;
   for (int blk = blockIdx.x; blk < a.n_blocks; blk += gridDim.x) {
     const fofse_block bd = a.blocks[blk];
     if (bd.plan != a.plan_index) continue;
@@ -49,7 +52,7 @@ __global__ void __launch_bounds__(kCurveThreads) fofse_error_curve_kernel(const 
       for (int j = tid; j < nc; j += kCurveThreads) {
         const fofse_trace_entry e = tr[i0 + j];
         const int u1 = e.u1 & (T - 1), u2 = e.u2 & (T - 1);
-        const bool sc = ((u1 & (T / 2 - 1)) == 0) && ((u2 & (T / 2 - 1)) == 0);
+        const bool sc = dct || (((u1 & (T / 2 - 1)) == 0) && ((u2 & (T / 2 - 1)) == 0));
         s_c[j] = make_float4(e.dc_re, e.dc_im, sc ? 1.f : 2.f, __int_as_float(u1 | (u2 << 16)));
       }
       __syncthreads();
@@ -61,8 +64,14 @@ __global__ void __launch_bounds__(kCurveThreads) fofse_error_curve_kernel(const 
 #pragma unroll
         for (int k = 0; k < kCurvePix; ++k) {
           if (val[k]) {
-            const float2 cs = __ldg(&syn[(u1 * mm[k] + u2 * nn[k]) & (T - 1)]);
-            acc[k] += c.z * (c.x * cs.x - c.y * cs.y);
+            if (dct) {
+              const float c1 = __ldg(&dcs[(u1 * (2 * mm[k] + 1)) & (4 * T - 1)]).x;
+              const float c2 = __ldg(&dcs[(u2 * (2 * nn[k] + 1)) & (4 * T - 1)]).x;
+              acc[k] += c.x * (c1 * c2);
+            } else {
+              const float2 cs = __ldg(&syn[(u1 * mm[k] + u2 * nn[k]) & (T - 1)]);
+              acc[k] += c.z * (c.x * cs.x - c.y * cs.y);
+            }
             const float d = fminf(fmaxf(acc[k], 0.f), 255.f) - tru[k];
             err = __fmaf_rn(d, d, err);
           }

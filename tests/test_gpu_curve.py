@@ -40,7 +40,8 @@ def _oracle_curves(wl, ora):
         Ls = p.block + 2 * p.border
         tb = wl.truth[y:y + p.block, x:x + p.block].astype(np.float64)
         out[i, :p.iters] = oracle.error_curve(Ls, p.fft_size, p.block, p.border,
-                                              ora.path[i, :p.iters], ora.dc[i, :p.iters], tb)
+                                              ora.path[i, :p.iters], ora.dc[i, :p.iters], tb,
+                                              basis=getattr(p, "basis", 0))
     return out
 
 
@@ -59,7 +60,8 @@ def _check(wl, res, sse, ora, ref):
 
 @pytest.mark.parametrize("specs", [[synth.PlanSpec(16, 16, 64, 0.8, 0.5, 120)],
                                    [synth.PlanSpec(8, 8, 32, 0.8, 0.3, 100), synth.PlanSpec(4, 4, 32, 0.8, 0.3, 40)],
-                                   [synth.PlanSpec(32, 16, 128, 0.8, 0.5, 90)]])
+                                   [synth.PlanSpec(32, 16, 128, 0.8, 0.5, 90)],
+                                   [synth.PlanSpec(16, 16, 64, 0.8, 0.5, 80, 0, 0, 1)]])
 def test_curve_small_frames(specs):
     big = specs[0].fft_size == 128
     wl = synth.small_frame(31, plan=specs[0], n_lost=7, height=160 if big else 96,

@@ -87,3 +87,17 @@ def test_quality_over_iterations_follows_the_papers_fig5_description():
     assert 0.5 * gain < lo.max() - hi.max() < 2.0 * gain
     assert hi[-1] < hi.max() - 0.1
     assert lo[-1] >= lo.max() - 0.05
+
+
+def test_dct_basis_curve_ends_at_the_final_model():
+    wl = synth.single_block(seed=6)
+    fL, aL = oracle.cut_area(wl.frame, wl.avail, 16, 16, 16, 16)
+    w = oracle.weights(16, 16, 0.8, aL)
+    res = oracle.extrapolate_area_dct(fL, w, 64, 0.5, 40)
+    truth = wl.truth[16:32, 16:32].astype(np.float64)
+    sse = oracle.error_curve(48, 64, 16, 16, res.u, res.dc, truth, basis=1)
+    gB = np.clip(res.g[16:32, 16:32], 0, 255)
+    assert sse[-1] == pytest.approx(np.sum((gB - truth) ** 2), rel=1e-12)
+    short = oracle.extrapolate_area_dct(fL, w, 64, 0.5, 9)
+    gB = np.clip(short.g[16:32, 16:32], 0, 255)
+    assert sse[8] == pytest.approx(np.sum((gB - truth) ** 2), rel=1e-12)
