@@ -79,6 +79,11 @@ def _declare(L):
     L.oracle_adjoint_area.argtypes = [_c_int, _c_int, _dp, _dp, _c_double, _c_int, _ip, _ip, _dp, _dp,
                                       _dp, _dp]
     L.oracle_adjoint_area.restype = _c_int
+    L.oracle_adjoint_area_dct.argtypes = L.oracle_adjoint_area.argtypes
+    L.oracle_adjoint_area_dct.restype = _c_int
+    L.oracle_replay_area_dct.argtypes = [_c_int, _c_int, _dp, _dp, _c_double, _c_int, _ip, _ip, _dp,
+                                         _dp, _dp]
+    L.oracle_replay_area_dct.restype = _c_int
     L.oracle_rho_chain.argtypes = [_c_int, _dp, _dp, _c_double, _dp]
     L.oracle_rho_chain.restype = _c_double
     L.oracle_tangent_area.argtypes = [_c_int, _c_int, _dp, _dp, _dp, _c_double, _c_double, _c_int,
@@ -255,8 +260,9 @@ def replay_area(fL, wL, T: int, gamma: float, path) -> tuple:
     return g, dr + 1j * di
 
 
-def adjoint_area(fL, wL, T: int, gamma: float, path, gbar):
-    """Reverse-mode adjoint along a fixed path: returns (fbar, wbar, gammabar)."""
+def adjoint_area(fL, wL, T: int, gamma: float, path, gbar, basis: int = 0):
+    """Reverse-mode adjoint along a fixed path: returns (fbar, wbar, gammabar);
+    basis 0 = DFT pairs, 1 = DCT-II."""
     fL, wL, gbar = _f64(fL), _f64(wL), _f64(gbar)
     path = _i32(path)
     Ls, iters = fL.shape[0], path.shape[0]
@@ -264,10 +270,23 @@ def adjoint_area(fL, wL, T: int, gamma: float, path, gbar):
     fbar = np.empty((Ls, Ls))
     wbar = np.empty((Ls, Ls))
     gb = ctypes.c_double()
-    lib().oracle_adjoint_area(Ls, T, _p(fL, _dp), _p(wL, _dp), float(gamma), iters, _p(u1, _ip),
-                              _p(u2, _ip), _p(gbar, _dp), _p(fbar, _dp), _p(wbar, _dp),
-                              ctypes.byref(gb))
+    fn = lib().oracle_adjoint_area_dct if basis == 1 else lib().oracle_adjoint_area
+    fn(Ls, T, _p(fL, _dp), _p(wL, _dp), float(gamma), iters, _p(u1, _ip), _p(u2, _ip),
+       _p(gbar, _dp), _p(fbar, _dp), _p(wbar, _dp), ctypes.byref(gb))
     return fbar, wbar, gb.value
+
+
+def replay_area_dct(fL, wL, T: int, gamma: float, path) -> tuple:
+    """DCT-II basis: forward along a fixed path; returns (g over L, coefficients)."""
+    fL, wL = _f64(fL), _f64(wL)
+    path = _i32(path)
+    Ls, iters = fL.shape[0], path.shape[0]
+    u1, u2 = _i32(path[:, 0]), _i32(path[:, 1])
+    g = np.empty((Ls, Ls))
+    dc = np.zeros(iters)
+    lib().oracle_replay_area_dct(Ls, T, _p(fL, _dp), _p(wL, _dp), float(gamma), iters, _p(u1, _ip),
+                                 _p(u2, _ip), _p(g, _dp), _p(dc, _dp), None)
+    return g, dc
 
 
 def rho_chain(wL, dist, rho, wbar) -> float:

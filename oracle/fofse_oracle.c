@@ -652,6 +652,90 @@ int oracle_adjoint_area(int Ls, int T, const double* fL, const double* wL, doubl
     return ORC_OK;
 }
 
+/* phi_u over L for the DCT-II basis: cos(pi u1 (2m+1)/(2T)) cos(pi u2 (2n+1)/(2T)) */
+static void dct_basis(int Ls, int T, int u1, int u2, double* phi) {
+    for (int m = 0; m < Ls; ++m)
+        for (int n = 0; n < Ls; ++n) {
+            int p1 = (u1 * (2 * m + 1)) % (4 * T), p2 = (u2 * (2 * n + 1)) % (4 * T);
+            phi[m * Ls + n] = cos(TWO_PI * (double)p1 / (4.0 * T)) * cos(TWO_PI * (double)p2 / (4.0 * T));
+        }
+}
+
+/* DCT-II basis: forward along a fixed path (c = gamma sum w r phi / sum w phi^2,
+ * Eq. 5, 14); g over L, coefficients, and (nullable) the model before each
+ * iteration. */
+int oracle_replay_area_dct(int Ls, int T, const double* fL, const double* wL, double gamma,
+                           int iters, const int* u1, const int* u2, double* g, double* dc,
+                           double* g_hist) {
+    int N = Ls * Ls;
+    double W0 = 0.0;
+    for (int i = 0; i < N; ++i) W0 += wL[i];
+    for (int i = 0; i < N; ++i) g[i] = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    double* phi = (double*)malloc(sizeof(double) * N);
+    for (int it = 0; it < iters; ++it) {
+        if (g_hist) memcpy(g_hist + (size_t)it * N, g, sizeof(double) * N);
+        dct_basis(Ls, T, u1[it], u2[it], phi);
+        double p = 0.0, nrm = 0.0;
+        for (int i = 0; i < N; ++i) {
+            if (wL[i] == 0.0) continue;
+            p += wL[i] * (fL[i] - g[i]) * phi[i];
+            nrm += wL[i] * phi[i] * phi[i];
+        }
+        double c = nrm > 0.0 ? gamma * p / nrm : 0.0;
+        for (int i = 0; i < N; ++i) g[i] += c * phi[i];
+        if (dc) dc[it] = c;
+    }
+    free(phi);
+    return ORC_OK;
+}
+
+/*
+ * DCT-II basis: reverse-mode adjoint along a fixed path (as oracle_adjoint_area).
+ * Per iteration, reverse order: cbar = <gbar, phi>; gammabar += cbar c / gamma;
+ * pbar = gamma cbar / N, Nbar = -cbar c / N with p = sum_A w (f - g_prev) phi and
+ * N = sum_A w phi^2; then fbar += w pbar phi, gbar -= w pbar phi,
+ * wbar += (f - g_prev) pbar phi + Nbar phi^2.
+ */
+int oracle_adjoint_area_dct(int Ls, int T, const double* fL, const double* wL, double gamma,
+                            int iters, const int* u1, const int* u2, const double* gbar_out,
+                            double* fbar, double* wbar, double* gammabar) {
+    int N = Ls * Ls;
+    double W0 = 0.0;
+    for (int i = 0; i < N; ++i) W0 += wL[i];
+    for (int i = 0; i < N; ++i) fbar[i] = wbar[i] = 0.0;
+    *gammabar = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    double* g = (double*)malloc(sizeof(double) * N);
+    double* gh = (double*)malloc(sizeof(double) * (size_t)iters * N);
+    double* dc = (double*)malloc(sizeof(double) * iters);
+    double* gbar = (double*)malloc(sizeof(double) * N);
+    double* phi = (double*)malloc(sizeof(double) * N);
+    oracle_replay_area_dct(Ls, T, fL, wL, gamma, iters, u1, u2, g, dc, gh);
+    memcpy(gbar, gbar_out, sizeof(double) * N);
+    for (int it = iters - 1; it >= 0; --it) {
+        dct_basis(Ls, T, u1[it], u2[it], phi);
+        const double* gprev = gh + (size_t)it * N;
+        double cbar = 0.0, nrm = 0.0;
+        for (int i = 0; i < N; ++i) {
+            cbar += gbar[i] * phi[i];
+            if (wL[i] != 0.0) nrm += wL[i] * phi[i] * phi[i];
+        }
+        if (!(nrm > 0.0)) continue;
+        *gammabar += cbar * dc[it] / gamma;
+        double pbar = gamma * cbar / nrm, nbar = -cbar * dc[it] / nrm;
+        for (int i = 0; i < N; ++i) {
+            if (wL[i] == 0.0) continue;
+            double q = pbar * phi[i];
+            fbar[i] += wL[i] * q;
+            gbar[i] -= wL[i] * q;
+            wbar[i] += (fL[i] - gprev[i]) * q + nbar * phi[i] * phi[i];
+        }
+    }
+    free(g); free(gh); free(dc); free(gbar); free(phi);
+    return ORC_OK;
+}
+
 /* rho_bar = sum_A wbar * d/d rho (rho^dist) = sum_A wbar * dist * rho^(dist - 1). */
 double oracle_rho_chain(int N, const double* wL, const double* dist, double rho, const double* wbar) {
     double acc = 0.0;
@@ -867,8 +951,9 @@ static void adj_one(adj_job* J, int bi, double* gf, double* grg) {
         for (int n = 0; n < b; ++n) gbar[(m + br) * Ls + (n + br)] = e[m * b + n];
     double gam = 0.0;
     size_t to = (size_t)bi * J->trace_stride;
-    int st = oracle_adjoint_area(Ls, P->fft_size, fL, wL, P->gamma, P->iters, J->path_u1 + to,
-                                 J->path_u2 + to, gbar, fbar, wbar, &gam);
+    int st = (P->basis == 1 ? oracle_adjoint_area_dct : oracle_adjoint_area)(
+        Ls, P->fft_size, fL, wL, P->gamma, P->iters, J->path_u1 + to, J->path_u2 + to, gbar, fbar,
+        wbar, &gam);
     if (st == ORC_OK) {
         for (int m = 0; m < Ls; ++m)
             for (int n = 0; n < Ls; ++n) {

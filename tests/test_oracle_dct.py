@@ -126,3 +126,60 @@ def test_batch_with_the_dct_basis_matches_single_area_calls():
         assert np.array_equal(out.path[i], res.u)
         assert np.array_equal(out.blocks[i], res.g[8:16, 8:16])
         assert np.all(out.dc[i].imag == 0)
+
+
+def _grad_case(seed=4, b=4, br=4, T=16, iters=12):
+    rng = np.random.default_rng(seed)
+    Ls = b + 2 * br
+    f = rng.uniform(0, 255, size=(Ls, Ls))
+    a = (rng.uniform(size=(Ls, Ls)) > 0.1).astype(np.uint8)
+    rho, gamma = 0.8, 0.45
+    w = oracle.weights(b, br, rho, a)
+    path = oracle.extrapolate_area_dct(f, w, T, gamma, iters).u
+    e = np.zeros((Ls, Ls))
+    e[br:br + b, br:br + b] = rng.normal(size=(b, b))
+    return f, a, w, path, e, rho, gamma, T, b, br
+
+
+def test_dct_replay_reproduces_the_coefficients():
+    f, a, w, path, e, rho, gamma, T, b, br = _grad_case()
+    res = oracle.extrapolate_area_dct(f, w, T, gamma, len(path))
+    g, dc = oracle.replay_area_dct(f, w, T, gamma, path)
+    assert np.max(np.abs(dc - res.dc.real)) <= 1e-12 * np.max(np.abs(dc))
+    assert np.max(np.abs(g - res.g)) <= 1e-10
+
+
+def test_dct_adjoint_in_f_matches_finite_differences():
+    """Along a frozen path B_hat is linear in f: central differences are exact
+    up to rounding."""
+    f, a, w, path, e, rho, gamma, T, b, br = _grad_case()
+    fbar, wbar, gbar = oracle.adjoint_area(f, w, T, gamma, path, e, basis=1)
+    rng = np.random.default_rng(1)
+    for _ in range(6):
+        m, n = rng.integers(0, f.shape[0], size=2)
+        if w[m, n] == 0:
+            continue
+        h = 1e-3
+        fp, fm = f.copy(), f.copy()
+        fp[m, n] += h
+        fm[m, n] -= h
+        lp = np.sum(oracle.replay_area_dct(fp, w, T, gamma, path)[0] * e)
+        lm = np.sum(oracle.replay_area_dct(fm, w, T, gamma, path)[0] * e)
+        assert fbar[m, n] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-9)
+
+
+def test_dct_adjoint_in_rho_and_gamma_matches_richardson():
+    f, a, w, path, e, rho, gamma, T, b, br = _grad_case()
+    fbar, wbar, gbar = oracle.adjoint_area(f, w, T, gamma, path, e, basis=1)
+    dist = oracle.distance(b, br)
+    rbar = oracle.rho_chain(w, dist, rho, wbar)
+
+    def loss(r, g_):
+        return np.sum(oracle.replay_area_dct(f, oracle.weights(b, br, r, a), T, g_, path)[0] * e)
+
+    def rich(fun, x, h):
+        d1 = (fun(x + h) - fun(x - h)) / (2 * h)
+        d2 = (fun(x + h / 2) - fun(x - h / 2)) / h
+        return (4 * d2 - d1) / 3
+    assert rbar == pytest.approx(rich(lambda r: loss(r, gamma), rho, 1e-4), rel=1e-6, abs=1e-8)
+    assert gbar == pytest.approx(rich(lambda g_: loss(rho, g_), gamma, 1e-4), rel=1e-6, abs=1e-8)
