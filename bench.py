@@ -787,6 +787,24 @@ def main():
         return float(10 * np.log10(255.0 ** 2 / np.mean(e * e)))
     dct = {"ms_per_step": dt / 3, "blocks_per_s": n / (dt / 3 * 1e-3), "psnr_db": psnr_b(ob),
            "kernel": "fofse_forward_dct_kernel<64,256> (every bin in float-float)"}
+    # its backward (frozen-path adjoint of the squared error over B)
+    dgf = torch.zeros_like(frame)
+    dgrg = torch.zeros((len(dplans), 2), dtype=torch.float32, device=dev)
+    dgb = torch.empty_like(ob)
+
+    def dbwd():
+        truth_t = torch.from_numpy(np.ascontiguousarray(truth_b, dtype=np.float32)).to(dev)
+        torch.mul(torch.sub(ob[:, :16, :16], truth_t), 2.0, out=dgb[:, :16, :16])
+        binding.fofse_backward(dh, blocks, frame, avail, tr, w0, dgb, grad_frame=dgf,
+                               grad_rho_gamma=dgrg, workspace=dws, stream=stream)
+    drun()
+    dbwd()
+    torch.cuda.synchronize(dev)
+    d0.record(stream)
+    dbwd()
+    d1.record(stream)
+    torch.cuda.synchronize(dev)
+    dct["backward_ms"] = d0.elapsed_time(d1)
     fwd()
     torch.cuda.synchronize(dev)
     dct["psnr_db_dft"] = psnr_b(ob)

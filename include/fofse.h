@@ -147,8 +147,9 @@ fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation);
  * 64, precision FOFSE_FP32 or FOFSE_FP32_FULLFF and the constant compensation
  * (the batch calls return FOFSE_E_UNSUPPORTED otherwise); it needs no
  * workspace (work-queue counters are used when one is given).  The trace holds
- * u = (k1, k2) in [0, T)^2 and the real coefficient (dc_im = 0).  No backward
- * (FOFSE_E_UNSUPPORTED).  FOFSE_E_ARG for other values. */
+ * u = (k1, k2) in [0, T)^2 and the real coefficient (dc_im = 0); fofse_backward
+ * runs the adjoint of this basis' recursion (one block per CTA).  FOFSE_E_ARG
+ * for other values. */
 fofse_status fofse_plan_set_basis(fofse_plan plan, int basis);
 /* Number of launch shapes (threads per block / resident blocks per SM) of the
  * plan's kernel for its current precision; 0 for a NULL plan. */

@@ -21,13 +21,14 @@ def _plans_for(specs, precision, device):
     """Plans of these block classes, created once per (classes, precision,
     device); their own rho / gamma are placeholders (every call passes the
     values on the device)."""
-    key = (tuple((s.block, s.border, s.fft_size, s.iters, getattr(s, "support", 0)) for s in specs),
-           precision, str(device))
+    key = (tuple((s.block, s.border, s.fft_size, s.iters, getattr(s, "support", 0),
+                  getattr(s, "basis", 0)) for s in specs), precision, str(device))
     with _plans_lock:
         plans = _plans.get(key)
         if plans is None:
             plans = [api.Plan(s.block, s.border, s.fft_size, 0.5, 0.5, s.iters,
-                              getattr(s, "support", 0), precision) for s in specs]
+                              getattr(s, "support", 0), precision, 0, getattr(s, "basis", 0))
+                     for s in specs]
             _plans[key] = plans
         return plans
 

@@ -679,7 +679,7 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
     if (!plans[i]) return FOFSE_E_ARG;
     if (plans[i]->dev.precision == FOFSE_FP64_VALIDATE) return FOFSE_E_UNSUPPORTED;
     if (plans[i]->dev.compensation == FOFSE_COMP_OFSE) return FOFSE_E_UNSUPPORTED;
-    if (plans[i]->dev.basis == FOFSE_BASIS_DCT) return FOFSE_E_UNSUPPORTED;
+    if (!dct_supported(plans[i]->dev)) return FOFSE_E_UNSUPPORTED;
     bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
     imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
   }

@@ -543,6 +543,7 @@ template <int T, int NT, int NTS, int S> cudaError_t launch_bwd(const BwdArgs& a
 
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s) {
   if (a.plan.precision == FOFSE_FP64_VALIDATE) return cudaErrorNotSupported;
+  if (a.plan.basis == FOFSE_BASIS_DCT) return launch_backward_dct(a, s);
   if (a.plan.T == 128) return launch_bwd<128, 512, 128, 4>(a, s);
   if (a.plan.T == 64) return launch_bwd<64, 256, 128, 4>(a, s);
   if (a.plan.T == 32) return launch_bwd<32, 128, 64, 4>(a, s);

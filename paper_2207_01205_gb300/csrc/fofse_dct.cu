@@ -350,7 +350,208 @@ template <int T, int NT> struct VariantDct {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Backward (adjoint along the frozen path) with the DCT basis.  With
+// c_i = gamma p_i / N_i, p_i = sum_A w (f - g_{i-1}) phi_i, N_i = sum_A w phi_i^2
+// and B_hat = sum_i c_i phi_i on B, for the loss gradient e on B, in reverse
+// order of the iterations:
+//   cbar_i = sum_L gbar phi_i            (gbar starts as e on B)
+//   gammabar += cbar_i c_i / gamma
+//   pbar = gamma cbar_i / N_i, Nbar = -cbar_i c_i / N_i
+//   on A:  fbar += w pbar phi_i,  gbar -= w pbar phi_i,
+//          wbar += (f - g_{i-1}) pbar phi_i + Nbar phi_i^2
+// with g_{i-1} = g_i - c_i phi_i un-built from the final model; then
+// rhobar = sum_A wbar w dist / rho (Eq. 15).  One block per CTA; each thread
+// keeps its samples of L in registers; FP32, FP64 for the rho sums.
+// ---------------------------------------------------------------------------
+template <int T, int NT> struct DctBwd {
+  static constexpr int KS = T * T / NT;  // samples of L per thread (Ls <= T)
+  static constexpr int NW = NT / 32;
+  static constexpr int CHI = 32;         // iterations per reduction batch
+};
+
+template <int T, int NT>
+__global__ void __launch_bounds__(NT) fofse_backward_dct_kernel(const __grid_constant__ BwdArgs a) {
+  using G = DctBwd<T, NT>;
+  constexpr int KS = G::KS, NW = G::NW, CHI = G::CHI;
+  extern __shared__ unsigned char smem_raw[];
+  float* cosT = reinterpret_cast<float*>(smem_raw);                // [4T]
+  float* part = cosT + 4 * T;                                      // [NW][CHI] warp partials
+  float* nrm = part + NW * CHI;                                    // [iters]
+  float* cco = nrm + a.plan.iters;                                 // [iters] coefficients
+  int* uu = reinterpret_cast<int*>(cco + a.plan.iters);            // [iters] packed u1 | u2 << 16
+  double* dred = reinterpret_cast<double*>(uu + a.plan.iters + (a.plan.iters & 1));  // [3][NW]
+  const PlanDev& P = a.plan;
+  const int blk = blockIdx.x;
+  const fofse_block bd = a.blocks[blk];
+  if (bd.plan != a.plan_index) return;
+  const float w0 = a.w0[blk];
+  if (!(w0 > 0.f)) return;  // the block had no valid extrapolation
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int iters = P.iters, b = P.block, br = P.border, Ls = P.Ls;
+  const float gamma = P.rho_gamma_dev ? P.rho_gamma_dev[1] : (float)P.gamma;
+  const double rho = P.rho_gamma_dev ? (double)P.rho_gamma_dev[0] : (double)P.rho;
+  for (int e = tid; e < 4 * T; e += NT) cosT[e] = P.tab.dct_cos_ff[e].x;
+  for (int i = tid; i < iters; i += NT) {
+    const fofse_trace_entry t = a.trace[(size_t)blk * a.trace_stride + i];
+    cco[i] = t.dc_re;
+    uu[i] = (t.u1 & (T - 1)) | ((t.u2 & (T - 1)) << 16);
+  }
+  // this thread's samples of L: weight, value, model, adjoints
+  float wv[KS], fv[KS], gv[KS], gb[KS], fb[KS], wb[KS];
+  int mm[KS], nn[KS];
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    const int x = tid + k * NT;
+    const int m = x / Ls, n = x - (x / Ls) * Ls;
+    mm[k] = x < Ls * Ls ? m : 0;
+    nn[k] = x < Ls * Ls ? n : 0;
+    wv[k] = fv[k] = gv[k] = gb[k] = fb[k] = wb[k] = 0.f;
+    if (x >= Ls * Ls) continue;
+    const bool inB = m >= br && m < br + b && n >= br && n < br + b;
+    bool inS = true;
+    if (P.support == FOFSE_SUPPORT_CAUSAL_L) inS = (m < br) ? (n < br + b) : (m < br + b ? n < br : false);
+    const int fy = bd.y - br + m, fx = bd.x - br + n;
+    const bool in = fy >= 0 && fy < a.height && fx >= 0 && fx < a.width;
+    if (in && !inB && inS && a.avail[(size_t)fy * a.pitch + fx]) {
+      wv[k] = P.tab.w_f32[m * Ls + n];
+      fv[k] = a.frame[(size_t)fy * a.pitch + fx];
+    }
+    if (inB) gb[k] = a.grad_blocks[(size_t)blk * a.grad_stride + (m - br) * a.grad_ld + (n - br)];
+  }
+  __syncthreads();
+  auto phi = [&](int u, int k) -> float {
+    const int u1 = u & 0xffff, u2 = u >> 16;
+    return cosT[(u1 * (2 * mm[k] + 1)) & (4 * T - 1)] * cosT[(u2 * (2 * nn[k] + 1)) & (4 * T - 1)];
+  };
+  // ---- weighted norms N_i, and the final model g_I = sum_i c_i phi_i ----
+  for (int i0 = 0; i0 < iters; i0 += CHI) {
+    const int ni = min(CHI, iters - i0);
+    for (int j = 0; j < ni; ++j) {
+      const int u = uu[i0 + j];
+      const float c = cco[i0 + j];
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const float ph = phi(u, k);
+        s = __fmaf_rn(wv[k] * ph, ph, s);
+        gv[k] = __fmaf_rn(c, ph, gv[k]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFullMask, s, o);
+      if (lane == 0) part[warp * CHI + j] = s;
+    }
+    __syncthreads();
+    for (int j = tid; j < ni; j += NT) {
+      float s = 0.f;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s += part[w * CHI + j];
+      nrm[i0 + j] = s;
+    }
+    __syncthreads();
+  }
+  // ---- reverse pass ----
+  float gam_acc = 0.f;
+  for (int i = iters - 1; i >= 0; --i) {
+    const int u = uu[i];
+    const float c = cco[i];
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) s = __fmaf_rn(gb[k], phi(u, k), s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFullMask, s, o);
+    float* pw = part + (i & 1) * NW;  // double-buffered warp partials
+    if (lane == 0) pw[warp] = s;
+    __syncthreads();
+    float cbar = 0.f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cbar += pw[w];
+    const float N = nrm[i];
+    if (!(N > 0.f)) continue;
+    gam_acc += cbar * c;
+    const float pbar = gamma * cbar / N, nbar = -cbar * c / N;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const float ph = phi(u, k);
+      gv[k] = __fmaf_rn(-c, ph, gv[k]);  // g_{i-1}
+      if (wv[k] != 0.f) {
+        const float q = pbar * ph;
+        fb[k] = __fmaf_rn(wv[k], q, fb[k]);
+        gb[k] = __fmaf_rn(-wv[k], q, gb[k]);
+        wb[k] = __fmaf_rn(fv[k] - gv[k], q, __fmaf_rn(nbar * ph, ph, wb[k]));
+      }
+    }
+  }
+  // ---- outputs: frame gradient, d/dgamma, d/drho ----
+  double s_a = 0.0, s_b = 0.0, s_w = 0.0, s_wd = 0.0;
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    if (wv[k] == 0.f) continue;
+    const int m = mm[k], n = nn[k];
+    if (a.grad_frame) {
+      const int fy = bd.y - br + m, fx = bd.x - br + n;
+      atomicAdd(&a.grad_frame[(size_t)fy * a.pitch + fx], fb[k]);
+    }
+    const double d = P.tab.dist[m * Ls + n];
+    const double ww = (double)wb[k] * (double)wv[k];
+    s_a += ww * d;
+    s_b += ww;
+    s_w += (double)wv[k];
+    s_wd += (double)wv[k] * d;
+  }
+  if (a.grad_rho_gamma) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s_a += __shfl_xor_sync(kFullMask, s_a, o);
+      s_b += __shfl_xor_sync(kFullMask, s_b, o);
+      s_w += __shfl_xor_sync(kFullMask, s_w, o);
+      s_wd += __shfl_xor_sync(kFullMask, s_wd, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+      dred[warp] = s_a;
+      dred[NW + warp] = s_b;
+      dred[2 * NW + warp] = s_wd;
+      part[warp] = (float)s_w;  // the weights' sum (for the mean distance)
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double A = 0.0, Bs = 0.0, W = 0.0, WD = 0.0;
+      for (int w = 0; w < NW; ++w) {
+        A += dred[w];
+        Bs += dred[NW + w];
+        WD += dred[2 * NW + w];
+        W += (double)part[w];
+      }
+      // sum_A wbar w = 0 up to rounding (B_hat does not change when w is scaled):
+      // subtract it at the mean distance to keep the cancellation small
+      const double dbar = W > 0.0 ? WD / W : 0.0;
+      atomicAdd(&a.grad_rho_gamma[0], (float)((A - dbar * Bs) / rho));
+      atomicAdd(&a.grad_rho_gamma[1], gam_acc / gamma);
+    }
+  }
+}
+
+template <int T, int NT> cudaError_t launch_bwd_dct(const BwdArgs& a, cudaStream_t s) {
+  const int iters = a.plan.iters;
+  const size_t sm = sizeof(float) * (4 * T + DctBwd<T, NT>::NW * DctBwd<T, NT>::CHI) +
+                    (sizeof(float) * 2 + sizeof(int)) * (size_t)iters + 16 +
+                    sizeof(double) * 3 * DctBwd<T, NT>::NW;
+  int grid = 0;
+  const cudaError_t e = prepare_kernel(fofse_backward_dct_kernel<T, NT>, NT, sm, &grid);
+  if (e != cudaSuccess) return e;
+  if (a.n_blocks < 1) return cudaSuccess;
+  fofse_backward_dct_kernel<T, NT><<<a.n_blocks, NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_backward_dct(const BwdArgs& a, cudaStream_t s) {
+  if (a.plan.T == 32) return launch_bwd_dct<32, 128>(a, s);
+  if (a.plan.T == 64) return launch_bwd_dct<64, 512>(a, s);
+  return cudaErrorNotSupported;
+}
 
 cudaError_t launch_forward_dct(const FwdArgs& a, cudaStream_t s) {
   const bool alt = a.plan.variant == 1;

@@ -132,6 +132,7 @@ size_t forward_f3_scratch_bytes(const PlanDev& p);
 int forward_f3_variant_count(const PlanDev& p);
 // FOFSE with the 2-D DCT-II basis (fofse_dct.cu): all bins in float-float.
 cudaError_t launch_forward_dct(const FwdArgs& a, cudaStream_t stream);
+cudaError_t launch_backward_dct(const BwdArgs& a, cudaStream_t stream);
 int forward_dct_variant_count(const PlanDev& p);
 // The same kernel with OFSE's compensation (fofse_ofse.cu); one launch shape.
 cudaError_t launch_forward_ofse(const FwdArgs& a, const CUtensorMap* tm_frame,
