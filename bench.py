@@ -790,10 +790,10 @@ def main():
     # its backward (frozen-path adjoint of the squared error over B)
     dgf = torch.zeros_like(frame)
     dgrg = torch.zeros((len(dplans), 2), dtype=torch.float32, device=dev)
-    dgb = torch.empty_like(ob)
+    dgb = torch.zeros_like(ob)
+    truth_t = torch.from_numpy(np.ascontiguousarray(truth_b, dtype=np.float32)).to(dev)
 
     def dbwd():
-        truth_t = torch.from_numpy(np.ascontiguousarray(truth_b, dtype=np.float32)).to(dev)
         torch.mul(torch.sub(ob[:, :16, :16], truth_t), 2.0, out=dgb[:, :16, :16])
         binding.fofse_backward(dh, blocks, frame, avail, tr, w0, dgb, grad_frame=dgf,
                                grad_rho_gamma=dgrg, workspace=dws, stream=stream)
