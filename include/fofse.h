@@ -139,7 +139,8 @@ fofse_status fofse_plan_set_precision(fofse_plan plan, int precision);
 /* Compensation (FOFSE_COMP_*); default FOFSE_COMP_CONSTANT.  FOFSE_COMP_OFSE
  * runs only with FOFSE_FP32 and a workspace (fofse_extrapolate_batch returns
  * FOFSE_E_UNSUPPORTED otherwise) and has no backward (fofse_backward returns
- * FOFSE_E_UNSUPPORTED: c is not linear in the samples).  It needs twice the
+ * FOFSE_E_UNSUPPORTED: the adjoint of c = P^2 / Q and of Q's recurrence is not
+ * built; OFSE serves as the paper's comparison method).  It needs twice the
  * forward scratch of the constant compensation.  FOFSE_E_ARG for other values. */
 fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation);
 /* Basis (FOFSE_BASIS_*); default FOFSE_BASIS_DFT.  FOFSE_BASIS_DCT runs one
