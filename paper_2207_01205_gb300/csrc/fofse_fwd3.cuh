@@ -207,6 +207,35 @@ __device__ __forceinline__ void recur_fixed(const float2* Whi, const float2* Zg,
 // during the setup), transformed there by radix-2 DIT stages and written
 // back.  Two reads and three writes of the scratch instead of one read and
 // one write per stage.  Twiddles exp(-j 2 pi e / T) come from the plan table.
+// exp(-j 2 pi e / T) for 0 <= e < T (the plan's table covers e < T/2; the
+// rest is its negative)
+template <int T> __device__ __forceinline__ ArFF::C twiddle_full(const PlanTables& tab, int e) {
+  const ArFF::C w = PlanIO<ArFF>::twiddle(tab, e & (T / 2 - 1));
+  return e >= T / 2 ? ArFF::C{ff_neg(w.re), ff_neg(w.im)} : w;
+}
+
+// One radix-4 decimation-in-time butterfly (two radix-2 stages of distance h
+// and 2h merged): inputs at offsets 0, h, 2h, 3h (stride `st` elements apart
+// per unit of h), twiddles W^j, W^2j, W^3j with W = exp(-j 2 pi / (4h)).
+template <int T>
+__device__ __forceinline__ void radix4(float2* buf, int i0, int hs, int ld, int e1, const PlanTables& tab) {
+  using A = ArFF;
+  using C = ArFF::C;
+  const C a = A::load(buf, i0, ld);
+  C b = A::load(buf, i0 + hs, ld), c = A::load(buf, i0 + 2 * hs, ld), d = A::load(buf, i0 + 3 * hs, ld);
+  if (e1 != 0) {
+    b = A::mul_norm(twiddle_full<T>(tab, 2 * e1), b);
+    c = A::mul_norm(twiddle_full<T>(tab, e1), c);
+    d = A::mul_norm(twiddle_full<T>(tab, 3 * e1), d);
+  }
+  const C s0 = A::add(a, b), s1 = A::sub(a, b), s2 = A::add(c, d), s3 = A::sub(c, d);
+  const C is3 = {s3.im, ff_neg(s3.re)};  // -j (c - d)
+  A::store(buf, i0, ld, A::add(s0, s2));
+  A::store(buf, i0 + hs, ld, A::add(s1, is3));
+  A::store(buf, i0 + 2 * hs, ld, A::sub(s0, s2));
+  A::store(buf, i0 + 3 * hs, ld, A::sub(s1, is3));
+}
+
 template <int T, int NT>
 __device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const PlanTables& tab, int Ls) {
   using A = ArFF;
@@ -225,7 +254,17 @@ __device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const Plan
     }
     __syncthreads();
 #pragma unroll 1
-    for (int lh = 0; lh < LOGT; ++lh) {
+    for (int lh = 0; lh + 1 < LOGT; lh += 2) {
+      const int h = 1 << lh;
+      for (int it = tid; it < nr * (T / 4); it += NT) {
+        const int lr = it >> (LOGT - 2), q = it & (T / 4 - 1);
+        const int j = q & (h - 1);
+        radix4<T>(buf, lr * T2 + (((q >> lh) << (lh + 2)) | j), h, T, j << (LOGT - 2 - lh), tab);
+      }
+      __syncthreads();
+    }
+#pragma unroll 1
+    for (int lh = LOGT & ~1; lh < LOGT; ++lh) {
       const int h = 1 << lh;
       for (int it = tid; it < nr * (T / 2); it += NT) {
         const int lr = it >> (LOGT - 1), q = it & (T / 2 - 1);
@@ -254,7 +293,17 @@ __device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const Plan
     }
     __syncthreads();
 #pragma unroll 1
-    for (int lh = 0; lh < LOGT; ++lh) {
+    for (int lh = 0; lh + 1 < LOGT; lh += 2) {
+      const int h = 1 << lh;
+      for (int it = tid; it < CH * (T / 4); it += NT) {
+        const int lc = it % CH, q = it / CH;
+        const int j = q & (h - 1);
+        radix4<T>(buf, (((q >> lh) << (lh + 2)) | j) * 2 * CH + lc, h * 2 * CH, CH, j << (LOGT - 2 - lh), tab);
+      }
+      __syncthreads();
+    }
+#pragma unroll 1
+    for (int lh = LOGT & ~1; lh < LOGT; ++lh) {
       const int h = 1 << lh;
       for (int it = tid; it < CH * (T / 2); it += NT) {
         const int lc = it % CH, q = it / CH;
