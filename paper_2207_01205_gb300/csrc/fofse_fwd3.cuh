@@ -242,6 +242,9 @@ __device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const Plan
   using C = ArFF::C;
   using IO = PlanIO<A>;
   constexpr int LOGT = ilog2(T), T2 = 2 * T, CH = T / 2;
+  // radix-4 stages from fft_size 64 on (measured faster there; at 32, with
+  // one warp per block, slower than radix-2)
+  constexpr int R4 = T >= 64 ? (LOGT & ~1) : 0;  // stages done in radix-4 pairs
   const int tid = threadIdx.x;
   // ---- rows: chunk rows are storage rows brev(rr), rr in [r0, r0 + CH) ----
 #pragma unroll 1
@@ -254,7 +257,7 @@ __device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const Plan
     }
     __syncthreads();
 #pragma unroll 1
-    for (int lh = 0; lh + 1 < LOGT; lh += 2) {
+    for (int lh = 0; lh + 1 < R4; lh += 2) {
       const int h = 1 << lh;
       for (int it = tid; it < nr * (T / 4); it += NT) {
         const int lr = it >> (LOGT - 2), q = it & (T / 4 - 1);
@@ -264,7 +267,7 @@ __device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const Plan
       __syncthreads();
     }
 #pragma unroll 1
-    for (int lh = LOGT & ~1; lh < LOGT; ++lh) {
+    for (int lh = R4; lh < LOGT; ++lh) {
       const int h = 1 << lh;
       for (int it = tid; it < nr * (T / 2); it += NT) {
         const int lr = it >> (LOGT - 1), q = it & (T / 2 - 1);
@@ -293,7 +296,7 @@ __device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const Plan
     }
     __syncthreads();
 #pragma unroll 1
-    for (int lh = 0; lh + 1 < LOGT; lh += 2) {
+    for (int lh = 0; lh + 1 < R4; lh += 2) {
       const int h = 1 << lh;
       for (int it = tid; it < CH * (T / 4); it += NT) {
         const int lc = it % CH, q = it / CH;
@@ -303,7 +306,7 @@ __device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const Plan
       __syncthreads();
     }
 #pragma unroll 1
-    for (int lh = LOGT & ~1; lh < LOGT; ++lh) {
+    for (int lh = R4; lh < LOGT; ++lh) {
       const int h = 1 << lh;
       for (int it = tid; it < CH * (T / 2); it += NT) {
         const int lc = it % CH, q = it / CH;
