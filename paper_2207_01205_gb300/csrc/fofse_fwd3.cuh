@@ -204,7 +204,8 @@ __device__ __forceinline__ void recur_fixed(const float2* Whi, const float2* Zg,
 // rows brev(m), m < Ls, nonzero), through shared memory: the row pass in
 // chunks of T/2 storage rows, the column pass in chunks of T/2 columns, each
 // chunk loaded into `buf` (8 T^2 bytes: the region of W's FP32 plane, free
-// during the setup), transformed there by radix-2 DIT stages and written
+// during the setup), transformed there by decimation-in-time stages (radix-4
+// pairs of stages from fft_size 64 on, radix-2 otherwise) and written
 // back.  Two reads and three writes of the scratch instead of one read and
 // one write per stage.  Twiddles exp(-j 2 pi e / T) come from the plan table.
 // exp(-j 2 pi e / T) for 0 <= e < T (the plan's table covers e < T/2; the
