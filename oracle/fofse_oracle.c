@@ -36,6 +36,16 @@
  * Frozen-path companions (the selection sequence fixed, so the output is
  * linear in f): a replay, a reverse-mode adjoint of the spatial recursion,
  * and a forward-mode tangent in rho and gamma.
+ *
+ * Beside the DFT basis with the constant compensation:
+ *  - the transform-domain form of the same method (Sec. 2, closing remark),
+ *    the like-for-like CPU program and a second check of the re-projection;
+ *  - OFSE's compensation (Sec. 3, Eq. 10-13) with Q[u] = sum_l P[l] W[u - l]
+ *    summed directly, and its factors gamma_u;
+ *  - the 2-D DCT-II basis (Sec. 2 names it as the other transform-domain
+ *    basis), with its replay and adjoint;
+ *  - the squared error over B after every iteration count (Fig. 4, Fig. 5);
+ *  - a threaded batch driver over a frame and its lost blocks.
  */
 #include <math.h>
 #include <pthread.h>
