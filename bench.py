@@ -94,6 +94,17 @@ def reduce_max(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def allreduce_sum_(t, world: int):
+    """In-place sum of a tensor over ranks: the gradient of the whole job's
+    loss with respect to the shared rho and gamma in a data-parallel tuning
+    step (each rank holds other frames' blocks; the only exchange of the
+    backward).  A no-op on one rank."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
+
+
 def job_value(units_per_rank: int, world: int, ms: float) -> float:
     """Whole-job throughput: the units all ranks processed over the slowest
     rank's time (weak scaling, every rank runs its own batch)."""
@@ -576,6 +587,7 @@ def main():
         torch.mul(torch.sub(ob, truth, out=gblk), 2.0, out=gblk)   # dl/dB for l = sum (B - f)^2
         binding.fofse_backward(handles, blocks, frame, avail, tr, w0, gblk, grad_frame=gframe,
                                grad_rho_gamma=grg, workspace=ws, stream=stream)
+        allreduce_sum_(grg, world)   # shared rho / gamma: the job's gradient
 
     for _ in range(3):
         fwd_bwd()
@@ -600,7 +612,8 @@ def main():
     fwd_bwd_line = {"ms_per_step": fb_tot / args.steps,
                     "blocks_per_s": world * n * args.steps / (fb_tot * 1e-3),
                     "backward_ms": bw_only, "loss": "sum over B of (B_hat - f_true)^2",
-                    "grads": "support samples, rho, gamma (path frozen)"}
+                    "grads": "support samples, rho, gamma (path frozen); rho / gamma summed "
+                             "over ranks (all-reduce) when there are several"}
 
     # ---- end to end through the C ABI with host buffers ----
     h_frame = torch.from_numpy(wl.frame).pin_memory()

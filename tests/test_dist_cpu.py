@@ -1,7 +1,8 @@
 """The multi-process path of bench.py on CPU: two gloo ranks (the lost blocks
-shard with no collective; the only collectives are the barrier around the
-timed region and the max over ranks of the elapsed time), and the reference
-arm printing only on rank 0."""
+shard with no collective in the forward; the collectives are the barrier
+around the timed region, the max over ranks of the elapsed time, and in the
+forward+backward step the sum over ranks of the shared rho / gamma
+gradients), and the reference arm printing only on rank 0."""
 import json
 import os
 import socket
@@ -30,7 +31,9 @@ def _worker(rank, world, port, out):
     try:
         bench.barrier(w)
         t = bench.reduce_max(1.0 + 10.0 * r, w)     # rank 1 is the slowest
-        out[r] = (r, w, local, t, bench.job_value(1000, w, t))
+        import torch
+        g = bench.allreduce_sum_(torch.tensor([[1.0 + r, 2.0 * r]]), w)   # rho / gamma gradients
+        out[r] = (r, w, local, t, bench.job_value(1000, w, t), g.tolist())
         bench.barrier(w)
     finally:
         dist.destroy_process_group()
@@ -45,10 +48,11 @@ def test_two_gloo_ranks_max_time_and_job_value():
         res = dict(out)
     assert sorted(res) == [0, 1]
     for r in range(world):
-        rank, w, local, t, v = res[r]
+        rank, w, local, t, v, g = res[r]
         assert (rank, w, local) == (r, world, r)
         assert t == 11.0                              # max over ranks, on every rank
         assert v == pytest.approx(2 * 1000 / 11.0e-3)  # all ranks' units / slowest time
+        assert g == [[3.0, 2.0]]                      # rho / gamma gradients summed over ranks
 
 
 def test_single_rank_helpers_need_no_process_group():
@@ -57,6 +61,9 @@ def test_single_rank_helpers_need_no_process_group():
     assert bench.reduce_max(3.5, 1) == 3.5
     bench.barrier(1)
     assert bench.job_value(804, 1, 1.0) == pytest.approx(804e3)
+    import torch
+    g = torch.tensor([[1.0, 2.0]])
+    assert bench.allreduce_sum_(g, 1) is g and g.tolist() == [[1.0, 2.0]]
 
 
 def test_reference_arm_rank_nonzero_exits_quietly():
