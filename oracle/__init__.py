@@ -49,7 +49,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = ctypes.CDLL(build())
+            # FOFSE_ORACLE_LIB: a build of a deliberately broken copy of the
+            # oracle, loaded by the mutation test to show that a pin fails
+            _lib = ctypes.CDLL(os.environ.get("FOFSE_ORACLE_LIB") or build())
             _declare(_lib)
     return _lib
 
