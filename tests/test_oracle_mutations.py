@@ -26,6 +26,11 @@ MUTATIONS = [
      ["tests/test_oracle_dct.py"]),
     ("curve-clip", "v = v < 0.0 ? 0.0 : (v > 255.0 ? 255.0 : v);", "v = v < 0.0 ? 0.0 : v;",
      ["tests/test_oracle_curve.py"]),
+    ("fd-conjugate", "ti += cr * W_im[b] - ci * W_re[b];", "ti += cr * W_im[b] + ci * W_re[b];", [PINS]),
+    ("ofse-factor", "gr = W0 * (pr * q_re + pi * q_im) / den;", "gr = (pr * q_re + pi * q_im) / den;",
+     ["tests/test_oracle_ofse.py"]),
+    ("dct-energy-scale", "double e = P[i] * P[i] * (k1 ? 2.0 : 1.0) * (k2 ? 2.0 : 1.0);",
+     "double e = P[i] * P[i];", ["tests/test_oracle_dct.py"]),
 ]
 
 
