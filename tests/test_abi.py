@@ -60,3 +60,22 @@ def test_batch_calls_reject_null_arguments(lib):
     assert lib.fofse_plan_set_precision(None, 0) == B.E_ARG
     assert lib.fofse_workspace_bytes(None, 1, 10) == 0
     lib.fofse_plan_destroy(None)
+
+
+def test_newer_entry_points_reject_null_arguments(lib):
+    """Setters, the factor-returning batch call, the error curve and the
+    probes validate their arguments on the host (no GPU needed)."""
+    null = ctypes.c_void_p()
+    assert lib.fofse_plan_set_compensation(None, 1) == B.E_ARG
+    assert lib.fofse_plan_set_basis(None, 1) == B.E_ARG
+    assert lib.fofse_plan_set_variant(None, 0) == B.E_ARG
+    assert lib.fofse_plan_variant_count(None) == 0
+    assert lib.fofse_extrapolate_batch_gamma(None, 1, null, 1, null, null, 8, 8, 8, null, null, null,
+                                             null, null, null, null, null, null) == B.E_ARG
+    assert lib.fofse_extrapolate_batch_noalloc(None, 1, null, 1, null, null, 8, 8, 8, null, null,
+                                               null, null, null, null) == B.E_ARG
+    assert lib.fofse_error_curve(None, 1, null, 1, null, null, 8, 8, 8, null, null) == B.E_ARG
+    out = ctypes.c_double()
+    assert lib.fofse_probe_smem(0, 1, null, ctypes.byref(out), null) == B.E_ARG
+    assert lib.fofse_probe_fma(1, 0, null, ctypes.byref(out), null) == B.E_ARG
+    assert lib.fofse_probe_smem(1, 1, None, ctypes.byref(out), null) == B.E_ARG
