@@ -754,3 +754,9 @@ fofse_status fofse_check(void* stream) {
 }
 
 }  // extern "C"
+
+namespace fofse {
+// FOFSE_E_CUDA for `e`, remembered for fofse_last_cuda_error (used by the
+// translation units outside this file)
+fofse_status record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+}  // namespace fofse

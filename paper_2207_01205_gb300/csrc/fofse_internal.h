@@ -113,6 +113,9 @@ struct CurveArgs {
   float* sse;  // n_blocks x trace_stride
 };
 
+// FOFSE_E_CUDA for a failed CUDA call, remembered for fofse_last_cuda_error.
+fofse_status record_cuda_error(cudaError_t e);
+
 // Launchers (one per translation unit).  Return cudaSuccess or the launch error.
 cudaError_t launch_forward(const FwdArgs& a, const CUtensorMap* tm_frame,
                            const CUtensorMap* tm_avail, cudaStream_t stream);

@@ -71,7 +71,7 @@ fofse_status fofse_probe_smem(int ctas, int rounds, float* d_sink, double* bytes
   if (ctas < 1 || rounds < 1 || !d_sink || !bytes) return FOFSE_E_ARG;
   fofse_smem_probe_kernel<<<ctas, kProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(d_sink, rounds);
   const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return FOFSE_E_CUDA;
+  if (e != cudaSuccess) return record_cuda_error(e);
   *bytes = (double)ctas * kProbeThreads * rounds * kProbeUnroll * 16.0;
   return FOFSE_OK;
 }
@@ -81,7 +81,7 @@ fofse_status fofse_probe_fma(int ctas, int rounds, float* d_sink, double* fmas, 
   fofse_fma_probe_kernel<<<ctas, kProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       d_sink, rounds, 0.999f, 1e-3f);
   const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return FOFSE_E_CUDA;
+  if (e != cudaSuccess) return record_cuda_error(e);
   *fmas = (double)ctas * kProbeThreads * rounds * 8.0;
   return FOFSE_OK;
 }
