@@ -24,6 +24,14 @@
  * the smallest k1 T + k2; the coefficient of a self-conjugate index is real;
  * samples outside the frame, in other lost blocks or outside the chosen
  * support shape are not in A.
+ * Variants selected per plan: OFSE's compensation (Sec. 3, Eq. 10-13:
+ * c = P[u]^2 / Q[u] with Q[u] = sum_l P[l] W[u - l]) instead of the constant
+ * gamma, and the real 2-D DCT-II basis instead of the DFT (fofse_plan_set_
+ * compensation, fofse_plan_set_basis).  Besides the forward: the adjoint along
+ * the frozen selection path (fofse_backward), the squared error after every
+ * iteration count (fofse_error_curve), the compensation factor of every
+ * iteration (fofse_extrapolate_batch_gamma), and rho / gamma read from device
+ * memory per call (d_rho_gamma).
  *
  * Conventions for every entry point:
  *  - Pointers named d_* are DEVICE memory owned by the caller, on the device
