@@ -26,7 +26,7 @@ def _key(plan, n_blocks, device):
     name = torch.cuda.get_device_name(device)
     bucket = 1 << max(0, int(n_blocks) - 1).bit_length()
     return (f"{name}|T{plan.fft_size}|b{plan.block}|br{plan.border}|I{plan.iters}|"
-            f"{plan.precision}|s{plan.support}|c{getattr(plan, 'compensation', 0)}|b{getattr(plan, 'basis', 0)}|n{bucket}")
+            f"{plan.precision}|s{plan.support}|c{getattr(plan, 'compensation', 0)}|basis{getattr(plan, 'basis', 0)}|n{bucket}")
 
 
 def _load(path):
