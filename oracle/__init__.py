@@ -34,6 +34,12 @@ class OraclePlan(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("compensation", ctypes.c_int), ("basis", ctypes.c_int)]
 
 
+class OracleVolumePlan(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("border", ctypes.c_int), ("depth", ctypes.c_int),
+                ("fft_size", ctypes.c_int), ("fft_time", ctypes.c_int), ("iters", ctypes.c_int),
+                ("rho", ctypes.c_double), ("gamma", ctypes.c_double)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (gcc, -O2, IEEE double, no contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -110,6 +116,18 @@ def _declare(L):
                                        ctypes.POINTER(OraclePlan), _c_int, _ip, _ip, _c_int, _dp,
                                        _c_int, _dp, _dp, _c_int]
     L.oracle_batch_adjoint.restype = _c_int
+    L.oracle_distance3.argtypes = [_c_int, _c_int, _c_int, _dp]
+    L.oracle_weights3.argtypes = [_c_int, _c_int, _c_int, _c_double, _u8p, _dp]
+    L.oracle_cut_volume.argtypes = [_fp, _u8p] + [_c_int] * 10 + [_dp, _u8p]
+    L.oracle_project3.argtypes = [_c_int, _c_int, _c_int, _c_int, _dp, _dp, _dp]
+    L.oracle_select3.argtypes = [_c_int, _c_int, _dp, _dp, _ip, _dp]
+    L.oracle_extrapolate_volume.argtypes = [_c_int, _c_int, _c_int, _c_int, _dp, _dp, _c_double,
+                                            _c_int, _dp, _ip, _dp, _dp, _dp, _dp]
+    L.oracle_extrapolate_volume.restype = _c_int
+    L.oracle_batch_volume.argtypes = [_fp, _u8p, _c_int, _c_int, _c_int, _c_int, _ip, _c_int,
+                                      ctypes.POINTER(OracleVolumePlan), _dp, _ip, _dp, _ip, _dp,
+                                      _dp, _dp, _c_int]
+    L.oracle_batch_volume.restype = _c_int
 
 
 def _p(a, t):
@@ -408,3 +426,95 @@ def batch_adjoint(frame, avail, blocks, plans, path, e_blocks, threads: int | No
                                _p(e, _dp), bmax * bmax, _p(gf, _dp), _p(grg, _dp),
                                threads or os.cpu_count() or 1)
     return gf, grg
+
+
+# ----------------------------------------------------------------------------
+# video volumes (the method over three-dimensional sets, Sec. 1)
+# ----------------------------------------------------------------------------
+
+def distance3(block: int, border: int, depth: int) -> np.ndarray:
+    """(Lt, Ls, Ls) distances to the centre of B in the centre frame."""
+    Ls, Lt = block + 2 * border, 2 * depth + 1
+    d = np.empty((Lt, Ls, Ls))
+    lib().oracle_distance3(block, border, depth, _p(d, _dp))
+    return d
+
+
+def weights3(block: int, border: int, depth: int, rho: float, avail_L: np.ndarray) -> np.ndarray:
+    aL = np.ascontiguousarray(avail_L, dtype=np.uint8)
+    w = np.empty(aL.shape)
+    lib().oracle_weights3(block, border, depth, float(rho), _p(aL, _u8p), _p(w, _dp))
+    return w
+
+
+def cut_volume(video, avail, t, y, x, block, border, depth):
+    """(fL, aL) of the volume around B (top-left (y, x) in frame t)."""
+    video = np.ascontiguousarray(video, dtype=np.float32)
+    avail = np.ascontiguousarray(avail, dtype=np.uint8)
+    F, H, W = video.shape
+    Ls, Lt = block + 2 * border, 2 * depth + 1
+    fL = np.empty((Lt, Ls, Ls))
+    aL = np.empty((Lt, Ls, Ls), dtype=np.uint8)
+    lib().oracle_cut_volume(_p(video, _fp), _p(avail, _u8p), F, H, W, W, int(t), int(y), int(x),
+                            block, border, depth, _p(fL, _dp), _p(aL, _u8p))
+    return fL, aL
+
+
+def project3(rw: np.ndarray, T: int, Tt: int) -> np.ndarray:
+    """P[k1, k2, k3] = sum rw exp(-j2pi (k1 m / T + k2 n / T + k3 tau / Tt)),
+    rw indexed (tau, m, n); returns shape (T, T, Tt)."""
+    rw = _f64(rw)
+    Lt, Ls = rw.shape[0], rw.shape[1]
+    pr = np.empty((T, T, Tt))
+    pi = np.empty((T, T, Tt))
+    lib().oracle_project3(Lt, Ls, T, Tt, _p(rw, _dp), _p(pr, _dp), _p(pi, _dp))
+    return pr + 1j * pi
+
+
+def select3(P: np.ndarray):
+    """Eq. 9 over the canonical set of the 3-D grid; returns ((u1, u2, u3), gap)."""
+    T, Tt = P.shape[0], P.shape[2]
+    pr, pi = _f64(P.real), _f64(P.imag)
+    u = np.zeros(3, dtype=np.int32)
+    gap = ctypes.c_double()
+    lib().oracle_select3(T, Tt, _p(pr, _dp), _p(pi, _dp), _p(u, _ip), ctypes.byref(gap))
+    return tuple(int(v) for v in u), gap.value
+
+
+def extrapolate_volume(fL, wL, T: int, Tt: int, gamma: float, iters: int) -> AreaResult:
+    """FOFSE over one volume (spatial re-projection): g (Lt, Ls, Ls), path
+    (iters, 3), dc complex, gap, w0."""
+    fL, wL = _f64(fL), _f64(wL)
+    Lt, Ls = fL.shape[0], fL.shape[1]
+    g = np.empty((Lt, Ls, Ls))
+    path = np.zeros((iters, 3), dtype=np.int32)
+    dr, di, gap = np.zeros(iters), np.zeros(iters), np.zeros(iters)
+    w0 = ctypes.c_double()
+    st = lib().oracle_extrapolate_volume(Lt, Ls, T, Tt, _p(fL, _dp), _p(wL, _dp), float(gamma),
+                                         iters, _p(g, _dp), _p(path, _ip), _p(dr, _dp),
+                                         _p(di, _dp), _p(gap, _dp), ctypes.byref(w0))
+    return AreaResult(st, g, path, dr + 1j * di, gap, w0.value)
+
+
+def run_batch_volume(video, avail, blocks, plan, threads: int | None = None) -> BatchResult:
+    """Extrapolate every block of ``blocks`` ((n, 3) int: t, y, x) of a video
+    (F, H, W) with one volume plan (fields block, border, depth, fft_size,
+    fft_time, rho, gamma, iters).  path (n, iters, 3)."""
+    video = np.ascontiguousarray(video, dtype=np.float32)
+    avail = np.ascontiguousarray(avail, dtype=np.uint8)
+    blocks = _i32(blocks).reshape(-1, 3)
+    F, H, W = video.shape
+    n, b, it = blocks.shape[0], plan.block, plan.iters
+    out = np.zeros((n, b, b))
+    status = np.zeros(n, dtype=np.int32)
+    w0 = np.zeros(n)
+    path = np.zeros((n, it, 3), dtype=np.int32)
+    dr, di, gap = np.zeros((n, it)), np.zeros((n, it)), np.zeros((n, it))
+    cp = OracleVolumePlan(plan.block, plan.border, plan.depth, plan.fft_size, plan.fft_time,
+                          plan.iters, float(plan.rho), float(plan.gamma))
+    threads = threads or os.cpu_count() or 1
+    used = lib().oracle_batch_volume(_p(video, _fp), _p(avail, _u8p), F, H, W, W,
+                                     _p(blocks, _ip), n, ctypes.byref(cp), _p(out, _dp),
+                                     _p(status, _ip), _p(w0, _dp), _p(path, _ip), _p(dr, _dp),
+                                     _p(di, _dp), _p(gap, _dp), threads)
+    return BatchResult(out, status, w0, path, dr + 1j * di, gap, used)

@@ -45,7 +45,9 @@
  *  - the 2-D DCT-II basis (Sec. 2 names it as the other transform-domain
  *    basis), with its replay and adjoint;
  *  - the squared error over B after every iteration count (Fig. 4, Fig. 5);
- *  - a threaded batch driver over a frame and its lost blocks.
+ *  - a threaded batch driver over a frame and its lost blocks;
+ *  - video volumes (Sec. 1: the method carried over to three-dimensional
+ *    sets), with the readings listed at the head of that section.
  */
 #include <math.h>
 #include <pthread.h>
@@ -1031,6 +1033,288 @@ int oracle_batch_adjoint(const float* frame, const unsigned char* avail, int hei
         free(J.grad_rg_t[t]);
     }
     free(J.grad_frame_t); free(J.grad_rg_t); free(th); free(args);
+    pthread_mutex_destroy(&J.lock);
+    return n_threads;
+}
+
+/* -------------------------------------------------------------------------- */
+/* Video volumes (Sec. 1: the method carried over to three-dimensional sets)   */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * The paper states the algorithm for images only and notes that it carries
+ * over to three-dimensional signals; the readings taken here:
+ *  - the area L is a volume of Lt = 2 depth + 1 frames (the frame of the lost
+ *    block B at its centre, index tau = depth) x Ls x Ls samples, stored
+ *    tau-major, tau then m then n;
+ *  - A = the usable samples of L outside B in the centre frame; the samples
+ *    of B's position in the other frames belong to A when they are usable;
+ *  - w[tau,m,n] = rho_hat^d with d the Euclidean distance to the centre of B
+ *    in the centre frame, one frame counting as one sample (Eq. 15 over three
+ *    coordinates);
+ *  - basis phi_k[tau,m,n] = exp(+j 2 pi (k1 m / T + k2 n / T + k3 tau / Tt))
+ *    over a T x T x Tt grid with L at its origin (the 3-D DFT), so that
+ *    p_k = P[k] / W0 as in two dimensions;
+ *  - conjugate pairs and the canonical set as in two dimensions with the
+ *    row-major index lin(k) = (k1 T + k2) Tt + k3: k is canonical when
+ *    lin(k) <= lin(-k), exact ties of the selection go to the smallest lin(k),
+ *    and s(u) = 0 for the self-conjugate indices (2u = 0 mod (T, T, Tt));
+ *  - constant compensation c_u = gamma p_u (Eq. 14).
+ * With depth 0 and Tt = 1 every step reduces to the two-dimensional oracle.
+ */
+
+typedef struct {
+    int block;     /* lost block side b                               */
+    int border;    /* spatial support border width                    */
+    int depth;     /* frames on each side of B's frame (Lt = 2 depth + 1) */
+    int fft_size;  /* T (both spatial axes)                           */
+    int fft_time;  /* Tt (time axis), Tt >= Lt                        */
+    int iters;     /* I                                               */
+    double rho;    /* rho_hat of Eq. 15                               */
+    double gamma;  /* constant compensation factor of Eq. 14          */
+} oracle_vplan;
+
+static int pair_weight_s3(int u1, int u2, int u3, int T, int Tt) {
+    return ((2 * u1) % T == 0 && (2 * u2) % T == 0 && (2 * u3) % Tt == 0) ? 0 : 1;
+}
+
+static long lin3(int k1, int k2, int k3, int T, int Tt) {
+    return ((long)k1 * T + k2) * Tt + k3;
+}
+
+static int in_canonical_set3(int k1, int k2, int k3, int T, int Tt) {
+    return lin3(k1, k2, k3, T, Tt) <= lin3((T - k1) % T, (T - k2) % T, (Tt - k3) % Tt, T, Tt);
+}
+
+/* Distance of every sample of the volume to the centre of B in frame tau = depth. */
+void oracle_distance3(int block, int border, int depth, double* dist) {
+    int Ls = block + 2 * border, Lt = 2 * depth + 1;
+    double c = border + (block - 1) / 2.0;
+    for (int t = 0; t < Lt; ++t)
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) {
+                double dt = t - depth, dm = m - c, dn = n - c;
+                dist[((size_t)t * Ls + m) * Ls + n] = sqrt(dt * dt + dm * dm + dn * dn);
+            }
+}
+
+/* w = rho_hat^d on A (usable, and not B of the centre frame), 0 elsewhere. */
+void oracle_weights3(int block, int border, int depth, double rho, const unsigned char* availL,
+                     double* w) {
+    int Ls = block + 2 * border, Lt = 2 * depth + 1;
+    size_t N = (size_t)Lt * Ls * Ls;
+    double* dist = (double*)malloc(sizeof(double) * N);
+    oracle_distance3(block, border, depth, dist);
+    for (int t = 0; t < Lt; ++t)
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) {
+                size_t i = ((size_t)t * Ls + m) * Ls + n;
+                int inB = t == depth && m >= border && m < border + block && n >= border &&
+                          n < border + block;
+                w[i] = (availL[i] && !inB) ? pow(rho, dist[i]) : 0.0;
+            }
+    free(dist);
+}
+
+/* Cut the volume of a block (B's top-left corner (y, x) in frame t) out of a
+ * video of `frames` frames, each height x width with `pitch` elements per row
+ * and frames back to back; samples outside the video are unusable (0). */
+void oracle_cut_volume(const float* video, const unsigned char* avail, int frames, int height,
+                       int width, int pitch, int t, int y, int x, int block, int border, int depth,
+                       double* fL, unsigned char* aL) {
+    int Ls = block + 2 * border, Lt = 2 * depth + 1;
+    for (int tau = 0; tau < Lt; ++tau)
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) {
+                int ft = t - depth + tau, fy = y - border + m, fx = x - border + n;
+                int in = ft >= 0 && ft < frames && fy >= 0 && fy < height && fx >= 0 && fx < width;
+                size_t i = ((size_t)tau * Ls + m) * Ls + n;
+                size_t s = ((size_t)ft * height + fy) * pitch + fx;
+                fL[i] = in ? (double)video[s] : 0.0;
+                aL[i] = in ? avail[s] : 0;
+            }
+}
+
+/* P[k] = sum over the volume of rw exp(-j 2 pi (k1 m / T + k2 n / T + k3 tau / Tt)),
+ * P stored at lin(k): every frame's 2-D projection, then the sum over tau. */
+void oracle_project3(int Lt, int Ls, int T, int Tt, const double* rw, double* P_re,
+                     double* P_im) {
+    size_t plane = (size_t)T * T;
+    double* Y_re = (double*)malloc(sizeof(double) * Lt * plane);
+    double* Y_im = (double*)malloc(sizeof(double) * Lt * plane);
+    double* ct = (double*)malloc(sizeof(double) * Tt);
+    double* st = (double*)malloc(sizeof(double) * Tt);
+    twiddles(Tt, ct, st);
+    for (int tau = 0; tau < Lt; ++tau)
+        oracle_project(Ls, T, rw + (size_t)tau * Ls * Ls, Y_re + tau * plane, Y_im + tau * plane);
+    for (int k1 = 0; k1 < T; ++k1)
+        for (int k2 = 0; k2 < T; ++k2)
+            for (int k3 = 0; k3 < Tt; ++k3) {
+                double re = 0.0, im = 0.0;
+                for (int tau = 0; tau < Lt; ++tau) {
+                    int p = (k3 * tau) % Tt;
+                    double yr = Y_re[tau * plane + k1 * T + k2], yi = Y_im[tau * plane + k1 * T + k2];
+                    re += yr * ct[p] + yi * st[p];  /* (yr + j yi)(ct - j st) */
+                    im += yi * ct[p] - yr * st[p];
+                }
+                P_re[lin3(k1, k2, k3, T, Tt)] = re;
+                P_im[lin3(k1, k2, k3, T, Tt)] = im;
+            }
+    free(Y_re); free(Y_im); free(ct); free(st);
+}
+
+/* Eq. 9 over the canonical set of the 3-D grid; u[3]; gap as oracle_select. */
+void oracle_select3(int T, int Tt, const double* P_re, const double* P_im, int* u, double* gap) {
+    double top = -1.0, second = -1.0;
+    long bi = 0;
+    for (int k1 = 0; k1 < T; ++k1)
+        for (int k2 = 0; k2 < T; ++k2)
+            for (int k3 = 0; k3 < Tt; ++k3) {
+                if (!in_canonical_set3(k1, k2, k3, T, Tt)) continue;
+                long i = lin3(k1, k2, k3, T, Tt);
+                double e = P_re[i] * P_re[i] + P_im[i] * P_im[i];
+                if (e > top) {
+                    second = top;
+                    top = e;
+                    bi = i;
+                } else if (e > second) {
+                    second = e;
+                }
+            }
+    u[0] = (int)(bi / Tt / T);
+    u[1] = (int)(bi / Tt % T);
+    u[2] = (int)(bi % Tt);
+    if (gap) *gap = top > 0.0 ? (top - (second < 0.0 ? 0.0 : second)) / top : 0.0;
+}
+
+/* g += (1 + s(u)) Re(c phi_u) over the volume, phases as integers mod T Tt. */
+static void add_basis_pair3(int Lt, int Ls, int T, int Tt, const int* u, double c_re, double c_im,
+                            double* g) {
+    int M = T * Tt;
+    double mult = 1.0 + pair_weight_s3(u[0], u[1], u[2], T, Tt);
+    for (int tau = 0; tau < Lt; ++tau)
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) {
+                long p = (((long)u[0] * m + (long)u[1] * n) * Tt + (long)u[2] * tau * T) % M;
+                double th = TWO_PI * (double)p / (double)M;
+                g[((size_t)tau * Ls + m) * Ls + n] += mult * (c_re * cos(th) - c_im * sin(th));
+            }
+}
+
+/*
+ * FOFSE over one volume, spatial re-projection in every iteration: fL, wL
+ * Lt x Ls x Ls; g the final model over the volume; path (iters x 3), dc,
+ * gap, w0 as oracle_extrapolate_area (any may be NULL).
+ */
+int oracle_extrapolate_volume(int Lt, int Ls, int T, int Tt, const double* fL, const double* wL,
+                              double gamma, int iters, double* g, int* path, double* dc_re,
+                              double* dc_im, double* gap, double* w0_out) {
+    size_t N = (size_t)Lt * Ls * Ls, K = (size_t)T * T * Tt;
+    double W0 = 0.0;
+    for (size_t i = 0; i < N; ++i) W0 += wL[i];
+    if (w0_out) *w0_out = W0;
+    for (size_t i = 0; i < N; ++i) g[i] = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    for (size_t i = 0; i < N; ++i)
+        if (wL[i] != 0.0 && !isfinite(fL[i])) return ORC_NONFINITE;
+    double* rw = (double*)malloc(sizeof(double) * N);
+    double* P_re = (double*)malloc(sizeof(double) * K);
+    double* P_im = (double*)malloc(sizeof(double) * K);
+    for (int it = 0; it < iters; ++it) {
+        for (size_t i = 0; i < N; ++i) rw[i] = wL[i] != 0.0 ? wL[i] * (fL[i] - g[i]) : 0.0;
+        oracle_project3(Lt, Ls, T, Tt, rw, P_re, P_im);
+        int u[3];
+        double gp;
+        oracle_select3(T, Tt, P_re, P_im, u, &gp);
+        long ui = lin3(u[0], u[1], u[2], T, Tt);
+        double cr = gamma * P_re[ui] / W0;
+        double ci = pair_weight_s3(u[0], u[1], u[2], T, Tt) ? gamma * P_im[ui] / W0 : 0.0;
+        add_basis_pair3(Lt, Ls, T, Tt, u, cr, ci, g);
+        if (path) {
+            path[3 * it] = u[0];
+            path[3 * it + 1] = u[1];
+            path[3 * it + 2] = u[2];
+        }
+        if (dc_re) dc_re[it] = cr;
+        if (dc_im) dc_im[it] = ci;
+        if (gap) gap[it] = gp;
+    }
+    free(rw); free(P_re); free(P_im);
+    return ORC_OK;
+}
+
+typedef struct {
+    const float* video;
+    const unsigned char* avail;
+    int frames, height, width, pitch;
+    const int* blocks;          /* n x 3: t, y, x */
+    oracle_vplan plan;
+    int n_blocks;
+    double* out_blocks;         /* n x b x b */
+    int* status;
+    double* w0;
+    int* path;                  /* n x iters x 3 (nullable) */
+    double* dc_re;              /* n x iters (nullable) */
+    double* dc_im;
+    double* gap;
+    int next;
+    pthread_mutex_t lock;
+} vbatch_job;
+
+static void run_one_volume(vbatch_job* J, int bi) {
+    const oracle_vplan* P = &J->plan;
+    const int* bd = J->blocks + 3 * bi;
+    int Ls = P->block + 2 * P->border, Lt = 2 * P->depth + 1;
+    size_t N = (size_t)Lt * Ls * Ls, I = (size_t)P->iters;
+    double* fL = (double*)malloc(sizeof(double) * N);
+    double* wL = (double*)malloc(sizeof(double) * N);
+    double* g = (double*)malloc(sizeof(double) * N);
+    unsigned char* aL = (unsigned char*)malloc(N);
+    oracle_cut_volume(J->video, J->avail, J->frames, J->height, J->width, J->pitch, bd[0], bd[1],
+                      bd[2], P->block, P->border, P->depth, fL, aL);
+    oracle_weights3(P->block, P->border, P->depth, P->rho, aL, wL);
+    J->status[bi] = oracle_extrapolate_volume(
+        Lt, Ls, P->fft_size, P->fft_time, fL, wL, P->gamma, P->iters, g,
+        J->path ? J->path + 3 * I * bi : NULL, J->dc_re ? J->dc_re + I * bi : NULL,
+        J->dc_im ? J->dc_im + I * bi : NULL, J->gap ? J->gap + I * bi : NULL,
+        J->w0 ? J->w0 + bi : NULL);
+    double* ob = J->out_blocks + (size_t)bi * P->block * P->block;
+    for (int m = 0; m < P->block; ++m)
+        for (int n = 0; n < P->block; ++n)
+            ob[m * P->block + n] = g[((size_t)P->depth * Ls + m + P->border) * Ls + n + P->border];
+    free(fL); free(wL); free(g); free(aL);
+}
+
+static void* vbatch_worker(void* arg) {
+    vbatch_job* J = (vbatch_job*)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int bi = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (bi >= J->n_blocks) break;
+        run_one_volume(J, bi);
+    }
+    return NULL;
+}
+
+/* Extrapolate every listed block of a video with one volume plan; returns
+ * the number of threads used. */
+int oracle_batch_volume(const float* video, const unsigned char* avail, int frames, int height,
+                        int width, int pitch, const int* blocks, int n_blocks,
+                        const oracle_vplan* plan, double* out_blocks, int* status, double* w0,
+                        int* path, double* dc_re, double* dc_im, double* gap, int n_threads) {
+    vbatch_job J;
+    J.video = video; J.avail = avail; J.frames = frames; J.height = height; J.width = width;
+    J.pitch = pitch; J.blocks = blocks; J.plan = *plan; J.n_blocks = n_blocks;
+    J.out_blocks = out_blocks; J.status = status; J.w0 = w0; J.path = path; J.dc_re = dc_re;
+    J.dc_im = dc_im; J.gap = gap; J.next = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_blocks) n_threads = n_blocks > 0 ? n_blocks : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, vbatch_worker, &J);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(th);
     pthread_mutex_destroy(&J.lock);
     return n_threads;
 }

@@ -276,3 +276,122 @@ def small_frame(seed: int, *, height: int = 96, width: int = 128, n_lost: int = 
     frame = truth.copy()
     _mark_lost(frame, avail, blocks, [plan], fill)
     return Workload(f"small-{width}x{height}", frame, truth, avail, blocks, [plan])
+
+
+# ----------------------------------------------------------------------------
+# video volumes
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class VolumePlanSpec:
+    """Parameters of extrapolation over video volumes: lost block b x b in one
+    frame, spatial border, ``depth`` frames on each side of it, a
+    T x T x Tt DFT grid (T = fft_size, Tt = fft_time), rho-hat, gamma, I."""
+    block: int
+    border: int
+    depth: int
+    fft_size: int
+    fft_time: int
+    rho: float
+    gamma: float
+    iters: int
+
+    def __post_init__(self):
+        self.rho = float(np.float32(self.rho))
+        self.gamma = float(np.float32(self.gamma))
+
+
+@dataclasses.dataclass
+class VideoWorkload:
+    name: str
+    video: np.ndarray          # (F, H, W) float32 observed frames (lost samples hold `fill`)
+    truth: np.ndarray          # (F, H, W) float32 ground truth
+    avail: np.ndarray          # (F, H, W) uint8
+    blocks: np.ndarray         # (n, 3) int32: frame t, y, x (top-left of B)
+    plan: VolumePlanSpec
+
+    @property
+    def n_blocks(self):
+        return int(self.blocks.shape[0])
+
+
+def moving_frames(rng: np.random.Generator, n_frames: int, height: int, width: int, *,
+                  max_step: int = 2, noise_sigma: float = 2.0, **frame_kw) -> np.ndarray:
+    """Frames of a camera pan: crops of one natural_frame canvas, frame i
+    offset from frame i-1 by a random integer step of 0..max_step px per axis,
+    each with its own sensor noise N(0, sigma^2), clipped and rounded to 8 bit.
+    Returns float32 (n_frames, height, width)."""
+    margin = n_frames * max_step
+    canvas = natural_frame(rng, height + margin, width + margin, noise_sigma=0.0, **frame_kw)
+    steps = rng.integers(0, max_step + 1, size=(n_frames, 2))
+    offs = np.cumsum(steps, axis=0) - steps[0]
+    out = np.empty((n_frames, height, width), dtype=np.float32)
+    for i, (oy, ox) in enumerate(offs):
+        f = canvas[oy:oy + height, ox:ox + width].astype(np.float64)
+        f += rng.normal(0.0, noise_sigma, size=f.shape)
+        out[i] = np.rint(np.clip(f, 0.0, 255.0))
+    return out
+
+
+def _lose_tiles(rng, avail, frame_index, b, loss):
+    """Pick round(loss * tiles) of frame frame_index's full b x b tiles."""
+    _, H, W = avail.shape
+    ty, tx = H // b, W // b
+    n = int(round(loss * ty * tx))
+    pick = np.sort(rng.choice(ty * tx, size=n, replace=False))
+    return np.stack([np.full_like(pick, frame_index), (pick // tx) * b, (pick % tx) * b], axis=1)
+
+
+def video_concealment(seed: int | None = None, *, n_frames: int = 3, height: int = 1080,
+                      width: int = 1920, loss: float = 0.10, plan: VolumePlanSpec | None = None,
+                      fill: float = 0.0) -> VideoWorkload:
+    """A camera pan of ``n_frames`` 1920x1080 frames; in every frame 10 % of
+    the full 16x16 tiles are lost uniformly at random and independently of
+    the other frames.  The blocks to conceal are the centre frame's; those of
+    the other frames only make samples of the volumes unusable.  Plan: border
+    8 (32x32 spatial area), one frame on each side (depth 1), 32x32x4 DFT,
+    rho 0.8, gamma 0.5, 200 iterations."""
+    rng = rng_for(5, seed)
+    plan = plan or VolumePlanSpec(16, 8, 1, 32, 4, 0.8, 0.5, 200)
+    b = plan.block
+    truth = moving_frames(rng, n_frames, height, width)
+    avail = np.ones(truth.shape, dtype=np.uint8)
+    video = truth.copy()
+    tc = n_frames // 2
+    lost = [_lose_tiles(rng, avail, t, b, loss) for t in range(n_frames)]
+    for tiles in lost:
+        for (t, y, x) in tiles:
+            avail[t, y:y + b, x:x + b] = 0
+            video[t, y:y + b, x:x + b] = fill
+    blocks = lost[tc].astype(np.int32)
+    return VideoWorkload(f"video-{n_frames}x{width}x{height}-16x16-T{plan.fft_size}x{plan.fft_time}"
+                         f"-I{plan.iters}", video, truth, avail, blocks, plan)
+
+
+def small_video(seed: int, *, n_frames: int = 3, height: int = 64, width: int = 96,
+                n_lost: int = 5, plan: VolumePlanSpec | None = None,
+                fill: float = 0.0) -> VideoWorkload:
+    """A few frames with a handful of lost blocks in every frame; the blocks to
+    conceal include the corners of the first and last frames (volumes that
+    reach beyond the video in space and time); for tests."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    plan = plan or VolumePlanSpec(8, 4, 1, 16, 4, 0.8, 0.5, 40)
+    b = plan.block
+    truth = moving_frames(rng, n_frames, height, width, n_sines=6, n_polys=4)
+    gy, gx = height // b, width // b
+    avail = np.ones(truth.shape, dtype=np.uint8)
+    video = truth.copy()
+    blocks = []
+    for t in range(n_frames):
+        cells = rng.choice(gy * gx, size=min(n_lost, gy * gx), replace=False)
+        if t == 0:
+            cells[0] = 0
+        if t == n_frames - 1:
+            cells[0] = gy * gx - 1
+        for c in np.unique(cells):
+            y, x = (c // gx) * b, (c % gx) * b
+            avail[t, y:y + b, x:x + b] = 0
+            video[t, y:y + b, x:x + b] = fill
+            blocks.append((t, y, x))
+    return VideoWorkload(f"small-video-{n_frames}x{width}x{height}", video, truth, avail,
+                         np.array(blocks, dtype=np.int32), plan)

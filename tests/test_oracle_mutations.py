@@ -13,6 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "fofse_oracle.c")
 OUT = os.path.join(ROOT, "oracle", "_build", "mutants")
 PINS = "tests/test_oracle_pins.py"
+VOL = "tests/test_oracle_volume.py"
 
 MUTATIONS = [
     ("projection-sign", "im -= rw[m * Ls + n] * s[p];", "im += rw[m * Ls + n] * s[p];", [PINS]),
@@ -31,6 +32,16 @@ MUTATIONS = [
      ["tests/test_oracle_ofse.py"]),
     ("dct-energy-scale", "double e = P[i] * P[i] * (k1 ? 2.0 : 1.0) * (k2 ? 2.0 : 1.0);",
      "double e = P[i] * P[i];", ["tests/test_oracle_dct.py"]),
+    ("volume-temporal-sign", "im += yi * ct[p] - yr * st[p];", "im += yi * ct[p] + yr * st[p];", [VOL]),
+    ("volume-centre", "double dt = t - depth, dm = m - c, dn = n - c;",
+     "double dt = t - depth - 1, dm = m - c, dn = n - c;", [VOL]),
+    ("volume-B-every-frame", "int inB = t == depth && m >= border", "int inB = m >= border", [VOL]),
+    ("volume-pair-weight", "(2 * u2) % T == 0 && (2 * u3) % Tt == 0) ? 0 : 1;",
+     "(2 * u2) % T == 0) ? 0 : 1;", [VOL]),
+    ("volume-canonical", "return lin3(k1, k2, k3, T, Tt) <= lin3(", "return lin3(k1, k2, k3, T, Tt) < lin3(",
+     [VOL]),
+    ("volume-tie-break", "if (e > top) {", "if (e >= top) {", [VOL]),
+    ("volume-synthesis-phase", "(long)u[2] * tau * T) % M;", "(long)u[2] * tau) % M;", [VOL]),
 ]
 
 
