@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--workload", default="conceal-1080p",
-                    choices=["conceal-1080p", "uneven-4k", "predict-720p"],
+                    choices=["conceal-1080p", "uneven-4k", "predict-720p", "video-1080p"],
                     help="the 1080p batch (default, the headline) or another workload")
     return ap.parse_args()
 
@@ -411,6 +411,160 @@ def run_other_workload(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+# FP64 work of the video-volume kernel (fofse_volume_kernel), per bin and
+# iteration: the update R -= c W[k-u] + s conj(c) W[k+u] as 8 fused
+# multiply-adds (16 flops) and, on the canonical bins, |R|^2 (a multiply and a
+# fused multiply-add, 3 flops); per spectrum the three separable DFT passes
+# (2 FMAs per real-input term along n, 4 per complex term along m and tau).
+# The nominal FP64 rate of a GB300 is 1.25 TFLOP/s at 2070 MHz over 152 SMs:
+# 4 flops per clock and SM.
+FP64_FLOPS_PER_CLK_PER_SM = 4
+
+
+def volume_flops(spec, n_ok):
+    T, Tt, Ls, Lt, it = spec.fft_size, spec.fft_time, spec.block + 2 * spec.border, \
+        2 * spec.depth + 1, spec.iters
+    K = T * T * Tt
+    canon = (K + 8) // 2 if Tt > 1 else (K + 4) // 2
+    per_iter = 16 * K + 3 * canon
+    dft = 2 * (4 * Lt * Ls * T * Ls + 8 * Lt * T * T * Ls + 8 * T * T * Tt * Lt)
+    return n_ok * (it * per_iter + dft)
+
+
+def run_volume_workload(args, rank, world, local):
+    """Device-timed extrapolation over video volumes: the 804 lost 16x16 blocks
+    of the centre frame of a three-frame 1920x1080 camera pan (10 % of every
+    frame's tiles lost), border 8, one frame on each side, 32x32x4 DFT grid,
+    rho 0.8, gamma 0.5, 200 iterations, FP64; one launch per step."""
+    import numpy as np
+    import torch
+    from paper_2207_01205_gb300 import api, binding, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    init_dist(world, "nccl")
+    binding.load()
+    wl = synth.video_concealment()
+    spec = wl.plan
+    plan = api.VolumePlan.from_spec(spec)
+    video = torch.from_numpy(wl.video).to(dev)
+    avail = torch.from_numpy(wl.avail).to(dev)
+    blocks = torch.from_numpy(wl.blocks).to(dev)
+    n, b, it = wl.n_blocks, spec.block, spec.iters
+    out = torch.empty((n, b, b), dtype=torch.float32, device=dev)
+    path = torch.empty((n, it, 3), dtype=torch.int32, device=dev)
+    coef = torch.empty((n, it, 2), dtype=torch.float64, device=dev)
+    w0 = torch.empty((n,), dtype=torch.float64, device=dev)
+    st = torch.empty((n,), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def fwd():
+        binding.fofse_extrapolate_volume_batch(plan.handle, blocks, video, avail, out_blocks=out,
+                                               path=path, coef=coef, w0=w0, status=st, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        fwd()
+    torch.cuda.synchronize(dev)
+    binding.fofse_check(stream)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            fwd()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+    ms = reduce_max(sum(e[0].elapsed_time(e[1]) for e in ev), world, dev) / args.steps
+
+    # end to end: pinned host video, mask and block list in, B_hat out, every step
+    hv, ha = torch.from_numpy(wl.video).pin_memory(), torch.from_numpy(wl.avail).pin_memory()
+    hb = torch.from_numpy(wl.blocks).pin_memory()
+    hout = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        video.copy_(hv, non_blocking=True)
+        avail.copy_(ha, non_blocking=True)
+        blocks.copy_(hb, non_blocking=True)
+        fwd()
+        hout.copy_(out, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = reduce_max(e0.elapsed_time(e1), world, dev) / args.steps
+    h2d = hv.numel() * 4 + ha.numel() + hb.numel() * 4
+    d2h = hout.numel() * 4
+
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz") or 1500.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    st_np = st.cpu().numpy()
+    flops = volume_flops(spec, int((st_np == 0).sum()))
+    sink = torch.empty(2 * sms * 1024, dtype=torch.float64, device=dev)
+    binding.fofse_probe_dfma(2 * sms, 2000, sink, stream=stream)
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    dfmas = binding.fofse_probe_dfma(2 * sms, 2000, sink, stream=stream)
+    q1.record(stream)
+    torch.cuda.synchronize(dev)
+    probe_flops = 2 * dfmas / (q0.elapsed_time(q1) * 1e-3)
+    peak = sms * FP64_FLOPS_PER_CLK_PER_SM * mhz * 1e6
+    achieved = flops / (ms * 1e-3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s (FP64)", "frac": achieved / peak, "traffic": None,
+                "kernel": "fofse_volume_kernel<32,4>",
+                "work_per_launch": f"{flops:.4g} FP64 flops (19/bin-iteration on the canonical "
+                                   f"half, 16 elsewhere, plus the DFTs of W and R)",
+                "peak_basis": f"nominal {FP64_FLOPS_PER_CLK_PER_SM} FP64 flops/clk/SM x {sms} SMs x "
+                              f"{mhz:.0f} MHz (sampled)",
+                "probe_fp64_tflops": probe_flops / 1e12,
+                "frac_of_probe": achieved / probe_flops}
+    # parity on a sample and the quality against the truth
+    g = out.cpu().numpy().astype(np.float64)
+    truth = np.stack([wl.truth[t, y:y + b, x:x + b] for (t, y, x) in wl.blocks]).astype(np.float64)
+    mse = float(np.mean((np.clip(g, 0, 255) - truth) ** 2))
+    cpu = parity = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        cores = os.cpu_count() or 1
+        pick = np.sort(np.random.default_rng(2207).choice(n, size=min(n, 4 * cores), replace=False))
+        oracle.build()
+        t0 = time.perf_counter()
+        ora = oracle.run_batch_volume(wl.video, wl.avail, wl.blocks[pick], spec, threads=cores)
+        dt = time.perf_counter() - t0
+        pth = path.cpu().numpy()[pick]
+        same = [bool(np.array_equal(pth[i], ora.path[i])) for i in range(len(pick))]
+        parity = {"blocks": len(pick), "identical_paths": float(np.mean(same)),
+                  "max_abs_err": float(np.abs(g[pick] - ora.blocks).max())}
+        cpu = {"value": len(pick) / dt, "unit": "blocks/s", "cores": int(ora.threads), "kind": "oracle",
+               "sample": f"{len(pick)} of the {n} blocks, FP64 spatial re-projection over the "
+                         f"volume, {ora.threads} threads, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": "16x16 blocks/s (video volumes, 32x32x4 grid, 200 it)",
+                "value": job_value(n, world, ms), "unit": "blocks/s", "n_gpus": world,
+                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "video-3x1920x1080: 804 lost 16x16 blocks in the centre "
+                                       "frame, border 8, depth 1, 32x32x4 grid, rho 0.8, gamma 0.5, "
+                                       "200 it", "blocks_per_gpu": n,
+                           "status_ok": int((st_np == 0).sum()),
+                           "l2": "flushed between steps (512 MiB write)"},
+                "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": "blocks/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "psnr_db": 10 * np.log10(255.0 ** 2 / mse) if mse > 0 else None,
+                "parity_sample": parity, "roofline": roofline, "cpu_baseline": cpu,
+                "gpu_launches": 2 * args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
 def stream_prediction_frames(plans, handles, blocks, ws, dev, bmax, n_frames=64):
     """The streamed prediction workload: n_frames frames (cumulative random
     0-4 px translations) go from pinned host memory through the forward call
@@ -514,6 +668,9 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "video-1080p":
+        run_volume_workload(args, rank, world, local)
         return
     if args.workload != "conceal-1080p":
         run_other_workload(args, rank, world, local)

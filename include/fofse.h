@@ -354,15 +354,99 @@ const char* fofse_last_cuda_error_string(void);
 /*
  * Measurement probes (no counterpart in the paper): kernels that only load
  * shared memory (16 B per thread and load, no bank conflicts) or only issue
- * FP32 fused multiply-adds, giving this GPU's rates for the rooflines of the
- * kernels above.  Each launches `ctas` blocks of 1024 threads doing `rounds`
- * rounds on `stream` and returns the work queued: *bytes loaded from shared
- * memory, or *fmas lane FMAs.  d_sink: device buffer of ctas x 1024 floats
- * (it keeps the work from being optimised away; in practice never written).
- * The caller times the launch.  FOFSE_E_ARG for non-positive sizes or NULL.
+ * FP32 (fofse_probe_fma) or FP64 (fofse_probe_dfma) fused multiply-adds,
+ * giving this GPU's rates for the rooflines of the kernels above.  Each
+ * launches `ctas` blocks of 1024 threads doing `rounds` rounds on `stream`
+ * and returns the work queued: *bytes loaded from shared memory, or *fmas
+ * lane FMAs.  d_sink: device buffer of ctas x 1024 floats (doubles for the
+ * FP64 probe); it keeps the work from being optimised away and is in
+ * practice never written.  The caller times the launch.  FOFSE_E_ARG for
+ * non-positive sizes or NULL.
  */
 fofse_status fofse_probe_smem(int ctas, int rounds, float* d_sink, double* bytes, void* stream);
 fofse_status fofse_probe_fma(int ctas, int rounds, float* d_sink, double* fmas, void* stream);
+fofse_status fofse_probe_dfma(int ctas, int rounds, double* d_sink, double* fmas, void* stream);
+
+/*
+ * Video volumes (Sec. 1: the method carried over to three-dimensional sets;
+ * the paper gives no formulas for them, so the following are this library's
+ * readings).  The area around a lost b x b block B in frame t is a volume of
+ * Lt = 2 depth + 1 frames (t - depth .. t + depth) of Ls x Ls samples,
+ * Ls = b + 2 border, indexed (tau, m, n) with B's frame at tau = depth.
+ *   w     rho^d on A, d = Euclidean distance to the centre of B in frame t,
+ *         one frame counting as one sample (Eq. 15 over three coordinates);
+ *         A = the usable samples of the volume (inside the video, mask 1)
+ *         except B in frame t (B's position in the other frames is in A).
+ *   basis the 3-D DFT on a T x T x Tt grid (T = fft_size for m and n,
+ *         Tt = fft_time for tau), the volume at its origin:
+ *         phi_k = exp(+j 2 pi (k1 m / T + k2 n / T + k3 tau / Tt)).
+ *   loop  as for images (Sec. 2, Eq. 1-9, Eq. 14): R = DFT(w f), W = DFT(w);
+ *         u = argmax |R[k]| over the canonical set {k : lin(k) <= lin(-k)},
+ *         lin(k) = (k1 T + k2) Tt + k3, exact ties to the smallest lin(k);
+ *         c = gamma R[u] / W[0] (real for the eight self-conjugate u, 2u = 0
+ *         mod (T, T, Tt)); R[k] -= c W[k - u] + s(u) conj(c) W[k + u].
+ *   out   B_hat[m,n] = sum_i (1 + s(u_i)) Re(c_i phi_{u_i}[depth, border + m,
+ *         border + n]), the model over B in frame t (Eq. 1).
+ * The whole recursion runs in FP64 (one CTA per block, both spectra in
+ * shared memory).  With depth 0 and fft_time 1 it is the two-dimensional
+ * method with the full support shape.
+ */
+typedef struct fofse_volume_plan_s* fofse_volume_plan;
+
+/* One lost block of a video: frame index and top-left corner of B. */
+typedef struct {
+  int32_t t, y, x;
+} fofse_volume_block;
+
+/*
+ * fofse_volume_plan_create -- parameters of extrapolation over volumes.
+ *   block     lost block side b, 1 <= b, b * b <= 512 (1024 when
+ *             fft_size^2 * fft_time >= 2048)
+ *   border    spatial border width, 0 <= border, b + 2 border <= fft_size
+ *   depth     frames on each side of B's frame, 0 <= depth, 2 depth + 1 <= fft_time
+ *   fft_size  T in {16, 32}
+ *   fft_time  Tt in {1, 2, 4, 8}, T^2 Tt <= 4096
+ *   rho       rho_hat of Eq. 15, 0 < rho <= 1
+ *   gamma     constant compensation factor of Eq. 14, 0 < gamma <= 1
+ *   iters     number of iterations I, 1 <= I <= 4096
+ * Builds the weight table rho^d (FP64, by a kernel on the current device)
+ * and synchronises the legacy default stream.  FOFSE_E_ARG for invalid
+ * values, FOFSE_E_UNSUPPORTED for a valid grid without a kernel (other T or
+ * Tt, or T^2 Tt > 4096: both spectra must fit one SM's shared memory),
+ * FOFSE_E_NOMEM / FOFSE_E_CUDA if the table cannot be built.  *out is set
+ * only on FOFSE_OK.
+ */
+fofse_status fofse_volume_plan_create(int block, int border, int depth, int fft_size, int fft_time,
+                                      float rho, float gamma, int iters, fofse_volume_plan* out);
+
+/* Frees the plan's table (cudaFree: not while a CUDA graph is being captured).
+ * NULL is ignored. */
+void fofse_volume_plan_destroy(fofse_volume_plan plan);
+
+/*
+ * fofse_extrapolate_volume_batch -- extrapolate every block of d_blocks.
+ *   d_blocks          device array of n_blocks fofse_volume_block (any position:
+ *                     samples outside the video are not in A)
+ *   d_video, d_avail  device video (float32) and availability (uint8):
+ *                     `frames` frames back to back, each height rows of
+ *                     `pitch` elements (frame stride height * pitch)
+ *   d_out_blocks      n_blocks x b x b floats, B_hat row-major (required)
+ *   d_path            nullable; n_blocks x iters x 3 int32 (u1, u2, u3)
+ *   d_coef            nullable; n_blocks x iters x 2 doubles (re, im of c)
+ *   d_w0              nullable; n_blocks doubles, W[0] = sum of w
+ *   d_block_status    nullable; n_blocks int32 (FOFSE_BLK_*); blocks that are
+ *                     not OK get B_hat = 0 and an all-zero path and coef
+ *   stream            cudaStream_t
+ * Returns FOFSE_OK once queued (n_blocks = 0 launches nothing), FOFSE_E_ARG for
+ * a NULL plan or required pointer or a non-positive size, FOFSE_E_CUDA if the
+ * launch failed.
+ */
+fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
+                                            const fofse_volume_block* d_blocks, int n_blocks,
+                                            const float* d_video, const uint8_t* d_avail,
+                                            int frames, int height, int width, int pitch,
+                                            float* d_out_blocks, int32_t* d_path, double* d_coef,
+                                            double* d_w0, int32_t* d_block_status, void* stream);
 
 /* Static, human-readable name of a status code. */
 const char* fofse_status_string(fofse_status status);

@@ -25,13 +25,19 @@ def _capturing() -> bool:
         return False
 
 
-def _release(handle):
-    if _capturing():
-        _deferred.append(handle)
-        return
+def _destroy_deferred():
     while _deferred:
-        B.fofse_plan_destroy(_deferred.pop())
-    B.fofse_plan_destroy(handle)
+        destroy, h = _deferred.pop()
+        destroy(h)
+
+
+def _release(handle, destroy=None):
+    destroy = destroy or B.fofse_plan_destroy
+    if _capturing():
+        _deferred.append((destroy, handle))
+        return
+    _destroy_deferred()
+    destroy(handle)
 
 
 class Plan:
@@ -48,8 +54,8 @@ class Plan:
         self.precision = precision
         self.compensation = int(compensation)
         self.basis = int(basis)
-        while _deferred and not _capturing():
-            B.fofse_plan_destroy(_deferred.pop())
+        if not _capturing():
+            _destroy_deferred()
         self.handle = B.fofse_plan_create(block, border, fft_size, rho, gamma, iters)
         try:
             B.fofse_plan_set_support(self.handle, self.support)
@@ -142,3 +148,63 @@ def extrapolate(plans, blocks, frame, avail, *, out_frame=None, with_trace=True,
                               out_blocks=ob, trace=tr, w0=w0, status=st, workspace=ws,
                               rho_gamma=rho_gamma, stream=stream)
     return Result(ob, tr, w0, st, out_frame)
+
+
+# ----------------------------------------------------------------------------
+# video volumes
+# ----------------------------------------------------------------------------
+
+class VolumePlan:
+    """Extrapolation over video volumes: b x b lost block, spatial border,
+    ``depth`` frames on each side of the block's frame, T x T x Tt DFT grid
+    (T = fft_size, Tt = fft_time), rho_hat, gamma, iterations."""
+
+    def __init__(self, block, border, depth, fft_size, fft_time, rho, gamma, iters):
+        self.block, self.border, self.depth = int(block), int(border), int(depth)
+        self.fft_size, self.fft_time = int(fft_size), int(fft_time)
+        self.rho, self.gamma, self.iters = float(rho), float(gamma), int(iters)
+        if not _capturing():
+            _destroy_deferred()
+        self.handle = B.fofse_volume_plan_create(block, border, depth, fft_size, fft_time, rho,
+                                                 gamma, iters)
+
+    @classmethod
+    def from_spec(cls, spec):
+        return cls(spec.block, spec.border, spec.depth, spec.fft_size, spec.fft_time, spec.rho,
+                   spec.gamma, spec.iters)
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self.handle = None
+            _release(h, B.fofse_volume_plan_destroy)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclasses.dataclass
+class VolumeResult:
+    blocks: torch.Tensor               # (n, b, b) float32
+    w0: torch.Tensor                   # (n,) float64
+    status: torch.Tensor               # (n,) int32
+    path: torch.Tensor | None = None   # (n, iters, 3) int32
+    coef: torch.Tensor | None = None   # (n, iters, 2) float64
+
+
+def extrapolate_volume(plan, blocks, video, avail, *, with_path=True, stream=None) -> VolumeResult:
+    """Extrapolate every block ((n, 3) int32 device tensor: t, y, x) of a video
+    ((F, H, W) float32 device tensor, availability uint8 of the same layout)."""
+    n = int(blocks.shape[0])
+    dev = video.device
+    out = torch.empty((n, plan.block, plan.block), dtype=torch.float32, device=dev)
+    w0 = torch.empty((n,), dtype=torch.float64, device=dev)
+    status = torch.empty((n,), dtype=torch.int32, device=dev)
+    path = torch.empty((n, plan.iters, 3), dtype=torch.int32, device=dev) if with_path else None
+    coef = torch.empty((n, plan.iters, 2), dtype=torch.float64, device=dev) if with_path else None
+    B.fofse_extrapolate_volume_batch(plan.handle, blocks, video, avail, out_blocks=out, path=path,
+                                     coef=coef, w0=w0, status=status, stream=stream)
+    return VolumeResult(out, w0, status, path, coef)

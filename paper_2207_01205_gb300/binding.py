@@ -96,6 +96,16 @@ def _declare(L):
     L.fofse_probe_smem.restype = _i
     L.fofse_probe_fma.argtypes = [_i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp]
     L.fofse_probe_fma.restype = _i
+    L.fofse_probe_dfma.argtypes = [_i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+    L.fofse_probe_dfma.restype = _i
+    L.fofse_volume_plan_create.argtypes = [_i, _i, _i, _i, _i, ctypes.c_float, ctypes.c_float, _i,
+                                           ctypes.POINTER(_vp)]
+    L.fofse_volume_plan_create.restype = _i
+    L.fofse_volume_plan_destroy.argtypes = [_vp]
+    L.fofse_volume_plan_destroy.restype = None
+    L.fofse_extrapolate_volume_batch.argtypes = [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _vp, _vp,
+                                                 _vp, _vp, _vp, _vp]
+    L.fofse_extrapolate_volume_batch.restype = _i
     L.fofse_check.argtypes = [_vp]
     L.fofse_check.restype = _i
     L.fofse_last_cuda_error.restype = _i
@@ -280,6 +290,15 @@ def fofse_probe_fma(ctas, rounds, sink, *, stream=None) -> float:
     return out.value
 
 
+def fofse_probe_dfma(ctas, rounds, sink, *, stream=None) -> float:
+    """Queues the FP64 FMA probe (sink: ctas x 1024 float64); returns the lane
+    FMAs it issues."""
+    out = ctypes.c_double()
+    _check(load().fofse_probe_dfma(int(ctas), int(rounds), _ptr(sink), ctypes.byref(out),
+                                   _stream(stream)), "fofse_probe_dfma")
+    return out.value
+
+
 def fofse_last_cuda_error() -> int:
     return load().fofse_last_cuda_error()
 
@@ -290,3 +309,31 @@ def fofse_last_cuda_error_string() -> str:
 
 def fofse_check(stream=None):
     _check(load().fofse_check(_stream(stream)), "fofse_check")
+
+
+def fofse_volume_plan_create(block, border, depth, fft_size, fft_time, rho, gamma, iters) -> int:
+    h = ctypes.c_void_p()
+    _check(load().fofse_volume_plan_create(int(block), int(border), int(depth), int(fft_size),
+                                           int(fft_time), float(rho), float(gamma), int(iters),
+                                           ctypes.byref(h)), "fofse_volume_plan_create")
+    return h.value
+
+
+def fofse_volume_plan_destroy(plan):
+    load().fofse_volume_plan_destroy(ctypes.c_void_p(plan) if plan else None)
+
+
+def fofse_extrapolate_volume_batch(plan, blocks, video, avail, *, out_blocks, path=None, coef=None,
+                                   w0=None, status=None, stream=None):
+    """blocks: (n, 3) int32 device tensor (t, y, x); video float32 and avail
+    uint8 device tensors of shape (F, H, W) with row pitch stride(1) and frame
+    stride H * pitch; out_blocks (n, b, b) float32; path (n, iters, 3) int32,
+    coef (n, iters, 2) float64, w0 (n,) float64, status (n,) int32."""
+    F, H, W = video.shape
+    pitch = video.stride(1)
+    assert video.stride(2) == 1 and video.stride(0) == H * pitch
+    assert tuple(avail.shape) == tuple(video.shape) and tuple(avail.stride()) == tuple(video.stride())
+    _check(load().fofse_extrapolate_volume_batch(
+        ctypes.c_void_p(plan), _ptr(blocks), int(blocks.shape[0]), _ptr(video), _ptr(avail), F, H, W,
+        pitch, _ptr(out_blocks), _ptr(path), _ptr(coef), _ptr(w0), _ptr(status), _stream(stream)),
+        "fofse_extrapolate_volume_batch")

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfofse.so")
 SOURCES = ["fofse_api.cu", "fofse_fwd.cu", "fofse_fwd3.cu", "fofse_ofse.cu", "fofse_bwd.cu",
-           "fofse_curve.cu", "fofse_probe.cu", "fofse_dct.cu"]
+           "fofse_curve.cu", "fofse_probe.cu", "fofse_dct.cu", "fofse_volume.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 

@@ -1,5 +1,5 @@
-// Measurement probes for the rooflines of the product kernel (no counterpart
-// in the paper): the shared-memory load bandwidth and the FP32 FMA rate of
+// Measurement probes for the rooflines of the kernels (no counterpart in the
+// paper): the shared-memory load bandwidth and the FP32 and FP64 FMA rates of
 // this GPU, each from a kernel that does nothing else.  The caller times the
 // launch (CUDA events) and divides the work reported here by the time and the
 // sampled SM clock.
@@ -60,6 +60,22 @@ __global__ void __launch_bounds__(kProbeThreads) fofse_fma_probe_kernel(float* s
   if (t == -1.f) sink[blockIdx.x * kProbeThreads + threadIdx.x] = t;
 }
 
+// The same with FP64 FMAs (the pipe of the video-volume kernel).
+__global__ void __launch_bounds__(kProbeThreads) fofse_dfma_probe_kernel(double* sink, int rounds, double a,
+                                                                         double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (double)(threadIdx.x + k);
+  for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += x[k];
+  if (t == -1.0) sink[blockIdx.x * kProbeThreads + threadIdx.x] = t;
+}
+
 }  // namespace
 }  // namespace fofse
 
@@ -80,6 +96,16 @@ fofse_status fofse_probe_fma(int ctas, int rounds, float* d_sink, double* fmas, 
   if (ctas < 1 || rounds < 1 || !d_sink || !fmas) return FOFSE_E_ARG;
   fofse_fma_probe_kernel<<<ctas, kProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       d_sink, rounds, 0.999f, 1e-3f);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return record_cuda_error(e);
+  *fmas = (double)ctas * kProbeThreads * rounds * 8.0;
+  return FOFSE_OK;
+}
+
+fofse_status fofse_probe_dfma(int ctas, int rounds, double* d_sink, double* fmas, void* stream) {
+  if (ctas < 1 || rounds < 1 || !d_sink || !fmas) return FOFSE_E_ARG;
+  fofse_dfma_probe_kernel<<<ctas, kProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      d_sink, rounds, 0.999, 1e-3);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return record_cuda_error(e);
   *fmas = (double)ctas * kProbeThreads * rounds * 8.0;

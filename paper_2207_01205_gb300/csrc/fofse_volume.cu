@@ -1,0 +1,514 @@
+// FOFSE over video volumes (Sec. 1: the method carried over to
+// three-dimensional sets; Sec. 2's transform-domain recursion on a 3-D grid).
+//
+// Per lost block the volume L holds Lt = 2 depth + 1 frames (B's frame at its
+// centre) of Ls x Ls samples, Ls = block + 2 border.  With the 3-D DFT on a
+// T x T x Tt grid (L at the origin):
+//   W = DFT(w), R = DFT(w f), w = rho^d on A (d: distance to the centre of B
+//   in B's frame, a frame counting as one sample; A = the usable samples of L
+//   outside B in B's own frame);
+//   iters times: u = argmax |R[k]| over one index per conjugate pair
+//   (lin(k) = (k1 T + k2) Tt + k3 <= lin(-k), ties to the smallest lin);
+//   c = gamma R[u] / W[0] (real for the self-conjugate u);
+//   R[k] -= c W[k - u] + s(u) conj(c) W[k + u];
+//   B_hat += (1 + s(u)) Re(c exp(+j 2 pi (u1 m / T + u2 n / T + u3 depth / Tt))).
+//
+// One CTA per block, everything in FP64 in shared memory: R and W (T^2 Tt
+// complex each, at most 4096 bins = 64 KB each), a stage buffer for the
+// separable DFTs that build them, and the twiddle tables.  Each iteration is
+// one pass over the bins that applies the update and evaluates the next
+// selection's energies, then a block-wide argmax (two barriers per
+// iteration).  The output samples of B accumulate in registers as the
+// iterations run.  The kernel is bound by the FP64 pipe.
+#include <math.h>
+
+#include <new>
+
+#include "fofse_internal.h"
+
+struct fofse_volume_plan_s {
+  int block, border, depth, T, Tt, Ls, Lt, iters;
+  float rho, gamma;
+  double* wtab;  // device: rho^d over the Lt x Ls x Ls volume (tau, m, n)
+};
+
+namespace fofse {
+namespace {
+
+struct VolArgs {
+  int block, border, depth, Ls, Lt, iters;
+  double gamma;
+  const double* wtab;
+  const fofse_volume_block* blocks;
+  const float* video;
+  const uint8_t* avail;
+  int frames, height, width, pitch;
+  float* out;       // n x block x block
+  int32_t* path;    // n x iters x 3, nullable
+  double* coef;     // n x iters x 2, nullable
+  double* w0;       // n, nullable
+  int32_t* status;  // n, nullable
+};
+
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+template <int T, int TT> struct VolGeom {
+  static constexpr int K = T * T * TT;                  // bins
+  static constexpr int NT = K >= 2048 ? 512 : 256;      // threads
+  static constexpr int NW = NT / 32;
+  static constexpr int BPT = K / NT;                    // bins per thread
+  static constexpr int LOGT = ilog2(T);
+  static constexpr int LOGTT = ilog2(TT);
+  static constexpr int PPT = 2;                         // samples of B per thread
+  static_assert(K % NT == 0 && BPT >= 1, "bins must tile the threads");
+  static_assert((1 << LOGT) == T && (1 << LOGTT) == TT, "power-of-two grid");
+};
+
+// Dynamic shared memory: R, W, then the stage buffer (Lt T^2 complex, which
+// also holds the 2 Lt Ls^2 input doubles at first).
+__host__ __device__ inline size_t vol_smem_bytes(int T, int TT, int Lt) {
+  return sizeof(double2) * ((size_t)2 * T * T * TT + (size_t)Lt * T * T);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// (e, lin) pairs: the larger energy wins, equal energies go to the smaller lin.
+__device__ __forceinline__ void better(double& e, int& l, double oe, int ol) {
+  if (oe > e || (oe == e && ol < l)) {
+    e = oe;
+    l = ol;
+  }
+}
+
+__device__ __forceinline__ void warp_argmax(double& e, int& l) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double oe = __shfl_xor_sync(0xffffffffu, e, o);
+    const int ol = __shfl_xor_sync(0xffffffffu, l, o);
+    better(e, l, oe, ol);
+  }
+}
+
+// Stage 1 (along n): z[(tau Ls + m) T + k2] = sum_n x[(tau Ls + m) Ls + n] e^{-j 2 pi k2 n / T}.
+template <int T, int NT>
+__device__ void dft_rows(const double* x, double2* z, int Lt, int Ls, const double2* tw) {
+  constexpr int LOGT = ilog2(T);
+  const int nq = Lt * Ls * T;
+  for (int q = threadIdx.x; q < nq; q += NT) {
+    const int row = q >> LOGT, k2 = q & (T - 1);
+    const double* xr = x + row * Ls;
+    double re = 0.0, im = 0.0;
+    for (int n = 0; n < Ls; ++n) {
+      const double v = xr[n];
+      const double2 t = tw[(k2 * n) & (T - 1)];
+      re = fma(v, t.x, re);
+      im = fma(v, t.y, im);
+    }
+    z[q] = make_double2(re, im);
+  }
+}
+
+// Stage 2 (along m): z2[(tau T + k1) T + k2] = sum_m z1[(tau Ls + m) T + k2] e^{-j 2 pi k1 m / T}.
+template <int T, int NT>
+__device__ void dft_cols(const double2* z1, double2* z2, int Lt, int Ls, const double2* tw) {
+  constexpr int LOGT = ilog2(T);
+  const int nq = Lt * T * T;
+  for (int q = threadIdx.x; q < nq; q += NT) {
+    const int k2 = q & (T - 1), k1 = (q >> LOGT) & (T - 1), tau = q >> (2 * LOGT);
+    const double2* zc = z1 + tau * Ls * T + k2;
+    double re = 0.0, im = 0.0;
+    for (int m = 0; m < Ls; ++m) {
+      const double2 v = zc[m * T];
+      const double2 t = tw[(k1 * m) & (T - 1)];
+      re = fma(v.x, t.x, re);
+      re = fma(-v.y, t.y, re);
+      im = fma(v.x, t.y, im);
+      im = fma(v.y, t.x, im);
+    }
+    z2[q] = make_double2(re, im);
+  }
+}
+
+// Stage 3 (along tau), column c = k1 T + k2: out[k3 T^2 + c] =
+// sum_tau in[tau T^2 + c] e^{-j 2 pi k3 tau / Tt}.  A thread reads its whole
+// column before writing it, so `in` may equal `out`.
+template <int T, int TT, int NT>
+__device__ void dft_time(const double2* in, double2* out, int Lt, const double2* twt) {
+  for (int c = threadIdx.x; c < T * T; c += NT) {
+    double2 v[TT];
+#pragma unroll
+    for (int tau = 0; tau < TT; ++tau) v[tau] = tau < Lt ? in[tau * T * T + c] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int k3 = 0; k3 < TT; ++k3) {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int tau = 0; tau < TT; ++tau) {
+        const double2 t = twt[(k3 * tau) & (TT - 1)];
+        re = fma(v[tau].x, t.x, re);
+        re = fma(-v[tau].y, t.y, re);
+        im = fma(v[tau].x, t.y, im);
+        im = fma(v[tau].y, t.x, im);
+      }
+      out[k3 * T * T + c] = make_double2(re, im);
+    }
+  }
+}
+
+template <int T, int TT>
+__global__ void __launch_bounds__(VolGeom<T, TT>::NT, 1)
+    fofse_volume_kernel(const __grid_constant__ VolArgs a) {
+  using G = VolGeom<T, TT>;
+  constexpr int K = G::K, NT = G::NT, NW = G::NW, BPT = G::BPT, LOGT = G::LOGT,
+                LOGTT = G::LOGTT, PPT = G::PPT;
+  extern __shared__ __align__(16) unsigned char vol_smem[];
+  double2* R = reinterpret_cast<double2*>(vol_smem);
+  double2* W = R + K;
+  double2* X = W + K;
+  __shared__ double2 twT[T], twTT[TT], syn[T * TT];
+  __shared__ double red_e[NW];
+  __shared__ int red_l[NW];
+  __shared__ double2 bc_c;
+  __shared__ int bc_u[4];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int bi = blockIdx.x;
+  const fofse_volume_block blk = a.blocks[bi];
+  const int Ls = a.Ls, Lt = a.Lt, b = a.block, e = a.border, D = a.depth;
+  const int NS = Lt * Ls * Ls;
+
+  for (int p = tid; p < T; p += NT) {
+    double s, c;
+    sincospi(2.0 * p / T, &s, &c);
+    twT[p] = make_double2(c, -s);
+  }
+  for (int p = tid; p < TT; p += NT) {
+    double s, c;
+    sincospi(2.0 * p / TT, &s, &c);
+    twTT[p] = make_double2(c, -s);
+  }
+  for (int p = tid; p < T * TT; p += NT) {
+    double s, c;
+    sincospi(2.0 * p / (T * TT), &s, &c);
+    syn[p] = make_double2(c, s);
+  }
+
+  // ---- weighted volume (Eq. 3, Eq. 4, Eq. 15 over three coordinates) ----
+  double* xw = reinterpret_cast<double*>(X);
+  double* xr = xw + NS;
+  double wsum = 0.0;
+  int bad = 0;
+  for (int s = tid; s < NS; s += NT) {
+    const int tau = s / (Ls * Ls), r = s - tau * Ls * Ls, m = r / Ls, n = r - m * Ls;
+    const int ft = blk.t - D + tau, fy = blk.y - e + m, fx = blk.x - e + n;
+    const bool inB = tau == D && m >= e && m < e + b && n >= e && n < e + b;
+    double w = 0.0, wf = 0.0;
+    if (!inB && ft >= 0 && ft < a.frames && fy >= 0 && fy < a.height && fx >= 0 && fx < a.width) {
+      const long long o = ((long long)ft * a.height + fy) * a.pitch + fx;
+      if (a.avail[o]) {
+        w = a.wtab[s];
+        const float f = a.video[o];
+        if (w != 0.0) {
+          if (isfinite(f))
+            wf = w * (double)f;
+          else
+            bad = 1;
+        }
+      }
+    }
+    xw[s] = w;
+    xr[s] = wf;
+    wsum += w;
+  }
+  wsum = warp_sum(wsum);
+  if (lane == 0) red_e[warp] = wsum;
+  const int any_bad = __syncthreads_or(bad);
+  double W0 = 0.0;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) W0 += red_e[i];
+  const int st = !(W0 > 0.0) ? FOFSE_BLK_NO_SUPPORT : any_bad ? FOFSE_BLK_NONFINITE : FOFSE_BLK_OK;
+  if (tid == 0) {
+    if (a.w0) a.w0[bi] = W0;
+    if (a.status) a.status[bi] = st;
+  }
+  if (st != FOFSE_BLK_OK) {
+    for (int p = tid; p < b * b; p += NT) a.out[(size_t)bi * b * b + p] = 0.0f;
+    for (int p = tid; p < a.iters; p += NT) {
+      const size_t o = (size_t)bi * a.iters + p;
+      if (a.path) a.path[3 * o] = a.path[3 * o + 1] = a.path[3 * o + 2] = 0;
+      if (a.coef) a.coef[2 * o] = a.coef[2 * o + 1] = 0.0;
+    }
+    return;
+  }
+
+  // ---- W = DFT(w) into W, then R = DFT(w f) into R (Eq. 8 on the 3-D grid) ----
+  dft_rows<T, NT>(xw, R, Lt, Ls, twT);
+  __syncthreads();
+  dft_cols<T, NT>(R, W, Lt, Ls, twT);
+  __syncthreads();
+  dft_time<T, TT, NT>(W, W, Lt, twTT);
+  __syncthreads();
+  dft_rows<T, NT>(xr, R, Lt, Ls, twT);
+  __syncthreads();
+  dft_cols<T, NT>(R, X, Lt, Ls, twT);
+  __syncthreads();
+  dft_time<T, TT, NT>(X, R, Lt, twTT);
+  __syncthreads();
+
+  // ---- canonical indices of this thread's bins (-1: not canonical) ----
+  int can[BPT];
+#pragma unroll
+  for (int j = 0; j < BPT; ++j) {
+    const int i = tid + j * NT;
+    const int k2 = i & (T - 1), k1 = (i >> LOGT) & (T - 1), k3 = i >> (2 * LOGT);
+    const int lin = ((k1 << LOGT) + k2) * TT + k3;
+    const int nlin = ((((-k1) & (T - 1)) << LOGT) + ((-k2) & (T - 1))) * TT + ((-k3) & (TT - 1));
+    can[j] = lin <= nlin ? lin : -1;
+  }
+  double be = -1.0;
+  int bl = 0x7fffffff;
+#pragma unroll
+  for (int j = 0; j < BPT; ++j) {
+    if (can[j] >= 0) {
+      const double2 r = R[tid + j * NT];
+      better(be, bl, r.x * r.x + r.y * r.y, can[j]);
+    }
+  }
+
+  double g[PPT];
+  int gm[PPT], gn[PPT];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int p = tid + q * NT;
+    g[q] = 0.0;
+    gm[q] = e + (p < b * b ? p / b : 0);
+    gn[q] = e + (p < b * b ? p % b : 0);
+  }
+
+  const double gamma = a.gamma;
+  for (int it = 0; it < a.iters; ++it) {
+    // ---- Eq. 9: block-wide argmax over the canonical set ----
+    warp_argmax(be, bl);
+    if (lane == 0) {
+      red_e[warp] = be;
+      red_l[warp] = bl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double e2 = lane < NW ? red_e[lane] : -1.0;
+      int l2 = lane < NW ? red_l[lane] : 0x7fffffff;
+      warp_argmax(e2, l2);
+      // every energy NaN (an overflow on absurd inputs) leaves the sentinel:
+      // take k = 0 so that the index below stays inside R
+      if (l2 == 0x7fffffff) l2 = 0;
+      if (lane == 0) {
+        const int u3 = l2 & (TT - 1), u2 = (l2 >> LOGTT) & (T - 1), u1 = l2 >> (LOGTT + LOGT);
+        const double2 ru = R[(u3 << (2 * LOGT)) | (u1 << LOGT) | u2];
+        const int s = (((2 * u1) & (T - 1)) == 0 && ((2 * u2) & (T - 1)) == 0 &&
+                       ((2 * u3) & (TT - 1)) == 0)
+                          ? 0
+                          : 1;
+        // Eq. 5 (p_u = R[u] / W0) and Eq. 14 (c = gamma p_u)
+        const double cr = gamma * ru.x / W0;
+        const double ci = s ? gamma * ru.y / W0 : 0.0;
+        bc_c = make_double2(cr, ci);
+        bc_u[0] = u1;
+        bc_u[1] = u2;
+        bc_u[2] = u3;
+        bc_u[3] = s;
+        const size_t o = (size_t)bi * a.iters + it;
+        if (a.path) {
+          a.path[3 * o] = u1;
+          a.path[3 * o + 1] = u2;
+          a.path[3 * o + 2] = u3;
+        }
+        if (a.coef) {
+          a.coef[2 * o] = cr;
+          a.coef[2 * o + 1] = ci;
+        }
+      }
+    }
+    __syncthreads();
+    const double cr = bc_c.x, ci = bc_c.y;
+    const int u1 = bc_u[0], u2 = bc_u[1], u3 = bc_u[2], s = bc_u[3];
+    const double sd = s ? 1.0 : 0.0;
+    const double crs = sd * cr;  // ci is 0 when s is
+
+    // ---- Eq. 1-2: B_hat += (1 + s) Re(c phi_u) at B (frame tau = depth) ----
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int ph = ((((u1 * gm[q] + u2 * gn[q]) & (T - 1)) * TT) + ((u3 * D) & (TT - 1)) * T) &
+                     (T * TT - 1);
+      const double2 y = syn[ph];
+      g[q] += (1.0 + sd) * (cr * y.x - ci * y.y);
+    }
+
+    // ---- R[k] -= c W[k - u] + s conj(c) W[k + u]; energies of the next pick ----
+    be = -1.0;
+    bl = 0x7fffffff;
+#pragma unroll
+    for (int j = 0; j < BPT; ++j) {
+      const int i = tid + j * NT;
+      const int k2 = i & (T - 1), k1 = (i >> LOGT) & (T - 1), k3 = i >> (2 * LOGT);
+      const int im_ = (((k3 - u3) & (TT - 1)) << (2 * LOGT)) | (((k1 - u1) & (T - 1)) << LOGT) |
+                      ((k2 - u2) & (T - 1));
+      const int ip_ = (((k3 + u3) & (TT - 1)) << (2 * LOGT)) | (((k1 + u1) & (T - 1)) << LOGT) |
+                      ((k2 + u2) & (T - 1));
+      const double2 wa = W[im_], wb = W[ip_];
+      // c W[k-u] = (cr wa.x - ci wa.y) + j (cr wa.y + ci wa.x)
+      // conj(c) W[k+u] = (cr wb.x + ci wb.y) + j (cr wb.y - ci wb.x)
+      double2 r = R[i];
+      r.x = fma(-cr, wa.x, r.x);
+      r.x = fma(ci, wa.y, r.x);
+      r.x = fma(-crs, wb.x, r.x);
+      r.x = fma(-ci, wb.y, r.x);
+      r.y = fma(-cr, wa.y, r.y);
+      r.y = fma(-ci, wa.x, r.y);
+      r.y = fma(-crs, wb.y, r.y);
+      r.y = fma(ci, wb.x, r.y);
+      R[i] = r;
+      if (can[j] >= 0) better(be, bl, r.x * r.x + r.y * r.y, can[j]);
+    }
+  }
+
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int p = tid + q * NT;
+    if (p < b * b) a.out[(size_t)bi * b * b + p] = (float)g[q];
+  }
+}
+
+// rho^d over the volume, d the distance to the centre of B in frame tau = depth.
+__global__ void fofse_volume_weights_kernel(double* wtab, int block, int border, int depth,
+                                            double rho) {
+  const int Ls = block + 2 * border, Lt = 2 * depth + 1;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Lt * Ls * Ls) return;
+  const int tau = s / (Ls * Ls), r = s - tau * Ls * Ls, m = r / Ls, n = r - m * Ls;
+  const double c = border + (block - 1) / 2.0;
+  const double dt = tau - depth, dm = m - c, dn = n - c;
+  wtab[s] = pow(rho, sqrt(dt * dt + dm * dm + dn * dn));
+}
+
+template <int T, int TT>
+cudaError_t launch_volume_T(const VolArgs& a, int n_blocks, cudaStream_t stream) {
+  using G = VolGeom<T, TT>;
+  const size_t smem = vol_smem_bytes(T, TT, a.Lt);
+  cudaError_t e = cudaFuncSetAttribute(fofse_volume_kernel<T, TT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fofse_volume_kernel<T, TT><<<n_blocks, G::NT, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// Grids with kernels: T in {16, 32}, Tt in {1, 2, 4, 8}, T^2 Tt <= 4096.
+bool volume_grid_supported(int T, int Tt) {
+  if (T == 16) return Tt == 1 || Tt == 2 || Tt == 4 || Tt == 8;
+  if (T == 32) return Tt == 1 || Tt == 2 || Tt == 4;
+  return false;
+}
+
+cudaError_t launch_volume(int T, int Tt, const VolArgs& a, int n_blocks, cudaStream_t s) {
+  switch (T * 100 + Tt) {
+    case 1601: return launch_volume_T<16, 1>(a, n_blocks, s);
+    case 1602: return launch_volume_T<16, 2>(a, n_blocks, s);
+    case 1604: return launch_volume_T<16, 4>(a, n_blocks, s);
+    case 1608: return launch_volume_T<16, 8>(a, n_blocks, s);
+    case 3201: return launch_volume_T<32, 1>(a, n_blocks, s);
+    case 3202: return launch_volume_T<32, 2>(a, n_blocks, s);
+    case 3204: return launch_volume_T<32, 4>(a, n_blocks, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int volume_threads(int T, int Tt) { return T * T * Tt >= 2048 ? 512 : 256; }
+
+}  // namespace
+}  // namespace fofse
+
+using namespace fofse;
+
+extern "C" {
+
+fofse_status fofse_volume_plan_create(int block, int border, int depth, int fft_size, int fft_time,
+                                      float rho, float gamma, int iters, fofse_volume_plan* out) {
+  if (!out || block < 1 || border < 0 || depth < 0 || fft_size < 1 || fft_time < 1) return FOFSE_E_ARG;
+  if (!(rho > 0.0f && rho <= 1.0f) || !(gamma > 0.0f && gamma <= 1.0f)) return FOFSE_E_ARG;
+  if (iters < 1 || iters > 4096) return FOFSE_E_ARG;
+  const int Ls = block + 2 * border, Lt = 2 * depth + 1;
+  if (Ls > fft_size || Lt > fft_time) return FOFSE_E_ARG;
+  if (!volume_grid_supported(fft_size, fft_time)) return FOFSE_E_UNSUPPORTED;
+  if (block * block > 2 * volume_threads(fft_size, fft_time)) return FOFSE_E_UNSUPPORTED;
+  fofse_volume_plan_s* p = new (std::nothrow) fofse_volume_plan_s();
+  if (!p) return FOFSE_E_NOMEM;
+  p->block = block;
+  p->border = border;
+  p->depth = depth;
+  p->T = fft_size;
+  p->Tt = fft_time;
+  p->Ls = Ls;
+  p->Lt = Lt;
+  p->iters = iters;
+  p->rho = rho;
+  p->gamma = gamma;
+  const int ns = Lt * Ls * Ls;
+  cudaError_t e = cudaMalloc(&p->wtab, sizeof(double) * ns);
+  if (e != cudaSuccess) {
+    delete p;
+    return e == cudaErrorMemoryAllocation ? FOFSE_E_NOMEM : record_cuda_error(e);
+  }
+  fofse_volume_weights_kernel<<<(ns + 255) / 256, 256>>>(p->wtab, block, border, depth, (double)rho);
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(0)) != cudaSuccess) {
+    cudaFree(p->wtab);
+    delete p;
+    return record_cuda_error(e);
+  }
+  *out = p;
+  return FOFSE_OK;
+}
+
+void fofse_volume_plan_destroy(fofse_volume_plan plan) {
+  if (!plan) return;
+  cudaFree(plan->wtab);
+  delete plan;
+}
+
+fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
+                                            const fofse_volume_block* d_blocks, int n_blocks,
+                                            const float* d_video, const uint8_t* d_avail,
+                                            int frames, int height, int width, int pitch,
+                                            float* d_out_blocks, int32_t* d_path, double* d_coef,
+                                            double* d_w0, int32_t* d_block_status, void* stream) {
+  if (!plan || n_blocks < 0 || frames < 1 || height < 1 || width < 1 || pitch < width)
+    return FOFSE_E_ARG;
+  if (n_blocks == 0) return FOFSE_OK;
+  if (!d_blocks || !d_video || !d_avail || !d_out_blocks) return FOFSE_E_ARG;
+  VolArgs a;
+  a.block = plan->block;
+  a.border = plan->border;
+  a.depth = plan->depth;
+  a.Ls = plan->Ls;
+  a.Lt = plan->Lt;
+  a.iters = plan->iters;
+  a.gamma = (double)plan->gamma;
+  a.wtab = plan->wtab;
+  a.blocks = d_blocks;
+  a.video = d_video;
+  a.avail = d_avail;
+  a.frames = frames;
+  a.height = height;
+  a.width = width;
+  a.pitch = pitch;
+  a.out = d_out_blocks;
+  a.path = d_path;
+  a.coef = d_coef;
+  a.w0 = d_w0;
+  a.status = d_block_status;
+  const cudaError_t e = launch_volume(plan->T, plan->Tt, a, n_blocks, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? FOFSE_OK : record_cuda_error(e);
+}
+
+}  // extern "C"

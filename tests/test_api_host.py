@@ -15,10 +15,24 @@ def test_plans_released_during_a_capture_are_destroyed_after_it(monkeypatch):
     monkeypatch.setattr(api, "_capturing", lambda: True)
     api._release(11)
     api._release(12)
-    assert destroyed == [] and api._deferred == [11, 12]
+    assert destroyed == [] and [h for _, h in api._deferred] == [11, 12]
     monkeypatch.setattr(api, "_capturing", lambda: False)
     api._release(13)
     assert sorted(destroyed) == [11, 12, 13] and api._deferred == []
+
+
+def test_volume_plans_are_released_with_their_own_destroy(monkeypatch):
+    destroyed = []
+    monkeypatch.setattr(api.B, "fofse_plan_destroy", lambda h: destroyed.append(("2d", h)))
+    monkeypatch.setattr(api.B, "fofse_volume_plan_destroy", lambda h: destroyed.append(("3d", h)))
+    monkeypatch.setattr(api, "_deferred", [])
+    monkeypatch.setattr(api, "_capturing", lambda: True)
+    api._release(21)
+    api._release(22, api.B.fofse_volume_plan_destroy)
+    assert destroyed == []
+    monkeypatch.setattr(api, "_capturing", lambda: False)
+    api._destroy_deferred()
+    assert sorted(destroyed) == [("2d", 21), ("3d", 22)]
 
 
 def test_autotune_keys_separate_the_kernel_selecting_settings(monkeypatch):
@@ -34,3 +48,29 @@ def test_autotune_keys_separate_the_kernel_selecting_settings(monkeypatch):
     p = types.SimpleNamespace(**base)
     assert autotune._key(p, 700, 0) == autotune._key(p, 1000, 0)      # same power-of-two bucket
     assert autotune._key(p, 700, 0) != autotune._key(p, 1100, 0)
+
+
+def test_volume_plan_arguments_are_checked_before_any_cuda_call():
+    """fofse_volume_plan_create rejects invalid values (FOFSE_E_ARG) and grids
+    without a kernel (FOFSE_E_UNSUPPORTED) before touching the device, and the
+    batch call rejects a NULL plan; the library loads without a GPU."""
+    from paper_2207_01205_gb300 import binding as B
+    bad = [(0, 4, 1, 16, 4), (8, -1, 1, 16, 4), (8, 4, -1, 16, 4), (8, 5, 1, 16, 4),
+           (8, 4, 2, 16, 4)]
+    for args in bad:
+        with pytest.raises(B.FofseError) as ei:
+            B.fofse_volume_plan_create(*args, 0.8, 0.5, 10)
+        assert ei.value.status == B.E_ARG, args
+    for rho, gamma, iters in [(0.0, 0.5, 10), (1.5, 0.5, 10), (0.8, 0.0, 10), (0.8, 0.5, 0),
+                              (0.8, 0.5, 5000), (float("nan"), 0.5, 10)]:
+        with pytest.raises(B.FofseError) as ei:
+            B.fofse_volume_plan_create(8, 4, 1, 16, 4, rho, gamma, iters)
+        assert ei.value.status == B.E_ARG
+    for args in [(8, 4, 1, 64, 4), (8, 4, 1, 32, 8), (8, 4, 1, 16, 16), (8, 4, 1, 16, 3),
+                 (24, 4, 0, 32, 1)]:
+        with pytest.raises(B.FofseError) as ei:
+            B.fofse_volume_plan_create(*args, 0.8, 0.5, 10)
+        assert ei.value.status == B.E_UNSUPPORTED, args
+    st = B.load().fofse_extrapolate_volume_batch(None, None, 1, None, None, 1, 1, 1, 1, None, None,
+                                                 None, None, None, None)
+    assert st == B.E_ARG
