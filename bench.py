@@ -411,11 +411,12 @@ def run_other_workload(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-# FP64 work of the video-volume kernel (fofse_volume_kernel), per bin and
-# iteration: the update R -= c W[k-u] + s conj(c) W[k+u] as 8 fused
-# multiply-adds (16 flops) and, on the canonical bins, |R|^2 (a multiply and a
-# fused multiply-add, 3 flops); per spectrum the three separable DFT passes
-# (2 FMAs per real-input term along n, 4 per complex term along m and tau).
+# FP64 work of the video-volume kernel (fofse_volume_kernel), per canonical
+# bin (one of each conjugate pair, the bins the kernel keeps) and iteration:
+# the update R -= c W[k-u] + s conj(c) W[k+u] as 8 fused multiply-adds (16
+# flops) and |R|^2 (a multiply and a fused multiply-add, 3 flops); per
+# spectrum the three separable DFT passes (2 FMAs per real-input term along
+# n, 4 per complex term along m and tau).
 # The nominal FP64 rate of a GB300 is 1.25 TFLOP/s at 2070 MHz over 152 SMs:
 # 4 flops per clock and SM.
 FP64_FLOPS_PER_CLK_PER_SM = 4
@@ -426,7 +427,7 @@ def volume_flops(spec, n_ok):
         2 * spec.depth + 1, spec.iters
     K = T * T * Tt
     canon = (K + 8) // 2 if Tt > 1 else (K + 4) // 2
-    per_iter = 16 * K + 3 * canon
+    per_iter = 19 * canon
     dft = 2 * (4 * Lt * Ls * T * Ls + 8 * Lt * T * T * Ls + 8 * T * T * Tt * Lt)
     return n_ok * (it * per_iter + dft)
 
@@ -520,8 +521,8 @@ def run_volume_workload(args, rank, world, local):
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s (FP64)", "frac": achieved / peak, "traffic": None,
                 "kernel": "fofse_volume_kernel<32,4>",
-                "work_per_launch": f"{flops:.4g} FP64 flops (19/bin-iteration on the canonical "
-                                   f"half, 16 elsewhere, plus the DFTs of W and R)",
+                "work_per_launch": f"{flops:.4g} FP64 flops (19 per canonical bin and "
+                                   f"iteration, plus the DFTs of W and R)",
                 "peak_basis": f"nominal {FP64_FLOPS_PER_CLK_PER_SM} FP64 flops/clk/SM x {sms} SMs x "
                               f"{mhz:.0f} MHz (sampled)",
                 "probe_fp64_tflops": probe_flops / 1e12,

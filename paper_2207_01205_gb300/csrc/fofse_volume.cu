@@ -16,10 +16,12 @@
 // One CTA per block, everything in FP64 in shared memory: R and W (T^2 Tt
 // complex each, at most 4096 bins = 64 KB each), a stage buffer for the
 // separable DFTs that build them, and the twiddle tables.  Each iteration is
-// one pass over the bins that applies the update and evaluates the next
-// selection's energies, then a block-wide argmax (two barriers per
-// iteration).  The output samples of B accumulate in registers as the
-// iterations run.  The kernel is bound by the FP64 pipe.
+// one pass over the canonical half of the bins (a compact index list built
+// once per CTA) that applies the update and evaluates the next selection's
+// energies, then a block-wide argmax (two barriers per iteration).  The
+// output samples of B accumulate in registers as the iterations run.  The
+// kernel is bound by the FP64 pipe: the energy compares run on 64-bit integer
+// keys, and the per-iteration products of c are formed once per CTA.
 #include <math.h>
 
 #include <new>
@@ -76,18 +78,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// (e, lin) pairs: the larger energy wins, equal energies go to the smaller lin.
-__device__ __forceinline__ void better(double& e, int& l, double oe, int ol) {
+// Energies |R[k]|^2 >= 0 are compared through their bit patterns as signed
+// 64-bit integers, which order non-negative doubles as their values do (and
+// keep the compares off the FP64 pipe); -1 is below every energy.
+__device__ __forceinline__ long long energy_key(double2 r) {
+  return __double_as_longlong(fma(r.x, r.x, r.y * r.y));
+}
+
+// (key, lin) pairs: the larger energy wins, equal energies go to the smaller lin.
+__device__ __forceinline__ void better(long long& e, int& l, long long oe, int ol) {
   if (oe > e || (oe == e && ol < l)) {
     e = oe;
     l = ol;
   }
 }
 
-__device__ __forceinline__ void warp_argmax(double& e, int& l) {
+__device__ __forceinline__ void warp_argmax(long long& e, int& l) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    const double oe = __shfl_xor_sync(0xffffffffu, e, o);
+    const long long oe = __shfl_xor_sync(0xffffffffu, e, o);
     const int ol = __shfl_xor_sync(0xffffffffu, l, o);
     better(e, l, oe, ol);
   }
@@ -170,9 +179,17 @@ __global__ void __launch_bounds__(VolGeom<T, TT>::NT, 1)
   double2* X = W + K;
   __shared__ double2 twT[T], twTT[TT], syn[T * TT];
   __shared__ double red_e[NW];
+  __shared__ long long red_k[NW];
   __shared__ int red_l[NW];
-  __shared__ double2 bc_c;
-  __shared__ int bc_u[4];
+  __shared__ double bc[5];  // cr, ci, s cr, (1 + s) cr, (1 + s) ci
+  __shared__ int bc_u[3];
+  // the canonical set H as a list of layout indices: only H's bins are
+  // updated and searched (the others hold the conjugates of H's and are
+  // never read); |H| = (K + number of self-conjugate k) / 2 <= K / 2 + 4
+  constexpr int NCMAX = K / 2 + 4;
+  constexpr int RC = (NCMAX + NT - 1) / NT;  // list entries per thread
+  __shared__ int hidx[NCMAX];
+  __shared__ int wcnt[NW];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bi = blockIdx.x;
@@ -195,6 +212,39 @@ __global__ void __launch_bounds__(VolGeom<T, TT>::NT, 1)
     sincospi(2.0 * p / (T * TT), &s, &c);
     syn[p] = make_double2(c, s);
   }
+
+  // ---- H in increasing layout order: per-thread chunks of BPT bins, block scan ----
+  {
+    unsigned mask = 0;
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < BPT; ++j) {
+      const int i = tid * BPT + j;
+      const int k2 = i & (T - 1), k1 = (i >> LOGT) & (T - 1), k3 = i >> (2 * LOGT);
+      const int lin = ((k1 << LOGT) + k2) * TT + k3;
+      const int nlin = ((((-k1) & (T - 1)) << LOGT) + ((-k2) & (T - 1))) * TT + ((-k3) & (TT - 1));
+      if (lin <= nlin) {
+        mask |= 1u << j;
+        ++cnt;
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wcnt[warp] = incl;
+    __syncthreads();
+    int off = incl - cnt;
+    for (int w = 0; w < warp; ++w) off += wcnt[w];
+#pragma unroll
+    for (int j = 0; j < BPT; ++j)
+      if ((mask >> j) & 1u) hidx[off++] = tid * BPT + j;
+  }
+  int nc = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) nc += wcnt[w];
 
   // ---- weighted volume (Eq. 3, Eq. 4, Eq. 15 over three coordinates) ----
   double* xw = reinterpret_cast<double*>(X);
@@ -258,25 +308,25 @@ __global__ void __launch_bounds__(VolGeom<T, TT>::NT, 1)
   dft_time<T, TT, NT>(X, R, Lt, twTT);
   __syncthreads();
 
-  // ---- canonical indices of this thread's bins (-1: not canonical) ----
-  int can[BPT];
+  // ---- this thread's entries of H: layout index and lin (-1: none) ----
+  int hi[RC], hl[RC];
 #pragma unroll
-  for (int j = 0; j < BPT; ++j) {
-    const int i = tid + j * NT;
-    const int k2 = i & (T - 1), k1 = (i >> LOGT) & (T - 1), k3 = i >> (2 * LOGT);
-    const int lin = ((k1 << LOGT) + k2) * TT + k3;
-    const int nlin = ((((-k1) & (T - 1)) << LOGT) + ((-k2) & (T - 1))) * TT + ((-k3) & (TT - 1));
-    can[j] = lin <= nlin ? lin : -1;
-  }
-  double be = -1.0;
-  int bl = 0x7fffffff;
-#pragma unroll
-  for (int j = 0; j < BPT; ++j) {
-    if (can[j] >= 0) {
-      const double2 r = R[tid + j * NT];
-      better(be, bl, r.x * r.x + r.y * r.y, can[j]);
+  for (int r = 0; r < RC; ++r) {
+    const int j = tid + r * NT;
+    hi[r] = -1;
+    hl[r] = 0x7fffffff;
+    if (j < nc) {
+      const int i = hidx[j];
+      const int k2 = i & (T - 1), k1 = (i >> LOGT) & (T - 1), k3 = i >> (2 * LOGT);
+      hi[r] = i;
+      hl[r] = ((k1 << LOGT) + k2) * TT + k3;
     }
   }
+  long long bk = -1;
+  int bl = 0x7fffffff;
+#pragma unroll
+  for (int r = 0; r < RC; ++r)
+    if (hi[r] >= 0) better(bk, bl, energy_key(R[hi[r]]), hl[r]);
 
   double g[PPT];
   int gm[PPT], gn[PPT];
@@ -291,18 +341,18 @@ __global__ void __launch_bounds__(VolGeom<T, TT>::NT, 1)
   const double gamma = a.gamma;
   for (int it = 0; it < a.iters; ++it) {
     // ---- Eq. 9: block-wide argmax over the canonical set ----
-    warp_argmax(be, bl);
+    warp_argmax(bk, bl);
     if (lane == 0) {
-      red_e[warp] = be;
+      red_k[warp] = bk;
       red_l[warp] = bl;
     }
     __syncthreads();
     if (warp == 0) {
-      double e2 = lane < NW ? red_e[lane] : -1.0;
+      long long k2_ = lane < NW ? red_k[lane] : -1;
       int l2 = lane < NW ? red_l[lane] : 0x7fffffff;
-      warp_argmax(e2, l2);
-      // every energy NaN (an overflow on absurd inputs) leaves the sentinel:
-      // take k = 0 so that the index below stays inside R
+      warp_argmax(k2_, l2);
+      // no entry at all would leave the sentinel: take k = 0 so that the
+      // index below stays inside R
       if (l2 == 0x7fffffff) l2 = 0;
       if (lane == 0) {
         const int u3 = l2 & (TT - 1), u2 = (l2 >> LOGTT) & (T - 1), u1 = l2 >> (LOGTT + LOGT);
@@ -314,11 +364,15 @@ __global__ void __launch_bounds__(VolGeom<T, TT>::NT, 1)
         // Eq. 5 (p_u = R[u] / W0) and Eq. 14 (c = gamma p_u)
         const double cr = gamma * ru.x / W0;
         const double ci = s ? gamma * ru.y / W0 : 0.0;
-        bc_c = make_double2(cr, ci);
+        const double mult = s ? 2.0 : 1.0;
+        bc[0] = cr;
+        bc[1] = ci;
+        bc[2] = s ? cr : 0.0;  // ci is 0 when s is
+        bc[3] = mult * cr;
+        bc[4] = mult * ci;
         bc_u[0] = u1;
         bc_u[1] = u2;
         bc_u[2] = u3;
-        bc_u[3] = s;
         const size_t o = (size_t)bi * a.iters + it;
         if (a.path) {
           a.path[3 * o] = u1;
@@ -332,26 +386,28 @@ __global__ void __launch_bounds__(VolGeom<T, TT>::NT, 1)
       }
     }
     __syncthreads();
-    const double cr = bc_c.x, ci = bc_c.y;
-    const int u1 = bc_u[0], u2 = bc_u[1], u3 = bc_u[2], s = bc_u[3];
-    const double sd = s ? 1.0 : 0.0;
-    const double crs = sd * cr;  // ci is 0 when s is
+    const double cr = bc[0], ci = bc[1], crs = bc[2], mcr = bc[3], mci = bc[4];
+    const int u1 = bc_u[0], u2 = bc_u[1], u3 = bc_u[2];
 
     // ---- Eq. 1-2: B_hat += (1 + s) Re(c phi_u) at B (frame tau = depth) ----
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-      const int ph = ((((u1 * gm[q] + u2 * gn[q]) & (T - 1)) * TT) + ((u3 * D) & (TT - 1)) * T) &
-                     (T * TT - 1);
-      const double2 y = syn[ph];
-      g[q] += (1.0 + sd) * (cr * y.x - ci * y.y);
+      if (tid + q * NT < b * b) {
+        const int ph = ((((u1 * gm[q] + u2 * gn[q]) & (T - 1)) * TT) + ((u3 * D) & (TT - 1)) * T) &
+                       (T * TT - 1);
+        const double2 y = syn[ph];
+        g[q] = fma(mcr, y.x, g[q]);
+        g[q] = fma(-mci, y.y, g[q]);
+      }
     }
 
-    // ---- R[k] -= c W[k - u] + s conj(c) W[k + u]; energies of the next pick ----
-    be = -1.0;
+    // ---- R[k] -= c W[k - u] + s conj(c) W[k + u] on H; energies of the next pick ----
+    bk = -1;
     bl = 0x7fffffff;
 #pragma unroll
-    for (int j = 0; j < BPT; ++j) {
-      const int i = tid + j * NT;
+    for (int r = 0; r < RC; ++r) {
+      const int i = hi[r];
+      if (i < 0) continue;
       const int k2 = i & (T - 1), k1 = (i >> LOGT) & (T - 1), k3 = i >> (2 * LOGT);
       const int im_ = (((k3 - u3) & (TT - 1)) << (2 * LOGT)) | (((k1 - u1) & (T - 1)) << LOGT) |
                       ((k2 - u2) & (T - 1));
@@ -360,17 +416,17 @@ __global__ void __launch_bounds__(VolGeom<T, TT>::NT, 1)
       const double2 wa = W[im_], wb = W[ip_];
       // c W[k-u] = (cr wa.x - ci wa.y) + j (cr wa.y + ci wa.x)
       // conj(c) W[k+u] = (cr wb.x + ci wb.y) + j (cr wb.y - ci wb.x)
-      double2 r = R[i];
-      r.x = fma(-cr, wa.x, r.x);
-      r.x = fma(ci, wa.y, r.x);
-      r.x = fma(-crs, wb.x, r.x);
-      r.x = fma(-ci, wb.y, r.x);
-      r.y = fma(-cr, wa.y, r.y);
-      r.y = fma(-ci, wa.x, r.y);
-      r.y = fma(-crs, wb.y, r.y);
-      r.y = fma(ci, wb.x, r.y);
-      R[i] = r;
-      if (can[j] >= 0) better(be, bl, r.x * r.x + r.y * r.y, can[j]);
+      double2 rr = R[i];
+      rr.x = fma(-cr, wa.x, rr.x);
+      rr.x = fma(ci, wa.y, rr.x);
+      rr.x = fma(-crs, wb.x, rr.x);
+      rr.x = fma(-ci, wb.y, rr.x);
+      rr.y = fma(-cr, wa.y, rr.y);
+      rr.y = fma(-ci, wa.x, rr.y);
+      rr.y = fma(-crs, wb.y, rr.y);
+      rr.y = fma(ci, wb.x, rr.y);
+      R[i] = rr;
+      better(bk, bl, energy_key(rr), hl[r]);
     }
   }
 
