@@ -128,6 +128,12 @@ def _declare(L):
                                       ctypes.POINTER(OracleVolumePlan), _dp, _ip, _dp, _ip, _dp,
                                       _dp, _dp, _c_int]
     L.oracle_batch_volume.restype = _c_int
+    L.oracle_replay_volume.argtypes = [_c_int, _c_int, _c_int, _c_int, _dp, _dp, _c_double, _c_int,
+                                       _ip, _dp, _dp, _dp, _dp]
+    L.oracle_replay_volume.restype = _c_int
+    L.oracle_adjoint_volume.argtypes = [_c_int, _c_int, _c_int, _c_int, _dp, _dp, _c_double, _c_int,
+                                        _ip, _dp, _dp, _dp, _dp]
+    L.oracle_adjoint_volume.restype = _c_int
 
 
 def _p(a, t):
@@ -518,3 +524,29 @@ def run_batch_volume(video, avail, blocks, plan, threads: int | None = None) -> 
                                      _p(status, _ip), _p(w0, _dp), _p(path, _ip), _p(dr, _dp),
                                      _p(di, _dp), _p(gap, _dp), threads)
     return BatchResult(out, status, w0, path, dr + 1j * di, gap, used)
+
+
+def replay_volume(fL, wL, T: int, Tt: int, gamma: float, path) -> tuple:
+    """The volume recursion along a given path ((iters, 3)): (status, g, dc)."""
+    fL, wL = _f64(fL), _f64(wL)
+    path = _i32(path).reshape(-1, 3)
+    Lt, Ls, iters = fL.shape[0], fL.shape[1], path.shape[0]
+    g = np.empty(fL.shape)
+    dr, di = np.zeros(iters), np.zeros(iters)
+    st = lib().oracle_replay_volume(Lt, Ls, T, Tt, _p(fL, _dp), _p(wL, _dp), float(gamma), iters,
+                                    _p(path, _ip), _p(g, _dp), _p(dr, _dp), _p(di, _dp), None)
+    return st, g, dr + 1j * di
+
+
+def adjoint_volume(fL, wL, T: int, Tt: int, gamma: float, path, gbar):
+    """Reverse-mode adjoint of the volume recursion along ``path`` for the
+    loss <gbar, g>: (fbar, wbar, gammabar)."""
+    fL, wL, gbar = _f64(fL), _f64(wL), _f64(gbar)
+    path = _i32(path).reshape(-1, 3)
+    Lt, Ls, iters = fL.shape[0], fL.shape[1], path.shape[0]
+    fbar, wbar = np.empty(fL.shape), np.empty(fL.shape)
+    gam = ctypes.c_double()
+    lib().oracle_adjoint_volume(Lt, Ls, T, Tt, _p(fL, _dp), _p(wL, _dp), float(gamma), iters,
+                                _p(path, _ip), _p(gbar, _dp), _p(fbar, _dp), _p(wbar, _dp),
+                                ctypes.byref(gam))
+    return fbar, wbar, gam.value

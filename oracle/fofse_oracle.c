@@ -47,7 +47,8 @@
  *  - the squared error over B after every iteration count (Fig. 4, Fig. 5);
  *  - a threaded batch driver over a frame and its lost blocks;
  *  - video volumes (Sec. 1: the method carried over to three-dimensional
- *    sets), with the readings listed at the head of that section.
+ *    sets), with the readings listed at the head of that section, and their
+ *    frozen-path replay and adjoint.
  */
 #include <math.h>
 #include <pthread.h>
@@ -1317,4 +1318,123 @@ int oracle_batch_volume(const float* video, const unsigned char* avail, int fram
     free(th);
     pthread_mutex_destroy(&J.lock);
     return n_threads;
+}
+
+/* -------------------------------------------------------------------------- */
+/* Video volumes along a frozen path: replay and reverse-mode adjoint          */
+/* -------------------------------------------------------------------------- */
+
+/* Phase index of phi_u at (tau, m, n) over the common denominator T Tt. */
+static long phase3(const int* u, int tau, int m, int n, int T, int Tt) {
+    return ((((long)u[0] * m + (long)u[1] * n) * Tt) + (long)u[2] * tau * T) % ((long)T * Tt);
+}
+
+/* p_u = sum over the volume of rw exp(-j theta_u): the one projection the path needs. */
+static void project_one3(int Lt, int Ls, int T, int Tt, const double* rw, const int* u,
+                         double* pr, double* pi) {
+    double M = (double)T * Tt, re = 0.0, im = 0.0;
+    for (int tau = 0; tau < Lt; ++tau)
+        for (int m = 0; m < Ls; ++m)
+            for (int n = 0; n < Ls; ++n) {
+                double th = TWO_PI * (double)phase3(u, tau, m, n, T, Tt) / M;
+                double v = rw[((size_t)tau * Ls + m) * Ls + n];
+                re += v * cos(th);
+                im -= v * sin(th);
+            }
+    *pr = re;
+    *pi = im;
+}
+
+/* The recursion of oracle_extrapolate_volume with the selection replaced by
+ * the given path (iters x 3); g, coefficients, and optionally the model
+ * before every iteration (g_hist, iters x Lt Ls Ls). */
+int oracle_replay_volume(int Lt, int Ls, int T, int Tt, const double* fL, const double* wL,
+                         double gamma, int iters, const int* path, double* g, double* dc_re,
+                         double* dc_im, double* g_hist) {
+    size_t N = (size_t)Lt * Ls * Ls;
+    double W0 = 0.0;
+    for (size_t i = 0; i < N; ++i) W0 += wL[i];
+    for (size_t i = 0; i < N; ++i) g[i] = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    double* rw = (double*)malloc(sizeof(double) * N);
+    for (int it = 0; it < iters; ++it) {
+        const int* u = path + 3 * it;
+        if (g_hist) memcpy(g_hist + (size_t)it * N, g, sizeof(double) * N);
+        for (size_t i = 0; i < N; ++i) rw[i] = wL[i] != 0.0 ? wL[i] * (fL[i] - g[i]) : 0.0;
+        double pr, pi;
+        project_one3(Lt, Ls, T, Tt, rw, u, &pr, &pi);
+        double cr = gamma * pr / W0;
+        double ci = pair_weight_s3(u[0], u[1], u[2], T, Tt) ? gamma * pi / W0 : 0.0;
+        add_basis_pair3(Lt, Ls, T, Tt, u, cr, ci, g);
+        if (dc_re) dc_re[it] = cr;
+        if (dc_im) dc_im[it] = ci;
+    }
+    free(rw);
+    return ORC_OK;
+}
+
+/*
+ * Reverse-mode adjoint of the volume recursion along a fixed path.
+ *   gbar_out: adjoint of the final model over the volume (Lt x Ls x Ls),
+ *   e.g. dloss/dB on B in the centre frame and 0 elsewhere.
+ * Outputs fbar and wbar (nonzero only on A) and gammabar; rho enters only
+ * through w (oracle_rho_chain with the volume's distances chains wbar to rho).
+ */
+int oracle_adjoint_volume(int Lt, int Ls, int T, int Tt, const double* fL, const double* wL,
+                          double gamma, int iters, const int* path, const double* gbar_out,
+                          double* fbar, double* wbar, double* gammabar) {
+    size_t N = (size_t)Lt * Ls * Ls;
+    double W0 = 0.0, M = (double)T * Tt;
+    for (size_t i = 0; i < N; ++i) W0 += wL[i];
+    for (size_t i = 0; i < N; ++i) fbar[i] = wbar[i] = 0.0;
+    *gammabar = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    double* g = (double*)malloc(sizeof(double) * N);
+    double* gh = (double*)malloc(sizeof(double) * (size_t)iters * N);
+    double* dcr = (double*)malloc(sizeof(double) * iters);
+    double* dci = (double*)malloc(sizeof(double) * iters);
+    double* gbar = (double*)malloc(sizeof(double) * N);
+    double* cs = (double*)malloc(sizeof(double) * N);
+    double* sn = (double*)malloc(sizeof(double) * N);
+    oracle_replay_volume(Lt, Ls, T, Tt, fL, wL, gamma, iters, path, g, dcr, dci, gh);
+    memcpy(gbar, gbar_out, sizeof(double) * N);
+    double W0bar = 0.0;
+    for (int it = iters - 1; it >= 0; --it) {
+        const int* u = path + 3 * it;
+        int sp = pair_weight_s3(u[0], u[1], u[2], T, Tt);
+        double mult = 1.0 + sp;
+        const double* gprev = gh + (size_t)it * N;
+        for (int tau = 0; tau < Lt; ++tau)
+            for (int m = 0; m < Ls; ++m)
+                for (int n = 0; n < Ls; ++n) {
+                    size_t i = ((size_t)tau * Ls + m) * Ls + n;
+                    double th = TWO_PI * (double)phase3(u, tau, m, n, T, Tt) / M;
+                    cs[i] = cos(th);
+                    sn[i] = sin(th);
+                }
+        /* g_it = g_prev + mult (c_re cos - c_im sin): adjoint of the coefficient */
+        double cbar_re = 0.0, cbar_im = 0.0;
+        for (size_t i = 0; i < N; ++i) {
+            cbar_re += mult * gbar[i] * cs[i];
+            cbar_im -= mult * gbar[i] * sn[i];
+        }
+        if (!sp) cbar_im = 0.0;
+        /* c = gamma p / W0 */
+        double p_re = dcr[it] * W0 / gamma, p_im = dci[it] * W0 / gamma;
+        *gammabar += (cbar_re * p_re + cbar_im * p_im) / W0;
+        W0bar -= (cbar_re * dcr[it] + cbar_im * dci[it]) / W0;
+        double pbar_re = gamma / W0 * cbar_re, pbar_im = gamma / W0 * cbar_im;
+        /* p_re = sum rw cos, p_im = -sum rw sin, rw = w (f - g_prev) on A */
+        for (size_t i = 0; i < N; ++i) {
+            if (wL[i] == 0.0) continue;
+            double qv = pbar_re * cs[i] - pbar_im * sn[i];
+            fbar[i] += wL[i] * qv;
+            gbar[i] -= wL[i] * qv;
+            wbar[i] += (fL[i] - gprev[i]) * qv;
+        }
+    }
+    for (size_t i = 0; i < N; ++i)
+        if (wL[i] != 0.0) wbar[i] += W0bar;
+    free(g); free(gh); free(dcr); free(dci); free(gbar); free(cs); free(sn);
+    return ORC_OK;
 }

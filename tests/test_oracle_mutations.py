@@ -14,6 +14,7 @@ SRC = os.path.join(ROOT, "oracle", "fofse_oracle.c")
 OUT = os.path.join(ROOT, "oracle", "_build", "mutants")
 PINS = "tests/test_oracle_pins.py"
 VOL = "tests/test_oracle_volume.py"
+VOLADJ = "tests/test_oracle_volume_adjoint.py"
 
 MUTATIONS = [
     ("projection-sign", "im -= rw[m * Ls + n] * s[p];", "im += rw[m * Ls + n] * s[p];", [PINS]),
@@ -42,6 +43,9 @@ MUTATIONS = [
      [VOL]),
     ("volume-tie-break", "if (e > top) {", "if (e >= top) {", [VOL]),
     ("volume-synthesis-phase", "(long)u[2] * tau * T) % M;", "(long)u[2] * tau) % M;", [VOL]),
+    ("volume-adjoint-projection-sign", "double qv = pbar_re * cs[i] - pbar_im * sn[i];",
+     "double qv = pbar_re * cs[i] + pbar_im * sn[i];", [VOLADJ]),
+    ("volume-adjoint-model-sign", "gbar[i] -= wL[i] * qv;", "gbar[i] += wL[i] * qv;", [VOLADJ]),
 ]
 
 
