@@ -106,3 +106,30 @@ def test_1080p_three_frame_workload_on_a_sample():
     assert same.all(), f"{(~same).sum()} of {len(pick)} sampled paths differ"
     g = res.blocks.cpu().numpy()[pick].astype(np.float64)
     assert np.abs(g - ora.blocks).max() <= 1e-3
+
+
+LIMIT_PLANS = [  # (plan, seed of the test video)
+    (synth.VolumePlanSpec(24, 4, 1, 32, 4, 0.8, 0.5, 60), 45),   # b^2 > threads: two samples of B per thread
+    (synth.VolumePlanSpec(20, 6, 0, 32, 1, 0.8, 0.5, 60), 41),   # the same with 256 threads
+    (synth.VolumePlanSpec(16, 0, 3, 16, 8, 0.8, 0.5, 40), 337),  # deepest volume of its grid (7 frames), no border
+    (synth.VolumePlanSpec(8, 4, 1, 16, 4, 0.8, 0.9, 500), 29),   # long run
+]
+
+
+@pytest.mark.parametrize("spec,seed", LIMIT_PLANS,
+                         ids=[f"b{p.block}e{p.border}d{p.depth}T{p.fft_size}x{p.fft_time}I{p.iters}"
+                              for p, _ in LIMIT_PLANS])
+def test_largest_blocks_deepest_volumes_and_long_runs(spec, seed):
+    """Seeds chosen so that no selection of the oracle is an exact tie: where
+    the usable frames of a volume alias temporal frequencies (one usable
+    frame, or every other frame) two bins have equal magnitude in exact
+    arithmetic, and the pick between them depends on rounding (both are
+    correct)."""
+    n_frames = max(3, 2 * spec.depth + 1)
+    h, w = (96, 128) if spec.fft_size == 32 else (64, 96)
+    wl = synth.small_video(seed, n_frames=n_frames, height=h, width=w, n_lost=3, plan=spec)
+    ora = oracle.run_batch_volume(wl.video, wl.avail, wl.blocks, wl.plan)
+    assert ora.gap[ora.status == 0].min() > 0.0
+    res = _run(wl)
+    same, _ = _compare(res, ora, min_same=1.0)
+    assert same.all()
