@@ -323,16 +323,54 @@ def fofse_volume_plan_destroy(plan):
     load().fofse_volume_plan_destroy(ctypes.c_void_p(plan) if plan else None)
 
 
+def _require(t, name, dtype, shape=None, optional=False):
+    """Host-side check of a tensor handed to the C ABI as a device pointer:
+    a CUDA tensor of the given dtype (and leading shape), its last dimension
+    contiguous.  Raises ValueError, so that a host tensor or a wrong dtype
+    never reaches a kernel."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError(f"{name} is required")
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape[:len(shape)]) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}..., got {tuple(t.shape)}")
+    if t.dim() and t.numel() and t.stride(-1) != 1:
+        raise ValueError(f"{name} must be contiguous in its last dimension")
+
+
 def fofse_extrapolate_volume_batch(plan, blocks, video, avail, *, out_blocks, path=None, coef=None,
                                    w0=None, status=None, stream=None):
     """blocks: (n, 3) int32 device tensor (t, y, x); video float32 and avail
     uint8 device tensors of shape (F, H, W) with row pitch stride(1) and frame
     stride H * pitch; out_blocks (n, b, b) float32; path (n, iters, 3) int32,
     coef (n, iters, 2) float64, w0 (n,) float64, status (n,) int32."""
+    import torch
+    n = int(blocks.shape[0])
+    _require(blocks, "blocks", torch.int32, (n, 3))
+    if not blocks.is_contiguous():
+        raise ValueError("blocks must be contiguous")
+    _require(video, "video", torch.float32)
+    _require(avail, "avail", torch.uint8)
+    if video.dim() != 3:
+        raise ValueError(f"video must be (frames, height, width), got {tuple(video.shape)}")
+    _require(out_blocks, "out_blocks", torch.float32, (n,))
+    if not out_blocks.is_contiguous():
+        raise ValueError("out_blocks must be contiguous")
+    for t, name, dt in ((path, "path", torch.int32), (coef, "coef", torch.float64),
+                        (w0, "w0", torch.float64), (status, "status", torch.int32)):
+        _require(t, name, dt, (n,), optional=True)
+        if t is not None and not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
     F, H, W = video.shape
     pitch = video.stride(1)
-    assert video.stride(2) == 1 and video.stride(0) == H * pitch
-    assert tuple(avail.shape) == tuple(video.shape) and tuple(avail.stride()) == tuple(video.stride())
+    if video.stride(0) != H * pitch:
+        raise ValueError("video frames must be back to back (frame stride = height * row pitch)")
+    if tuple(avail.shape) != tuple(video.shape) or tuple(avail.stride()) != tuple(video.stride()):
+        raise ValueError("avail must have the video's shape and strides")
     _check(load().fofse_extrapolate_volume_batch(
         ctypes.c_void_p(plan), _ptr(blocks), int(blocks.shape[0]), _ptr(video), _ptr(avail), F, H, W,
         pitch, _ptr(out_blocks), _ptr(path), _ptr(coef), _ptr(w0), _ptr(status), _stream(stream)),

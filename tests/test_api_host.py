@@ -74,3 +74,37 @@ def test_volume_plan_arguments_are_checked_before_any_cuda_call():
     st = B.load().fofse_extrapolate_volume_batch(None, None, 1, None, None, 1, 1, 1, 1, None, None,
                                                  None, None, None, None)
     assert st == B.E_ARG
+
+
+def test_volume_batch_rejects_host_tensors_and_wrong_dtypes():
+    """The binding checks every tensor it hands to the C ABI as a device
+    pointer (no GPU needed: the checks run before the call)."""
+    import torch
+    from paper_2207_01205_gb300 import binding as B
+    n = 2
+    blocks = torch.zeros((n, 3), dtype=torch.int32)
+    video = torch.zeros((3, 8, 8), dtype=torch.float32)
+    avail = torch.ones((3, 8, 8), dtype=torch.uint8)
+    out = torch.zeros((n, 4, 4), dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA"):
+        B.fofse_extrapolate_volume_batch(1, blocks, video, avail, out_blocks=out)
+
+    class OnDevice:  # a host tensor that reports itself as a CUDA tensor
+        is_cuda = True
+
+        def __init__(self, t):
+            self.t, self.dtype, self.shape = t, t.dtype, t.shape
+
+        def __getattr__(self, k):
+            return getattr(self.t, k)
+
+    with pytest.raises(ValueError, match="int32"):
+        B._require(OnDevice(blocks.long()), "blocks", torch.int32, (n, 3))
+    with pytest.raises(ValueError, match="shape"):
+        B._require(OnDevice(torch.zeros((3, 3), dtype=torch.int32)), "blocks", torch.int32, (2, 3))
+    with pytest.raises(ValueError, match="contiguous"):
+        B._require(OnDevice(torch.zeros((2, 6), dtype=torch.int32)[:, ::2]), "blocks", torch.int32)
+    B._require(OnDevice(blocks), "blocks", torch.int32, (n, 3))
+    with pytest.raises(ValueError, match="required"):
+        B._require(None, "out_blocks", torch.float32)
+    B._require(None, "path", torch.int32, optional=True)
