@@ -128,6 +128,10 @@ def _declare(L):
                                       ctypes.POINTER(OracleVolumePlan), _dp, _ip, _dp, _ip, _dp,
                                       _dp, _dp, _c_int]
     L.oracle_batch_volume.restype = _c_int
+    L.oracle_batch_volume_mode.argtypes = L.oracle_batch_volume.argtypes + [_c_int]
+    L.oracle_batch_volume_mode.restype = _c_int
+    L.oracle_extrapolate_volume_fd.argtypes = L.oracle_extrapolate_volume.argtypes
+    L.oracle_extrapolate_volume_fd.restype = _c_int
     L.oracle_replay_volume.argtypes = [_c_int, _c_int, _c_int, _c_int, _dp, _dp, _c_double, _c_int,
                                        _ip, _dp, _dp, _dp, _dp]
     L.oracle_replay_volume.restype = _c_int
@@ -487,25 +491,29 @@ def select3(P: np.ndarray):
     return tuple(int(v) for v in u), gap.value
 
 
-def extrapolate_volume(fL, wL, T: int, Tt: int, gamma: float, iters: int) -> AreaResult:
-    """FOFSE over one volume (spatial re-projection): g (Lt, Ls, Ls), path
-    (iters, 3), dc complex, gap, w0."""
+def extrapolate_volume(fL, wL, T: int, Tt: int, gamma: float, iters: int,
+                       transform_domain: bool = False) -> AreaResult:
+    """FOFSE over one volume (spatial re-projection; with ``transform_domain``
+    the transform-domain form): g (Lt, Ls, Ls), path (iters, 3), dc complex,
+    gap, w0."""
     fL, wL = _f64(fL), _f64(wL)
     Lt, Ls = fL.shape[0], fL.shape[1]
     g = np.empty((Lt, Ls, Ls))
     path = np.zeros((iters, 3), dtype=np.int32)
     dr, di, gap = np.zeros(iters), np.zeros(iters), np.zeros(iters)
     w0 = ctypes.c_double()
-    st = lib().oracle_extrapolate_volume(Lt, Ls, T, Tt, _p(fL, _dp), _p(wL, _dp), float(gamma),
-                                         iters, _p(g, _dp), _p(path, _ip), _p(dr, _dp),
-                                         _p(di, _dp), _p(gap, _dp), ctypes.byref(w0))
+    fn = lib().oracle_extrapolate_volume_fd if transform_domain else lib().oracle_extrapolate_volume
+    st = fn(Lt, Ls, T, Tt, _p(fL, _dp), _p(wL, _dp), float(gamma), iters, _p(g, _dp),
+            _p(path, _ip), _p(dr, _dp), _p(di, _dp), _p(gap, _dp), ctypes.byref(w0))
     return AreaResult(st, g, path, dr + 1j * di, gap, w0.value)
 
 
-def run_batch_volume(video, avail, blocks, plan, threads: int | None = None) -> BatchResult:
+def run_batch_volume(video, avail, blocks, plan, threads: int | None = None,
+                     transform_domain: bool = False) -> BatchResult:
     """Extrapolate every block of ``blocks`` ((n, 3) int: t, y, x) of a video
     (F, H, W) with one volume plan (fields block, border, depth, fft_size,
-    fft_time, rho, gamma, iters).  path (n, iters, 3)."""
+    fft_time, rho, gamma, iters).  path (n, iters, 3).  ``transform_domain``
+    runs the transform-domain form instead of the spatial re-projection."""
     video = np.ascontiguousarray(video, dtype=np.float32)
     avail = np.ascontiguousarray(avail, dtype=np.uint8)
     blocks = _i32(blocks).reshape(-1, 3)
@@ -519,10 +527,11 @@ def run_batch_volume(video, avail, blocks, plan, threads: int | None = None) -> 
     cp = OracleVolumePlan(plan.block, plan.border, plan.depth, plan.fft_size, plan.fft_time,
                           plan.iters, float(plan.rho), float(plan.gamma))
     threads = threads or os.cpu_count() or 1
-    used = lib().oracle_batch_volume(_p(video, _fp), _p(avail, _u8p), F, H, W, W,
-                                     _p(blocks, _ip), n, ctypes.byref(cp), _p(out, _dp),
-                                     _p(status, _ip), _p(w0, _dp), _p(path, _ip), _p(dr, _dp),
-                                     _p(di, _dp), _p(gap, _dp), threads)
+    used = lib().oracle_batch_volume_mode(_p(video, _fp), _p(avail, _u8p), F, H, W, W,
+                                          _p(blocks, _ip), n, ctypes.byref(cp), _p(out, _dp),
+                                          _p(status, _ip), _p(w0, _dp), _p(path, _ip),
+                                          _p(dr, _dp), _p(di, _dp), _p(gap, _dp), threads,
+                                          1 if transform_domain else 0)
     return BatchResult(out, status, w0, path, dr + 1j * di, gap, used)
 
 

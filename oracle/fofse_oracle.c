@@ -1244,6 +1244,72 @@ int oracle_extrapolate_volume(int Lt, int Ls, int T, int Tt, const double* fL, c
     return ORC_OK;
 }
 
+/*
+ * The same method on the volume in the paper's transform-domain form (the
+ * closing remark of Sec. 2 on a 3-D grid): R = DFT(w f) and W = DFT(w) once
+ * (oracle_project3), then per iteration the pick over the canonical set, c =
+ * gamma R[u] / W0 and R[k] -= c W[k - u] + s(u) conj(c) W[k + u] over every
+ * bin, FP64.  The like-for-like CPU program for the GPU/CPU ratio, and a
+ * second, independently written check of the re-projection.  Arguments and
+ * outputs as oracle_extrapolate_volume.
+ */
+int oracle_extrapolate_volume_fd(int Lt, int Ls, int T, int Tt, const double* fL,
+                                 const double* wL, double gamma, int iters, double* g, int* path,
+                                 double* dc_re, double* dc_im, double* gap, double* w0_out) {
+    size_t N = (size_t)Lt * Ls * Ls, K = (size_t)T * T * Tt;
+    double W0 = 0.0;
+    for (size_t i = 0; i < N; ++i) W0 += wL[i];
+    if (w0_out) *w0_out = W0;
+    for (size_t i = 0; i < N; ++i) g[i] = 0.0;
+    if (!(W0 > 0.0)) return ORC_NO_SUPPORT;
+    for (size_t i = 0; i < N; ++i)
+        if (wL[i] != 0.0 && !isfinite(fL[i])) return ORC_NONFINITE;
+    double* x = (double*)malloc(sizeof(double) * N);
+    double* R_re = (double*)malloc(sizeof(double) * K);
+    double* R_im = (double*)malloc(sizeof(double) * K);
+    double* W_re = (double*)malloc(sizeof(double) * K);
+    double* W_im = (double*)malloc(sizeof(double) * K);
+    for (size_t i = 0; i < N; ++i) x[i] = wL[i] != 0.0 ? wL[i] * fL[i] : 0.0;
+    oracle_project3(Lt, Ls, T, Tt, x, R_re, R_im);
+    oracle_project3(Lt, Ls, T, Tt, wL, W_re, W_im);
+    for (int it = 0; it < iters; ++it) {
+        int u[3];
+        double gp;
+        oracle_select3(T, Tt, R_re, R_im, u, &gp);
+        long ui = lin3(u[0], u[1], u[2], T, Tt);
+        int sp = pair_weight_s3(u[0], u[1], u[2], T, Tt);
+        double cr = gamma * R_re[ui] / W0;
+        double ci = sp ? gamma * R_im[ui] / W0 : 0.0;
+        for (int k1 = 0; k1 < T; ++k1)
+            for (int k2 = 0; k2 < T; ++k2)
+                for (int k3 = 0; k3 < Tt; ++k3) {
+                    long k = lin3(k1, k2, k3, T, Tt);
+                    long a = lin3((k1 - u[0] + T) % T, (k2 - u[1] + T) % T, (k3 - u[2] + Tt) % Tt, T, Tt);
+                    long b = lin3((k1 + u[0]) % T, (k2 + u[1]) % T, (k3 + u[2]) % Tt, T, Tt);
+                    /* c W[a] */
+                    double tr = cr * W_re[a] - ci * W_im[a];
+                    double ti = cr * W_im[a] + ci * W_re[a];
+                    if (sp) {  /* + conj(c) W[b] */
+                        tr += cr * W_re[b] + ci * W_im[b];
+                        ti += cr * W_im[b] - ci * W_re[b];
+                    }
+                    R_re[k] -= tr;
+                    R_im[k] -= ti;
+                }
+        add_basis_pair3(Lt, Ls, T, Tt, u, cr, ci, g);
+        if (path) {
+            path[3 * it] = u[0];
+            path[3 * it + 1] = u[1];
+            path[3 * it + 2] = u[2];
+        }
+        if (dc_re) dc_re[it] = cr;
+        if (dc_im) dc_im[it] = ci;
+        if (gap) gap[it] = gp;
+    }
+    free(x); free(R_re); free(R_im); free(W_re); free(W_im);
+    return ORC_OK;
+}
+
 typedef struct {
     const float* video;
     const unsigned char* avail;
@@ -1258,6 +1324,7 @@ typedef struct {
     double* dc_re;              /* n x iters (nullable) */
     double* dc_im;
     double* gap;
+    int transform_domain;       /* 0: spatial re-projection, 1: transform-domain form */
     int next;
     pthread_mutex_t lock;
 } vbatch_job;
@@ -1274,7 +1341,7 @@ static void run_one_volume(vbatch_job* J, int bi) {
     oracle_cut_volume(J->video, J->avail, J->frames, J->height, J->width, J->pitch, bd[0], bd[1],
                       bd[2], P->block, P->border, P->depth, fL, aL);
     oracle_weights3(P->block, P->border, P->depth, P->rho, aL, wL);
-    J->status[bi] = oracle_extrapolate_volume(
+    J->status[bi] = (J->transform_domain ? oracle_extrapolate_volume_fd : oracle_extrapolate_volume)(
         Lt, Ls, P->fft_size, P->fft_time, fL, wL, P->gamma, P->iters, g,
         J->path ? J->path + 3 * I * bi : NULL, J->dc_re ? J->dc_re + I * bi : NULL,
         J->dc_im ? J->dc_im + I * bi : NULL, J->gap ? J->gap + I * bi : NULL,
@@ -1299,12 +1366,15 @@ static void* vbatch_worker(void* arg) {
 }
 
 /* Extrapolate every listed block of a video with one volume plan; returns
- * the number of threads used. */
-int oracle_batch_volume(const float* video, const unsigned char* avail, int frames, int height,
-                        int width, int pitch, const int* blocks, int n_blocks,
-                        const oracle_vplan* plan, double* out_blocks, int* status, double* w0,
-                        int* path, double* dc_re, double* dc_im, double* gap, int n_threads) {
+ * the number of threads used.  transform_domain selects
+ * oracle_extrapolate_volume_fd instead of the spatial re-projection. */
+int oracle_batch_volume_mode(const float* video, const unsigned char* avail, int frames,
+                             int height, int width, int pitch, const int* blocks, int n_blocks,
+                             const oracle_vplan* plan, double* out_blocks, int* status, double* w0,
+                             int* path, double* dc_re, double* dc_im, double* gap, int n_threads,
+                             int transform_domain) {
     vbatch_job J;
+    J.transform_domain = transform_domain;
     J.video = video; J.avail = avail; J.frames = frames; J.height = height; J.width = width;
     J.pitch = pitch; J.blocks = blocks; J.plan = *plan; J.n_blocks = n_blocks;
     J.out_blocks = out_blocks; J.status = status; J.w0 = w0; J.path = path; J.dc_re = dc_re;
@@ -1437,4 +1507,13 @@ int oracle_adjoint_volume(int Lt, int Ls, int T, int Tt, const double* fL, const
         if (wL[i] != 0.0) wbar[i] += W0bar;
     free(g); free(gh); free(dcr); free(dci); free(gbar); free(cs); free(sn);
     return ORC_OK;
+}
+
+int oracle_batch_volume(const float* video, const unsigned char* avail, int frames, int height,
+                        int width, int pitch, const int* blocks, int n_blocks,
+                        const oracle_vplan* plan, double* out_blocks, int* status, double* w0,
+                        int* path, double* dc_re, double* dc_im, double* gap, int n_threads) {
+    return oracle_batch_volume_mode(video, avail, frames, height, width, pitch, blocks, n_blocks,
+                                    plan, out_blocks, status, w0, path, dc_re, dc_im, gap,
+                                    n_threads, 0);
 }

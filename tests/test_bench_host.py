@@ -42,3 +42,19 @@ def test_cpu_samples_are_seeded_subsets():
     assert len({tuple(r) for r in a}) == 10
     assert bench._sample(wl, None) is wl.blocks
     assert bench._sample(wl, 1000) is wl.blocks
+
+
+def test_volume_cpu_legs_on_a_small_video():
+    """The video workload's CPU legs: a seeded oracle sample (the same blocks
+    every run) and the transform-domain form over all blocks, which takes the
+    oracle's paths."""
+    wl = synth.small_video(5, plan=synth.VolumePlanSpec(8, 4, 1, 16, 4, 0.8, 0.5, 20))
+    pick, ora, dt = bench.volume_oracle_sample(wl, 6, threads=2)
+    pick2, _, _ = bench.volume_oracle_sample(wl, 6, threads=2)
+    assert np.array_equal(pick, pick2) and len(pick) == 6 and dt > 0
+    assert (ora.status == 0).all()
+    fd = bench.cpu_volume_transform_domain(wl, threads=2)
+    assert fd["unit"] == "blocks/s" and fd["value"] > 0 and fd["cores"] == 2
+    import oracle
+    full = oracle.run_batch_volume(wl.video, wl.avail, wl.blocks, wl.plan, transform_domain=True)
+    assert np.array_equal(full.path[pick], ora.path)

@@ -46,6 +46,8 @@ MUTATIONS = [
     ("volume-adjoint-projection-sign", "double qv = pbar_re * cs[i] - pbar_im * sn[i];",
      "double qv = pbar_re * cs[i] + pbar_im * sn[i];", [VOLADJ]),
     ("volume-adjoint-model-sign", "gbar[i] -= wL[i] * qv;", "gbar[i] += wL[i] * qv;", [VOLADJ]),
+    ("volume-fd-shift", "long a = lin3((k1 - u[0] + T) % T, (k2 - u[1] + T) % T, (k3 - u[2] + Tt) % Tt, T, Tt);",
+     "long a = lin3((k1 - u[0] + T) % T, (k2 - u[1] + T) % T, (k3 + u[2]) % Tt, T, Tt);", [VOL]),
 ]
 
 

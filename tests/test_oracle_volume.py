@@ -222,3 +222,22 @@ def test_statuses_and_temporal_support_helps():
     e3 = np.mean((np.clip(r3.blocks, 0, 255) - truth) ** 2)
     e2 = np.mean((np.clip(r2.blocks, 0, 255) - truth) ** 2)
     assert e3 < e2
+
+
+@pytest.mark.parametrize("plan,seed", [
+    (synth.VolumePlanSpec(8, 4, 1, 16, 4, 0.8, 0.5, 40), 1),
+    (synth.VolumePlanSpec(8, 4, 2, 16, 8, 0.8, 0.7, 40), 2),
+    (synth.VolumePlanSpec(4, 2, 0, 8, 2, 0.9, 0.5, 30), 3),
+])
+def test_transform_domain_form_equals_the_reprojection(plan, seed):
+    """The transform-domain form (spectra transformed once, the spectrum of
+    each added pair subtracted from every bin) and the spatial re-projection
+    take the same path, coefficients to 1e-9 and models to 1e-9."""
+    n_frames = max(3, 2 * plan.depth + 1)
+    wl = synth.small_video(seed, n_frames=n_frames, plan=plan)
+    a = oracle.run_batch_volume(wl.video, wl.avail, wl.blocks, plan)
+    b = oracle.run_batch_volume(wl.video, wl.avail, wl.blocks, plan, transform_domain=True)
+    np.testing.assert_array_equal(a.status, b.status)
+    np.testing.assert_array_equal(a.path, b.path)
+    np.testing.assert_allclose(b.dc, a.dc, rtol=0, atol=1e-9 * np.abs(a.dc).max())
+    np.testing.assert_allclose(b.blocks, a.blocks, rtol=0, atol=1e-9 * np.abs(a.blocks).max())
