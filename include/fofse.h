@@ -438,8 +438,9 @@ void fofse_volume_plan_destroy(fofse_volume_plan plan);
  *                     not OK get B_hat = 0 and an all-zero path and coef
  *   stream            cudaStream_t
  * Returns FOFSE_OK once queued (n_blocks = 0 launches nothing), FOFSE_E_ARG for
- * a NULL plan or required pointer or a non-positive size, FOFSE_E_CUDA if the
- * launch failed.
+ * a NULL plan or required pointer, a non-positive size, or a current device
+ * other than the one the plan was created on; FOFSE_E_CUDA if the launch
+ * failed.
  */
 fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
                                             const fofse_volume_block* d_blocks, int n_blocks,

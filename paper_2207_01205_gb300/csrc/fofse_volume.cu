@@ -31,6 +31,7 @@
 struct fofse_volume_plan_s {
   int block, border, depth, T, Tt, Ls, Lt, iters;
   float rho, gamma;
+  int device;    // the device current at creation, which owns wtab
   double* wtab;  // device: rho^d over the Lt x Ls x Ls volume (tau, m, n)
 };
 
@@ -511,7 +512,12 @@ fofse_status fofse_volume_plan_create(int block, int border, int depth, int fft_
   p->rho = rho;
   p->gamma = gamma;
   const int ns = Lt * Ls * Ls;
-  cudaError_t e = cudaMalloc(&p->wtab, sizeof(double) * ns);
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return record_cuda_error(e);
+  }
+  e = cudaMalloc(&p->wtab, sizeof(double) * ns);
   if (e != cudaSuccess) {
     delete p;
     return e == cudaErrorMemoryAllocation ? FOFSE_E_NOMEM : record_cuda_error(e);
@@ -542,6 +548,8 @@ fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
     return FOFSE_E_ARG;
   if (n_blocks == 0) return FOFSE_OK;
   if (!d_blocks || !d_video || !d_avail || !d_out_blocks) return FOFSE_E_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return FOFSE_E_ARG;
   VolArgs a;
   a.block = plan->block;
   a.border = plan->border;
