@@ -31,7 +31,10 @@
  * the frozen selection path (fofse_backward), the squared error after every
  * iteration count (fofse_error_curve), the compensation factor of every
  * iteration (fofse_extrapolate_batch_gamma), and rho / gamma read from device
- * memory per call (d_rho_gamma).
+ * memory per call (d_rho_gamma).  Video volumes (the method over
+ * three-dimensional sets, Sec. 1) have their own plans and batch call
+ * (fofse_volume_plan_create, fofse_extrapolate_volume_batch), documented with
+ * their readings further down.
  *
  * Conventions for every entry point:
  *  - Pointers named d_* are DEVICE memory owned by the caller, on the device
