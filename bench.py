@@ -573,14 +573,12 @@ def run_volume_workload(args, rank, world, local):
                "sample": f"{len(pick)} of the {n} blocks, FP64 spatial re-projection over the "
                          f"volume, {ora.threads} threads, {dt:.1f} s"}
     if rank == 0:
-        line = {"metric": "16x16 blocks/s (video volumes, 32x32x4 grid, 200 it)",
+        line = {"metric": VIDEO_METRIC,
                 "value": job_value(n, world, ms), "unit": "blocks/s", "n_gpus": world,
                 "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": "video-3x1920x1080: 804 lost 16x16 blocks in the centre "
-                                       "frame, border 8, depth 1, 32x32x4 grid, rho 0.8, gamma 0.5, "
-                                       "200 it", "blocks_per_gpu": n,
+                "config": {"workload": VIDEO_WORKLOAD, "blocks_per_gpu": n,
                            "status_ok": int((st_np == 0).sum()),
                            "l2": "flushed between steps (512 MiB write)"},
                 "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": "blocks/s",
@@ -656,34 +654,73 @@ def stream_prediction_frames(plans, handles, blocks, ws, dev, bmax, n_frames=64)
             "includes": "H2D frame, forward, prediction-error gradient w.r.t. rho and gamma, D2H blocks"}
 
 
+VIDEO_METRIC = "16x16 blocks/s (video volumes, 32x32x4 grid, 200 it)"
+VIDEO_WORKLOAD = ("video-3x1920x1080: 804 lost 16x16 blocks in the centre frame, border 8, depth 1, "
+                  "32x32x4 grid, rho 0.8, gamma 0.5, 200 it")
+
+
+def _reference_workload(name):
+    """(metric, workload description, run(blocks), all blocks, threads) of the
+    oracle for the named workload: run(blocks) extrapolates the given rows of
+    the block list on all host cores."""
+    import oracle
+    from paper_2207_01205_gb300 import synth
+    threads = os.cpu_count() or 1
+    if name == "video-1080p":
+        wl = synth.video_concealment()
+        return (VIDEO_METRIC, VIDEO_WORKLOAD,
+                lambda b: oracle.run_batch_volume(wl.video, wl.avail, b, wl.plan, threads=threads),
+                wl.blocks, threads)
+    if name == "uneven-4k":
+        wl = synth.uneven_batch()
+        frame, avail, blocks, plans = wl.frame, wl.avail, wl.blocks, wl.plans
+        desc = "uneven-3840x2160: 4x4/8x8/16x16/32x32 blocks (T 32/32/64/128, I 50/100/200/400), 20 % area lost"
+        metric = f"blocks/s ({name})"
+    elif name == "predict-720p":
+        import numpy as np
+        frames, blocks, plans = synth.prediction_sequence(n_frames=1)
+        frame, avail = frames[0], np.ones(frames[0].shape, dtype=np.uint8)
+        desc = "predict-1280x720: 14,400 causal 8x8 blocks, border 8, 32x32 FFT, 64 it"
+        metric = f"blocks/s ({name})"
+    else:
+        wl = synth.frame_concealment()
+        frame, avail, blocks, plans = wl.frame, wl.avail, wl.blocks, wl.plans
+        desc, metric = WORKLOAD, METRIC
+    return (metric, desc,
+            lambda b: oracle.run_batch(frame, avail, b, plans, threads=threads, with_path=False),
+            blocks, threads)
+
+
 def run_reference(args, rank, world):
-    """The reference arm: the FP64 oracle timed on the host cores."""
+    """The reference arm: the FP64 oracle as it stands, timed on the host
+    cores on a bounded sample of the chosen workload's blocks per step (a
+    seeded random subset, so that a mixed batch keeps its class mix)."""
     if rank != 0:
         return
-    from paper_2207_01205_gb300 import synth
+    import numpy as np
     import oracle
-    wl = synth.frame_concealment()
-    threads = os.cpu_count() or 1
-    sample = max(threads, 16)
     oracle.build()
+    metric, desc, run, blocks, threads = _reference_workload(args.workload)
+    sample = max(threads, 16)
+    pick = np.sort(np.random.default_rng(2207).choice(len(blocks), size=min(sample, len(blocks)),
+                                                     replace=False))
+    sub = np.ascontiguousarray(blocks[pick])
     for _ in range(max(args.warmup, 0)):
-        oracle.run_batch(wl.frame, wl.avail, wl.blocks[:threads], wl.plans, threads=threads,
-                         with_path=False)
+        run(np.ascontiguousarray(sub[:threads]))
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.run_batch(wl.frame, wl.avail, wl.blocks[:sample], wl.plans, threads=threads,
-                         with_path=False)
+        run(sub)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
-    value = sample * args.steps / tot
-    line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": args.gpus,
+    value = len(sub) * args.steps / tot
+    line = {"metric": metric, "value": value, "unit": "blocks/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample_blocks_per_step": sample},
+            "config": {"workload": desc, "sample_blocks_per_step": len(sub)},
             "cpu_baseline": {"value": value, "unit": "blocks/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{sample} of {wl.n_blocks} blocks per step"},
+                             "sample": f"{len(sub)} of {len(blocks)} blocks per step (seeded random)"},
             "e2e": {"value": value, "unit": "blocks/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
