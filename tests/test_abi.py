@@ -19,6 +19,14 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def test_the_binding_has_a_function_of_each_name(lib):
+    """The Python binding mirrors the C ABI name for name."""
+    names = B.header_functions()
+    assert {"fofse_volume_plan_create", "fofse_extrapolate_volume_batch", "fofse_probe_dfma"} <= set(names)
+    for n in names:
+        assert callable(getattr(B, n, None)), n
+
+
 def test_status_strings_and_version(lib):
     for s in range(7):
         assert B.fofse_status_string(s) != "unknown status"
