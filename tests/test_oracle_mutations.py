@@ -15,6 +15,7 @@ OUT = os.path.join(ROOT, "oracle", "_build", "mutants")
 PINS = "tests/test_oracle_pins.py"
 VOL = "tests/test_oracle_volume.py"
 VOLADJ = "tests/test_oracle_volume_adjoint.py"
+BADJ = "tests/test_oracle_batch_adjoint.py"
 
 MUTATIONS = [
     ("projection-sign", "im -= rw[m * Ls + n] * s[p];", "im += rw[m * Ls + n] * s[p];", [PINS]),
@@ -48,6 +49,12 @@ MUTATIONS = [
     ("volume-adjoint-model-sign", "gbar[i] -= wL[i] * qv;", "gbar[i] += wL[i] * qv;", [VOLADJ]),
     ("volume-fd-shift", "long a = lin3((k1 - u[0] + T) % T, (k2 - u[1] + T) % T, (k3 - u[2] + Tt) % Tt, T, Tt);",
      "long a = lin3((k1 - u[0] + T) % T, (k2 - u[1] + T) % T, (k3 + u[2]) % Tt, T, Tt);", [VOL]),
+    ("batch-adjoint-plan-index", "grg[2 * bd[2]] += oracle_rho_chain(", "grg[0] += oracle_rho_chain(", [BADJ]),
+    ("batch-adjoint-gamma-overwrite", "grg[2 * bd[2] + 1] += gam;", "grg[2 * bd[2] + 1] = gam;", [BADJ]),
+    ("batch-adjoint-frame-overwrite", "gf[(size_t)fy * J->width + fx] += fbar[i];",
+     "gf[(size_t)fy * J->width + fx] = fbar[i];", [BADJ]),
+    ("batch-adjoint-thread-sum", "grad_frame[i] += J.grad_frame_t[t][i];",
+     "grad_frame[i] = J.grad_frame_t[t][i];", [BADJ]),
 ]
 
 
