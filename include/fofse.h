@@ -38,7 +38,9 @@
  *
  * Conventions for every entry point:
  *  - Pointers named d_* are DEVICE memory owned by the caller, on the device
- *    that was current when the plans were created.  The library never
+ *    that was current when the plans were created.  Every plan of a call must
+ *    have been created on the device that is current at the call: the calls
+ *    return FOFSE_E_ARG otherwise (before any launch).  The library never
  *    allocates or frees memory on the launch path (plans allocate their small
  *    constant tables once, in fofse_plan_create).
  *  - Frames are row-major float32 with `pitch` elements per row; availability
@@ -171,6 +173,12 @@ int fofse_plan_variant_count(fofse_plan plan);
  * to the rounding of float-float sums.  FOFSE_E_ARG otherwise.  Changing the
  * precision resets an out-of-range variant to 0. */
 fofse_status fofse_plan_set_variant(fofse_plan plan, int variant);
+/* The plan's block side, border, fft_size and iteration count (the values it
+ * was created with); each output pointer may be NULL.  Lets a caller size the
+ * outputs of a batch (bmax = largest block side, max_iters = largest
+ * iteration count over the call's plans).  FOFSE_E_ARG for a NULL plan. */
+fofse_status fofse_plan_get_shape(fofse_plan plan, int* block, int* border, int* fft_size,
+                                  int* iters);
 /* Frees the plan's tables (synchronises the device, so not while a CUDA graph
  * is being captured on it).  NULL is ignored. */
 void fofse_plan_destroy(fofse_plan plan);
@@ -278,9 +286,17 @@ fofse_status fofse_extrapolate_batch_gamma(const fofse_plan* plans, int n_plans,
  * library holds until the process exits.  It never calls cudaMalloc or
  * cudaFree.  Limits: at most 64 plans (FOFSE_E_ARG beyond), fft_size 32 or 64
  * only (a 128 x 128 FFT needs 256 KB of scratch per SM: FOFSE_E_UNSUPPORTED).
+ * Without a workspace there is no per-CTA scratch for the exact spectra, so
+ * FOFSE_FP32 plans run the kernel that updates every bin in float-float (the
+ * FOFSE_FP32_FULLFF arithmetic: the same exact selection path and
+ * coefficients up to float-float rounding, about half the speed of the
+ * workspace path) and the plan's launch-shape variant is ignored; DCT and
+ * FOFSE_FP64_VALIDATE plans run their usual kernels.
  *  - The first call on a device looks up that array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept per device for the life
+ *    of the process: after a cudaDeviceReset in the same process it is stale,
+ *    so do not call this entry point again after a reset.
  *  - Every call shares the array and clears the counters it uses at its start
  *    (an asynchronous memset on `stream`).  Calls whose work can overlap on the
  *    GPU (different streams, or different host threads) race on it: serialise

@@ -76,6 +76,9 @@ def _declare(L):
     L.fofse_plan_set_variant.restype = _i
     L.fofse_plan_destroy.argtypes = [_vp]
     L.fofse_plan_destroy.restype = None
+    _ip = ctypes.POINTER(_i)
+    L.fofse_plan_get_shape.argtypes = [_vp, _ip, _ip, _ip, _ip]
+    L.fofse_plan_get_shape.restype = _i
     L.fofse_workspace_bytes.argtypes = [ctypes.POINTER(_vp), _i, _i]
     L.fofse_workspace_bytes.restype = ctypes.c_size_t
     L.fofse_extrapolate_batch.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i,
@@ -193,6 +196,14 @@ def fofse_plan_set_variant(plan, variant):
     _check(load().fofse_plan_set_variant(ctypes.c_void_p(plan), int(variant)), "fofse_plan_set_variant")
 
 
+def fofse_plan_get_shape(plan) -> tuple[int, int, int, int]:
+    """(block, border, fft_size, iters) of a plan."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().fofse_plan_get_shape(ctypes.c_void_p(plan), *[ctypes.byref(x) for x in v]),
+           "fofse_plan_get_shape")
+    return tuple(x.value for x in v)
+
+
 def fofse_plan_destroy(plan):
     if plan:
         load().fofse_plan_destroy(ctypes.c_void_p(plan))
@@ -209,14 +220,116 @@ def fofse_workspace_bytes(plans, n_blocks) -> int:
     return load().fofse_workspace_bytes(_plan_array(plans), len(plans), int(n_blocks))
 
 
+def _require(t, name, dtype, shape=None, optional=False):
+    """Host-side check of a tensor handed to the C ABI as a device pointer:
+    the given dtype, a CUDA tensor (and leading shape), its last dimension
+    contiguous.  Raises ValueError, so that a host tensor or a wrong dtype
+    never reaches a kernel."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError(f"{name} is required")
+    if getattr(t, "dtype", None) != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {getattr(t, 'dtype', type(t))}")
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if shape is not None and tuple(t.shape[:len(shape)]) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}..., got {tuple(t.shape)}")
+    if t.dim() and t.numel() and t.stride(-1) != 1:
+        raise ValueError(f"{name} must be contiguous in its last dimension")
+
+
+def _require_buffer(t, name, dtype, min_numel, optional=True):
+    """A contiguous CUDA buffer of ``dtype`` with at least ``min_numel`` elements."""
+    _require(t, name, dtype, optional=optional)
+    if t is None:
+        return
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call writes {min_numel}")
+
+
+def _check_frame_args(blocks, frame, avail, out_frame=None, name_out="out_frame"):
+    """The block list and the frame / mask pair of a 2-D batch call; returns
+    (n, H, W, pitch)."""
+    import torch
+    # dtypes first, so that each argument's own error shows before any device check
+    for t, nm, dt in ((blocks, "blocks", torch.int32), (frame, "frame", torch.float32),
+                      (avail, "avail", torch.uint8), (out_frame, name_out, torch.float32)):
+        if t is not None and getattr(t, "dtype", None) != dt:
+            raise ValueError(f"{nm} must be {dt}, got {getattr(t, 'dtype', type(t))}")
+    if blocks.dim() != 2 or blocks.shape[1] != 3:
+        raise ValueError(f"blocks must be an (n, 3) int32 tensor, got shape {tuple(blocks.shape)}")
+    n = int(blocks.shape[0])
+    _require(blocks, "blocks", torch.int32, (n, 3))
+    if not blocks.is_contiguous():
+        raise ValueError("blocks must be contiguous")
+    _require(frame, "frame", torch.float32)
+    _require(avail, "avail", torch.uint8)
+    if frame.dim() != 2:
+        raise ValueError(f"frame must be (height, width), got {tuple(frame.shape)}")
+    if tuple(avail.shape) != tuple(frame.shape) or tuple(avail.stride()) != tuple(frame.stride()):
+        raise ValueError("avail must have the frame's shape and strides")
+    for t, nm in ((out_frame, name_out),):
+        _require(t, nm, torch.float32, optional=True)
+        if t is not None and (tuple(t.shape) != tuple(frame.shape)
+                              or tuple(t.stride()) != tuple(frame.stride())):
+            raise ValueError(f"{nm} must have the frame's shape and strides")
+    dev = frame.device
+    for t, nm in ((blocks, "blocks"), (avail, "avail"), (out_frame, name_out)):
+        if t is not None and t.device != dev:
+            raise ValueError(f"{nm} is on {t.device}, the frame on {dev}")
+    if dev.index != torch.cuda.current_device():
+        raise ValueError(f"the tensors are on {dev}, the current device is "
+                         f"cuda:{torch.cuda.current_device()} (plans belong to one device)")
+    H, W = frame.shape
+    return n, H, W, frame.stride(0)
+
+
+def _dims(plans):
+    """(bmax, imax) over the plans of a call: the output tile side and the
+    trace length per block."""
+    shapes = [fofse_plan_get_shape(p) for p in plans]
+    return max(s[0] for s in shapes), max(s[3] for s in shapes)
+
+
+def _check_on(dev, *named):
+    for t, nm in named:
+        if t is not None and t.device != dev:
+            raise ValueError(f"{nm} is on {t.device}, the frame on {dev}")
+
+
+def _check_batch_outputs(plans, n, dev, out_blocks, trace, w0, status, gamma=None, rho_gamma=None,
+                         workspace=None):
+    import torch
+    if not plans:
+        raise ValueError("at least one plan is required")
+    bmax, imax = _dims(plans)
+    _require_buffer(out_blocks, "out_blocks", torch.float32, n * bmax * bmax)
+    _require_buffer(trace, "trace", torch.int32, n * imax * 3)
+    _require_buffer(w0, "w0", torch.float32, n)
+    _require_buffer(status, "status", torch.int32, n)
+    _require_buffer(gamma, "gamma", torch.float32, n * imax * 2)
+    _require_buffer(rho_gamma, "rho_gamma", torch.float32, 2 * len(plans))
+    _require_buffer(workspace, "workspace", torch.uint8, fofse_workspace_bytes(plans, n))
+    _check_on(dev, (out_blocks, "out_blocks"), (trace, "trace"), (w0, "w0"), (status, "status"),
+              (gamma, "gamma"), (rho_gamma, "rho_gamma"), (workspace, "workspace"))
+    return bmax, imax
+
+
 def fofse_extrapolate_batch(plans, blocks, frame, avail, *, out_frame=None, out_blocks=None,
                             trace=None, w0=None, status=None, workspace=None, rho_gamma=None,
                             stream=None):
     """blocks: (n, 3) int32 device tensor; frame float32 and avail uint8 device
-    tensors of shape (H, W) (row pitch = stride(0))."""
-    H, W = frame.shape
-    pitch = frame.stride(0)
-    assert frame.stride(1) == 1 and avail.stride(1) == 1 and avail.stride(0) == pitch
+    tensors of shape (H, W) (row pitch = stride(0)); out_blocks (n, bmax, bmax)
+    float32, trace (n, max_iters, 3) int32, w0 (n,) float32, status (n,) int32,
+    workspace uint8 of fofse_workspace_bytes(plans, n) bytes, rho_gamma
+    (n_plans, 2) float32.  Every tensor is checked (CUDA, dtype, size, device)
+    before the call."""
+    n, H, W, pitch = _check_frame_args(blocks, frame, avail, out_frame)
+    _check_batch_outputs(plans, n, frame.device, out_blocks, trace, w0, status,
+                         rho_gamma=rho_gamma, workspace=workspace)
     _check(load().fofse_extrapolate_batch(
         _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
         _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(out_frame), _ptr(out_blocks), _ptr(trace),
@@ -228,9 +341,9 @@ def fofse_extrapolate_batch_gamma(plans, blocks, frame, avail, *, out_frame=None
                                   rho_gamma=None, stream=None):
     """fofse_extrapolate_batch that also writes the compensation factor of
     every iteration into ``gamma`` ((n, max_iters, 2) float32 device tensor)."""
-    H, W = frame.shape
-    pitch = frame.stride(0)
-    assert frame.stride(1) == 1 and avail.stride(1) == 1 and avail.stride(0) == pitch
+    n, H, W, pitch = _check_frame_args(blocks, frame, avail, out_frame)
+    _check_batch_outputs(plans, n, frame.device, out_blocks, trace, w0, status, gamma=gamma,
+                         rho_gamma=rho_gamma, workspace=workspace)
     _check(load().fofse_extrapolate_batch_gamma(
         _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
         _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(out_frame), _ptr(out_blocks), _ptr(trace),
@@ -243,10 +356,9 @@ def fofse_extrapolate_batch_noalloc(plans, blocks, frame, avail, *, out_frame=No
     """The forward batch call for callers that cannot allocate device memory:
     no workspace argument; the library's fixed 256-byte counter array is used
     instead (fft_size 32/64 only; calls that overlap on the GPU must be
-    serialised)."""
-    H, W = frame.shape
-    pitch = frame.stride(0)
-    assert frame.stride(1) == 1 and avail.stride(1) == 1 and avail.stride(0) == pitch
+    serialised).  Tensors are checked as in fofse_extrapolate_batch."""
+    n, H, W, pitch = _check_frame_args(blocks, frame, avail, out_frame)
+    _check_batch_outputs(plans, n, frame.device, out_blocks, trace, w0, status)
     _check(load().fofse_extrapolate_batch_noalloc(
         _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
         _ptr(avail), H, W, pitch, _ptr(out_frame), _ptr(out_blocks), _ptr(trace), _ptr(w0),
@@ -255,8 +367,19 @@ def fofse_extrapolate_batch_noalloc(plans, blocks, frame, avail, *, out_frame=No
 
 def fofse_backward(plans, blocks, frame, avail, trace, w0, grad_blocks, *, grad_frame=None,
                    grad_rho_gamma=None, workspace=None, rho_gamma=None, stream=None):
-    H, W = frame.shape
-    pitch = frame.stride(0)
+    """Frozen-path adjoint: trace and w0 from the forward call, grad_blocks
+    (n, bmax, bmax) float32 dloss/dB_hat; grad_frame (frame's shape and
+    strides) and grad_rho_gamma (n_plans, 2) float32 are accumulated.  Every
+    tensor is checked (CUDA, dtype, size, device) before the call."""
+    import torch
+    n, H, W, pitch = _check_frame_args(blocks, frame, avail, grad_frame, "grad_frame")
+    if trace is None or w0 is None or grad_blocks is None:
+        raise ValueError("trace, w0 and grad_blocks are required")
+    bmax, imax = _check_batch_outputs(plans, n, frame.device, None, trace, w0, None,
+                                      rho_gamma=rho_gamma, workspace=workspace)
+    _require_buffer(grad_blocks, "grad_blocks", torch.float32, n * bmax * bmax, optional=False)
+    _require_buffer(grad_rho_gamma, "grad_rho_gamma", torch.float32, 2 * len(plans))
+    _check_on(frame.device, (grad_blocks, "grad_blocks"), (grad_rho_gamma, "grad_rho_gamma"))
     _check(load().fofse_backward(
         _plan_array(plans), len(plans), _ptr(blocks), int(blocks.shape[0]), _ptr(frame),
         _ptr(avail), H, W, pitch, _ptr(rho_gamma), _ptr(trace), _ptr(w0), _ptr(grad_blocks),
@@ -321,25 +444,6 @@ def fofse_volume_plan_create(block, border, depth, fft_size, fft_time, rho, gamm
 
 def fofse_volume_plan_destroy(plan):
     load().fofse_volume_plan_destroy(ctypes.c_void_p(plan) if plan else None)
-
-
-def _require(t, name, dtype, shape=None, optional=False):
-    """Host-side check of a tensor handed to the C ABI as a device pointer:
-    a CUDA tensor of the given dtype (and leading shape), its last dimension
-    contiguous.  Raises ValueError, so that a host tensor or a wrong dtype
-    never reaches a kernel."""
-    if t is None:
-        if optional:
-            return
-        raise ValueError(f"{name} is required")
-    if not getattr(t, "is_cuda", False):
-        raise ValueError(f"{name} must be a CUDA tensor")
-    if t.dtype != dtype:
-        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
-    if shape is not None and tuple(t.shape[:len(shape)]) != tuple(shape):
-        raise ValueError(f"{name} must have shape {tuple(shape)}..., got {tuple(t.shape)}")
-    if t.dim() and t.numel() and t.stride(-1) != 1:
-        raise ValueError(f"{name} must be contiguous in its last dimension")
 
 
 def fofse_extrapolate_volume_batch(plan, blocks, video, avail, *, out_blocks, path=None, coef=None,

@@ -44,9 +44,10 @@ cudaError_t launch_plan_weights(const PlanDev& p, const float* rho_gamma, float2
 }  // namespace fofse
 
 struct fofse_plan_s {
+  int device;    // the device current at creation, which owns the tables (first
+                 // member: host tests build a stand-in plan with only this set)
   PlanDev dev;   // scalars + device table pointers
   void* mem;     // one device allocation holding every table
-  int device;
 };
 
 namespace {
@@ -123,6 +124,17 @@ bool encode_2d(CUtensorMap* map, CUtensorMapDataType ty, int esize, const void* 
 }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Every plan of a call must belong to the current device: its tables live in
+// that device's memory, and the kernels run on the current device.  False for
+// a NULL plan, and when no device is current.
+bool plans_on_current_device(const fofse_plan* plans, int n_plans) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  for (int i = 0; i < n_plans; ++i)
+    if (!plans[i] || plans[i]->device != dev) return false;
+  return true;
+}
 
 bool supported_T(int T) { return T == 32 || T == 64 || T == 128; }
 
@@ -408,6 +420,16 @@ fofse_status fofse_plan_set_variant(fofse_plan plan, int variant) {
   return FOFSE_OK;
 }
 
+fofse_status fofse_plan_get_shape(fofse_plan plan, int* block, int* border, int* fft_size,
+                                  int* iters) {
+  if (!plan) return FOFSE_E_ARG;
+  if (block) *block = plan->dev.block;
+  if (border) *border = plan->dev.border;
+  if (fft_size) *fft_size = plan->dev.T;
+  if (iters) *iters = plan->dev.iters;
+  return FOFSE_OK;
+}
+
 void fofse_plan_destroy(fofse_plan plan) {
   if (!plan) return;
   cudaDeviceSynchronize();
@@ -452,9 +474,9 @@ fofse_status fofse_extrapolate_batch_gamma(const fofse_plan* plans, int n_plans,
   if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail)) return FOFSE_E_ARG;
   if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
   if (d_rho_gamma && !d_workspace) return FOFSE_E_ARG;  // the rebuilt weights live there
+  if (!plans_on_current_device(plans, n_plans)) return FOFSE_E_ARG;
   int bmax = 0, imax = 0;
   for (int i = 0; i < n_plans; ++i) {
-    if (!plans[i]) return FOFSE_E_ARG;
     if (plans[i]->dev.precision != plans[0]->dev.precision) return FOFSE_E_ARG;
     bmax = plans[i]->dev.block > bmax ? plans[i]->dev.block : bmax;
     imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
@@ -548,10 +570,12 @@ fofse_status fofse_extrapolate_batch_gamma(const fofse_plan* plans, int n_plans,
   return FOFSE_OK;
 }
 
-// fofse_extrapolate_batch without a workspace: see include/fofse.h.  It
-// launches the same forward kernels as fofse_extrapolate_batch; only the
+// fofse_extrapolate_batch without a workspace: see include/fofse.h.  The
 // work-queue counters come from the library's fixed device array instead of
-// the caller's workspace.  Nothing here allocates or frees device memory.
+// the caller's workspace, and with no scratch for the exact spectra
+// FOFSE_FP32 plans run the all-bins float-float kernel (the plan's launch
+// shape variant is ignored); DCT and FP64-validation plans run their usual
+// kernels.  Nothing here allocates or frees device memory.
 fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plans,
                                              const fofse_block* d_blocks, int n_blocks,
                                              const float* d_frame, const uint8_t* d_avail,
@@ -563,9 +587,9 @@ fofse_status fofse_extrapolate_batch_noalloc(const fofse_plan* plans, int n_plan
   if (n_plans > kNoAllocCounters) return FOFSE_E_ARG;  // one counter per plan in the fixed array
   if (n_blocks > 0 && (!d_blocks || !d_frame || !d_avail)) return FOFSE_E_ARG;
   if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
+  if (!plans_on_current_device(plans, n_plans)) return FOFSE_E_ARG;
   int bmax = 0, imax = 0;
   for (int i = 0; i < n_plans; ++i) {
-    if (!plans[i]) return FOFSE_E_ARG;
     if (plans[i]->dev.precision != plans[0]->dev.precision) return FOFSE_E_ARG;
     // a 128 x 128 FFT needs 256 KB of scratch per SM, beyond the fixed array;
     // OFSE needs the scratch of the register-blocked kernel
@@ -635,9 +659,9 @@ fofse_status fofse_error_curve(const fofse_plan* plans, int n_plans, const fofse
   if (!plans || n_plans < 1 || n_plans > kMaxPlans || n_blocks < 0) return FOFSE_E_ARG;
   if (n_blocks > 0 && (!d_blocks || !d_trace || !d_truth || !d_sse)) return FOFSE_E_ARG;
   if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
+  if (!plans_on_current_device(plans, n_plans)) return FOFSE_E_ARG;
   int imax = 0;
   for (int i = 0; i < n_plans; ++i) {
-    if (!plans[i]) return FOFSE_E_ARG;
     if (plans[i]->dev.block > 32) return FOFSE_E_UNSUPPORTED;
     imax = plans[i]->dev.iters > imax ? plans[i]->dev.iters : imax;
   }
@@ -674,9 +698,9 @@ fofse_status fofse_backward(const fofse_plan* plans, int n_plans, const fofse_bl
     return FOFSE_E_ARG;
   if (height < 1 || width < 1 || pitch < width) return FOFSE_E_ARG;
   if (d_rho_gamma && !d_workspace) return FOFSE_E_ARG;
+  if (!plans_on_current_device(plans, n_plans)) return FOFSE_E_ARG;
   int bmax = 0, imax = 0;
   for (int i = 0; i < n_plans; ++i) {
-    if (!plans[i]) return FOFSE_E_ARG;
     if (plans[i]->dev.precision == FOFSE_FP64_VALIDATE) return FOFSE_E_UNSUPPORTED;
     if (plans[i]->dev.compensation == FOFSE_COMP_OFSE) return FOFSE_E_UNSUPPORTED;
     if (!dct_supported(plans[i]->dev)) return FOFSE_E_UNSUPPORTED;

@@ -87,3 +87,85 @@ def test_newer_entry_points_reject_null_arguments(lib):
     assert lib.fofse_probe_smem(0, 1, null, ctypes.byref(out), null) == B.E_ARG
     assert lib.fofse_probe_fma(1, 0, null, ctypes.byref(out), null) == B.E_ARG
     assert lib.fofse_probe_smem(1, 1, None, ctypes.byref(out), null) == B.E_ARG
+
+
+def _foreign_plan():
+    """A stand-in plan whose creating device (the first member of the plan
+    struct) is 63, a device that is never current: the 2-D calls must refuse
+    it before looking at anything else in it or launching."""
+    buf = (ctypes.c_int32 * 2048)()
+    buf[0] = 63
+    return buf
+
+
+def test_2d_calls_refuse_a_plan_of_another_device(lib):
+    fake = _foreign_plan()
+    plans = (ctypes.c_void_p * 1)(ctypes.addressof(fake))
+    d = ctypes.c_void_p(256)  # never dereferenced: the call returns first
+    null = ctypes.c_void_p()
+    assert lib.fofse_extrapolate_batch(plans, 1, d, 1, d, d, 8, 8, 8, null, null, d, null, null,
+                                       null, d, null) == B.E_ARG
+    assert lib.fofse_extrapolate_batch_gamma(plans, 1, d, 1, d, d, 8, 8, 8, null, null, d, null,
+                                             null, null, null, d, null) == B.E_ARG
+    assert lib.fofse_extrapolate_batch_noalloc(plans, 1, d, 1, d, d, 8, 8, 8, null, d, null, null,
+                                               null, null) == B.E_ARG
+    assert lib.fofse_backward(plans, 1, d, 1, d, d, 8, 8, 8, null, d, d, d, d, null, d,
+                              null) == B.E_ARG
+    assert lib.fofse_error_curve(plans, 1, d, 1, d, d, 8, 8, 8, d, null) == B.E_ARG
+
+
+def test_plan_shape_query_rejects_null(lib):
+    v = ctypes.c_int()
+    assert lib.fofse_plan_get_shape(None, ctypes.byref(v), None, None, None) == B.E_ARG
+
+
+class _Called(Exception):
+    pass
+
+
+@pytest.fixture
+def no_c_calls(monkeypatch):
+    """Fails the test if a batch call reaches the C library."""
+    def boom(*a, **k):
+        raise _Called()
+    L = B.load()
+    for name in ("fofse_extrapolate_batch", "fofse_extrapolate_batch_gamma",
+                 "fofse_extrapolate_batch_noalloc", "fofse_backward", "fofse_plan_get_shape",
+                 "fofse_workspace_bytes"):
+        monkeypatch.setattr(L, name, boom)
+
+
+def _host_inputs():
+    import torch
+    blocks = torch.zeros((2, 3), dtype=torch.int32)
+    frame = torch.zeros((32, 32), dtype=torch.float32)
+    avail = torch.ones((32, 32), dtype=torch.uint8)
+    return blocks, frame, avail
+
+
+@pytest.mark.parametrize("call", ["batch", "gamma", "noalloc", "backward"])
+def test_binding_rejects_host_tensors_and_wrong_dtypes_before_the_c_call(no_c_calls, call):
+    import torch
+    blocks, frame, avail = _host_inputs()
+
+    def run(bl, fr, av):
+        if call == "batch":
+            B.fofse_extrapolate_batch([1], bl, fr, av)
+        elif call == "gamma":
+            B.fofse_extrapolate_batch_gamma([1], bl, fr, av)
+        elif call == "noalloc":
+            B.fofse_extrapolate_batch_noalloc([1], bl, fr, av)
+        else:
+            tr = torch.zeros((2, 4, 3), dtype=torch.int32)
+            B.fofse_backward([1], bl, fr, av, tr, torch.zeros(2), torch.zeros((2, 4, 4)))
+
+    with pytest.raises(ValueError, match="int32"):
+        run(blocks.long(), frame, avail)
+    with pytest.raises(ValueError, match="float32"):
+        run(blocks, frame.double(), avail)
+    with pytest.raises(ValueError, match="uint8"):
+        run(blocks, frame, avail.bool())
+    with pytest.raises(ValueError, match="CUDA"):
+        run(blocks, frame, avail)
+    with pytest.raises(ValueError, match=r"\(n, 3\)|shape"):
+        run(blocks[:, :2].contiguous(), frame, avail)
