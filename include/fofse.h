@@ -78,7 +78,7 @@ typedef enum {
 enum { FOFSE_SUPPORT_FULL = 0,      /* all of L outside B (concealment)                 */
        FOFSE_SUPPORT_CAUSAL_L = 1 }; /* rows above B up to B's right edge, plus the
                                         samples left of B in B's rows (prediction)      */
-/* arithmetic of the kernels */
+/* arithmetic of the kernels (the values 2 and 4 are not used) */
 enum { FOFSE_FP32 = 0,           /* the product: exact selection path and coefficients
                                     with FP32 instructions.  With the workspace: FP32
                                     working spectrum with a rigorous error bound, near
@@ -86,13 +86,7 @@ enum { FOFSE_FP32 = 0,           /* the product: exact selection path and coeffi
                                     register-blocked kernel); without it, as
                                     FOFSE_FP32_FULLFF                                   */
        FOFSE_FP64_VALIDATE = 1,  /* IEEE double; slow on GB300, for validation           */
-       FOFSE_FP32_PLAIN = 2,     /* plain FP32; diverges from the exact selection path at
-                                    near-ties, kept for comparison                       */
-       FOFSE_FP32_FULLFF = 3,    /* every bin updated in float-float (pairs of FP32)      */
-       FOFSE_FP32_FILTERED = 4 };/* the same decisions as FOFSE_FP32 by the earlier
-                                    filtered kernel layout (kept for comparison).
-                                    Needs the workspace's scratch; without it runs as
-                                    FOFSE_FP32_FULLFF                                   */
+       FOFSE_FP32_FULLFF = 3 };  /* every bin updated in float-float (pairs of FP32)      */
 /* compensation of the projection coefficient */
 enum { FOFSE_COMP_CONSTANT = 0,  /* c = gamma p_u with the plan's constant gamma (Eq. 14):
                                     FOFSE, the default                                  */
@@ -146,8 +140,8 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
                                int iters, fofse_plan* out);
 /* Support shape (FOFSE_SUPPORT_*); default FULL.  FOFSE_E_ARG for other values. */
 fofse_status fofse_plan_set_support(fofse_plan plan, int shape);
-/* Arithmetic (FOFSE_FP32 default, FOFSE_FP64_VALIDATE, FOFSE_FP32_PLAIN,
- * FOFSE_FP32_FULLFF, FOFSE_FP32_FILTERED). */
+/* Arithmetic (FOFSE_FP32 default, FOFSE_FP64_VALIDATE, FOFSE_FP32_FULLFF);
+ * FOFSE_E_ARG for other values. */
 fofse_status fofse_plan_set_precision(fofse_plan plan, int precision);
 /* Compensation (FOFSE_COMP_*); default FOFSE_COMP_CONSTANT.  FOFSE_COMP_OFSE
  * runs only with FOFSE_FP32 and a workspace (fofse_extrapolate_batch returns
@@ -369,22 +363,6 @@ fofse_status fofse_check(void* stream);
  * reporting of this library. */
 int fofse_last_cuda_error(void);
 const char* fofse_last_cuda_error_string(void);
-
-/*
- * Measurement probes (no counterpart in the paper): kernels that only load
- * shared memory (16 B per thread and load, no bank conflicts) or only issue
- * FP32 (fofse_probe_fma) or FP64 (fofse_probe_dfma) fused multiply-adds,
- * giving this GPU's rates for the rooflines of the kernels above.  Each
- * launches `ctas` blocks of 1024 threads doing `rounds` rounds on `stream`
- * and returns the work queued: *bytes loaded from shared memory, or *fmas
- * lane FMAs.  d_sink: device buffer of ctas x 1024 floats (doubles for the
- * FP64 probe); it keeps the work from being optimised away and is in
- * practice never written.  The caller times the launch.  FOFSE_E_ARG for
- * non-positive sizes or NULL.
- */
-fofse_status fofse_probe_smem(int ctas, int rounds, float* d_sink, double* bytes, void* stream);
-fofse_status fofse_probe_fma(int ctas, int rounds, float* d_sink, double* fmas, void* stream);
-fofse_status fofse_probe_dfma(int ctas, int rounds, double* d_sink, double* fmas, void* stream);
 
 /*
  * Video volumes (Sec. 1: the method carried over to three-dimensional sets;

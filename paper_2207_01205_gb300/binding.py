@@ -16,18 +16,19 @@ from . import build as _build
 
 OK, E_ARG, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_STATE = range(7)
 SUPPORT_FULL, SUPPORT_CAUSAL_L = 0, 1
-FP32, FP64_VALIDATE, FP32_PLAIN, FP32_FULLFF, FP32_FILTERED = 0, 1, 2, 3, 4
+FP32, FP64_VALIDATE, FP32_FULLFF = 0, 1, 3
 BLK_OK, BLK_NO_SUPPORT, BLK_NONFINITE, BLK_TIMEOUT = 0, 1, 2, 3
 COMP_CONSTANT, COMP_OFSE = 0, 1
 BASIS_DFT, BASIS_DCT = 0, 1
-PRECISIONS = {"fp32": FP32, "fp64": FP64_VALIDATE, "fp32_plain": FP32_PLAIN,
-              "fp32_fullff": FP32_FULLFF, "fp32_filtered": FP32_FILTERED}
+PRECISIONS = {"fp32": FP32, "fp64": FP64_VALIDATE, "fp32_fullff": FP32_FULLFF}
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
-                      "fofse.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+HEADER = os.path.join(INCLUDE, "fofse.h")
+PROBES_HEADER = os.path.join(INCLUDE, "fofse_probes.h")
 
 _lock = threading.Lock()
 _lib = None
+_probes = None
 
 
 class FofseError(RuntimeError):
@@ -48,9 +49,9 @@ _vp = ctypes.c_void_p
 _i = ctypes.c_int
 
 
-def header_functions() -> list[str]:
-    """Names of the functions declared in include/fofse.h."""
-    txt = open(HEADER).read()
+def header_functions(header: str = HEADER) -> list[str]:
+    """Names of the functions declared in a header (default include/fofse.h)."""
+    txt = open(header).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(fofse_\w+)\s*\(", txt)))
 
@@ -95,12 +96,6 @@ def _declare(L):
     L.fofse_backward.restype = _i
     L.fofse_error_curve.argtypes = [ctypes.POINTER(_vp), _i, _vp, _i, _vp, _vp, _i, _i, _i, _vp, _vp]
     L.fofse_error_curve.restype = _i
-    L.fofse_probe_smem.argtypes = [_i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp]
-    L.fofse_probe_smem.restype = _i
-    L.fofse_probe_fma.argtypes = [_i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp]
-    L.fofse_probe_fma.restype = _i
-    L.fofse_probe_dfma.argtypes = [_i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp]
-    L.fofse_probe_dfma.restype = _i
     L.fofse_volume_plan_create.argtypes = [_i, _i, _i, _i, _i, ctypes.c_float, ctypes.c_float, _i,
                                            ctypes.POINTER(_vp)]
     L.fofse_volume_plan_create.restype = _i
@@ -127,6 +122,25 @@ def load(build: bool = True):
             _declare(L)
             _lib = L
     return _lib
+
+
+def load_probes():
+    """Load ``libfofse_probes.so``, the measurement probes of
+    include/fofse_probes.h (built with the product library)."""
+    global _probes
+    load()
+    with _lock:
+        if _probes is None:
+            path = _build.PROBES_LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libfofse_probes.so not built ({path})")
+            L = ctypes.CDLL(path)
+            for name in ("fofse_probe_smem", "fofse_probe_fma", "fofse_probe_dfma"):
+                fn = getattr(L, name)
+                fn.argtypes = [_i, _i, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+                fn.restype = _i
+            _probes = L
+    return _probes
 
 
 def library_path() -> str:
@@ -400,7 +414,7 @@ def fofse_error_curve(plans, blocks, trace, truth, sse, *, stream=None):
 def fofse_probe_smem(ctas, rounds, sink, *, stream=None) -> float:
     """Queues the shared-memory load probe; returns the bytes it loads."""
     out = ctypes.c_double()
-    _check(load().fofse_probe_smem(int(ctas), int(rounds), _ptr(sink), ctypes.byref(out),
+    _check(load_probes().fofse_probe_smem(int(ctas), int(rounds), _ptr(sink), ctypes.byref(out),
                                    _stream(stream)), "fofse_probe_smem")
     return out.value
 
@@ -408,7 +422,7 @@ def fofse_probe_smem(ctas, rounds, sink, *, stream=None) -> float:
 def fofse_probe_fma(ctas, rounds, sink, *, stream=None) -> float:
     """Queues the FP32 FMA probe; returns the lane FMAs it issues."""
     out = ctypes.c_double()
-    _check(load().fofse_probe_fma(int(ctas), int(rounds), _ptr(sink), ctypes.byref(out),
+    _check(load_probes().fofse_probe_fma(int(ctas), int(rounds), _ptr(sink), ctypes.byref(out),
                                   _stream(stream)), "fofse_probe_fma")
     return out.value
 
@@ -417,7 +431,7 @@ def fofse_probe_dfma(ctas, rounds, sink, *, stream=None) -> float:
     """Queues the FP64 FMA probe (sink: ctas x 1024 float64); returns the lane
     FMAs it issues."""
     out = ctypes.c_double()
-    _check(load().fofse_probe_dfma(int(ctas), int(rounds), _ptr(sink), ctypes.byref(out),
+    _check(load_probes().fofse_probe_dfma(int(ctas), int(rounds), _ptr(sink), ctypes.byref(out),
                                    _stream(stream)), "fofse_probe_dfma")
     return out.value
 

@@ -1,7 +1,10 @@
-"""Builds the CUDA library ``libfofse.so`` for sm_103a (in-tree, into ``_build/``).
+"""Builds the CUDA libraries for sm_103a (in-tree, into ``_build/``):
+``libfofse.so``, the product, exporting the C ABI of ``include/fofse.h``, and
+``libfofse_probes.so``, the measurement probes of ``include/fofse_probes.h``
+that the benchmark uses (no part of the method).
 
 Each translation unit is compiled by its own nvcc process (in parallel), then
-linked into one shared library that exports the C ABI of ``include/fofse.h``.
+linked into its library.
 """
 from __future__ import annotations
 
@@ -14,8 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfofse.so")
+PROBES_LIB = os.path.join(BUILD, "libfofse_probes.so")
 SOURCES = ["fofse_api.cu", "fofse_fwd.cu", "fofse_fwd3.cu", "fofse_ofse.cu", "fofse_bwd.cu",
-           "fofse_curve.cu", "fofse_probe.cu", "fofse_dct.cu", "fofse_volume.cu"]
+           "fofse_curve.cu", "fofse_dct.cu", "fofse_volume.cu"]
+PROBE_SOURCES = ["fofse_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 
@@ -28,14 +33,15 @@ def nvcc() -> str:
 
 
 def _deps():
+    inc = os.path.join(HERE, "..", "include")
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
-        os.path.join(HERE, "..", "include", "fofse.h"), __file__]
+        os.path.join(inc, f) for f in os.listdir(inc)] + [__file__]
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(PROBES_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBES_LIB))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -56,13 +62,18 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
-    r = subprocess.run([exe, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + len(PROBE_SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES + PROBE_SOURCES))
+
+    def link(lib, parts):
+        tmp = lib + f".{os.getpid()}.tmp"
+        r = subprocess.run([exe, *ARCH, "-shared", "-o", tmp, *parts], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link of {os.path.basename(lib)} failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
+
+    link(LIB, objs[:len(SOURCES)])
+    link(PROBES_LIB, objs[len(SOURCES):])
     return LIB
 
 

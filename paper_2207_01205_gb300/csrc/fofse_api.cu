@@ -402,8 +402,7 @@ fofse_status fofse_plan_set_basis(fofse_plan plan, int basis) {
 
 fofse_status fofse_plan_set_precision(fofse_plan plan, int precision) {
   if (!plan || (precision != FOFSE_FP32 && precision != FOFSE_FP64_VALIDATE &&
-                precision != FOFSE_FP32_PLAIN && precision != FOFSE_FP32_FULLFF &&
-                precision != FOFSE_FP32_FILTERED))
+                precision != FOFSE_FP32_FULLFF))
     return FOFSE_E_ARG;
   plan->dev.precision = precision;
   if (plan->dev.variant >= forward_variant_count(plan->dev)) plan->dev.variant = 0;

@@ -7,7 +7,8 @@
 //             plain FP32 diverge from the exact path, so this is the product's
 //             arithmetic.
 //  * ArF64 -- IEEE double, for the FP64 validation mode.
-//  * ArF32 -- plain FP32 (fast, diverges at near-ties; kept for comparison).
+//  * ArF32 -- plain FP32, the arithmetic of the frozen-path backward (linear
+//             along the path: no decision to keep exact).
 //
 // The error-free transformations are Knuth's TwoSum, Dekker's FastTwoSum and
 // the FMA-based TwoProduct; intrinsics with explicit rounding (__fadd_rn ...)

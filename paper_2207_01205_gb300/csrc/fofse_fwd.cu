@@ -19,7 +19,7 @@
 //
 // Shared-memory spectrum layout: T rows of 2T elements of type A::E; element
 // (k1, k2) has part 0 at k1*2T + k2 and part 1 at k1*2T + T + k2 (float-float:
-// hi plane / lo plane; FP64 and plain FP32: real / imaginary plane).  With
+// hi plane / lo plane; FP64: real / imaginary plane).  With
 // that stride the cyclic shifts k -+ u of a bin stored as x_k = k1*2T + k2
 // are one add and one AND: ((x_k + T - y_u) & M) and ((x_k + y_u) & M),
 // M = (T-1)*2T + (T-1).
@@ -43,20 +43,11 @@ template <> struct Cand<ArF64> {
   int code;
   double re, im;
 };
-template <> struct Cand<ArF32> {
-  float m;
-  int code;
-  float re, im;
-};
-
 __device__ __forceinline__ Cand<ArFF> make_cand(const ArFF::C& r, int code) {
   return {__fmaf_rn(r.re.h, r.re.h, __fmul_rn(r.im.h, r.im.h)), code, r.re, r.im};
 }
 __device__ __forceinline__ Cand<ArF64> make_cand(const ArF64::C& r, int code) {
   return {__dadd_rn(__dmul_rn(r.re, r.re), __dmul_rn(r.im, r.im)), code, r.re, r.im};
-}
-__device__ __forceinline__ Cand<ArF32> make_cand(const ArF32::C& r, int code) {
-  return {__fadd_rn(__fmul_rn(r.re, r.re), __fmul_rn(r.im, r.im)), code, r.re, r.im};
 }
 template <class A> __device__ __forceinline__ Cand<A> empty_cand() {
   Cand<A> c;
@@ -84,10 +75,6 @@ __device__ __forceinline__ bool better(const Cand<ArFF>& a, const Cand<ArFF>& b)
 __device__ __forceinline__ bool better(const Cand<ArF64>& a, const Cand<ArF64>& b) {
   return a.m > b.m || (a.m == b.m && a.code < b.code);
 }
-__device__ __forceinline__ bool better(const Cand<ArF32>& a, const Cand<ArF32>& b) {
-  return a.m > b.m || (a.m == b.m && a.code < b.code);
-}
-
 __device__ __forceinline__ Cand<ArFF> shfl(const Cand<ArFF>& c, int off) {
   Cand<ArFF> o;
   o.m = __shfl_xor_sync(0xffffffffu, c.m, off);
@@ -106,15 +93,6 @@ __device__ __forceinline__ Cand<ArF64> shfl(const Cand<ArF64>& c, int off) {
   o.im = __shfl_xor_sync(0xffffffffu, c.im, off);
   return o;
 }
-__device__ __forceinline__ Cand<ArF32> shfl(const Cand<ArF32>& c, int off) {
-  Cand<ArF32> o;
-  o.m = __shfl_xor_sync(0xffffffffu, c.m, off);
-  o.code = __shfl_xor_sync(0xffffffffu, c.code, off);
-  o.re = __shfl_xor_sync(0xffffffffu, c.re, off);
-  o.im = __shfl_xor_sync(0xffffffffu, c.im, off);
-  return o;
-}
-
 // Warp-wide argmax; every lane returns the winner.  Exact compare for the
 // FP64 / plain FP32 back-ends.  For float-float, the FP32 estimates are
 // reduced first; only if another lane's estimate lies within the near margin
@@ -163,9 +141,6 @@ template <int NW, class A> __device__ __forceinline__ Cand<A> block_argmax_gener
 template <int NW> __device__ __forceinline__ Cand<ArF64> block_argmax(const Cand<ArF64>* sl) {
   return block_argmax_generic<NW>(sl);
 }
-template <int NW> __device__ __forceinline__ Cand<ArF32> block_argmax(const Cand<ArF32>* sl) {
-  return block_argmax_generic<NW>(sl);
-}
 template <int NW> __device__ __forceinline__ Cand<ArFF> block_argmax(const Cand<ArFF>* sl) {
   float M = sl[0].m;
   int wi = 0;
@@ -203,10 +178,6 @@ __device__ __forceinline__ ArFF::C coef(const Cand<ArFF>& w, ff inv, bool sc) {
 __device__ __forceinline__ ArF64::C coef(const Cand<ArF64>& w, double inv, bool sc) {
   return {w.re * inv, sc ? 0.0 : w.im * inv};
 }
-__device__ __forceinline__ ArF32::C coef(const Cand<ArF32>& w, float inv, bool sc) {
-  return {w.re * inv, sc ? 0.f : w.im * inv};
-}
-
 // R -= c Wm + conj(c) Wp, written as
 //   Re: p (Wm.re + Wp.re) - q (Wm.im - Wp.im),  Im: p (Wm.im + Wp.im) + q (Wm.re - Wp.re)
 __device__ __forceinline__ void update_pair(ArFF::C& R, const ArFF::C& c, const ArFF::C& Wm,
@@ -632,495 +603,6 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_kernel(const __grid_co
   }
 }
 
-// ===========================================================================
-// Filtered-exact forward, second layout: the exact W (float-float, both
-// planes), the exact initial spectrum R0 and the FFT live in a per-CTA slot of
-// L2-resident global scratch; shared memory holds only the FP32 (hi) plane of
-// W for the working-spectrum updates (32 KB at T = 64), so more blocks are
-// resident per SM.  Four warps per block at T = 64 (16 bins per thread) keep
-// the per-iteration reductions small next to the bin work.
-// ===========================================================================
-template <int T, bool HALF> struct WHi;
-template <int T> struct WHi<T, false> {  // full T x T hi plane, row-major
-  static constexpr int LOGT = ilog2(T);
-  static constexpr size_t elems = (size_t)T * T;
-  __device__ __forceinline__ static float2 get(const float2* W, int a) {  // a = a1*2T + a2
-    return W[((a >> (LOGT + 1)) << LOGT) | (a & (T - 1))];
-  }
-};
-template <int T> struct WHi<T, true> {  // Hermitian half, rows of T/2 + 1
-  static constexpr int LOGT = ilog2(T), HO = T / 2 + 1;
-  static constexpr size_t elems = (size_t)T * HO;
-  __device__ __forceinline__ static float2 get(const float2* W, int a) {
-    const int a1 = a >> (LOGT + 1), a2 = a & (T - 1);
-    const bool mir = a2 > T / 2;
-    const int r = mir ? ((T - a1) & (T - 1)) : a1;
-    const int c = mir ? (T - a2) : a2;
-    const float2 v = W[r * HO + c];
-    return mir ? make_float2(v.x, -v.y) : v;
-  }
-};
-
-template <int T, int NT, bool HALF> struct F2Layout {
-  static constexpr int NW = NT / 32, NSLOT = T * T / 2, LIST = 64;
-  static constexpr size_t whi_bytes = sizeof(float2) * WHi<T, HALF>::elems;
-  static constexpr size_t tw_off = (whi_bytes + 15) & ~size_t(15);
-  static constexpr size_t t2_off = tw_off + sizeof(ArFF::C) * (T / 2);
-  static constexpr size_t red_off = t2_off + sizeof(Top2) * 2 * NW;
-  static constexpr size_t wtot_off = red_off + sizeof(float4) * NW;
-  static constexpr size_t list_off = (wtot_off + sizeof(int) * NW + 15) & ~size_t(15);
-  static constexpr size_t ww_off = list_off + sizeof(int2) * LIST;
-  static constexpr size_t ex_off = ww_off + (sizeof(float4) + sizeof(int2)) * NW;
-  static constexpr size_t try_off = (ex_off + 2 * sizeof(float2) + 15) & ~size_t(15);
-  __host__ __device__ static size_t trc_off(int iters) {
-    return try_off + sizeof(int) * (((size_t)iters + 3) & ~size_t(3));
-  }
-  __host__ __device__ static size_t bytes(int iters) {
-    return 128 + trc_off(iters) + sizeof(float4) * (size_t)iters;
-  }
-  static constexpr size_t z_bytes = sizeof(float2) * (size_t)T * 2 * T;  // FFT, then exact W
-  static constexpr size_t scratch_bytes = z_bytes + sizeof(float4) * (size_t)(NSLOT + 2);
-};
-
-// FP32 update of one working bin from the shared hi plane
-template <class WH>
-__device__ __forceinline__ void upd_hi(float2& R, float p, float q, const float2* Whi, int x, int y,
-                                       bool pair, int M, int T) {
-  const float2 Wm = WH::get(Whi, (x + T - y) & M);
-  float br = 0.f, bi = 0.f;
-  if (pair) {
-    const float2 Wp = WH::get(Whi, (x + y) & M);
-    br = Wp.x;
-    bi = Wp.y;
-  }
-  R.x -= __fmaf_rn(p, Wm.x + br, -(q * (Wm.y - bi)));
-  R.y -= __fmaf_rn(p, Wm.y + bi, q * (Wm.x - br));
-}
-
-// Sum of the NW warp partials (red4), float-float, returned to every lane.
-template <int NW> __device__ __forceinline__ ffc block_partials_sum(const float4* red4, int lane) {
-  ffc v = {{0.f, 0.f}, {0.f, 0.f}};
-  if (lane < NW) {
-    const float4 r = red4[lane];
-    v = {{r.x, r.y}, {r.z, r.w}};
-  }
-#pragma unroll
-  for (int o = NW / 2; o > 0; o >>= 1) v = ffc_add(v, ffc_shfl(v, o));
-  return {{__shfl_sync(0xffffffffu, v.re.h, 0), __shfl_sync(0xffffffffu, v.re.l, 0)},
-          {__shfl_sync(0xffffffffu, v.im.h, 0), __shfl_sync(0xffffffffu, v.im.l, 0)}};
-}
-
-template <int T, int NT, bool HALF>
-__device__ __forceinline__ void forward_block_f2(const FwdArgs& args, const CUtensorMap* tmF,
-                                                 const CUtensorMap* tmA, int blk, unsigned char* smem,
-                                                 uint64_t* mbar, unsigned& tma_phase,
-                                                 unsigned char* cta_scratch) {
-  using A = ArFF;
-  using C = ArFF::C;
-  using IO = PlanIO<A>;
-  using L = F2Layout<T, NT, HALF>;
-  using WG = WTab<A, T, false>;  // exact W, full grid, in global scratch
-  using WH = WHi<T, HALF>;
-  constexpr int T2 = 2 * T, LOGT = ilog2(T), NSLOT = T * T / 2;
-  constexpr int NB = NSLOT / NT, NW = NT / 32, LIST = L::LIST;
-  constexpr int M = (T - 1) * 2 * T + (T - 1);
-  static_assert(NSLOT % NT == 0 && NW >= 2 && (NW & (NW - 1)) == 0, "slot grid");
-  constexpr float kU = 5.9604644775390625e-08f;  // 2^-24
-  constexpr float kUp = 1.f + 4.f * kU, kDn = 1.f - 4.f * kU;
-
-  float2* Whi = reinterpret_cast<float2*>(smem);
-  C* tw = reinterpret_cast<C*>(smem + L::tw_off);
-  Top2* t2s = reinterpret_cast<Top2*>(smem + L::t2_off);
-  float4* red4 = reinterpret_cast<float4*>(smem + L::red_off);
-  int* wtot = reinterpret_cast<int*>(smem + L::wtot_off);
-  int2* list = reinterpret_cast<int2*>(smem + L::list_off);
-  float4* wwv = reinterpret_cast<float4*>(smem + L::ww_off);
-  int2* wwc = reinterpret_cast<int2*>(smem + L::ww_off + sizeof(float4) * NW);
-  float2* ex32 = reinterpret_cast<float2*>(smem + L::ex_off);
-  const PlanDev& P = args.plan;
-  const int iters = P.iters;
-  int* trY = reinterpret_cast<int*>(smem + L::try_off);
-  float4* trC = reinterpret_cast<float4*>(smem + L::trc_off(iters));
-  float2* Zg = reinterpret_cast<float2*>(cta_scratch);
-  float4* Rx = reinterpret_cast<float4*>(cta_scratch + L::z_bytes);
-
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const fofse_block bd = args.blocks[blk];
-  const int b = P.block, br = P.border, Ls = P.Ls;
-  const int ly0 = bd.y - br, lx0 = bd.x - br;
-
-  // ---- 1. stage the support tile into shared memory (TMA) -------------------
-  float* stF = reinterpret_cast<float*>(smem);
-  const int bytesF = args.box_f * Ls * 4;
-  uint8_t* stA = smem + ((bytesF + 127) & ~127);
-  const int fx0 = lx0 & ~3, fo = lx0 - fx0;
-  const int ax0 = lx0 & ~15, ao = lx0 - ax0;
-  if (args.use_tma) {
-    if (tid == 0) {
-      fence_proxy_async();
-      mbar_expect_tx(mbar, (unsigned)(bytesF + args.box_a * Ls));
-      tma_load_2d(stF, tmF, fx0, ly0, mbar);
-      tma_load_2d(stA, tmA, ax0, ly0, mbar);
-    }
-    bool done = false;
-    for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mbar, tma_phase);
-    if (!done) {
-      atomicOr(args.err, kErrTimeout);
-      for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mbar, tma_phase);
-    }
-    tma_phase ^= 1u;
-    if (!__syncthreads_and(done)) {
-      if (tid == 0 && args.status) args.status[blk] = kBlkTimeout;
-      return;
-    }
-  }
-
-  // ---- 2. z = w f + j w at bit-reversed positions of the global FFT buffer --
-  bool bad = false;
-  for (int e = tid; e < T * T; e += NT) {
-    const int r = e >> LOGT, cc = e & (T - 1);
-    const int m = __brev(r) >> (32 - LOGT), n = __brev(cc) >> (32 - LOGT);
-    C z = A::zero();
-    if (m < Ls && n < Ls) {
-      const bool inB = m >= br && m < br + b && n >= br && n < br + b;
-      bool inS = true;
-      if (P.support == FOFSE_SUPPORT_CAUSAL_L)
-        inS = (m < br) ? (n < br + b) : (m < br + b ? n < br : false);
-      int av;
-      float f;
-      if (args.use_tma) {
-        av = stA[m * args.box_a + ao + n];
-        f = stF[m * args.box_f + fo + n];
-      } else {
-        const int fy = ly0 + m, fx = lx0 + n;
-        const bool in = fy >= 0 && fy < args.height && fx >= 0 && fx < args.width;
-        av = in ? args.avail[(size_t)fy * args.pitch + fx] : 0;
-        f = in ? args.frame[(size_t)fy * args.pitch + fx] : 0.f;
-      }
-      if (av && !inB && inS) {
-        bad |= !isfinite(f);
-        C wd;
-        z = IO::weighted(P.tab, m * Ls + n, f, wd);
-      }
-    }
-    A::store(Zg, r * T2 + cc, T, z);
-  }
-  for (int e = tid; e < T / 2; e += NT) tw[e] = IO::twiddle(P.tab, e);
-  int any_bad = __syncthreads_or(bad);
-
-  // ---- 3. FFT (float-float) in the global buffer ------------------------------
-  fft2d_dit<A, T, NT, false>(Zg, tw, Ls, T);
-
-  // ---- split: exact R0 -> scratch, FP32 copy -> registers --------------------
-  float2 R32[NB];
-  int kc[NB];
-  Top2 loc = {-1.f, 0x7fffffff, -1, -1.f};
-#pragma unroll
-  for (int i = 0; i <= NB; ++i) {
-    if (i == NB && tid >= 2) break;
-    const int slot = i < NB ? tid + i * NT : NSLOT + tid;
-    const int x = i < NB ? slot_xk<T>(slot) : extra_xk<T>(tid);
-    const int k1 = x >> (LOGT + 1), k2 = x & (T2 - 1);
-    const int mx = ((T - k1) & (T - 1)) * T2 + ((T - k2) & (T - 1));
-    const C a = A::load(Zg, x, T), mm = A::load(Zg, mx, T);
-    const C r = A::half(A::add(a, A::conj(mm)));
-    if (!A::finite(r)) bad = true;
-    Rx[slot] = make_float4(r.re.h, r.re.l, r.im.h, r.im.l);
-    const float2 r32 = make_float2(r.re.h, r.im.h);
-    const int code = code_of<T>(x);
-    if (i < NB) {
-      kc[i] = x | (code << 16);
-      R32[i] = r32;
-    } else {
-      ex32[tid] = r32;
-    }
-    top2_insert(loc, m32(r32), code, slot);
-  }
-  any_bad |= __syncthreads_or(bad);
-  build_wtab<A, T, NT, false>(Zg, nullptr);  // exact W in place (global)
-  __syncthreads();
-  if constexpr (!HALF) {
-    for (int e = tid; e < T * T; e += NT) Whi[e] = Zg[(e >> LOGT) * T2 + (e & (T - 1))];
-  } else {
-    constexpr int HO = T / 2 + 1;
-    for (int e = tid; e < T * HO; e += NT) {
-      const int k1 = e / HO, k2 = e - k1 * HO;
-      Whi[e] = Zg[k1 * T2 + k2];
-    }
-  }
-  __syncthreads();
-  const C W0c = A::load(Zg, 0, T);
-  int st = FOFSE_BLK_OK;
-  if (IO::w0_zero(W0c)) st = FOFSE_BLK_NO_SUPPORT;
-  else if (any_bad || !IO::w0_finite(W0c)) st = FOFSE_BLK_NONFINITE;
-
-  if (st == FOFSE_BLK_OK) {
-    const ff inv = IO::inv_w0(IO::gamma(P), W0c.re);
-    const float W0f = W0c.re.h * (1.f + 1e-6f);
-    float bnd = 0.f, prevabs = 0.f;
-#pragma unroll 1
-    for (int it = 0; it < iters; ++it) {
-      // ---- FP32 top-2 over the block ----
-      Top2 t = loc;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) top2_merge(t, top2_shfl(t, o));
-      Top2* ts = t2s + (it & 1) * NW;
-      if (lane == 0) ts[warp] = t;
-      __syncthreads();
-      Top2 g = ts[0];
-#pragma unroll
-      for (int w = 1; w < NW; ++w) top2_merge(g, ts[w]);
-      const float sM1 = sqrtf(fmaxf(g.m1, 0.f)), sM2 = sqrtf(fmaxf(g.m2, 0.f));
-      bnd += 1.01f * kU * sM1 + 16.f * kU * W0f * prevabs;
-      const bool certain = (sM1 * kDn - bnd * kUp) > (sM2 * kUp + bnd * kUp) ||
-                           (bnd == 0.f && g.m1 == 0.f);
-      int wcode, wslot;
-      ffc Rt;
-      if (certain) {
-        wcode = g.c1;
-        wslot = g.s1;
-        const int canon = wcode >> 1;
-        const int w1 = canon >> LOGT, w2 = canon & (T - 1);
-        const int x = (wcode & 1) ? (((T - w1) & (T - 1)) * T2 + ((T - w2) & (T - 1))) : (w1 * T2 + w2);
-        const float4 r0 = Rx[wslot];
-        ffc part = recur_partial<WG, T>(Zg, trY, trC, x, tid, it, NT);
-        part = ffc_warp_sum(part);
-        float4* rb = red4;  // one buffer: read below before the next write (barriers in between)
-        if (lane == 0) rb[warp] = make_float4(part.re.h, part.re.l, part.im.h, part.im.l);
-        __syncthreads();
-        const ffc S = block_partials_sum<NW>(rb, lane);
-        Rt = {ff_sub(ff{r0.x, r0.y}, S.re), ff_sub(ff{r0.z, r0.w}, S.im)};
-      } else {
-        // ---- near-tie: exact values of every bin within the band ----
-        const float Lb = (sM1 * kDn - 2.f * bnd * kUp) / kUp;
-        const float thr = Lb > 0.f ? Lb * Lb * kDn : -1.f;
-        int cnt = 0;
-#pragma unroll
-        for (int i = 0; i < NB; ++i) cnt += m32(R32[i]) >= thr ? 1 : 0;
-        if (tid < 2) cnt += m32(ex32[tid]) >= thr ? 1 : 0;
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += v;
-        }
-        if (lane == 31) wtot[warp] = incl;
-        __syncthreads();
-        int before = 0, total = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const int v = wtot[w];
-          before += w < warp ? v : 0;
-          total += v;
-        }
-        const int rank0 = before + incl - cnt;
-        ffc wb = {{0.f, 0.f}, {0.f, 0.f}};
-        int wbc = 0x7fffffff, wbs = -1;
-        for (int pass = 0; pass < total; pass += LIST) {
-          int r = rank0;
-#pragma unroll
-          for (int i = 0; i < NB; ++i) {
-            if (m32(R32[i]) >= thr) {
-              if (r >= pass && r < pass + LIST) list[r - pass] = make_int2(kc[i], tid + i * NT);
-              ++r;
-            }
-          }
-          if (tid < 2 && m32(ex32[tid]) >= thr && r >= pass && r < pass + LIST) {
-            const int x = extra_xk<T>(tid);
-            list[r - pass] = make_int2(x | (code_of<T>(x) << 16), NSLOT + tid);
-          }
-          __syncthreads();
-          const int n = min(LIST, total - pass);
-          for (int c = warp; c < n; c += NW) {
-            const int2 e = list[c];
-            const float4 r0 = Rx[e.y];
-            ffc part = recur_partial<WG, T>(Zg, trY, trC, e.x & 0xffff, lane, it, 32);
-            part = ffc_warp_sum(part);
-            const ffc v = {ff_sub(ff{r0.x, r0.y}, part.re), ff_sub(ff{r0.z, r0.w}, part.im)};
-            const int code = e.x >> 16;
-            if (wbc == 0x7fffffff || exact_better(v, code, wb, wbc)) {
-              wb = v;
-              wbc = code;
-              wbs = e.y;
-            }
-          }
-          __syncthreads();
-        }
-        if (lane == 0) {
-          wwv[warp] = make_float4(wb.re.h, wb.re.l, wb.im.h, wb.im.l);
-          wwc[warp] = make_int2(wbc, wbs);
-        }
-        __syncthreads();
-        wcode = 0x7fffffff;
-        wslot = -1;
-        Rt = {{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const int2 cs = wwc[w];
-          if (cs.x == 0x7fffffff) continue;
-          const float4 v4 = wwv[w];
-          const ffc v = {{v4.x, v4.y}, {v4.z, v4.w}};
-          if (wcode == 0x7fffffff || exact_better(v, cs.x, Rt, wcode)) {
-            Rt = v;
-            wcode = cs.x;
-            wslot = cs.y;
-          }
-        }
-      }
-      // ---- exact coefficient (Eq. 5, Eq. 14) ----
-      const int canon = wcode >> 1;
-      const bool mir = wcode & 1;
-      const int u1 = canon >> LOGT, u2 = canon & (T - 1);
-      const int s1 = mir ? ((T - u1) & (T - 1)) : u1;
-      const int s2 = mir ? ((T - u2) & (T - 1)) : u2;
-      const bool sc = ((s1 & (T / 2 - 1)) == 0) && ((s2 & (T / 2 - 1)) == 0);
-      C c;
-      c.re = ff_mul(Rt.re, inv);
-      c.im = sc ? ff{0.f, 0.f} : ff_mul(Rt.im, inv);
-      if (tid == 0) {
-        trY[it] = u1 * T2 + u2;
-        trC[it] = mir ? make_float4(c.re.h, c.re.l, -c.im.h, -c.im.l)
-                      : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
-      }
-      // ---- FP32 update of the working spectrum + next local top-2 ----
-      const float p = c.re.h, q = c.im.h;
-      prevabs = fabsf(p) + fabsf(q);
-      const int y = s1 * T2 + s2;
-      loc = {-1.f, 0x7fffffff, -1, -1.f};
-#pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        upd_hi<WH>(R32[i], p, q, Whi, kc[i] & 0xffff, y, !sc, M, T);
-        top2_insert(loc, m32(R32[i]), kc[i] >> 16, tid + i * NT);
-      }
-      if (tid < 2) {
-        const int x = extra_xk<T>(tid);
-        float2 r = ex32[tid];
-        upd_hi<WH>(r, p, q, Whi, x, y, !sc, M, T);
-        ex32[tid] = r;
-        top2_insert(loc, m32(r), code_of<T>(x), NSLOT + tid);
-      }
-    }
-  }
-  __syncthreads();
-
-  // ---- synthesis of B (Eq. 1) from the exact coefficients; outputs ----------
-  const int nIt = (st == FOFSE_BLK_OK) ? iters : 0;
-  const int ld = args.out_ld;
-  const float2* syn = P.tab.syn_f32;
-  for (int pidx = tid; pidx < ld * ld; pidx += NT) {
-    const int bm = pidx / ld, bn = pidx - bm * ld;
-    float v = 0.f;
-    if (bm < b && bn < b) {
-      const int m = br + bm, n = br + bn;
-      float acc = 0.f;
-      for (int i = 0; i < nIt; ++i) {
-        const int yy = trY[i];
-        const int a1 = yy >> (LOGT + 1), a2 = yy & (T2 - 1);
-        const float4 c4 = trC[i];
-        const float mult = (((a1 & (T / 2 - 1)) == 0) && ((a2 & (T / 2 - 1)) == 0)) ? 1.f : 2.f;
-        const float2 cs = __ldg(&syn[(a1 * m + a2 * n) & (T - 1)]);
-        acc += mult * (c4.x * cs.x - c4.z * cs.y);
-      }
-      v = acc;
-      if (args.out_frame) {
-        const int fy = bd.y + bm, fx = bd.x + bn;
-        if (fy >= 0 && fy < args.height && fx >= 0 && fx < args.width)
-          args.out_frame[(size_t)fy * args.pitch + fx] = v;
-      }
-    }
-    if (args.out_blocks) args.out_blocks[(size_t)blk * args.out_stride + pidx] = v;
-  }
-  if (args.trace) {
-    for (int i = tid; i < args.trace_stride; i += NT) {
-      fofse_trace_entry e;
-      if (i < nIt) {
-        const int yy = trY[i];
-        const float4 c4 = trC[i];
-        e.u1 = (int16_t)(yy >> (LOGT + 1));
-        e.u2 = (int16_t)(yy & (T2 - 1));
-        e.dc_re = c4.x;
-        e.dc_im = c4.z;
-      } else {
-        e.u1 = e.u2 = 0;
-        e.dc_re = e.dc_im = 0.f;
-      }
-      args.trace[(size_t)blk * args.trace_stride + i] = e;
-    }
-  }
-  if (tid == 0) {
-    if (args.w0) args.w0[blk] = st == FOFSE_BLK_OK ? W0c.re.h + W0c.re.l : 0.f;
-    if (args.status) args.status[blk] = st;
-  }
-  __syncthreads();
-}
-
-template <int T, int NT, int MINB, bool HALF>
-__global__ void __launch_bounds__(NT, MINB) fofse_forward_f2_kernel(const __grid_constant__ FwdArgs args,
-                                                              const __grid_constant__ CUtensorMap tmF,
-                                                              const __grid_constant__ CUtensorMap tmA) {
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  __shared__ uint64_t mbar;
-  __shared__ int s_item;
-  unsigned tma_phase = 0;
-  if (args.use_tma) {
-    if (threadIdx.x == 0) {
-      mbar_init(&mbar, 1);
-      fence_mbar_init();
-    }
-    __syncthreads();
-  }
-  unsigned char* cta_scratch = static_cast<unsigned char*>(args.scratch) +
-                               (size_t)blockIdx.x * F2Layout<T, NT, HALF>::scratch_bytes;
-  int next = blockIdx.x;
-  for (;;) {
-    int item;
-    if (args.queue) {
-      if (threadIdx.x == 0) s_item = atomicAdd(args.queue, 1);
-      __syncthreads();
-      item = s_item;
-      __syncthreads();
-    } else {
-      item = next;
-      next += gridDim.x;
-    }
-    if (item >= args.n_blocks) break;
-    if (args.blocks[item].plan != args.plan_index) continue;
-    forward_block_f2<T, NT, HALF>(args, &tmF, &tmA, item, smem, &mbar, tma_phase, cta_scratch);
-  }
-}
-
-template <int T, int NT, int MINB, bool HALF> struct VariantF2 {
-  static constexpr size_t per_cta = F2Layout<T, NT, HALF>::scratch_bytes;
-  static cudaError_t prepare(int iters, size_t* smem, int* max_ctas) {
-    *smem = F2Layout<T, NT, HALF>::bytes(iters);
-    return prepare_kernel(fofse_forward_f2_kernel<T, NT, MINB, HALF>, NT, *smem, max_ctas);
-  }
-  static cudaError_t scratch(int iters, size_t* bytes) {
-    size_t sm;
-    int ctas;
-    cudaError_t e = prepare(iters, &sm, &ctas);
-    *bytes = e == cudaSuccess ? per_cta * (size_t)ctas : 0;
-    return e;
-  }
-  static cudaError_t launch(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
-                            cudaStream_t s) {
-    size_t sm;
-    int grid;
-    cudaError_t e = prepare(a.plan.iters, &sm, &grid);
-    if (e != cudaSuccess) return e;
-    const size_t fit = a.scratch ? a.scratch_bytes / per_cta : 0;
-    if (fit < 1) return cudaErrorInvalidValue;
-    if ((size_t)grid > fit) grid = (int)fit;
-    if (grid > a.n_blocks) grid = a.n_blocks;
-    if (grid < 1) return cudaSuccess;
-    fofse_forward_f2_kernel<T, NT, MINB, HALF><<<grid, NT, sm, s>>>(a, *tf, *ta);
-    return cudaGetLastError();
-  }
-};
-
 template <class A, int T, int NT, int MINB, bool HALF> struct Variant {
   static constexpr size_t per_cta = FwdLayout<A, T, NT, HALF>::scratch_bytes;
   static cudaError_t prepare(int iters, size_t* smem, int* max_ctas) {
@@ -1152,89 +634,49 @@ template <class A, int T, int NT, int MINB, bool HALF> struct Variant {
   }
 };
 
-// Kernel choice per (precision, T).  FOFSE_FP32 runs the filtered-exact variant
-// when scratch is available and the all-bins float-float variant otherwise.
+// Kernel choice per (precision, T).  FOFSE_FP32 runs the register-blocked
+// filtered-exact kernel (fofse_fwd3.cu) when the workspace's scratch is given,
+// and this all-bins float-float kernel otherwise (also FOFSE_FP32_FULLFF);
+// FOFSE_FP64_VALIDATE runs it in IEEE double.
 template <int T> struct Pick;
-// Launch shapes of the product (filtered) kernel: threads per block and the
-// minimum resident blocks per SM the register allocation is held to.  The
-// autotuner picks one per plan (fofse_plan_set_variant); variant 0 is the default.
 template <> struct Pick<32> {
   using FF = Variant<ArFF, 32, 128, 6, false>;
   using F64 = Variant<ArF64, 32, 128, 1, false>;
-  using F32 = Variant<ArF32, 32, 128, 6, false>;
-  using V0 = VariantF2<32, 64, 8, false>;
-  using V1 = VariantF2<32, 128, 6, false>;
-  using V2 = VariantF2<32, 64, 12, false>;
-  static constexpr int NV = 3;
 };
 template <> struct Pick<64> {
   using FF = Variant<ArFF, 64, 256, 3, false>;
   using F64 = Variant<ArF64, 64, 256, 1, false>;
-  using F32 = Variant<ArF32, 64, 256, 3, false>;
-  using V0 = VariantF2<64, 128, 5, false>;
-  using V1 = VariantF2<64, 256, 3, false>;
-  using V2 = VariantF2<64, 64, 6, false>;
-  static constexpr int NV = 3;
 };
 template <> struct Pick<128> {
   using FF = Variant<ArFF, 128, 512, 1, true>;
   using F64 = Variant<ArF64, 128, 512, 1, true>;
-  using F32 = Variant<ArF32, 128, 512, 1, true>;
-  using V0 = VariantF2<128, 512, 1, true>;
-  using V1 = VariantF2<128, 512, 1, true>;
-  using V2 = VariantF2<128, 512, 1, true>;
-  static constexpr int NV = 1;
 };
-
-template <int T>
-cudaError_t launch_filtered(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta,
-                            cudaStream_t s) {
-  using Pk = Pick<T>;
-  switch (a.plan.variant) {
-    case 1: if (a.scratch_bytes >= Pk::V1::per_cta) return Pk::V1::launch(a, tf, ta, s); break;
-    case 2: if (a.scratch_bytes >= Pk::V2::per_cta) return Pk::V2::launch(a, tf, ta, s); break;
-    default: if (a.scratch_bytes >= Pk::V0::per_cta) return Pk::V0::launch(a, tf, ta, s); break;
-  }
-  return Pk::FF::launch(a, tf, ta, s);
-}
 
 template <int T>
 cudaError_t launch_T(const FwdArgs& a, const CUtensorMap* tf, const CUtensorMap* ta, cudaStream_t s) {
   using Pk = Pick<T>;
   switch (a.plan.precision) {
     case FOFSE_FP64_VALIDATE: return Pk::F64::launch(a, tf, ta, s);
-    case FOFSE_FP32_PLAIN: return Pk::F32::launch(a, tf, ta, s);
     case FOFSE_FP32_FULLFF: return Pk::FF::launch(a, tf, ta, s);
-    case FOFSE_FP32_FILTERED:
-      if (!a.scratch) return Pk::FF::launch(a, tf, ta, s);
-      return launch_filtered<T>(a, tf, ta, s);
     default:  // FOFSE_FP32
       if (!a.scratch || a.scratch_bytes < forward_f3_scratch_bytes(a.plan))
         return Pk::FF::launch(a, tf, ta, s);
       return launch_forward_f3(a, tf, ta, s);
   }
 }
-// Scratch for whichever variant the plan may select (the largest of them).
+// Scratch of the plan's kernel (for FOFSE_FP32, the largest launch shape).
 template <int T> cudaError_t scratch_T(const PlanDev& p, size_t* bytes) {
   using Pk = Pick<T>;
   switch (p.precision) {
     case FOFSE_FP64_VALIDATE: return Pk::F64::scratch(p.iters, bytes);
-    case FOFSE_FP32_PLAIN: return Pk::F32::scratch(p.iters, bytes);
     case FOFSE_FP32_FULLFF: return Pk::FF::scratch(p.iters, bytes);
-    case FOFSE_FP32: *bytes = forward_f3_scratch_bytes(p); return *bytes ? cudaSuccess : cudaErrorInvalidValue;
-    default: {
-      size_t b0 = 0, b1 = 0, b2 = 0;
-      cudaError_t e = Pk::V0::scratch(p.iters, &b0);
-      if (e == cudaSuccess && Pk::NV > 1) e = Pk::V1::scratch(p.iters, &b1);
-      if (e == cudaSuccess && Pk::NV > 2) e = Pk::V2::scratch(p.iters, &b2);
-      *bytes = b0 > b1 ? (b0 > b2 ? b0 : b2) : (b1 > b2 ? b1 : b2);
-      return e;
-    }
+    default:
+      *bytes = forward_f3_scratch_bytes(p);
+      return *bytes ? cudaSuccess : cudaErrorInvalidValue;
   }
 }
 template <int T> int variants_T(const PlanDev& p) {
-  if (p.precision == FOFSE_FP32) return forward_f3_variant_count(p);
-  return p.precision == FOFSE_FP32_FILTERED ? Pick<T>::NV : 1;
+  return p.precision == FOFSE_FP32 ? forward_f3_variant_count(p) : 1;
 }
 
 }  // namespace

@@ -80,31 +80,6 @@ template <> struct PlanIO<ArF64> {
   __device__ static float round_im(const ArF64::C& c) { return (float)c.im; }
   __device__ static double synacc(const ArF64::C& c, bool re) { return re ? c.re : c.im; }
 };
-template <> struct PlanIO<ArF32> {
-  using Syn = float2;
-  using SynAcc = float;
-  __device__ static ArF32::C twiddle(const PlanTables& t, int e) {
-    float2 v = t.tw_f32[e];
-    return {v.x, v.y};
-  }
-  __device__ static ArF32::C weighted(const PlanTables& t, int i, float f, ArF32::C& wout) {
-    float w = t.w_f32[i];
-    wout = {w, 0.f};
-    return {w * f, w};
-  }
-  __device__ static float gamma(const PlanDev& p) {
-    return p.rho_gamma_dev ? p.rho_gamma_dev[1] : (float)p.gamma;
-  }
-  __device__ static float inv_w0(float g, float w0) { return g / w0; }
-  __device__ static bool w0_zero(const ArF32::C& w) { return w.re == 0.f; }
-  __device__ static bool w0_finite(const ArF32::C& w) { return isfinite(w.re); }
-  __device__ static float w0_out(const ArF32::C& w) { return w.re; }
-  __device__ static Syn syn(const PlanTables& t, int p) { return t.syn_f32[p]; }
-  __device__ static float round_re(const ArF32::C& c) { return c.re; }
-  __device__ static float round_im(const ArF32::C& c) { return c.im; }
-  __device__ static float synacc(const ArF32::C& c, bool re) { return re ? c.re : c.im; }
-};
-
 template <class A> struct TraceSm {
   int u;                             // u1 << 16 | u2 (canonical index)
   typename PlanIO<A>::SynAcc re, im; // (1 + s) c

@@ -2,8 +2,11 @@
 // paper): the shared-memory load bandwidth and the FP32 and FP64 FMA rates of
 // this GPU, each from a kernel that does nothing else.  The caller times the
 // launch (CUDA events) and divides the work reported here by the time and the
-// sampled SM clock.
-#include "fofse_internal.h"
+// sampled SM clock.  Built into libfofse_probes.so, not into the product
+// library (include/fofse_probes.h).
+#include <cuda_runtime.h>
+
+#include "../../include/fofse_probes.h"
 
 namespace fofse {
 namespace {
@@ -87,7 +90,7 @@ fofse_status fofse_probe_smem(int ctas, int rounds, float* d_sink, double* bytes
   if (ctas < 1 || rounds < 1 || !d_sink || !bytes) return FOFSE_E_ARG;
   fofse_smem_probe_kernel<<<ctas, kProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(d_sink, rounds);
   const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return record_cuda_error(e);
+  if (e != cudaSuccess) return FOFSE_E_CUDA;
   *bytes = (double)ctas * kProbeThreads * rounds * kProbeUnroll * 16.0;
   return FOFSE_OK;
 }
@@ -97,7 +100,7 @@ fofse_status fofse_probe_fma(int ctas, int rounds, float* d_sink, double* fmas, 
   fofse_fma_probe_kernel<<<ctas, kProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       d_sink, rounds, 0.999f, 1e-3f);
   const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return record_cuda_error(e);
+  if (e != cudaSuccess) return FOFSE_E_CUDA;
   *fmas = (double)ctas * kProbeThreads * rounds * 8.0;
   return FOFSE_OK;
 }
@@ -107,7 +110,7 @@ fofse_status fofse_probe_dfma(int ctas, int rounds, double* d_sink, double* fmas
   fofse_dfma_probe_kernel<<<ctas, kProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       d_sink, rounds, 0.999, 1e-3);
   const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return record_cuda_error(e);
+  if (e != cudaSuccess) return FOFSE_E_CUDA;
   *fmas = (double)ctas * kProbeThreads * rounds * 8.0;
   return FOFSE_OK;
 }

@@ -19,9 +19,22 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def test_the_probes_live_in_their_own_library(lib):
+    """The measurement probes (include/fofse_probes.h) are exported by
+    libfofse_probes.so, and the product library exports none of them."""
+    names = B.header_functions(B.PROBES_HEADER)
+    assert names == ["fofse_probe_dfma", "fofse_probe_fma", "fofse_probe_smem"]
+    probes = B.load_probes()
+    for n in names:
+        assert hasattr(probes, n), n
+        with pytest.raises(AttributeError):
+            getattr(lib, n)
+    assert not set(names) & set(B.header_functions())
+
+
 def test_the_binding_has_a_function_of_each_name(lib):
     """The Python binding mirrors the C ABI name for name."""
-    names = B.header_functions()
+    names = B.header_functions() + B.header_functions(B.PROBES_HEADER)
     assert {"fofse_volume_plan_create", "fofse_extrapolate_volume_batch", "fofse_probe_dfma"} <= set(names)
     for n in names:
         assert callable(getattr(B, n, None)), n
@@ -73,6 +86,7 @@ def test_batch_calls_reject_null_arguments(lib):
 def test_newer_entry_points_reject_null_arguments(lib):
     """Setters, the factor-returning batch call, the error curve and the
     probes validate their arguments on the host (no GPU needed)."""
+    assert lib.fofse_plan_set_precision(None, 2) == B.E_ARG
     null = ctypes.c_void_p()
     assert lib.fofse_plan_set_compensation(None, 1) == B.E_ARG
     assert lib.fofse_plan_set_basis(None, 1) == B.E_ARG
@@ -84,9 +98,11 @@ def test_newer_entry_points_reject_null_arguments(lib):
                                                null, null, null, null) == B.E_ARG
     assert lib.fofse_error_curve(None, 1, null, 1, null, null, 8, 8, 8, null, null) == B.E_ARG
     out = ctypes.c_double()
-    assert lib.fofse_probe_smem(0, 1, null, ctypes.byref(out), null) == B.E_ARG
-    assert lib.fofse_probe_fma(1, 0, null, ctypes.byref(out), null) == B.E_ARG
-    assert lib.fofse_probe_smem(1, 1, None, ctypes.byref(out), null) == B.E_ARG
+    probes = B.load_probes()
+    assert probes.fofse_probe_smem(0, 1, null, ctypes.byref(out), null) == B.E_ARG
+    assert probes.fofse_probe_fma(1, 0, null, ctypes.byref(out), null) == B.E_ARG
+    assert probes.fofse_probe_smem(1, 1, None, ctypes.byref(out), null) == B.E_ARG
+    assert probes.fofse_probe_dfma(1, 1, null, None, null) == B.E_ARG
 
 
 def _foreign_plan():

@@ -52,7 +52,7 @@ def test_single_block_fp32_matches_oracle():
                                   synth.PlanSpec(8, 8, 32, 0.8, 0.5, 100),
                                   synth.PlanSpec(4, 4, 32, 0.7, 0.3, 50),
                                   synth.PlanSpec(8, 8, 32, 0.8, 0.5, 64, support=1)])
-@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_filtered"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_fullff"])
 def test_small_frames_with_edge_blocks(spec, precision):
     """Several tiles, blocks in the frame corners (partial support, L beyond the
     frame), lost neighbours, and the lost samples poisoned with NaN."""
@@ -164,10 +164,12 @@ def test_full_frame_1080p_fp32_acceptance(c1):
     assert abs(d_psnr) <= 0.01, d_psnr
 
 
-def test_full_frame_1080p_filtered_exact_paths(c1):
-    """The FP32-working-spectrum variant with exact near-tie resolution."""
+def test_full_frame_1080p_all_bins_float_float_paths(c1):
+    """The all-bins float-float kernel (no scratch needed: the path without a
+    workspace and of the no-allocation entry point) takes the same exact
+    decisions."""
     wl, ora = c1
-    res, _ = run_gpu(wl, "fp32_filtered")
+    res, _ = run_gpu(wl, "fp32_fullff")
     c = compare(wl, res, ora)
     assert c["status_equal"]
     assert c["same"] == c["n"], c
@@ -182,20 +184,7 @@ def test_full_frame_1080p_fp64_validation_identical_paths(c1):
     assert c["max_err"] <= FP32_OUT
 
 
-def test_plain_fp32_mode_runs_and_is_close(c1):
-    """Plain FP32 is not the product arithmetic: it leaves the exact selection
-    path at near-ties on a large share of blocks (the reason the product uses
-    float-float); blocks whose path is intact are still close."""
-    wl, ora = c1
-    res, _ = run_gpu(wl, "fp32_plain")
-    c = compare(wl, res, ora)
-    print("plain fp32: identical paths on", c["same"], "of", c["n"], "max err", c["max_err"])
-    assert c["status_equal"]
-    assert c["frac"] > 0.3, c["frac"]
-    assert c["max_err"] <= 0.05, c["max_err"]
-
-
-@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_filtered"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_fullff"])
 def test_fft128_class_small_frame(precision):
     """32x32 blocks, border 16, 128x128 FFT (Hermitian-half W in shared memory,
     FFT in global scratch), 400 iterations; corners included."""
@@ -209,20 +198,60 @@ def test_fft128_class_small_frame(precision):
     assert c["max_err"] <= (FP32_OUT if precision == "fp64" else 1e-3)
 
 
-def test_uneven_batch_4k_sampled():
+@pytest.fixture(scope="module")
+def c2():
     """The 3840x2160 uneven batch (4x4 / 8x8 / 16x16 / 32x32 blocks, T 32/32/64/128,
-    50/100/200/400 iterations, ~20 % of the area lost) in one call; the oracle
-    checks a sample of blocks of every class one by one."""
+    50/100/200/400 iterations, ~20 % of the area lost) run in one call, and
+    the FP64 oracle on every block (its transform-domain form, which the CPU
+    pins hold equal to the spatial re-projection: paths identical,
+    coefficients to 1e-12)."""
     wl = synth.uneven_batch()
     res, _ = run_gpu(wl, "fp32")
+    ora = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans, transform_domain=True)
+    return wl, res, ora
+
+
+def test_uneven_batch_4k_every_block(c2):
+    """Acceptance on all ~5.1k blocks: identical selection paths on >= 99.9 %
+    (near-tie flips reported), max abs error <= 1e-3 on matching paths,
+    aggregate PSNR within 0.01 dB; the 32x32 / T = 128 / 400-iteration class
+    (where near-ties are most frequent) also on its own."""
+    wl, res, ora = c2
+    c = compare(wl, res, ora)
+    n = c["n"]
     st = res.status.cpu().numpy()
+    assert c["status_equal"]
     assert (st == 0).mean() > 0.98          # bursts can leave small blocks without support
-    assert set(np.unique(st)) <= {0, 1}
+    flips = {i: g for i, g in c["gaps"].items() if g < 1e-4}
+    cls = wl.blocks[:, 2]
+    per_class = {}
+    for k in range(len(wl.plans)):
+        idx = np.flatnonzero(cls == k)
+        per_class[k] = (len(idx), sum(1 for i in idx if i not in c["diverged"]))
+    print(f"uneven 4K: {c['same']} of {n} paths identical, {len(flips)} near-tie flips, "
+          f"max err {c['max_err']:.2e}; per class (blocks, identical): {per_class}")
+    assert c["same"] >= 0.999 * n, c["diverged"]
+    assert len(c["diverged"]) == len(flips), "a divergence away from a near-tie"
+    assert c["max_err"] <= 1e-3, c["max_err"]
+    n128, same128 = per_class[3]
+    assert wl.plans[3].fft_size == 128 and wl.plans[3].iters == 400 and n128 > 1000
+    assert same128 >= 0.999 * n128
+    keep = np.ones(n, dtype=bool)
+    keep[list(c["diverged"])] = False
+    tb, mask = truth_blocks(wl)
+    mask = mask & keep[:, None, None] & (st == 0)[:, None, None]
+    g = res.blocks.cpu().numpy().astype(np.float64)
+    assert abs(psnr(g, tb, mask) - psnr(ora.blocks, tb, mask)) <= 0.01
+
+
+def test_uneven_batch_4k_sample_against_the_spatial_oracle(c2):
+    """A sample of every class against the spatial re-projection itself."""
+    wl, res, _ = c2
+    st = res.status.cpu().numpy()
     rng = np.random.default_rng(7)
     pick = []
     for c in range(len(wl.plans)):
         idx = np.flatnonzero(wl.blocks[:, 2] == c)
-        assert len(idx) > 100
         pick += list(rng.choice(idx, size=6 if c == 3 else 12, replace=False))
     pick = np.array(sorted(pick))
     sub = synth.Workload(wl.name, wl.frame, wl.truth, wl.avail, wl.blocks[pick], wl.plans)
@@ -230,13 +259,10 @@ def test_uneven_batch_4k_sampled():
     assert np.array_equal(st[pick], ora.status)
     g_path = res.path()[pick]
     g_blocks = res.blocks.cpu().numpy()[pick].astype(np.float64)
-    same = 0
     for j, i in enumerate(pick):
         p = wl.plans[wl.blocks[i, 2]]
-        if np.array_equal(g_path[j, :p.iters], ora.path[j, :p.iters]):
-            same += 1
-            assert np.abs(g_blocks[j, :p.block, :p.block] - ora.blocks[j, :p.block, :p.block]).max() <= 1e-3
-    assert same == len(pick)
+        assert np.array_equal(g_path[j, :p.iters], ora.path[j, :p.iters]), i
+        assert np.abs(g_blocks[j, :p.block, :p.block] - ora.blocks[j, :p.block, :p.block]).max() <= 1e-3
 
 
 def test_empty_batch_is_a_no_op():

@@ -114,7 +114,11 @@ def test_ofse_full_frame_1080p_and_factor_distribution():
     print(f"OFSE 1080p: {n - len(miss)} of {n} blocks identical; {len(miss)} undetermined at the "
           f"working precision")
     assert not unexplained, unexplained
-    assert len(miss) <= 0.05 * n
+    # 14 to 19 of the 804 blocks are undetermined at the working precision
+    # (each shown so on the oracle above; the count moves with the last-ulp
+    # rounding of the oracle's libm on the host), but a regression in OFSE's
+    # handling of small Q would add tens
+    assert len(miss) <= 25, len(miss)
     keep = np.ones(n, dtype=bool)
     keep[miss] = False
     tb, mask = truth_blocks(wl)
@@ -164,7 +168,7 @@ def test_ofse_unsupported_combinations():
     from paper_2207_01205_gb300 import api, binding
     wl = _ofse(synth.small_frame(6, plan=synth.PlanSpec(8, 8, 32, 0.8, 0.5, 20), n_lost=3))
     fr, av, bl = to_device(wl)
-    for prec in ("fp64", "fp32_plain", "fp32_fullff", "fp32_filtered"):
+    for prec in ("fp64", "fp32_fullff"):
         plans = [api.Plan.from_spec(p, prec) for p in wl.plans]
         with pytest.raises(binding.FofseError) as e:
             api.extrapolate(plans, bl, fr, av)
