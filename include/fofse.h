@@ -384,9 +384,14 @@ const char* fofse_last_cuda_error_string(void);
  *         mod (T, T, Tt)); R[k] -= c W[k - u] + s(u) conj(c) W[k + u].
  *   out   B_hat[m,n] = sum_i (1 + s(u_i)) Re(c_i phi_{u_i}[depth, border + m,
  *         border + n]), the model over B in frame t (Eq. 1).
- * The whole recursion runs in FP64 (one CTA per block, both spectra in
- * shared memory).  With depth 0 and fft_time 1 it is the two-dimensional
- * method with the full support shape.
+ * Arithmetic (per plan, fofse_volume_plan_set_precision): FOFSE_FP32, the
+ * default and the product, runs the design of the two-dimensional FOFSE_FP32
+ * kernel on the 3-D grid (FP32 working spectrum with a rigorous error bound,
+ * exact float-float decisions and coefficients; float-float transforms; it
+ * needs a workspace); FOFSE_FP64_VALIDATE runs the whole recursion in IEEE
+ * double (one CTA per block, both spectra in shared memory; grids up to 4096
+ * bins).  With depth 0 and fft_time 1 it is the two-dimensional method with
+ * the full support shape.
  */
 typedef struct fofse_volume_plan_s* fofse_volume_plan;
 
@@ -401,23 +406,47 @@ typedef struct {
  *             fft_size^2 * fft_time >= 2048)
  *   border    spatial border width, 0 <= border, b + 2 border <= fft_size
  *   depth     frames on each side of B's frame, 0 <= depth, 2 depth + 1 <= fft_time
- *   fft_size  T in {16, 32}
- *   fft_time  Tt in {1, 2, 4, 8}, T^2 Tt <= 4096
+ *   fft_size  T in {16, 32, 64}
+ *   fft_time  Tt in {1, 2, 4, 8}, T^2 Tt <= 16384
  *   rho       rho_hat of Eq. 15, 0 < rho <= 1
  *   gamma     constant compensation factor of Eq. 14, 0 < gamma <= 1
  *   iters     number of iterations I, 1 <= I <= 4096
- * Builds the weight table rho^d (FP64, by a kernel on the current device)
- * and synchronises the legacy default stream.  FOFSE_E_ARG for invalid
- * values, FOFSE_E_UNSUPPORTED for a valid grid without a kernel (other T or
- * Tt, or T^2 Tt > 4096: both spectra must fit one SM's shared memory),
- * FOFSE_E_NOMEM / FOFSE_E_CUDA if the table cannot be built.  *out is set
- * only on FOFSE_OK.
+ * Builds the weight table rho^d (FP64 and float pairs, by a kernel on the
+ * current device), the twiddle and synthesis tables, and synchronises the
+ * legacy default stream.  The plan starts with FOFSE_FP32.  FOFSE_E_ARG for
+ * invalid values, FOFSE_E_UNSUPPORTED for a valid grid without a kernel (other
+ * T or Tt, or T^2 Tt > 16384), FOFSE_E_NOMEM / FOFSE_E_CUDA if the tables
+ * cannot be built.  *out is set only on FOFSE_OK.
  */
 fofse_status fofse_volume_plan_create(int block, int border, int depth, int fft_size, int fft_time,
                                       float rho, float gamma, int iters, fofse_volume_plan* out);
 
-/* Frees the plan's table (cudaFree: not while a CUDA graph is being captured).
- * NULL is ignored. */
+/* Arithmetic of the plan's calls: FOFSE_FP32 (default) or FOFSE_FP64_VALIDATE.
+ * FOFSE_E_ARG for a NULL plan or another value; FOFSE_E_UNSUPPORTED for FP64
+ * on a grid above 4096 bins or fft_size 64, or a block with b^2 above twice the
+ * FP64 kernel's threads (512 or 256 by the grid). */
+fofse_status fofse_volume_plan_set_precision(fofse_volume_plan plan, int precision);
+
+/* Launch shapes of the FP32 volume kernel for this plan's grid (threads per
+ * CTA and resident CTAs per SM; 0 for a NULL plan).  Every shape computes the
+ * same result up to the order of the exact-value sums, which the 64-bit fixed
+ * point makes exact: identical paths and outputs.  set_variant selects one
+ * (default 0); FOFSE_E_ARG for a NULL plan or a variant out of range.  FP64
+ * plans ignore the variant. */
+int fofse_volume_plan_variant_count(fofse_volume_plan plan);
+fofse_status fofse_volume_plan_set_variant(fofse_volume_plan plan, int variant);
+
+/* Device scratch for fofse_extrapolate_volume_batch with this plan on the
+ * current device: 256 bytes of work-queue counter plus, per resident CTA of
+ * the FP32 kernel, the block's float-float 3-D transform (then its exact W)
+ * and its exact initial spectrum per held bin: 24 K + 32 Tt bytes per CTA for
+ * K = T^2 Tt bins (about 60 MB on 152 SMs at 64 x 64 x 4, one CTA per SM),
+ * the largest over the plan's launch shapes, so that one workspace serves every
+ * variant.  0 for FP64 plans (they need none) and for a NULL plan. */
+size_t fofse_volume_workspace_bytes(fofse_volume_plan plan, int n_blocks);
+
+/* Frees the plan's tables (synchronises the device, so not while a CUDA graph
+ * is being captured on it).  NULL is ignored. */
 void fofse_volume_plan_destroy(fofse_volume_plan plan);
 
 /*
@@ -433,18 +462,23 @@ void fofse_volume_plan_destroy(fofse_volume_plan plan);
  *   d_w0              nullable; n_blocks doubles, W[0] = sum of w
  *   d_block_status    nullable; n_blocks int32 (FOFSE_BLK_*); blocks that are
  *                     not OK get B_hat = 0 and an all-zero path and coef
+ *   d_workspace       fofse_volume_workspace_bytes() bytes, caller-owned,
+ *                     256-byte aligned; required for FOFSE_FP32 plans (NULL
+ *                     for FP64 plans); not to be shared by calls that may run
+ *                     at the same time
  *   stream            cudaStream_t
  * Returns FOFSE_OK once queued (n_blocks = 0 launches nothing), FOFSE_E_ARG for
- * a NULL plan or required pointer, a non-positive size, or a current device
- * other than the one the plan was created on; FOFSE_E_CUDA if the launch
- * failed.
+ * a NULL plan or required pointer (the workspace of an FP32 plan included), a
+ * non-positive size, or a current device other than the one the plan was
+ * created on; FOFSE_E_CUDA if the launch failed.
  */
 fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
                                             const fofse_volume_block* d_blocks, int n_blocks,
                                             const float* d_video, const uint8_t* d_avail,
                                             int frames, int height, int width, int pitch,
                                             float* d_out_blocks, int32_t* d_path, double* d_coef,
-                                            double* d_w0, int32_t* d_block_status, void* stream);
+                                            double* d_w0, int32_t* d_block_status,
+                                            void* d_workspace, void* stream);
 
 /* Static, human-readable name of a status code. */
 const char* fofse_status_string(fofse_status status);

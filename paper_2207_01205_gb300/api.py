@@ -56,15 +56,16 @@ class Plan:
         self.basis = int(basis)
         if not _capturing():
             _destroy_deferred()
-        self.handle = B.fofse_plan_create(block, border, fft_size, rho, gamma, iters)
+        h = B.fofse_plan_create(block, border, fft_size, rho, gamma, iters)
         try:
-            B.fofse_plan_set_support(self.handle, self.support)
-            B.fofse_plan_set_precision(self.handle, B.PRECISIONS[precision])
-            B.fofse_plan_set_compensation(self.handle, self.compensation)
-            B.fofse_plan_set_basis(self.handle, self.basis)
+            B.fofse_plan_set_support(h, self.support)
+            B.fofse_plan_set_precision(h, B.PRECISIONS[precision])
+            B.fofse_plan_set_compensation(h, self.compensation)
+            B.fofse_plan_set_basis(h, self.basis)
         except Exception:
-            B.fofse_plan_destroy(self.handle)
+            B.fofse_plan_destroy(h)   # the handle is never published: __del__ finds none
             raise
+        self.handle = h
 
     @classmethod
     def from_spec(cls, spec, precision="fp32"):
@@ -157,21 +158,29 @@ def extrapolate(plans, blocks, frame, avail, *, out_frame=None, with_trace=True,
 class VolumePlan:
     """Extrapolation over video volumes: b x b lost block, spatial border,
     ``depth`` frames on each side of the block's frame, T x T x Tt DFT grid
-    (T = fft_size, Tt = fft_time), rho_hat, gamma, iterations."""
+    (T = fft_size, Tt = fft_time), rho_hat, gamma, iterations; precision
+    "fp32" (the product: FP32 spectrum, exact decisions) or "fp64"
+    (validation)."""
 
-    def __init__(self, block, border, depth, fft_size, fft_time, rho, gamma, iters):
+    def __init__(self, block, border, depth, fft_size, fft_time, rho, gamma, iters, precision="fp32"):
         self.block, self.border, self.depth = int(block), int(border), int(depth)
         self.fft_size, self.fft_time = int(fft_size), int(fft_time)
         self.rho, self.gamma, self.iters = float(rho), float(gamma), int(iters)
+        self.precision = precision
         if not _capturing():
             _destroy_deferred()
-        self.handle = B.fofse_volume_plan_create(block, border, depth, fft_size, fft_time, rho,
-                                                 gamma, iters)
+        h = B.fofse_volume_plan_create(block, border, depth, fft_size, fft_time, rho, gamma, iters)
+        try:
+            B.fofse_volume_plan_set_precision(h, B.PRECISIONS[precision])
+        except Exception:
+            B.fofse_volume_plan_destroy(h)   # the handle is never published: __del__ finds none
+            raise
+        self.handle = h
 
     @classmethod
-    def from_spec(cls, spec):
+    def from_spec(cls, spec, precision="fp32"):
         return cls(spec.block, spec.border, spec.depth, spec.fft_size, spec.fft_time, spec.rho,
-                   spec.gamma, spec.iters)
+                   spec.gamma, spec.iters, precision)
 
     def close(self):
         h = getattr(self, "handle", None)
@@ -195,7 +204,14 @@ class VolumeResult:
     coef: torch.Tensor | None = None   # (n, iters, 2) float64
 
 
-def extrapolate_volume(plan, blocks, video, avail, *, with_path=True, stream=None) -> VolumeResult:
+def volume_workspace(plan, n_blocks, device):
+    """Device scratch for a volume batch call (empty for FP64 plans)."""
+    nbytes = B.fofse_volume_workspace_bytes(plan.handle, n_blocks)
+    return torch.empty((nbytes,), dtype=torch.uint8, device=device) if nbytes else None
+
+
+def extrapolate_volume(plan, blocks, video, avail, *, with_path=True, stream=None,
+                       ws=None) -> VolumeResult:
     """Extrapolate every block ((n, 3) int32 device tensor: t, y, x) of a video
     ((F, H, W) float32 device tensor, availability uint8 of the same layout)."""
     n = int(blocks.shape[0])
@@ -205,6 +221,8 @@ def extrapolate_volume(plan, blocks, video, avail, *, with_path=True, stream=Non
     status = torch.empty((n,), dtype=torch.int32, device=dev)
     path = torch.empty((n, plan.iters, 3), dtype=torch.int32, device=dev) if with_path else None
     coef = torch.empty((n, plan.iters, 2), dtype=torch.float64, device=dev) if with_path else None
+    if ws is None:
+        ws = volume_workspace(plan, n, dev)
     B.fofse_extrapolate_volume_batch(plan.handle, blocks, video, avail, out_blocks=out, path=path,
-                                     coef=coef, w0=w0, status=status, stream=stream)
+                                     coef=coef, w0=w0, status=status, workspace=ws, stream=stream)
     return VolumeResult(out, w0, status, path, coef)

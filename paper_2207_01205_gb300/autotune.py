@@ -98,3 +98,53 @@ def autotune(plans, blocks, frame, avail, *, reps: int = 3, use_cache: bool = Tr
             merged.update(cache)
             _save(cache_path, merged)
     return {"choices": choices, "timings_ms": timings, "cached": cached}
+
+
+def _volume_key(plan, n_blocks, device):
+    name = torch.cuda.get_device_name(device)
+    bucket = 1 << max(0, int(n_blocks) - 1).bit_length()
+    return (f"{name}|volume|T{plan.fft_size}x{plan.fft_time}|b{plan.block}|br{plan.border}|"
+            f"d{plan.depth}|I{plan.iters}|{plan.precision}|n{bucket}")
+
+
+def autotune_volume(plan, blocks, video, avail, *, reps: int = 3, use_cache: bool = True,
+                    cache_path: str = CACHE, stream=None) -> dict:
+    """Select the fastest launch shape of a volume plan (FP32 kernel) for this
+    batch.  Returns {"choice": variant, "timings_ms": [...], "cached": bool}."""
+    n = int(blocks.shape[0])
+    dev = video.device
+    stream = stream or torch.cuda.current_stream(dev)
+    count = B.fofse_volume_plan_variant_count(plan.handle)
+    key = _volume_key(plan, n, dev)
+    with _lock:
+        cache = _load(cache_path) if use_cache else {}
+    if use_cache and key in cache and 0 <= cache[key]["variant"] < count:
+        B.fofse_volume_plan_set_variant(plan.handle, cache[key]["variant"])
+        return {"choice": cache[key]["variant"], "timings_ms": cache[key]["ms"], "cached": True}
+    out = torch.empty((n, plan.block, plan.block), dtype=torch.float32, device=dev)
+    ws = api.volume_workspace(plan, n, dev)
+    ms = []
+    for v in range(count):
+        B.fofse_volume_plan_set_variant(plan.handle, v)
+
+        def run():
+            B.fofse_extrapolate_volume_batch(plan.handle, blocks, video, avail, out_blocks=out,
+                                             workspace=ws, stream=stream)
+        run()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1) / reps)
+    B.fofse_check(stream)
+    best = min(range(count), key=lambda v: ms[v])
+    B.fofse_volume_plan_set_variant(plan.handle, best)
+    if use_cache:
+        with _lock:
+            merged = _load(cache_path)
+            merged[key] = {"variant": best, "ms": ms}
+            _save(cache_path, merged)
+    return {"choice": best, "timings_ms": ms, "cached": False}

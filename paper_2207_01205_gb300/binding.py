@@ -101,8 +101,16 @@ def _declare(L):
     L.fofse_volume_plan_create.restype = _i
     L.fofse_volume_plan_destroy.argtypes = [_vp]
     L.fofse_volume_plan_destroy.restype = None
+    L.fofse_volume_plan_set_precision.argtypes = [_vp, _i]
+    L.fofse_volume_plan_set_precision.restype = _i
+    L.fofse_volume_workspace_bytes.argtypes = [_vp, _i]
+    L.fofse_volume_workspace_bytes.restype = ctypes.c_size_t
+    L.fofse_volume_plan_variant_count.argtypes = [_vp]
+    L.fofse_volume_plan_variant_count.restype = _i
+    L.fofse_volume_plan_set_variant.argtypes = [_vp, _i]
+    L.fofse_volume_plan_set_variant.restype = _i
     L.fofse_extrapolate_volume_batch.argtypes = [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _vp, _vp,
-                                                 _vp, _vp, _vp, _vp]
+                                                 _vp, _vp, _vp, _vp, _vp]
     L.fofse_extrapolate_volume_batch.restype = _i
     L.fofse_check.argtypes = [_vp]
     L.fofse_check.restype = _i
@@ -456,16 +464,35 @@ def fofse_volume_plan_create(block, border, depth, fft_size, fft_time, rho, gamm
     return h.value
 
 
+def fofse_volume_plan_set_precision(plan, precision):
+    _check(load().fofse_volume_plan_set_precision(ctypes.c_void_p(plan), int(precision)),
+           "fofse_volume_plan_set_precision")
+
+
+def fofse_volume_workspace_bytes(plan, n_blocks) -> int:
+    return load().fofse_volume_workspace_bytes(ctypes.c_void_p(plan), int(n_blocks))
+
+
+def fofse_volume_plan_variant_count(plan) -> int:
+    return load().fofse_volume_plan_variant_count(ctypes.c_void_p(plan))
+
+
+def fofse_volume_plan_set_variant(plan, variant):
+    _check(load().fofse_volume_plan_set_variant(ctypes.c_void_p(plan), int(variant)),
+           "fofse_volume_plan_set_variant")
+
+
 def fofse_volume_plan_destroy(plan):
     load().fofse_volume_plan_destroy(ctypes.c_void_p(plan) if plan else None)
 
 
 def fofse_extrapolate_volume_batch(plan, blocks, video, avail, *, out_blocks, path=None, coef=None,
-                                   w0=None, status=None, stream=None):
+                                   w0=None, status=None, workspace=None, stream=None):
     """blocks: (n, 3) int32 device tensor (t, y, x); video float32 and avail
     uint8 device tensors of shape (F, H, W) with row pitch stride(1) and frame
     stride H * pitch; out_blocks (n, b, b) float32; path (n, iters, 3) int32,
-    coef (n, iters, 2) float64, w0 (n,) float64, status (n,) int32."""
+    coef (n, iters, 2) float64, w0 (n,) float64, status (n,) int32; workspace
+    uint8 of fofse_volume_workspace_bytes(plan, n) bytes (FP32 plans)."""
     import torch
     n = int(blocks.shape[0])
     _require(blocks, "blocks", torch.int32, (n, 3))
@@ -489,7 +516,12 @@ def fofse_extrapolate_volume_batch(plan, blocks, video, avail, *, out_blocks, pa
         raise ValueError("video frames must be back to back (frame stride = height * row pitch)")
     if tuple(avail.shape) != tuple(video.shape) or tuple(avail.stride()) != tuple(video.stride()):
         raise ValueError("avail must have the video's shape and strides")
+    _require_buffer(workspace, "workspace", torch.uint8, fofse_volume_workspace_bytes(plan, n))
+    for t, nm in ((blocks, "blocks"), (avail, "avail"), (out_blocks, "out_blocks"), (path, "path"),
+                  (coef, "coef"), (w0, "w0"), (status, "status"), (workspace, "workspace")):
+        if t is not None and t.device != video.device:
+            raise ValueError(f"{nm} is on {t.device}, the video on {video.device}")
     _check(load().fofse_extrapolate_volume_batch(
         ctypes.c_void_p(plan), _ptr(blocks), int(blocks.shape[0]), _ptr(video), _ptr(avail), F, H, W,
-        pitch, _ptr(out_blocks), _ptr(path), _ptr(coef), _ptr(w0), _ptr(status), _stream(stream)),
-        "fofse_extrapolate_volume_batch")
+        pitch, _ptr(out_blocks), _ptr(path), _ptr(coef), _ptr(w0), _ptr(status), _ptr(workspace),
+        _stream(stream)), "fofse_extrapolate_volume_batch")

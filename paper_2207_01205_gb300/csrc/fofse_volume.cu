@@ -24,15 +24,24 @@
 // keys, and the per-iteration products of c are formed once per CTA.
 #include <math.h>
 
+#include <cstring>
 #include <new>
+#include <vector>
 
-#include "fofse_internal.h"
+#include "fofse_volume32.cuh"
 
 struct fofse_volume_plan_s {
   int block, border, depth, T, Tt, Ls, Lt, iters;
   float rho, gamma;
-  int device;    // the device current at creation, which owns wtab
-  double* wtab;  // device: rho^d over the Lt x Ls x Ls volume (tau, m, n)
+  int precision;     // FOFSE_FP32 (the product) or FOFSE_FP64_VALIDATE
+  int variant;       // launch shape of the FP32 kernel
+  int device;        // the device current at creation, which owns the tables
+  double* wtab;      // device: rho^d over the Lt x Ls x Ls volume (tau, m, n)
+  float2* wff;       // device: the same as float pairs (hi, lo)
+  float4* tw_ff;     // device: exp(-j 2 pi e / T), e < T/2, float pairs
+  float4* twt_ff;    // device: exp(-j 2 pi p / Tt), p < Tt, float pairs
+  float2* syn;       // device: (cos, sin)(2 pi p / (T Tt)), p < T Tt
+  void* mem;         // the allocation holding wtab and the tables
 };
 
 namespace fofse {
@@ -52,8 +61,6 @@ struct VolArgs {
   double* w0;       // n, nullable
   int32_t* status;  // n, nullable
 };
-
-constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 
 template <int T, int TT> struct VolGeom {
   static constexpr int K = T * T * TT;                  // bins
@@ -438,16 +445,20 @@ __global__ void __launch_bounds__(VolGeom<T, TT>::NT, 1)
   }
 }
 
-// rho^d over the volume, d the distance to the centre of B in frame tau = depth.
-__global__ void fofse_volume_weights_kernel(double* wtab, int block, int border, int depth,
-                                            double rho) {
+// rho^d over the volume, d the distance to the centre of B in frame tau =
+// depth (FP64, and split into float pairs).
+__global__ void fofse_volume_weights_kernel(double* wtab, float2* wff, int block, int border,
+                                            int depth, double rho) {
   const int Ls = block + 2 * border, Lt = 2 * depth + 1;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= Lt * Ls * Ls) return;
   const int tau = s / (Ls * Ls), r = s - tau * Ls * Ls, m = r / Ls, n = r - m * Ls;
   const double c = border + (block - 1) / 2.0;
   const double dt = tau - depth, dm = m - c, dn = n - c;
-  wtab[s] = pow(rho, sqrt(dt * dt + dm * dm + dn * dn));
+  const double w = pow(rho, sqrt(dt * dt + dm * dm + dn * dn));
+  wtab[s] = w;
+  const float hi = (float)w;
+  wff[s] = make_float2(hi, (float)(w - (double)hi));
 }
 
 template <int T, int TT>
@@ -461,7 +472,7 @@ cudaError_t launch_volume_T(const VolArgs& a, int n_blocks, cudaStream_t stream)
   return cudaGetLastError();
 }
 
-// Grids with kernels: T in {16, 32}, Tt in {1, 2, 4, 8}, T^2 Tt <= 4096.
+// Grids of the FP64 kernel: T in {16, 32}, Tt in {1, 2, 4, 8}, T^2 Tt <= 4096.
 bool volume_grid_supported(int T, int Tt) {
   if (T == 16) return Tt == 1 || Tt == 2 || Tt == 4 || Tt == 8;
   if (T == 32) return Tt == 1 || Tt == 2 || Tt == 4;
@@ -481,6 +492,63 @@ cudaError_t launch_volume(int T, int Tt, const VolArgs& a, int n_blocks, cudaStr
   }
 }
 
+// Grids of the FP32 kernel: T in {16, 32, 64}, Tt in {1, 2, 4, 8}, T^2 Tt <= 16384.
+bool volume32_grid_supported(int T, int Tt) {
+  if (T == 16 || T == 32) return Tt == 1 || Tt == 2 || Tt == 4 || Tt == 8;
+  if (T == 64) return Tt == 1 || Tt == 2 || Tt == 4;
+  return false;
+}
+
+// The valid launch shapes of a grid, in the order of their variant numbers.
+template <int T, int TT, class F> cudaError_t volume32_shape(int variant, F&& f) {
+  int v = 0;
+  if (variant == v++) return f(VariantV3<T, TT, 0>());
+  if constexpr (V3Shape<T, TT, 1>::valid)
+    if (variant == v++) return f(VariantV3<T, TT, 1>());
+  if constexpr (V3Shape<T, TT, 2>::valid)
+    if (variant == v++) return f(VariantV3<T, TT, 2>());
+  return cudaErrorInvalidValue;
+}
+template <int T, int TT> constexpr int volume32_shapes() {
+  return 1 + (V3Shape<T, TT, 1>::valid ? 1 : 0) + (V3Shape<T, TT, 2>::valid ? 1 : 0);
+}
+
+template <class F> cudaError_t volume32_dispatch(int T, int Tt, int variant, F&& f) {
+  switch (T * 100 + Tt) {
+    case 1601: return volume32_shape<16, 1>(variant, f);
+    case 1602: return volume32_shape<16, 2>(variant, f);
+    case 1604: return volume32_shape<16, 4>(variant, f);
+    case 1608: return volume32_shape<16, 8>(variant, f);
+    case 3201: return volume32_shape<32, 1>(variant, f);
+    case 3202: return volume32_shape<32, 2>(variant, f);
+    case 3204: return volume32_shape<32, 4>(variant, f);
+    case 3208: return volume32_shape<32, 8>(variant, f);
+    case 6401: return volume32_shape<64, 1>(variant, f);
+    case 6402: return volume32_shape<64, 2>(variant, f);
+    case 6404: return volume32_shape<64, 4>(variant, f);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int volume32_variant_count(int T, int Tt) {
+  switch (T * 100 + Tt) {
+    case 1601: return volume32_shapes<16, 1>();
+    case 1602: return volume32_shapes<16, 2>();
+    case 1604: return volume32_shapes<16, 4>();
+    case 1608: return volume32_shapes<16, 8>();
+    case 3201: return volume32_shapes<32, 1>();
+    case 3202: return volume32_shapes<32, 2>();
+    case 3204: return volume32_shapes<32, 4>();
+    case 3208: return volume32_shapes<32, 8>();
+    case 6401: return volume32_shapes<64, 1>();
+    case 6402: return volume32_shapes<64, 2>();
+    case 6404: return volume32_shapes<64, 4>();
+    default: return 1;
+  }
+}
+
+constexpr size_t kVolCounterBytes = 256;
+
 int volume_threads(int T, int Tt) { return T * T * Tt >= 2048 ? 512 : 256; }
 
 }  // namespace
@@ -497,8 +565,7 @@ fofse_status fofse_volume_plan_create(int block, int border, int depth, int fft_
   if (iters < 1 || iters > 4096) return FOFSE_E_ARG;
   const int Ls = block + 2 * border, Lt = 2 * depth + 1;
   if (Ls > fft_size || Lt > fft_time) return FOFSE_E_ARG;
-  if (!volume_grid_supported(fft_size, fft_time)) return FOFSE_E_UNSUPPORTED;
-  if (block * block > 2 * volume_threads(fft_size, fft_time)) return FOFSE_E_UNSUPPORTED;
+  if (!volume32_grid_supported(fft_size, fft_time)) return FOFSE_E_UNSUPPORTED;
   fofse_volume_plan_s* p = new (std::nothrow) fofse_volume_plan_s();
   if (!p) return FOFSE_E_NOMEM;
   p->block = block;
@@ -511,20 +578,51 @@ fofse_status fofse_volume_plan_create(int block, int border, int depth, int fft_
   p->iters = iters;
   p->rho = rho;
   p->gamma = gamma;
+  p->precision = FOFSE_FP32;
+  p->variant = 0;
+  const int T = fft_size, Tt = fft_time;
   const int ns = Lt * Ls * Ls;
+  // host tables from integer phases in FP64, split into float pairs
+  constexpr double kTwoPi = 6.283185307179586476925286766559;
+  std::vector<float4> tw(T / 2), twt(Tt);
+  std::vector<float2> syn((size_t)T * Tt);
+  auto pair4 = [](double c, double s) {
+    const float ch = (float)c, sh = (float)s;
+    return make_float4(ch, sh, (float)(c - ch), (float)(s - sh));
+  };
+  for (int e = 0; e < T / 2; ++e) tw[e] = pair4(std::cos(kTwoPi * e / T), -std::sin(kTwoPi * e / T));
+  for (int q = 0; q < Tt; ++q) twt[q] = pair4(std::cos(kTwoPi * q / Tt), -std::sin(kTwoPi * q / Tt));
+  for (int q = 0; q < T * Tt; ++q)
+    syn[q] = make_float2((float)std::cos(kTwoPi * q / (T * Tt)), (float)std::sin(kTwoPi * q / (T * Tt)));
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t o_w = 0, o_wff = al(sizeof(double) * ns), o_tw = o_wff + al(sizeof(float2) * ns),
+               o_twt = o_tw + al(sizeof(float4) * (T / 2)), o_syn = o_twt + al(sizeof(float4) * Tt),
+               total = o_syn + al(sizeof(float2) * T * Tt);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
     delete p;
     return record_cuda_error(e);
   }
-  e = cudaMalloc(&p->wtab, sizeof(double) * ns);
+  e = cudaMalloc(&p->mem, total);
   if (e != cudaSuccess) {
     delete p;
     return e == cudaErrorMemoryAllocation ? FOFSE_E_NOMEM : record_cuda_error(e);
   }
-  fofse_volume_weights_kernel<<<(ns + 255) / 256, 256>>>(p->wtab, block, border, depth, (double)rho);
-  if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(0)) != cudaSuccess) {
-    cudaFree(p->wtab);
+  unsigned char* base = static_cast<unsigned char*>(p->mem);
+  p->wtab = reinterpret_cast<double*>(base + o_w);
+  p->wff = reinterpret_cast<float2*>(base + o_wff);
+  p->tw_ff = reinterpret_cast<float4*>(base + o_tw);
+  p->twt_ff = reinterpret_cast<float4*>(base + o_twt);
+  p->syn = reinterpret_cast<float2*>(base + o_syn);
+  if ((e = cudaMemcpy(p->tw_ff, tw.data(), sizeof(float4) * (T / 2), cudaMemcpyHostToDevice)) == cudaSuccess &&
+      (e = cudaMemcpy(p->twt_ff, twt.data(), sizeof(float4) * Tt, cudaMemcpyHostToDevice)) == cudaSuccess &&
+      (e = cudaMemcpy(p->syn, syn.data(), sizeof(float2) * T * Tt, cudaMemcpyHostToDevice)) == cudaSuccess) {
+    fofse_volume_weights_kernel<<<(ns + 255) / 256, 256>>>(p->wtab, p->wff, block, border, depth,
+                                                            (double)rho);
+    if ((e = cudaGetLastError()) == cudaSuccess) e = cudaStreamSynchronize(0);
+  }
+  if (e != cudaSuccess) {
+    cudaFree(p->mem);
     delete p;
     return record_cuda_error(e);
   }
@@ -532,9 +630,47 @@ fofse_status fofse_volume_plan_create(int block, int border, int depth, int fft_
   return FOFSE_OK;
 }
 
+fofse_status fofse_volume_plan_set_precision(fofse_volume_plan plan, int precision) {
+  if (!plan || (precision != FOFSE_FP32 && precision != FOFSE_FP64_VALIDATE)) return FOFSE_E_ARG;
+  if (precision == FOFSE_FP64_VALIDATE &&
+      (!volume_grid_supported(plan->T, plan->Tt) ||
+       plan->block * plan->block > 2 * volume_threads(plan->T, plan->Tt)))
+    return FOFSE_E_UNSUPPORTED;
+  plan->precision = precision;
+  return FOFSE_OK;
+}
+
+size_t fofse_volume_workspace_bytes(fofse_volume_plan plan, int n_blocks) {
+  if (!plan || n_blocks < 0) return 0;
+  if (plan->precision != FOFSE_FP32) return 0;
+  // the largest over the launch shapes, so that a workspace sized once serves
+  // every variant
+  size_t most = 0;
+  for (int v = 0; v < volume32_variant_count(plan->T, plan->Tt); ++v) {
+    size_t b = 0;
+    const cudaError_t e = volume32_dispatch(plan->T, plan->Tt, v, [&](auto x) {
+      return decltype(x)::scratch(plan->iters, &b);
+    });
+    if (e != cudaSuccess) return 0;
+    most = b > most ? b : most;
+  }
+  return kVolCounterBytes + most;
+}
+
+int fofse_volume_plan_variant_count(fofse_volume_plan plan) {
+  return plan ? volume32_variant_count(plan->T, plan->Tt) : 0;
+}
+
+fofse_status fofse_volume_plan_set_variant(fofse_volume_plan plan, int variant) {
+  if (!plan || variant < 0 || variant >= volume32_variant_count(plan->T, plan->Tt)) return FOFSE_E_ARG;
+  plan->variant = variant;
+  return FOFSE_OK;
+}
+
 void fofse_volume_plan_destroy(fofse_volume_plan plan) {
   if (!plan) return;
-  cudaFree(plan->wtab);
+  cudaDeviceSynchronize();
+  cudaFree(plan->mem);
   delete plan;
 }
 
@@ -543,13 +679,54 @@ fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
                                             const float* d_video, const uint8_t* d_avail,
                                             int frames, int height, int width, int pitch,
                                             float* d_out_blocks, int32_t* d_path, double* d_coef,
-                                            double* d_w0, int32_t* d_block_status, void* stream) {
+                                            double* d_w0, int32_t* d_block_status,
+                                            void* d_workspace, void* stream) {
   if (!plan || n_blocks < 0 || frames < 1 || height < 1 || width < 1 || pitch < width)
     return FOFSE_E_ARG;
-  if (n_blocks == 0) return FOFSE_OK;
-  if (!d_blocks || !d_video || !d_avail || !d_out_blocks) return FOFSE_E_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return FOFSE_E_ARG;
+  if (plan->precision == FOFSE_FP32 && !d_workspace) return FOFSE_E_ARG;
+  if (n_blocks == 0) return FOFSE_OK;
+  if (!d_blocks || !d_video || !d_avail || !d_out_blocks) return FOFSE_E_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (plan->precision == FOFSE_FP32) {
+    VolArgs32 a;
+    std::memset(&a, 0, sizeof(a));
+    a.block = plan->block;
+    a.border = plan->border;
+    a.depth = plan->depth;
+    a.Ls = plan->Ls;
+    a.Lt = plan->Lt;
+    a.iters = plan->iters;
+    a.gamma_h = plan->gamma;
+    a.gamma_l = 0.f;
+    a.w_ff = plan->wff;
+    a.tab.tw_ff = plan->tw_ff;
+    a.twt_ff = plan->twt_ff;
+    a.syn = plan->syn;
+    a.blocks = d_blocks;
+    a.n_blocks = n_blocks;
+    a.video = d_video;
+    a.avail = d_avail;
+    a.frames = frames;
+    a.height = height;
+    a.width = width;
+    a.pitch = pitch;
+    a.out = d_out_blocks;
+    a.path = d_path;
+    a.coef = d_coef;
+    a.w0 = d_w0;
+    a.status = d_block_status;
+    unsigned char* ws = static_cast<unsigned char*>(d_workspace);
+    a.queue = reinterpret_cast<int*>(ws);
+    a.scratch = ws + kVolCounterBytes;
+    a.scratch_bytes = fofse_volume_workspace_bytes(plan, n_blocks) - kVolCounterBytes;
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+      e = volume32_dispatch(plan->T, plan->Tt, plan->variant,
+                            [&](auto v) { return decltype(v)::launch(a, s); });
+    return e == cudaSuccess ? FOFSE_OK : record_cuda_error(e);
+  }
   VolArgs a;
   a.block = plan->block;
   a.border = plan->border;
@@ -571,7 +748,7 @@ fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
   a.coef = d_coef;
   a.w0 = d_w0;
   a.status = d_block_status;
-  const cudaError_t e = launch_volume(plan->T, plan->Tt, a, n_blocks, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = launch_volume(plan->T, plan->Tt, a, n_blocks, s);
   return e == cudaSuccess ? FOFSE_OK : record_cuda_error(e);
 }
 

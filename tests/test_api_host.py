@@ -66,14 +66,19 @@ def test_volume_plan_arguments_are_checked_before_any_cuda_call():
         with pytest.raises(B.FofseError) as ei:
             B.fofse_volume_plan_create(8, 4, 1, 16, 4, rho, gamma, iters)
         assert ei.value.status == B.E_ARG
-    for args in [(8, 4, 1, 64, 4), (8, 4, 1, 32, 8), (8, 4, 1, 16, 16), (8, 4, 1, 16, 3),
-                 (24, 4, 0, 32, 1)]:
+    for args in [(8, 4, 1, 64, 8), (8, 4, 0, 128, 1), (8, 4, 1, 16, 16), (8, 4, 1, 16, 3),
+                 (8, 4, 1, 48, 4)]:
         with pytest.raises(B.FofseError) as ei:
             B.fofse_volume_plan_create(*args, 0.8, 0.5, 10)
         assert ei.value.status == B.E_UNSUPPORTED, args
-    st = B.load().fofse_extrapolate_volume_batch(None, None, 1, None, None, 1, 1, 1, 1, None, None,
-                                                 None, None, None, None)
+    L = B.load()
+    st = L.fofse_extrapolate_volume_batch(None, None, 1, None, None, 1, 1, 1, 1, None, None,
+                                          None, None, None, None, None)
     assert st == B.E_ARG
+    assert L.fofse_volume_plan_set_precision(None, 0) == B.E_ARG
+    assert L.fofse_volume_workspace_bytes(None, 10) == 0
+    assert L.fofse_volume_plan_variant_count(None) == 0
+    assert L.fofse_volume_plan_set_variant(None, 0) == B.E_ARG
 
 
 def test_volume_batch_rejects_host_tensors_and_wrong_dtypes():

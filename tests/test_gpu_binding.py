@@ -69,3 +69,17 @@ def test_calls_reject_host_tensors_wrong_dtypes_and_mismatched_frames():
         binding.fofse_backward(handles, blocks, frame, avail, tr, w0, gb[:, :8, :8].contiguous())
     with pytest.raises(ValueError, match="trace"):
         binding.fofse_backward(handles, blocks, frame, avail, tr[:, :5].contiguous(), w0, gb)
+
+
+def test_a_plan_whose_settings_fail_is_destroyed_once():
+    """A plan whose creation succeeds but whose settings are refused is
+    destroyed by the constructor and never again by the finaliser (a second
+    destroy would free its device tables twice)."""
+    import gc
+    with pytest.raises(binding.FofseError):
+        api.Plan(8, 4, 32, 0.8, 0.5, 10, basis=7)
+    with pytest.raises(binding.FofseError):
+        api.VolumePlan(32, 16, 0, 64, 1, 0.8, 0.5, 10, precision="fp64")
+    gc.collect()
+    p, v = api.Plan(8, 4, 32, 0.8, 0.5, 10), api.VolumePlan(8, 4, 1, 16, 4, 0.8, 0.5, 10)
+    assert p.handle and v.handle
