@@ -42,7 +42,8 @@
  *    have been created on the device that is current at the call: the calls
  *    return FOFSE_E_ARG otherwise (before any launch).  The library never
  *    allocates or frees memory on the launch path (plans allocate their small
- *    constant tables once, in fofse_plan_create).
+ *    constant tables once, in fofse_plan_create, and the DCT basis' table in
+ *    fofse_plan_set_basis).
  *  - Frames are row-major float32 with `pitch` elements per row; availability
  *    masks are uint8 (1 = usable sample, 0 = lost) with the same pitch.
  *  - Argument errors are reported synchronously through the return value and
@@ -138,7 +139,8 @@ typedef struct {
  */
 fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, float gamma,
                                int iters, fofse_plan* out);
-/* Support shape (FOFSE_SUPPORT_*); default FULL.  FOFSE_E_ARG for other values. */
+/* Support shape (FOFSE_SUPPORT_*); default FULL.  FOFSE_E_ARG for other values.
+ * For a DCT plan this rebuilds the plan's shared table (fofse_plan_set_basis). */
 fofse_status fofse_plan_set_support(fofse_plan plan, int shape);
 /* Arithmetic (FOFSE_FP32 default, FOFSE_FP64_VALIDATE, FOFSE_FP32_FULLFF);
  * FOFSE_E_ARG for other values. */
@@ -156,8 +158,15 @@ fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation);
  * (the batch calls return FOFSE_E_UNSUPPORTED otherwise); it needs no
  * workspace (work-queue counters are used when one is given).  The trace holds
  * u = (k1, k2) in [0, T)^2 and the real coefficient (dc_im = 0); fofse_backward
- * runs the adjoint of this basis' recursion (one block per CTA).  FOFSE_E_ARG
- * for other values. */
+ * runs the adjoint of this basis' recursion (one block per CTA).  Selecting
+ * the DCT basis builds, synchronously on the current device (the plan's), the
+ * basis' product table C of the complete support -- every sample of L outside
+ * B, and inside the support shape, usable -- for the plan's rho: (2T - 1) x 2T
+ * float pairs (130 KB at fft_size 64), freed with the plan.  Blocks whose
+ * support is complete copy it instead of building C (calls with d_rho_gamma
+ * build it per block).  FOFSE_E_ARG for other values or another current
+ * device; FOFSE_E_NOMEM / FOFSE_E_CUDA if the table could not be built (the
+ * basis is set all the same, and every block then builds C itself). */
 fofse_status fofse_plan_set_basis(fofse_plan plan, int basis);
 /* Number of launch shapes (threads per block / resident blocks per SM) of the
  * plan's kernel for its current precision; 0 for a NULL plan. */

@@ -48,6 +48,7 @@ struct fofse_plan_s {
                  // member: host tests build a stand-in plan with only this set)
   PlanDev dev;   // scalars + device table pointers
   void* mem;     // one device allocation holding every table
+  void* dct_mem; // the DCT basis' shared complete-support table (allocated with the basis)
 };
 
 namespace {
@@ -210,6 +211,7 @@ cudaError_t apply_override(const fofse_plan* plans, int pi, const float* d_rho_g
   P.tab.w_ff = wff;
   P.tab.w_f64 = w64;
   P.tab.w_f32 = w32;
+  P.tab.dct_c_full = nullptr;  // built for the plan's own rho
   P.rho_gamma_dev = rg;
   return e;
 }
@@ -357,6 +359,7 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
   d.tab.syn_ff = reinterpret_cast<const float4*>(base + o_sff);
   d.tab.dist = reinterpret_cast<const double*>(base + o_dist);
   d.tab.dct_cos_ff = reinterpret_cast<const float2*>(base + o_dcos);
+  d.tab.dct_c_full = nullptr;
   d.rho_gamma_dev = nullptr;
   {
     unsigned* err = err_word_ptr();
@@ -374,15 +377,43 @@ fofse_status fofse_plan_create(int block, int border, int fft_size, float rho, f
     }
   }
   p->mem = mem;
+  p->dct_mem = nullptr;
   cudaGetDevice(&p->device);
   *out = p;
   return FOFSE_OK;
 }
 
+namespace {
+// (Re)builds the DCT basis' complete-support table of a DCT plan (fft_size 32
+// or 64) for its current support shape; synchronous.  On failure the plan
+// keeps no table (its blocks then build C themselves) and the error is
+// returned.
+fofse_status refresh_dct_table(fofse_plan plan) {
+  PlanDev& d = plan->dev;
+  d.tab.dct_c_full = nullptr;
+  if (d.basis != FOFSE_BASIS_DCT || (d.T != 32 && d.T != 64)) return FOFSE_OK;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return FOFSE_E_ARG;
+  cudaError_t e = cudaSuccess;
+  if (!plan->dct_mem) {
+    e = cudaMalloc(&plan->dct_mem, sizeof(float2) * dct_table_elems(d.T));
+    if (e != cudaSuccess) {
+      plan->dct_mem = nullptr;
+      return e == cudaErrorMemoryAllocation ? FOFSE_E_NOMEM : cuda_fail(e);
+    }
+  }
+  e = build_dct_table(d, static_cast<float2*>(plan->dct_mem), 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  d.tab.dct_c_full = static_cast<const float2*>(plan->dct_mem);
+  return FOFSE_OK;
+}
+}  // namespace
+
 fofse_status fofse_plan_set_support(fofse_plan plan, int shape) {
   if (!plan || (shape != FOFSE_SUPPORT_FULL && shape != FOFSE_SUPPORT_CAUSAL_L)) return FOFSE_E_ARG;
   plan->dev.support = shape;
-  return FOFSE_OK;
+  return refresh_dct_table(plan);
 }
 
 fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation) {
@@ -397,7 +428,7 @@ fofse_status fofse_plan_set_basis(fofse_plan plan, int basis) {
   if (!plan || (basis != FOFSE_BASIS_DFT && basis != FOFSE_BASIS_DCT)) return FOFSE_E_ARG;
   plan->dev.basis = basis;
   if (plan->dev.variant >= forward_variant_count(plan->dev)) plan->dev.variant = 0;
-  return FOFSE_OK;
+  return refresh_dct_table(plan);
 }
 
 fofse_status fofse_plan_set_precision(fofse_plan plan, int precision) {
@@ -433,6 +464,7 @@ void fofse_plan_destroy(fofse_plan plan) {
   if (!plan) return;
   cudaDeviceSynchronize();
   cudaFree(plan->mem);
+  if (plan->dct_mem) cudaFree(plan->dct_mem);
   delete plan;
 }
 

@@ -57,6 +57,87 @@ __device__ __forceinline__ void ff_mac(ff& acc, ff a, ff b) {
 }
 __device__ __forceinline__ ff ff_norm(ff a) { return ff_fast_two_sum(a.h, a.l); }
 
+// One element of the row sums of the masked weights over n (row r of the
+// chunk), zc[r][a] = sum_n w[r][n] cos(pi a (2n+1) / (2T)), and one element of
+// C's accumulation over the chunk's rows, C[a1][a2] += sum_r cos(a1, m0 + r)
+// zc[r][a2].  The per-block setup and the build of the complete-support table
+// both use these, so a shared table equals the one a block would build, bit
+// for bit (the order of each element's sum is fixed; the split of elements
+// over threads does not enter).
+template <int T, class Cos>
+__device__ __forceinline__ float2 dct_row_sum(const float2* src, int a, int Ls, Cos cosv) {
+  ff acc = {0.f, 0.f};
+  for (int n = 0; n < Ls; ++n) {
+    const float2 v = src[n];
+    ff_mac(acc, ff{v.x, v.y}, cosv(a, n));
+  }
+  acc = ff_norm(acc);
+  return make_float2(acc.h, acc.l);
+}
+template <int T, class Cos>
+__device__ __forceinline__ float2 dct_c_accumulate(float2 c0, const float2* zc, int a1, int a2,
+                                                   int m0, int nr, Cos cosv) {
+  constexpr int TT = 2 * T - 1;
+  ff acc = {c0.x, c0.y};
+  for (int r = 0; r < nr; ++r) {
+    const float2 v = zc[r * TT + a2];
+    ff_mac(acc, cosv(a1, m0 + r), ff{v.x, v.y});
+  }
+  acc = ff_norm(acc);
+  return make_float2(acc.h, acc.l);
+}
+// KB independent elements of either kind at once (interleaved chains for
+// latency; each element's own sum runs in the order of the one-element forms
+// above, so the values are the same bit for bit).  Elements with on[k] false
+// are computed on a valid stand-in and not stored by the caller.
+template <int T, int KB, class Cos>
+__device__ __forceinline__ void dct_row_sums(const float2* (&src)[KB], const int (&a)[KB], int Ls,
+                                             Cos cosv, float2 (&out)[KB]) {
+  ff acc[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) acc[k] = {0.f, 0.f};
+  for (int n = 0; n < Ls; ++n) {
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      const float2 v = src[k][n];
+      ff_mac(acc[k], ff{v.x, v.y}, cosv(a[k], n));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const ff r = ff_norm(acc[k]);
+    out[k] = make_float2(r.h, r.l);
+  }
+}
+template <int T, int KB, class Cos>
+__device__ __forceinline__ void dct_c_accumulates(float2 (&c)[KB], const float2* zc, const int (&a1)[KB],
+                                                  const int (&a2)[KB], int m0, int nr, Cos cosv) {
+  constexpr int TT = 2 * T - 1;
+  ff acc[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) acc[k] = {c[k].x, c[k].y};
+  for (int r = 0; r < nr; ++r) {
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      const float2 v = zc[r * TT + a2[k]];
+      ff_mac(acc[k], cosv(a1[k], m0 + r), ff{v.x, v.y});
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const ff r = ff_norm(acc[k]);
+    c[k] = make_float2(r.h, r.l);
+  }
+}
+
+// (m, n) of L in the support shape and outside B
+__device__ __forceinline__ bool dct_in_support(int support, int m, int n, int b, int br) {
+  const bool inB = m >= br && m < br + b && n >= br && n < br + b;
+  bool inS = true;
+  if (support == FOFSE_SUPPORT_CAUSAL_L) inS = (m < br) ? (n < br + b) : (m < br + b ? n < br : false);
+  return inS && !inB;
+}
+
 // (a, b) better than (c, d): larger value, or equal value and smaller index
 __device__ __forceinline__ bool better(ff a, int ia, ff b, int ib) {
   return a.h > b.h || (a.h == b.h && (a.l > b.l || (a.l == b.l && ia < ib)));
@@ -87,8 +168,29 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   };
 
   // ---- setup: C and R0 by chunks of CH rows of L ----------------------------
+  // A block whose support is complete (every sample of L in the support shape
+  // and outside B usable) has the plan's shared table C: it is copied, and
+  // only R0 is summed here.
+  bool full = P.tab.dct_c_full != nullptr;
+  if (full) {
+    bool miss = false;
+    for (int e = tid; e < Ls * Ls; e += NT) {
+      const int m = e / Ls, n = e - m * Ls;
+      if (!dct_in_support(P.support, m, n, b, br)) continue;
+      const int fy = ly0 + m, fx = lx0 + n;
+      const bool in = fy >= 0 && fy < args.height && fx >= 0 && fx < args.width;
+      miss |= !(in && args.avail[(size_t)fy * args.pitch + fx]);
+    }
+    full = !__syncthreads_or(miss);
+  }
   for (int e = tid; e < 4 * T; e += NT) cosT[e] = P.tab.dct_cos_ff[e];
-  for (int e = tid; e < TT * S; e += NT) ct[e] = make_float2(0.f, 0.f);
+  if (full) {
+    const float4* src = reinterpret_cast<const float4*>(P.tab.dct_c_full);
+    float4* dst = reinterpret_cast<float4*>(ct);
+    for (int e = tid; e < TT * S / 2; e += NT) dst[e] = src[e];
+  } else {
+    for (int e = tid; e < TT * S; e += NT) ct[e] = make_float2(0.f, 0.f);
+  }
   const int k2 = tid & (T - 1), r0 = tid / T;  // bins (r0 + j RS, k2)
   ff R[NB];
 #pragma unroll
@@ -102,13 +204,9 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
       const int r = e / T, n = e - r * T, m = m0 + r;
       float2 wv = make_float2(0.f, 0.f), xv = make_float2(0.f, 0.f);
       if (r < nr && n < Ls) {
-        const bool inB = m >= br && m < br + b && n >= br && n < br + b;
-        bool inS = true;
-        if (P.support == FOFSE_SUPPORT_CAUSAL_L)
-          inS = (m < br) ? (n < br + b) : (m < br + b ? n < br : false);
         const int fy = ly0 + m, fx = lx0 + n;
         const bool in = fy >= 0 && fy < args.height && fx >= 0 && fx < args.width;
-        if (in && !inB && inS && args.avail[(size_t)fy * args.pitch + fx]) {
+        if (in && dct_in_support(P.support, m, n, b, br) && args.avail[(size_t)fy * args.pitch + fx]) {
           const float f = args.frame[(size_t)fy * args.pitch + fx];
           bad |= !isfinite(f);
           ArFF::C wd;
@@ -121,44 +219,66 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
       xsm[e] = xv;
     }
     __syncthreads();
-    // row sums over n: zc[r][a2] = sum_n w cos(a2, n), yc[r][k] = sum_n x cos(k, n)
-    for (int e = tid; e < CH * (TT + T); e += NT) {
-      const bool isz = e < CH * TT;
-      const int ee = isz ? e : e - CH * TT;
-      const int r = isz ? ee / TT : ee / T, a = isz ? ee - r * TT : ee - r * T;
-      const float2* src = (isz ? wsm : xsm) + r * T;
-      ff acc = {0.f, 0.f};
-      for (int n = 0; n < Ls; ++n) {
-        const float2 v = src[n];
-        ff_mac(acc, ff{v.x, v.y}, cosv(a, n));
+    // row sums over n: zc[r][a2] = sum_n w cos(a2, n) (not for a shared C),
+    // yc[r][k] = sum_n x cos(k, n)
+    // (KB elements per thread and pass)
+    constexpr int KB = 4;
+    {
+      const int e0 = full ? CH * TT : 0, e1 = CH * (TT + T);
+      for (int eb = e0 + tid; eb < e1; eb += KB * NT) {
+        const float2* src[KB];
+        int a[KB], dst[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const int e = eb + k * NT;
+          const bool on = e < e1;
+          const int ec = on ? e : e0;
+          const bool isz = ec < CH * TT;
+          const int ee = isz ? ec : ec - CH * TT;
+          const int r = isz ? ee / TT : ee / T;
+          a[k] = isz ? ee - r * TT : ee - r * T;
+          src[k] = (isz ? wsm : xsm) + r * T;
+          dst[k] = on ? (isz ? r * TT + a[k] : CH * TT + r * T + a[k]) : -1;  // zc, then yc
+        }
+        float2 v[KB];
+        dct_row_sums<T, KB>(src, a, Ls, cosv, v);
+#pragma unroll
+        for (int k = 0; k < KB; ++k)
+          if (dst[k] >= 0) zc[dst[k]] = v[k];  // yc follows zc in the chunk region
       }
-      acc = ff_norm(acc);
-      if (isz) zc[r * TT + a] = make_float2(acc.h, acc.l);
-      else yc[r * T + a] = make_float2(acc.h, acc.l);
     }
     __syncthreads();
     // C[a1][a2] += sum_r cos(a1, m0 + r) zc[r][a2]
-    for (int e = tid; e < TT * TT; e += NT) {
-      const int a1 = e / TT, a2 = e - a1 * TT;
-      const float2 c0 = ct[a1 * S + a2];
-      ff acc = {c0.x, c0.y};
-      for (int r = 0; r < nr; ++r) {
-        const float2 v = zc[r * TT + a2];
-        ff_mac(acc, cosv(a1, m0 + r), ff{v.x, v.y});
+    if (!full) {
+      for (int eb = tid; eb < TT * TT; eb += KB * NT) {
+        int a1[KB], a2[KB];
+        float2 c[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const int e = eb + k * NT, ec = e < TT * TT ? e : 0;
+          a1[k] = ec / TT;
+          a2[k] = ec - a1[k] * TT;
+          c[k] = ct[a1[k] * S + a2[k]];
+        }
+        dct_c_accumulates<T, KB>(c, zc, a1, a2, m0, nr, cosv);
+#pragma unroll
+        for (int k = 0; k < KB; ++k)
+          if (eb + k * NT < TT * TT) ct[a1[k] * S + a2[k]] = c[k];
       }
-      acc = ff_norm(acc);
-      ct[a1 * S + a2] = make_float2(acc.h, acc.l);
     }
     // R0 of the held bins: R[k1][k2] += sum_r cos(k1, m0 + r) yc[r][k2]
+    // (the bins' chains interleaved, each over r in order)
+    {
+      ff acc[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      const int k1 = r0 + j * RS;
-      ff acc = R[j];
+      for (int j = 0; j < NB; ++j) acc[j] = R[j];
       for (int r = 0; r < nr; ++r) {
         const float2 v = yc[r * T + k2];
-        ff_mac(acc, cosv(k1, m0 + r), ff{v.x, v.y});
+#pragma unroll
+        for (int j = 0; j < NB; ++j) ff_mac(acc[j], cosv(r0 + j * RS, m0 + r), ff{v.x, v.y});
       }
-      R[j] = ff_norm(acc);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) R[j] = ff_norm(acc[j]);
     }
     __syncthreads();
   }
@@ -335,6 +455,61 @@ __global__ void __launch_bounds__(NT) fofse_forward_dct_kernel(const __grid_cons
     if (args.blocks[item].plan != args.plan_index) continue;
     forward_block_dct<T, NT>(args, item, dsm);
   }
+}
+
+// The table C of the complete support of plan P (the per-block setup's C
+// loop with every sample of L in the support shape and outside B usable), for
+// the blocks that share it; one CTA.
+template <int T, int NT>
+__global__ void __launch_bounds__(NT) fofse_dct_table_kernel(const PlanDev P, float2* out) {
+  using G = Dct<T, NT>;
+  constexpr int TT = G::TT, S = G::S, CH = G::CH;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* dsm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float2* ct = reinterpret_cast<float2*>(dsm);
+  float2* cosT = reinterpret_cast<float2*>(dsm + G::cos_off);
+  float2* wsm = reinterpret_cast<float2*>(dsm + G::chunk_off);  // [CH][T]
+  float2* zc = wsm + 2 * CH * T;                                 // [CH][TT], as in the forward
+  const int tid = threadIdx.x, b = P.block, br = P.border, Ls = P.Ls;
+  auto cosv = [&](int a, int m) -> ff {
+    const float2 v = cosT[(a * (2 * m + 1)) & (4 * T - 1)];
+    return {v.x, v.y};
+  };
+  for (int e = tid; e < 4 * T; e += NT) cosT[e] = P.tab.dct_cos_ff[e];
+  for (int e = tid; e < TT * S; e += NT) ct[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int m0 = 0; m0 < Ls; m0 += CH) {
+    const int nr = min(CH, Ls - m0);
+    for (int e = tid; e < CH * T; e += NT) {
+      const int r = e / T, n = e - r * T, m = m0 + r;
+      float2 wv = make_float2(0.f, 0.f);
+      if (r < nr && n < Ls && dct_in_support(P.support, m, n, b, br)) wv = P.tab.w_ff[m * Ls + n];
+      wsm[e] = wv;
+    }
+    __syncthreads();
+    for (int e = tid; e < CH * TT; e += NT) {
+      const int r = e / TT, a = e - r * TT;
+      zc[r * TT + a] = dct_row_sum<T>(wsm + r * T, a, Ls, cosv);
+    }
+    __syncthreads();
+    for (int e = tid; e < TT * TT; e += NT) {
+      const int a1 = e / TT, a2 = e - a1 * TT;
+      ct[a1 * S + a2] = dct_c_accumulate<T>(ct[a1 * S + a2], zc, a1, a2, m0, nr, cosv);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < TT * S; e += NT) out[e] = ct[e];
+}
+
+template <int T> cudaError_t build_dct_table_T(const PlanDev& p, float2* out, cudaStream_t s) {
+  constexpr int NT = 256;
+  const size_t sm = Dct<T, NT>::bytes(1);
+  cudaError_t e = cudaFuncSetAttribute(fofse_dct_table_kernel<T, NT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  fofse_dct_table_kernel<T, NT><<<1, NT, sm, s>>>(p, out);
+  return cudaGetLastError();
 }
 
 template <int T, int NT> struct VariantDct {
@@ -561,5 +736,13 @@ cudaError_t launch_forward_dct(const FwdArgs& a, cudaStream_t s) {
 }
 
 int forward_dct_variant_count(const PlanDev& p) { return (p.T == 32 || p.T == 64) ? 2 : 1; }
+
+size_t dct_table_elems(int T) { return (size_t)(2 * T - 1) * 2 * T; }
+
+cudaError_t build_dct_table(const PlanDev& p, float2* out, cudaStream_t s) {
+  if (p.T == 32) return build_dct_table_T<32>(p, out, s);
+  if (p.T == 64) return build_dct_table_T<64>(p, out, s);
+  return cudaErrorNotSupported;
+}
 
 }  // namespace fofse

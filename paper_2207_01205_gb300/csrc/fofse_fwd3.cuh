@@ -109,6 +109,38 @@ __device__ __forceinline__ void key_insert(unsigned& k1, unsigned& k2, float m, 
   k1 = max(k1, key);
 }
 
+// The FP32 update of one held bin, R -= c W[k - u] + conj(c) W[k + u] with
+// c = p + j q:
+//   R.x = fma(-p, Wm.x + Wp.x, fma( q, Wm.y - Wp.y, R.x))
+//   R.y = fma(-p, Wm.y + Wp.y, fma(-q, Wm.x - Wp.x, R.y))
+// with the sum, the difference and the p terms as packed FP32x2 operations
+// (each lane rounds as the scalar instruction does, so the result is that of
+// the scalar form bit for bit).  npp = (-p, -p) as one 64-bit pair.
+__device__ __forceinline__ unsigned long long f3_pair(float v) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ void f3_update_bin(float2& R, float2 Wm, float2 Wp, float q,
+                                              unsigned long long npp) {
+  asm("{\n\t.reg .b64 m, w, s, d, r;\n\t.reg .f32 dx, dy, rx, ry;\n\t"
+      "mov.b64 m, {%2, %3};\n\tmov.b64 w, {%4, %5};\n\t"
+      "add.rn.f32x2 s, m, w;\n\tsub.rn.f32x2 d, m, w;\n\t"
+      "mov.b64 {dx, dy}, d;\n\t"
+      "fma.rn.f32 rx, %6, dy, %0;\n\tfma.rn.f32 ry, %7, dx, %1;\n\t"
+      "mov.b64 r, {rx, ry};\n\tfma.rn.f32x2 r, %8, s, r;\n\t"
+      "mov.b64 {%0, %1}, r;\n\t}"
+      : "+f"(R.x), "+f"(R.y)
+      : "f"(Wm.x), "f"(Wm.y), "f"(Wp.x), "f"(Wp.y), "f"(q), "f"(-q), "l"(npp));
+}
+// the same for a self-conjugate u (c real): R = fma(-p, Wm, R)
+__device__ __forceinline__ void f3_update_bin_sc(float2& R, float2 Wm, unsigned long long npp) {
+  asm("{\n\t.reg .b64 m, r;\n\tmov.b64 m, {%2, %3};\n\tmov.b64 r, {%0, %1};\n\t"
+      "fma.rn.f32x2 r, %4, m, r;\n\tmov.b64 {%0, %1}, r;\n\t}"
+      : "+f"(R.x), "+f"(R.y)
+      : "f"(Wm.x), "f"(Wm.y), "l"(npp));
+}
+
 // 2^s with bound * 2^s < 2^62 and s <= 126 (bound finite, >= 0)
 __device__ __forceinline__ int fx_shift(float bound) {
   const int eb = (__float_as_int(bound) >> 23) & 0xff;  // bound < 2^(eb - 126)
@@ -793,6 +825,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
         const int bpl = (rp | ((ct + wk2) & (T - 1))) << 3, bph = (rp | ((chi + wk2) & (T - 1))) << 3;
         const int bmi = rt > 0 ? bmh : bml, bpi = rt > 0 ? bph : bpl;
         unsigned k1a = 0u, k2a = 0u, k1b = 0u, k2b = 0u;  // two key chains (even / odd bins)
+        const unsigned long long npp = f3_pair(-p);
         if (!sc) {
 #pragma unroll
           for (int i = 0; i < NB; ++i) {
@@ -800,9 +833,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
             const int bp = i < IB ? bpl : (i == IB ? bpi : bph);
             const float2 Wm = *reinterpret_cast<const float2*>(wb8 + ((bm + i * STEP8) & MSK8));
             const float2 Wp = *reinterpret_cast<const float2*>(wb8 + ((bp + i * STEP8) & MSK8));
-            const float a = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
-            R32[i].x = __fmaf_rn(-p, a, __fmaf_rn(q, bb, R32[i].x));
-            R32[i].y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, R32[i].y));
+            f3_update_bin(R32[i], Wm, Wp, q, npp);
             if (kTwoChains && (i & 1)) key_insert(k1b, k2b, m32(R32[i]), i);
             else key_insert(k1a, k2a, m32(R32[i]), i);
           }
@@ -811,8 +842,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           for (int i = 0; i < NB; ++i) {
             const int bm = i < IB ? bml : (i == IB ? bmi : bmh);
             const float2 Wm = *reinterpret_cast<const float2*>(wb8 + ((bm + i * STEP8) & MSK8));
-            R32[i].x = __fmaf_rn(-p, Wm.x, R32[i].x);
-            R32[i].y = __fmaf_rn(-p, Wm.y, R32[i].y);
+            f3_update_bin_sc(R32[i], Wm, npp);
             if (kTwoChains && (i & 1)) key_insert(k1b, k2b, m32(R32[i]), i);
             else key_insert(k1a, k2a, m32(R32[i]), i);
           }
@@ -868,6 +898,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
       const int bpl = (rp | ((ct + wk2) & (T - 1))) << 3, bph = (rp | ((chi + wk2) & (T - 1))) << 3;
       const int bmi = rt > 0 ? bmh : bml, bpi = rt > 0 ? bph : bpl;
       unsigned k1a = 0u, k2a = 0u, k1b = 0u, k2b = 0u;  // two key chains (even / odd bins)
+      const unsigned long long npp = f3_pair(-p);
       if (!sc) {
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
@@ -875,9 +906,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           const int bp = i < IB ? bpl : (i == IB ? bpi : bph);
           const float2 Wm = *reinterpret_cast<const float2*>(wb8 + ((bm + i * STEP8) & MSK8));
           const float2 Wp = *reinterpret_cast<const float2*>(wb8 + ((bp + i * STEP8) & MSK8));
-          const float a = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
-          R32[i].x = __fmaf_rn(-p, a, __fmaf_rn(q, bb, R32[i].x));
-          R32[i].y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, R32[i].y));
+          f3_update_bin(R32[i], Wm, Wp, q, npp);
           if (kTwoChains && (i & 1)) key_insert(k1b, k2b, m32(R32[i]), i);
             else key_insert(k1a, k2a, m32(R32[i]), i);
         }
@@ -886,8 +915,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
         for (int i = 0; i < NB; ++i) {
           const int bm = i < IB ? bml : (i == IB ? bmi : bmh);
           const float2 Wm = *reinterpret_cast<const float2*>(wb8 + ((bm + i * STEP8) & MSK8));
-          R32[i].x = __fmaf_rn(-p, Wm.x, R32[i].x);
-          R32[i].y = __fmaf_rn(-p, Wm.y, R32[i].y);
+          f3_update_bin_sc(R32[i], Wm, npp);
           if (kTwoChains && (i & 1)) key_insert(k1b, k2b, m32(R32[i]), i);
             else key_insert(k1a, k2a, m32(R32[i]), i);
         }

@@ -28,6 +28,11 @@ struct PlanTables {
   const float4* syn_ff;   // T: (cos.h, sin.h, cos.l, sin.l)(2 pi p / T)
   const double* dist;     // Ls*Ls: distance to the centre of B (Eq. 15)
   const float2* dct_cos_ff;  // 4T: cos(2 pi p / (4T)) as (hi, lo), the DCT basis' phases
+  // nullable: the DCT basis' product table C (rows 0 .. 2T-2 of 2T (hi, lo)
+  // pairs) of the complete support -- every sample of L outside B (and inside
+  // the causal shape where that support is set) usable -- for the plan's own
+  // rho; blocks whose support is complete copy it instead of rebuilding it
+  const float2* dct_c_full;
 };
 
 struct PlanDev {
@@ -137,6 +142,10 @@ int forward_f3_variant_count(const PlanDev& p);
 cudaError_t launch_forward_dct(const FwdArgs& a, cudaStream_t stream);
 cudaError_t launch_backward_dct(const BwdArgs& a, cudaStream_t stream);
 int forward_dct_variant_count(const PlanDev& p);
+// Elements (float2) of the DCT table C for fft_size T, and its build for the
+// complete support of plan p into `out` (one CTA, queued on s).
+size_t dct_table_elems(int T);
+cudaError_t build_dct_table(const PlanDev& p, float2* out, cudaStream_t s);
 // The same kernel with OFSE's compensation (fofse_ofse.cu); one launch shape.
 cudaError_t launch_forward_ofse(const FwdArgs& a, const CUtensorMap* tm_frame,
                                 const CUtensorMap* tm_avail, cudaStream_t stream);

@@ -118,6 +118,35 @@ def test_dct_long_run_and_device_values():
     assert torch.equal(own.trace, dev.trace)
 
 
+def test_dct_shared_table_equals_the_per_block_table():
+    """1080p batch: blocks with a complete support copy the plan's shared table
+    C; a call with device-side (rho, gamma) builds C in every block.  Both give
+    the same blocks and trace bit for bit, and the batch has complete blocks."""
+    import torch
+    from paper_2207_01205_gb300 import api, binding
+    wl = _dct(synth.frame_concealment())
+    spec = wl.plans[0]
+    Ls = spec.block + 2 * spec.border
+    full = 0
+    for y, x, _ in wl.blocks:
+        y0, x0 = y - spec.border, x - spec.border
+        if y0 < 0 or x0 < 0 or y0 + Ls > wl.avail.shape[0] or x0 + Ls > wl.avail.shape[1]:
+            continue
+        a = wl.avail[y0:y0 + Ls, x0:x0 + Ls].astype(bool).copy()
+        a[spec.border:spec.border + spec.block, spec.border:spec.border + spec.block] = True
+        full += bool(a.all())
+    assert full >= 100, full
+    fr, av, bl = to_device(wl)
+    own = api.extrapolate([api.Plan.from_spec(spec)], bl, fr, av)
+    other = api.Plan(spec.block, spec.border, spec.fft_size, 0.6, 0.3, spec.iters, 0, "fp32", 0, 1)
+    rg = torch.tensor([[spec.rho, spec.gamma]], dtype=torch.float32, device="cuda")
+    dev = api.extrapolate([other], bl, fr, av, rho_gamma=rg)
+    torch.cuda.synchronize()
+    binding.fofse_check()
+    assert torch.equal(own.blocks, dev.blocks)
+    assert torch.equal(own.trace, dev.trace)
+
+
 def test_dct_empty_batch_is_a_no_op():
     import torch
     from paper_2207_01205_gb300 import api, binding
