@@ -45,10 +45,13 @@ L2_FLUSH_BYTES = 512 << 20
 # the run's trace.
 OPS_PER_BIN_ITER = 14
 # DRAM bytes of one launch of the product kernel on the 1080p batch, launch
-# shape 0, from an ncu capture (dram__bytes_read.sum 9.21 MB +
-# dram__bytes_write.sum 65.46 MB: the write-back of the per-CTA scratch, not
-# algorithmic bytes; the kernel is ALU-bound)
-F3_TRAFFIC_BYTES_1080P = 74.67e6
+# shape 0, from an ncu capture of the current kernel (dram__bytes_read.sum
+# 9.44 MB + dram__bytes_write.sum 65.60 MB: mostly the write-back of the
+# per-CTA scratch, not algorithmic bytes)
+F3_TRAFFIC_BYTES_1080P = 75.04e6
+# the same for the FP32 volume kernel on the three-frame 1080p batch, launch
+# shape 0 (None until an ncu capture of the current kernel is recorded)
+V3_TRAFFIC_BYTES_1080P = None
 SMEM_BYTES_PER_BIN_ITER = 16
 OPS_PER_RECURRENCE_TERM = 66
 FP32_LANES_PER_SM = 128
@@ -588,7 +591,9 @@ def run_volume_workload(args, rank, world, local):
     smem_bytes = n_ok * spec.iters * canon * SMEM_BYTES_PER_BIN_ITER
     smem_peak = sms * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6
     roofline = {"bound": "smem", "achieved": smem_bytes / (ms * 1e-3) / 1e9, "peak": smem_peak / 1e9,
-                "unit": "GB/s", "frac": smem_bytes / (ms * 1e-3) / smem_peak, "traffic": None,
+                "unit": "GB/s", "frac": smem_bytes / (ms * 1e-3) / smem_peak,
+                "traffic": V3_TRAFFIC_BYTES_1080P if tuned is None or tuned["choice"] == 0 else None,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "kernel": f"fofse_volume_f32_kernel<{spec.fft_size},{spec.fft_time},...> "
                           f"(launch shape {tuned['choice'] if tuned else 0})",
                 "work_per_launch": f"{smem_bytes:.4g} B = {n_ok} blocks x {spec.iters} it x {canon} "

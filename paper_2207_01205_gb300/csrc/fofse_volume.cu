@@ -501,6 +501,7 @@ bool volume32_grid_supported(int T, int Tt) {
 
 // The valid launch shapes of a grid, in the order of their variant numbers.
 template <int T, int TT, class F> cudaError_t volume32_shape(int variant, F&& f) {
+  static_assert(V3Shape<T, TT, 0>::valid, "shape 0 exists on every grid");
   int v = 0;
   if (variant == v++) return f(VariantV3<T, TT, 0>());
   if constexpr (V3Shape<T, TT, 1>::valid)

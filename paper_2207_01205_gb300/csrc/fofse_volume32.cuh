@@ -61,7 +61,7 @@ template <int T, int TT, int NT> struct V3 {
   static constexpr int NB = NB2 * TT;      // held bins per thread (threads 0, 1: + TT extras)
   static constexpr int RS = 2 * NT / T;    // rows between a thread's consecutive 2-D bins
   static constexpr int IB = NB2 / 2;       // the 2-D bin whose row is T/2 + r_t
-  static constexpr int LIST = 32;          // near-tie candidates per pass
+  static constexpr int LIST = 16;          // near-tie candidates per pass
   // packed index of a bin for the exact terms: k2 | k1 << (LOGT + 1) | k3 << (2 LOGT + 2),
   // one guard bit above each field so that componentwise differences and sums
   // are one add and one AND
@@ -69,6 +69,7 @@ template <int T, int TT, int NT> struct V3 {
   static constexpr int PM = ((TT - 1) << SH3) | ((T - 1) << SH1) | (T - 1);
   static constexpr int PG = (TT << SH3) | (T << SH1) | T;
   static_assert((1 << LOGT) == T && (1 << LOGTT) == TT && NB2 >= 2 && NB <= 32 && NB + TT <= 127 &&
+                    PM <= 0xFFFF &&
                     NW <= 32,
                 "grid");
   // shared memory, bytes from a 128-aligned base
@@ -81,7 +82,7 @@ template <int T, int TT, int NT> struct V3 {
   static constexpr size_t nd_off = ww_off + 24 * NW;                // int
   static constexpr size_t trc_off = (nd_off + 4 + 15) & ~size_t(15);  // float4 [iters]
   __host__ __device__ static size_t try_off(int iters) { return trc_off + 16 * (size_t)iters; }
-  __host__ __device__ static size_t bytes(int iters) { return 128 + try_off(iters) + 4 * (size_t)iters; }
+  __host__ __device__ static size_t bytes(int iters) { return 128 + try_off(iters) + 2 * (size_t)iters; }
   // per-CTA global scratch: the 3-D packed transform, then the exact W
   // ([k3][k1] rows of 2T float2: hi plane, lo plane), and R0 per held bin
   static constexpr size_t z_bytes = sizeof(float2) * (size_t)K * 2;
@@ -127,7 +128,7 @@ __device__ __forceinline__ ArFF::C vwex(const float2* Whi, const float2* Zg, int
 // sum over j in {j0, j0 + stride, ...} < j1 of C_j W[x - u_j] + s_j conj(C_j) W[x + u_j]
 // (float-float terms), added to sre / sim in fixed point with unit 1/scale
 template <int T, int TT, int NT>
-__device__ __forceinline__ void vrecur(const float2* Whi, const float2* Zg, const int* ty,
+__device__ __forceinline__ void vrecur(const float2* Whi, const float2* Zg, const unsigned short* ty,
                                        const float4* tc, int x, int j0, int j1, int stride,
                                        float scale, long long& sre, long long& sim) {
   using G = V3<T, TT, NT>;
@@ -183,7 +184,8 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
   int* nd_s = reinterpret_cast<int*>(dsm + G::nd_off);
   const int iters = a.iters;
   float4* trC = reinterpret_cast<float4*>(dsm + G::trc_off);
-  int* trY = reinterpret_cast<int*>(dsm + G::try_off(iters));
+  // packed indices of the recurrence's terms (16 bits hold every supported grid's)
+  unsigned short* trY = reinterpret_cast<unsigned short*>(dsm + G::try_off(iters));
   int nd = 0;
 
   const int tid = threadIdx.x;
@@ -494,7 +496,7 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
             const ff sr = ff_add(ff{o.x, o.y}, ff{cc.x, cc.y}), si = ff_add(ff{o.z, o.w}, ff{cc.z, cc.w});
             trC[pos] = make_float4(sr.h, sr.l, si.h, si.l);
           } else {
-            trY[nd] = up;
+            trY[nd] = (unsigned short)up;
             trC[nd] = cc;
           }
           const size_t o = (size_t)blk * iters + it;
@@ -627,19 +629,24 @@ __global__ void __launch_bounds__(NT, MINB) fofse_volume_f32_kernel(const __grid
 
 // Launch shapes: threads per block NT (held bins per thread NB = K / (2 NT))
 // and the minimum resident blocks per SM that the register allocation is held
-// to.  Shape 0: 16 bins per thread from 1024 bins on (one warp below); shape
-// 1: 32 bins per thread (half the threads); shape 2: 8 bins per thread (twice
-// the threads).  A shape exists where the 2-D slot grid still gives every
-// thread two rows (NB2 >= 2) and a block at least one warp.
+// to.  Shape 0: 32 bins per thread with at least two warps (measured best or
+// tied on every grid: 1.20 ms against 1.26 ms with 16 bins per thread on the
+// 32 x 32 x 4 video batch, where it fits six CTAs per SM and the 804 blocks in
+// one wave); shape 1: twice the threads; shape 2: half the threads.  A shape
+// exists where the 2-D slot grid still gives every thread two rows
+// (NB2 >= 2), a block has at least one warp and a thread at most 32 bins.
 template <int T, int TT, int V> struct V3Shape {
   static constexpr int K = T * T * TT;
-  static constexpr int NT0 = K >= 1024 ? K / 32 : 32;
-  static constexpr int NT = V == 0 ? NT0 : (V == 1 ? NT0 / 2 : NT0 * 2);
-  static constexpr bool valid = NT >= 32 && NT <= 1024 && NT <= T * T / 4 && K / (2 * NT) <= 32;
+  static constexpr int NTA = K / 64 > 64 ? K / 64 : 64;
+  static constexpr int NT = V == 0 ? NTA : (V == 1 ? NTA * 2 : NTA / 2);
+  static constexpr bool valid = NT >= 32 && NT <= 1024 && NT <= T * T / 4 && K / (2 * NT) <= 32 &&
+                                K / (2 * NT) >= 1;
   static constexpr int NB = K / (2 * NT);
-  static constexpr int REGS = 2 * NB + 112 > 255 ? 255 : 2 * NB + 112;  // register target
+  static constexpr int REGS = 2 * NB + 104 > 255 ? 255 : 2 * NB + 104;  // register target
   static constexpr int BY_REGS = 65536 / (NT * ((REGS + 7) & ~7));
-  static constexpr int BY_SMEM = (227 * 1024) / (K * 8 + 6 * 1024);
+  // the SM's 228 KB over W's plane, about 5 KB of slots and term list (200
+  // iterations) and the 1 KB the hardware reserves per CTA
+  static constexpr int BY_SMEM = 233472 / (K * 8 + 6 * 1024);
   static constexpr int MINB0 = BY_REGS < BY_SMEM ? BY_REGS : BY_SMEM;
   static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 > 8 ? 8 : MINB0);
 };
