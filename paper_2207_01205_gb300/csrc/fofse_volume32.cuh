@@ -68,7 +68,7 @@ template <int T, int TT, int NT> struct V3 {
   static constexpr int SH1 = LOGT + 1, SH3 = 2 * LOGT + 2;
   static constexpr int PM = ((TT - 1) << SH3) | ((T - 1) << SH1) | (T - 1);
   static constexpr int PG = (TT << SH3) | (T << SH1) | T;
-  static_assert((1 << LOGT) == T && (1 << LOGTT) == TT && NB2 >= 2 && NB <= 32 && NB + TT <= 127 &&
+  static_assert((1 << LOGT) == T && (1 << LOGTT) == TT && NB2 >= 2 && NB <= 32 && NT >= 2 * TT &&
                     PM <= 0xFFFF &&
                     NW <= 32,
                 "grid");
@@ -246,38 +246,43 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
   __syncthreads();
 
   // ---- 3. split: exact R0 -> scratch, FP32 copy -> registers, first top-2 ----
-  // local bin i = i2 TT + k3 (i2 < NB2), and NB + k3 for the extra 2-D bin of
-  // threads 0 and 1; "dead" bins (non-canonical members held twice) get no key
+  // local bin i = i2 TT + k3 (i2 < NB2); the 2 TT bins of the two 2-D bins
+  // outside the slot grid, (0, T/2) and (T/2, T/2), are held one per thread by
+  // threads e < 2 TT (2-D bin e & 1, k3 = e >> 1) as local bin NB.  "Dead"
+  // bins (the non-canonical member of a temporal pair held twice) get no key.
   float2 R32[NB];
-  float2 rex[TT];
+  float2 rex = make_float2(0.f, 0.f);
   unsigned m1k = 0u, m2k = 0u;
-  unsigned dead = 0u, deadx = 0u;
+  unsigned dead = 0u;
+  const bool hasx = tid < 2 * TT;
+  bool xdead = false;
+  auto split_bin = [&](int k1, int k2, int k3, int slot) -> float2 {
+    const int x = ((k3 << LOGT) | k1) * T2 + k2;
+    const int mx = ((((TT - k3) & (TT - 1)) << LOGT) | ((T - k1) & (T - 1))) * T2 + ((T - k2) & (T - 1));
+    const C za = A::load(Zg, x, T), zm = A::load(Zg, mx, T);
+    const C r = A::half(A::add(za, A::conj(zm)));
+    if (!A::finite(r)) bad = true;
+    Rx[slot] = make_float4(r.re.h, r.re.l, r.im.h, r.im.l);
+    return make_float2(r.re.h, r.im.h);
+  };
 #pragma unroll
-  for (int i2 = 0; i2 <= NB2; ++i2) {
-    if (i2 == NB2 && tid >= 2) break;
-    const int2 kk = i2 < NB2 ? f3_bin<T, NT>(tid, i2) : f3_extra<T>(tid);
+  for (int i2 = 0; i2 < NB2; ++i2) {
+    const int2 kk = f3_bin<T, NT>(tid, i2);
     const bool sc2 = (kk.x & (T / 2 - 1)) == 0 && (kk.y & (T / 2 - 1)) == 0;
 #pragma unroll
     for (int k3 = 0; k3 < TT; ++k3) {
-      const int x = ((k3 << LOGT) | kk.x) * T2 + kk.y;
-      const int mx = ((((TT - k3) & (TT - 1)) << LOGT) | ((T - kk.x) & (T - 1))) * T2 + ((T - kk.y) & (T - 1));
-      const C za = A::load(Zg, x, T), zm = A::load(Zg, mx, T);
-      const C r = A::half(A::add(za, A::conj(zm)));
-      if (!A::finite(r)) bad = true;
-      const int slot2 = i2 < NB2 ? tid + i2 * NT : NS2 + tid;
-      Rx[slot2 * TT + k3] = make_float4(r.re.h, r.re.l, r.im.h, r.im.l);
-      const float2 r32 = make_float2(r.re.h, r.im.h);
-      const bool dd = sc2 && TT > 1 && k3 > TT / 2;
-      if (i2 < NB2) {
-        R32[i2 * TT + k3] = r32;
-        if (dd) dead |= 1u << (i2 * TT + k3);
-        else key_insert(m1k, m2k, m32(r32), i2 * TT + k3);
-      } else {
-        rex[k3] = r32;
-        if (dd) deadx |= 1u << k3;
-        else key_insert(m1k, m2k, m32(r32), NB + k3);
-      }
+      const float2 r32 = split_bin(kk.x, kk.y, k3, (tid + i2 * NT) * TT + k3);
+      R32[i2 * TT + k3] = r32;
+      if (sc2 && TT > 1 && k3 > TT / 2) dead |= 1u << (i2 * TT + k3);
+      else key_insert(m1k, m2k, m32(r32), i2 * TT + k3);
     }
+  }
+  if (hasx) {
+    const int2 kk = f3_extra<T>(tid & 1);
+    const int k3 = tid >> 1;
+    rex = split_bin(kk.x, kk.y, k3, (NS2 + (tid & 1)) * TT + k3);
+    xdead = TT > 1 && k3 > TT / 2;  // both extra 2-D bins are self-conjugate
+    if (!xdead) key_insert(m1k, m2k, m32(rex), NB);
   }
   any_bad |= __syncthreads_or(bad);
   // exact W in place: W[k] = (Z[k] - conj Z[-k]) / (2 j) over the pairs (k, -k)
@@ -347,12 +352,12 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
       ffc Rt;
       if (certain) {
         const int wt = (int)g.z, li = (int)(g.x & kKeyMask);
-        const int i2 = li < NB ? li / TT : NB2, k3 = li < NB ? li % TT : li - NB;
-        const int2 kk = i2 < NB2 ? f3_bin<T, NT>(wt, i2) : f3_extra<T>(wt);
+        const int2 kk = li < NB ? f3_bin<T, NT>(wt, li / TT) : f3_extra<T>(wt & 1);
+        const int k3 = li < NB ? li % TT : wt >> 1;
         wk1 = kk.x;
         wk2 = kk.y;
         wk3 = k3;
-        const int wslot = (i2 < NB2 ? wt + i2 * NT : NS2 + wt) * TT + k3;
+        const int wslot = li < NB ? (wt + (li / TT) * NT) * TT + k3 : (NS2 + (wt & 1)) * TT + k3;
         const float4 r0 = Rx[wslot];
         long long sre = 0, sim = 0, Sr = 0, Si = 0;
         if (warp * 32 < nd) {
@@ -375,10 +380,7 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
         int cnt = 0;
 #pragma unroll
         for (int i = 0; i < NB; ++i) cnt += (!((dead >> i) & 1u) && m32(R32[i]) >= thr) ? 1 : 0;
-        if (tid < 2) {
-#pragma unroll
-          for (int k3 = 0; k3 < TT; ++k3) cnt += (!((deadx >> k3) & 1u) && m32(rex[k3]) >= thr) ? 1 : 0;
-        }
+        if (hasx && !xdead && m32(rex) >= thr) ++cnt;
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -415,17 +417,9 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
               ++r;
             }
           }
-          if (tid < 2) {
-#pragma unroll
-            for (int k3 = 0; k3 < TT; ++k3) {
-              if (!((deadx >> k3) & 1u) && m32(rex[k3]) >= thr) {
-                if (r >= pass && r < pass + LIST) {
-                  const int2 kk = f3_extra<T>(tid);
-                  list[r - pass] = cand(kk.x, kk.y, k3, (NS2 + tid) * TT + k3);
-                }
-                ++r;
-              }
-            }
+          if (hasx && !xdead && m32(rex) >= thr && r >= pass && r < pass + LIST) {
+            const int2 kk = f3_extra<T>(tid & 1);
+            list[r - pass] = cand(kk.x, kk.y, tid >> 1, (NS2 + (tid & 1)) * TT + (tid >> 1));
           }
           __syncthreads();
           const int n = min(LIST, total - pass);
@@ -523,6 +517,7 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
       const int cml = ((ct - wk2) & (T - 1)) << 3, cmh = ((chi - wk2) & (T - 1)) << 3;
       const int cpl = ((ct + wk2) & (T - 1)) << 3, cph = ((chi + wk2) & (T - 1)) << 3;
       unsigned k1a = 0u, k2a = 0u;
+      const unsigned long long npp = f3_pair(-p);
 #pragma unroll
       for (int i2 = 0; i2 < NB2; ++i2) {
         const int rowm = (rm0 + i2 * G::RS * ROWB) & (PLANEB - 1);
@@ -537,12 +532,9 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
           if (!sc) {
             const int plp = (pp0 + k3 * PLANEB) & (TT * PLANEB - 1);
             const float2 Wp = *reinterpret_cast<const float2*>(wb8 + (plp + rowp + colp));
-            const float aa = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
-            R32[i].x = __fmaf_rn(-p, aa, __fmaf_rn(q, bb, R32[i].x));
-            R32[i].y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, R32[i].y));
+            f3_update_bin(R32[i], Wm, Wp, q, npp);
           } else {
-            R32[i].x = __fmaf_rn(-p, Wm.x, R32[i].x);
-            R32[i].y = __fmaf_rn(-p, Wm.y, R32[i].y);
+            f3_update_bin_sc(R32[i], Wm, npp);
           }
           // the bins that can be dead are those of the 2-D self-conjugate
           // (k1, k2) held by thread 0 (rows 0 and T/2 of column 0)
@@ -550,22 +542,20 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
           if (!(maybe_dead && ((dead >> i) & 1u))) key_insert(k1a, k2a, m32(R32[i]), i);
         }
       }
-      if (tid < 2) {
-        const int2 kk = f3_extra<T>(tid);
-#pragma unroll
-        for (int k3 = 0; k3 < TT; ++k3) {
-          const int sm = ((((k3 - wk3) & (TT - 1)) << LOGT) | ((kk.x - wk1) & (T - 1))) * T + ((kk.y - wk2) & (T - 1));
-          const float2 Wm = Whi[sm];
-          float2 Wp = make_float2(0.f, 0.f);
-          if (!sc) {
-            const int sp = ((((k3 + wk3) & (TT - 1)) << LOGT) | ((kk.x + wk1) & (T - 1))) * T + ((kk.y + wk2) & (T - 1));
-            Wp = Whi[sp];
-          }
-          const float aa = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
-          rex[k3].x = __fmaf_rn(-p, aa, __fmaf_rn(q, bb, rex[k3].x));
-          rex[k3].y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, rex[k3].y));
-          if (!((deadx >> k3) & 1u)) key_insert(k1a, k2a, m32(rex[k3]), NB + k3);
+      if (hasx) {
+        const int2 kk = f3_extra<T>(tid & 1);
+        const int k3 = tid >> 1;
+        const int sm = ((((k3 - wk3) & (TT - 1)) << LOGT) | ((kk.x - wk1) & (T - 1))) * T + ((kk.y - wk2) & (T - 1));
+        const float2 Wm = Whi[sm];
+        float2 Wp = make_float2(0.f, 0.f);
+        if (!sc) {
+          const int sp = ((((k3 + wk3) & (TT - 1)) << LOGT) | ((kk.x + wk1) & (T - 1))) * T + ((kk.y + wk2) & (T - 1));
+          Wp = Whi[sp];
         }
+        const float aa = Wm.x + Wp.x, bb = Wm.y - Wp.y, cc = Wm.y + Wp.y, d = Wm.x - Wp.x;
+        rex.x = __fmaf_rn(-p, aa, __fmaf_rn(q, bb, rex.x));
+        rex.y = __fmaf_rn(-p, cc, __fmaf_rn(-q, d, rex.y));
+        if (!xdead) key_insert(k1a, k2a, m32(rex), NB);
       }
       m1k = k1a;
       m2k = k2a;
