@@ -48,9 +48,8 @@ template <int T> __device__ __forceinline__ bool self_conj(int u1, int u2) {
 template <int T, int NT, bool SPLIT>
 __global__ void __launch_bounds__(NT) fofse_backward_kernel(const __grid_constant__ BwdArgs args) {
   constexpr int LOGT = ilog2c(T), T2 = 2 * T, NW = NT / 32;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte slots, no TMA
+  unsigned char* smem = smem_raw;
   const PlanDev& P = args.plan;
   const int iters = P.iters;
   // split form: no synthesis table and no copy of c_i (the sample kernel

@@ -435,9 +435,8 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
 
 template <int T, int NT>
 __global__ void __launch_bounds__(NT) fofse_forward_dct_kernel(const __grid_constant__ FwdArgs args) {
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* dsm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte slots, no TMA
+  unsigned char* dsm = smem_raw;
   __shared__ int s_item;
   int next = blockIdx.x;
   for (;;) {
@@ -464,9 +463,8 @@ template <int T, int NT>
 __global__ void __launch_bounds__(NT) fofse_dct_table_kernel(const PlanDev P, float2* out) {
   using G = Dct<T, NT>;
   constexpr int TT = G::TT, S = G::S, CH = G::CH;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* dsm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte slots, no TMA
+  unsigned char* dsm = smem_raw;
   float2* ct = reinterpret_cast<float2*>(dsm);
   float2* cosT = reinterpret_cast<float2*>(dsm + G::cos_off);
   float2* wsm = reinterpret_cast<float2*>(dsm + G::chunk_off);  // [CH][T]

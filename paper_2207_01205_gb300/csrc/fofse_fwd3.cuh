@@ -1010,14 +1010,18 @@ __global__ void __launch_bounds__(NT, MINB) fofse_forward_f3_kernel(const __grid
                                                               const __grid_constant__ CUtensorMap tmF,
                                                               const __grid_constant__ CUtensorMap tmA) {
   using G = F3<T, NT>;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* dsm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  // dynamic shared memory: 16-byte alignment serves its slots; where W's
+  // plane lives there (fft_size 128) it is the TMA staging target and starts
+  // on a 128-byte boundary
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* dsm;
   float2* Whi;
   if constexpr (G::STATIC_W) {
     __shared__ __align__(128) float2 s_whi[G::STATIC_W ? T * T : 1];
     Whi = s_whi;
+    dsm = smem_raw;
   } else {
+    dsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     Whi = reinterpret_cast<float2*>(dsm);
   }
   __shared__ uint64_t mbar;

@@ -599,9 +599,8 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
 template <int T, int TT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) fofse_volume_f32_kernel(const __grid_constant__ VolArgs32 a) {
   using G = V3<T, TT, NT>;
-  extern __shared__ unsigned char smem_v32[];
-  unsigned char* dsm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_v32) + 127) & ~uintptr_t(127));
+  extern __shared__ __align__(16) unsigned char smem_v32[];  // 16-byte slots, no TMA
+  unsigned char* dsm = smem_v32;
   __shared__ int s_item;
   float2* Whi = reinterpret_cast<float2*>(dsm);
   unsigned char* slot = static_cast<unsigned char*>(a.scratch) + (size_t)blockIdx.x * G::scratch_bytes;
