@@ -293,25 +293,42 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
 
   if (st == FOFSE_BLK_OK) {
     const ff gam = IO::gamma(P);
-    // this thread's best bin by e_k R[k]^2 (exact comparison in float-float);
-    // kept up to date by the update loop below
+    // this thread's best bin by e_k R[k]^2 (exact comparison in float-float),
+    // found again after every update
     ff best = {-1.f, 0.f}, bestR = {0.f, 0.f};
     int bidx = 0x7fffffff;
-    auto consider = [&](int j) {
-      const int k1 = r0 + j * RS;
-      const float sc = (k1 > 0 ? 2.f : 1.f) * (k2 > 0 ? 2.f : 1.f);
-      const ff q = ff_two_prod(R[j].h, R[j].h);
-      const ff e2 = ff_fast_two_sum(q.h, __fmaf_rn(2.f * R[j].h, R[j].l, q.l));
-      const ff ev = {e2.h * sc, e2.l * sc};
-      const int idx = k1 * T + k2;
-      if (better(ev, idx, best, bidx)) {
-        best = ev;
-        bidx = idx;
-        bestR = R[j];
-      }
-    };
+    // the thread's best bin: every bin's value, then a pairwise tree (the
+    // order "larger value, then smaller index" is total, so the tree finds the
+    // bin a scan would, with a dependency depth of log2(NB) instead of NB)
+    auto thread_best = [&]() {
+      ff ev[NB], rv[NB];
+      int ix[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) consider(j);
+      for (int j = 0; j < NB; ++j) {
+        const int k1 = r0 + j * RS;
+        const float sc = (k1 > 0 ? 2.f : 1.f) * (k2 > 0 ? 2.f : 1.f);
+        const ff q = ff_two_prod(R[j].h, R[j].h);
+        const ff e2 = ff_fast_two_sum(q.h, __fmaf_rn(2.f * R[j].h, R[j].l, q.l));
+        ev[j] = {e2.h * sc, e2.l * sc};
+        ix[j] = k1 * T + k2;
+        rv[j] = R[j];
+      }
+#pragma unroll
+      for (int w = 1; w < NB; w *= 2) {
+#pragma unroll
+        for (int j = 0; j + w < NB; j += 2 * w) {
+          if (better(ev[j + w], ix[j + w], ev[j], ix[j])) {
+            ev[j] = ev[j + w];
+            ix[j] = ix[j + w];
+            rv[j] = rv[j + w];
+          }
+        }
+      }
+      best = ev[0];
+      bidx = ix[0];
+      bestR = rv[0];
+    };
+    thread_best();
 #pragma unroll 1
     for (int it = 0; it < iters; ++it) {
       // ---- block argmax ----
@@ -358,9 +375,6 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
       // ---- R[k] -= c/4 sum C[|k1 +- u1|, |k2 +- u2|], and the next best ----
       const ff c4 = ff_scale(cff, 0.25f);
       const int cp = k2 + u2, cm = abs(k2 - u2);
-      best = {-1.f, 0.f};
-      bestR = {0.f, 0.f};
-      bidx = 0x7fffffff;
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
         const int k1 = r0 + j * RS;
@@ -374,8 +388,8 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
         const float pe = __fmaf_rn(c4.h, lo, __fmaf_rn(c4.l, s.h, pr.l));
         const ff dd = ff_two_sum(R[j].h, -pr.h);
         R[j] = ff_fast_two_sum(dd.h, dd.l + (R[j].l - pe));
-        consider(j);
       }
+      thread_best();
     }
   }
   __syncthreads();
