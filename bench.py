@@ -632,9 +632,40 @@ def run_volume_workload(args, rank, world, local):
             "max_abs_diff_to_fp32": float((out64 - out).abs().max()),
             "fp64_frac": flops / (ms64 * 1e-3) / peak64, "probe_fp64_tflops": probe_flops / 1e12}
     del plan64
+    # backward of the squared error over B against the truth, along the frozen
+    # path (gradients w.r.t. the video samples, rho and gamma)
+    truth = np.stack([wl.truth[t, y:y + b, x:x + b] for (t, y, x) in wl.blocks]).astype(np.float64)
+    truth_dev = torch.from_numpy(truth.astype(np.float32)).to(dev)
+    fwd()
+    gblk = (2.0 * (out - truth_dev)).contiguous()
+    gvid = torch.zeros_like(video)
+    grg = torch.zeros((2,), dtype=torch.float32, device=dev)
+
+    def bwd():
+        gvid.zero_()
+        grg.zero_()
+        binding.fofse_volume_backward(plan.handle, blocks, video, avail, path, coef, w0, gblk,
+                                      status=st, grad_video=gvid, grad_rho_gamma=grg, stream=stream)
+    for _ in range(3):
+        bwd()
+    torch.cuda.synchronize(dev)
+    binding.fofse_check(stream)
+    bt = []
+    for _ in range(args.steps):
+        flush.zero_()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        bwd()
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        bt.append(b0.elapsed_time(b1))
+    bwd_ms = reduce_max(sum(bt), world, dev) / args.steps
+    fwd_bwd = {"ms_per_step": ms + bwd_ms, "blocks_per_s": world * n / ((ms + bwd_ms) * 1e-3),
+               "backward_ms": bwd_ms, "loss": "sum over B of (B_hat - f_true)^2",
+               "grads": "video samples, rho, gamma (path frozen)",
+               "kernel": "fofse_volume_backward_kernel (spatial adjoint, FP32, one CTA per block)"}
     # parity on a sample and the quality against the truth
     g = out.cpu().numpy().astype(np.float64)
-    truth = np.stack([wl.truth[t, y:y + b, x:x + b] for (t, y, x) in wl.blocks]).astype(np.float64)
     mse = float(np.mean((np.clip(g, 0, 255) - truth) ** 2))
     cpu = cpu_fd = parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -662,7 +693,7 @@ def run_volume_workload(args, rank, world, local):
                 "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": "blocks/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "psnr_db": 10 * np.log10(255.0 ** 2 / mse) if mse > 0 else None,
-                "parity_sample": parity, "roofline": roofline, "fp64_validate": fp64,
+                "parity_sample": parity, "roofline": roofline, "fwd_bwd": fwd_bwd, "fp64_validate": fp64,
                 "cpu_baseline": cpu, "cpu_transform_domain": cpu_fd, "gpu_launches": args.steps,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -226,3 +226,17 @@ def extrapolate_volume(plan, blocks, video, avail, *, with_path=True, stream=Non
     B.fofse_extrapolate_volume_batch(plan.handle, blocks, video, avail, out_blocks=out, path=path,
                                      coef=coef, w0=w0, status=status, workspace=ws, stream=stream)
     return VolumeResult(out, w0, status, path, coef)
+
+
+def volume_backward(plan, blocks, video, avail, res: VolumeResult, grad_blocks, *, stream=None):
+    """Gradients of a loss on ``res.blocks`` (its gradient ``grad_blocks``,
+    (n, b, b) float32) along the forward's frozen selection path: returns
+    (dl/dvideo with the video's layout, (dl/drho, dl/dgamma))."""
+    if res.path is None or res.coef is None:
+        raise ValueError("the forward result must carry its path and coefficients")
+    gv = torch.zeros_like(video)
+    grg = torch.zeros((2,), dtype=torch.float32, device=video.device)
+    B.fofse_volume_backward(plan.handle, blocks, video, avail, res.path, res.coef, res.w0,
+                            grad_blocks.contiguous(), status=res.status, grad_video=gv,
+                            grad_rho_gamma=grg, stream=stream)
+    return gv, grg

@@ -112,6 +112,9 @@ def _declare(L):
     L.fofse_extrapolate_volume_batch.argtypes = [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _vp, _vp,
                                                  _vp, _vp, _vp, _vp, _vp]
     L.fofse_extrapolate_volume_batch.restype = _i
+    L.fofse_volume_backward.argtypes = [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp,
+                                        _vp, _vp, _vp, _vp]
+    L.fofse_volume_backward.restype = _i
     L.fofse_check.argtypes = [_vp]
     L.fofse_check.restype = _i
     L.fofse_last_cuda_error.restype = _i
@@ -525,3 +528,52 @@ def fofse_extrapolate_volume_batch(plan, blocks, video, avail, *, out_blocks, pa
         ctypes.c_void_p(plan), _ptr(blocks), int(blocks.shape[0]), _ptr(video), _ptr(avail), F, H, W,
         pitch, _ptr(out_blocks), _ptr(path), _ptr(coef), _ptr(w0), _ptr(status), _ptr(workspace),
         _stream(stream)), "fofse_extrapolate_volume_batch")
+
+
+def fofse_volume_backward(plan, blocks, video, avail, path, coef, w0, grad_blocks, *, status=None,
+                          grad_video=None, grad_rho_gamma=None, stream=None):
+    """Gradients of a loss on the volume batch's B_hat along the frozen path:
+    path (n, iters, 3) int32, coef (n, iters, 2) float64, w0 (n,) float64 and
+    status (n,) int32 from the forward call; grad_blocks (n, b, b) float32;
+    grad_video (F, H, W) float32 with the video's strides and grad_rho_gamma
+    (2,) float32 are accumulated into."""
+    import torch
+    n = int(blocks.shape[0])
+    # dtypes first, so that each argument's own error shows before any device check
+    for t, name, dt in ((video, "video", torch.float32), (avail, "avail", torch.uint8),
+                        (blocks, "blocks", torch.int32), (path, "path", torch.int32),
+                        (coef, "coef", torch.float64), (w0, "w0", torch.float64),
+                        (grad_blocks, "grad_blocks", torch.float32)):
+        if getattr(t, "dtype", None) != dt:
+            raise ValueError(f"{name} must be {dt}, got {getattr(t, 'dtype', type(t))}")
+    _require(video, "video", torch.float32)
+    _require(avail, "avail", torch.uint8)
+    if video.dim() != 3:
+        raise ValueError(f"video must be (frames, height, width), got {tuple(video.shape)}")
+    for t, name, dt in ((blocks, "blocks", torch.int32), (path, "path", torch.int32),
+                        (coef, "coef", torch.float64), (w0, "w0", torch.float64),
+                        (grad_blocks, "grad_blocks", torch.float32)):
+        _require(t, name, dt, (n,))
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    _require(status, "status", torch.int32, (n,), optional=True)
+    F, H, W = video.shape
+    pitch = video.stride(1)
+    if video.stride(0) != H * pitch:
+        raise ValueError("video frames must be back to back (frame stride = height * row pitch)")
+    if tuple(avail.shape) != tuple(video.shape) or tuple(avail.stride()) != tuple(video.stride()):
+        raise ValueError("avail must have the video's shape and strides")
+    if grad_video is not None:
+        _require(grad_video, "grad_video", torch.float32)
+        if tuple(grad_video.shape) != tuple(video.shape) or tuple(grad_video.stride()) != tuple(video.stride()):
+            raise ValueError("grad_video must have the video's shape and strides")
+    _require_buffer(grad_rho_gamma, "grad_rho_gamma", torch.float32, 2)
+    for t, nm in ((blocks, "blocks"), (avail, "avail"), (path, "path"), (coef, "coef"), (w0, "w0"),
+                  (grad_blocks, "grad_blocks"), (status, "status"), (grad_video, "grad_video"),
+                  (grad_rho_gamma, "grad_rho_gamma")):
+        if t is not None and t.device != video.device:
+            raise ValueError(f"{nm} is on {t.device}, the video on {video.device}")
+    _check(load().fofse_volume_backward(
+        ctypes.c_void_p(plan), _ptr(blocks), n, _ptr(video), _ptr(avail), F, H, W, pitch, _ptr(path),
+        _ptr(coef), _ptr(w0), _ptr(status), _ptr(grad_blocks), _ptr(grad_video), _ptr(grad_rho_gamma),
+        _stream(stream)), "fofse_volume_backward")

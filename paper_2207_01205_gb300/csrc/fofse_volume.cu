@@ -552,6 +552,197 @@ constexpr size_t kVolCounterBytes = 256;
 
 int volume_threads(int T, int Tt) { return T * T * Tt >= 2048 ? 512 : 256; }
 
+
+// ---------------------------------------------------------------------------
+// Backward over video volumes: the adjoint of the recursion along the frozen
+// selection path, in the spatial form (per iteration i, in reverse order,
+// with phi_i = exp(+j 2 pi (u1 m / T + u2 n / T + u3 tau / Tt)), mult_i =
+// 1 + s(u_i), c_i = gamma p_i / W0, p_i = sum_A w r_{i-1} conj(phi_i)):
+//   cbar_i = mult_i sum_L gbar conj(phi_i)         (imaginary part 0 if s = 0)
+//   gammabar += Re(conj(cbar_i) c_i) / gamma,  W0bar -= Re(conj(cbar_i) c_i) / W0
+//   pbar = gamma cbar_i / W0,  q = Re(pbar phi_i)
+//   on A:  fbar += w q,  gbar -= w q,  wbar += r_{i-1} q
+// with r_{i-1} = r_i + mult_i Re(c_i phi_i) un-built from the final residual
+// r_I = f - g_I; at the end wbar += W0bar on A, rhobar = sum_A wbar w d / rho
+// (d the distance to the centre of B; summed in FP64 with the mean distance
+// subtracted: sum_A wbar w vanishes, since B_hat does not change when w is
+// scaled).  One CTA per block; every sample of the volume L keeps its state
+// (r, gbar, sum q, wbar, w, packed position) in shared memory; FP32.
+// ---------------------------------------------------------------------------
+struct VolBwdArgs {
+  int block, border, depth, Ls, Lt, T, Tt, iters;
+  float gamma, rho;
+  const float2* wff;
+  const float2* syn;
+  const fofse_volume_block* blocks;
+  const float* video;
+  const uint8_t* avail;
+  int frames, height, width, pitch;
+  const int32_t* path;
+  const double* coef;
+  const double* w0;
+  const int32_t* status;
+  const float* grad_blocks;
+  float* grad_video;
+  float* grad_rho_gamma;
+};
+
+constexpr int kVolBwdThreads = 256;
+constexpr int kVolBwdMaxSamples = 9216;  // 24 B of state per sample: 216 KB
+// reduction slots first (double [NW], float2 [2][NW]), then the per-sample state
+size_t vol_bwd_smem(int n) { return (size_t)24 * (kVolBwdThreads / 32) + (size_t)24 * n; }
+
+__device__ __forceinline__ double vb_block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kVolBwdThreads / 32; ++w) t += red[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_backward_kernel(const __grid_constant__ VolBwdArgs a) {
+  constexpr int NT = kVolBwdThreads, NW = NT / 32;
+  extern __shared__ __align__(16) unsigned char vb_smem[];
+  const int blk = blockIdx.x;
+  if (a.status && a.status[blk] != FOFSE_BLK_OK) return;
+  const double W0d = a.w0[blk];
+  if (!(W0d > 0.0) || !isfinite(W0d)) return;
+  const int Ls = a.Ls, N = a.Lt * Ls * Ls, b = a.block, br = a.border, D = a.depth;
+  const int T = a.T, Tt = a.Tt, M = T * Tt, iters = a.iters;
+  double* redd = reinterpret_cast<double*>(vb_smem);   // [NW]
+  float2* red2 = reinterpret_cast<float2*>(redd + NW);  // [2][NW]
+  float* r = reinterpret_cast<float*>(red2 + 2 * NW);   // f - g
+  float* gb = r + N;                                    // adjoint of g
+  float* qs = gb + N;                                   // sum of q (fbar = w qs)
+  float* wb = qs + N;                                   // adjoint of w
+  float* wv = wb + N;                                   // w
+  int* pos = reinterpret_cast<int*>(wv + N);            // tau | m << 8 | n << 16
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const fofse_volume_block bd = a.blocks[blk];
+  const float W0 = (float)W0d, gamma = a.gamma;
+  const int32_t* path = a.path + (size_t)blk * iters * 3;
+  const double* coef = a.coef + (size_t)blk * iters * 2;
+  auto phase = [&](int x, int i) -> float2 {  // (cos, sin) of phi_i at sample x
+    const int pp = pos[x], tau = pp & 255, m = (pp >> 8) & 255, n = pp >> 16;
+    const int u1 = path[3 * i], u2 = path[3 * i + 1], u3 = path[3 * i + 2];
+    const int ph = (((u1 * m + u2 * n) & (T - 1)) * Tt + ((u3 * tau) & (Tt - 1)) * T) & (M - 1);
+    return __ldg(&a.syn[ph]);
+  };
+  auto mult_of = [&](int i) -> float {
+    const int u1 = path[3 * i], u2 = path[3 * i + 1], u3 = path[3 * i + 2];
+    const bool sc = (u1 & (T / 2 - 1)) == 0 && (u2 & (T / 2 - 1)) == 0 && (Tt == 1 || (u3 & (Tt / 2 - 1)) == 0);
+    return sc ? 1.f : 2.f;
+  };
+  // state: w, f - g_I (g_I = sum_i mult_i Re(c_i phi_i) over L), gbar = dl/dB on B
+  for (int x = tid; x < N; x += NT) {
+    const int tau = x / (Ls * Ls), rm = x - tau * Ls * Ls, m = rm / Ls, n = rm - m * Ls;
+    pos[x] = tau | (m << 8) | (n << 16);
+    const bool inB = tau == D && m >= br && m < br + b && n >= br && n < br + b;
+    const int ft = bd.t - D + tau, fy = bd.y - br + m, fx = bd.x - br + n;
+    float w = 0.f, f = 0.f;
+    if (!inB && ft >= 0 && ft < a.frames && fy >= 0 && fy < a.height && fx >= 0 && fx < a.width) {
+      const size_t o = ((size_t)ft * a.height + fy) * a.pitch + fx;
+      if (a.avail[o]) {
+        w = a.wff[x].x + a.wff[x].y;
+        f = a.video[o];
+      }
+    }
+    wv[x] = w;
+    r[x] = f;
+    qs[x] = 0.f;
+    wb[x] = 0.f;
+    gb[x] = inB ? a.grad_blocks[(size_t)blk * b * b + (m - br) * b + (n - br)] : 0.f;
+  }
+  __syncthreads();
+  // r_I = f - g_I
+  for (int i = 0; i < iters; ++i) {
+    const float cr = (float)coef[2 * i], ci = (float)coef[2 * i + 1], mu = mult_of(i);
+    for (int x = tid; x < N; x += NT) {
+      const float2 cs = phase(x, i);
+      r[x] -= mu * (cr * cs.x - ci * cs.y);
+    }
+  }
+  // reverse sweep: per iteration the block sum of cbar, then the update of
+  // every sample (two passes and one block reduction per iteration; merging
+  // the update with the next iteration's sum in one pass measured slower)
+  float gam_part = 0.f, w0bar = 0.f;
+  for (int i = iters - 1; i >= 0; --i) {
+    const float cr = (float)coef[2 * i], ci = (float)coef[2 * i + 1], mu = mult_of(i);
+    float2 part = make_float2(0.f, 0.f);
+    for (int x = tid; x < N; x += NT) {
+      const float2 cs = phase(x, i);
+      part.x += gb[x] * cs.x;
+      part.y -= gb[x] * cs.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+      part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+    }
+    float2* rs = red2 + (i & 1) * NW;
+    if (lane == 0) rs[warp] = part;
+    __syncthreads();
+    float2 cb = make_float2(0.f, 0.f);
+    for (int w = 0; w < NW; ++w) {
+      cb.x += rs[w].x;
+      cb.y += rs[w].y;
+    }
+    cb.x *= mu;
+    cb.y = mu > 1.f ? cb.y * mu : 0.f;
+    const float cc = cb.x * cr + cb.y * ci;  // Re(conj(cbar) c)
+    gam_part += cc / gamma;
+    w0bar -= cc / W0;
+    const float pr = gamma * cb.x / W0, pi = gamma * cb.y / W0;
+    for (int x = tid; x < N; x += NT) {
+      const float w = wv[x];
+      const float2 cs = phase(x, i);
+      const float rp = r[x] + mu * (cr * cs.x - ci * cs.y);  // r_{i-1}
+      r[x] = rp;
+      if (w != 0.f) {
+        const float q = pr * cs.x - pi * cs.y;
+        qs[x] += q;
+        gb[x] -= w * q;
+        wb[x] += rp * q;
+      }
+    }
+  }
+  // outputs: fbar into the video gradient; rho and gamma
+  double s0 = 0.0, s1 = 0.0, sd = 0.0, na = 0.0;
+  const double cen = br + (b - 1) / 2.0;
+  for (int x = tid; x < N; x += NT) {
+    const float w = wv[x];
+    if (w == 0.f) continue;
+    const int pp = pos[x], tau = pp & 255, m = (pp >> 8) & 255, n = pp >> 16;
+    if (a.grad_video) {
+      const int ft = bd.t - D + tau, fy = bd.y - br + m, fx = bd.x - br + n;
+      atomicAdd(&a.grad_video[((size_t)ft * a.height + fy) * a.pitch + fx], w * qs[x]);
+    }
+    const double dt = tau - D, dm = m - cen, dn = n - cen;
+    sd += sqrt(dt * dt + dm * dm + dn * dn);
+    na += 1.0;
+  }
+  if (!a.grad_rho_gamma) return;
+  const double nA = vb_block_sum(na, redd), dmean = nA > 0.0 ? vb_block_sum(sd, redd) / nA : 0.0;
+  for (int x = tid; x < N; x += NT) {
+    const float w = wv[x];
+    if (w == 0.f) continue;
+    const int pp = pos[x], tau = pp & 255, m = (pp >> 8) & 255, n = pp >> 16;
+    const double dt = tau - D, dm = m - cen, dn = n - cen;
+    const double d = sqrt(dt * dt + dm * dm + dn * dn);
+    const double wbar = (double)wb[x] + (double)w0bar;
+    s1 += wbar * (double)w * (d - dmean);
+    s0 += wbar * (double)w;
+  }
+  const double rho_bar = vb_block_sum(s1, redd) / (double)a.rho;
+  (void)s0;
+  if (tid == 0) {
+    atomicAdd(&a.grad_rho_gamma[0], (float)rho_bar);
+    atomicAdd(&a.grad_rho_gamma[1], gam_part);
+  }
+}
+
 }  // namespace
 }  // namespace fofse
 
@@ -750,6 +941,59 @@ fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
   a.w0 = d_w0;
   a.status = d_block_status;
   const cudaError_t e = launch_volume(plan->T, plan->Tt, a, n_blocks, s);
+  return e == cudaSuccess ? FOFSE_OK : record_cuda_error(e);
+}
+
+fofse_status fofse_volume_backward(fofse_volume_plan plan, const fofse_volume_block* d_blocks,
+                                   int n_blocks, const float* d_video, const uint8_t* d_avail,
+                                   int frames, int height, int width, int pitch,
+                                   const int32_t* d_path, const double* d_coef, const double* d_w0,
+                                   const int32_t* d_block_status, const float* d_grad_blocks,
+                                   float* d_grad_video, float* d_grad_rho_gamma, void* stream) {
+  if (!plan || n_blocks < 0 || frames < 1 || height < 1 || width < 1 || pitch < width)
+    return FOFSE_E_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return FOFSE_E_ARG;
+  const int N = plan->Lt * plan->Ls * plan->Ls;
+  if (N > kVolBwdMaxSamples || plan->Ls > 255 || plan->Lt > 255) return FOFSE_E_UNSUPPORTED;
+  if (n_blocks == 0) return FOFSE_OK;
+  if (!d_blocks || !d_video || !d_avail || !d_path || !d_coef || !d_w0 || !d_grad_blocks)
+    return FOFSE_E_ARG;
+  VolBwdArgs a;
+  a.block = plan->block;
+  a.border = plan->border;
+  a.depth = plan->depth;
+  a.Ls = plan->Ls;
+  a.Lt = plan->Lt;
+  a.T = plan->T;
+  a.Tt = plan->Tt;
+  a.iters = plan->iters;
+  a.gamma = plan->gamma;
+  a.rho = plan->rho;
+  a.wff = plan->wff;
+  a.syn = plan->syn;
+  a.blocks = d_blocks;
+  a.video = d_video;
+  a.avail = d_avail;
+  a.frames = frames;
+  a.height = height;
+  a.width = width;
+  a.pitch = pitch;
+  a.path = d_path;
+  a.coef = d_coef;
+  a.w0 = d_w0;
+  a.status = d_block_status;
+  a.grad_blocks = d_grad_blocks;
+  a.grad_video = d_grad_video;
+  a.grad_rho_gamma = d_grad_rho_gamma;
+  const size_t sm = vol_bwd_smem(N);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaFuncSetAttribute(fofse_volume_backward_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) {
+    fofse_volume_backward_kernel<<<n_blocks, kVolBwdThreads, sm, s>>>(a);
+    e = cudaGetLastError();
+  }
   return e == cudaSuccess ? FOFSE_OK : record_cuda_error(e);
 }
 

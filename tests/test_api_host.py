@@ -79,6 +79,8 @@ def test_volume_plan_arguments_are_checked_before_any_cuda_call():
     assert L.fofse_volume_workspace_bytes(None, 10) == 0
     assert L.fofse_volume_plan_variant_count(None) == 0
     assert L.fofse_volume_plan_set_variant(None, 0) == B.E_ARG
+    assert L.fofse_volume_backward(None, None, 1, None, None, 1, 1, 1, 1, None, None, None, None,
+                                   None, None, None, None) == B.E_ARG
 
 
 def test_volume_batch_rejects_host_tensors_and_wrong_dtypes():
@@ -113,3 +115,21 @@ def test_volume_batch_rejects_host_tensors_and_wrong_dtypes():
     with pytest.raises(ValueError, match="required"):
         B._require(None, "out_blocks", torch.float32)
     B._require(None, "path", torch.int32, optional=True)
+
+
+def test_volume_backward_rejects_host_tensors_and_wrong_dtypes():
+    """The backward's binding checks its tensors before the C call too."""
+    import torch
+    from paper_2207_01205_gb300 import binding as B
+    n, it = 2, 5
+    blocks = torch.zeros((n, 3), dtype=torch.int32)
+    video = torch.zeros((3, 8, 8), dtype=torch.float32)
+    avail = torch.ones((3, 8, 8), dtype=torch.uint8)
+    path = torch.zeros((n, it, 3), dtype=torch.int32)
+    coef = torch.zeros((n, it, 2), dtype=torch.float64)
+    w0 = torch.ones((n,), dtype=torch.float64)
+    gb = torch.zeros((n, 4, 4), dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA"):
+        B.fofse_volume_backward(1, blocks, video, avail, path, coef, w0, gb)
+    with pytest.raises(ValueError, match="float64"):
+        B.fofse_volume_backward(1, blocks, video, avail, path, coef.float(), w0, gb)
