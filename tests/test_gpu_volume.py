@@ -224,3 +224,25 @@ def test_every_launch_shape_gives_the_same_result(spec):
             np.testing.assert_array_equal(a, b)
     with pytest.raises(RuntimeError):
         binding.fofse_volume_plan_set_variant(plan.handle, count)
+
+
+def test_volume_autotuner_picks_a_shape_and_caches_it(tmp_path):
+    """The volume autotuner times every launch shape on the caller's batch,
+    keeps one (the default unless another is clearly faster), caches the
+    choice per GPU, grid and batch size, and the plan then runs with it."""
+    from paper_2207_01205_gb300 import autotune, binding
+    spec = PLANS[4]
+    wl = synth.small_video(17, n_frames=3, height=96, width=128, n_lost=8, plan=spec)
+    plan = api.VolumePlan.from_spec(spec)
+    args = (torch.from_numpy(wl.blocks).cuda(), torch.from_numpy(wl.video).cuda(),
+            torch.from_numpy(wl.avail).cuda())
+    ref = api.extrapolate_volume(plan, *args)
+    path = str(tmp_path / "tune.json")
+    first = autotune.autotune_volume(plan, *args, cache_path=path)
+    count = binding.fofse_volume_plan_variant_count(plan.handle)
+    assert not first["cached"] and 0 <= first["choice"] < count and len(first["timings_ms"]) == count
+    again = autotune.autotune_volume(plan, *args, cache_path=path)
+    assert again["cached"] and again["choice"] == first["choice"]
+    res = api.extrapolate_volume(plan, *args)
+    torch.cuda.synchronize()
+    assert torch.equal(res.path, ref.path) and torch.equal(res.blocks, ref.blocks)
