@@ -640,12 +640,15 @@ def run_volume_workload(args, rank, world, local):
     gblk = (2.0 * (out - truth_dev)).contiguous()
     gvid = torch.zeros_like(video)
     grg = torch.zeros((2,), dtype=torch.float32, device=dev)
+    bws = torch.empty((binding.fofse_volume_backward_workspace_bytes(plan.handle, n),),
+                      dtype=torch.uint8, device=dev)
 
     def bwd():
         gvid.zero_()
         grg.zero_()
         binding.fofse_volume_backward(plan.handle, blocks, video, avail, path, coef, w0, gblk,
-                                      status=st, grad_video=gvid, grad_rho_gamma=grg, stream=stream)
+                                      status=st, grad_video=gvid, grad_rho_gamma=grg, workspace=bws,
+                                      stream=stream)
     for _ in range(3):
         bwd()
     torch.cuda.synchronize(dev)
@@ -663,7 +666,8 @@ def run_volume_workload(args, rank, world, local):
     fwd_bwd = {"ms_per_step": ms + bwd_ms, "blocks_per_s": world * n / ((ms + bwd_ms) * 1e-3),
                "backward_ms": bwd_ms, "loss": "sum over B of (B_hat - f_true)^2",
                "grads": "video samples, rho, gamma (path frozen)",
-               "kernel": "fofse_volume_backward_kernel (spatial adjoint, FP32, one CTA per block)"}
+               "kernel": "fofse_volume_bwd_solve_kernel (W, triangular solve) + "
+                         "fofse_volume_bwd_samples_kernel (sample pass)"}
     # parity on a sample and the quality against the truth
     g = out.cpu().numpy().astype(np.float64)
     mse = float(np.mean((np.clip(g, 0, 255) - truth) ** 2))

@@ -494,13 +494,15 @@ fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
  * along the frozen selection path (not in the paper: the adjoint of the
  * recursion of fofse_extrapolate_volume_batch with every u_i fixed, as
  * fofse_backward does for images).  With p_i = sum_A w r_{i-1} conj(phi_i),
- * c_i = gamma p_i / W[0] and g_i = g_{i-1} + (1 + s(u_i)) Re(c_i phi_i), the
- * reverse sweep gives, per block, dl/df on A (w times the sum over i of
- * Re(pbar_i phi_i), pbar_i = gamma cbar_i / W[0], cbar_i = (1 + s(u_i))
- * sum_L gbar conj(phi_i)), dl/dgamma and dl/drho (through w = rho^d, d the
- * distance to the centre of B in frame `depth`).  Spatial form, FP32, one
- * CTA per block; volumes of at most 9216 samples (Lt Ls^2; FOFSE_E_UNSUPPORTED
- * above).
+ * c_i = gamma p_i / W[0], g_i = g_{i-1} + (1 + s(u_i)) Re(c_i phi_i) and
+ * W = DFT(w) on the grid, the reverse sweep is a triangular solve on W's
+ * values at the sums and differences of the path's indices (pbar_i, the
+ * adjoint of p_i, from the DFT of dl/dB_hat at u_i), then a pass over the
+ * trace per sample of A: dl/df = w sum_i Re(pbar_i phi_i), dl/dw = sum_i
+ * r_{i-1} Re(pbar_i phi_i) + dl/dW[0], dl/drho through w = rho^d (d the
+ * distance to the centre of B in frame `depth`), and dl/dgamma.  FP32 (FP64
+ * for the rho sums); two kernels (per block: W by separable DFTs and the
+ * solve; over chunks of each block's samples: the sample pass).
  *   d_blocks .. pitch    the forward call's blocks and video
  *   d_path, d_coef, d_w0 the forward call's outputs for these blocks (path
  *                        n x iters x 3 int32, coefficients n x iters x 2 FP64,
@@ -511,18 +513,23 @@ fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
  *   d_grad_video         nullable; dl/df ACCUMULATED (+=) into a buffer of
  *                        the video's layout (atomics: overlapping volumes add)
  *   d_grad_rho_gamma     nullable; 2 floats, (dl/drho, dl/dgamma) ACCUMULATED
+ *   d_workspace          fofse_volume_backward_workspace_bytes() bytes,
+ *                        caller-owned, 256-byte aligned
  * Returns FOFSE_OK once queued (n_blocks = 0 launches nothing), FOFSE_E_ARG
  * for a NULL plan or required pointer, a non-positive size or a current
- * device other than the plan's, FOFSE_E_UNSUPPORTED for volumes above 9216
- * samples, FOFSE_E_CUDA if the launch failed.  The plan's precision does not
- * matter (the coefficients are read as given).
+ * device other than the plan's, FOFSE_E_UNSUPPORTED where the solve's shared
+ * memory (8 T^2 Tt bytes of W, the row transforms of w and the per-iteration
+ * arrays) exceeds 227 KB, FOFSE_E_CUDA if a launch failed.  The plan's
+ * precision does not matter (the coefficients are read as given).
  */
+size_t fofse_volume_backward_workspace_bytes(fofse_volume_plan plan, int n_blocks);
 fofse_status fofse_volume_backward(fofse_volume_plan plan, const fofse_volume_block* d_blocks,
                                    int n_blocks, const float* d_video, const uint8_t* d_avail,
                                    int frames, int height, int width, int pitch,
                                    const int32_t* d_path, const double* d_coef, const double* d_w0,
                                    const int32_t* d_block_status, const float* d_grad_blocks,
-                                   float* d_grad_video, float* d_grad_rho_gamma, void* stream);
+                                   float* d_grad_video, float* d_grad_rho_gamma, void* d_workspace,
+                                   void* stream);
 
 /* Static, human-readable name of a status code. */
 const char* fofse_status_string(fofse_status status);

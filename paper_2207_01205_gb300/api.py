@@ -236,7 +236,10 @@ def volume_backward(plan, blocks, video, avail, res: VolumeResult, grad_blocks, 
         raise ValueError("the forward result must carry its path and coefficients")
     gv = torch.zeros_like(video)
     grg = torch.zeros((2,), dtype=torch.float32, device=video.device)
+    n = int(blocks.shape[0])
+    ws = torch.empty((B.fofse_volume_backward_workspace_bytes(plan.handle, n),), dtype=torch.uint8,
+                     device=video.device)
     B.fofse_volume_backward(plan.handle, blocks, video, avail, res.path, res.coef, res.w0,
                             grad_blocks.contiguous(), status=res.status, grad_video=gv,
-                            grad_rho_gamma=grg, stream=stream)
+                            grad_rho_gamma=grg, workspace=ws, stream=stream)
     return gv, grg

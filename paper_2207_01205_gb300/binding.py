@@ -113,8 +113,10 @@ def _declare(L):
                                                  _vp, _vp, _vp, _vp, _vp]
     L.fofse_extrapolate_volume_batch.restype = _i
     L.fofse_volume_backward.argtypes = [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp,
-                                        _vp, _vp, _vp, _vp]
+                                        _vp, _vp, _vp, _vp, _vp]
     L.fofse_volume_backward.restype = _i
+    L.fofse_volume_backward_workspace_bytes.argtypes = [_vp, _i]
+    L.fofse_volume_backward_workspace_bytes.restype = ctypes.c_size_t
     L.fofse_check.argtypes = [_vp]
     L.fofse_check.restype = _i
     L.fofse_last_cuda_error.restype = _i
@@ -530,13 +532,18 @@ def fofse_extrapolate_volume_batch(plan, blocks, video, avail, *, out_blocks, pa
         _stream(stream)), "fofse_extrapolate_volume_batch")
 
 
+def fofse_volume_backward_workspace_bytes(plan, n_blocks) -> int:
+    return load().fofse_volume_backward_workspace_bytes(ctypes.c_void_p(plan), int(n_blocks))
+
+
 def fofse_volume_backward(plan, blocks, video, avail, path, coef, w0, grad_blocks, *, status=None,
-                          grad_video=None, grad_rho_gamma=None, stream=None):
+                          grad_video=None, grad_rho_gamma=None, workspace=None, stream=None):
     """Gradients of a loss on the volume batch's B_hat along the frozen path:
     path (n, iters, 3) int32, coef (n, iters, 2) float64, w0 (n,) float64 and
     status (n,) int32 from the forward call; grad_blocks (n, b, b) float32;
     grad_video (F, H, W) float32 with the video's strides and grad_rho_gamma
-    (2,) float32 are accumulated into."""
+    (2,) float32 are accumulated into; workspace uint8 of
+    fofse_volume_backward_workspace_bytes(plan, n) bytes."""
     import torch
     n = int(blocks.shape[0])
     # dtypes first, so that each argument's own error shows before any device check
@@ -568,12 +575,13 @@ def fofse_volume_backward(plan, blocks, video, avail, path, coef, w0, grad_block
         if tuple(grad_video.shape) != tuple(video.shape) or tuple(grad_video.stride()) != tuple(video.stride()):
             raise ValueError("grad_video must have the video's shape and strides")
     _require_buffer(grad_rho_gamma, "grad_rho_gamma", torch.float32, 2)
+    _require_buffer(workspace, "workspace", torch.uint8, fofse_volume_backward_workspace_bytes(plan, n))
     for t, nm in ((blocks, "blocks"), (avail, "avail"), (path, "path"), (coef, "coef"), (w0, "w0"),
                   (grad_blocks, "grad_blocks"), (status, "status"), (grad_video, "grad_video"),
-                  (grad_rho_gamma, "grad_rho_gamma")):
+                  (grad_rho_gamma, "grad_rho_gamma"), (workspace, "workspace")):
         if t is not None and t.device != video.device:
             raise ValueError(f"{nm} is on {t.device}, the video on {video.device}")
     _check(load().fofse_volume_backward(
         ctypes.c_void_p(plan), _ptr(blocks), n, _ptr(video), _ptr(avail), F, H, W, pitch, _ptr(path),
         _ptr(coef), _ptr(w0), _ptr(status), _ptr(grad_blocks), _ptr(grad_video), _ptr(grad_rho_gamma),
-        _stream(stream)), "fofse_volume_backward")
+        _ptr(workspace), _stream(stream)), "fofse_volume_backward")

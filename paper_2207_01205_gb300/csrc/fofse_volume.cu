@@ -555,19 +555,27 @@ int volume_threads(int T, int Tt) { return T * T * Tt >= 2048 ? 512 : 256; }
 
 // ---------------------------------------------------------------------------
 // Backward over video volumes: the adjoint of the recursion along the frozen
-// selection path, in the spatial form (per iteration i, in reverse order,
-// with phi_i = exp(+j 2 pi (u1 m / T + u2 n / T + u3 tau / Tt)), mult_i =
-// 1 + s(u_i), c_i = gamma p_i / W0, p_i = sum_A w r_{i-1} conj(phi_i)):
-//   cbar_i = mult_i sum_L gbar conj(phi_i)         (imaginary part 0 if s = 0)
-//   gammabar += Re(conj(cbar_i) c_i) / gamma,  W0bar -= Re(conj(cbar_i) c_i) / W0
-//   pbar = gamma cbar_i / W0,  q = Re(pbar phi_i)
-//   on A:  fbar += w q,  gbar -= w q,  wbar += r_{i-1} q
-// with r_{i-1} = r_i + mult_i Re(c_i phi_i) un-built from the final residual
-// r_I = f - g_I; at the end wbar += W0bar on A, rhobar = sum_A wbar w d / rho
-// (d the distance to the centre of B; summed in FP64 with the mean distance
-// subtracted: sum_A wbar w vanishes, since B_hat does not change when w is
-// scaled).  One CTA per block; every sample of the volume L keeps its state
-// (r, gbar, sum q, wbar, w, packed position) in shared memory; FP32.
+// selection path, in the transform domain (as for images).  With phi_i =
+// exp(+j 2 pi (u1 m / T + u2 n / T + u3 tau / Tt)), mult_i = 1 + s(u_i),
+// c_i = gamma p_i / W0, p_i = sum_A w r_{i-1} conj(phi_i) and W[k] = sum w
+// conj(phi_k), the reverse sweep of the spatial recursion (gbar_{i-1} =
+// gbar_i - w Re(pbar_i phi_i) on A, gbar_I = dl/dB_hat on B) only needs, per
+// iteration, acc_i = sum gbar_i conj(phi_i), and acc_j for j < i changes by
+//   -1/2 (pbar_i conj(W[u_i - u_j]) + conj(pbar_i) W[u_i + u_j]),
+// a triangular solve on W's values at the path's sums and differences:
+//   acc_j = sum_B e conj(phi_j) (the DFT of e = dl/dB_hat at u_j)
+//   for i = I..1: cbar_i = mult_i acc_i (imaginary part 0 if s = 0),
+//     gammabar += Re(conj(cbar_i) c_i) / gamma, W0bar -= Re(conj(cbar_i) c_i) / W0,
+//     pbar_i = gamma cbar_i / W0, then acc_j for j < i as above.
+// A sample pass then goes over the trace per sample of A with the residual
+// rebuilt along it (r_0 = f, r_i = r_{i-1} - mult_i Re(c_i phi_i)):
+//   q_i = Re(pbar_i phi_i),  fbar = w sum_i q_i,  wbar = sum_i r_{i-1} q_i + W0bar,
+// and rhobar = sum_A wbar w d / rho (d the distance to the centre of B, summed
+// in FP64 with the mean distance subtracted: sum_A wbar w vanishes, since
+// B_hat does not change when w is scaled).  Kernel 1 (one CTA per block):
+// W in FP32 by separable DFTs of w (rows, columns, then the frames), the
+// solve; kernel 2 (CTAs over chunks of each block's samples): the sample
+// pass.  FP32, FP64 for the rho sums.
 // ---------------------------------------------------------------------------
 struct VolBwdArgs {
   int block, border, depth, Ls, Lt, T, Tt, iters;
@@ -585,12 +593,32 @@ struct VolBwdArgs {
   const float* grad_blocks;
   float* grad_video;
   float* grad_rho_gamma;
+  float2* pbar;       // workspace: n x iters
+  double* scal;       // workspace: n x 2 (W0bar, mean distance over A)
+  size_t off_y, off_ws, off_it;  // solve kernel: byte offsets of Y, w, the per-iteration arrays
+  int chunks;         // sample kernel: CTAs per block
 };
 
 constexpr int kVolBwdThreads = 256;
-constexpr int kVolBwdMaxSamples = 9216;  // 24 B of state per sample: 216 KB
-// reduction slots first (double [NW], float2 [2][NW]), then the per-sample state
-size_t vol_bwd_smem(int n) { return (size_t)24 * (kVolBwdThreads / 32) + (size_t)24 * n; }
+
+struct VolBwdLayout {  // shared memory of the solve kernel
+  size_t off_y, off_ws, off_it, bytes;
+};
+VolBwdLayout vol_bwd_layout(int T, int Tt, int Ls, int Lt, int iters) {
+  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+  VolBwdLayout L;
+  const size_t wb = (size_t)8 * T * T * Tt;            // W [k3][k1][k2] float2
+  const size_t yb = (size_t)8 * Lt * Ls * T;           // row transforms [tau][m][k2]
+  const size_t wsb = (size_t)4 * Lt * Ls * Ls;         // w of the volume
+  const size_t itb = (size_t)28 * iters;               // acc, pbar, c (float2), packed u
+  L.off_y = wb;
+  // w sits in W's frames beyond Lt (free until the DFT over the frames) when it fits
+  const bool w_in_W = Lt < Tt && (size_t)8 * (Tt - Lt) * T * T >= wsb;
+  L.off_ws = w_in_W ? (size_t)8 * Lt * T * T : al(wb + (yb > itb ? yb : itb));
+  L.off_it = wb;  // the per-iteration arrays reuse Y's region after the DFTs
+  L.bytes = w_in_W ? al(wb + (yb > itb ? yb : itb)) : al(L.off_ws + wsb);
+  return L;
+}
 
 __device__ __forceinline__ double vb_block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -599,148 +627,221 @@ __device__ __forceinline__ double vb_block_sum(double v, double* red) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double t = 0.0;
-  for (int w = 0; w < kVolBwdThreads / 32; ++w) t += red[w];
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
   return t;
 }
 
-__global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_backward_kernel(const __grid_constant__ VolBwdArgs a) {
-  constexpr int NT = kVolBwdThreads, NW = NT / 32;
+// w of a volume sample: the plan's weight where the sample is usable (in the
+// video, available, not in B), else 0
+__device__ __forceinline__ float vb_weight(const VolBwdArgs& a, const fofse_volume_block& bd, int tau,
+                                           int m, int n) {
+  const int b = a.block, br = a.border, D = a.depth, Ls = a.Ls;
+  const bool inB = tau == D && m >= br && m < br + b && n >= br && n < br + b;
+  const int ft = bd.t - D + tau, fy = bd.y - br + m, fx = bd.x - br + n;
+  if (inB || ft < 0 || ft >= a.frames || fy < 0 || fy >= a.height || fx < 0 || fx >= a.width) return 0.f;
+  if (!a.avail[((size_t)ft * a.height + fy) * a.pitch + fx]) return 0.f;
+  const float2 w = a.wff[(tau * Ls + m) * Ls + n];
+  return w.x + w.y;
+}
+
+__device__ __forceinline__ bool vb_block_ok(const VolBwdArgs& a, int blk) {
+  if (a.status && a.status[blk] != FOFSE_BLK_OK) return false;
+  const double W0 = a.w0[blk];
+  return W0 > 0.0 && isfinite(W0);
+}
+
+__global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_bwd_solve_kernel(const __grid_constant__ VolBwdArgs a) {
+  constexpr int NT = kVolBwdThreads;
   extern __shared__ __align__(16) unsigned char vb_smem[];
+  __shared__ double redd[NT / 32];
   const int blk = blockIdx.x;
-  if (a.status && a.status[blk] != FOFSE_BLK_OK) return;
-  const double W0d = a.w0[blk];
-  if (!(W0d > 0.0) || !isfinite(W0d)) return;
-  const int Ls = a.Ls, N = a.Lt * Ls * Ls, b = a.block, br = a.border, D = a.depth;
-  const int T = a.T, Tt = a.Tt, M = T * Tt, iters = a.iters;
-  double* redd = reinterpret_cast<double*>(vb_smem);   // [NW]
-  float2* red2 = reinterpret_cast<float2*>(redd + NW);  // [2][NW]
-  float* r = reinterpret_cast<float*>(red2 + 2 * NW);   // f - g
-  float* gb = r + N;                                    // adjoint of g
-  float* qs = gb + N;                                   // sum of q (fbar = w qs)
-  float* wb = qs + N;                                   // adjoint of w
-  float* wv = wb + N;                                   // w
-  int* pos = reinterpret_cast<int*>(wv + N);            // tau | m << 8 | n << 16
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (!vb_block_ok(a, blk)) return;
+  const int T = a.T, Tt = a.Tt, Ls = a.Ls, Lt = a.Lt, M = T * Tt, iters = a.iters;
+  const int b = a.block, br = a.border, D = a.depth;
+  const int tid = threadIdx.x;
   const fofse_volume_block bd = a.blocks[blk];
-  const float W0 = (float)W0d, gamma = a.gamma;
-  const int32_t* path = a.path + (size_t)blk * iters * 3;
-  const double* coef = a.coef + (size_t)blk * iters * 2;
-  auto phase = [&](int x, int i) -> float2 {  // (cos, sin) of phi_i at sample x
-    const int pp = pos[x], tau = pp & 255, m = (pp >> 8) & 255, n = pp >> 16;
-    const int u1 = path[3 * i], u2 = path[3 * i + 1], u3 = path[3 * i + 2];
-    const int ph = (((u1 * m + u2 * n) & (T - 1)) * Tt + ((u3 * tau) & (Tt - 1)) * T) & (M - 1);
-    return __ldg(&a.syn[ph]);
+  float2* Wb = reinterpret_cast<float2*>(vb_smem);                 // [k3][k1][k2]
+  float2* Y = reinterpret_cast<float2*>(vb_smem + a.off_y);        // [tau][m][k2]
+  float* ws = reinterpret_cast<float*>(vb_smem + a.off_ws);        // [tau][m][n]
+  // e^{-j 2 pi p / M} from the synthesis table (cos, sin)(2 pi p / M)
+  auto twd = [&](int p) -> float2 {
+    const float2 v = __ldg(&a.syn[p & (M - 1)]);
+    return make_float2(v.x, -v.y);
   };
-  auto mult_of = [&](int i) -> float {
-    const int u1 = path[3 * i], u2 = path[3 * i + 1], u3 = path[3 * i + 2];
-    const bool sc = (u1 & (T / 2 - 1)) == 0 && (u2 & (T / 2 - 1)) == 0 && (Tt == 1 || (u3 & (Tt / 2 - 1)) == 0);
-    return sc ? 1.f : 2.f;
-  };
-  // state: w, f - g_I (g_I = sum_i mult_i Re(c_i phi_i) over L), gbar = dl/dB on B
-  for (int x = tid; x < N; x += NT) {
+  // w of the volume, and the mean distance over A (for the rho sums of the
+  // sample pass)
+  double sd = 0.0, na = 0.0;
+  const double cen = br + (b - 1) / 2.0;
+  for (int x = tid; x < Lt * Ls * Ls; x += NT) {
     const int tau = x / (Ls * Ls), rm = x - tau * Ls * Ls, m = rm / Ls, n = rm - m * Ls;
-    pos[x] = tau | (m << 8) | (n << 16);
-    const bool inB = tau == D && m >= br && m < br + b && n >= br && n < br + b;
-    const int ft = bd.t - D + tau, fy = bd.y - br + m, fx = bd.x - br + n;
-    float w = 0.f, f = 0.f;
-    if (!inB && ft >= 0 && ft < a.frames && fy >= 0 && fy < a.height && fx >= 0 && fx < a.width) {
-      const size_t o = ((size_t)ft * a.height + fy) * a.pitch + fx;
-      if (a.avail[o]) {
-        w = a.wff[x].x + a.wff[x].y;
-        f = a.video[o];
-      }
+    const float w = vb_weight(a, bd, tau, m, n);
+    ws[x] = w;
+    if (w != 0.f) {
+      const double dt = tau - D, dmm = m - cen, dn = n - cen;
+      sd += sqrt(dt * dt + dmm * dmm + dn * dn);
+      na += 1.0;
     }
-    wv[x] = w;
-    r[x] = f;
-    qs[x] = 0.f;
-    wb[x] = 0.f;
-    gb[x] = inB ? a.grad_blocks[(size_t)blk * b * b + (m - br) * b + (n - br)] : 0.f;
+  }
+  const double nA = vb_block_sum(na, redd), sdA = vb_block_sum(sd, redd);  // (barriers)
+  // rows: Y[tau][m][k2] = sum_n w e^{-j 2 pi k2 n / T}
+  for (int e = tid; e < Lt * Ls * T; e += NT) {
+    const int k2 = e % T, tm = e / T;
+    const float* wr = ws + (size_t)tm * Ls;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int n = 0; n < Ls; ++n) {
+      const float2 t = twd(((k2 * n) & (T - 1)) * Tt);
+      acc.x += wr[n] * t.x;
+      acc.y += wr[n] * t.y;
+    }
+    Y[e] = acc;
   }
   __syncthreads();
-  // r_I = f - g_I
-  for (int i = 0; i < iters; ++i) {
-    const float cr = (float)coef[2 * i], ci = (float)coef[2 * i + 1], mu = mult_of(i);
-    for (int x = tid; x < N; x += NT) {
-      const float2 cs = phase(x, i);
-      r[x] -= mu * (cr * cs.x - ci * cs.y);
+  // columns: Z[tau][k1][k2] = sum_m Y[tau][m][k2] e^{-j 2 pi k1 m / T}, into W's frames tau < Lt
+  for (int e = tid; e < Lt * T * T; e += NT) {
+    const int k2 = e % T, k1 = (e / T) % T, tau = e / (T * T);
+    const float2* yc = Y + (size_t)tau * Ls * T + k2;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int m = 0; m < Ls; ++m) {
+      const float2 y = yc[(size_t)m * T], t = twd(((k1 * m) & (T - 1)) * Tt);
+      acc.x += y.x * t.x - y.y * t.y;
+      acc.y += y.x * t.y + y.y * t.x;
     }
+    Wb[e] = acc;
   }
-  // reverse sweep: per iteration the block sum of cbar, then the update of
-  // every sample (two passes and one block reduction per iteration; merging
-  // the update with the next iteration's sum in one pass measured slower)
-  float gam_part = 0.f, w0bar = 0.f;
-  for (int i = iters - 1; i >= 0; --i) {
-    const float cr = (float)coef[2 * i], ci = (float)coef[2 * i + 1], mu = mult_of(i);
-    float2 part = make_float2(0.f, 0.f);
-    for (int x = tid; x < N; x += NT) {
-      const float2 cs = phase(x, i);
-      part.x += gb[x] * cs.x;
-      part.y -= gb[x] * cs.y;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
-      part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
-    }
-    float2* rs = red2 + (i & 1) * NW;
-    if (lane == 0) rs[warp] = part;
-    __syncthreads();
-    float2 cb = make_float2(0.f, 0.f);
-    for (int w = 0; w < NW; ++w) {
-      cb.x += rs[w].x;
-      cb.y += rs[w].y;
-    }
-    cb.x *= mu;
-    cb.y = mu > 1.f ? cb.y * mu : 0.f;
-    const float cc = cb.x * cr + cb.y * ci;  // Re(conj(cbar) c)
-    gam_part += cc / gamma;
-    w0bar -= cc / W0;
-    const float pr = gamma * cb.x / W0, pi = gamma * cb.y / W0;
-    for (int x = tid; x < N; x += NT) {
-      const float w = wv[x];
-      const float2 cs = phase(x, i);
-      const float rp = r[x] + mu * (cr * cs.x - ci * cs.y);  // r_{i-1}
-      r[x] = rp;
-      if (w != 0.f) {
-        const float q = pr * cs.x - pi * cs.y;
-        qs[x] += q;
-        gb[x] -= w * q;
-        wb[x] += rp * q;
+  __syncthreads();
+  // frames: W[k3][k1][k2] = sum_tau Z[tau][k1][k2] e^{-j 2 pi k3 tau / Tt}, in place per column
+  for (int c = tid; c < T * T; c += NT) {
+    float2 z[8];
+#pragma unroll
+    for (int tau = 0; tau < 8; ++tau) z[tau] = tau < Lt ? Wb[(size_t)tau * T * T + c] : make_float2(0.f, 0.f);
+    for (int k3 = 0; k3 < Tt; ++k3) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int tau = 0; tau < 8; ++tau) {
+        if (tau >= Lt) break;
+        const float2 t = twd(((k3 * tau) & (Tt - 1)) * T);
+        acc.x += z[tau].x * t.x - z[tau].y * t.y;
+        acc.y += z[tau].x * t.y + z[tau].y * t.x;
       }
+      Wb[(size_t)k3 * T * T + c] = acc;
     }
   }
-  // outputs: fbar into the video gradient; rho and gamma
-  double s0 = 0.0, s1 = 0.0, sd = 0.0, na = 0.0;
-  const double cen = br + (b - 1) / 2.0;
-  for (int x = tid; x < N; x += NT) {
-    const float w = wv[x];
-    if (w == 0.f) continue;
-    const int pp = pos[x], tau = pp & 255, m = (pp >> 8) & 255, n = pp >> 16;
-    if (a.grad_video) {
-      const int ft = bd.t - D + tau, fy = bd.y - br + m, fx = bd.x - br + n;
-      atomicAdd(&a.grad_video[((size_t)ft * a.height + fy) * a.pitch + fx], w * qs[x]);
+  __syncthreads();
+  // per-iteration arrays (Y's region is free now)
+  float2* acc = reinterpret_cast<float2*>(vb_smem + a.off_it);
+  float2* pbs = acc + iters;
+  float2* cs = pbs + iters;
+  int* up = reinterpret_cast<int*>(cs + iters);
+  const int32_t* path = a.path + (size_t)blk * iters * 3;
+  const double* coef = a.coef + (size_t)blk * iters * 2;
+  // acc_i = sum_B e conj(phi_i) (phases of frame `depth`)
+  for (int i = tid; i < iters; i += NT) {
+    const int u1 = path[3 * i], u2 = path[3 * i + 1], u3 = path[3 * i + 2];
+    up[i] = u1 | (u2 << 8) | (u3 << 16);
+    cs[i] = make_float2((float)coef[2 * i], (float)coef[2 * i + 1]);
+    const int p3 = ((u3 * D) & (Tt - 1)) * T;
+    const float* e = a.grad_blocks + (size_t)blk * b * b;
+    float2 s = make_float2(0.f, 0.f);
+    for (int bm = 0; bm < b; ++bm)
+      for (int bn = 0; bn < b; ++bn) {
+        const int m = br + bm, n = br + bn;
+        const float2 t = twd(((u1 * m + u2 * n) & (T - 1)) * Tt + p3);  // conj(phi)
+        const float ev = e[bm * b + bn];
+        s.x += ev * t.x;
+        s.y += ev * t.y;
+      }
+    acc[i] = s;
+  }
+  __syncthreads();
+  const float W0 = (float)a.w0[blk], gamma = a.gamma;
+  float gam = 0.f, w0bar = 0.f;
+  for (int i = iters - 1; i >= 0; --i) {
+    const int ui = up[i], u1 = ui & 255, u2 = (ui >> 8) & 255, u3 = ui >> 16;
+    const bool sc = (u1 & (T / 2 - 1)) == 0 && (u2 & (T / 2 - 1)) == 0 && (Tt == 1 || (u3 & (Tt / 2 - 1)) == 0);
+    const float mu = sc ? 1.f : 2.f;
+    const float2 ai = acc[i], ci = cs[i];
+    const float cbr = mu * ai.x, cbi = sc ? 0.f : mu * ai.y;
+    const float cc = cbr * ci.x + cbi * ci.y;  // Re(conj(cbar) c)
+    gam += cc / gamma;
+    w0bar -= cc / W0;
+    const float pr = gamma * cbr / W0, pi = gamma * cbi / W0;
+    if (tid == 0) pbs[i] = make_float2(pr, pi);
+    for (int j = tid; j < i; j += NT) {
+      const int uj = up[j], v1 = uj & 255, v2 = (uj >> 8) & 255, v3 = uj >> 16;
+      const int dm = ((((u3 - v3) & (Tt - 1)) * T + ((u1 - v1) & (T - 1))) * T) + ((u2 - v2) & (T - 1));
+      const int dp = ((((u3 + v3) & (Tt - 1)) * T + ((u1 + v1) & (T - 1))) * T) + ((u2 + v2) & (T - 1));
+      const float2 wm = Wb[dm], wp = Wb[dp];
+      // pbar conj(wm) + conj(pbar) wp
+      const float tr = pr * wm.x + pi * wm.y + pr * wp.x + pi * wp.y;
+      const float ti = pi * wm.x - pr * wm.y + pr * wp.y - pi * wp.x;
+      float2 v = acc[j];
+      v.x -= 0.5f * tr;
+      v.y -= 0.5f * ti;
+      acc[j] = v;
     }
-    const double dt = tau - D, dm = m - cen, dn = n - cen;
-    sd += sqrt(dt * dt + dm * dm + dn * dn);
-    na += 1.0;
+    __syncthreads();
+  }
+  for (int i = tid; i < iters; i += NT) a.pbar[(size_t)blk * iters + i] = pbs[i];
+  if (tid == 0) {
+    a.scal[2 * blk] = (double)w0bar;
+    a.scal[2 * blk + 1] = nA > 0.0 ? sdA / nA : 0.0;
+    if (a.grad_rho_gamma) atomicAdd(&a.grad_rho_gamma[1], gam);
+  }
+}
+
+__global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_bwd_samples_kernel(const __grid_constant__ VolBwdArgs a) {
+  constexpr int NT = kVolBwdThreads;
+  extern __shared__ __align__(16) unsigned char vb_smem[];
+  __shared__ double redd[NT / 32];
+  const int blk = blockIdx.x;  // blockIdx.y: the chunk of the block's samples
+  if (!vb_block_ok(a, blk)) return;
+  const int T = a.T, Tt = a.Tt, Ls = a.Ls, Lt = a.Lt, M = T * Tt, iters = a.iters;
+  const int b = a.block, br = a.border, D = a.depth;
+  const int tid = threadIdx.x;
+  const fofse_volume_block bd = a.blocks[blk];
+  // per iteration: (pbar, c) and the packed index with its weight
+  float4* pc = reinterpret_cast<float4*>(vb_smem);
+  int* up = reinterpret_cast<int*>(pc + iters);
+  const int32_t* path = a.path + (size_t)blk * iters * 3;
+  const double* coef = a.coef + (size_t)blk * iters * 2;
+  for (int i = tid; i < iters; i += NT) {
+    const float2 pb = a.pbar[(size_t)blk * iters + i];
+    pc[i] = make_float4(pb.x, pb.y, (float)coef[2 * i], (float)coef[2 * i + 1]);
+    const int u1 = path[3 * i], u2 = path[3 * i + 1], u3 = path[3 * i + 2];
+    const bool sc = (u1 & (T / 2 - 1)) == 0 && (u2 & (T / 2 - 1)) == 0 && (Tt == 1 || (u3 & (Tt / 2 - 1)) == 0);
+    up[i] = u1 | (u2 << 8) | (u3 << 16) | (sc ? 0 : 1 << 24);
+  }
+  __syncthreads();
+  const int N = Lt * Ls * Ls;
+  const int x = blockIdx.y * NT + tid;
+  double s1 = 0.0;
+  if (x < N) {
+    const int tau = x / (Ls * Ls), rm = x - tau * Ls * Ls, m = rm / Ls, n = rm - m * Ls;
+    const float w = vb_weight(a, bd, tau, m, n);
+    if (w != 0.f) {
+      const int ft = bd.t - D + tau, fy = bd.y - br + m, fx = bd.x - br + n;
+      const size_t o = ((size_t)ft * a.height + fy) * a.pitch + fx;
+      float r = a.video[o], xb = 0.f, wbar = 0.f;
+      for (int i = 0; i < iters; ++i) {
+        const int ui = up[i], u1 = ui & 255, u2 = (ui >> 8) & 255, u3 = (ui >> 16) & 255;
+        const float mu = (ui >> 24) ? 2.f : 1.f;
+        const float2 t = __ldg(&a.syn[(((u1 * m + u2 * n) & (T - 1)) * Tt + ((u3 * tau) & (Tt - 1)) * T) & (M - 1)]);
+        const float4 v = pc[i];
+        const float q = v.x * t.x - v.y * t.y;
+        xb += q;
+        wbar += r * q;
+        r -= mu * (v.z * t.x - v.w * t.y);
+      }
+      if (a.grad_video) atomicAdd(&a.grad_video[o], w * xb);
+      const double cen = br + (b - 1) / 2.0;
+      const double dt = tau - D, dm = m - cen, dn = n - cen;
+      const double d = sqrt(dt * dt + dm * dm + dn * dn);
+      s1 = ((double)wbar + a.scal[2 * blk]) * (double)w * (d - a.scal[2 * blk + 1]);
+    }
   }
   if (!a.grad_rho_gamma) return;
-  const double nA = vb_block_sum(na, redd), dmean = nA > 0.0 ? vb_block_sum(sd, redd) / nA : 0.0;
-  for (int x = tid; x < N; x += NT) {
-    const float w = wv[x];
-    if (w == 0.f) continue;
-    const int pp = pos[x], tau = pp & 255, m = (pp >> 8) & 255, n = pp >> 16;
-    const double dt = tau - D, dm = m - cen, dn = n - cen;
-    const double d = sqrt(dt * dt + dm * dm + dn * dn);
-    const double wbar = (double)wb[x] + (double)w0bar;
-    s1 += wbar * (double)w * (d - dmean);
-    s0 += wbar * (double)w;
-  }
-  const double rho_bar = vb_block_sum(s1, redd) / (double)a.rho;
-  (void)s0;
-  if (tid == 0) {
-    atomicAdd(&a.grad_rho_gamma[0], (float)rho_bar);
-    atomicAdd(&a.grad_rho_gamma[1], gam_part);
-  }
+  const double s = vb_block_sum(s1, redd);
+  if (tid == 0 && s != 0.0) atomicAdd(&a.grad_rho_gamma[0], (float)(s / (double)a.rho));
 }
 
 }  // namespace
@@ -944,20 +1045,28 @@ fofse_status fofse_extrapolate_volume_batch(fofse_volume_plan plan,
   return e == cudaSuccess ? FOFSE_OK : record_cuda_error(e);
 }
 
+size_t fofse_volume_backward_workspace_bytes(fofse_volume_plan plan, int n_blocks) {
+  if (!plan || n_blocks < 0) return 0;
+  return (((size_t)8 * plan->iters * n_blocks + 255) & ~size_t(255)) + (size_t)16 * n_blocks;
+}
+
 fofse_status fofse_volume_backward(fofse_volume_plan plan, const fofse_volume_block* d_blocks,
                                    int n_blocks, const float* d_video, const uint8_t* d_avail,
                                    int frames, int height, int width, int pitch,
                                    const int32_t* d_path, const double* d_coef, const double* d_w0,
                                    const int32_t* d_block_status, const float* d_grad_blocks,
-                                   float* d_grad_video, float* d_grad_rho_gamma, void* stream) {
+                                   float* d_grad_video, float* d_grad_rho_gamma, void* d_workspace,
+                                   void* stream) {
   if (!plan || n_blocks < 0 || frames < 1 || height < 1 || width < 1 || pitch < width)
     return FOFSE_E_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return FOFSE_E_ARG;
-  const int N = plan->Lt * plan->Ls * plan->Ls;
-  if (N > kVolBwdMaxSamples || plan->Ls > 255 || plan->Lt > 255) return FOFSE_E_UNSUPPORTED;
+  const VolBwdLayout L = vol_bwd_layout(plan->T, plan->Tt, plan->Ls, plan->Lt, plan->iters);
+  const size_t sm2 = (size_t)20 * plan->iters;
+  if (L.bytes > 227 * 1024 || sm2 > 227 * 1024) return FOFSE_E_UNSUPPORTED;
   if (n_blocks == 0) return FOFSE_OK;
-  if (!d_blocks || !d_video || !d_avail || !d_path || !d_coef || !d_w0 || !d_grad_blocks)
+  if (!d_blocks || !d_video || !d_avail || !d_path || !d_coef || !d_w0 || !d_grad_blocks ||
+      !d_workspace)
     return FOFSE_E_ARG;
   VolBwdArgs a;
   a.block = plan->block;
@@ -986,12 +1095,26 @@ fofse_status fofse_volume_backward(fofse_volume_plan plan, const fofse_volume_bl
   a.grad_blocks = d_grad_blocks;
   a.grad_video = d_grad_video;
   a.grad_rho_gamma = d_grad_rho_gamma;
-  const size_t sm = vol_bwd_smem(N);
+  unsigned char* ws = static_cast<unsigned char*>(d_workspace);
+  a.pbar = reinterpret_cast<float2*>(ws);
+  a.scal = reinterpret_cast<double*>(ws + (((size_t)8 * plan->iters * n_blocks + 255) & ~size_t(255)));
+  a.off_y = L.off_y;
+  a.off_ws = L.off_ws;
+  a.off_it = L.off_it;
+  const int N = plan->Lt * plan->Ls * plan->Ls;
+  a.chunks = (N + kVolBwdThreads - 1) / kVolBwdThreads;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaFuncSetAttribute(fofse_volume_backward_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(fofse_volume_bwd_solve_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fofse_volume_bwd_samples_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   if (e == cudaSuccess) {
-    fofse_volume_backward_kernel<<<n_blocks, kVolBwdThreads, sm, s>>>(a);
+    fofse_volume_bwd_solve_kernel<<<n_blocks, kVolBwdThreads, L.bytes, s>>>(a);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    fofse_volume_bwd_samples_kernel<<<dim3(n_blocks, a.chunks), kVolBwdThreads, sm2, s>>>(a);
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? FOFSE_OK : record_cuda_error(e);

@@ -80,7 +80,8 @@ def test_volume_plan_arguments_are_checked_before_any_cuda_call():
     assert L.fofse_volume_plan_variant_count(None) == 0
     assert L.fofse_volume_plan_set_variant(None, 0) == B.E_ARG
     assert L.fofse_volume_backward(None, None, 1, None, None, 1, 1, 1, 1, None, None, None, None,
-                                   None, None, None, None) == B.E_ARG
+                                   None, None, None, None, None) == B.E_ARG
+    assert L.fofse_volume_backward_workspace_bytes(None, 10) == 0
 
 
 def test_volume_batch_rejects_host_tensors_and_wrong_dtypes():

@@ -78,7 +78,8 @@ SPECS = [
     synth.VolumePlanSpec(8, 4, 1, 16, 4, 0.8, 0.5, 40),
     synth.VolumePlanSpec(8, 4, 0, 16, 1, 0.85, 0.4, 30),
     synth.VolumePlanSpec(16, 8, 1, 32, 4, 0.8, 0.5, 60),
-    synth.VolumePlanSpec(24, 12, 1, 64, 4, 0.8, 0.5, 40),
+    synth.VolumePlanSpec(24, 12, 1, 64, 4, 0.8, 0.5, 40),   # w of the volume inside W's free frame
+    synth.VolumePlanSpec(16, 8, 3, 32, 8, 0.8, 0.5, 40),    # seven frames: w beside W
 ]
 
 
@@ -121,8 +122,10 @@ def test_1080p_video_batch_on_a_sample():
     _check(wl, wl.blocks[pick], "fp32", 9)
 
 
-def test_volumes_beyond_the_sample_limit_are_refused():
-    spec = synth.VolumePlanSpec(32, 16, 1, 64, 4, 0.8, 0.5, 10)   # 3 x 64 x 64 samples
+def test_volumes_beyond_the_shared_memory_limit_are_refused():
+    """The solve keeps W (128 KB at 64 x 64 x 4), the row transforms of w and
+    w itself in shared memory: a 3 x 64 x 64 volume needs 275 KB."""
+    spec = synth.VolumePlanSpec(32, 16, 1, 64, 4, 0.8, 0.5, 10)
     wl = synth.small_video(4, n_frames=3, height=128, width=192, n_lost=1, plan=spec)
     plan = api.VolumePlan.from_spec(spec)
     bl = torch.from_numpy(wl.blocks).cuda()
