@@ -135,3 +135,53 @@ def test_volumes_beyond_the_shared_memory_limit_are_refused():
     with pytest.raises(binding.FofseError) as ei:
         api.volume_backward(plan, bl, video, avail, res, torch.zeros_like(res.blocks))
     assert ei.value.status == binding.E_UNSUPPORTED
+
+
+def test_forward_and_backward_replay_in_a_cuda_graph():
+    """The FP32 volume forward (queue reset + one launch) and the backward (two
+    launches) captured in one CUDA graph replay the eager results bit for bit."""
+    spec = SPECS[2]
+    wl = synth.small_video(21, n_frames=3, height=96, width=128, plan=spec)
+    plan = api.VolumePlan.from_spec(spec)
+    bl = torch.from_numpy(wl.blocks).cuda()
+    video = torch.from_numpy(wl.video).cuda()
+    avail = torch.from_numpy(wl.avail).cuda()
+    n, b, it = wl.n_blocks, spec.block, spec.iters
+    ge = torch.from_numpy(np.random.default_rng(3).normal(size=(n, b, b)).astype(np.float32)).cuda()
+    eager = api.extrapolate_volume(plan, bl, video, avail)
+    egv, egrg = api.volume_backward(plan, bl, video, avail, eager, ge)
+    out = torch.empty((n, b, b), dtype=torch.float32, device="cuda")
+    path = torch.empty((n, it, 3), dtype=torch.int32, device="cuda")
+    coef = torch.empty((n, it, 2), dtype=torch.float64, device="cuda")
+    w0 = torch.empty((n,), dtype=torch.float64, device="cuda")
+    st = torch.empty((n,), dtype=torch.int32, device="cuda")
+    ws = api.volume_workspace(plan, n, "cuda")
+    bws = torch.empty((binding.fofse_volume_backward_workspace_bytes(plan.handle, n),),
+                      dtype=torch.uint8, device="cuda")
+    gv = torch.zeros_like(video)
+    grg = torch.zeros((2,), dtype=torch.float32, device="cuda")
+
+    def step(s):
+        binding.fofse_extrapolate_volume_batch(plan.handle, bl, video, avail, out_blocks=out, path=path,
+                                               coef=coef, w0=w0, status=st, workspace=ws, stream=s)
+        gv.zero_()
+        grg.zero_()
+        binding.fofse_volume_backward(plan.handle, bl, video, avail, path, coef, w0, ge, status=st,
+                                      grad_video=gv, grad_rho_gamma=grg, workspace=bws, stream=s)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up outside the capture
+        step(s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step(torch.cuda.current_stream())
+    for _ in range(2):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        binding.fofse_check()
+        assert torch.equal(out, eager.blocks) and torch.equal(path, eager.path)
+        assert torch.allclose(gv, egv, rtol=0, atol=1e-6 * float(egv.abs().max()))
+        assert torch.allclose(grg, egrg, rtol=1e-6, atol=0)
