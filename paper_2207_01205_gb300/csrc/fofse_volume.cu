@@ -595,14 +595,15 @@ struct VolBwdArgs {
   float* grad_rho_gamma;
   float2* pbar;       // workspace: n x iters
   double* scal;       // workspace: n x 2 (W0bar, mean distance over A)
-  size_t off_y, off_ws, off_it;  // solve kernel: byte offsets of Y, w, the per-iteration arrays
+  size_t off_y, off_ws, off_it, off_tw;  // solve kernel: byte offsets of Y, w, the per-iteration
+                                         // arrays and the twiddle table
   int chunks;         // sample kernel: CTAs per block
 };
 
 constexpr int kVolBwdThreads = 256;
 
 struct VolBwdLayout {  // shared memory of the solve kernel
-  size_t off_y, off_ws, off_it, bytes;
+  size_t off_y, off_ws, off_it, off_tw, bytes;
 };
 VolBwdLayout vol_bwd_layout(int T, int Tt, int Ls, int Lt, int iters) {
   auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
@@ -616,7 +617,8 @@ VolBwdLayout vol_bwd_layout(int T, int Tt, int Ls, int Lt, int iters) {
   const bool w_in_W = Lt < Tt && (size_t)8 * (Tt - Lt) * T * T >= wsb;
   L.off_ws = w_in_W ? (size_t)8 * Lt * T * T : al(wb + (yb > itb ? yb : itb));
   L.off_it = wb;  // the per-iteration arrays reuse Y's region after the DFTs
-  L.bytes = w_in_W ? al(wb + (yb > itb ? yb : itb)) : al(L.off_ws + wsb);
+  L.off_tw = w_in_W ? al(wb + (yb > itb ? yb : itb)) : al(L.off_ws + wsb);  // (cos, -sin), T Tt
+  L.bytes = L.off_tw + (size_t)8 * T * Tt;
   return L;
 }
 
@@ -663,11 +665,13 @@ __global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_bwd_solve_kernel(
   float2* Wb = reinterpret_cast<float2*>(vb_smem);                 // [k3][k1][k2]
   float2* Y = reinterpret_cast<float2*>(vb_smem + a.off_y);        // [tau][m][k2]
   float* ws = reinterpret_cast<float*>(vb_smem + a.off_ws);        // [tau][m][n]
-  // e^{-j 2 pi p / M} from the synthesis table (cos, sin)(2 pi p / M)
-  auto twd = [&](int p) -> float2 {
-    const float2 v = __ldg(&a.syn[p & (M - 1)]);
-    return make_float2(v.x, -v.y);
-  };
+  float2* tw = reinterpret_cast<float2*>(vb_smem + a.off_tw);      // e^{-j 2 pi p / M}
+  const int LT = __ffs(T) - 1;  // T and Tt are powers of two
+  for (int p = tid; p < M; p += NT) {
+    const float2 v = a.syn[p];
+    tw[p] = make_float2(v.x, -v.y);
+  }
+  auto twd = [&](int p) -> float2 { return tw[p & (M - 1)]; };
   // w of the volume, and the mean distance over A (for the rho sums of the
   // sample pass)
   double sd = 0.0, na = 0.0;
@@ -685,7 +689,7 @@ __global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_bwd_solve_kernel(
   const double nA = vb_block_sum(na, redd), sdA = vb_block_sum(sd, redd);  // (barriers)
   // rows: Y[tau][m][k2] = sum_n w e^{-j 2 pi k2 n / T}
   for (int e = tid; e < Lt * Ls * T; e += NT) {
-    const int k2 = e % T, tm = e / T;
+    const int k2 = e & (T - 1), tm = e >> LT;
     const float* wr = ws + (size_t)tm * Ls;
     float2 acc = make_float2(0.f, 0.f);
     for (int n = 0; n < Ls; ++n) {
@@ -698,7 +702,7 @@ __global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_bwd_solve_kernel(
   __syncthreads();
   // columns: Z[tau][k1][k2] = sum_m Y[tau][m][k2] e^{-j 2 pi k1 m / T}, into W's frames tau < Lt
   for (int e = tid; e < Lt * T * T; e += NT) {
-    const int k2 = e % T, k1 = (e / T) % T, tau = e / (T * T);
+    const int k2 = e & (T - 1), k1 = (e >> LT) & (T - 1), tau = e >> (2 * LT);
     const float2* yc = Y + (size_t)tau * Ls * T + k2;
     float2 acc = make_float2(0.f, 0.f);
     for (int m = 0; m < Ls; ++m) {
@@ -754,6 +758,7 @@ __global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_bwd_solve_kernel(
   }
   __syncthreads();
   const float W0 = (float)a.w0[blk], gamma = a.gamma;
+  const float iW0 = 1.f / W0, ig = 1.f / gamma, gW0 = gamma / W0;
   float gam = 0.f, w0bar = 0.f;
   for (int i = iters - 1; i >= 0; --i) {
     const int ui = up[i], u1 = ui & 255, u2 = (ui >> 8) & 255, u3 = ui >> 16;
@@ -762,9 +767,9 @@ __global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_bwd_solve_kernel(
     const float2 ai = acc[i], ci = cs[i];
     const float cbr = mu * ai.x, cbi = sc ? 0.f : mu * ai.y;
     const float cc = cbr * ci.x + cbi * ci.y;  // Re(conj(cbar) c)
-    gam += cc / gamma;
-    w0bar -= cc / W0;
-    const float pr = gamma * cbr / W0, pi = gamma * cbi / W0;
+    gam += cc * ig;
+    w0bar -= cc * iW0;
+    const float pr = gW0 * cbr, pi = gW0 * cbi;
     if (tid == 0) pbs[i] = make_float2(pr, pi);
     for (int j = tid; j < i; j += NT) {
       const int uj = up[j], v1 = uj & 255, v2 = (uj >> 8) & 255, v3 = uj >> 16;
@@ -813,32 +818,57 @@ __global__ void __launch_bounds__(kVolBwdThreads) fofse_volume_bwd_samples_kerne
   }
   __syncthreads();
   const int N = Lt * Ls * Ls;
-  const int x = blockIdx.y * NT + tid;
-  double s1 = 0.0;
-  if (x < N) {
-    const int tau = x / (Ls * Ls), rm = x - tau * Ls * Ls, m = rm / Ls, n = rm - m * Ls;
-    const float w = vb_weight(a, bd, tau, m, n);
-    if (w != 0.f) {
-      const int ft = bd.t - D + tau, fy = bd.y - br + m, fx = bd.x - br + n;
-      const size_t o = ((size_t)ft * a.height + fy) * a.pitch + fx;
-      float r = a.video[o], xb = 0.f, wbar = 0.f;
-      for (int i = 0; i < iters; ++i) {
-        const int ui = up[i], u1 = ui & 255, u2 = (ui >> 8) & 255, u3 = (ui >> 16) & 255;
-        const float mu = (ui >> 24) ? 2.f : 1.f;
-        const float2 t = __ldg(&a.syn[(((u1 * m + u2 * n) & (T - 1)) * Tt + ((u3 * tau) & (Tt - 1)) * T) & (M - 1)]);
-        const float4 v = pc[i];
-        const float q = v.x * t.x - v.y * t.y;
-        xb += q;
-        wbar += r * q;
-        r -= mu * (v.z * t.x - v.w * t.y);
+  // two samples per thread share each iteration's decode
+  int xs[2], ms[2], ns[2], ts[2];
+  float wv[2], r[2], xb[2], wbar[2];
+  size_t os[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int x = blockIdx.y * (2 * NT) + k * NT + tid;
+    xs[k] = x;
+    wv[k] = 0.f;
+    ts[k] = ms[k] = ns[k] = 0;
+    os[k] = 0;
+    r[k] = xb[k] = wbar[k] = 0.f;
+    if (x < N) {
+      const int tau = x / (Ls * Ls), rm = x - tau * Ls * Ls, m = rm / Ls, n = rm - m * Ls;
+      ts[k] = tau;
+      ms[k] = m;
+      ns[k] = n;
+      wv[k] = vb_weight(a, bd, tau, m, n);
+      if (wv[k] != 0.f) {
+        os[k] = ((size_t)(bd.t - D + tau) * a.height + (bd.y - br + m)) * a.pitch + (bd.x - br + n);
+        r[k] = a.video[os[k]];
       }
-      if (a.grad_video) atomicAdd(&a.grad_video[o], w * xb);
-      const double cen = br + (b - 1) / 2.0;
-      const double dt = tau - D, dm = m - cen, dn = n - cen;
-      const double d = sqrt(dt * dt + dm * dm + dn * dn);
-      s1 = ((double)wbar + a.scal[2 * blk]) * (double)w * (d - a.scal[2 * blk + 1]);
     }
   }
+  if (wv[0] != 0.f || wv[1] != 0.f) {
+    for (int i = 0; i < iters; ++i) {
+      const int ui = up[i], u1 = ui & 255, u2 = (ui >> 8) & 255, u3 = (ui >> 16) & 255;
+      const float mu = (ui >> 24) ? 2.f : 1.f;
+      const float4 v = pc[i];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float2 t = __ldg(&a.syn[(((u1 * ms[k] + u2 * ns[k]) & (T - 1)) * Tt +
+                                       ((u3 * ts[k]) & (Tt - 1)) * T) & (M - 1)]);
+        const float q = v.x * t.x - v.y * t.y;
+        xb[k] += q;
+        wbar[k] += r[k] * q;
+        r[k] -= mu * (v.z * t.x - v.w * t.y);
+      }
+    }
+  }
+  double s1 = 0.0;
+  const double cen = br + (b - 1) / 2.0;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (wv[k] == 0.f) continue;
+    if (a.grad_video) atomicAdd(&a.grad_video[os[k]], wv[k] * xb[k]);
+    const double dt = ts[k] - D, dm = ms[k] - cen, dn = ns[k] - cen;
+    const double d = sqrt(dt * dt + dm * dm + dn * dn);
+    s1 += ((double)wbar[k] + a.scal[2 * blk]) * (double)wv[k] * (d - a.scal[2 * blk + 1]);
+  }
+  (void)xs;
   if (!a.grad_rho_gamma) return;
   const double s = vb_block_sum(s1, redd);
   if (tid == 0 && s != 0.0) atomicAdd(&a.grad_rho_gamma[0], (float)(s / (double)a.rho));
@@ -1101,8 +1131,9 @@ fofse_status fofse_volume_backward(fofse_volume_plan plan, const fofse_volume_bl
   a.off_y = L.off_y;
   a.off_ws = L.off_ws;
   a.off_it = L.off_it;
+  a.off_tw = L.off_tw;
   const int N = plan->Lt * plan->Ls * plan->Ls;
-  a.chunks = (N + kVolBwdThreads - 1) / kVolBwdThreads;
+  a.chunks = (N + 2 * kVolBwdThreads - 1) / (2 * kVolBwdThreads);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaFuncSetAttribute(fofse_volume_bwd_solve_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
