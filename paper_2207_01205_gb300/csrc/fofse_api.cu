@@ -157,13 +157,6 @@ fofse_status cuda_fail(cudaError_t e) {
 constexpr int kMaxPlans = 64;
 constexpr size_t kCounterBytes = 256;  // one int work-queue counter per plan
 
-int sm_count() {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  return sms;
-}
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Backward workspace: abar (n x imax float2), W0bar (n floats), then the
@@ -182,13 +175,19 @@ struct BwdLayout {
 };
 
 // Device-side (rho, gamma): per plan, the three weight tables rebuilt for the
-// call sit at the start of the workspace, before the forward or backward part.
+// call (and, for a DCT plan of fft_size 32 or 64, its complete-support table
+// C for the call's rho) sit at the start of the workspace, before the forward
+// or backward part.
+size_t override_plan_bytes(const PlanDev& d) {
+  const size_t N = (size_t)d.Ls * d.Ls;
+  size_t b = align256(N * sizeof(float2)) + align256(N * sizeof(double)) + align256(N * sizeof(float));
+  if (d.basis == FOFSE_BASIS_DCT && (d.T == 32 || d.T == 64))
+    b += align256(dct_table_elems(d.T) * sizeof(float2));
+  return b;
+}
 size_t override_bytes(const fofse_plan* plans, int n_plans) {
   size_t b = 0;
-  for (int i = 0; i < n_plans; ++i) {
-    const size_t N = (size_t)plans[i]->dev.Ls * plans[i]->dev.Ls;
-    b += align256(N * sizeof(float2)) + align256(N * sizeof(double)) + align256(N * sizeof(float));
-  }
+  for (int i = 0; i < n_plans; ++i) b += override_plan_bytes(plans[i]->dev);
   return b;
 }
 
@@ -197,22 +196,26 @@ size_t override_bytes(const fofse_plan* plans, int n_plans) {
 cudaError_t apply_override(const fofse_plan* plans, int pi, const float* d_rho_gamma,
                            unsigned char* region, unsigned* err, PlanDev& P, cudaStream_t s) {
   size_t off = 0;
-  for (int i = 0; i < pi; ++i) {
-    const size_t N = (size_t)plans[i]->dev.Ls * plans[i]->dev.Ls;
-    off += align256(N * sizeof(float2)) + align256(N * sizeof(double)) + align256(N * sizeof(float));
-  }
+  for (int i = 0; i < pi; ++i) off += override_plan_bytes(plans[i]->dev);
   const size_t N = (size_t)P.Ls * P.Ls;
   float2* wff = reinterpret_cast<float2*>(region + off);
   double* w64 = reinterpret_cast<double*>(region + off + align256(N * sizeof(float2)));
   float* w32 = reinterpret_cast<float*>(region + off + align256(N * sizeof(float2)) +
                                         align256(N * sizeof(double)));
   const float* rg = d_rho_gamma + 2 * pi;
-  const cudaError_t e = launch_plan_weights(P, rg, wff, w64, w32, err, s);
+  cudaError_t e = launch_plan_weights(P, rg, wff, w64, w32, err, s);
   P.tab.w_ff = wff;
   P.tab.w_f64 = w64;
   P.tab.w_f32 = w32;
-  P.tab.dct_c_full = nullptr;  // built for the plan's own rho
+  P.tab.dct_c_full = nullptr;  // the plan's own table is for its own rho
   P.rho_gamma_dev = rg;
+  if (e == cudaSuccess && P.basis == FOFSE_BASIS_DCT && (P.T == 32 || P.T == 64)) {
+    // the complete-support table for this call's rho, by the plan's build
+    float2* tab = reinterpret_cast<float2*>(region + off + align256(N * sizeof(float2)) +
+                                            align256(N * sizeof(double)) + align256(N * sizeof(float)));
+    e = build_dct_table(P, tab, s);
+    if (e == cudaSuccess) P.tab.dct_c_full = tab;
+  }
   return e;
 }
 

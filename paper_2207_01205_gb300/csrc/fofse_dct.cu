@@ -60,9 +60,7 @@ __device__ __forceinline__ ff ff_norm(ff a) { return ff_fast_two_sum(a.h, a.l); 
 // One element of the row sums of the masked weights over n (row r of the
 // chunk), zc[r][a] = sum_n w[r][n] cos(pi a (2n+1) / (2T)), and one element of
 // C's accumulation over the chunk's rows, C[a1][a2] += sum_r cos(a1, m0 + r)
-// zc[r][a2].  The per-block setup and the build of the complete-support table
-// both use these, so a shared table equals the one a block would build, bit
-// for bit (the order of each element's sum is fixed; the split of elements
+// zc[r][a2] (the order of each element's sum is fixed; the split of elements
 // over threads does not enter).
 template <int T, class Cos>
 __device__ __forceinline__ float2 dct_row_sum(const float2* src, int a, int Ls, Cos cosv) {
@@ -168,23 +166,15 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   };
 
   // ---- setup: C and R0 by chunks of CH rows of L ----------------------------
-  // A block whose support is complete (every sample of L in the support shape
-  // and outside B usable) has the plan's shared table C: it is copied, and
-  // only R0 is summed here.
-  bool full = P.tab.dct_c_full != nullptr;
-  if (full) {
-    bool miss = false;
-    for (int e = tid; e < Ls * Ls; e += NT) {
-      const int m = e / Ls, n = e - m * Ls;
-      if (!dct_in_support(P.support, m, n, b, br)) continue;
-      const int fy = ly0 + m, fx = lx0 + n;
-      const bool in = fy >= 0 && fy < args.height && fx >= 0 && fx < args.width;
-      miss |= !(in && args.avail[(size_t)fy * args.pitch + fx]);
-    }
-    full = !__syncthreads_or(miss);
-  }
+  // C is linear in w.  With the complete-support table C_full of the plan (or
+  // of the call's rho), a block starts from C_full and subtracts the
+  // contribution of its missing samples (in the support shape, outside B, but
+  // not usable), summed over the chunks of rows that hold any: a block whose
+  // support is complete only copies the table.  Without a table, C is summed
+  // over every chunk from the usable samples.
+  const bool have_table = P.tab.dct_c_full != nullptr;
   for (int e = tid; e < 4 * T; e += NT) cosT[e] = P.tab.dct_cos_ff[e];
-  if (full) {
+  if (have_table) {
     const float4* src = reinterpret_cast<const float4*>(P.tab.dct_c_full);
     float4* dst = reinterpret_cast<float4*>(ct);
     for (int e = tid; e < TT * S / 2; e += NT) dst[e] = src[e];
@@ -195,32 +185,41 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   ff R[NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) R[j] = {0.f, 0.f};
-  bool bad = false;
+  bool bad = false, use = false;
   __syncthreads();
   for (int m0 = 0; m0 < Ls; m0 += CH) {
     const int nr = min(CH, Ls - m0);
-    // masked weights and weighted samples of rows m0 .. m0 + nr (zero beyond Ls)
+    // weights for C (with a table: the missing samples' weights, negated;
+    // else the usable samples' weights) and weighted samples of rows
+    // m0 .. m0 + nr (zero beyond Ls)
+    bool cmiss = false;
     for (int e = tid; e < CH * T; e += NT) {
       const int r = e / T, n = e - r * T, m = m0 + r;
       float2 wv = make_float2(0.f, 0.f), xv = make_float2(0.f, 0.f);
-      if (r < nr && n < Ls) {
+      if (r < nr && n < Ls && dct_in_support(P.support, m, n, b, br)) {
         const int fy = ly0 + m, fx = lx0 + n;
         const bool in = fy >= 0 && fy < args.height && fx >= 0 && fx < args.width;
-        if (in && dct_in_support(P.support, m, n, b, br) && args.avail[(size_t)fy * args.pitch + fx]) {
+        if (in && args.avail[(size_t)fy * args.pitch + fx]) {
           const float f = args.frame[(size_t)fy * args.pitch + fx];
           bad |= !isfinite(f);
+          use = true;
           ArFF::C wd;
           const ArFF::C z = IO::weighted(P.tab, m * Ls + n, f, wd);
-          wv = make_float2(wd.re.h, wd.re.l);
+          if (!have_table) wv = make_float2(wd.re.h, wd.re.l);
           xv = make_float2(z.re.h, z.re.l);
+        } else if (have_table) {
+          const float2 w = P.tab.w_ff[m * Ls + n];
+          wv = make_float2(-w.x, -w.y);
+          cmiss = true;
         }
       }
       wsm[e] = wv;
       xsm[e] = xv;
     }
-    __syncthreads();
-    // row sums over n: zc[r][a2] = sum_n w cos(a2, n) (not for a shared C),
-    // yc[r][k] = sum_n x cos(k, n)
+    // this chunk's rows change C (a barrier either way)
+    const bool full = have_table && !__syncthreads_or(cmiss);
+    // row sums over n: zc[r][a2] = sum_n w cos(a2, n) (only for chunks that
+    // change C), yc[r][k] = sum_n x cos(k, n)
     // (KB elements per thread and pass)
     constexpr int KB = 4;
     {
@@ -283,12 +282,14 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
     __syncthreads();
   }
   const int any_bad = __syncthreads_or(bad);
+  // no usable sample: C_full minus every sample's part need not round to 0
+  const int any_use = __syncthreads_or(use);
   // the chunk region now holds the trace: packed index and coefficient
   short* trU = reinterpret_cast<short*>(chunk);
   float2* trC = reinterpret_cast<float2*>(chunk + ((2 * (size_t)iters + 15) & ~size_t(15)));
   const ff W0 = {ct[0].x, ct[0].y};  // C[0,0] = sum w
   int st = FOFSE_BLK_OK;
-  if (W0.h == 0.f) st = FOFSE_BLK_NO_SUPPORT;
+  if (!any_use || W0.h == 0.f) st = FOFSE_BLK_NO_SUPPORT;
   else if (any_bad || !isfinite(W0.h)) st = FOFSE_BLK_NONFINITE;
 
   if (st == FOFSE_BLK_OK) {
@@ -470,57 +471,67 @@ __global__ void __launch_bounds__(NT) fofse_forward_dct_kernel(const __grid_cons
   }
 }
 
-// The table C of the complete support of plan P (the per-block setup's C
-// loop with every sample of L in the support shape and outside B usable), for
-// the blocks that share it; one CTA.
-template <int T, int NT>
-__global__ void __launch_bounds__(NT) fofse_dct_table_kernel(const PlanDev P, float2* out) {
-  using G = Dct<T, NT>;
-  constexpr int TT = G::TT, S = G::S, CH = G::CH;
-  extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte slots, no TMA
-  unsigned char* dsm = smem_raw;
-  float2* ct = reinterpret_cast<float2*>(dsm);
-  float2* cosT = reinterpret_cast<float2*>(dsm + G::cos_off);
-  float2* wsm = reinterpret_cast<float2*>(dsm + G::chunk_off);  // [CH][T]
-  float2* zc = wsm + 2 * CH * T;                                 // [CH][TT], as in the forward
+// The table C of the complete support of plan P (every sample of L in the
+// support shape and outside B usable): C[a1][a2] = sum_m cos(a1, m) zc[m][a2],
+// zc[m][a2] = sum_n w[m][n] cos(a2, n), in float-float.  A CTA owns DCT_TAB_A
+// columns a2 of C: it sums zc for its columns over every row m of L, then its
+// columns of C over m (renormalised every 16 rows); the padding column a2 =
+// 2T - 1 is written as 0.  The same kernel builds the plan's table and the
+// per-call table of a call with device-side (rho, gamma), so both hold the
+// same values for the same rho, bit for bit.
+constexpr int DCT_TAB_A = 4;
+constexpr int DCT_TAB_NT = 256;
+template <int T> __host__ __device__ constexpr size_t dct_table_smem() {
+  return sizeof(float2) * ((size_t)T * T + 4 * T + (size_t)T * DCT_TAB_A);
+}
+template <int T>
+__global__ void __launch_bounds__(DCT_TAB_NT) fofse_dct_table_kernel(const PlanDev P, float2* out) {
+  constexpr int TT = 2 * T - 1, S = 2 * T, A = DCT_TAB_A, NT = DCT_TAB_NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // 8-byte slots, no TMA
+  float2* wsm = reinterpret_cast<float2*>(smem_raw);  // [Ls][Ls] masked w
+  float2* cosT = wsm + T * T;                         // [4T]
+  float2* zc = cosT + 4 * T;                          // [Ls][A]
   const int tid = threadIdx.x, b = P.block, br = P.border, Ls = P.Ls;
+  const int c0 = blockIdx.x * A;
   auto cosv = [&](int a, int m) -> ff {
     const float2 v = cosT[(a * (2 * m + 1)) & (4 * T - 1)];
     return {v.x, v.y};
   };
   for (int e = tid; e < 4 * T; e += NT) cosT[e] = P.tab.dct_cos_ff[e];
-  for (int e = tid; e < TT * S; e += NT) ct[e] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int m0 = 0; m0 < Ls; m0 += CH) {
-    const int nr = min(CH, Ls - m0);
-    for (int e = tid; e < CH * T; e += NT) {
-      const int r = e / T, n = e - r * T, m = m0 + r;
-      float2 wv = make_float2(0.f, 0.f);
-      if (r < nr && n < Ls && dct_in_support(P.support, m, n, b, br)) wv = P.tab.w_ff[m * Ls + n];
-      wsm[e] = wv;
-    }
-    __syncthreads();
-    for (int e = tid; e < CH * TT; e += NT) {
-      const int r = e / TT, a = e - r * TT;
-      zc[r * TT + a] = dct_row_sum<T>(wsm + r * T, a, Ls, cosv);
-    }
-    __syncthreads();
-    for (int e = tid; e < TT * TT; e += NT) {
-      const int a1 = e / TT, a2 = e - a1 * TT;
-      ct[a1 * S + a2] = dct_c_accumulate<T>(ct[a1 * S + a2], zc, a1, a2, m0, nr, cosv);
-    }
-    __syncthreads();
+  for (int e = tid; e < Ls * Ls; e += NT) {
+    const int m = e / Ls, n = e - m * Ls;
+    wsm[e] = dct_in_support(P.support, m, n, b, br) ? P.tab.w_ff[e] : make_float2(0.f, 0.f);
   }
-  for (int e = tid; e < TT * S; e += NT) out[e] = ct[e];
+  __syncthreads();
+  for (int e = tid; e < Ls * A; e += NT) {
+    const int m = e / A, a2 = min(c0 + e % A, TT - 1);
+    zc[e] = dct_row_sum<T>(wsm + m * Ls, a2, Ls, cosv);
+  }
+  __syncthreads();
+  for (int e = tid; e < TT * A; e += NT) {
+    const int a1 = e / A, j = e - a1 * A, a2 = c0 + j;
+    if (a2 >= S) continue;
+    float2 c = make_float2(0.f, 0.f);
+    if (a2 < TT) {
+      ff acc = {0.f, 0.f};
+      for (int m0 = 0; m0 < Ls; m0 += 16) {
+        for (int m = m0; m < min(m0 + 16, Ls); ++m) {
+          const float2 v = zc[m * A + j];
+          ff_mac(acc, cosv(a1, m), ff{v.x, v.y});
+        }
+        acc = ff_norm(acc);
+      }
+      c = make_float2(acc.h, acc.l);
+    }
+    out[(size_t)a1 * S + a2] = c;
+  }
 }
 
 template <int T> cudaError_t build_dct_table_T(const PlanDev& p, float2* out, cudaStream_t s) {
-  constexpr int NT = 256;
-  const size_t sm = Dct<T, NT>::bytes(1);
-  cudaError_t e = cudaFuncSetAttribute(fofse_dct_table_kernel<T, NT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  fofse_dct_table_kernel<T, NT><<<1, NT, sm, s>>>(p, out);
+  constexpr size_t sm = dct_table_smem<T>();
+  static_assert(sm <= 48 * 1024, "table kernel shared memory");
+  constexpr int grid = (2 * T + DCT_TAB_A - 1) / DCT_TAB_A;  // the S columns of C
+  fofse_dct_table_kernel<T><<<grid, DCT_TAB_NT, sm, s>>>(p, out);
   return cudaGetLastError();
 }
 

@@ -118,10 +118,12 @@ def test_dct_long_run_and_device_values():
     assert torch.equal(own.trace, dev.trace)
 
 
-def test_dct_shared_table_equals_the_per_block_table():
-    """1080p batch: blocks with a complete support copy the plan's shared table
-    C; a call with device-side (rho, gamma) builds C in every block.  Both give
-    the same blocks and trace bit for bit, and the batch has complete blocks."""
+def test_dct_shared_table_equals_the_per_call_table():
+    """1080p batch: every block starts from the plan's complete-support table C
+    (blocks with a complete support copy it, the others subtract their missing
+    samples' part); a call with device-side (rho, gamma) builds the same table
+    for its rho.  Both give the same blocks and trace bit for bit; the batch
+    has complete and incomplete blocks, and matches the oracle's paths."""
     import torch
     from paper_2207_01205_gb300 import api, binding
     wl = _dct(synth.frame_concealment())
@@ -145,6 +147,7 @@ def test_dct_shared_table_equals_the_per_block_table():
     binding.fofse_check()
     assert torch.equal(own.blocks, dev.blocks)
     assert torch.equal(own.trace, dev.trace)
+    assert full < wl.n_blocks
 
 
 def test_dct_empty_batch_is_a_no_op():
