@@ -63,8 +63,22 @@ template <int T, int NT> struct F3 {
   static constexpr size_t nd_off = ww_off + 24 * NW;                       // int: terms in the list
   static constexpr size_t trc_off = (nd_off + 4 + 15) & ~size_t(15);       // float4 [iters]
   __host__ __device__ static size_t try_off(int iters) { return trc_off + 16 * (size_t)iters; }
+  // Where W's FP32 plane is dynamic (fft_size 128, one block per SM), the low
+  // parts of the exact W also live in shared memory when they fit, as the
+  // Hermitian half k2 <= T/2 (W[-k] = conj(W[k]) holds bit for bit in the
+  // table the setup builds), so that the recurrence reads no global memory
+  // for W.
+  static constexpr int LO_LD = T / 2 + 1;
+  static constexpr size_t lo_bytes = sizeof(float2) * (size_t)T * LO_LD;
+  __host__ __device__ static size_t lo_off(int iters) {
+    return (try_off(iters) + 2 * (((size_t)iters + 7) & ~size_t(7)) + 15) & ~size_t(15);
+  }
+  __host__ __device__ static bool lo_smem(int iters) {
+    return !STATIC_W && 128 + lo_off(iters) + lo_bytes <= 231 * 1024;
+  }
   __host__ __device__ static size_t bytes(int iters) {  // + alignment slack
-    return 128 + try_off(iters) + 2 * (((size_t)iters + 7) & ~size_t(7));
+    return 128 + (lo_smem(iters) ? lo_off(iters) + lo_bytes
+                                 : try_off(iters) + 2 * (((size_t)iters + 7) & ~size_t(7)));
   }
   // per-CTA global scratch: the packed FFT (then the exact W), exact R0 per slot
   static constexpr size_t z_bytes = sizeof(float2) * (size_t)T * 2 * T;
@@ -189,17 +203,28 @@ __device__ __forceinline__ long long redux_sum64(long long v) {
 // sum over j in {j0, j0 + stride, ...} < j1 of c_j W[k - u_j] + s_j conj(c_j) W[k + u_j]
 // (float-float terms, exact W from the global table), added to sre / sim in
 // fixed point with unit 1/scale.  HI_GLOBAL: both planes of the table are
-// read from Zg (a table without an FP32 copy in shared memory).
+// read from Zg (a table without an FP32 copy in shared memory).  Wlo: the low
+// parts as the Hermitian half in shared memory (row stride T/2 + 1), or null
+// for the global table.
 template <int T, bool HI_GLOBAL = false>
-__device__ __forceinline__ void recur_fixed(const float2* Whi, const float2* Zg, const short* ty,
-                                            const float4* tc, int x, int j0, int j1, int stride,
-                                            float scale, long long& sre, long long& sim) {
-  constexpr int LOGT = ilog2(T), M = (T - 1) * 2 * T + (T - 1);
+__device__ __forceinline__ void recur_fixed(const float2* Whi, const float2* Zg, const float2* Wlo,
+                                            const short* ty, const float4* tc, int x, int j0, int j1,
+                                            int stride, float scale, long long& sre, long long& sim) {
+  constexpr int LOGT = ilog2(T), M = (T - 1) * 2 * T + (T - 1), LD = T / 2 + 1;
   // exact W: hi part from the FP32 plane in shared memory (row stride T), lo
-  // part from the global table (two planes of row stride 2T)
+  // part from the global table (two planes of row stride 2T) or the half
+  // plane in shared memory (k2 > T/2: the conjugate of the mirror -k)
   auto wex = [&](int a) -> ArFF::C {  // a = packed a1 * 2T + a2
-    const float2 h = HI_GLOBAL ? Zg[a] : Whi[((a >> (LOGT + 1)) << LOGT) | (a & (T - 1))];
-    const float2 l = Zg[a + T];
+    const int a1 = a >> (LOGT + 1), a2 = a & (T - 1);
+    const float2 h = HI_GLOBAL ? Zg[a] : Whi[(a1 << LOGT) | a2];
+    float2 l;
+    if (Wlo) {
+      const bool mr = a2 > T / 2;
+      l = Wlo[(mr ? (T - a1) & (T - 1) : a1) * LD + (mr ? T - a2 : a2)];
+      if (mr) l.y = -l.y;
+    } else {
+      l = Zg[a + T];
+    }
     return {{h.x, l.x}, {h.y, l.y}};
   };
   // a thread's few terms are summed in float-float and converted once
@@ -397,6 +422,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   float4* trC = reinterpret_cast<float4*>(dsm + G::trc_off);
   short* trY = reinterpret_cast<short*>(dsm + G::try_off(iters));
   int* nd_s = reinterpret_cast<int*>(dsm + G::nd_off);
+  float2* Wlo = G::lo_smem(iters) ? reinterpret_cast<float2*>(dsm + G::lo_off(iters)) : nullptr;
   int nd = 0;  // entries in the list (warp 0 maintains it; the others read it each iteration)
   float2* Zg = reinterpret_cast<float2*>(cta_scratch);
   float4* Rx = reinterpret_cast<float4*>(cta_scratch + G::z_bytes);
@@ -511,6 +537,11 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   if constexpr (OFSE) build_wtab<A, T, NT, false>(Vg, nullptr);  // exact V = DFT(w^2)
   __syncthreads();
   for (int e = tid; e < T * T; e += NT) Whi[e] = Zg[(e >> LOGT) * T2 + (e & (T - 1))];
+  if (Wlo)
+    for (int e = tid; e < T * G::LO_LD; e += NT) {
+      const int r = e / G::LO_LD, c = e - r * G::LO_LD;
+      Wlo[e] = Zg[r * T2 + c + T];
+    }
   __syncthreads();
   const C W0c = A::load(Zg, 0, T);
   int st = FOFSE_BLK_OK;
@@ -599,7 +630,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           long long Sr = 0, Si = 0;
           if constexpr (NW <= 4) {
             if (warp * 32 < nd) {  // warp-uniform: this warp holds terms
-              recur_fixed<T>(Whi, Zg, trY, trC, wk1 * T2 + wk2, tid, nd, NT, scale, sre, sim);
+              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, wk1 * T2 + wk2, tid, nd, NT, scale, sre, sim);
               warp_sum64(sre, sim);
             }
             if (lane == 0) red[warp] = make_longlong2(sre, sim);
@@ -612,7 +643,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
             }
           } else {
             if (warp * 32 < nd) {
-              recur_fixed<T>(Whi, Zg, trY, trC, wk1 * T2 + wk2, tid, nd, NT, scale, sre, sim);
+              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, wk1 * T2 + wk2, tid, nd, NT, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
             }
@@ -671,7 +702,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               const int4 e = list[c];
               const float4 r0 = Rx[e.z];
               long long sre = 0, sim = 0;
-              recur_fixed<T>(Whi, Zg, trY, trC, e.x, lane, nd, 32, scale, sre, sim);
+              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, e.x, lane, nd, 32, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
               const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
@@ -728,7 +759,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           long long sre = 0, sim = 0, Sr = 0, Si = 0;
           if constexpr (NW <= 4) {
             if (warp * 32 < nd) {
-              recur_fixed<T, true>(Whi, Vg, trY, trC, xw, tid, nd, NT, scale, sre, sim);
+              recur_fixed<T, true>(Whi, Vg, nullptr, trY, trC, xw, tid, nd, NT, scale, sre, sim);
               warp_sum64(sre, sim);
             }
             if (lane == 0) red2[warp] = make_longlong2(sre, sim);
@@ -741,7 +772,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
             }
           } else {
             if (warp * 32 < nd) {
-              recur_fixed<T, true>(Whi, Vg, trY, trC, xw, tid, nd, NT, scale, sre, sim);
+              recur_fixed<T, true>(Whi, Vg, nullptr, trY, trC, xw, tid, nd, NT, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
             }
