@@ -1228,7 +1228,7 @@ def main():
                                  "precision (tests), at most 25 of 804 not matching"}
     del oplans, ows
 
-    # ---- the 2-D DCT-II basis on the same batch (all bins float-float) ----
+    # ---- the 2-D DCT-II basis on the same batch (FP32 working spectrum, exact decisions) ----
     dplans = [api.Plan.from_spec(dataclasses.replace(p, basis=1), "fp32") for p in wl.plans]
     dws = api.workspace(dplans, n, dev)
     dh = [p.handle for p in dplans]
@@ -1253,7 +1253,7 @@ def main():
         e = np.clip(bl_.cpu().numpy().astype(np.float64)[:, :16, :16], 0, 255) - truth_b
         return float(10 * np.log10(255.0 ** 2 / np.mean(e * e)))
     dct = {"ms_per_step": dt / 3, "blocks_per_s": n / (dt / 3 * 1e-3), "psnr_db": psnr_b(ob),
-           "kernel": "fofse_forward_dct_kernel<64,256> (every bin in float-float)"}
+           "kernel": "fofse_forward_dct_kernel<64,256,1> (FP32 working spectrum, exact decisions)"}
     # its backward (frozen-path adjoint of the squared error over B)
     dgf = torch.zeros_like(frame)
     dgrg = torch.zeros((len(dplans), 2), dtype=torch.float32, device=dev)

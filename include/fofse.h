@@ -152,21 +152,25 @@ fofse_status fofse_plan_set_precision(fofse_plan plan, int precision);
  * built; OFSE serves as the paper's comparison method).  It needs twice the
  * forward scratch of the constant compensation.  FOFSE_E_ARG for other values. */
 fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation);
-/* Basis (FOFSE_BASIS_*); default FOFSE_BASIS_DFT.  FOFSE_BASIS_DCT runs one
- * kernel with every bin in float-float (exact decisions), for fft_size 32 and
- * 64, precision FOFSE_FP32 or FOFSE_FP32_FULLFF and the constant compensation
- * (the batch calls return FOFSE_E_UNSUPPORTED otherwise); it needs no
- * workspace (work-queue counters are used when one is given).  The trace holds
- * u = (k1, k2) in [0, T)^2 and the real coefficient (dc_im = 0); fofse_backward
- * runs the adjoint of this basis' recursion (one block per CTA).  Selecting
- * the DCT basis builds, synchronously on the current device (the plan's), the
- * basis' product table C of the complete support -- every sample of L outside
- * B, and inside the support shape, usable -- for the plan's rho: (2T - 1) x 2T
- * float pairs (130 KB at fft_size 64), freed with the plan.  Blocks whose
- * support is complete copy it instead of building C (calls with d_rho_gamma
- * build it per block).  FOFSE_E_ARG for other values or another current
- * device; FOFSE_E_NOMEM / FOFSE_E_CUDA if the table could not be built (the
- * basis is set all the same, and every block then builds C itself). */
+/* Basis (FOFSE_BASIS_*); default FOFSE_BASIS_DFT.  FOFSE_BASIS_DCT runs its
+ * own kernel with exact decisions, for fft_size 32 and 64, precision
+ * FOFSE_FP32 or FOFSE_FP32_FULLFF and the constant compensation (the batch
+ * calls return FOFSE_E_UNSUPPORTED otherwise): with FOFSE_FP32 an FP32
+ * working spectrum with a rigorous bound, near-ties and coefficients resolved
+ * exactly (launch-shape variant 0), or every bin in float-float (variant 1,
+ * and always with FOFSE_FP32_FULLFF).  It needs no workspace (work-queue
+ * counters are used when one is given).  The trace holds u = (k1, k2) in
+ * [0, T)^2 and the real coefficient (dc_im = 0); fofse_backward runs the
+ * adjoint of this basis' recursion (one block per CTA).  Selecting the DCT
+ * basis builds, synchronously on the current device (the plan's), the basis'
+ * product table C of the complete support -- every sample of L outside B, and
+ * inside the support shape, usable -- for the plan's rho: (2T - 1) x 2T float
+ * pairs (130 KB at fft_size 64), freed with the plan.  Every block starts
+ * from it (C is linear in the weights; a block with missing samples subtracts
+ * their part); a call with d_rho_gamma builds the table for its rho in its
+ * workspace.  FOFSE_E_ARG for other values or another current device;
+ * FOFSE_E_NOMEM / FOFSE_E_CUDA if the table could not be built (the basis is
+ * set all the same, and every block then builds C itself). */
 fofse_status fofse_plan_set_basis(fofse_plan plan, int basis);
 /* Number of launch shapes (threads per block / resident blocks per SM) of the
  * plan's kernel for its current precision; 0 for a NULL plan. */

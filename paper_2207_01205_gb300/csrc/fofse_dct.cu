@@ -12,13 +12,17 @@
 //   c = gamma R[u] / N_u,  N_u = 1/4 (C[0,0] + C[2u1,0] + C[0,2u2] + C[2u1,2u2])
 //       (Eq. 5 with the weighted norm sum w phi_u^2, Eq. 14)
 //   R[k] -= c/4 sum_{+-,+-} C[|k1 +- u1|, |k2 +- u2|]     for every k.
-// Every bin is kept in float-float (pairs of FP32, about 48 bits) in
-// registers and compared exactly, C in float-float in shared memory, so the
-// decisions are those of the exact algorithm up to float-float rounding.
-// Setup per block: R0 = DCT of w f and the table C of w, both by separable
-// float-float sums over the rows of L in chunks (cosines from integer phases,
-// table of the plan).  The model of B is rebuilt from the trace.
-#include "fofse_fwd_common.cuh"
+// C is kept in float-float (pairs of FP32, about 48 bits) in shared memory.
+// Two iteration loops: the product one keeps the working spectrum in FP32 in
+// registers with a rigorous bound on its distance to the exact recursion and
+// takes every decision and coefficient from exact values (as the DFT's
+// register-blocked kernel does); the other keeps every bin in float-float and
+// compares exactly.  Either way the decisions are those of the exact
+// algorithm up to float-float rounding.  Setup per block: R0 = DCT of w f and
+// the table C of w, both by separable float-float sums over the rows of L in
+// chunks (cosines from integer phases, table of the plan).  The model of B is
+// rebuilt from the coefficients.
+#include "fofse_fwd3.cuh"  // fixed-point recurrence sums, packed top-2 keys
 
 namespace fofse {
 namespace {
@@ -36,13 +40,28 @@ template <int T, int NT> struct Dct {
   static constexpr size_t ct_bytes = sizeof(float2) * (size_t)TT * S;  // (hi, lo) pairs
   static constexpr size_t cos_off = ct_bytes;                          // float2 [4T]
   static constexpr size_t red_off = cos_off + sizeof(float2) * 4 * T;  // float4 [2][NW], float2 [2][NW]
-  static constexpr size_t chunk_off = (red_off + 48 * NW + 15) & ~size_t(15);
+  // the FP32 loop's exchange slots: the same bytes as uint4 [2][NW] top-2 keys
+  // and longlong2 [NW] recurrence sums, then (aux) int [NW] near-tie counts,
+  // int4 [LIST] candidates, float4 [NW] + int2 [NW] warp results, int count
+  static constexpr int LIST = 32;
+  static constexpr size_t aux_off = red_off + 48 * NW;
+  static constexpr size_t wtot_off = aux_off;
+  static constexpr size_t list_off = (wtot_off + 4 * NW + 15) & ~size_t(15);
+  static constexpr size_t ww_off = list_off + 16 * LIST;
+  static constexpr size_t ndx_off = ww_off + 24 * NW;
+  static constexpr size_t chunk_off = (ndx_off + 4 + 15) & ~size_t(15);
   // setup chunk: masked w and x = w f (CH x T each), then the row sums of C
   // (CH x TT) and of R0 (CH x T), all float-float
   static constexpr size_t chunk_bytes = sizeof(float2) * (size_t)CH * (T + T + TT + T);
   __host__ __device__ static size_t trace_bytes(int iters) { return 10 * (size_t)iters + 16; }
-  __host__ __device__ static size_t bytes(int iters) {
-    const size_t tb = trace_bytes(iters);
+  // the FP32 loop keeps the exact R0 of every bin (float-float, by slot) and
+  // the term list (distinct index, summed coefficient) in the chunk region
+  static constexpr size_t r0x_bytes = sizeof(float2) * (size_t)T * T;
+  __host__ __device__ static size_t filt_bytes(int iters) {
+    return r0x_bytes + ((2 * (size_t)iters + 15) & ~size_t(15)) + 8 * (size_t)iters;
+  }
+  __host__ __device__ static size_t bytes(int iters, bool filt) {
+    const size_t tb = filt ? filt_bytes(iters) : trace_bytes(iters);
     return 128 + chunk_off + (chunk_bytes > tb ? chunk_bytes : tb);
   }
 };
@@ -141,7 +160,39 @@ __device__ __forceinline__ bool better(ff a, int ia, ff b, int ib) {
   return a.h > b.h || (a.h == b.h && (a.l > b.l || (a.l == b.l && ia < ib)));
 }
 
-template <int T, int NT>
+// The exact value's correction at bin (k1, k2) from the terms j in {j0, j0 +
+// stride, ...} < j1 of the term list (distinct index v_j, summed coefficient
+// c_j, float-float):  sum_j c_j / 4 sum_{+-,+-} C[|k1 +- v1|, |k2 +- v2|],
+// each term in float-float from the table C in shared memory, returned in
+// fixed point with unit 1/scale (so that warp and block sums are exact).
+template <int T>
+__device__ __forceinline__ long long dct_recur(const float2* ct, const short* ty, const float2* tc,
+                                               int k1, int k2, int j0, int j1, int stride,
+                                               float scale) {
+  constexpr int S = 2 * T, LOGT = ilog2(T);
+  ff acc = {0.f, 0.f};
+  for (int j = j0; j < j1; j += stride) {
+    const int y = ty[j];
+    const int v1 = y >> LOGT, v2 = y & (T - 1);
+    const float2 cj = tc[j];
+    const int rp = (k1 + v1) * S, rm = abs(k1 - v1) * S, cp = k2 + v2, cm = abs(k2 - v2);
+    const float2 a = ct[rp + cp], b = ct[rp + cm], c = ct[rm + cp], d = ct[rm + cm];
+    const ff sum = ff_add(ff_add(ff{a.x, a.y}, ff{b.x, b.y}), ff_add(ff{c.x, c.y}, ff{d.x, d.y}));
+    acc = ff_add(acc, ff_mul(ff{cj.x, cj.y}, sum));
+  }
+  const float sq = 0.25f * scale;  // the 1/4, exactly
+  return fx_round(acc.h * sq) + fx_round(acc.l * sq);
+}
+
+// e_k R^2 in float-float (the comparison value of Eq. 9 with the orthonormal
+// DCT's magnitude), e a power of two
+__device__ __forceinline__ ff dct_energy(ff r, float e) {
+  const ff q = ff_two_prod(r.h, r.h);
+  const ff e2 = ff_fast_two_sum(q.h, __fmaf_rn(2.f * r.h, r.l, q.l));
+  return {e2.h * e, e2.l * e};
+}
+
+template <int T, int NT, bool FILT>
 __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, unsigned char* dsm) {
   using G = Dct<T, NT>;
   using IO = PlanIO<ArFF>;
@@ -293,110 +344,347 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   else if (any_bad || !isfinite(W0.h)) st = FOFSE_BLK_NONFINITE;
 
   if (st == FOFSE_BLK_OK) {
-    const ff gam = IO::gamma(P);
-    // this thread's best bin by e_k R[k]^2 (exact comparison in float-float),
-    // found again after every update
-    ff best = {-1.f, 0.f}, bestR = {0.f, 0.f};
-    int bidx = 0x7fffffff;
-    // the thread's best bin: every bin's value, then a pairwise tree (the
-    // order "larger value, then smaller index" is total, so the tree finds the
-    // bin a scan would, with a dependency depth of log2(NB) instead of NB)
-    auto thread_best = [&]() {
-      ff ev[NB], rv[NB];
-      int ix[NB];
+    if constexpr (FILT) {
+      // ---- FP32 working spectrum with exact decisions ----
+      // As in the register-blocked DFT kernel: R32 (FP32, registers) with a
+      // running bound B on its distance to the exact recursion; the block's
+      // FP32 top-2 of e_k R32[k]^2 decide the argmax when further apart than
+      // the bound allows (sqrt(e_k) <= 2 scales B), otherwise every bin that
+      // can still win is evaluated exactly and compared in float-float; the
+      // winner's exact value comes from the recurrence
+      //   R~[k] = R0[k] - sum_j c_j / 4 sum_{+-,+-} C[|k1 +- v1|, |k2 +- v2|]
+      // over the distinct selected indices v_j (summed coefficients c_j).
+      // Bound per update R <- fma(-c/4, s, R), s the FP32 sum of the four
+      // C entries (hi parts; |C[a]| <= C[0,0] = W[0]): rounding C to FP32
+      // (u W[0] each), the two-level sum (8u W[0]), c to FP32 (u |c|) and the
+      // fma (u |R_new|) give u |R_new| + 4u |c| W[0]; the kernel adds
+      // 1.5u max|R32| + 6u |c| W[0] per iteration (the first term of the
+      // first iteration also covers the rounding of R0 to FP32).
+      constexpr int LIST = G::LIST;
+      constexpr float kU = 5.9604644775390625e-08f;  // 2^-24
+      constexpr float kDn = 1.f - 16.f * kU, kUp = 1.f + 256.f * kU, kUpB = 1.f + 16.f * kU;
+      constexpr float kTiny = 7.888609052210118e-31f;     // 2^-100
+      constexpr float kTinySqrt = 8.881784197001252e-16f; // 2^-50
+      constexpr float kA = 1.5f * kU, kB = 6.f * kU;
+      uint4* t2s = reinterpret_cast<uint4*>(dsm + G::red_off);                  // [2][NW]
+      longlong2* redx = reinterpret_cast<longlong2*>(dsm + G::red_off + 32 * NW);  // [NW]
+      int* wtot = reinterpret_cast<int*>(dsm + G::wtot_off);
+      int4* list = reinterpret_cast<int4*>(dsm + G::list_off);
+      float4* wwv = reinterpret_cast<float4*>(dsm + G::ww_off);
+      int2* wwc = reinterpret_cast<int2*>(dsm + G::ww_off + 16 * NW);
+      int* ndx = reinterpret_cast<int*>(dsm + G::ndx_off);
+      float2* R0x = reinterpret_cast<float2*>(chunk);  // exact R0 by slot tid + j NT
+      short* trY = reinterpret_cast<short*>(chunk + G::r0x_bytes);
+      float2* trCm = reinterpret_cast<float2*>(chunk + G::r0x_bytes + ((2 * (size_t)iters + 15) & ~size_t(15)));
+      const ff gam = IO::gamma(P);
+      const float W0f = W0.h * (1.f + 1e-6f);
+      float R32[NB], ew[NB];
+      unsigned m1k = 0u, m2k = 0u;
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
-        const int k1 = r0 + j * RS;
-        const float sc = (k1 > 0 ? 2.f : 1.f) * (k2 > 0 ? 2.f : 1.f);
-        const ff q = ff_two_prod(R[j].h, R[j].h);
-        const ff e2 = ff_fast_two_sum(q.h, __fmaf_rn(2.f * R[j].h, R[j].l, q.l));
-        ev[j] = {e2.h * sc, e2.l * sc};
-        ix[j] = k1 * T + k2;
-        rv[j] = R[j];
+        R0x[tid + j * NT] = make_float2(R[j].h, R[j].l);
+        R32[j] = R[j].h;
+        ew[j] = (r0 + j * RS > 0 ? 2.f : 1.f) * (k2 > 0 ? 2.f : 1.f);
+        key_insert(m1k, m2k, ew[j] * (R32[j] * R32[j]), j);
       }
+      float bnd = 0.f, prevabs = 0.f, csum = 0.f;
+      int nd = 0;  // terms in the list (warp 0 maintains it; the others read it each iteration)
+      __syncthreads();
+#pragma unroll 1
+      for (int it = 0; it < iters; ++it) {
+        // ---- top-2 over the block (packed keys) ----
+        const unsigned wm1 = __reduce_max_sync(kFullMask, m1k);
+        const unsigned hold = __ballot_sync(kFullMask, m1k == wm1);
+        const int ldr = __ffs(hold) - 1;
+        const unsigned wm2 = __reduce_max_sync(kFullMask, lane == ldr ? m2k : m1k);
+        uint4* ts = t2s + (it & 1) * NW;
+        if (lane == 0) ts[warp] = make_uint4(wm1, wm2, (unsigned)(warp * 32 + ldr), (unsigned)nd);
+        __syncthreads();
+        uint4 g = ts[0];
+        nd = (int)g.w;  // warp 0's count, after its update of the previous iteration
 #pragma unroll
-      for (int w = 1; w < NB; w *= 2) {
-#pragma unroll
-        for (int j = 0; j + w < NB; j += 2 * w) {
-          if (better(ev[j + w], ix[j + w], ev[j], ix[j])) {
-            ev[j] = ev[j + w];
-            ix[j] = ix[j + w];
-            rv[j] = rv[j + w];
+        for (int w = 1; w < NW; ++w) {
+          const uint4 o = ts[w];
+          if (o.x > g.x) {
+            g.y = max(g.x, o.y);
+            g.x = o.x;
+            g.z = o.z;
+          } else {
+            g.y = max(g.y, o.x);
           }
         }
-      }
-      best = ev[0];
-      bidx = ix[0];
-      bestR = rv[0];
-    };
-    thread_best();
-#pragma unroll 1
-    for (int it = 0; it < iters; ++it) {
-      // ---- block argmax ----
+        const float m1 = __uint_as_float(g.x & ~kKeyMask), m2 = __uint_as_float(g.y & ~kKeyMask);
+        const bool n1 = m1 >= kTiny, n2 = m2 >= kTiny;
+        const float q1 = m1 * rsqrtf(n1 ? m1 : 1.f), q2 = m2 * rsqrtf(n2 ? m2 : 1.f);
+        const float sM1 = n1 ? q1 : 0.f, sM1u = n1 ? q1 * kUp : kTinySqrt;
+        const float sM2 = n2 ? q2 : kTinySqrt;
+        bnd += kA * sM1u + kB * W0f * prevabs;
+        const float bw = 2.f * bnd;  // bound of sqrt(e_k) |R32[k] - R~[k]|
+        const bool certain = (sM1 * kDn - bw * kUpB) > (sM2 * kUp + bw * kUpB);
+        const int sh = fx_shift(4.f * W0f * csum);
+        const float scale = pow2f(sh), iscale = pow2f(-sh);
+        int u1, u2;
+        ff Rt;
+        if (certain) {
+          const int wt = (int)g.z, li = (int)(g.x & kKeyMask);
+          u1 = wt / T + li * RS;
+          u2 = wt & (T - 1);
+          const float2 rx = R0x[wt + li * NT];
+          long long sv = 0;
+          if (warp * 32 < nd) {  // warp-uniform: this warp holds terms
+            sv = dct_recur<T>(ct, trY, trCm, u1, u2, tid, nd, NT, scale);
+            sv = redux_sum64(sv);
+          }
+          if (lane == 0) redx[warp] = make_longlong2(sv, 0);
+          __syncthreads();
+          const longlong2 v = lane < NW ? redx[lane] : make_longlong2(0, 0);
+          Rt = ff_sub(ff{rx.x, rx.y}, fx_to_ff(redux_sum64(v.x), iscale));
+        } else {
+          // ---- near-tie: exact values of every bin that can still win ----
+          const float Lb = (sM1 * kDn - 2.f * bw * kUpB) * kDn;
+          const float thr = Lb > 0.f ? Lb * Lb * kDn : -1.f;
+          int cnt = 0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const ff ob = {__shfl_xor_sync(kFullMask, best.h, o), __shfl_xor_sync(kFullMask, best.l, o)};
-        const int oi = __shfl_xor_sync(kFullMask, bidx, o);
-        const ff orr = {__shfl_xor_sync(kFullMask, bestR.h, o), __shfl_xor_sync(kFullMask, bestR.l, o)};
-        if (better(ob, oi, best, bidx)) {
-          best = ob;
-          bidx = oi;
-          bestR = orr;
+          for (int j = 0; j < NB; ++j) cnt += ew[j] * (R32[j] * R32[j]) >= thr ? 1 : 0;
+          int incl = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFullMask, incl, o);
+            if (lane >= o) incl += v;
+          }
+          if (lane == 31) wtot[warp] = incl;
+          __syncthreads();
+          int before = 0, total = 0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const int v = wtot[w];
+            before += w < warp ? v : 0;
+            total += v;
+          }
+          const int rank0 = before + incl - cnt;
+          ff wbe = {-1.f, 0.f}, wbr = {0.f, 0.f};
+          int wbl = 0x7fffffff;
+          for (int pass = 0; pass < total; pass += LIST) {
+            int r = rank0;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+              if (ew[j] * (R32[j] * R32[j]) >= thr) {
+                if (r >= pass && r < pass + LIST)
+                  list[r - pass] = make_int4((r0 + j * RS) * T + k2, tid + j * NT, __float_as_int(ew[j]), 0);
+                ++r;
+              }
+            }
+            __syncthreads();
+            const int n = min(LIST, total - pass);
+            for (int c = warp; c < n; c += NW) {
+              const int4 e = list[c];
+              const int c1 = e.x / T, c2 = e.x - c1 * T;
+              const float2 rx = R0x[e.y];
+              long long sv = dct_recur<T>(ct, trY, trCm, c1, c2, lane, nd, 32, scale);
+              sv = redux_sum64(sv);
+              const ff rv = ff_sub(ff{rx.x, rx.y}, fx_to_ff(sv, iscale));
+              const ff ev = dct_energy(rv, __int_as_float(e.z));
+              if (better(ev, e.x, wbe, wbl)) {
+                wbe = ev;
+                wbl = e.x;
+                wbr = rv;
+              }
+            }
+            __syncthreads();
+          }
+          if (lane == 0) {
+            wwv[warp] = make_float4(wbe.h, wbe.l, wbr.h, wbr.l);
+            wwc[warp] = make_int2(wbl, 0);
+          }
+          __syncthreads();
+          ff be = {-1.f, 0.f};
+          int bl = 0x7fffffff;
+          Rt = {0.f, 0.f};
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const float4 v4 = wwv[w];
+            const int l = wwc[w].x;
+            if (l != 0x7fffffff && better(ff{v4.x, v4.y}, l, be, bl)) {
+              be = {v4.x, v4.y};
+              bl = l;
+              Rt = {v4.z, v4.w};
+            }
+          }
+          if (bl == 0x7fffffff) bl = 0;  // no candidate (cannot happen for finite data)
+          u1 = bl / T;
+          u2 = bl - u1 * T;
+        }
+        // ---- coefficient (Eq. 5, Eq. 14) ----
+        const float2 n0 = ct[0], n1c = ct[2 * u1 * S], n2c = ct[2 * u2], n3 = ct[2 * u1 * S + 2 * u2];
+        ff nrm = ff_add(ff_add(ff{n0.x, n0.y}, ff{n1c.x, n1c.y}), ff_add(ff{n2c.x, n2c.y}, ff{n3.x, n3.y}));
+        nrm = ff_scale(nrm, 0.25f);
+        const ff cff = nrm.h > 0.f ? ff_div(ff_mul(gam, Rt), nrm) : ff{0.f, 0.f};
+        // ---- record: the trace entry, and the term of the recurrence ----
+        // (every read of the list in this iteration lies before a barrier
+        // that precedes this update)
+        if (warp == 0) {
+          const short y = (short)(u1 * T + u2);
+          int pos = -1;
+          for (int j0 = 0; j0 < nd; j0 += 32) {
+            const int jj = j0 + lane;
+            const unsigned hit = __ballot_sync(kFullMask, jj < nd && trY[jj] == y);
+            if (hit) {
+              pos = j0 + __ffs(hit) - 1;
+              break;
+            }
+          }
+          if (lane == 0) {
+            if (pos >= 0) {
+              const float2 o = trCm[pos];
+              const ff sm = ff_add(ff{o.x, o.y}, cff);
+              trCm[pos] = make_float2(sm.h, sm.l);
+            } else {
+              trY[nd] = y;
+              trCm[nd] = make_float2(cff.h, cff.l);
+            }
+            if (args.trace) {
+              fofse_trace_entry e;
+              e.u1 = (int16_t)u1;
+              e.u2 = (int16_t)u2;
+              e.dc_re = cff.h;
+              e.dc_im = 0.f;
+              args.trace[(size_t)blk * args.trace_stride + it] = e;
+            }
+          }
+          if (pos < 0) ++nd;
+        }
+        // ---- FP32 update R -= c/4 sum C[|k1 +- u1|, |k2 +- u2|] + next keys ----
+        const float p = cff.h, c4 = 0.25f * p;
+        prevabs = fabsf(p);
+        csum += prevabs;
+        const int cp = k2 + u2, cm = abs(k2 - u2);
+        m1k = 0u;
+        m2k = 0u;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          const int k1 = r0 + j * RS;
+          const int rp = (k1 + u1) * S, rm = abs(k1 - u1) * S;
+          const float sv = (ct[rp + cp].x + ct[rp + cm].x) + (ct[rm + cp].x + ct[rm + cm].x);
+          R32[j] = __fmaf_rn(-c4, sv, R32[j]);
+          key_insert(m1k, m2k, ew[j] * (R32[j] * R32[j]), j);
         }
       }
-      float4* rv = redv + (it & 1) * NW;
-      float2* rr = redr + (it & 1) * NW;
-      if (lane == 0) {
-        rv[warp] = make_float4(best.h, best.l, __int_as_float(bidx), 0.f);
-        rr[warp] = make_float2(bestR.h, bestR.l);
-      }
-      __syncthreads();
-      float4 g = rv[0];
-      float2 gr = rr[0];
+      if (tid == 0) *ndx = nd;  // thread 0 is in warp 0, which holds the count
+    } else {
+      const ff gam = IO::gamma(P);
+      // this thread's best bin by e_k R[k]^2 (exact comparison in float-float),
+      // found again after every update
+      ff best = {-1.f, 0.f}, bestR = {0.f, 0.f};
+      int bidx = 0x7fffffff;
+      // the thread's best bin: every bin's value, then a pairwise tree (the
+      // order "larger value, then smaller index" is total, so the tree finds the
+      // bin a scan would, with a dependency depth of log2(NB) instead of NB)
+      auto thread_best = [&]() {
+        ff ev[NB], rv[NB];
+        int ix[NB];
 #pragma unroll
-      for (int w = 1; w < NW; ++w) {
-        const float4 o = rv[w];
-        if (better(ff{o.x, o.y}, __float_as_int(o.z), ff{g.x, g.y}, __float_as_int(g.z))) {
-          g = o;
-          gr = rr[w];
+        for (int j = 0; j < NB; ++j) {
+          const int k1 = r0 + j * RS;
+          const float sc = (k1 > 0 ? 2.f : 1.f) * (k2 > 0 ? 2.f : 1.f);
+          const ff q = ff_two_prod(R[j].h, R[j].h);
+          const ff e2 = ff_fast_two_sum(q.h, __fmaf_rn(2.f * R[j].h, R[j].l, q.l));
+          ev[j] = {e2.h * sc, e2.l * sc};
+          ix[j] = k1 * T + k2;
+          rv[j] = R[j];
         }
-      }
-      int ui = __float_as_int(g.z);
-      if (ui < 0 || ui >= T * T) ui = 0;  // no comparable value (cannot happen for finite data)
-      const int u1 = ui / T, u2 = ui - u1 * T;
-      // ---- coefficient (Eq. 5, Eq. 14) ----
-      const float2 n0 = ct[0], n1 = ct[2 * u1 * S], n2 = ct[2 * u2], n3 = ct[2 * u1 * S + 2 * u2];
-      ff nrm = ff_add(ff_add(ff{n0.x, n0.y}, ff{n1.x, n1.y}), ff_add(ff{n2.x, n2.y}, ff{n3.x, n3.y}));
-      nrm = ff_scale(nrm, 0.25f);
-      const ff cff = nrm.h > 0.f ? ff_div(ff_mul(gam, ff{gr.x, gr.y}), nrm) : ff{0.f, 0.f};
-      if (tid == 0) {
-        trU[it] = (short)ui;
-        trC[it] = make_float2(cff.h, cff.l);
-      }
-      // ---- R[k] -= c/4 sum C[|k1 +- u1|, |k2 +- u2|], and the next best ----
-      const ff c4 = ff_scale(cff, 0.25f);
-      const int cp = k2 + u2, cm = abs(k2 - u2);
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int k1 = r0 + j * RS;
-        const int rp = (k1 + u1) * S, rm = abs(k1 - u1) * S;
-        const float2 a = ct[rp + cp], bq = ct[rp + cm], cq = ct[rm + cp], d = ct[rm + cm];
-        // four-term float-float sum: exact sums of the high parts, low parts added
-        const ff s1 = ff_two_sum(a.x, bq.x), s2 = ff_two_sum(cq.x, d.x), s = ff_two_sum(s1.h, s2.h);
-        const float lo = ((a.y + bq.y) + (cq.y + d.y)) + (s1.l + s2.l) + s.l;
-        // R - c4 t with one product and one compensated subtraction
-        const ff pr = ff_two_prod(c4.h, s.h);
-        const float pe = __fmaf_rn(c4.h, lo, __fmaf_rn(c4.l, s.h, pr.l));
-        const ff dd = ff_two_sum(R[j].h, -pr.h);
-        R[j] = ff_fast_two_sum(dd.h, dd.l + (R[j].l - pe));
-      }
+        for (int w = 1; w < NB; w *= 2) {
+#pragma unroll
+          for (int j = 0; j + w < NB; j += 2 * w) {
+            if (better(ev[j + w], ix[j + w], ev[j], ix[j])) {
+              ev[j] = ev[j + w];
+              ix[j] = ix[j + w];
+              rv[j] = rv[j + w];
+            }
+          }
+        }
+        best = ev[0];
+        bidx = ix[0];
+        bestR = rv[0];
+      };
       thread_best();
+#pragma unroll 1
+      for (int it = 0; it < iters; ++it) {
+        // ---- block argmax ----
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const ff ob = {__shfl_xor_sync(kFullMask, best.h, o), __shfl_xor_sync(kFullMask, best.l, o)};
+          const int oi = __shfl_xor_sync(kFullMask, bidx, o);
+          const ff orr = {__shfl_xor_sync(kFullMask, bestR.h, o), __shfl_xor_sync(kFullMask, bestR.l, o)};
+          if (better(ob, oi, best, bidx)) {
+            best = ob;
+            bidx = oi;
+            bestR = orr;
+          }
+        }
+        float4* rv = redv + (it & 1) * NW;
+        float2* rr = redr + (it & 1) * NW;
+        if (lane == 0) {
+          rv[warp] = make_float4(best.h, best.l, __int_as_float(bidx), 0.f);
+          rr[warp] = make_float2(bestR.h, bestR.l);
+        }
+        __syncthreads();
+        float4 g = rv[0];
+        float2 gr = rr[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) {
+          const float4 o = rv[w];
+          if (better(ff{o.x, o.y}, __float_as_int(o.z), ff{g.x, g.y}, __float_as_int(g.z))) {
+            g = o;
+            gr = rr[w];
+          }
+        }
+        int ui = __float_as_int(g.z);
+        if (ui < 0 || ui >= T * T) ui = 0;  // no comparable value (cannot happen for finite data)
+        const int u1 = ui / T, u2 = ui - u1 * T;
+        // ---- coefficient (Eq. 5, Eq. 14) ----
+        const float2 n0 = ct[0], n1 = ct[2 * u1 * S], n2 = ct[2 * u2], n3 = ct[2 * u1 * S + 2 * u2];
+        ff nrm = ff_add(ff_add(ff{n0.x, n0.y}, ff{n1.x, n1.y}), ff_add(ff{n2.x, n2.y}, ff{n3.x, n3.y}));
+        nrm = ff_scale(nrm, 0.25f);
+        const ff cff = nrm.h > 0.f ? ff_div(ff_mul(gam, ff{gr.x, gr.y}), nrm) : ff{0.f, 0.f};
+        if (tid == 0) {
+          trU[it] = (short)ui;
+          trC[it] = make_float2(cff.h, cff.l);
+        }
+        // ---- R[k] -= c/4 sum C[|k1 +- u1|, |k2 +- u2|], and the next best ----
+        const ff c4 = ff_scale(cff, 0.25f);
+        const int cp = k2 + u2, cm = abs(k2 - u2);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          const int k1 = r0 + j * RS;
+          const int rp = (k1 + u1) * S, rm = abs(k1 - u1) * S;
+          const float2 a = ct[rp + cp], bq = ct[rp + cm], cq = ct[rm + cp], d = ct[rm + cm];
+          // four-term float-float sum: exact sums of the high parts, low parts added
+          const ff s1 = ff_two_sum(a.x, bq.x), s2 = ff_two_sum(cq.x, d.x), s = ff_two_sum(s1.h, s2.h);
+          const float lo = ((a.y + bq.y) + (cq.y + d.y)) + (s1.l + s2.l) + s.l;
+          // R - c4 t with one product and one compensated subtraction
+          const ff pr = ff_two_prod(c4.h, s.h);
+          const float pe = __fmaf_rn(c4.h, lo, __fmaf_rn(c4.l, s.h, pr.l));
+          const ff dd = ff_two_sum(R[j].h, -pr.h);
+          R[j] = ff_fast_two_sum(dd.h, dd.l + (R[j].l - pe));
+        }
+        thread_best();
+      }
     }
   }
   __syncthreads();
 
   // ---- synthesis of B (Eq. 1) from the trace; outputs ----------------------
   const int nIt = st == FOFSE_BLK_OK ? iters : 0;
+  // the terms: one per iteration, or (FP32 loop) one per distinct index
+  const short* syY = trU;
+  const float2* syC = trC;
+  int nSyn = nIt;
+  if constexpr (FILT) {
+    syY = reinterpret_cast<const short*>(chunk + G::r0x_bytes);
+    syC = reinterpret_cast<const float2*>(chunk + G::r0x_bytes + ((2 * (size_t)iters + 15) & ~size_t(15)));
+    nSyn = st == FOFSE_BLK_OK ? *reinterpret_cast<const int*>(dsm + G::ndx_off) : 0;
+  }
   const int ld = args.out_ld;
   for (int pidx = tid; pidx < ld * ld; pidx += NT) {
     const int bm = pidx / ld, bn = pidx - bm * ld;
@@ -404,10 +692,10 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
     if (bm < b && bn < b) {
       const int m = br + bm, n = br + bn;
       ff acc = {0.f, 0.f};
-      for (int i = 0; i < nIt; ++i) {
-        const int yy = trU[i];
+      for (int i = 0; i < nSyn; ++i) {
+        const int yy = syY[i];
         const int a1 = yy / T, a2 = yy - a1 * T;
-        const float2 c = trC[i];
+        const float2 c = syC[i];
         ff_mac(acc, ff{c.x, c.y}, ff_mul(cosv(a1, m), cosv(a2, n)));
       }
       acc = ff_norm(acc);
@@ -420,8 +708,8 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
     }
     if (args.out_blocks) args.out_blocks[(size_t)blk * args.out_stride + pidx] = v;
   }
-  if (args.trace) {
-    for (int i = tid; i < args.trace_stride; i += NT) {
+  if (args.trace) {  // (the FP32 loop wrote its iterations' entries as they ran)
+    for (int i = (FILT ? nIt : 0) + tid; i < args.trace_stride; i += NT) {
       fofse_trace_entry e;
       if (i < nIt) {
         const int yy = trU[i];
@@ -448,7 +736,7 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   __syncthreads();
 }
 
-template <int T, int NT>
+template <int T, int NT, bool FILT>
 __global__ void __launch_bounds__(NT) fofse_forward_dct_kernel(const __grid_constant__ FwdArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte slots, no TMA
   unsigned char* dsm = smem_raw;
@@ -467,7 +755,7 @@ __global__ void __launch_bounds__(NT) fofse_forward_dct_kernel(const __grid_cons
     }
     if (item >= args.n_blocks) break;
     if (args.blocks[item].plan != args.plan_index) continue;
-    forward_block_dct<T, NT>(args, item, dsm);
+    forward_block_dct<T, NT, FILT>(args, item, dsm);
   }
 }
 
@@ -535,15 +823,15 @@ template <int T> cudaError_t build_dct_table_T(const PlanDev& p, float2* out, cu
   return cudaGetLastError();
 }
 
-template <int T, int NT> struct VariantDct {
+template <int T, int NT, bool FILT> struct VariantDct {
   static cudaError_t launch(const FwdArgs& a, cudaStream_t s) {
-    const size_t sm = Dct<T, NT>::bytes(a.plan.iters);
+    const size_t sm = Dct<T, NT>::bytes(a.plan.iters, FILT);
     int grid = 0;
-    const cudaError_t e = prepare_kernel(fofse_forward_dct_kernel<T, NT>, NT, sm, &grid);
+    const cudaError_t e = prepare_kernel(fofse_forward_dct_kernel<T, NT, FILT>, NT, sm, &grid);
     if (e != cudaSuccess) return e;
     if (grid > a.n_blocks) grid = a.n_blocks;
     if (grid < 1) return cudaSuccess;
-    fofse_forward_dct_kernel<T, NT><<<grid, NT, sm, s>>>(a);
+    fofse_forward_dct_kernel<T, NT, FILT><<<grid, NT, sm, s>>>(a);
     return cudaGetLastError();
   }
 };
@@ -751,10 +1039,13 @@ cudaError_t launch_backward_dct(const BwdArgs& a, cudaStream_t s) {
   return cudaErrorNotSupported;
 }
 
+// FOFSE_FP32: the FP32 working spectrum with exact decisions (variant 0) or
+// every bin in float-float (variant 1); FOFSE_FP32_FULLFF: every bin in
+// float-float.
 cudaError_t launch_forward_dct(const FwdArgs& a, cudaStream_t s) {
-  const bool alt = a.plan.variant == 1;
-  if (a.plan.T == 32) return alt ? VariantDct<32, 256>::launch(a, s) : VariantDct<32, 128>::launch(a, s);
-  if (a.plan.T == 64) return alt ? VariantDct<64, 512>::launch(a, s) : VariantDct<64, 256>::launch(a, s);
+  const bool ff = a.plan.variant == 1 || a.plan.precision == FOFSE_FP32_FULLFF;
+  if (a.plan.T == 32) return ff ? VariantDct<32, 128, false>::launch(a, s) : VariantDct<32, 128, true>::launch(a, s);
+  if (a.plan.T == 64) return ff ? VariantDct<64, 256, false>::launch(a, s) : VariantDct<64, 256, true>::launch(a, s);
   return cudaErrorNotSupported;
 }
 
