@@ -343,6 +343,7 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   if (!any_use || W0.h == 0.f) st = FOFSE_BLK_NO_SUPPORT;
   else if (any_bad || !isfinite(W0.h)) st = FOFSE_BLK_NONFINITE;
 
+  int done_it = 0;  // iterations the FP32 loop ran (any later one repeats a zero residual's (0, 0), 0)
   if (st == FOFSE_BLK_OK) {
     if constexpr (FILT) {
       // ---- FP32 working spectrum with exact decisions ----
@@ -390,8 +391,9 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
       float bnd = 0.f, prevabs = 0.f, csum = 0.f;
       int nd = 0;  // terms in the list (warp 0 maintains it; the others read it each iteration)
       __syncthreads();
+      int it = 0;
 #pragma unroll 1
-      for (int it = 0; it < iters; ++it) {
+      for (; it < iters; ++it) {
         // ---- top-2 over the block (packed keys) ----
         const unsigned wm1 = __reduce_max_sync(kFullMask, m1k);
         const unsigned hold = __ballot_sync(kFullMask, m1k == wm1);
@@ -553,6 +555,14 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
           }
           if (pos < 0) ++nd;
         }
+        // an exactly zero winner (the exact maximum of e_k R~[k]^2) means a
+        // zero residual in every bin: every later iteration selects (0, 0),
+        // as this one did, with a zero coefficient; they are written as such
+        // at the end instead of being run
+        if (Rt.h == 0.f && Rt.l == 0.f) {
+          ++it;
+          break;
+        }
         // ---- FP32 update R -= c/4 sum C[|k1 +- u1|, |k2 +- u2|] + next keys ----
         const float p = cff.h, c4 = 0.25f * p;
         prevabs = fabsf(p);
@@ -569,6 +579,7 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
           key_insert(m1k, m2k, ew[j] * (R32[j] * R32[j]), j);
         }
       }
+      done_it = it;
       if (tid == 0) *ndx = nd;  // thread 0 is in warp 0, which holds the count
     } else {
       const ff gam = IO::gamma(P);
@@ -709,9 +720,9 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
     if (args.out_blocks) args.out_blocks[(size_t)blk * args.out_stride + pidx] = v;
   }
   if (args.trace) {  // (the FP32 loop wrote its iterations' entries as they ran)
-    for (int i = (FILT ? nIt : 0) + tid; i < args.trace_stride; i += NT) {
+    for (int i = (FILT ? done_it : 0) + tid; i < args.trace_stride; i += NT) {
       fofse_trace_entry e;
-      if (i < nIt) {
+      if (!FILT && i < nIt) {
         const int yy = trU[i];
         e.u1 = (int16_t)(yy / T);
         e.u2 = (int16_t)(yy - (yy / T) * T);

@@ -466,7 +466,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   }
 
   // ---- 2. z = w f + j w at bit-reversed positions of the global FFT buffer --
-  bool bad = false;
+  bool bad = false, nzf = false;
   for (int e = tid; e < T * T; e += NT) {
     const int r = e >> LOGT, cc = e & (T - 1);
     const int m = __brev(r) >> (32 - LOGT), n = __brev(cc) >> (32 - LOGT);
@@ -489,6 +489,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
       }
       if (av && !inB && inS) {
         bad |= !isfinite(f);
+        nzf |= f != 0.f;
         C wd;
         z = IO::weighted(P.tab, m * Ls + n, f, wd);
         if constexpr (OFSE) {
@@ -502,6 +503,9 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   }
   // the staging tiles are read: the W region becomes the FFT's chunk buffer
   int any_bad = __syncthreads_or(bad);
+  // f = 0 on the whole support: R0 = DFT(w f) is exactly zero (the packed
+  // transform would leave W's rounding in it, about 1e-16 of |W|)
+  const bool zero_f = !__syncthreads_or(nzf);
 
   // ---- 3. FFT (float-float), through shared memory in chunks -------------------
   fft2d_chunked<T, NT>(Zg, Whi, P.tab, Ls);
@@ -518,7 +522,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
     const int x = kk.x * T2 + kk.y;
     const int mx = ((T - kk.x) & (T - 1)) * T2 + ((T - kk.y) & (T - 1));
     const C a = A::load(Zg, x, T), mm = A::load(Zg, mx, T);
-    const C r = A::half(A::add(a, A::conj(mm)));
+    const C r = zero_f ? A::zero() : A::half(A::add(a, A::conj(mm)));
     if (!A::finite(r)) bad = true;
     const int slot = i < NB ? tid + i * NT : NSLOT + tid;
     Rx[slot] = make_float4(r.re.h, r.re.l, r.im.h, r.im.l);
@@ -528,7 +532,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
     key_insert(m1k, m2k, m32(r32), i);
     if constexpr (OFSE) {
       const C qa = A::load(Vg, x, T), qm = A::load(Vg, mx, T);
-      const C qv = A::half(A::add(qa, A::conj(qm)));
+      const C qv = zero_f ? A::zero() : A::half(A::add(qa, A::conj(qm)));
       Qx[slot] = make_float4(qv.re.h, qv.re.l, qv.im.h, qv.im.l);
     }
   }
@@ -548,6 +552,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   if (IO::w0_zero(W0c)) st = FOFSE_BLK_NO_SUPPORT;
   else if (any_bad || !IO::w0_finite(W0c)) st = FOFSE_BLK_NONFINITE;
 
+  int done_it = 0;  // iterations the loop ran (any later one repeats a zero residual's (0, 0), 0)
   if (st == FOFSE_BLK_OK) {
     const ff inv = IO::inv_w0(IO::gamma(P), W0c.re);
     const float W0f = W0c.re.h * (1.f + 1e-6f);
@@ -839,6 +844,16 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           }
           if (pos < 0) ++nd;
         }
+        // The winner is the exact maximum, so an exactly zero winner means
+        // the exact residual is zero in every bin: every later iteration
+        // selects the smallest index, (0, 0) (which this one did), with a zero
+        // coefficient and changes nothing.  They are written as such at the
+        // end instead of being run (each would resolve a near-tie over every
+        // bin).
+        if (Rt.re.h == 0.f && Rt.re.l == 0.f && Rt.im.h == 0.f && Rt.im.l == 0.f) {
+          ++it;
+          break;
+        }
         p = c.re.h;
         q = c.im.h;
         if (kRefresh && dc_run && !(wk1 == 0 && wk2 == 0)) {
@@ -965,6 +980,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
       m2k = max(max(k2a, k2b), min(k1a, k1b));
       ++it;
     }
+    done_it = it;
   }
   if (tid == 0) *nd_s = nd;  // thread 0 is in warp 0, which holds the count
   __syncthreads();
@@ -1014,8 +1030,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
     }
     if (args.out_blocks) args.out_blocks[(size_t)blk * args.out_stride + pidx] = v;
   }
-  if (args.trace) {  // entries of the iterations were written as they ran
-    for (int i = nIt + tid; i < args.trace_stride; i += NT) {
+  if (args.trace) {  // entries of the iterations that ran were written as they ran
+    for (int i = done_it + tid; i < args.trace_stride; i += NT) {
       fofse_trace_entry e;
       e.u1 = e.u2 = 0;
       e.dc_re = e.dc_im = 0.f;
@@ -1025,7 +1041,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   if (args.gamma_out) {  // the compensation factor of each iteration (Eq. 13)
     for (int i = tid; i < args.trace_stride; i += NT) {
       float2* gp = args.gamma_out + (size_t)blk * args.trace_stride + i;
-      if (i >= nIt) *gp = make_float2(0.f, 0.f);
+      if (i >= (OFSE ? done_it : nIt)) *gp = make_float2(0.f, 0.f);
       else if (!OFSE) *gp = make_float2(IO::gamma(P).h, 0.f);  // OFSE: written per iteration
     }
   }

@@ -196,7 +196,7 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
   const int b = a.block, br = a.border, Ls = a.Ls, Lt = a.Lt, D = a.depth;
 
   // ---- 1. z = w f + j w per frame at bit-reversed positions; planes tau >= Lt zero ----
-  bool bad = false;
+  bool bad = false, nzf = false;
   for (int e = tid; e < K; e += NT) {
     const int tau = e >> (2 * LOGT), r = (e >> LOGT) & (T - 1), cc = e & (T - 1);
     const int m = __brev(r) >> (32 - LOGT), n = __brev(cc) >> (32 - LOGT);
@@ -213,6 +213,7 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
           // transform of w (W[0] among it) stays finite
           bad |= !isfinite(f0);
           const float f = isfinite(f0) ? f0 : 0.f;
+          nzf |= f != 0.f;
           ff x = ff_two_prod(w.x, f);
           x.l = __fmaf_rn(w.y, f, x.l);
           z = {ff_fast_two_sum(x.h, x.l), {w.x, w.y}};
@@ -222,6 +223,9 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
     A::store(Zg, ((tau << LOGT) | r) * T2 + cc, T, z);
   }
   int any_bad = __syncthreads_or(bad);
+  // f = 0 on the whole support: R0 = DFT(w f) is exactly zero (the packed
+  // transform would leave W's rounding in it, about 1e-16 of |W|)
+  const bool zero_f = !__syncthreads_or(nzf);
 
   // ---- 2. 2-D FFT per frame (float-float), then the DFT over the frames ----
   for (int tau = 0; tau < Lt; ++tau) fft2d_chunked<T, NT>(Zg + (size_t)tau * T * T2, Whi, a.tab, Ls);
@@ -260,7 +264,7 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
     const int x = ((k3 << LOGT) | k1) * T2 + k2;
     const int mx = ((((TT - k3) & (TT - 1)) << LOGT) | ((T - k1) & (T - 1))) * T2 + ((T - k2) & (T - 1));
     const C za = A::load(Zg, x, T), zm = A::load(Zg, mx, T);
-    const C r = A::half(A::add(za, A::conj(zm)));
+    const C r = zero_f ? A::zero() : A::half(A::add(za, A::conj(zm)));
     if (!A::finite(r)) bad = true;
     Rx[slot] = make_float4(r.re.h, r.re.l, r.im.h, r.im.l);
     return make_float2(r.re.h, r.im.h);
@@ -310,13 +314,15 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
   if (W0c.re.h == 0.f) st = FOFSE_BLK_NO_SUPPORT;
   else if (any_bad || !isfinite(W0c.re.h)) st = FOFSE_BLK_NONFINITE;
 
+  int done_it = 0;  // iterations the loop ran (any later one repeats a zero residual's (0, 0, 0), 0)
   if (st == FOFSE_BLK_OK) {
     const ff inv = ff_div(ff{a.gamma_h, a.gamma_l}, W0c.re);
     const float W0f = W0c.re.h * (1.f + 1e-6f);
     const char* wb8 = reinterpret_cast<const char*>(Whi);
     float bnd = 0.f, prevabs = 0.f, csum = 0.f;
+    int it = 0;
 #pragma unroll 1
-    for (int it = 0; it < iters; ++it) {
+    for (; it < iters; ++it) {
       // ---- top-2 over the block (packed keys) ----
       const unsigned wm1 = __reduce_max_sync(kFull, m1k);
       const unsigned hold = __ballot_sync(kFull, m1k == wm1);
@@ -506,6 +512,14 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
         }
         if (pos < 0) ++nd;
       }
+      // The winner is the exact maximum, so an exactly zero winner means a
+      // zero residual in every bin: every later iteration selects the
+      // smallest index, (0, 0, 0) (which this one did), with a zero
+      // coefficient; they are written as such at the end instead of being run.
+      if (Rt.re.h == 0.f && Rt.re.l == 0.f && Rt.im.h == 0.f && Rt.im.l == 0.f) {
+        ++it;
+        break;
+      }
       // ---- FP32 update of the working spectrum + next top-2 keys ----
       const float p = c.re.h, q = c.im.h;
       prevabs = fabsf(p) + fabsf(q);
@@ -560,6 +574,7 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
       m1k = k1a;
       m2k = k2a;
     }
+    done_it = it;
   }
   if (tid == 0) *nd_s = nd;  // thread 0 is in warp 0, which holds the count
   __syncthreads();
@@ -581,8 +596,8 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
     }
     a.out[(size_t)blk * b * b + pidx] = acc;
   }
-  if (st != FOFSE_BLK_OK) {
-    for (int i = tid; i < iters; i += NT) {
+  {  // the iterations that did not run: (0, 0, 0) with a zero coefficient
+    for (int i = done_it + tid; i < iters; i += NT) {
       const size_t o = (size_t)blk * iters + i;
       if (a.path) a.path[3 * o] = a.path[3 * o + 1] = a.path[3 * o + 2] = 0;
       if (a.coef) a.coef[2 * o] = a.coef[2 * o + 1] = 0.0;
