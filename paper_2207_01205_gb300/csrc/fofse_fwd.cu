@@ -352,7 +352,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
   using Mask = typename std::conditional<(PER > 32), unsigned long long, unsigned>::type;
   float fv[PER];
   Mask use = 0;
-  bool bad = false;
+  bool bad = false, nzf = false;
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
     const int e = tid + s * NT;
@@ -380,11 +380,15 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
           use |= Mask(1) << s;
           fv[s] = f;
           bad |= !isfinite(f);
+          nzf |= f != 0.f;
         }
       }
     }
   }
   int any_bad = __syncthreads_or(bad);  // the staging area may be overwritten below
+  // f = 0 on the whole support: R_w = DFT(w f) is exactly zero (the packed
+  // transform would leave W's rounding in it)
+  const bool zero_f = !__syncthreads_or(nzf);
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
     const int e = tid + s * NT;
@@ -419,7 +423,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& args, const CUtenso
     const int k1 = x >> (LOGT + 1), k2 = x & (T2 - 1);
     const int mx = ((T - k1) & (T - 1)) * T2 + ((T - k2) & (T - 1));
     const C a = A::load(Z, x, T), m = A::load(Z, mx, T);
-    const C r = A::half(A::add(a, A::conj(m)));
+    const C r = zero_f ? A::zero() : A::half(A::add(a, A::conj(m)));
     if (!A::finite(r)) bad = true;
     if (i < NB) {
       kc[i] = x | (code_of<T>(x) << 16);

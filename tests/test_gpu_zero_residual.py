@@ -3,7 +3,8 @@ zero in every bin from the start, so every iteration selects the smallest
 index, (0, 0), with a zero coefficient.  The kernels resolve the first such
 iteration exactly and write the remaining ones as such instead of running
 them; paths, coefficients and blocks must equal the oracle's, beside ordinary
-blocks of the same batch (DFT and DCT bases, video volumes)."""
+blocks of the same batch (DFT and DCT bases, every precision, video
+volumes)."""
 import dataclasses
 
 import numpy as np
@@ -25,16 +26,19 @@ def _lib(gpu_lib):
 
 SPECS = [synth.PlanSpec(16, 16, 64, 0.8, 0.5, 60), synth.PlanSpec(8, 8, 32, 0.8, 0.5, 40),
          synth.PlanSpec(32, 16, 128, 0.8, 0.5, 30)]
-CASES = [(s, basis) for s in SPECS for basis in (0, 1) if not (basis == 1 and s.fft_size == 128)]
+CASES = [(s, basis, prec) for s in SPECS for basis in (0, 1) for prec in ("fp32", "fp32_fullff", "fp64")
+         if not (basis == 1 and (s.fft_size == 128 or prec == "fp64"))
+         and not (prec != "fp32" and s.fft_size == 128)]
 
 
-@pytest.mark.parametrize("spec,basis", CASES, ids=[f"T{s.fft_size}-basis{b}" for s, b in CASES])
-def test_zero_support_blocks_match_the_oracle(spec, basis):
+@pytest.mark.parametrize("spec,basis,precision", CASES,
+                         ids=[f"T{s.fft_size}-basis{b}-{q}" for s, b, q in CASES])
+def test_zero_support_blocks_match_the_oracle(spec, basis, precision):
     spec = dataclasses.replace(spec, basis=basis)
     wl = synth.small_frame(41, height=160, width=256, plan=spec, n_lost=10)
     wl.frame[:, : wl.frame.shape[1] // 2] = 0.0  # a black left half
     ora = oracle.run_batch(wl.frame, wl.avail, wl.blocks, wl.plans)
-    res, _ = run_gpu(wl, "fp32")
+    res, _ = run_gpu(wl, precision)
     c = compare(wl, res, ora)
     assert c["status_equal"]
     assert c["same"] == c["n"], (c["diverged"], c["gaps"])
