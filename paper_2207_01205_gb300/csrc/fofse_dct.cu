@@ -390,6 +390,9 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
       }
       float bnd = 0.f, prevabs = 0.f, csum = 0.f;
       int nd = 0;  // terms in the list (warp 0 maintains it; the others read it each iteration)
+      // entries before nb belong to coefficients taken into R0 by a rebase
+      // (below): they count for the synthesis only
+      int nb = 0;
       __syncthreads();
       int it = 0;
 #pragma unroll 1
@@ -433,8 +436,8 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
           u2 = wt & (T - 1);
           const float2 rx = R0x[wt + li * NT];
           long long sv = 0;
-          if (warp * 32 < nd) {  // warp-uniform: this warp holds terms
-            sv = dct_recur<T>(ct, trY, trCm, u1, u2, tid, nd, NT, scale);
+          if (warp * 32 < nd - nb) {  // warp-uniform: this warp holds terms
+            sv = dct_recur<T>(ct, trY, trCm, u1, u2, nb + tid, nd, NT, scale);
             sv = redux_sum64(sv);
           }
           if (lane == 0) redx[warp] = make_longlong2(sv, 0);
@@ -466,7 +469,44 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
           const int rank0 = before + incl - cnt;
           ff wbe = {-1.f, 0.f}, wbr = {0.f, 0.f};
           int wbl = 0x7fffffff;
-          for (int pass = 0; pass < total; pass += LIST) {
+          const bool rebase = total > T * T / 4;
+          if (rebase) {
+            // ---- rebase: the bound has grown to the size of the residual
+            // (a residual that decays far, as over flat content) and nearly
+            // every bin is a candidate.  Each thread evaluates its own bins
+            // exactly; these values become R0 (the recurrence continues from
+            // entry nb), R32 their FP32 roundings, and the bound restarts.
+#pragma unroll 1
+            for (int j = 0; j < NB; ++j) {
+              const int k1 = r0 + j * RS, lin = k1 * T + k2;
+              const float2 rx = R0x[tid + j * NT];
+              const long long sv = dct_recur<T>(ct, trY, trCm, k1, k2, nb, nd, 1, scale);
+              const ff rv = ff_sub(ff{rx.x, rx.y}, fx_to_ff(sv, iscale));
+              R0x[tid + j * NT] = make_float2(rv.h, rv.l);
+              const ff ev = dct_energy(rv, (k1 > 0 ? 2.f : 1.f) * (k2 > 0 ? 2.f : 1.f));
+              if (better(ev, lin, wbe, wbl)) {
+                wbe = ev;
+                wbl = lin;
+                wbr = rv;
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < NB; ++j) R32[j] = R0x[tid + j * NT].x;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const ff oe = {__shfl_xor_sync(kFullMask, wbe.h, o), __shfl_xor_sync(kFullMask, wbe.l, o)};
+              const ff orv = {__shfl_xor_sync(kFullMask, wbr.h, o), __shfl_xor_sync(kFullMask, wbr.l, o)};
+              const int ol = __shfl_xor_sync(kFullMask, wbl, o);
+              if (better(oe, ol, wbe, wbl)) {
+                wbe = oe;
+                wbl = ol;
+                wbr = orv;
+              }
+            }
+            nb = nd;
+            csum = 0.f;
+          }
+          for (int pass = 0; !rebase && pass < total; pass += LIST) {
             int r = rank0;
 #pragma unroll
             for (int j = 0; j < NB; ++j) {
@@ -482,7 +522,7 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
               const int4 e = list[c];
               const int c1 = e.x / T, c2 = e.x - c1 * T;
               const float2 rx = R0x[e.y];
-              long long sv = dct_recur<T>(ct, trY, trCm, c1, c2, lane, nd, 32, scale);
+              long long sv = dct_recur<T>(ct, trY, trCm, c1, c2, nb + lane, nd, 32, scale);
               sv = redux_sum64(sv);
               const ff rv = ff_sub(ff{rx.x, rx.y}, fx_to_ff(sv, iscale));
               const ff ev = dct_energy(rv, __int_as_float(e.z));
@@ -515,6 +555,10 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
           if (bl == 0x7fffffff) bl = 0;  // no candidate (cannot happen for finite data)
           u1 = bl / T;
           u2 = bl - u1 * T;
+          // after a rebase the bound restarts from the roundings of the new
+          // R0 to FP32: u |R[k]| <= 2u |R[u]| (e_u R[u]^2 is the largest
+          // e_k R[k]^2 and e_k / e_u >= 1/4)
+          if (rebase) bnd = 2.f * kA * fabsf(Rt.h) * kUp;
         }
         // ---- coefficient (Eq. 5, Eq. 14) ----
         const float2 n0 = ct[0], n1c = ct[2 * u1 * S], n2c = ct[2 * u2], n3 = ct[2 * u1 * S + 2 * u2];
@@ -527,7 +571,7 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
         if (warp == 0) {
           const short y = (short)(u1 * T + u2);
           int pos = -1;
-          for (int j0 = 0; j0 < nd; j0 += 32) {
+          for (int j0 = nb; j0 < nd; j0 += 32) {
             const int jj = j0 + lane;
             const unsigned hit = __ballot_sync(kFullMask, jj < nd && trY[jj] == y);
             if (hit) {

@@ -50,6 +50,9 @@ template <int T, int NT> struct F3 {
   static constexpr int RS = 2 * NT / T;  // rows between a thread's consecutive bins
   static constexpr int IB = NB / 2;      // the bin whose row is T/2 + r_t
   static constexpr int LIST = 32;        // near-tie candidates per pass
+  // near-tie candidates beyond which the exact values of every bin are taken
+  // as a new R0 instead (evaluating them all costs about as much)
+  static constexpr int REBASE = NSLOT / 4;
   static constexpr bool STATIC_W = T <= 64;
   static_assert(NSLOT % NT == 0 && NB >= 2 && NB <= 64 && NW >= 1 && (NW & (NW - 1)) == 0,
                 "slot grid");
@@ -424,6 +427,9 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
   int* nd_s = reinterpret_cast<int*>(dsm + G::nd_off);
   float2* Wlo = G::lo_smem(iters) ? reinterpret_cast<float2*>(dsm + G::lo_off(iters)) : nullptr;
   int nd = 0;  // entries in the list (warp 0 maintains it; the others read it each iteration)
+  // entries before nb belong to coefficients taken into R0 by a rebase (below):
+  // they count for the synthesis only, the recurrence sums entries nb .. nd
+  int nb = 0;
   float2* Zg = reinterpret_cast<float2*>(cta_scratch);
   float4* Rx = reinterpret_cast<float4*>(cta_scratch + G::z_bytes);
   // OFSE: the packed FFT of w^2 f + j w^2, then the exact V = DFT(w^2) (the
@@ -634,8 +640,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           long long sre = 0, sim = 0;
           long long Sr = 0, Si = 0;
           if constexpr (NW <= 4) {
-            if (warp * 32 < nd) {  // warp-uniform: this warp holds terms
-              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, wk1 * T2 + wk2, tid, nd, NT, scale, sre, sim);
+            if (warp * 32 < nd - nb) {  // warp-uniform: this warp holds terms
+              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, wk1 * T2 + wk2, nb + tid, nd, NT, scale, sre, sim);
               warp_sum64(sre, sim);
             }
             if (lane == 0) red[warp] = make_longlong2(sre, sim);
@@ -647,8 +653,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               Si += v.y;
             }
           } else {
-            if (warp * 32 < nd) {
-              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, wk1 * T2 + wk2, tid, nd, NT, scale, sre, sim);
+            if (warp * 32 < nd - nb) {
+              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, wk1 * T2 + wk2, nb + tid, nd, NT, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
             }
@@ -685,6 +691,53 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           const int rank0 = before + incl - cnt;
           ffc wb = {{0.f, 0.f}, {0.f, 0.f}};
           int wbc = 0x7fffffff, wbx = 0;
+          if (!OFSE && total > G::REBASE) {
+            // ---- rebase: when the bound has grown to the size of the
+            // residual (a residual that decays far, as over flat content)
+            // nearly every bin is a candidate.  Each thread then evaluates
+            // its own bins exactly, these values become R0 (the coefficients
+            // so far are folded in: the recurrence continues from entry nb),
+            // R32 their FP32 roundings, and the bound restarts from their
+            // rounding.  The winner is their exact maximum.
+            for (int i = 0; i <= NB; ++i) {
+              if (i == NB && tid >= 2) break;
+              const int2 kk = i < NB ? f3_bin<T, NT>(tid, i) : f3_extra<T>(tid);
+              const int x = kk.x * T2 + kk.y, slot = i < NB ? tid + i * NT : NSLOT + tid;
+              long long sre = 0, sim = 0;
+              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, x, nb, nd, 1, scale, sre, sim);
+              const float4 r0 = Rx[slot];
+              const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
+                             ff_sub(ff{r0.z, r0.w}, fx_to_ff(sim, iscale))};
+              Rx[slot] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+              const int code = f3_code<T>(kk.x, kk.y);
+              if (wbc == 0x7fffffff || exact_better(v, code, wb, wbc)) {
+                wb = v;
+                wbc = code;
+                wbx = x;
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+              const float4 r = Rx[tid + i * NT];
+              R32[i] = make_float2(r.x, r.z);
+            }
+            if (tid < 2) {
+              const float4 r = Rx[NSLOT + tid];
+              rex = make_float2(r.x, r.z);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const ffc ov = ffc_shfl(wb, o);
+              const int oc = __shfl_xor_sync(kFull, wbc, o), ox = __shfl_xor_sync(kFull, wbx, o);
+              if (exact_better(ov, oc, wb, wbc)) {
+                wb = ov;
+                wbc = oc;
+                wbx = ox;
+              }
+            }
+            nb = nd;
+            csum = 0.f;
+          } else {
           for (int pass = 0; pass < total; pass += LIST) {
             int r = rank0;
 #pragma unroll
@@ -707,7 +760,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               const int4 e = list[c];
               const float4 r0 = Rx[e.z];
               long long sre = 0, sim = 0;
-              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, e.x, lane, nd, 32, scale, sre, sim);
+              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, e.x, nb + lane, nd, 32, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
               const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
@@ -719,6 +772,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               }
             }
             __syncthreads();
+          }
           }
           if (lane == 0) {
             wwv[warp] = make_float4(wb.re.h, wb.re.l, wb.im.h, wb.im.l);
@@ -741,6 +795,10 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           }
           wk1 = wx >> (LOGT + 1);
           wk2 = wx & (T2 - 1);
+          // after a rebase the bound restarts: the roundings of the new R0 to
+          // FP32 (u of the largest value, the winner's) are covered by the
+          // first increment, as for the first R0
+          if (!OFSE && total > G::REBASE) bnd = kA * (fabsf(Rt.re.h) + fabsf(Rt.im.h)) * kUp;
         }
         // ---- exact coefficient (Eq. 5, Eq. 14) of the held winner ----
         const bool mir = wk1 > T / 2;
@@ -763,8 +821,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
           longlong2* red2 = red + NW;
           long long sre = 0, sim = 0, Sr = 0, Si = 0;
           if constexpr (NW <= 4) {
-            if (warp * 32 < nd) {
-              recur_fixed<T, true>(Whi, Vg, nullptr, trY, trC, xw, tid, nd, NT, scale, sre, sim);
+            if (warp * 32 < nd - nb) {
+              recur_fixed<T, true>(Whi, Vg, nullptr, trY, trC, xw, nb + tid, nd, NT, scale, sre, sim);
               warp_sum64(sre, sim);
             }
             if (lane == 0) red2[warp] = make_longlong2(sre, sim);
@@ -776,8 +834,8 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
               Si += v.y;
             }
           } else {
-            if (warp * 32 < nd) {
-              recur_fixed<T, true>(Whi, Vg, nullptr, trY, trC, xw, tid, nd, NT, scale, sre, sim);
+            if (warp * 32 < nd - nb) {
+              recur_fixed<T, true>(Whi, Vg, nullptr, trY, trC, xw, nb + tid, nd, NT, scale, sre, sim);
               sre = redux_sum64(sre);
               sim = redux_sum64(sim);
             }
@@ -816,7 +874,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
                                 : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
           const short y = (short)(u1 * T2 + u2);
           int pos = -1;
-          for (int j0 = 0; j0 < nd; j0 += 32) {
+          for (int j0 = nb; j0 < nd; j0 += 32) {
             const int j = j0 + lane;
             const unsigned hit = __ballot_sync(kFull, j < nd && trY[j] == y);
             if (hit) {
@@ -917,7 +975,7 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
       {
         // every earlier pick was the DC bin: its single list entry holds the
         // sum C (the entry is not written in this iteration)
-        const float4 c0 = trC[0];
+        const float4 c0 = nd > nb ? trC[nb] : make_float4(0.f, 0.f, 0.f, 0.f);
         const ff Cs = {c0.x, c0.y};
 #pragma unroll
         for (int i = 0; i <= NB; ++i) {

@@ -187,6 +187,9 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
   // packed indices of the recurrence's terms (16 bits hold every supported grid's)
   unsigned short* trY = reinterpret_cast<unsigned short*>(dsm + G::try_off(iters));
   int nd = 0;
+  // entries before nb belong to coefficients taken into R0 by a rebase
+  // (below): they count for the synthesis only
+  int nb = 0;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -366,8 +369,8 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
         const int wslot = li < NB ? (wt + (li / TT) * NT) * TT + k3 : (NS2 + (wt & 1)) * TT + k3;
         const float4 r0 = Rx[wslot];
         long long sre = 0, sim = 0, Sr = 0, Si = 0;
-        if (warp * 32 < nd) {
-          vrecur<T, TT, NT>(Whi, Zg, trY, trC, I::pack(wk1, wk2, wk3), tid, nd, NT, scale, sre, sim);
+        if (warp * 32 < nd - nb) {
+          vrecur<T, TT, NT>(Whi, Zg, trY, trC, I::pack(wk1, wk2, wk3), nb + tid, nd, NT, scale, sre, sim);
           sre = redux_sum64(sre);
           sim = redux_sum64(sim);
         }
@@ -411,7 +414,56 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
           const int cl = k1 > T / 2 ? I::lin(I::neg(p)) : I::lin(p);
           return make_int4(p, cl, slot, 0);
         };
-        for (int pass = 0; pass < total; pass += LIST) {
+        const bool rebase = total > T * T * TT / 8;
+        if (rebase) {
+          // ---- rebase: the bound has grown to the size of the residual
+          // (a residual that decays far, as over flat content) and nearly
+          // every bin is a candidate.  Each thread evaluates its own bins
+          // exactly; these values become R0 (the recurrence continues from
+          // entry nb), R32 their FP32 roundings, and the bound restarts.
+#pragma unroll 1
+          for (int i = 0; i <= NB; ++i) {
+            if (i == NB && !hasx) break;
+            const int2 kk = i < NB ? f3_bin<T, NT>(tid, i / TT) : f3_extra<T>(tid & 1);
+            const int k3 = i < NB ? i % TT : tid >> 1;
+            const int slot = i < NB ? (tid + (i / TT) * NT) * TT + k3 : (NS2 + (tid & 1)) * TT + k3;
+            const int4 e = cand(kk.x, kk.y, k3, slot);
+            const float4 r0 = Rx[slot];
+            long long sre = 0, sim = 0;
+            vrecur<T, TT, NT>(Whi, Zg, trY, trC, e.x, nb, nd, 1, scale, sre, sim);
+            const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
+                           ff_sub(ff{r0.z, r0.w}, fx_to_ff(sim, iscale))};
+            Rx[slot] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+            const bool live = i < NB ? !((dead >> i) & 1u) : !xdead;
+            if (live && (wbc == 0x7fffffff || exact_better(v, e.y, wb, wbc))) {
+              wb = v;
+              wbc = e.y;
+              wbx = e.x;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < NB; ++i) {
+            const float4 r = Rx[(tid + (i / TT) * NT) * TT + i % TT];
+            R32[i] = make_float2(r.x, r.z);
+          }
+          if (hasx) {
+            const float4 r = Rx[(NS2 + (tid & 1)) * TT + (tid >> 1)];
+            rex = make_float2(r.x, r.z);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const ffc ov = ffc_shfl(wb, o);
+            const int oc = __shfl_xor_sync(kFull, wbc, o), ox = __shfl_xor_sync(kFull, wbx, o);
+            if (oc != 0x7fffffff && (wbc == 0x7fffffff || exact_better(ov, oc, wb, wbc))) {
+              wb = ov;
+              wbc = oc;
+              wbx = ox;
+            }
+          }
+          nb = nd;
+          csum = 0.f;
+        }
+        for (int pass = 0; !rebase && pass < total; pass += LIST) {
           int r = rank0;
 #pragma unroll
           for (int i = 0; i < NB; ++i) {
@@ -433,7 +485,7 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
             const int4 e = list[c];
             const float4 r0 = Rx[e.z];
             long long sre = 0, sim = 0;
-            vrecur<T, TT, NT>(Whi, Zg, trY, trC, e.x, lane, nd, 32, scale, sre, sim);
+            vrecur<T, TT, NT>(Whi, Zg, trY, trC, e.x, nb + lane, nd, 32, scale, sre, sim);
             sre = redux_sum64(sre);
             sim = redux_sum64(sim);
             const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
@@ -468,6 +520,10 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
         wk1 = (wx >> G::SH1) & (T - 1);
         wk2 = wx & (T - 1);
         wk3 = wx >> G::SH3;
+        // after a rebase the bound restarts: the roundings of the new R0 to
+        // FP32 (u of the largest value, the winner's) are covered by the
+        // first increment, as for the first R0
+        if (rebase) bnd = kA * (fabsf(Rt.re.h) + fabsf(Rt.im.h)) * kUp;
       }
       // ---- exact coefficient (Eq. 5, Eq. 14) of the held winner ----
       const int wp = I::pack(wk1, wk2, wk3);
@@ -482,7 +538,7 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
         const float4 cc = mir ? make_float4(c.re.h, c.re.l, -c.im.h, -c.im.l)
                               : make_float4(c.re.h, c.re.l, c.im.h, c.im.l);
         int pos = -1;
-        for (int j0 = 0; j0 < nd; j0 += 32) {
+        for (int j0 = nb; j0 < nd; j0 += 32) {
           const int j = j0 + lane;
           const unsigned hit = __ballot_sync(kFull, j < nd && trY[j] == up);
           if (hit) {
