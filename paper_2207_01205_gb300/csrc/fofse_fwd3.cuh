@@ -388,6 +388,39 @@ __device__ __forceinline__ void fft2d_chunked(float2* Z, float2* buf, const Plan
   }
 }
 
+// The rebase of the FP32 loop (out of line: it runs rarely and keeps the hot
+// loop's code small): the exact values of thread tid's held bins, R0 minus
+// the terms nb .. nd of the list, written over R0 in the scratch (Rx); returns
+// the thread's best of them (exact comparison) as (slot, 0, code, packed
+// index).
+template <int T, int NT>
+__device__ __noinline__ int4 f3_rebase_bins(const float2* Whi, const float2* Zg, const float2* Wlo,
+                                            const short* trY, const float4* trC, float4* Rx, int tid,
+                                            int nb, int nd, float scale, float iscale) {
+  using G = F3<T, NT>;
+  constexpr int T2 = 2 * T;
+  ffc wb = {{0.f, 0.f}, {0.f, 0.f}};
+  int wbc = 0x7fffffff, wbx = 0, wbs = 0;
+  for (int i = 0; i <= G::NB; ++i) {
+    if (i == G::NB && tid >= 2) break;
+    const int2 kk = i < G::NB ? f3_bin<T, NT>(tid, i) : f3_extra<T>(tid);
+    const int x = kk.x * T2 + kk.y, slot = i < G::NB ? tid + i * NT : G::NSLOT + tid;
+    long long sre = 0, sim = 0;
+    recur_fixed<T>(Whi, Zg, Wlo, trY, trC, x, nb, nd, 1, scale, sre, sim);
+    const float4 r0 = Rx[slot];
+    const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)), ff_sub(ff{r0.z, r0.w}, fx_to_ff(sim, iscale))};
+    Rx[slot] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+    const int code = f3_code<T>(kk.x, kk.y);
+    if (wbc == 0x7fffffff || exact_better(v, code, wb, wbc)) {
+      wb = v;
+      wbc = code;
+      wbx = x;
+      wbs = slot;
+    }
+  }
+  return make_int4(wbs, 0, wbc, wbx);
+}
+
 template <int T, int NT, bool OFSE>
 __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUtensorMap* tmF,
                                                  const CUtensorMap* tmA, int blk, float2* Whi,
@@ -699,22 +732,12 @@ __device__ __forceinline__ void forward_block_f3(const FwdArgs& args, const CUte
             // so far are folded in: the recurrence continues from entry nb),
             // R32 their FP32 roundings, and the bound restarts from their
             // rounding.  The winner is their exact maximum.
-            for (int i = 0; i <= NB; ++i) {
-              if (i == NB && tid >= 2) break;
-              const int2 kk = i < NB ? f3_bin<T, NT>(tid, i) : f3_extra<T>(tid);
-              const int x = kk.x * T2 + kk.y, slot = i < NB ? tid + i * NT : NSLOT + tid;
-              long long sre = 0, sim = 0;
-              recur_fixed<T>(Whi, Zg, Wlo, trY, trC, x, nb, nd, 1, scale, sre, sim);
-              const float4 r0 = Rx[slot];
-              const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
-                             ff_sub(ff{r0.z, r0.w}, fx_to_ff(sim, iscale))};
-              Rx[slot] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
-              const int code = f3_code<T>(kk.x, kk.y);
-              if (wbc == 0x7fffffff || exact_better(v, code, wb, wbc)) {
-                wb = v;
-                wbc = code;
-                wbx = x;
-              }
+            {
+              const int4 r = f3_rebase_bins<T, NT>(Whi, Zg, Wlo, trY, trC, Rx, tid, nb, nd, scale, iscale);
+              wbc = r.z;
+              wbx = r.w;
+              const float4 v = Rx[r.x];  // the best value, as written
+              wb = {{v.x, v.y}, {v.z, v.w}};
             }
 #pragma unroll
             for (int i = 0; i < NB; ++i) {
