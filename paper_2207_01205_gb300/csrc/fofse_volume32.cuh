@@ -159,6 +159,43 @@ __device__ __forceinline__ void vrecur(const float2* Whi, const float2* Zg, cons
   }
 }
 
+// The rebase of the FP32 loop (out of line: it runs rarely and keeps the hot
+// loop's code small): the exact values of thread tid's held bins, R0 minus
+// the terms nb .. nd of the list, written over R0 in the scratch (Rx); returns
+// the thread's best live bin (exact comparison, ties to the smallest lin of
+// the canonical member) as (slot, 0, lin, packed index), lin 0x7fffffff if
+// none.
+template <int T, int TT, int NT>
+__device__ __noinline__ int4 vol_rebase_bins(const float2* Whi, const float2* Zg, const unsigned short* trY,
+                                             const float4* trC, float4* Rx, int tid, int nb, int nd,
+                                             float scale, float iscale, unsigned dead, bool hasx, bool xdead) {
+  using G = V3<T, TT, NT>;
+  using I = VIdx<T, TT, NT>;
+  ffc wb = {{0.f, 0.f}, {0.f, 0.f}};
+  int wbc = 0x7fffffff, wbx = 0, wbs = 0;
+  for (int i = 0; i <= G::NB; ++i) {
+    if (i == G::NB && !hasx) break;
+    const int2 kk = i < G::NB ? f3_bin<T, NT>(tid, i / TT) : f3_extra<T>(tid & 1);
+    const int k3 = i < G::NB ? i % TT : tid >> 1;
+    const int slot = i < G::NB ? (tid + (i / TT) * NT) * TT + k3 : (G::NS2 + (tid & 1)) * TT + k3;
+    const int pk = I::pack(kk.x, kk.y, k3);
+    const int cl = kk.x > T / 2 ? I::lin(I::neg(pk)) : I::lin(pk);
+    const float4 r0 = Rx[slot];
+    long long sre = 0, sim = 0;
+    vrecur<T, TT, NT>(Whi, Zg, trY, trC, pk, nb, nd, 1, scale, sre, sim);
+    const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)), ff_sub(ff{r0.z, r0.w}, fx_to_ff(sim, iscale))};
+    Rx[slot] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+    const bool live = i < G::NB ? !((dead >> i) & 1u) : !xdead;
+    if (live && (wbc == 0x7fffffff || exact_better(v, cl, wb, wbc))) {
+      wb = v;
+      wbc = cl;
+      wbx = pk;
+      wbs = slot;
+    }
+  }
+  return make_int4(wbs, 0, wbc, wbx);
+}
+
 template <int T, int TT, int NT>
 __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, unsigned char* dsm,
                                                  float2* Whi, float2* Zg, float4* Rx) {
@@ -421,25 +458,13 @@ __device__ __forceinline__ void volume_block_f32(const VolArgs32& a, int blk, un
           // every bin is a candidate.  Each thread evaluates its own bins
           // exactly; these values become R0 (the recurrence continues from
           // entry nb), R32 their FP32 roundings, and the bound restarts.
-#pragma unroll 1
-          for (int i = 0; i <= NB; ++i) {
-            if (i == NB && !hasx) break;
-            const int2 kk = i < NB ? f3_bin<T, NT>(tid, i / TT) : f3_extra<T>(tid & 1);
-            const int k3 = i < NB ? i % TT : tid >> 1;
-            const int slot = i < NB ? (tid + (i / TT) * NT) * TT + k3 : (NS2 + (tid & 1)) * TT + k3;
-            const int4 e = cand(kk.x, kk.y, k3, slot);
-            const float4 r0 = Rx[slot];
-            long long sre = 0, sim = 0;
-            vrecur<T, TT, NT>(Whi, Zg, trY, trC, e.x, nb, nd, 1, scale, sre, sim);
-            const ffc v = {ff_sub(ff{r0.x, r0.y}, fx_to_ff(sre, iscale)),
-                           ff_sub(ff{r0.z, r0.w}, fx_to_ff(sim, iscale))};
-            Rx[slot] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
-            const bool live = i < NB ? !((dead >> i) & 1u) : !xdead;
-            if (live && (wbc == 0x7fffffff || exact_better(v, e.y, wb, wbc))) {
-              wb = v;
-              wbc = e.y;
-              wbx = e.x;
-            }
+          {
+            const int4 r = vol_rebase_bins<T, TT, NT>(Whi, Zg, trY, trC, Rx, tid, nb, nd, scale, iscale,
+                                                      dead, hasx, xdead);
+            wbc = r.z;
+            wbx = r.w;
+            const float4 v = Rx[r.x];  // the best value, as written
+            wb = {{v.x, v.y}, {v.z, v.w}};
           }
 #pragma unroll
           for (int i = 0; i < NB; ++i) {
