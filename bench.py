@@ -46,13 +46,13 @@ L2_FLUSH_BYTES = 512 << 20
 OPS_PER_BIN_ITER = 14
 # DRAM bytes of one launch of the product kernel on the 1080p batch, launch
 # shape 0, from an ncu capture of the current kernel (dram__bytes_read.sum
-# 9.44 MB + dram__bytes_write.sum 66.06 MB: mostly the write-back of the
+# 9.01 MB + dram__bytes_write.sum 60.99 MB: mostly the write-back of the
 # per-CTA scratch, not algorithmic bytes)
-F3_TRAFFIC_BYTES_1080P = 75.50e6
+F3_TRAFFIC_BYTES_1080P = 70.00e6
 # the same for the FP32 volume kernel on the three-frame 1080p batch, launch
-# shape 0 (dram__bytes_read.sum 20.01 MB + dram__bytes_write.sum 72.26 MB,
+# shape 0 (dram__bytes_read.sum 19.64 MB + dram__bytes_write.sum 71.37 MB,
 # again mostly scratch write-back)
-V3_TRAFFIC_BYTES_1080P = 92.27e6
+V3_TRAFFIC_BYTES_1080P = 91.01e6
 SMEM_BYTES_PER_BIN_ITER = 16
 OPS_PER_RECURRENCE_TERM = 66
 FP32_LANES_PER_SM = 128
