@@ -938,17 +938,22 @@ __global__ void __launch_bounds__(NT) fofse_backward_dct_kernel(const __grid_con
     cco[i] = t.dc_re;
     uu[i] = (t.u1 & (T - 1)) | ((t.u2 & (T - 1)) << 16);
   }
-  // this thread's samples of L: weight, value, model, adjoints
+  // this thread's samples of L: weight, value, model, adjoints.  Thread t
+  // holds column n = t mod Ls in rows t / Ls + k RB (RB = NT / Ls row groups;
+  // RB KS >= T >= Ls, so every sample of L has a thread): the threads of a
+  // warp share each row's cosine (a broadcast load) and each thread loads its
+  // column's cosine once per iteration.
   float wv[KS], fv[KS], gv[KS], gb[KS], fb[KS], wb[KS];
-  int mm[KS], nn[KS];
+  int mm[KS];
+  const int RB = NT / Ls, cn = tid % Ls, rb = tid / Ls;
+  const int pn = 2 * cn + 1;  // the column's phase step
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
-    const int x = tid + k * NT;
-    const int m = x / Ls, n = x - (x / Ls) * Ls;
-    mm[k] = x < Ls * Ls ? m : 0;
-    nn[k] = x < Ls * Ls ? n : 0;
+    const int m = rb + k * RB, n = cn;
+    const bool on = rb < RB && m < Ls;
+    mm[k] = on ? m : 0;
     wv[k] = fv[k] = gv[k] = gb[k] = fb[k] = wb[k] = 0.f;
-    if (x >= Ls * Ls) continue;
+    if (!on) continue;
     const bool inB = m >= br && m < br + b && n >= br && n < br + b;
     bool inS = true;
     if (P.support == FOFSE_SUPPORT_CAUSAL_L) inS = (m < br) ? (n < br + b) : (m < br + b ? n < br : false);
@@ -961,20 +966,21 @@ __global__ void __launch_bounds__(NT) fofse_backward_dct_kernel(const __grid_con
     if (inB) gb[k] = a.grad_blocks[(size_t)blk * a.grad_stride + (m - br) * a.grad_ld + (n - br)];
   }
   __syncthreads();
-  auto phi = [&](int u, int k) -> float {
-    const int u1 = u & 0xffff, u2 = u >> 16;
-    return cosT[(u1 * (2 * mm[k] + 1)) & (4 * T - 1)] * cosT[(u2 * (2 * nn[k] + 1)) & (4 * T - 1)];
+  // phi_u at sample k: the row's cosine times the column's (cc)
+  auto colcos = [&](int u) -> float { return cosT[((u >> 16) * pn) & (4 * T - 1)]; };
+  auto phi = [&](int u, int k, float cc) -> float {
+    return cosT[((u & 0xffff) * (2 * mm[k] + 1)) & (4 * T - 1)] * cc;
   };
   // ---- weighted norms N_i, and the final model g_I = sum_i c_i phi_i ----
   for (int i0 = 0; i0 < iters; i0 += CHI) {
     const int ni = min(CHI, iters - i0);
     for (int j = 0; j < ni; ++j) {
       const int u = uu[i0 + j];
-      const float c = cco[i0 + j];
+      const float c = cco[i0 + j], cc = colcos(u);
       float s = 0.f;
 #pragma unroll
       for (int k = 0; k < KS; ++k) {
-        const float ph = phi(u, k);
+        const float ph = phi(u, k, cc);
         s = __fmaf_rn(wv[k] * ph, ph, s);
         gv[k] = __fmaf_rn(c, ph, gv[k]);
       }
@@ -995,10 +1001,10 @@ __global__ void __launch_bounds__(NT) fofse_backward_dct_kernel(const __grid_con
   float gam_acc = 0.f;
   for (int i = iters - 1; i >= 0; --i) {
     const int u = uu[i];
-    const float c = cco[i];
+    const float c = cco[i], cc = colcos(u);
     float s = 0.f;
 #pragma unroll
-    for (int k = 0; k < KS; ++k) s = __fmaf_rn(gb[k], phi(u, k), s);
+    for (int k = 0; k < KS; ++k) s = __fmaf_rn(gb[k], phi(u, k, cc), s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFullMask, s, o);
     float* pw = part + (i & 1) * NW;  // double-buffered warp partials
@@ -1013,7 +1019,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_dct_kernel(const __grid_con
     const float pbar = gamma * cbar / N, nbar = -cbar * c / N;
 #pragma unroll
     for (int k = 0; k < KS; ++k) {
-      const float ph = phi(u, k);
+      const float ph = phi(u, k, cc);
       gv[k] = __fmaf_rn(-c, ph, gv[k]);  // g_{i-1}
       if (wv[k] != 0.f) {
         const float q = pbar * ph;
@@ -1028,7 +1034,7 @@ __global__ void __launch_bounds__(NT) fofse_backward_dct_kernel(const __grid_con
 #pragma unroll
   for (int k = 0; k < KS; ++k) {
     if (wv[k] == 0.f) continue;
-    const int m = mm[k], n = nn[k];
+    const int m = mm[k], n = cn;
     if (a.grad_frame) {
       const int fy = bd.y - br + m, fx = bd.x - br + n;
       atomicAdd(&a.grad_frame[(size_t)fy * a.pitch + fx], fb[k]);
