@@ -164,8 +164,9 @@ fofse_status fofse_plan_set_compensation(fofse_plan plan, int compensation);
  * adjoint of this basis' recursion (one block per CTA).  Selecting the DCT
  * basis builds, synchronously on the current device (the plan's), the basis'
  * product table C of the complete support -- every sample of L outside B, and
- * inside the support shape, usable -- for the plan's rho: (2T - 1) x 2T float
- * pairs (130 KB at fft_size 64), freed with the plan.  Every block starts
+ * inside the support shape, usable -- for the plan's rho, folded to indices
+ * 0..T (C[2T - a] = -C[a]): (T + 1) x (T + 2) float pairs (34 KB at fft_size
+ * 64), freed with the plan.  Every block starts
  * from it (C is linear in the weights; a block with missing samples subtracts
  * their part); a call with d_rho_gamma builds the table for its rho in its
  * workspace.  FOFSE_E_ARG for other values or another current device;

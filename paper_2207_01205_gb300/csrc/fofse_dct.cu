@@ -30,14 +30,16 @@ namespace {
 constexpr unsigned kFullMask = 0xffffffffu;
 
 template <int T, int NT> struct Dct {
-  static constexpr int TT = 2 * T - 1;      // rows / columns of C
-  static constexpr int S = 2 * T;           // row stride of C's planes (floats)
+  // C[a1, a2] is needed for 0 <= a < 2T - 1; since C[2T - a1, a2] =
+  // -C[a1, a2] (and the same in a2), the table holds a in [0, T] only
+  static constexpr int TC = T + 1;          // rows / columns of the table
+  static constexpr int S = T + 2;           // row stride of the table (float pairs)
   static constexpr int NB = T * T / NT;     // bins per thread
   static constexpr int RS = NT / T;         // rows between a thread's bins
   static constexpr int NW = NT / 32;
   static constexpr int CH = 16;             // rows of L per setup chunk
   static_assert(T * T % NT == 0 && NT % T == 0 && NB >= 1, "bin grid");
-  static constexpr size_t ct_bytes = sizeof(float2) * (size_t)TT * S;  // (hi, lo) pairs
+  static constexpr size_t ct_bytes = sizeof(float2) * (size_t)TC * S;  // (hi, lo) pairs
   static constexpr size_t cos_off = ct_bytes;                          // float2 [4T]
   static constexpr size_t red_off = cos_off + sizeof(float2) * 4 * T;  // float4 [2][NW], float2 [2][NW]
   // the FP32 loop's exchange slots: the same bytes as uint4 [2][NW] top-2 keys
@@ -51,8 +53,8 @@ template <int T, int NT> struct Dct {
   static constexpr size_t ndx_off = ww_off + 24 * NW;
   static constexpr size_t chunk_off = (ndx_off + 4 + 15) & ~size_t(15);
   // setup chunk: masked w and x = w f (CH x T each), then the row sums of C
-  // (CH x TT) and of R0 (CH x T), all float-float
-  static constexpr size_t chunk_bytes = sizeof(float2) * (size_t)CH * (T + T + TT + T);
+  // (CH x TC) and of R0 (CH x T), all float-float
+  static constexpr size_t chunk_bytes = sizeof(float2) * (size_t)CH * (T + T + TC + T);
   __host__ __device__ static size_t trace_bytes(int iters) { return 10 * (size_t)iters + 16; }
   // the FP32 loop keeps the exact R0 of every bin (float-float, by slot) and
   // the term list (distinct index, summed coefficient) in the chunk region
@@ -94,10 +96,10 @@ __device__ __forceinline__ float2 dct_row_sum(const float2* src, int a, int Ls, 
 template <int T, class Cos>
 __device__ __forceinline__ float2 dct_c_accumulate(float2 c0, const float2* zc, int a1, int a2,
                                                    int m0, int nr, Cos cosv) {
-  constexpr int TT = 2 * T - 1;
+  constexpr int TC = T + 1;
   ff acc = {c0.x, c0.y};
   for (int r = 0; r < nr; ++r) {
-    const float2 v = zc[r * TT + a2];
+    const float2 v = zc[r * TC + a2];
     ff_mac(acc, cosv(a1, m0 + r), ff{v.x, v.y});
   }
   acc = ff_norm(acc);
@@ -129,14 +131,14 @@ __device__ __forceinline__ void dct_row_sums(const float2* (&src)[KB], const int
 template <int T, int KB, class Cos>
 __device__ __forceinline__ void dct_c_accumulates(float2 (&c)[KB], const float2* zc, const int (&a1)[KB],
                                                   const int (&a2)[KB], int m0, int nr, Cos cosv) {
-  constexpr int TT = 2 * T - 1;
+  constexpr int TC = T + 1;
   ff acc[KB];
 #pragma unroll
   for (int k = 0; k < KB; ++k) acc[k] = {c[k].x, c[k].y};
   for (int r = 0; r < nr; ++r) {
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
-      const float2 v = zc[r * TT + a2[k]];
+      const float2 v = zc[r * TC + a2[k]];
       ff_mac(acc[k], cosv(a1[k], m0 + r), ff{v.x, v.y});
     }
   }
@@ -146,6 +148,15 @@ __device__ __forceinline__ void dct_c_accumulates(float2 (&c)[KB], const float2*
     c[k] = make_float2(r.h, r.l);
   }
 }
+
+// The table index of C's index a in [0, 2T - 1) and its sign: C[2T - a] =
+// -C[a], since cos(pi (2T - a)(2m+1) / (2T)) = -cos(pi a (2m+1) / (2T))
+template <int T> __device__ __forceinline__ int dct_fold(int a, float& sign) {
+  const bool hi = a > T;
+  sign = hi ? -1.f : 1.f;
+  return hi ? 2 * T - a : a;
+}
+__device__ __forceinline__ ff ff_sign(ff a, float s) { return {a.h * s, a.l * s}; }
 
 // (m, n) of L in the support shape and outside B
 __device__ __forceinline__ bool dct_in_support(int support, int m, int n, int b, int br) {
@@ -169,15 +180,18 @@ template <int T>
 __device__ __forceinline__ long long dct_recur(const float2* ct, const short* ty, const float2* tc,
                                                int k1, int k2, int j0, int j1, int stride,
                                                float scale) {
-  constexpr int S = 2 * T, LOGT = ilog2(T);
+  constexpr int S = T + 2, LOGT = ilog2(T);
   ff acc = {0.f, 0.f};
   for (int j = j0; j < j1; j += stride) {
     const int y = ty[j];
     const int v1 = y >> LOGT, v2 = y & (T - 1);
     const float2 cj = tc[j];
-    const int rp = (k1 + v1) * S, rm = abs(k1 - v1) * S, cp = k2 + v2, cm = abs(k2 - v2);
+    float sr, sc;
+    const int rp = dct_fold<T>(k1 + v1, sr) * S, rm = abs(k1 - v1) * S;
+    const int cp = dct_fold<T>(k2 + v2, sc), cm = abs(k2 - v2);
     const float2 a = ct[rp + cp], b = ct[rp + cm], c = ct[rm + cp], d = ct[rm + cm];
-    const ff sum = ff_add(ff_add(ff{a.x, a.y}, ff{b.x, b.y}), ff_add(ff{c.x, c.y}, ff{d.x, d.y}));
+    const ff sum = ff_add(ff_sign(ff_add(ff_sign(ff{a.x, a.y}, sc), ff{b.x, b.y}), sr),
+                          ff_add(ff_sign(ff{c.x, c.y}, sc), ff{d.x, d.y}));
     acc = ff_add(acc, ff_mul(ff{cj.x, cj.y}, sum));
   }
   const float sq = 0.25f * scale;  // the 1/4, exactly
@@ -196,7 +210,7 @@ template <int T, int NT, bool FILT>
 __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, unsigned char* dsm) {
   using G = Dct<T, NT>;
   using IO = PlanIO<ArFF>;
-  constexpr int TT = G::TT, S = G::S, NB = G::NB, RS = G::RS, NW = G::NW, CH = G::CH;
+  constexpr int TC = G::TC, S = G::S, NB = G::NB, RS = G::RS, NW = G::NW, CH = G::CH;
   float2* ct = reinterpret_cast<float2*>(dsm);
   float2* cosT = reinterpret_cast<float2*>(dsm + G::cos_off);
   float4* redv = reinterpret_cast<float4*>(dsm + G::red_off);             // [2][NW]: e.h, e.l, idx, -
@@ -204,8 +218,8 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   unsigned char* chunk = dsm + G::chunk_off;
   float2* wsm = reinterpret_cast<float2*>(chunk);                  // [CH][T]
   float2* xsm = wsm + CH * T;                                      // [CH][T]
-  float2* zc = xsm + CH * T;                                       // [CH][TT]
-  float2* yc = zc + CH * TT;                                       // [CH][T]
+  float2* zc = xsm + CH * T;                                       // [CH][TC]
+  float2* yc = zc + CH * TC;                                       // [CH][T]
   const PlanDev& P = args.plan;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int iters = P.iters, b = P.block, br = P.border, Ls = P.Ls;
@@ -228,9 +242,9 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
   if (have_table) {
     const float4* src = reinterpret_cast<const float4*>(P.tab.dct_c_full);
     float4* dst = reinterpret_cast<float4*>(ct);
-    for (int e = tid; e < TT * S / 2; e += NT) dst[e] = src[e];
+    for (int e = tid; e < TC * S / 2; e += NT) dst[e] = src[e];
   } else {
-    for (int e = tid; e < TT * S; e += NT) ct[e] = make_float2(0.f, 0.f);
+    for (int e = tid; e < TC * S; e += NT) ct[e] = make_float2(0.f, 0.f);
   }
   const int k2 = tid & (T - 1), r0 = tid / T;  // bins (r0 + j RS, k2)
   ff R[NB];
@@ -274,7 +288,7 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
     // (KB elements per thread and pass)
     constexpr int KB = 4;
     {
-      const int e0 = full ? CH * TT : 0, e1 = CH * (TT + T);
+      const int e0 = full ? CH * TC : 0, e1 = CH * (TC + T);
       for (int eb = e0 + tid; eb < e1; eb += KB * NT) {
         const float2* src[KB];
         int a[KB], dst[KB];
@@ -283,12 +297,12 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
           const int e = eb + k * NT;
           const bool on = e < e1;
           const int ec = on ? e : e0;
-          const bool isz = ec < CH * TT;
-          const int ee = isz ? ec : ec - CH * TT;
-          const int r = isz ? ee / TT : ee / T;
-          a[k] = isz ? ee - r * TT : ee - r * T;
+          const bool isz = ec < CH * TC;
+          const int ee = isz ? ec : ec - CH * TC;
+          const int r = isz ? ee / TC : ee / T;
+          a[k] = isz ? ee - r * TC : ee - r * T;
           src[k] = (isz ? wsm : xsm) + r * T;
-          dst[k] = on ? (isz ? r * TT + a[k] : CH * TT + r * T + a[k]) : -1;  // zc, then yc
+          dst[k] = on ? (isz ? r * TC + a[k] : CH * TC + r * T + a[k]) : -1;  // zc, then yc
         }
         float2 v[KB];
         dct_row_sums<T, KB>(src, a, Ls, cosv, v);
@@ -300,20 +314,20 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
     __syncthreads();
     // C[a1][a2] += sum_r cos(a1, m0 + r) zc[r][a2]
     if (!full) {
-      for (int eb = tid; eb < TT * TT; eb += KB * NT) {
+      for (int eb = tid; eb < TC * TC; eb += KB * NT) {
         int a1[KB], a2[KB];
         float2 c[KB];
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
-          const int e = eb + k * NT, ec = e < TT * TT ? e : 0;
-          a1[k] = ec / TT;
-          a2[k] = ec - a1[k] * TT;
+          const int e = eb + k * NT, ec = e < TC * TC ? e : 0;
+          a1[k] = ec / TC;
+          a2[k] = ec - a1[k] * TC;
           c[k] = ct[a1[k] * S + a2[k]];
         }
         dct_c_accumulates<T, KB>(c, zc, a1, a2, m0, nr, cosv);
 #pragma unroll
         for (int k = 0; k < KB; ++k)
-          if (eb + k * NT < TT * TT) ct[a1[k] * S + a2[k]] = c[k];
+          if (eb + k * NT < TC * TC) ct[a1[k] * S + a2[k]] = c[k];
       }
     }
     // R0 of the held bins: R[k1][k2] += sum_r cos(k1, m0 + r) yc[r][k2]
@@ -561,8 +575,11 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
           if (rebase) bnd = 2.f * kA * fabsf(Rt.h) * kUp;
         }
         // ---- coefficient (Eq. 5, Eq. 14) ----
-        const float2 n0 = ct[0], n1c = ct[2 * u1 * S], n2c = ct[2 * u2], n3 = ct[2 * u1 * S + 2 * u2];
-        ff nrm = ff_add(ff_add(ff{n0.x, n0.y}, ff{n1c.x, n1c.y}), ff_add(ff{n2c.x, n2c.y}, ff{n3.x, n3.y}));
+        float s1n, s2n;
+        const int f1 = dct_fold<T>(2 * u1, s1n) * S, f2 = dct_fold<T>(2 * u2, s2n);
+        const float2 n0 = ct[0], n1c = ct[f1], n2c = ct[f2], n3 = ct[f1 + f2];
+        ff nrm = ff_add(ff_add(ff{n0.x, n0.y}, ff_sign(ff{n1c.x, n1c.y}, s1n)),
+                        ff_add(ff_sign(ff{n2c.x, n2c.y}, s2n), ff_sign(ff{n3.x, n3.y}, s1n * s2n)));
         nrm = ff_scale(nrm, 0.25f);
         const ff cff = nrm.h > 0.f ? ff_div(ff_mul(gam, Rt), nrm) : ff{0.f, 0.f};
         // ---- record: the trace entry, and the term of the recurrence ----
@@ -611,14 +628,19 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
         const float p = cff.h, c4 = 0.25f * p;
         prevabs = fabsf(p);
         csum += prevabs;
-        const int cp = k2 + u2, cm = abs(k2 - u2);
+        float sgc;
+        const int cp = dct_fold<T>(k2 + u2, sgc), cm = abs(k2 - u2);
         m1k = 0u;
         m2k = 0u;
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
           const int k1 = r0 + j * RS;
-          const int rp = (k1 + u1) * S, rm = abs(k1 - u1) * S;
-          const float sv = (ct[rp + cp].x + ct[rp + cm].x) + (ct[rm + cp].x + ct[rm + cm].x);
+          float sgr;
+          const int rp = dct_fold<T>(k1 + u1, sgr) * S, rm = abs(k1 - u1) * S;
+          // the four entries with their signs: sums of the same shape and
+          // rounding as without the folding (the signs are exact)
+          const float sv = __fmaf_rn(sgr, __fmaf_rn(sgc, ct[rp + cp].x, ct[rp + cm].x),
+                                     __fmaf_rn(sgc, ct[rm + cp].x, ct[rm + cm].x));
           R32[j] = __fmaf_rn(-c4, sv, R32[j]);
           key_insert(m1k, m2k, ew[j] * (R32[j] * R32[j]), j);
         }
@@ -698,8 +720,11 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
         if (ui < 0 || ui >= T * T) ui = 0;  // no comparable value (cannot happen for finite data)
         const int u1 = ui / T, u2 = ui - u1 * T;
         // ---- coefficient (Eq. 5, Eq. 14) ----
-        const float2 n0 = ct[0], n1 = ct[2 * u1 * S], n2 = ct[2 * u2], n3 = ct[2 * u1 * S + 2 * u2];
-        ff nrm = ff_add(ff_add(ff{n0.x, n0.y}, ff{n1.x, n1.y}), ff_add(ff{n2.x, n2.y}, ff{n3.x, n3.y}));
+        float s1n, s2n;
+        const int f1 = dct_fold<T>(2 * u1, s1n) * S, f2 = dct_fold<T>(2 * u2, s2n);
+        const float2 n0 = ct[0], n1 = ct[f1], n2 = ct[f2], n3 = ct[f1 + f2];
+        ff nrm = ff_add(ff_add(ff{n0.x, n0.y}, ff_sign(ff{n1.x, n1.y}, s1n)),
+                        ff_add(ff_sign(ff{n2.x, n2.y}, s2n), ff_sign(ff{n3.x, n3.y}, s1n * s2n)));
         nrm = ff_scale(nrm, 0.25f);
         const ff cff = nrm.h > 0.f ? ff_div(ff_mul(gam, ff{gr.x, gr.y}), nrm) : ff{0.f, 0.f};
         if (tid == 0) {
@@ -708,12 +733,17 @@ __device__ __forceinline__ void forward_block_dct(const FwdArgs& args, int blk, 
         }
         // ---- R[k] -= c/4 sum C[|k1 +- u1|, |k2 +- u2|], and the next best ----
         const ff c4 = ff_scale(cff, 0.25f);
-        const int cp = k2 + u2, cm = abs(k2 - u2);
+        float sgc;
+        const int cp = dct_fold<T>(k2 + u2, sgc), cm = abs(k2 - u2);
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
           const int k1 = r0 + j * RS;
-          const int rp = (k1 + u1) * S, rm = abs(k1 - u1) * S;
-          const float2 a = ct[rp + cp], bq = ct[rp + cm], cq = ct[rm + cp], d = ct[rm + cm];
+          float sgr;
+          const int rp = dct_fold<T>(k1 + u1, sgr) * S, rm = abs(k1 - u1) * S;
+          const float2 ap = ct[rp + cp], bp = ct[rp + cm], cp2 = ct[rm + cp];
+          const float sa = sgr * sgc, sb = sgr;
+          const float2 a = make_float2(ap.x * sa, ap.y * sa), bq = make_float2(bp.x * sb, bp.y * sb);
+          const float2 cq = make_float2(cp2.x * sgc, cp2.y * sgc), d = ct[rm + cm];
           // four-term float-float sum: exact sums of the high parts, low parts added
           const ff s1 = ff_two_sum(a.x, bq.x), s2 = ff_two_sum(cq.x, d.x), s = ff_two_sum(s1.h, s2.h);
           const float lo = ((a.y + bq.y) + (cq.y + d.y)) + (s1.l + s2.l) + s.l;
@@ -818,8 +848,8 @@ __global__ void __launch_bounds__(NT) fofse_forward_dct_kernel(const __grid_cons
 // support shape and outside B usable): C[a1][a2] = sum_m cos(a1, m) zc[m][a2],
 // zc[m][a2] = sum_n w[m][n] cos(a2, n), in float-float.  A CTA owns DCT_TAB_A
 // columns a2 of C: it sums zc for its columns over every row m of L, then its
-// columns of C over m (renormalised every 16 rows); the padding column a2 =
-// 2T - 1 is written as 0.  The same kernel builds the plan's table and the
+// columns of C over m (renormalised every 16 rows), for a1, a2 in [0, T];
+// the padding column a2 = T + 1 is written as 0.  The same kernel builds the plan's table and the
 // per-call table of a call with device-side (rho, gamma), so both hold the
 // same values for the same rho, bit for bit.
 constexpr int DCT_TAB_A = 4;
@@ -829,7 +859,7 @@ template <int T> __host__ __device__ constexpr size_t dct_table_smem() {
 }
 template <int T>
 __global__ void __launch_bounds__(DCT_TAB_NT) fofse_dct_table_kernel(const PlanDev P, float2* out) {
-  constexpr int TT = 2 * T - 1, S = 2 * T, A = DCT_TAB_A, NT = DCT_TAB_NT;
+  constexpr int TC = T + 1, S = T + 2, A = DCT_TAB_A, NT = DCT_TAB_NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];  // 8-byte slots, no TMA
   float2* wsm = reinterpret_cast<float2*>(smem_raw);  // [Ls][Ls] masked w
   float2* cosT = wsm + T * T;                         // [4T]
@@ -847,15 +877,15 @@ __global__ void __launch_bounds__(DCT_TAB_NT) fofse_dct_table_kernel(const PlanD
   }
   __syncthreads();
   for (int e = tid; e < Ls * A; e += NT) {
-    const int m = e / A, a2 = min(c0 + e % A, TT - 1);
+    const int m = e / A, a2 = min(c0 + e % A, TC - 1);
     zc[e] = dct_row_sum<T>(wsm + m * Ls, a2, Ls, cosv);
   }
   __syncthreads();
-  for (int e = tid; e < TT * A; e += NT) {
+  for (int e = tid; e < TC * A; e += NT) {
     const int a1 = e / A, j = e - a1 * A, a2 = c0 + j;
     if (a2 >= S) continue;
     float2 c = make_float2(0.f, 0.f);
-    if (a2 < TT) {
+    if (a2 < TC) {
       ff acc = {0.f, 0.f};
       for (int m0 = 0; m0 < Ls; m0 += 16) {
         for (int m = m0; m < min(m0 + 16, Ls); ++m) {
@@ -873,7 +903,7 @@ __global__ void __launch_bounds__(DCT_TAB_NT) fofse_dct_table_kernel(const PlanD
 template <int T> cudaError_t build_dct_table_T(const PlanDev& p, float2* out, cudaStream_t s) {
   constexpr size_t sm = dct_table_smem<T>();
   static_assert(sm <= 48 * 1024, "table kernel shared memory");
-  constexpr int grid = (2 * T + DCT_TAB_A - 1) / DCT_TAB_A;  // the S columns of C
+  constexpr int grid = (T + 2 + DCT_TAB_A - 1) / DCT_TAB_A;  // the S columns of the table
   fofse_dct_table_kernel<T><<<grid, DCT_TAB_NT, sm, s>>>(p, out);
   return cudaGetLastError();
 }
@@ -1112,7 +1142,7 @@ cudaError_t launch_forward_dct(const FwdArgs& a, cudaStream_t s) {
 
 int forward_dct_variant_count(const PlanDev& p) { return (p.T == 32 || p.T == 64) ? 2 : 1; }
 
-size_t dct_table_elems(int T) { return (size_t)(2 * T - 1) * 2 * T; }
+size_t dct_table_elems(int T) { return (size_t)(T + 1) * (T + 2); }
 
 cudaError_t build_dct_table(const PlanDev& p, float2* out, cudaStream_t s) {
   if (p.T == 32) return build_dct_table_T<32>(p, out, s);
