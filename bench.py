@@ -1254,6 +1254,10 @@ def main():
         return float(10 * np.log10(255.0 ** 2 / np.mean(e * e)))
     dct = {"ms_per_step": dt / 3, "blocks_per_s": n / (dt / 3 * 1e-3), "psnr_db": psnr_b(ob),
            "kernel": "fofse_forward_dct_kernel<64,256,1> (FP32 working spectrum, exact decisions)"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # every block against the oracle's DCT basis (spatial re-projection)
+        wl_dct = dataclasses.replace(wl, plans=[dataclasses.replace(p, basis=1) for p in wl.plans])
+        dct["parity"] = parity_summary(wl_dct, ob, tr, st)
     # its backward (frozen-path adjoint of the squared error over B)
     dgf = torch.zeros_like(frame)
     dgrg = torch.zeros((len(dplans), 2), dtype=torch.float32, device=dev)
